@@ -1,0 +1,410 @@
+#!/usr/bin/env python3
+"""Training throughput of gradient-optimised NEP on one GB300.
+
+One step = the whole hot path over one batch: descriptors, network, energies,
+forces, virials, loss, the exact gradient w.r.t. every parameter, and an Adam
+update with the Eq. 17 learning rate, captured once as a CUDA graph and
+replayed.  The workload is 256 synthetic Sb/Te structures of 32-400 atoms
+(perturbed rocksalt, liquid-like and strained cells in equal thirds),
+n_max 8/8, basis 12/12, l_max 4 with the 4-body term, 50 hidden neurons,
+labels from a random teacher model of the same shape.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gnep|reference]
+
+Prints one JSON line (rank 0).  The neighbour build is done once before the
+timed region (structures are fixed during training) and is reported apart.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "training atoms/sec per loss+grad step (E+F+V) at stated force error; % of roofline"
+UNIT = "atoms/s"
+WORKLOAD = dict(workload="sbte_256_structures_32-400_atoms_nmax8_basis12_lmax4_4body_h50",
+                n_struct=256, size_range=[32, 400], phases="rocksalt/liquid/strained thirds",
+                n_max=[8, 8], basis=[12, 12], l_max=4, four_body=True, hidden=50,
+                rc=[7.0, 4.0], batch="full (one step = all 256 structures)")
+MODEL_KW = dict(n_max=(8, 8), basis=(12, 12), hidden=50, four_body=True)
+LAMBDAS = dict(lambda_e=1.0, lambda_f=1.0, lambda_v=0.1)
+L2_BYTES = 129 * 1024 * 1024
+
+
+# ----------------------------------------------------------------- FLOP model
+
+def algo_flops(nqr=9, kr=13, nqa=9, ka=13, ns=2, H=50, fb=True, N=1, PR=1, PA=1):
+    """Algorithmic FP32 FLOPs per launch of each kernel (FMA = 2, add/mul = 1,
+    sqrt / reciprocal / sincos / tanh = 1).  Counts what the formulation needs
+    once per unit (pair or atom), not what an implementation repeats."""
+    D = nqr + 4 * nqa + (nqa if fb else 0)
+    geo = 10                        # |r|^2, sqrt, 1/r, unit vector
+    basis_f = 5 * ka + 8            # xi, cut-off, Chebyshev recursion, f_k
+    basis_fd = 12 * ka + 15         # ... and df_k/dr
+    harm = 40                       # 24 B_lm from the unit vector
+    harm_g = 384                    # B_lm and projected gradients
+    u = 18                          # u_ij = (a_j - a_i) + B_s r_ij
+    q4 = 60 if fb else 0
+    f = {}
+    f["desc_radial"] = PR * (6 * kr + 8) + N * 2 * ns * kr * nqr
+    f["desc_angular"] = PA * (geo + basis_f + harm + nqa * (2 * ka + 48)) + N * nqa * (48 + q4)
+    f["mlp_fwd"] = N * (4 * D * H + 6 * H + 2 * D)
+    f["shat"] = N * nqa * (72 + (80 if fb else 0))
+    f["force_radial"] = PR * (14 * kr + 19) + N * 2 * nqr * ns * kr
+    f["force_angular"] = PA * (geo + basis_fd + harm_g + nqa * (4 * ka + 201))
+    f["force_gather"] = (PR + PA) * 21
+    f["tangent_radial"] = PR * (14 * kr + 39) + N * 2 * ns * kr * nqr
+    f["tangent_angular"] = PA * (u + geo + basis_fd + harm_g + nqa * (4 * ka + 240)) + N * nqa * (48 + q4)
+    f["mlp_bwd"] = N * (4 * D * H + 8 * H + D)
+    f["cgrad_angular"] = PA * (u + geo + basis_fd + harm_g + nqa * (294 + 4 * ka)) + N * nqa * 24 * 6
+    f["reduce_W0"] = N * 4 * H * D
+    f["reduce_cR"] = N * 4 * nqr * ns * kr
+    return f
+
+
+# ----------------------------------------------------------------- helpers
+
+def csrc_sha() -> str:
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2507_00528_gb300", "csrc", "*"))):
+        h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(kernel: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    for p in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        txt = open(p).read()
+        m1 = re.search(r"^kernel:\s*(\S+)", txt, re.M)
+        m2 = re.search(r"^source_sha:\s*(\S+)", txt, re.M)
+        m3 = re.search(r"^dram_bytes_per_launch_full_workload:\s*([0-9.eE+]+)", txt, re.M)
+        if m1 and m2 and m3 and m1.group(1) == kernel and m2.group(1) == csrc_sha():
+            return float(m3.group(1))
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, ident: str):
+        self.ident = ident
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.ident}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# ----------------------------------------------------------------- oracle leg
+
+def oracle_sample_step(batch, seconds: float, steps: int = 1):
+    """Time the FP64 oracle (loss + explicit gradient + Adam) on a bounded
+    sample of the workload: the smallest structures whose estimated cost fits
+    in `seconds` per step."""
+    import oracle as O
+    from paper_2507_00528_gb300 import synth
+    cfg = O.Cfg(nq_r=9, nq_a=9, k_r=13, k_a=13, hidden=50, four_body=True)
+    sizes = batch.sizes()
+    per_atom = 0.07  # s/atom, measured order of magnitude for this shape
+    budget = max(1, int(seconds / per_atom))
+    idx, tot = [], 0
+    for s in np.argsort(sizes):  # smallest first keeps the sample bounded
+        if tot + sizes[s] > budget and idx:
+            break
+        idx.append(int(s))
+        tot += int(sizes[s])
+    sb = batch.subset(sorted(idx))
+    T = synth.uniform_params(cfg.n_params, 12).astype(np.float64)
+    P = synth.uniform_params(cfg.n_params, 11).astype(np.float64)
+    s = O.descriptor_scale(cfg, T, sb)
+    y = O.teacher_labels(cfg, T, s, sb, **LAMBDAS)
+    m = np.zeros_like(P); v = np.zeros_like(P)
+    times = []
+    for k in range(steps):
+        t0 = time.perf_counter()
+        _, g = O.loss_grad(cfg, P, s, sb, y)
+        O.adam(P, m, v, g, k + 1, 1e-3)
+        times.append(time.perf_counter() - t0)
+    return sb.n_atoms, len(idx), times
+
+
+def run_reference(args):
+    from paper_2507_00528_gb300 import synth
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    batch = synth.make_config(2)
+    per_step = 3.0  # seconds of oracle work per step
+    n_atoms, n_s, times = oracle_sample_step(batch, per_step, args.warmup + args.steps)
+    times = times[args.warmup:]
+    total = sum(times)
+    value = n_atoms * args.steps / total
+    sample = f"{n_s} smallest structures of the workload ({n_atoms} atoms) per step, FP64 explicit-route oracle"
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": dict(WORKLOAD),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- GPU leg
+
+def run_gnep(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2507_00528_gb300 import build as gbuild
+    gbuild.build()
+    from paper_2507_00528_gb300 import gnep, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    # per-rank workload: the same shape, independent structures (weak scaling)
+    batch = synth.make_config(2, seed=None if rank == 0 else 20250702 + 1000 * rank)
+    n_atoms = batch.n_atoms
+
+    teacher = gnep.GNEP(**MODEL_KW, seed=12)
+    dbatch = gnep.DeviceBatch.from_host(batch)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    nl = teacher.neighbors(dbatch)
+    torch.cuda.synchronize()
+    nbuild_ms = 1e3 * (time.perf_counter() - t0)
+    PR, PA = nl.info()
+    teacher.compute_scale(nl)
+    scale = teacher.get_scale()
+    sizes = batch.sizes()
+    y = teacher.teacher_labels(nl, sizes, **LAMBDAS)
+    student = gnep.GNEP(**MODEL_KW, seed=11, precision=args.precision)
+    student.set_scale(scale)
+
+    n_total = args.warmup + args.steps + 10
+    graph = gnep.TrainGraph(student, nl, y, 1e-3, 1e-5, 2, n_total)
+    stream = graph.stream
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        graph.launch()
+    torch.cuda.synchronize()
+    loss0 = graph.loss.cpu().numpy().copy()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    props = torch.cuda.get_device_properties(local)
+    uuid = str(getattr(props, "uuid", "") or "")
+    ident = ("GPU-" + uuid) if uuid and not uuid.startswith("GPU-") else (uuid or str(local))
+    with ClockSampler(ident) as clk:
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()  # evict L2 between steps (outside the timed events)
+                ev[k][0].record(stream)
+                graph.launch(stream)
+                ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    loss_end = graph.loss.cpu().numpy().copy()
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = t.item()
+        a = torch.tensor([n_atoms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(a)
+        atoms_all = a.item()
+    else:
+        atoms_all = n_atoms
+    value = atoms_all * args.steps / (total_ms / 1e3)
+    student.sync_status()
+
+    # per-kernel durations (CUDA events between launches, eager step)
+    stage_ms = {}
+    reps = 5
+    for _ in range(reps):
+        for name, ms in student_profile(student, nl, y, gnep):
+            stage_ms[name] = stage_ms.get(name, 0.0) + ms / reps
+    fl = algo_flops(N=n_atoms, PR=PR, PA=PA)
+    kernels = {k: v for k, v in stage_ms.items() if k in fl}
+    dom = max(kernels, key=kernels.get)
+    peaks = measured_peaks()
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
+    achieved = fl[dom] / (stage_ms[dom] / 1e3) / 1e12
+    step_flops = sum(fl.values())
+    clocks = clk.summary()
+
+    # end to end through the C ABI with host buffers: H2D of the structures and
+    # labels from pinned memory, neighbour rebuild, loss + gradient, Adam, D2H loss
+    e2e = run_e2e(student, nl, batch, y, args, gnep, torch)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        n_s_atoms, n_s, times = oracle_sample_step(batch, args.cpu_seconds, 1)
+        cpu = {"value": n_s_atoms / times[0], "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{n_s} smallest structures of the workload ({n_s_atoms} atoms), one full step "
+                         f"(FP64 loss + explicit-route gradient + Adam), {times[0]:.1f} s"}
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(WORKLOAD, atoms_per_step_per_gpu=n_atoms, radial_pairs=PR, angular_pairs=PA,
+                       graph=True, precision=args.precision, l2="flushed between steps (256 MB write)",
+                       neighbor_build_ms=round(nbuild_ms, 3)),
+        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32_peak,
+                     "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                     "traffic": committed_traffic(dom),
+                     "peak_source": f"FP32 {props.multi_processor_count} SMs x 128 lanes x 2 x {sm_max:.0f} MHz",
+                     "kernel_ms": stage_ms[dom], "kernel_algo_flops": fl[dom],
+                     "step_algo_gflop": step_flops / 1e9,
+                     "step_achieved_tflops": step_flops / (total_ms / args.steps / 1e3) / 1e12},
+        "kernel_ms": {k: round(v, 5) for k, v in stage_ms.items()},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": args.steps * len(stage_ms) - args.steps * sum(1 for k in stage_ms if k.startswith("memset")),
+        "clocks": clocks,
+        "loss": {"after_warmup": loss0.tolist(), "end": loss_end.tolist()},
+        "source_sha": csrc_sha(),
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def student_profile(student, nl, y, gnep):
+    import ctypes as C
+    L = gnep._lib.load()
+    ms = (C.c_float * 64)()
+    n = C.c_int32()
+    yc = y.c()
+    gnep.check(L.gnep_profile_step(student.h, nl.h, C.byref(yc), ms, 64, C.byref(n), gnep._stream()))
+    return [(L.gnep_profile_stage_name(i).decode(), ms[i]) for i in range(n.value)]
+
+
+def run_e2e(student, nl, batch, y, args, gnep, torch):
+    import ctypes as C
+    L = gnep._lib.load()
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    h_off = pin(batch.struct_off.astype(np.int32))
+    h_pos = pin(batch.pos.astype(np.float64))
+    h_typ = pin(batch.types.astype(np.int32))
+    h_cell = pin(batch.cell.astype(np.float64))
+    h_e = y.energy.cpu().pin_memory()
+    h_f = y.force.cpu().pin_memory()
+    h_v = y.virial.cpu().pin_memory()
+    h_loss = torch.zeros(4, dtype=torch.float64).pin_memory()
+    cb = gnep._lib.Batch(batch.n_struct, batch.n_atoms, h_off.data_ptr(), h_pos.data_ptr(), h_typ.data_ptr(),
+                         h_cell.data_ptr())
+    yc = gnep._lib.Labels(h_e.data_ptr(), h_f.data_ptr(), h_v.data_ptr(), y.lambda_e, y.lambda_f, y.lambda_v,
+                          y.lambda_l2, y.loss_form)
+    st = torch.cuda.Stream()
+    s = C.c_void_p(st.cuda_stream)
+    steps = max(3, min(args.steps, 10))
+
+    def one():
+        gnep.check(L.gnep_rebuild_neighbors(student.h, C.byref(cb), nl.h, s))
+        gnep.check(L.gnep_loss_grad(student.h, nl.h, C.byref(yc), C.c_void_p(h_loss.data_ptr()), None, s))
+        gnep.check(L.gnep_adam_step(student.h, 1e-4, 0.9, 0.999, 1e-8, 0.0, s))
+
+    one()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one()
+    st.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    h2d = sum(t.numel() * t.element_size() for t in (h_off, h_pos, h_typ, h_cell, h_e, h_f, h_v))
+    return {"value": batch.n_atoms / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(h_loss.numel() * 8), "ms_per_step": 1e3 * dt, "steps": steps,
+            "includes": "H2D structures+labels (pinned), neighbour rebuild, loss+gradient, Adam, D2H loss"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gnep", choices=["gnep", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gnep(args)
+
+
+if __name__ == "__main__":
+    main()

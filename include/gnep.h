@@ -1,0 +1,233 @@
+/*
+ * gnep.h -- C ABI of libgnep, gradient-optimised NEP training on one sm_103a GPU.
+ *
+ * The library evaluates, for a packed batch of periodic structures, the NEP
+ * descriptor (radial Chebyshev terms, Eqs. 5-6 with App. A; angular terms from
+ * real solid harmonics with l <= 4, Eqs. 7-8 with App. B; an optional 4-body
+ * term), a one-hidden-layer tanh network per element (D1.1), energies, forces
+ * and virials (Eqs. 1, 3, 4), the weighted energy/force/virial loss (Eqs. 9-12)
+ * and its exact gradient with respect to every network weight and descriptor
+ * coefficient c_nk^IJ (Eqs. 13-16, D1.18-D1.21), then an Adam update with the
+ * warm-up + cosine learning rate of Eq. 17.  Every step runs in the library's
+ * own CUDA kernels; there is no CPU fallback.
+ *
+ * Conventions for every entry point:
+ *  - Return value: GNEP_OK (0) on success, a negative gnep_status otherwise;
+ *    gnep_last_error() then gives a message (thread-local, valid until the next
+ *    call on the same thread).
+ *  - Pointers to arrays may be host or device memory; the library tells them
+ *    apart (cudaPointerGetAttributes).  Host inputs are copied to library-owned
+ *    device memory on `stream`; host outputs are written by a copy on `stream`
+ *    that has completed when the call returns.  Device outputs are written
+ *    asynchronously on `stream`.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *    ordered on it; the library never synchronises the device except where a
+ *    host output or a size is needed (documented per call).
+ *  - The library owns models, neighbour lists and their workspaces; the caller
+ *    owns every batch, label and output buffer.
+ *  - Errors detected inside kernels (non-finite loss) set a device flag that
+ *    gnep_sync_status() reports; a step whose loss is not finite leaves the
+ *    parameters unchanged.
+ *  - Positions are Cartesian (A) and must lie inside their cell (fractional
+ *    coordinates in [0, 1)).  Cells are row vectors a, b, c.
+ */
+#ifndef GNEP_H
+#define GNEP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GNEP_ABI_VERSION 1
+
+typedef enum {
+  GNEP_OK = 0,
+  GNEP_ERR_INVALID_ARG = -1,       /* bad argument or inconsistent sizes */
+  GNEP_ERR_OOM = -2,               /* device or host allocation failed */
+  GNEP_ERR_CUDA = -3,              /* a CUDA runtime call failed */
+  GNEP_ERR_NEIGHBOR_OVERFLOW = -4, /* more pairs than 32-bit indices hold */
+  GNEP_ERR_NONFINITE = -5,         /* loss or gradient not finite; step skipped */
+  GNEP_ERR_TIMEOUT = -6,           /* a bounded device-side wait gave up */
+  GNEP_ERR_CHECKPOINT_CORRUPT = -7,/* checkpoint failed validation */
+  GNEP_ERR_UNSUPPORTED = -8        /* hyper-parameters without a compiled kernel */
+} gnep_status;
+
+/* Arithmetic of the network contractions (descriptors and reductions stay
+ * FP32/FP64 in every mode). */
+enum { GNEP_PREC_FP32 = 0, GNEP_PREC_TF32 = 1, GNEP_PREC_BF16 = 2 };
+/* GNEP_LOSS_MSE: Eq. 9 with Eqs. 10-12.  GNEP_LOSS_RMSE: the same weighted sum
+ * of the square roots of Eqs. 10-12. */
+enum { GNEP_LOSS_MSE = 0, GNEP_LOSS_RMSE = 1 };
+/* Neighbour list selector for gnep_nlist_export. */
+enum { GNEP_LIST_RADIAL = 0, GNEP_LIST_ANGULAR = 1 };
+
+typedef struct gnep_model gnep_model; /* opaque */
+typedef struct gnep_nlist gnep_nlist; /* opaque: one batch's geometry, lists, workspace */
+
+/* A packed batch of n_struct periodic structures, n_atoms atoms in total. */
+typedef struct {
+  int32_t n_struct;
+  int32_t n_atoms;
+  const int32_t *struct_off; /* [n_struct+1] strictly increasing atom offsets, [0] = 0 */
+  const double *pos;         /* [n_atoms*3] positions (A), wrapped into the cell */
+  const int32_t *type;       /* [n_atoms] species index, 0..n_species-1 */
+  const double *cell;        /* [n_struct*9] cell rows a, b, c (A) */
+} gnep_batch;
+
+/* Labels and loss weights (Eqs. 9-12). */
+typedef struct {
+  const double *energy; /* [n_struct] per-atom energy E_s/N_s (eV/atom) */
+  const float *force;   /* [n_atoms*3] forces (eV/A) */
+  const double *virial; /* [n_struct*6] per-atom virial W_s/N_s, xx yy zz xy yz zx */
+  double lambda_e, lambda_f, lambda_v; /* Eq. 9 weights */
+  double lambda_l2;     /* L2 term lambda_l2 * sum(theta^2) / N_par */
+  int32_t loss_form;    /* GNEP_LOSS_MSE or GNEP_LOSS_RMSE */
+} gnep_labels;
+
+/* ---------------------------------------------------------------- model */
+
+/* Create a model (Sec. II.B-C; Eq. 6 basis, Eq. 8 harmonics, D1.1 network).
+ * n_species        species count (only 2 has compiled kernels in this build)
+ * species_z        [n_species] atomic numbers, informative (may be NULL)
+ * rc_radial/angular cut-offs r_c^R, r_c^A (A), 0 < rc_angular <= rc_radial
+ * n_max_*          descriptors per family are n_max + 1 (n = 0..n_max)
+ * basis_*          basis functions per family are basis + 1 (k = 0..N_bas, Eq. 6)
+ * l_max            angular degree, 4 in this build (B1-B4)
+ * four_body        0/1: add one tr(Q_n^3) descriptor per angular channel n
+ * hidden           hidden neurons N_neu (<= 128)
+ * seed             parameters are drawn U(-0.5, 0.5) from this seed
+ * precision        GNEP_PREC_* for the network contractions
+ * Errors: INVALID_ARG, UNSUPPORTED (no kernel for this shape), CUDA, OOM. */
+int gnep_create(gnep_model **out, int n_species, const int *species_z,
+                double rc_radial, double rc_angular, int n_max_radial,
+                int n_max_angular, int basis_radial, int basis_angular,
+                int l_max, int four_body, int hidden, uint64_t seed,
+                int precision);
+int gnep_destroy(gnep_model *m);
+int gnep_set_precision(gnep_model *m, int precision);
+
+/* Parameter count and descriptor length N_des = N_q^R + N_q^A l_max (+ N_q^A). */
+int gnep_num_params(const gnep_model *m, int64_t *n);
+int gnep_num_descriptors(const gnep_model *m, int32_t *n);
+
+/* Parameter vector (FP32, n = gnep_num_params) in this layout:
+ *   for each species e: W0[hidden][N_des] (D1.2), b0[hidden], w1[hidden], b1
+ *   then c^R[I][J][n][k] (Eq. 6, radial) then c^A[I][J][n][k] (angular).
+ * get: synchronises `stream` when dst is host memory. */
+int gnep_get_params(gnep_model *m, float *dst, int64_t n, void *stream);
+int gnep_set_params(gnep_model *m, const float *src, int64_t n, void *stream);
+
+/* Fixed per-component input scale s (the network sees s_v G_v; not trained).
+ * compute: s_v = 1 / (max_v - min_v) over the batch's atoms with the model's
+ * current coefficients (1 where max = min); synchronises `stream`. */
+int gnep_set_descriptor_scale(gnep_model *m, const float *scale, int32_t n, void *stream);
+int gnep_get_descriptor_scale(gnep_model *m, float *scale, int32_t n, void *stream);
+int gnep_compute_descriptor_scale(gnep_model *m, const gnep_nlist *nl, void *stream);
+
+/* ------------------------------------------------------------ neighbours */
+
+/* Build the radial and angular neighbour sets of Eq. 2 (|r_j + n.H - r_i| < r_c,
+ * every periodic image n, j != i or n != 0) for a batch, in canonical order
+ * (j ascending, then image shift lexicographic), with FP64 distance tests that
+ * round exactly like a plain FP64 evaluation without fused multiply-add.  The
+ * nlist keeps a device copy of the batch and the per-step workspace; structures
+ * are fixed while it lives.  Synchronises `stream` (the pair count sizes the
+ * lists).  Errors: INVALID_ARG (sizes, types, wrapping), NEIGHBOR_OVERFLOW,
+ * OOM, CUDA. */
+int gnep_build_neighbors(gnep_model *m, const gnep_batch *b, gnep_nlist **out,
+                         void *stream);
+/* Rebuild `nl` in place for a batch of the same n_struct and n_atoms (new
+ * positions, cells or species); grows the lists only if the pair count grows. */
+int gnep_rebuild_neighbors(gnep_model *m, const gnep_batch *b, gnep_nlist *nl,
+                           void *stream);
+int gnep_nlist_destroy(gnep_nlist *nl);
+int gnep_nlist_info(const gnep_nlist *nl, int64_t *n_pairs_radial,
+                    int64_t *n_pairs_angular);
+/* Copy one list out: off [n_atoms+1], j [pairs] (global atom index),
+ * shift [pairs*3] image (na, nb, nc).  Synchronises when any pointer is host. */
+int gnep_nlist_export(const gnep_nlist *nl, int which, int32_t *off, int32_t *j,
+                      int32_t *shift, void *stream);
+
+/* ---------------------------------------------------------- evaluation */
+
+/* Unscaled descriptors G [n_atoms][N_des] (Eqs. 5-8 and the 4-body term),
+ * radial n first, then angular (n, l) n-major, then 4-body n. */
+int gnep_descriptors(gnep_model *m, const gnep_nlist *nl, float *G, void *stream);
+
+/* Energies, forces and virials (Eqs. 1, 3, 4).  Any output may be NULL.
+ * E_atom [n_atoms] site energies; E_struct [n_struct] totals; F [n_atoms*3];
+ * W_struct [n_struct*6] total virial, symmetrised, xx yy zz xy yz zx. */
+int gnep_forward(gnep_model *m, const gnep_nlist *nl, float *E_atom,
+                 double *E_struct, float *F, double *W_struct, void *stream);
+
+/* Loss and exact parameter gradient of one training step (Eqs. 9-16,
+ * D1.18-D1.21).  loss_terms [4] = {L, L_e, L_f, L_v} (L_x are Eqs. 10-12, L the
+ * weighted total); grad [n_params] (may be NULL: the gradient stays in the
+ * model for gnep_adam_step).  Both may be NULL.  Labels may be host or device
+ * memory (host labels are staged on `stream`). */
+int gnep_loss_grad(gnep_model *m, const gnep_nlist *nl, const gnep_labels *y,
+                   double *loss_terms, float *grad, void *stream);
+
+/* Adam update (Kingma & Ba, bias-corrected; AdamW decay if weight_decay > 0)
+ * with the model's last gradient.  The update count t lives in device memory
+ * and advances by one per call.  lr is used as given. */
+int gnep_adam_step(gnep_model *m, double lr, double beta1, double beta2,
+                   double eps, double weight_decay, void *stream);
+/* Same, with the learning rate of Eq. 17 evaluated on the device from the
+ * update count (s = t before the update), so the call can be replayed inside a
+ * captured CUDA graph. */
+int gnep_adam_step_scheduled(gnep_model *m, double lr_start, double lr_stop,
+                             int64_t n_warmup, int64_t n_total, double beta1,
+                             double beta2, double eps, double weight_decay,
+                             void *stream);
+int gnep_get_step(gnep_model *m, int64_t *t, void *stream);
+
+/* Eq. 17: linear warm-up from lr_stop to lr_start over n_warmup steps, then a
+ * cosine decay to lr_stop at n_total.  Host-side scalar. */
+double gnep_lr_schedule(double lr_start, double lr_stop, int64_t s,
+                        int64_t n_warmup, int64_t n_total);
+
+/* One training step captured once as a CUDA graph and replayed: loss_grad then
+ * adam_step_scheduled.  loss_out is a device pointer [4] written each replay.
+ * The nlist, labels (device pointers) and loss_out must outlive the graph. */
+typedef struct gnep_graph gnep_graph;
+int gnep_graph_create(gnep_model *m, const gnep_nlist *nl, const gnep_labels *y,
+                      double *loss_out, double lr_start, double lr_stop,
+                      int64_t n_warmup, int64_t n_total, double beta1,
+                      double beta2, double eps, double weight_decay,
+                      void *stream, gnep_graph **out);
+int gnep_graph_launch(gnep_graph *g, void *stream);
+int gnep_graph_destroy(gnep_graph *g);
+
+/* ------------------------------------------------------------ profiling */
+
+/* Run one training step eagerly (loss_grad, then an Adam update with lr 1e-4)
+ * with a CUDA event recorded after every launch on `stream`, and return the
+ * duration of each launch in stage_ms [cap]; n_stages receives the count.
+ * The step changes the parameters like any step.  Synchronises `stream`.
+ * Not for concurrent use from several threads. */
+int gnep_profile_step(gnep_model *m, const gnep_nlist *nl, const gnep_labels *y,
+                      float *stage_ms, int32_t cap, int32_t *n_stages, void *stream);
+/* Name of stage i of the last gnep_profile_step ("" when out of range). */
+const char *gnep_profile_stage_name(int32_t i);
+
+/* ------------------------------------------------------- state, errors */
+
+/* Checkpoint: header (shape, parameter count, update count), FP32 parameters,
+ * descriptor scale, Adam moments, CRC32.  load validates the header against the
+ * model and the CRC; a mismatch returns CHECKPOINT_CORRUPT and leaves the model
+ * unchanged.  Both synchronise the device. */
+int gnep_save(gnep_model *m, const char *path);
+int gnep_load(gnep_model *m, const char *path);
+
+/* Synchronise `stream`, read and clear the model's device error flag. */
+int gnep_sync_status(gnep_model *m, void *stream);
+const char *gnep_last_error(void);
+int gnep_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

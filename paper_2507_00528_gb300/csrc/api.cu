@@ -1,0 +1,703 @@
+// C ABI of libgnep: models, neighbour lists, one training step, Adam, graphs,
+// checkpoints and error reporting.  See include/gnep.h for the contract.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gnep_internal.h"
+
+using namespace gnep;
+
+namespace gnep {
+
+static thread_local std::string g_last_error;
+
+int set_error(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int cuda_error(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? GNEP_ERR_OOM : GNEP_ERR_CUDA;
+}
+
+}  // namespace gnep
+
+namespace {
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Copy to a caller buffer (host or device); host destinations are complete on return.
+int copy_out(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  if (!dst || bytes == 0) return GNEP_OK;
+  GNEP_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st));
+  if (!is_device_ptr(dst)) GNEP_CUDA(cudaStreamSynchronize(st));
+  return GNEP_OK;
+}
+
+uint64_t splitmix64(uint64_t& s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+}  // namespace
+
+namespace gnep {
+
+void free_workspace(gnep_nlist* nl) {
+  if (nl->ws_mem) cudaFree(nl->ws_mem);
+  nl->ws_mem = nullptr;
+  nl->ws = Workspace();
+  nl->ws_pairs[0] = nl->ws_pairs[1] = -1;
+}
+
+int alloc_workspace(gnep_model* m, gnep_nlist* nl) {
+  if (nl->ws_mem && nl->ws_pairs[0] >= nl->L[0].n && nl->ws_pairs[1] >= nl->L[1].n) return GNEP_OK;
+  free_workspace(nl);
+  const Shape& s = m->shape;
+  const size_t N = nl->n_atoms > 0 ? nl->n_atoms : 1, S = nl->n_struct;
+  const size_t PR = nl->L[0].n > 0 ? nl->L[0].n : 1, PA = nl->L[1].n > 0 ? nl->L[1].n : 1;
+  const size_t D = s.ndes, H = s.H, A24 = (size_t)s.nqa * 24, FRn = (size_t)s.ns * s.kr;
+  struct Item { void** p; size_t bytes; };
+  Workspace& w = nl->ws;
+  w.red_len = loss_partial_doubles();
+  w.part_len = grad_partial_floats(m, nl->n_atoms);
+  std::vector<Item> items = {
+      {(void**)&w.G, 4 * N * D},        {(void**)&w.Ep, 4 * N * D},       {(void**)&w.X, 4 * N * H},
+      {(void**)&w.Eatom, 4 * N},        {(void**)&w.S, 4 * N * A24},      {(void**)&w.FR, 4 * N * FRn},
+      {(void**)&w.Shat, 4 * N * A24},   {(void**)&w.dR, 16 * PR},         {(void**)&w.dA, 16 * PA},
+      {(void**)&w.F, 12 * N},           {(void**)&w.Wat, 24 * N},         {(void**)&w.Es, 8 * S},
+      {(void**)&w.Ws, 48 * S},          {(void**)&w.a, 16 * N},           {(void**)&w.es, 4 * S},
+      {(void**)&w.Bs, 24 * S},          {(void**)&w.Gd, 4 * N * D},       {(void**)&w.Sd, 4 * N * A24},
+      {(void**)&w.FRd, 4 * N * FRn},    {(void**)&w.Gb, 4 * N * D},       {(void**)&w.alpha, 4 * N * H},
+      {(void**)&w.beta, 4 * N * H},     {(void**)&w.q1, 4 * N * H},       {(void**)&w.eatom, 4 * N},
+      {(void**)&w.dcA, 4 * N * s.nqa * s.ns * s.ka},
+      {(void**)&w.red, 8 * (size_t)w.red_len},
+      {(void**)&w.part, 4 * (size_t)w.part_len},
+      {(void**)&w.lab_e, 8 * S},        {(void**)&w.lab_f, 12 * N},       {(void**)&w.lab_v, 48 * S},
+      {(void**)&w.coef, 8 * 8},         {(void**)&w.gradf, 4 * (size_t)m->n_params}};
+  size_t total = 0;
+  for (auto& it : items) total += align256(it.bytes);
+  char* base = nullptr;
+  GNEP_CUDA(cudaMalloc(&base, total));
+  GNEP_CUDA(cudaMemset(base, 0, total));
+  size_t off = 0;
+  for (auto& it : items) {
+    *it.p = base + off;
+    off += align256(it.bytes);
+  }
+  nl->ws_mem = base;
+  nl->ws_pairs[0] = nl->L[0].n;
+  nl->ws_pairs[1] = nl->L[1].n;
+  return GNEP_OK;
+}
+
+}  // namespace gnep
+
+// ======================================================================= API
+
+extern "C" {
+
+const char* gnep_last_error(void) { return gnep::g_last_error.c_str(); }
+int gnep_abi_version(void) { return GNEP_ABI_VERSION; }
+
+int gnep_create(gnep_model** out, int n_species, const int* species_z, double rc_radial, double rc_angular,
+                int n_max_radial, int n_max_angular, int basis_radial, int basis_angular, int l_max,
+                int four_body, int hidden, uint64_t seed, int precision) {
+  (void)species_z;
+  if (!out) return set_error(GNEP_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (n_species < 1 || n_species > 8 || !(rc_radial > 0) || !(rc_angular > 0) || rc_angular > rc_radial ||
+      n_max_radial < 0 || n_max_angular < 0 || basis_radial < 0 || basis_angular < 0 || l_max < 1 ||
+      l_max > 4 || hidden < 1 || hidden > kMaxHidden || precision < 0 || precision > 2)
+    return set_error(GNEP_ERR_INVALID_ARG, "hyper-parameter out of range");
+  Shape s;
+  s.ns = n_species; s.nqr = n_max_radial + 1; s.kr = basis_radial + 1; s.nqa = n_max_angular + 1;
+  s.ka = basis_angular + 1; s.lmax = l_max; s.fb = four_body ? 1 : 0; s.H = hidden;
+  s.ndes = s.nqr + s.nqa * s.lmax + (s.fb ? s.nqa : 0);
+  if (!shape_supported(s))
+    return set_error(GNEP_ERR_UNSUPPORTED,
+                     "no compiled kernel for this shape (built: 2 species, l_max 4, n_max/basis 4/8 without "
+                     "4-body or 8/12 with or without 4-body)");
+  gnep_model* m = new gnep_model();
+  m->shape = s;
+  m->rcr = rc_radial;
+  m->rca = rc_angular;
+  m->precision = precision;
+  m->net_size = s.ndes * s.H + 2 * s.H + 1;
+  m->off_cR = s.ns * m->net_size;
+  m->off_cA = m->off_cR + s.ns * s.ns * s.nqr * s.kr;
+  m->n_params = (int64_t)m->off_cA + (int64_t)s.ns * s.ns * s.nqa * s.ka;
+  cudaGetDevice(&m->device);
+  int rc = shape_setup(s);
+  if (rc) { delete m; return rc; }
+  const size_t n = (size_t)m->n_params;
+  auto fail = [&](cudaError_t e, const char* w) {
+    gnep_destroy(m);
+    return cuda_error(e, w);
+  };
+  cudaError_t e;
+  if ((e = cudaMalloc(&m->params, 4 * n)) != cudaSuccess) return fail(e, "cudaMalloc params");
+  if ((e = cudaMalloc(&m->scale, 4 * (size_t)s.ndes)) != cudaSuccess) return fail(e, "cudaMalloc scale");
+  if ((e = cudaMalloc(&m->adam_m, 4 * n)) != cudaSuccess) return fail(e, "cudaMalloc adam");
+  if ((e = cudaMalloc(&m->adam_v, 4 * n)) != cudaSuccess) return fail(e, "cudaMalloc adam");
+  if ((e = cudaMalloc(&m->grad, 8 * n)) != cudaSuccess) return fail(e, "cudaMalloc grad");
+  if ((e = cudaMalloc(&m->step, sizeof(long long))) != cudaSuccess) return fail(e, "cudaMalloc step");
+  if ((e = cudaMalloc(&m->err, sizeof(int))) != cudaSuccess) return fail(e, "cudaMalloc err");
+  std::vector<float> h(n);
+  uint64_t st = seed;
+  for (size_t q = 0; q < n; ++q) h[q] = (float)((double)(splitmix64(st) >> 11) * 0x1.0p-53 - 0.5);
+  std::vector<float> one(s.ndes, 1.f);
+  cudaMemcpy(m->params, h.data(), 4 * n, cudaMemcpyHostToDevice);
+  cudaMemcpy(m->scale, one.data(), 4 * (size_t)s.ndes, cudaMemcpyHostToDevice);
+  cudaMemset(m->adam_m, 0, 4 * n);
+  cudaMemset(m->adam_v, 0, 4 * n);
+  cudaMemset(m->grad, 0, 8 * n);
+  cudaMemset(m->step, 0, sizeof(long long));
+  if ((e = cudaMemset(m->err, 0, sizeof(int))) != cudaSuccess) return fail(e, "init");
+  *out = m;
+  return GNEP_OK;
+}
+
+int gnep_destroy(gnep_model* m) {
+  if (!m) return GNEP_OK;
+  cudaFree(m->params); cudaFree(m->scale); cudaFree(m->adam_m); cudaFree(m->adam_v);
+  cudaFree(m->grad); cudaFree(m->step); cudaFree(m->err);
+  delete m;
+  return GNEP_OK;
+}
+
+int gnep_set_precision(gnep_model* m, int precision) {
+  if (!m || precision < 0 || precision > 2) return set_error(GNEP_ERR_INVALID_ARG, "bad precision");
+  m->precision = precision;
+  return GNEP_OK;
+}
+
+int gnep_num_params(const gnep_model* m, int64_t* n) {
+  if (!m || !n) return set_error(GNEP_ERR_INVALID_ARG, "NULL argument");
+  *n = m->n_params;
+  return GNEP_OK;
+}
+
+int gnep_num_descriptors(const gnep_model* m, int32_t* n) {
+  if (!m || !n) return set_error(GNEP_ERR_INVALID_ARG, "NULL argument");
+  *n = m->shape.ndes;
+  return GNEP_OK;
+}
+
+int gnep_get_params(gnep_model* m, float* dst, int64_t n, void* stream) {
+  if (!m || !dst || n != m->n_params) return set_error(GNEP_ERR_INVALID_ARG, "bad parameter buffer");
+  return copy_out(dst, m->params, 4 * (size_t)n, (cudaStream_t)stream);
+}
+
+int gnep_set_params(gnep_model* m, const float* src, int64_t n, void* stream) {
+  if (!m || !src || n != m->n_params) return set_error(GNEP_ERR_INVALID_ARG, "bad parameter buffer");
+  GNEP_CUDA(cudaMemcpyAsync(m->params, src, 4 * (size_t)n, cudaMemcpyDefault, (cudaStream_t)stream));
+  if (!is_device_ptr(src)) GNEP_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  return GNEP_OK;
+}
+
+int gnep_set_descriptor_scale(gnep_model* m, const float* scale, int32_t n, void* stream) {
+  if (!m || !scale || n != m->shape.ndes) return set_error(GNEP_ERR_INVALID_ARG, "bad scale buffer");
+  GNEP_CUDA(cudaMemcpyAsync(m->scale, scale, 4 * (size_t)n, cudaMemcpyDefault, (cudaStream_t)stream));
+  if (!is_device_ptr(scale)) GNEP_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  return GNEP_OK;
+}
+
+int gnep_get_descriptor_scale(gnep_model* m, float* scale, int32_t n, void* stream) {
+  if (!m || !scale || n != m->shape.ndes) return set_error(GNEP_ERR_INVALID_ARG, "bad scale buffer");
+  return copy_out(scale, m->scale, 4 * (size_t)n, (cudaStream_t)stream);
+}
+
+static int check_nlist(const gnep_model* m, const gnep_nlist* nl) {
+  if (!m || !nl) return set_error(GNEP_ERR_INVALID_ARG, "NULL model or neighbour list");
+  if (!(nl->shape == m->shape) || nl->rcr != m->rcr || nl->rca != m->rca)
+    return set_error(GNEP_ERR_INVALID_ARG, "neighbour list was built for a model of another shape or cut-off");
+  return GNEP_OK;
+}
+
+int gnep_compute_descriptor_scale(gnep_model* m, const gnep_nlist* nl_, void* stream) {
+  int rc = check_nlist(m, nl_);
+  if (rc) return rc;
+  gnep_nlist* nl = const_cast<gnep_nlist*>(nl_);
+  cudaStream_t st = (cudaStream_t)stream;
+  StepArgs A{m, nl, st};
+  if ((rc = run_descriptors(A, false))) return rc;
+  if ((rc = run_scale(m, nl, st))) return rc;
+  GNEP_CUDA(cudaStreamSynchronize(st));
+  return GNEP_OK;
+}
+
+// --------------------------------------------------------------- batches
+
+static int load_batch(gnep_model* m, const gnep_batch* b, gnep_nlist* nl, cudaStream_t st) {
+  const int S = b->n_struct, N = b->n_atoms;
+  std::vector<int> off(S + 1), typ(N > 0 ? N : 1);
+  GNEP_CUDA(cudaMemcpyAsync(off.data(), b->struct_off, sizeof(int) * (S + 1), cudaMemcpyDefault, st));
+  if (N > 0) GNEP_CUDA(cudaMemcpyAsync(typ.data(), b->type, sizeof(int) * N, cudaMemcpyDefault, st));
+  GNEP_CUDA(cudaStreamSynchronize(st));
+  if (off[0] != 0 || off[S] != N) return set_error(GNEP_ERR_INVALID_ARG, "struct_off must start at 0 and end at n_atoms");
+  for (int s = 0; s < S; ++s)
+    if (off[s + 1] <= off[s])
+      return set_error(GNEP_ERR_INVALID_ARG, "struct_off must be strictly increasing (every structure holds an atom)");
+  for (int i = 0; i < N; ++i)
+    if (typ[i] < 0 || typ[i] >= m->shape.ns) return set_error(GNEP_ERR_INVALID_ARG, "species index out of range");
+  GNEP_CUDA(cudaMemcpyAsync(nl->struct_off, off.data(), sizeof(int) * (S + 1), cudaMemcpyHostToDevice, st));
+  if (N > 0) {
+    GNEP_CUDA(cudaMemcpyAsync(nl->type, typ.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+    GNEP_CUDA(cudaMemcpyAsync(nl->pos, b->pos, sizeof(double) * 3 * (size_t)N, cudaMemcpyDefault, st));
+  }
+  GNEP_CUDA(cudaMemcpyAsync(nl->cell, b->cell, sizeof(double) * 9 * (size_t)S, cudaMemcpyDefault, st));
+  return GNEP_OK;
+}
+
+static int finish_build(gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
+  int rc;
+  if (nl->n_atoms > 0) {
+    if ((rc = build_lists(m, nl, st))) return rc;
+    if ((rc = run_species_perm(nl, st))) return rc;
+  } else {
+    for (int e = 0; e <= m->shape.ns; ++e) nl->species_off[e] = 0;
+    for (int L = 0; L < 2; ++L) {
+      if (!nl->L[L].off) GNEP_CUDA(cudaMalloc(&nl->L[L].off, sizeof(int)));
+      GNEP_CUDA(cudaMemsetAsync(nl->L[L].off, 0, sizeof(int), st));
+      nl->L[L].n = 0;
+    }
+  }
+  if ((rc = alloc_workspace(m, nl))) return rc;
+  GNEP_CUDA(cudaStreamSynchronize(st));
+  return GNEP_OK;
+}
+
+int gnep_nlist_destroy(gnep_nlist* nl) {
+  if (!nl) return GNEP_OK;
+  cudaFree(nl->struct_off); cudaFree(nl->type); cudaFree(nl->pos); cudaFree(nl->cell);
+  cudaFree(nl->atom_struct); cudaFree(nl->perm);
+  for (int L = 0; L < 2; ++L) {
+    PairList& P = nl->L[L];
+    cudaFree(P.off); cudaFree(P.j); cudaFree(P.owner); cudaFree(P.rev); cudaFree(P.rij); cudaFree(P.shift);
+  }
+  free_workspace(nl);
+  delete nl;
+  return GNEP_OK;
+}
+
+int gnep_build_neighbors(gnep_model* m, const gnep_batch* b, gnep_nlist** out, void* stream) {
+  if (!m || !b || !out) return set_error(GNEP_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  if (b->n_struct < 1 || b->n_atoms < 0 || !b->struct_off || !b->cell || (b->n_atoms > 0 && (!b->pos || !b->type)))
+    return set_error(GNEP_ERR_INVALID_ARG, "empty or incomplete batch");
+  cudaStream_t st = (cudaStream_t)stream;
+  gnep_nlist* nl = new gnep_nlist();
+  nl->shape = m->shape;
+  nl->rcr = m->rcr;
+  nl->rca = m->rca;
+  nl->n_struct = b->n_struct;
+  nl->n_atoms = b->n_atoms;
+  cudaGetDevice(&nl->device);
+  const size_t N = b->n_atoms > 0 ? b->n_atoms : 1, S = b->n_struct;
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaMalloc(&nl->struct_off, sizeof(int) * (S + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&nl->type, sizeof(int) * N);
+  if (e == cudaSuccess) e = cudaMalloc(&nl->pos, sizeof(double) * 3 * N);
+  if (e == cudaSuccess) e = cudaMalloc(&nl->cell, sizeof(double) * 9 * S);
+  if (e == cudaSuccess) e = cudaMalloc(&nl->atom_struct, sizeof(int) * N);
+  if (e == cudaSuccess) e = cudaMalloc(&nl->perm, sizeof(int) * N);
+  if (e != cudaSuccess) {
+    gnep_nlist_destroy(nl);
+    return cuda_error(e, "cudaMalloc batch");
+  }
+  int rc = load_batch(m, b, nl, st);
+  if (!rc) rc = finish_build(m, nl, st);
+  if (rc) {
+    gnep_nlist_destroy(nl);
+    return rc;
+  }
+  *out = nl;
+  return GNEP_OK;
+}
+
+int gnep_rebuild_neighbors(gnep_model* m, const gnep_batch* b, gnep_nlist* nl, void* stream) {
+  int rc = check_nlist(m, nl);
+  if (rc) return rc;
+  if (!b || b->n_struct != nl->n_struct || b->n_atoms != nl->n_atoms)
+    return set_error(GNEP_ERR_INVALID_ARG, "rebuild needs the same structure and atom counts");
+  cudaStream_t st = (cudaStream_t)stream;
+  if ((rc = load_batch(m, b, nl, st))) return rc;
+  return finish_build(m, nl, st);
+}
+
+int gnep_nlist_info(const gnep_nlist* nl, int64_t* nr, int64_t* na) {
+  if (!nl) return set_error(GNEP_ERR_INVALID_ARG, "NULL neighbour list");
+  if (nr) *nr = nl->L[0].n;
+  if (na) *na = nl->L[1].n;
+  return GNEP_OK;
+}
+
+namespace {
+__global__ void k_export_shift(int64_t n, const char4* __restrict__ s, int* __restrict__ o) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const char4 v = s[p];
+  o[3 * p] = v.x; o[3 * p + 1] = v.y; o[3 * p + 2] = v.z;
+}
+}  // namespace
+
+int gnep_nlist_export(const gnep_nlist* nl, int which, int32_t* off, int32_t* j, int32_t* shift, void* stream) {
+  if (!nl || which < 0 || which > 1) return set_error(GNEP_ERR_INVALID_ARG, "bad list");
+  cudaStream_t st = (cudaStream_t)stream;
+  const PairList& P = nl->L[which];
+  int rc;
+  if ((rc = copy_out(off, P.off, sizeof(int) * ((size_t)nl->n_atoms + 1), st))) return rc;
+  if (P.n == 0) return GNEP_OK;
+  if ((rc = copy_out(j, P.j, sizeof(int) * (size_t)P.n, st))) return rc;
+  if (shift) {
+    int* tmp = nullptr;
+    GNEP_CUDA(cudaMallocAsync(&tmp, sizeof(int) * 3 * (size_t)P.n, st));
+    k_export_shift<<<blocks_for(P.n, 256), 256, 0, st>>>(P.n, P.shift, tmp);
+    rc = copy_out(shift, tmp, sizeof(int) * 3 * (size_t)P.n, st);
+    cudaFreeAsync(tmp, st);
+    if (rc) return rc;
+  }
+  return GNEP_OK;
+}
+
+// ------------------------------------------------------------ evaluation
+
+int gnep_descriptors(gnep_model* m, const gnep_nlist* nl_, float* G, void* stream) {
+  int rc = check_nlist(m, nl_);
+  if (rc) return rc;
+  gnep_nlist* nl = const_cast<gnep_nlist*>(nl_);
+  cudaStream_t st = (cudaStream_t)stream;
+  StepArgs A{m, nl, st};
+  if ((rc = run_descriptors(A, false))) return rc;
+  return copy_out(G, nl->ws.G, sizeof(float) * (size_t)nl->n_atoms * m->shape.ndes, st);
+}
+
+int gnep_forward(gnep_model* m, const gnep_nlist* nl_, float* E_atom, double* E_struct, float* F,
+                 double* W_struct, void* stream) {
+  int rc = check_nlist(m, nl_);
+  if (rc) return rc;
+  gnep_nlist* nl = const_cast<gnep_nlist*>(nl_);
+  cudaStream_t st = (cudaStream_t)stream;
+  StepArgs A{m, nl, st};
+  if ((rc = run_descriptors(A, true))) return rc;
+  if ((rc = run_forward(A))) return rc;
+  const size_t N = nl->n_atoms, S = nl->n_struct;
+  if ((rc = copy_out(E_atom, nl->ws.Eatom, 4 * N, st))) return rc;
+  if ((rc = copy_out(E_struct, nl->ws.Es, 8 * S, st))) return rc;
+  if ((rc = copy_out(F, nl->ws.F, 12 * N, st))) return rc;
+  return copy_out(W_struct, nl->ws.Ws, 48 * S, st);
+}
+
+static int loss_grad_core(gnep_model* m, gnep_nlist* nl, const gnep_labels* y, cudaStream_t st) {
+  if (!y || (nl->n_struct > 0 && (!y->energy || !y->virial)) || (nl->n_atoms > 0 && !y->force))
+    return set_error(GNEP_ERR_INVALID_ARG, "incomplete labels");
+  if (y->loss_form != GNEP_LOSS_MSE && y->loss_form != GNEP_LOSS_RMSE)
+    return set_error(GNEP_ERR_INVALID_ARG, "unknown loss form");
+  Workspace& w = nl->ws;
+  const size_t N = nl->n_atoms, S = nl->n_struct;
+  const double* le = y->energy;
+  const float* lf = y->force;
+  const double* lv = y->virial;
+  if (!is_device_ptr(le)) { GNEP_CUDA(cudaMemcpyAsync(w.lab_e, le, 8 * S, cudaMemcpyDefault, st)); le = w.lab_e; }
+  if (N > 0 && !is_device_ptr(lf)) { GNEP_CUDA(cudaMemcpyAsync(w.lab_f, lf, 12 * N, cudaMemcpyDefault, st)); lf = w.lab_f; }
+  if (!is_device_ptr(lv)) { GNEP_CUDA(cudaMemcpyAsync(w.lab_v, lv, 48 * S, cudaMemcpyDefault, st)); lv = w.lab_v; }
+  if (N == 0) lf = w.lab_f;
+  StepArgs A{m, nl, st};
+  int rc;
+  if ((rc = run_descriptors(A, true))) return rc;
+  if ((rc = run_forward(A))) return rc;
+  if ((rc = run_loss_impl(m, nl, le, lf, lv, y, st))) return rc;
+  if ((rc = run_backward(A))) return rc;
+  return run_grad_reduce_impl(m, nl, y->lambda_l2, st);
+}
+
+int gnep_loss_grad(gnep_model* m, const gnep_nlist* nl_, const gnep_labels* y, double* loss_terms, float* grad,
+                   void* stream) {
+  int rc = check_nlist(m, nl_);
+  if (rc) return rc;
+  gnep_nlist* nl = const_cast<gnep_nlist*>(nl_);
+  cudaStream_t st = (cudaStream_t)stream;
+  if ((rc = loss_grad_core(m, nl, y, st))) return rc;
+  if (grad) {
+    if (is_device_ptr(grad)) {
+      if ((rc = grad_to_float(m, grad, st))) return rc;
+    } else {
+      if ((rc = grad_to_float(m, nl->ws.gradf, st))) return rc;
+      if ((rc = copy_out(grad, nl->ws.gradf, 4 * (size_t)m->n_params, st))) return rc;
+    }
+  }
+  return copy_out(loss_terms, nl->ws.coef, 4 * sizeof(double), st);
+}
+
+int gnep_adam_step(gnep_model* m, double lr, double beta1, double beta2, double eps, double weight_decay,
+                   void* stream) {
+  if (!m) return set_error(GNEP_ERR_INVALID_ARG, "NULL model");
+  return run_adam(m, nullptr, lr, beta1, beta2, eps, weight_decay, false, 0, 0, 0, 0, (cudaStream_t)stream);
+}
+
+int gnep_adam_step_scheduled(gnep_model* m, double lr_start, double lr_stop, int64_t n_warmup, int64_t n_total,
+                             double beta1, double beta2, double eps, double weight_decay, void* stream) {
+  if (!m || n_warmup < 0 || n_total < n_warmup) return set_error(GNEP_ERR_INVALID_ARG, "bad schedule");
+  return run_adam(m, nullptr, 0.0, beta1, beta2, eps, weight_decay, true, lr_start, lr_stop, n_warmup, n_total,
+                  (cudaStream_t)stream);
+}
+
+int gnep_get_step(gnep_model* m, int64_t* t, void* stream) {
+  if (!m || !t) return set_error(GNEP_ERR_INVALID_ARG, "NULL argument");
+  long long v = 0;
+  GNEP_CUDA(cudaMemcpyAsync(&v, m->step, sizeof(long long), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+  GNEP_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  *t = v;
+  return GNEP_OK;
+}
+
+double gnep_lr_schedule(double lr_start, double lr_stop, int64_t s, int64_t n_warmup, int64_t n_total) {
+  if (s < n_warmup) return lr_stop + (double)s / (double)n_warmup * (lr_start - lr_stop);
+  if (s > n_total) s = n_total;
+  const double span = (double)(n_total - n_warmup);
+  const double frac = span > 0 ? (double)(s - n_warmup) / span : 1.0;
+  return lr_stop + (lr_start - lr_stop) * 0.5 * (1.0 + std::cos(M_PI * frac));
+}
+
+// ----------------------------------------------------------------- graphs
+
+struct gnep_graph {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+};
+
+int gnep_graph_create(gnep_model* m, const gnep_nlist* nl_, const gnep_labels* y, double* loss_out,
+                      double lr_start, double lr_stop, int64_t n_warmup, int64_t n_total, double beta1,
+                      double beta2, double eps, double weight_decay, void* stream, gnep_graph** out) {
+  int rc = check_nlist(m, nl_);
+  if (rc) return rc;
+  if (!out || !y || !stream) return set_error(GNEP_ERR_INVALID_ARG, "graph capture needs labels and a non-default stream");
+  if (!is_device_ptr(y->energy) || !is_device_ptr(y->force) || !is_device_ptr(y->virial) ||
+      (loss_out && !is_device_ptr(loss_out)))
+    return set_error(GNEP_ERR_INVALID_ARG, "graph capture needs device labels and a device loss buffer");
+  gnep_nlist* nl = const_cast<gnep_nlist*>(nl_);
+  cudaStream_t st = (cudaStream_t)stream;
+  GNEP_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  rc = loss_grad_core(m, nl, y, st);
+  if (!rc && loss_out) {
+    if (cudaMemcpyAsync(loss_out, nl->ws.coef, 4 * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      rc = set_error(GNEP_ERR_CUDA, "capture memcpy");
+  }
+  if (!rc) rc = run_adam(m, nullptr, 0.0, beta1, beta2, eps, weight_decay, true, lr_start, lr_stop, n_warmup, n_total, st);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(st, &g);
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture");
+  gnep_graph* gr = new gnep_graph();
+  gr->g = g;
+  e = cudaGraphInstantiate(&gr->ge, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    delete gr;
+    return cuda_error(e, "cudaGraphInstantiate");
+  }
+  *out = gr;
+  return GNEP_OK;
+}
+
+int gnep_graph_launch(gnep_graph* g, void* stream) {
+  if (!g) return set_error(GNEP_ERR_INVALID_ARG, "NULL graph");
+  GNEP_CUDA(cudaGraphLaunch(g->ge, (cudaStream_t)stream));
+  return GNEP_OK;
+}
+
+int gnep_graph_destroy(gnep_graph* g) {
+  if (!g) return GNEP_OK;
+  if (g->ge) cudaGraphExecDestroy(g->ge);
+  if (g->g) cudaGraphDestroy(g->g);
+  delete g;
+  return GNEP_OK;
+}
+
+// ------------------------------------------------------------ checkpoints
+
+namespace {
+uint32_t crc32_update(uint32_t crc, const void* data, size_t n) {
+  static uint32_t table[256];
+  static bool init = false;
+  if (!init) {
+    for (uint32_t i = 0; i < 256; ++i) {
+      uint32_t c = i;
+      for (int k = 0; k < 8; ++k) c = (c & 1) ? 0xEDB88320u ^ (c >> 1) : c >> 1;
+      table[i] = c;
+    }
+    init = true;
+  }
+  const unsigned char* p = (const unsigned char*)data;
+  crc = ~crc;
+  for (size_t i = 0; i < n; ++i) crc = table[(crc ^ p[i]) & 0xFF] ^ (crc >> 8);
+  return ~crc;
+}
+
+struct CkptHeader {
+  char magic[8];
+  uint32_t version;
+  int32_t shape[9];
+  double rcr, rca;
+  int64_t n_params;
+  int64_t step;
+};
+}  // namespace
+
+int gnep_save(gnep_model* m, const char* path) {
+  if (!m || !path) return set_error(GNEP_ERR_INVALID_ARG, "NULL argument");
+  const size_t n = (size_t)m->n_params, d = (size_t)m->shape.ndes;
+  std::vector<float> p(n), mm(n), vv(n), sc(d);
+  CkptHeader h;
+  memset(&h, 0, sizeof(h));
+  memcpy(h.magic, "GNEPCKPT", 8);
+  h.version = 1;
+  const Shape& s = m->shape;
+  const int32_t sh[9] = {s.ns, s.nqr, s.kr, s.nqa, s.ka, s.lmax, s.fb, s.H, s.ndes};
+  memcpy(h.shape, sh, sizeof(sh));
+  h.rcr = m->rcr;
+  h.rca = m->rca;
+  h.n_params = m->n_params;
+  long long stp = 0;
+  GNEP_CUDA(cudaDeviceSynchronize());
+  GNEP_CUDA(cudaMemcpy(p.data(), m->params, 4 * n, cudaMemcpyDeviceToHost));
+  GNEP_CUDA(cudaMemcpy(mm.data(), m->adam_m, 4 * n, cudaMemcpyDeviceToHost));
+  GNEP_CUDA(cudaMemcpy(vv.data(), m->adam_v, 4 * n, cudaMemcpyDeviceToHost));
+  GNEP_CUDA(cudaMemcpy(sc.data(), m->scale, 4 * d, cudaMemcpyDeviceToHost));
+  GNEP_CUDA(cudaMemcpy(&stp, m->step, sizeof(long long), cudaMemcpyDeviceToHost));
+  h.step = stp;
+  uint32_t crc = 0;
+  crc = crc32_update(crc, &h, sizeof(h));
+  crc = crc32_update(crc, p.data(), 4 * n);
+  crc = crc32_update(crc, sc.data(), 4 * d);
+  crc = crc32_update(crc, mm.data(), 4 * n);
+  crc = crc32_update(crc, vv.data(), 4 * n);
+  FILE* f = fopen(path, "wb");
+  if (!f) return set_error(GNEP_ERR_INVALID_ARG, std::string("cannot open ") + path);
+  bool ok = fwrite(&h, sizeof(h), 1, f) == 1 && fwrite(p.data(), 4, n, f) == n && fwrite(sc.data(), 4, d, f) == d &&
+            fwrite(mm.data(), 4, n, f) == n && fwrite(vv.data(), 4, n, f) == n && fwrite(&crc, 4, 1, f) == 1;
+  ok = (fclose(f) == 0) && ok;
+  if (!ok) return set_error(GNEP_ERR_INVALID_ARG, std::string("write failed: ") + path);
+  return GNEP_OK;
+}
+
+int gnep_load(gnep_model* m, const char* path) {
+  if (!m || !path) return set_error(GNEP_ERR_INVALID_ARG, "NULL argument");
+  FILE* f = fopen(path, "rb");
+  if (!f) return set_error(GNEP_ERR_INVALID_ARG, std::string("cannot open ") + path);
+  CkptHeader h;
+  const size_t n = (size_t)m->n_params, d = (size_t)m->shape.ndes;
+  std::vector<float> p(n), mm(n), vv(n), sc(d);
+  uint32_t crc_file = 0;
+  bool ok = fread(&h, sizeof(h), 1, f) == 1;
+  const Shape& s = m->shape;
+  const int32_t sh[9] = {s.ns, s.nqr, s.kr, s.nqa, s.ka, s.lmax, s.fb, s.H, s.ndes};
+  if (ok) ok = memcmp(h.magic, "GNEPCKPT", 8) == 0 && h.version == 1 && memcmp(h.shape, sh, sizeof(sh)) == 0 &&
+               h.n_params == m->n_params && h.rcr == m->rcr && h.rca == m->rca;
+  if (ok) ok = fread(p.data(), 4, n, f) == n && fread(sc.data(), 4, d, f) == d && fread(mm.data(), 4, n, f) == n &&
+               fread(vv.data(), 4, n, f) == n && fread(&crc_file, 4, 1, f) == 1;
+  char extra;
+  if (ok) ok = fread(&extra, 1, 1, f) == 0;
+  fclose(f);
+  if (ok) {
+    uint32_t crc = 0;
+    crc = crc32_update(crc, &h, sizeof(h));
+    crc = crc32_update(crc, p.data(), 4 * n);
+    crc = crc32_update(crc, sc.data(), 4 * d);
+    crc = crc32_update(crc, mm.data(), 4 * n);
+    crc = crc32_update(crc, vv.data(), 4 * n);
+    ok = crc == crc_file;
+  }
+  if (!ok) return set_error(GNEP_ERR_CHECKPOINT_CORRUPT, std::string("checkpoint failed validation: ") + path);
+  long long stp = h.step;
+  GNEP_CUDA(cudaDeviceSynchronize());
+  GNEP_CUDA(cudaMemcpy(m->params, p.data(), 4 * n, cudaMemcpyHostToDevice));
+  GNEP_CUDA(cudaMemcpy(m->adam_m, mm.data(), 4 * n, cudaMemcpyHostToDevice));
+  GNEP_CUDA(cudaMemcpy(m->adam_v, vv.data(), 4 * n, cudaMemcpyHostToDevice));
+  GNEP_CUDA(cudaMemcpy(m->scale, sc.data(), 4 * d, cudaMemcpyHostToDevice));
+  GNEP_CUDA(cudaMemcpy(m->step, &stp, sizeof(long long), cudaMemcpyHostToDevice));
+  return GNEP_OK;
+}
+
+// -------------------------------------------------------------- profiling
+
+namespace gnep {
+Profiler g_prof;
+}
+
+static const char* g_stage_names[64];
+static int g_stage_count = 0;
+
+int gnep_profile_step(gnep_model* m, const gnep_nlist* nl_, const gnep_labels* y, float* stage_ms,
+                      int32_t cap, int32_t* n_stages, void* stream) {
+  int rc = check_nlist(m, nl_);
+  if (rc) return rc;
+  if (!stage_ms || !n_stages || cap < 1) return set_error(GNEP_ERR_INVALID_ARG, "bad output arrays");
+  gnep_nlist* nl = const_cast<gnep_nlist*>(nl_);
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int q = 0; q < 64; ++q) GNEP_CUDA(cudaEventCreate(&g_prof.ev[q]));
+  g_prof.st = st;
+  g_prof.n = 0;
+  GNEP_CUDA(cudaEventRecord(g_prof.ev[0], st));
+  g_prof.on = true;
+  rc = loss_grad_core(m, nl, y, st);
+  if (!rc) rc = run_adam(m, nullptr, 1e-4, 0.9, 0.999, 1e-8, 0.0, false, 0, 0, 0, 0, st);
+  g_prof.on = false;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (!rc && e != cudaSuccess) rc = cuda_error(e, "profile step");
+  if (!rc) {
+    const int n = g_prof.n < cap ? g_prof.n : cap;
+    for (int q = 0; q < n; ++q) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, g_prof.ev[q], g_prof.ev[q + 1]);
+      stage_ms[q] = ms;
+      g_stage_names[q] = g_prof.names[q];
+    }
+    g_stage_count = n;
+    *n_stages = n;
+  }
+  for (int q = 0; q < 64; ++q) cudaEventDestroy(g_prof.ev[q]);
+  return rc;
+}
+
+const char* gnep_profile_stage_name(int32_t i) {
+  return (i >= 0 && i < g_stage_count) ? g_stage_names[i] : "";
+}
+
+// ----------------------------------------------------------------- status
+
+int gnep_sync_status(gnep_model* m, void* stream) {
+  if (!m) return set_error(GNEP_ERR_INVALID_ARG, "NULL model");
+  cudaStream_t st = (cudaStream_t)stream;
+  GNEP_CUDA(cudaStreamSynchronize(st));
+  GNEP_CUDA(cudaGetLastError());
+  int flag = 0;
+  GNEP_CUDA(cudaMemcpy(&flag, m->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag) GNEP_CUDA(cudaMemset(m->err, 0, sizeof(int)));
+  if (flag & kErrNonFinite) return set_error(GNEP_ERR_NONFINITE, "loss was not finite; the update was skipped");
+  if (flag & kErrTimeout) return set_error(GNEP_ERR_TIMEOUT, "a device-side wait gave up");
+  if (flag) return set_error(GNEP_ERR_INVALID_ARG, "device reported an invalid input");
+  return GNEP_OK;
+}
+
+}  // extern "C"

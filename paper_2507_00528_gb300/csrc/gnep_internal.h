@@ -1,0 +1,188 @@
+// Internal structures of libgnep (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/gnep.h"
+
+namespace gnep {
+
+// Compile-time maxima of this build.
+constexpr int kMaxHidden = 128;
+constexpr int kMaxDes = 64;
+constexpr int kLmax = 4;
+
+// Runtime shape of a model.
+struct Shape {
+  int ns, nqr, kr, nqa, ka, lmax, fb, H, ndes;
+  bool operator==(const Shape& o) const {
+    return ns == o.ns && nqr == o.nqr && kr == o.kr && nqa == o.nqa && ka == o.ka &&
+           lmax == o.lmax && fb == o.fb && H == o.H;
+  }
+};
+
+// Everything a kernel needs to know about the model, passed by value.
+struct DevModel {
+  int ns, nqr, kr, nqa, ka, H, ndes;
+  int net_size;      // ndes*H + 2H + 1
+  int off_cR, off_cA;
+  long long n_params;
+  float rcr_inv, rca_inv;
+  const float* params;
+  const float* scale;
+};
+
+// One list of Eq. 2 in CSR form.
+struct PairList {
+  int64_t n = 0, cap = 0;
+  int* off = nullptr;      // [N+1]
+  int* j = nullptr;        // [n] neighbour (global atom index)
+  int* owner = nullptr;    // [n] central atom i
+  int* rev = nullptr;      // [n] index of (j, i, -shift)
+  float4* rij = nullptr;   // [n] r_ij (x, y, z), w = species of j (as float)
+  char4* shift = nullptr;  // [n] image (na, nb, nc, 0)
+};
+
+// Per-step device workspace of one batch (sized at build, reused every step).
+struct Workspace {
+  float *G = nullptr, *Ep = nullptr, *X = nullptr, *Eatom = nullptr;
+  float *S = nullptr, *FR = nullptr, *Shat = nullptr;
+  float4 *dR = nullptr, *dA = nullptr;
+  float *F = nullptr, *Wat = nullptr;
+  double *Es = nullptr, *Ws = nullptr;
+  float4* a = nullptr;            // force residual coefficients a_i
+  float *es = nullptr, *Bs = nullptr;  // energy and virial residual coefficients
+  float *Gd = nullptr, *Sd = nullptr, *FRd = nullptr;
+  float *Gb = nullptr, *alpha = nullptr, *beta = nullptr, *q1 = nullptr, *eatom = nullptr;
+  float *Sb = nullptr, *Sdb = nullptr, *dcA = nullptr;
+  double* red = nullptr;          // reduction partials
+  int64_t red_len = 0;
+  float* part = nullptr;          // GEMM split partials
+  int64_t part_len = 0;
+  double* lab_e = nullptr;        // staged labels
+  float* lab_f = nullptr;
+  double* lab_v = nullptr;
+  double* coef = nullptr;         // [8] loss scalars for the residual kernels
+  float* gradf = nullptr;         // FP32 copy of the gradient for host output
+};
+
+}  // namespace gnep
+
+struct gnep_nlist {
+  gnep::Shape shape;
+  int device = 0;
+  int n_struct = 0, n_atoms = 0;
+  double rcr = 0, rca = 0;
+  int* struct_off = nullptr;   // device [S+1]
+  int* type = nullptr;         // device [N]
+  double* pos = nullptr;       // device [N*3]
+  double* cell = nullptr;      // device [S*9]
+  int* atom_struct = nullptr;  // device [N]
+  int* perm = nullptr;         // device [N] atoms grouped by species
+  int species_off[9] = {0};    // host [ns+1]
+  gnep::PairList L[2];         // radial, angular
+  gnep::Workspace ws;
+  void* ws_mem = nullptr;      // one allocation carved into the workspace
+  int64_t ws_pairs[2] = {-1, -1};  // pair counts the workspace was sized for
+};
+
+struct gnep_model {
+  gnep::Shape shape;
+  int device = 0;
+  double rcr = 0, rca = 0;
+  int precision = GNEP_PREC_FP32;
+  int64_t n_params = 0;
+  int net_size = 0, off_cR = 0, off_cA = 0;
+  float* params = nullptr;  // device [n_params]
+  float* scale = nullptr;   // device [ndes]
+  float* adam_m = nullptr;
+  float* adam_v = nullptr;
+  double* grad = nullptr;   // device [n_params]
+  long long* step = nullptr;  // device update count
+  int* err = nullptr;       // device error flag
+  gnep::DevModel dev() const {
+    gnep::DevModel d;
+    d.ns = shape.ns; d.nqr = shape.nqr; d.kr = shape.kr; d.nqa = shape.nqa; d.ka = shape.ka;
+    d.H = shape.H; d.ndes = shape.ndes; d.net_size = net_size; d.off_cR = off_cR;
+    d.off_cA = off_cA; d.n_params = n_params;
+    d.rcr_inv = (float)(1.0 / rcr); d.rca_inv = (float)(1.0 / rca);
+    d.params = params; d.scale = scale;
+    return d;
+  }
+};
+
+namespace gnep {
+
+// Device error flag bits.
+enum : int { kErrNonFinite = 1, kErrUnwrapped = 2, kErrRevMissing = 4, kErrTimeout = 8 };
+
+// Error reporting helpers (api.cu).
+int set_error(int code, const std::string& msg);
+int cuda_error(cudaError_t e, const char* what);
+#define GNEP_CUDA(call)                                        \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    if (e_ != cudaSuccess) return gnep::cuda_error(e_, #call); \
+  } while (0)
+#define GNEP_CHECK_LAUNCH(what)                                \
+  do {                                                         \
+    cudaError_t e_ = cudaGetLastError();                       \
+    if (e_ != cudaSuccess) return gnep::cuda_error(e_, what);  \
+  } while (0)
+
+// neighbors.cu
+int build_lists(gnep_model* m, gnep_nlist* nl, cudaStream_t st);
+
+// Shape-specialised step (sweeps.cu).
+struct StepArgs {
+  const gnep_model* m;
+  gnep_nlist* nl;
+  cudaStream_t st;
+};
+bool shape_supported(const Shape& s);
+int run_descriptors(const StepArgs& a, bool with_mlp);
+int run_forward(const StepArgs& a);
+int run_backward(const StepArgs& a);
+
+int shape_setup(const Shape& s);
+
+// train.cu
+int64_t grad_partial_floats(const gnep_model* m, int n_atoms);
+int64_t loss_partial_doubles();
+int run_loss_impl(const gnep_model* m, gnep_nlist* nl, const double* le, const float* lf, const double* lv,
+                  const gnep_labels* y, cudaStream_t st);
+int run_grad_reduce_impl(const gnep_model* m, gnep_nlist* nl, double lambda_l2, cudaStream_t st);
+int grad_to_float(const gnep_model* m, float* dst, cudaStream_t st);
+int run_adam(gnep_model* m, const double* lr_dev, double lr, double b1, double b2, double eps,
+             double wd, bool scheduled, double lr_start, double lr_stop, int64_t nw, int64_t nt,
+             cudaStream_t st);
+int run_scale(gnep_model* m, gnep_nlist* nl, cudaStream_t st);
+int run_species_perm(gnep_nlist* nl, cudaStream_t st);
+
+// Workspace sizing (api.cu).
+int alloc_workspace(gnep_model* m, gnep_nlist* nl);
+void free_workspace(gnep_nlist* nl);
+
+// Stage profiler: when on, an event is recorded after every kernel launch of
+// a step (api.cu: gnep_profile_step).  Not thread-safe; off by default.
+struct Profiler {
+  bool on = false;
+  cudaStream_t st = nullptr;
+  int n = 0;
+  cudaEvent_t ev[64];
+  const char* names[64];
+};
+extern Profiler g_prof;
+inline void stage(const char* name) {
+  if (!g_prof.on || g_prof.n >= 63) return;
+  cudaEventRecord(g_prof.ev[g_prof.n + 1], g_prof.st);
+  g_prof.names[g_prof.n] = name;
+  g_prof.n++;
+}
+
+// Small launch helpers.
+inline int blocks_for(int64_t n, int t) { return (int)((n + t - 1) / t); }
+
+}  // namespace gnep

@@ -1,0 +1,303 @@
+// Neighbour sets of Eq. 2: N^i = { (j, n) : |r_j + n.H - r_i| < r_c, (j, n) != (i, 0) }
+// over every periodic image n, for the radial (r_c^R) and angular (r_c^A)
+// cut-offs, in canonical order (j ascending, then image shift lexicographic).
+//
+// The accept/reject decision is made in FP64 with explicitly rounded operations
+// (no fused multiply-add) in the fixed order
+//   s = (na a + nb b) + nc c,  d = (r_j + s) - r_i,  d2 = (dx^2 + dy^2) + dz^2,
+// so the list equals that of any plain FP64 evaluation of the same expression.
+// An FP32 prefilter only discards candidates far outside the larger cut-off.
+#include <cstdio>
+#include <vector>
+
+#include "gnep_internal.h"
+
+namespace gnep {
+
+namespace {
+
+__global__ void k_atom_struct(const int* __restrict__ off, int S, int N, int* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int lo = 0, hi = S - 1;
+  while (lo < hi) {  // last s with off[s] <= i
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= i) lo = mid; else hi = mid - 1;
+  }
+  out[i] = lo;
+}
+
+// Images needed per cell direction: floor(rc / w) + 1, w = V / |b x c| etc.
+__global__ void k_image_range(const double* __restrict__ cell, int S, double rc, int* __restrict__ kr) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= S) return;
+  const double* a = cell + 9 * s;
+  const double* b = a + 3;
+  const double* c = a + 6;
+  const double bc[3] = {b[1] * c[2] - b[2] * c[1], b[2] * c[0] - b[0] * c[2], b[0] * c[1] - b[1] * c[0]};
+  const double ca[3] = {c[1] * a[2] - c[2] * a[1], c[2] * a[0] - c[0] * a[2], c[0] * a[1] - c[1] * a[0]};
+  const double ab[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+  const double vol = fabs(a[0] * bc[0] + a[1] * bc[1] + a[2] * bc[2]);
+  const double n[3] = {norm3d(bc[0], bc[1], bc[2]), norm3d(ca[0], ca[1], ca[2]), norm3d(ab[0], ab[1], ab[2])};
+  for (int x = 0; x < 3; ++x) kr[3 * s + x] = (int)floor(rc / (vol / n[x])) + 1;
+}
+
+__device__ __forceinline__ double pair_d2_exact(const double* H, const double* pi, const double* pj,
+                                                int na, int nb, int nc, double d[3]) {
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    const double s = __dadd_rn(__dadd_rn(__dmul_rn((double)na, H[x]), __dmul_rn((double)nb, H[3 + x])),
+                               __dmul_rn((double)nc, H[6 + x]));
+    d[x] = __dsub_rn(__dadd_rn(pj[x], s), pi[x]);
+  }
+  return __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
+}
+
+struct ListParams {
+  double rc2[2];     // exact squared cut-offs (radial, angular)
+  float reject2;     // FP32 prefilter bound above max(rc2)
+};
+
+// One thread per central atom walks every (j, image) of its structure in
+// canonical order.  Pass 0 counts, pass 1 writes.
+template <bool kFill>
+__global__ void __launch_bounds__(128) k_pairs(
+    int N, const int* __restrict__ struct_off, const int* __restrict__ atom_struct,
+    const double* __restrict__ pos, const double* __restrict__ cell, const int* __restrict__ krange,
+    const int* __restrict__ type, ListParams lp, int* __restrict__ cnt0, int* __restrict__ cnt1,
+    const long long* __restrict__ off0, const long long* __restrict__ off1,
+    int* __restrict__ j0, int* __restrict__ own0, float4* __restrict__ r0, char4* __restrict__ sh0,
+    int* __restrict__ j1, int* __restrict__ own1, float4* __restrict__ r1, char4* __restrict__ sh1,
+    int* __restrict__ err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int s = atom_struct[i];
+  const int a0 = struct_off[s], a1 = struct_off[s + 1];
+  double H[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) H[q] = cell[9 * s + q];
+  float Hf[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) Hf[q] = (float)H[q];
+  const double pi[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
+  const float pif[3] = {(float)pi[0], (float)pi[1], (float)pi[2]};
+  const int ka = krange[3 * s], kb = krange[3 * s + 1], kc = krange[3 * s + 2];
+  if (!kFill) {
+    // fractional coordinates must lie in [0, 1) up to rounding
+    const double det = H[0] * (H[4] * H[8] - H[5] * H[7]) - H[1] * (H[3] * H[8] - H[5] * H[6]) +
+                       H[2] * (H[3] * H[7] - H[4] * H[6]);
+    const double inv[9] = {(H[4] * H[8] - H[5] * H[7]) / det, (H[2] * H[7] - H[1] * H[8]) / det,
+                           (H[1] * H[5] - H[2] * H[4]) / det, (H[5] * H[6] - H[3] * H[8]) / det,
+                           (H[0] * H[8] - H[2] * H[6]) / det, (H[2] * H[3] - H[0] * H[5]) / det,
+                           (H[3] * H[7] - H[4] * H[6]) / det, (H[1] * H[6] - H[0] * H[7]) / det,
+                           (H[0] * H[4] - H[1] * H[3]) / det};
+    for (int x = 0; x < 3; ++x) {
+      const double f = pi[0] * inv[x] + pi[1] * inv[3 + x] + pi[2] * inv[6 + x];
+      if (!(f > -1e-9 && f < 1.0 + 1e-9)) atomicOr(err, kErrUnwrapped);
+    }
+  }
+  int c0 = 0, c1 = 0;
+  long long w0 = kFill ? off0[i] : 0, w1 = kFill ? off1[i] : 0;
+  for (int j = a0; j < a1; ++j) {
+    const double pj[3] = {pos[3 * j], pos[3 * j + 1], pos[3 * j + 2]};
+    const float dj[3] = {(float)pj[0] - pif[0], (float)pj[1] - pif[1], (float)pj[2] - pif[2]};
+    const int tj = type[j];
+    for (int na = -ka; na <= ka; ++na)
+      for (int nb = -kb; nb <= kb; ++nb)
+        for (int nc = -kc; nc <= kc; ++nc) {
+          if (j == i && na == 0 && nb == 0 && nc == 0) continue;
+          const float fx = dj[0] + ((float)na * Hf[0] + (float)nb * Hf[3] + (float)nc * Hf[6]);
+          const float fy = dj[1] + ((float)na * Hf[1] + (float)nb * Hf[4] + (float)nc * Hf[7]);
+          const float fz = dj[2] + ((float)na * Hf[2] + (float)nb * Hf[5] + (float)nc * Hf[8]);
+          if (fx * fx + fy * fy + fz * fz > lp.reject2) continue;
+          double d[3];
+          const double d2 = pair_d2_exact(H, pi, pj, na, nb, nc, d);
+          const bool in0 = d2 < lp.rc2[0], in1 = d2 < lp.rc2[1];
+          if (kFill) {
+            const float4 rv = make_float4((float)d[0], (float)d[1], (float)d[2], (float)tj);
+            const char4 sv = make_char4((signed char)na, (signed char)nb, (signed char)nc, 0);
+            if (in0) { j0[w0] = j; own0[w0] = i; r0[w0] = rv; sh0[w0] = sv; ++w0; }
+            if (in1) { j1[w1] = j; own1[w1] = i; r1[w1] = rv; sh1[w1] = sv; ++w1; }
+          } else {
+            c0 += in0;
+            c1 += in1;
+          }
+        }
+  }
+  if (!kFill) {
+    cnt0[i] = c0;
+    cnt1[i] = c1;
+  }
+}
+
+// Exclusive scan of int counts into int64 offsets: one block per 1024 items,
+// then the block totals, recursively.
+__global__ void k_scan_block(const long long* __restrict__ in, const int* __restrict__ in32, int64_t n,
+                             long long* __restrict__ out, long long* __restrict__ block_sums) {
+  __shared__ long long sh[1024];
+  const int64_t g = (int64_t)blockIdx.x * 1024 + threadIdx.x;
+  long long v = 0;
+  if (g < n) v = in32 ? (long long)in32[g] : in[g];
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    long long t = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+    __syncthreads();
+    sh[threadIdx.x] += t;
+    __syncthreads();
+  }
+  if (g < n) out[g] = sh[threadIdx.x] - v;
+  if (threadIdx.x == 1023) block_sums[blockIdx.x] = sh[1023];
+}
+
+__global__ void k_scan_add(long long* __restrict__ out, int64_t n, const long long* __restrict__ add) {
+  const int64_t g = (int64_t)blockIdx.x * 1024 + threadIdx.x;
+  if (g < n) out[g] += add[blockIdx.x];
+}
+
+__global__ void k_to_int(const long long* __restrict__ in, int64_t n, int* __restrict__ out) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < n) out[g] = (int)in[g];
+}
+
+// Reverse pair: the entry (i, -n) in j's list, found by binary search on the
+// canonical key (j, na, nb, nc).
+__global__ void k_reverse(int64_t P, const int* __restrict__ off, const int* __restrict__ jj,
+                          const int* __restrict__ own, const char4* __restrict__ sh,
+                          int* __restrict__ rev, int* __restrict__ err) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const int i = own[p], j = jj[p];
+  const char4 s = sh[p];
+  const int key[4] = {i, -s.x, -s.y, -s.z};
+  int lo = off[j], hi = off[j + 1] - 1, found = -1;
+  while (lo <= hi) {
+    const int mid = (lo + hi) >> 1;
+    const char4 t = sh[mid];
+    const int cand[4] = {jj[mid], t.x, t.y, t.z};
+    int cmp = 0;
+    for (int q = 0; q < 4 && cmp == 0; ++q) cmp = (cand[q] < key[q]) ? -1 : (cand[q] > key[q]) ? 1 : 0;
+    if (cmp == 0) { found = mid; break; }
+    if (cmp < 0) lo = mid + 1; else hi = mid - 1;
+  }
+  if (found < 0) { atomicOr(err, kErrRevMissing); found = (int)p; }
+  rev[p] = found;
+}
+
+// Exclusive scan of in (int32 when in32 is set, else int64) into out.
+int scan_rec(const long long* in64, const int* in32, int64_t n, long long* out,
+             std::vector<void*>& tmp, cudaStream_t st) {
+  const int64_t nb = (n + 1023) / 1024;
+  long long* sums = nullptr;
+  GNEP_CUDA(cudaMallocAsync(&sums, sizeof(long long) * (nb + 1), st));
+  tmp.push_back(sums);
+  k_scan_block<<<(unsigned)nb, 1024, 0, st>>>(in64, in32, n, out, sums);
+  GNEP_CHECK_LAUNCH("k_scan_block");
+  if (nb > 1) {
+    long long* scanned = nullptr;
+    GNEP_CUDA(cudaMallocAsync(&scanned, sizeof(long long) * (nb + 1), st));
+    tmp.push_back(scanned);
+    const int rc = scan_rec(sums, nullptr, nb, scanned, tmp, st);
+    if (rc) return rc;
+    k_scan_add<<<(unsigned)nb, 1024, 0, st>>>(out, n, scanned);
+    GNEP_CHECK_LAUNCH("k_scan_add");
+  }
+  return GNEP_OK;
+}
+
+}  // namespace
+
+int build_lists(gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
+  const int N = nl->n_atoms, S = nl->n_struct;
+  std::vector<void*> tmp;
+  auto cleanup = [&]() {
+    for (auto p : tmp) cudaFreeAsync(p, st);
+  };
+  int *cnt = nullptr, *kr = nullptr;
+  long long* offs = nullptr;
+  GNEP_CUDA(cudaMallocAsync(&cnt, sizeof(int) * 2 * (size_t)(N + 1), st));
+  GNEP_CUDA(cudaMallocAsync(&kr, sizeof(int) * 3 * (size_t)S, st));
+  GNEP_CUDA(cudaMallocAsync(&offs, sizeof(long long) * 2 * (size_t)(N + 1), st));
+  tmp.push_back(cnt);
+  tmp.push_back(kr);
+  tmp.push_back(offs);
+  GNEP_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * 2 * (size_t)(N + 1), st));
+
+  k_atom_struct<<<blocks_for(N, 256), 256, 0, st>>>(nl->struct_off, S, N, nl->atom_struct);
+  const double rcmax = nl->rcr > nl->rca ? nl->rcr : nl->rca;
+  k_image_range<<<blocks_for(S, 128), 128, 0, st>>>(nl->cell, S, rcmax, kr);
+  GNEP_CHECK_LAUNCH("k_image_range");
+
+  ListParams lp;
+  lp.rc2[0] = nl->rcr * nl->rcr;
+  lp.rc2[1] = nl->rca * nl->rca;
+  lp.reject2 = (float)(rcmax * rcmax * 1.001 + 0.05);
+
+  int* cnt0 = cnt;
+  int* cnt1 = cnt + (N + 1);
+  k_pairs<false><<<blocks_for(N, 128), 128, 0, st>>>(
+      N, nl->struct_off, nl->atom_struct, nl->pos, nl->cell, kr, nl->type, lp, cnt0, cnt1, nullptr,
+      nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, m->err);
+  GNEP_CHECK_LAUNCH("k_pairs<count>");
+
+  long long* off0 = offs;
+  long long* off1 = offs + (N + 1);
+  int rc = scan_rec(nullptr, cnt0, N + 1, off0, tmp, st);
+  if (rc) { cleanup(); return rc; }
+  rc = scan_rec(nullptr, cnt1, N + 1, off1, tmp, st);
+  if (rc) { cleanup(); return rc; }
+  long long tot[2];
+  GNEP_CUDA(cudaMemcpyAsync(&tot[0], off0 + N, sizeof(long long), cudaMemcpyDeviceToHost, st));
+  GNEP_CUDA(cudaMemcpyAsync(&tot[1], off1 + N, sizeof(long long), cudaMemcpyDeviceToHost, st));
+  int herr = 0;
+  GNEP_CUDA(cudaMemcpyAsync(&herr, m->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  GNEP_CUDA(cudaStreamSynchronize(st));
+  if (herr & kErrUnwrapped) {
+    cleanup();
+    GNEP_CUDA(cudaMemsetAsync(m->err, 0, sizeof(int), st));
+    return set_error(GNEP_ERR_INVALID_ARG, "positions must be wrapped into their cell (fractional coordinates in [0,1))");
+  }
+  for (int L = 0; L < 2; ++L)
+    if (tot[L] >= (1LL << 31) - 1) {
+      cleanup();
+      return set_error(GNEP_ERR_NEIGHBOR_OVERFLOW, "pair count exceeds 32-bit indices; split the batch");
+    }
+
+  for (int L = 0; L < 2; ++L) {
+    PairList& P = nl->L[L];
+    if (tot[L] > P.cap) {
+      cudaFree(P.j); cudaFree(P.owner); cudaFree(P.rev); cudaFree(P.rij); cudaFree(P.shift);
+      const int64_t cap = tot[L] > 0 ? tot[L] : 1;
+      GNEP_CUDA(cudaMalloc(&P.j, sizeof(int) * cap));
+      GNEP_CUDA(cudaMalloc(&P.owner, sizeof(int) * cap));
+      GNEP_CUDA(cudaMalloc(&P.rev, sizeof(int) * cap));
+      GNEP_CUDA(cudaMalloc(&P.rij, sizeof(float4) * cap));
+      GNEP_CUDA(cudaMalloc(&P.shift, sizeof(char4) * cap));
+      P.cap = cap;
+    }
+    if (!P.off) GNEP_CUDA(cudaMalloc(&P.off, sizeof(int) * (size_t)(N + 1)));
+    P.n = tot[L];
+    k_to_int<<<blocks_for(N + 1, 256), 256, 0, st>>>(L == 0 ? off0 : off1, N + 1, P.off);
+  }
+  k_pairs<true><<<blocks_for(N, 128), 128, 0, st>>>(
+      N, nl->struct_off, nl->atom_struct, nl->pos, nl->cell, kr, nl->type, lp, nullptr, nullptr, off0,
+      off1, nl->L[0].j, nl->L[0].owner, nl->L[0].rij, nl->L[0].shift, nl->L[1].j, nl->L[1].owner,
+      nl->L[1].rij, nl->L[1].shift, m->err);
+  GNEP_CHECK_LAUNCH("k_pairs<fill>");
+  for (int L = 0; L < 2; ++L) {
+    PairList& P = nl->L[L];
+    if (P.n > 0)
+      k_reverse<<<blocks_for(P.n, 256), 256, 0, st>>>(P.n, P.off, P.j, P.owner, P.shift, P.rev, m->err);
+  }
+  GNEP_CHECK_LAUNCH("k_reverse");
+  cleanup();
+  GNEP_CUDA(cudaStreamSynchronize(st));
+  GNEP_CUDA(cudaMemcpy(&herr, m->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (herr & kErrRevMissing) {
+    GNEP_CUDA(cudaMemset(m->err, 0, sizeof(int)));
+    return set_error(GNEP_ERR_INVALID_ARG, "neighbour lists are not symmetric (internal error)");
+  }
+  return GNEP_OK;
+}
+
+}  // namespace gnep
