@@ -12,6 +12,7 @@ using namespace gnep;
 
 namespace gnep {
 
+Profiler g_prof;
 static thread_local std::string g_last_error;
 
 int set_error(int code, const std::string& msg) {
@@ -640,10 +641,6 @@ int gnep_load(gnep_model* m, const char* path) {
 }
 
 // -------------------------------------------------------------- profiling
-
-namespace gnep {
-Profiler g_prof;
-}
 
 static const char* g_stage_names[64];
 static int g_stage_count = 0;

@@ -147,7 +147,8 @@ def test_single_atom_self_images_and_isolated_atom():
     Eao, Eso, Fo, Wo = O.forward(c.cfg, c.P64, c.s64, b)
     assert rel_l2(Ea, Eao) < E_TOL
     assert np.abs(F[1]).max() == 0.0
-    assert rel_l2(F, Fo) < F_TOL and rel_l2(W, Wo) < F_TOL
+    # forces here are cancellation residuals of O(1) pair terms: absolute bound
+    assert np.abs(F - Fo).max() < 1e-5 and rel_l2(W, Wo) < F_TOL
     terms, g = c.m.loss_grad(c.nl, c.gpu_labels())
     ref_terms, ref_g = O.loss_grad(c.cfg, c.P64, c.s64, b, c.y)
     check_grad(g.cpu().numpy(), ref_g)
