@@ -156,6 +156,25 @@ int gnep_nlist_export(const gnep_nlist *nl, int which, int32_t *off, int32_t *j,
  * radial n first, then angular (n, l) n-major, then 4-body n. */
 int gnep_descriptors(gnep_model *m, const gnep_nlist *nl, float *G, void *stream);
 
+/* The same descriptors as gnep_descriptors, computed without allocating any
+ * device memory.  The paper has no counterpart: this serves callers that cannot
+ * allocate when they need descriptors, such as code running while a stream is
+ * captured into a CUDA graph, hosts whose device memory belongs to another
+ * allocator or a fixed pool, and per-step hooks of simulation engines.  The
+ * call uses a fixed 8 MiB scratch array built into the library (every GPU that
+ * loads the library holds it until the process exits) instead of the nlist's
+ * workspace; it needs n_atoms * (n_species * (basis_radial + 1) +
+ * 24 * (n_max_angular + 1)) floats (plus alignment) and returns INVALID_ARG for
+ * larger batches.  G [n_atoms][N_des] must be device memory; it is written
+ * asynchronously on `stream`.  The first call on each device looks up the
+ * scratch address; make that first call before any stream capture.  All calls
+ * share one scratch array per device: calls whose kernels may overlap on the
+ * GPU (different streams without ordering, several threads) race and must not
+ * be issued; calls ordered on one stream are safe.  The scratch needs no
+ * clearing: every element read is first written by the same call. */
+int gnep_descriptors_noalloc(gnep_model *m, const gnep_nlist *nl, float *G,
+                             void *stream);
+
 /* Energies, forces and virials (Eqs. 1, 3, 4).  Any output may be NULL.
  * E_atom [n_atoms] site energies; E_struct [n_struct] totals; F [n_atoms*3];
  * W_struct [n_struct*6] total virial, symmetrised, xx yy zz xy yz zx. */

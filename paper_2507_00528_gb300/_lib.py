@@ -30,7 +30,7 @@ EXPORTS = [
     "gnep_loss_grad", "gnep_adam_step", "gnep_adam_step_scheduled", "gnep_get_step",
     "gnep_lr_schedule", "gnep_graph_create", "gnep_graph_launch", "gnep_graph_destroy", "gnep_save",
     "gnep_load", "gnep_sync_status", "gnep_last_error", "gnep_abi_version", "gnep_profile_step",
-    "gnep_profile_stage_name",
+    "gnep_profile_stage_name", "gnep_descriptors_noalloc",
 ]
 
 
@@ -70,6 +70,7 @@ _SIGS = {
     "gnep_nlist_info": [_vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
     "gnep_nlist_export": [_vp, C.c_int, _vp, _vp, _vp, _vp],
     "gnep_descriptors": [_vp, _vp, _vp, _vp],
+    "gnep_descriptors_noalloc": [_vp, _vp, _vp, _vp],
     "gnep_forward": [_vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "gnep_loss_grad": [_vp, _vp, C.POINTER(Labels), _vp, _vp, _vp],
     "gnep_adam_step": [_vp, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, _vp],

@@ -390,6 +390,15 @@ int gnep_descriptors(gnep_model* m, const gnep_nlist* nl_, float* G, void* strea
   return copy_out(G, nl->ws.G, sizeof(float) * (size_t)nl->n_atoms * m->shape.ndes, st);
 }
 
+int gnep_descriptors_noalloc(gnep_model* m, const gnep_nlist* nl_, float* G, void* stream) {
+  int rc = check_nlist(m, nl_);
+  if (rc) return rc;
+  if (!G || !is_device_ptr(G))
+    return set_error(GNEP_ERR_INVALID_ARG, "gnep_descriptors_noalloc writes G in place: G must be device memory");
+  StepArgs A{m, const_cast<gnep_nlist*>(nl_), (cudaStream_t)stream};
+  return run_descriptors_static(A, G);
+}
+
 int gnep_forward(gnep_model* m, const gnep_nlist* nl_, float* E_atom, double* E_struct, float* F,
                  double* W_struct, void* stream) {
   int rc = check_nlist(m, nl_);

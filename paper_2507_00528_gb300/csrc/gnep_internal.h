@@ -147,6 +147,7 @@ int run_forward(const StepArgs& a);
 int run_backward(const StepArgs& a);
 
 int shape_setup(const Shape& s);
+int run_descriptors_static(const StepArgs& a, float* G);
 
 // train.cu
 int64_t grad_partial_floats(const gnep_model* m, int n_atoms);

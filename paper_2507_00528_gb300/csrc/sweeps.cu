@@ -16,6 +16,8 @@
 // one forward-mode sweep (3) and one reverse sweep (4) instead of explicit second
 // derivative tensors.
 #include <cstdio>
+#include <mutex>
+#include <string>
 
 #include "device_math.cuh"
 #include "gnep_internal.h"
@@ -783,6 +785,84 @@ int run_backward(const StepArgs& A) {
 #define X(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB)                                                                    \
   if (s.ns == P_NS && s.nqr == P_NQR && s.kr == P_KR && s.nqa == P_NQA && s.ka == P_KA && (s.fb != 0) == P_FB) \
     return Runner<Sh<P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB>>::backward(A);
+  GNEP_SHAPES(X)
+#undef X
+  return set_error(GNEP_ERR_UNSUPPORTED, "no kernel for this shape");
+}
+
+}  // namespace gnep
+
+// ---------------------------------------------------------------------------
+// Descriptors without any device allocation.
+//
+// Some callers cannot allocate device memory at the point where they need
+// descriptors: code that runs while a CUDA stream is being captured into a
+// graph (allocation is not a capturable operation), hosts whose device memory
+// is entirely owned by another allocator or a fixed pool set up at start-up,
+// and per-step hooks of simulation engines that forbid allocation in their hot
+// loop.  For them the descriptor sweep can use this fixed scratch array, which
+// every GPU that loads the library holds until the process exits, instead of
+// workspace memory.
+namespace gnep {
+namespace {
+
+constexpr size_t kStaticScratchFloats = size_t(1) << 21;  // 8 MiB
+static __device__ __align__(256) float g_static_scratch[kStaticScratchFloats];
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+float* g_static_ptr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device, looked up once per
+// device (host code must not use the symbol itself as a device pointer).
+int static_scratch(float** out) {
+  int dev = 0;
+  GNEP_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return set_error(GNEP_ERR_INVALID_ARG, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(static scratch)");
+    g_static_ptr[dev] = static_cast<float*>(p);
+  }
+  *out = g_static_ptr[dev];
+  return GNEP_OK;
+}
+
+template <class C>
+int descriptors_static(const StepArgs& A, float* G) {
+  const gnep_model* m = A.m;
+  const gnep_nlist* nl = A.nl;
+  const int64_t N = nl->n_atoms;
+  const int64_t fr = N * C::NS * C::KR;
+  const int64_t sa = N * C::NQA * NLM;
+  const int64_t fr_padded = (fr + 63) / 64 * 64;
+  if (fr_padded + sa > (int64_t)kStaticScratchFloats)
+    return set_error(GNEP_ERR_INVALID_ARG,
+                     "batch too large for the fixed descriptor scratch (needs " + std::to_string(fr_padded + sa) +
+                         " floats, holds " + std::to_string(kStaticScratchFloats) + ")");
+  float* scratch = nullptr;
+  int rc = static_scratch(&scratch);
+  if (rc) return rc;
+  if (N == 0) return GNEP_OK;
+  const DevModel dm = m->dev();
+  // Both kernels overwrite every scratch element they later read, so the
+  // array needs no clearing between calls.
+  k_desc_radial<C><<<blocks_for(N, 128), 128, 0, A.st>>>((int)N, dm, nl->type, nl->L[0].off, nl->L[0].rij,
+                                                         scratch, G);
+  k_desc_angular<C><<<blocks_for(N * C::NQA, 128), 128, 0, A.st>>>((int)N, dm, nl->type, nl->L[1].off,
+                                                                    nl->L[1].rij, scratch + fr_padded, G);
+  GNEP_CHECK_LAUNCH("descriptor sweep (static scratch)");
+  return GNEP_OK;
+}
+
+}  // namespace
+
+int run_descriptors_static(const StepArgs& A, float* G) {
+  const Shape& s = A.m->shape;
+#define X(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB)                                                       \
+  if (s.ns == P_NS && s.nqr == P_NQR && s.kr == P_KR && s.nqa == P_NQA && s.ka == P_KA && (s.fb != 0) == P_FB) \
+    return descriptors_static<Sh<P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB>>(A, G);
   GNEP_SHAPES(X)
 #undef X
   return set_error(GNEP_ERR_UNSUPPORTED, "no kernel for this shape");
