@@ -56,21 +56,19 @@ def algo_flops(nqr=9, kr=13, nqa=9, ka=13, ns=2, H=50, fb=True, N=1, PR=1, PA=1)
     harm = 40                       # 24 B_lm from the unit vector
     harm_g = 384                    # B_lm and projected gradients
     u = 18                          # u_ij = (a_j - a_i) + B_s r_ij
+    dirder = 144 + ka               # D_lm = grad B_lm . u and fu_k
     q4 = 60 if fb else 0
     f = {}
     f["desc_radial"] = PR * (6 * kr + 8) + N * 2 * ns * kr * nqr
     f["desc_angular"] = PA * (geo + basis_f + harm + nqa * (2 * ka + 48)) + N * nqa * (48 + q4)
-    f["mlp_fwd"] = N * (4 * D * H + 6 * H + 2 * D)
-    f["shat"] = N * nqa * (72 + (80 if fb else 0))
-    f["force_radial"] = PR * (14 * kr + 19) + N * 2 * nqr * ns * kr
-    f["force_angular"] = PA * (geo + basis_fd + harm_g + nqa * (4 * ka + 201))
-    f["force_gather"] = (PR + PA) * 21
+    f["mlp_fwd"] = N * (4 * D * H + 6 * H + 2 * D + 2 * ns * kr * nqr)
+    f["force_angular"] = PA * (geo + basis_fd + harm_g + nqa * (4 * ka + 96) + 200) + N * nqa * (72 + q4)
+    f["force_atoms"] = PR * (16 * kr + 40) + PA * 21
     f["tangent_radial"] = PR * (14 * kr + 39) + N * 2 * ns * kr * nqr
-    f["tangent_angular"] = PA * (u + geo + basis_fd + harm_g + nqa * (4 * ka + 240)) + N * nqa * (48 + q4)
-    f["mlp_bwd"] = N * (4 * D * H + 8 * H + D)
-    f["cgrad_angular"] = PA * (u + geo + basis_fd + harm_g + nqa * (294 + 4 * ka)) + N * nqa * 24 * 6
-    f["reduce_W0"] = N * 4 * H * D
-    f["reduce_cR"] = N * 4 * nqr * ns * kr
+    f["tangent_angular"] = PA * (u + geo + basis_fd + harm_g + dirder + nqa * (4 * ka + 96)) + N * nqa * (48 + q4)
+    f["mlp_bwd"] = N * (8 * D * H + 12 * H + D)
+    f["cgrad"] = PA * (u + geo + basis_fd + harm_g + dirder + nqa * (144 + 4 * ka)) + \
+        N * (nqa * (144 + 2 * q4) + 4 * nqr * ns * kr)
     return f
 
 

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "gnep_internal.h"
+#include "network.cuh"
 
 using namespace gnep;
 
@@ -77,21 +78,21 @@ int alloc_workspace(gnep_model* m, gnep_nlist* nl) {
   struct Item { void** p; size_t bytes; };
   Workspace& w = nl->ws;
   w.red_len = loss_partial_doubles();
-  w.part_len = grad_partial_floats(m, nl->n_atoms);
+  const size_t NC = (size_t)(m->n_params - (int64_t)s.ns * m->net_size);
   std::vector<Item> items = {
       {(void**)&w.G, 4 * N * D},        {(void**)&w.Ep, 4 * N * D},       {(void**)&w.X, 4 * N * H},
       {(void**)&w.Eatom, 4 * N},        {(void**)&w.S, 4 * N * A24},      {(void**)&w.FR, 4 * N * FRn},
-      {(void**)&w.Shat, 4 * N * A24},   {(void**)&w.dR, 16 * PR},         {(void**)&w.dA, 16 * PA},
-      {(void**)&w.F, 12 * N},           {(void**)&w.Wat, 24 * N},         {(void**)&w.Es, 8 * S},
-      {(void**)&w.Ws, 48 * S},          {(void**)&w.a, 16 * N},           {(void**)&w.es, 4 * S},
-      {(void**)&w.Bs, 24 * S},          {(void**)&w.Gd, 4 * N * D},       {(void**)&w.Sd, 4 * N * A24},
-      {(void**)&w.FRd, 4 * N * FRn},    {(void**)&w.Gb, 4 * N * D},       {(void**)&w.alpha, 4 * N * H},
-      {(void**)&w.beta, 4 * N * H},     {(void**)&w.q1, 4 * N * H},       {(void**)&w.eatom, 4 * N},
-      {(void**)&w.dcA, 4 * N * s.nqa * s.ns * s.ka},
+      {(void**)&w.chat, 4 * N * FRn},   {(void**)&w.dA, 16 * PA},         {(void**)&w.F, 12 * N},
+      {(void**)&w.Wat, 24 * N},         {(void**)&w.Es, 8 * S},           {(void**)&w.Ws, 48 * S},
+      {(void**)&w.a, 16 * N},           {(void**)&w.es, 4 * S},           {(void**)&w.Bs, 24 * S},
+      {(void**)&w.Gd, 4 * N * D},       {(void**)&w.Sd, 4 * N * A24},     {(void**)&w.FRd, 4 * N * FRn},
+      {(void**)&w.Gb, 4 * N * D},
+      {(void**)&w.net_part, 4 * (size_t)kNetBlocks * s.ns * m->net_size},
+      {(void**)&w.cpart, 4 * (size_t)kCgBlocksMax * NC},
       {(void**)&w.red, 8 * (size_t)w.red_len},
-      {(void**)&w.part, 4 * (size_t)w.part_len},
       {(void**)&w.lab_e, 8 * S},        {(void**)&w.lab_f, 12 * N},       {(void**)&w.lab_v, 48 * S},
       {(void**)&w.coef, 8 * 8},         {(void**)&w.gradf, 4 * (size_t)m->n_params}};
+  (void)PR;
   size_t total = 0;
   for (auto& it : items) total += align256(it.bytes);
   char* base = nullptr;

@@ -48,24 +48,22 @@ struct PairList {
 // Per-step device workspace of one batch (sized at build, reused every step).
 struct Workspace {
   float *G = nullptr, *Ep = nullptr, *X = nullptr, *Eatom = nullptr;
-  float *S = nullptr, *FR = nullptr, *Shat = nullptr;
-  float4 *dR = nullptr, *dA = nullptr;
+  float *S = nullptr, *FR = nullptr, *chat = nullptr;
+  float4* dA = nullptr;
   float *F = nullptr, *Wat = nullptr;
   double *Es = nullptr, *Ws = nullptr;
-  float4* a = nullptr;            // force residual coefficients a_i
+  float4* a = nullptr;                 // force residual coefficients a_i
   float *es = nullptr, *Bs = nullptr;  // energy and virial residual coefficients
-  float *Gd = nullptr, *Sd = nullptr, *FRd = nullptr;
-  float *Gb = nullptr, *alpha = nullptr, *beta = nullptr, *q1 = nullptr, *eatom = nullptr;
-  float *Sb = nullptr, *Sdb = nullptr, *dcA = nullptr;
-  double* red = nullptr;          // reduction partials
+  float *Gd = nullptr, *Sd = nullptr, *FRd = nullptr, *Gb = nullptr;
+  float* net_part = nullptr;           // network-gradient partials [blocks][species][net_size]
+  float* cpart = nullptr;              // coefficient-gradient partials [blocks][c^R + c^A]
+  double* red = nullptr;               // loss partials
   int64_t red_len = 0;
-  float* part = nullptr;          // GEMM split partials
-  int64_t part_len = 0;
-  double* lab_e = nullptr;        // staged labels
+  double* lab_e = nullptr;             // staged labels
   float* lab_f = nullptr;
   double* lab_v = nullptr;
-  double* coef = nullptr;         // [8] loss scalars for the residual kernels
-  float* gradf = nullptr;         // FP32 copy of the gradient for host output
+  double* coef = nullptr;              // [8] loss scalars for the residual kernels
+  float* gradf = nullptr;              // FP32 copy of the gradient for host output
 };
 
 }  // namespace gnep
@@ -148,9 +146,10 @@ int run_backward(const StepArgs& a);
 
 int shape_setup(const Shape& s);
 int run_descriptors_static(const StepArgs& a, float* G);
+int cgrad_blocks(int n_atoms, const Shape& s);
+constexpr int kCgBlocksMax = 608;
 
 // train.cu
-int64_t grad_partial_floats(const gnep_model* m, int n_atoms);
 int64_t loss_partial_doubles();
 int run_loss_impl(const gnep_model* m, gnep_nlist* nl, const double* le, const float* lf, const double* lv,
                   const gnep_labels* y, cudaStream_t st);

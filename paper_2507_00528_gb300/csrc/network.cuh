@@ -1,0 +1,30 @@
+// Network tile kernels (network.cu): declarations shared with the step driver.
+#pragma once
+#include "gnep_internal.h"
+
+namespace gnep {
+
+constexpr int kTileAtoms = 32;   // atoms per network tile
+constexpr int kNetBlocks = 456;  // persistent blocks of the backward pass (3 per SM)
+
+// Species-homogeneous tiles over the species-grouped atom order.
+struct Tiles {
+  const int* perm;
+  int soff[9];
+  int tbase[9];  // first tile of each species; tbase[ns] = tile count
+  int ns;
+};
+
+Tiles make_tiles(const gnep_nlist* nl, int ns);
+
+template <int D, int HP, int NS, int NQR, int KR>
+int mlp_setup();
+template <int D, int HP, int NS, int NQR, int KR>
+int mlp_forward(const gnep_model* m, gnep_nlist* nl, cudaStream_t st);
+template <int D, int HP>
+int mlp_backward(const gnep_model* m, gnep_nlist* nl, cudaStream_t st);
+
+// Hidden width padded to the instantiated tile width.
+inline int hidden_pad(int H) { return H <= 32 ? 32 : H <= 64 ? 64 : 128; }
+
+}  // namespace gnep

@@ -1,11 +1,11 @@
 // Shape-specialised sweeps of one training step over a packed batch.
 //
 //   sweep 1  descriptors  q_n (Eqs. 5-6), S_nlm and q_nl (Eqs. 7-8), 4-body q4_n
-//   network  E_i = F(s.G_i) (D1.1) with E'_i = dE_i/dG_i (D1.5)
-//   sweep 2  dE_i/dr_ij (C3.6) per pair, forces (Eq. 3), per-atom virial (Eq. 4)
+//   network  (network.cu) E_i, E'_i, per-atom radial contraction chat_i
+//   sweep 2  dE_i/dr_ij (C3.6), forces (Eq. 3), per-atom virial (Eq. 4)
 //   sweep 3  tangent  Gdot_i = sum_j dG_i/dr_ij . u_ij
-//   network  tangent and reverse pass, adjoints Gbar_i
-//   sweep 4  per-atom contributions to dL/dc^A
+//   network  (network.cu) tangent and reverse pass, adjoints Gbar_i
+//   sweep 4  dL/dc^R and dL/dc^A
 //
 // Gradient route.  With a_i = dL/dF_i and B_s = dL/dW_s held fixed (Eqs. 11-12),
 //   sum_i a_i.F_i + sum_s B_s:W_s = - sum_i sum_j u_ij . dE_i/dr_ij,
@@ -15,12 +15,21 @@
 // the mixed derivatives of App. C3 and D1.11-D1.17) equal -d/dtheta sum_i E'_i.Gdot_i:
 // one forward-mode sweep (3) and one reverse sweep (4) instead of explicit second
 // derivative tensors.
+//
+// Thread mappings.  Radial sweeps: RL consecutive lanes per atom, each taking
+// every RL-th pair, combined by warp shuffles.  Angular sweeps 1, 3, 4: a block
+// holds NA atoms; their pairs are processed in chunks of CH, the per-pair
+// geometry (basis, harmonics, directional derivatives) is computed once per
+// pair into shared memory, then consumed by one thread per (atom, channel
+// group).  Angular force: one thread per pair, with dE/dS_nlm of the block's
+// atoms in shared memory.  No float atomics anywhere: fixed summation order.
 #include <cstdio>
 #include <mutex>
 #include <string>
 
 #include "device_math.cuh"
 #include "gnep_internal.h"
+#include "network.cuh"
 
 namespace gnep {
 
@@ -33,11 +42,22 @@ struct Sh {
   __host__ __device__ static constexpr int v4b(int n) { return NQR + NQA * 4 + n; }
   static constexpr int NCR = NS * NS * NQR * KR;
   static constexpr int NCA = NS * NS * NQA * KA;
+  static constexpr int NQ = NQR > NQA ? NQR : NQA;
+};
+
+constexpr int RL = 4;           // lanes per atom in radial sweeps
+constexpr int CH = 128;         // pairs per geometry chunk
+constexpr int kCgBlocks = kCgBlocksMax;  // persistent blocks of the c-gradient sweep (4 per SM)
+
+// Angular thread map: TPA threads per atom, NPT channels per thread.
+template <int NQ, int NPT>
+struct AMap {
+  static constexpr int TPA = (NQ + NPT - 1) / NPT;
+  static constexpr int NA = 128 / TPA;
 };
 
 namespace {
 
-// Accumulate v into row J of acc[NS][K] without dynamic register indexing.
 template <int NS, int K>
 __device__ __forceinline__ void acc_row(float (&acc)[NS][K], int J, const float (&v)[K], float w) {
 #pragma unroll
@@ -66,8 +86,32 @@ __device__ __forceinline__ float3 sym_apply(const float* b, float3 r) {  // b = 
                      b[5] * r.x + b[4] * r.y + b[2] * r.z);
 }
 
+template <int NS, int K>
+__device__ __forceinline__ void lane_reduce(float (&acc)[NS][K]) {
+#pragma unroll
+  for (int o = 1; o < RL; o <<= 1)
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+#pragma unroll
+      for (int k = 0; k < K; ++k) acc[s][k] += __shfl_xor_sync(0xffffffffu, acc[s][k], o);
+}
+
+// Harmonics on the unit vector and, for a direction w, the directional
+// derivatives D_lm = grad_d B_lm . w = (I - u u^T) grad p(u) . w / r (B9.2).
+__device__ __forceinline__ void harmonics_dir(float x, float y, float z, float rinv, float wx, float wy, float wz,
+                                              float (&B)[NLM], float (&Dd)[NLM]) {
+  float gx[NLM], gy[NLM], gz[NLM];
+  harmonics_grad(x, y, z, 1.f, B, gx, gy, gz);  // projected gradient, not yet divided by r
+#pragma unroll
+  for (int q = 0; q < NLM; ++q) Dd[q] = (gx[q] * wx + gy[q] * wy + gz[q] * wz) * rinv;
+}
+
+}  // namespace
+
 // ------------------------------------------------------------- sweep 1
 
+// Radial descriptors: per-atom basis sums FR[J][k] = sum_{j in J} f_k(r_ij) and
+// q_n = sum_J sum_k c^R_nk^{IJ} FR[J][k]  (Eqs. 5-6).
 template <class C>
 __global__ void __launch_bounds__(128) k_desc_radial(int N, DevModel dm, const int* __restrict__ type,
                                                      const int* __restrict__ off, const float4* __restrict__ rij,
@@ -75,30 +119,36 @@ __global__ void __launch_bounds__(128) k_desc_radial(int N, DevModel dm, const i
   __shared__ float cR[C::NCR];
   for (int q = threadIdx.x; q < C::NCR; q += blockDim.x) cR[q] = dm.params[dm.off_cR + q];
   __syncthreads();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = gt / RL, lane = gt % RL;
+  const bool ok = i < N;
   float acc[C::NS][C::KR];
 #pragma unroll
   for (int s = 0; s < C::NS; ++s)
 #pragma unroll
     for (int k = 0; k < C::KR; ++k) acc[s][k] = 0.f;
-  const int p1 = off[i + 1];
-  for (int p = off[i]; p < p1; ++p) {
-    const float4 r = rij[p];
-    const float rr = sqrtf(r.x * r.x + r.y * r.y + r.z * r.z);
-    float f[C::KR];
-    radial_basis<C::KR>(rr, dm.rcr_inv, f);
-    acc_row<C::NS, C::KR>(acc, (int)r.w, f, 1.f);
+  if (ok) {
+    const int p1 = off[i + 1];
+    for (int p = off[i] + lane; p < p1; p += RL) {
+      const float4 r = rij[p];
+      const float rr = sqrtf(r.x * r.x + r.y * r.y + r.z * r.z);
+      float f[C::KR];
+      radial_basis<C::KR>(rr, dm.rcr_inv, f);
+      acc_row<C::NS, C::KR>(acc, (int)r.w, f, 1.f);
+    }
   }
+  lane_reduce(acc);
+  if (!ok) return;
+  const int I = type[i];
   float* fr = FR + (size_t)i * C::NS * C::KR;
 #pragma unroll
   for (int s = 0; s < C::NS; ++s)
 #pragma unroll
-    for (int k = 0; k < C::KR; ++k) fr[s * C::KR + k] = acc[s][k];
-  const int I = type[i];
-  // q_n = sum_J sum_k c^R_nk^{IJ} sum_{j in J} f_k(r_ij)   (Eqs. 5-6)
+    for (int k = 0; k < C::KR; ++k)
+      if ((s * C::KR + k) % RL == lane) fr[s * C::KR + k] = acc[s][k];
 #pragma unroll
   for (int n = 0; n < C::NQR; ++n) {
+    if (n % RL != lane) continue;
     float q = 0.f;
 #pragma unroll
     for (int s = 0; s < C::NS; ++s)
@@ -108,239 +158,245 @@ __global__ void __launch_bounds__(128) k_desc_radial(int N, DevModel dm, const i
   }
 }
 
-template <class C>
+// Angular descriptors S_nlm = sum_j g_n(r_ij) B_lm (Eq. 8), q_nl (Eq. 7), q4_n.
+template <class C, int NPT>
 __global__ void __launch_bounds__(128) k_desc_angular(int N, DevModel dm, const int* __restrict__ type,
                                                       const int* __restrict__ off, const float4* __restrict__ rij,
                                                       float* __restrict__ Sout, float* __restrict__ G) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i = t / C::NQA, n = t - i * C::NQA;
-  if (i >= N) return;
-  const int I = type[i];
-  float c[C::NS][C::KA];
+  using M = AMap<C::NQA, NPT>;
+  __shared__ float sf[C::KA][CH];
+  __shared__ float sB[NLM][CH];
+  __shared__ int sJ[CH];
+  const int tid = threadIdx.x;
+  const int i0 = blockIdx.x * M::NA;
+  const int a = tid / M::TPA, tq = tid % M::TPA;
+  const int i = i0 + a;
+  const bool ok = a < M::NA && i < N;
+  float c[NPT][C::NS][C::KA];
+  float S[NPT][NLM];
+  const int I = ok ? type[i] : 0;
 #pragma unroll
-  for (int s = 0; s < C::NS; ++s)
+  for (int h = 0; h < NPT; ++h) {
+    const int n = tq * NPT + h;
 #pragma unroll
-    for (int k = 0; k < C::KA; ++k) c[s][k] = dm.params[dm.off_cA + ((I * C::NS + s) * C::NQA + n) * C::KA + k];
-  float S[NLM];
+    for (int s = 0; s < C::NS; ++s)
 #pragma unroll
-  for (int q = 0; q < NLM; ++q) S[q] = 0.f;
-  const int p1 = off[i + 1];
-  for (int p = off[i]; p < p1; ++p) {
-    const float4 r = rij[p];
-    const float rr = sqrtf(r.x * r.x + r.y * r.y + r.z * r.z);
-    const float ri = 1.f / rr;
-    float f[C::KA];
-    radial_basis<C::KA>(rr, dm.rca_inv, f);
-    const float g = dot_row<C::NS, C::KA>(c, (int)r.w, f);  // Eq. 6
-    float B[NLM];
-    harmonics(r.x * ri, r.y * ri, r.z * ri, B);
+      for (int k = 0; k < C::KA; ++k)
+        c[h][s][k] = (ok && n < C::NQA) ? dm.params[dm.off_cA + ((I * C::NS + s) * C::NQA + n) * C::KA + k] : 0.f;
 #pragma unroll
-    for (int q = 0; q < NLM; ++q) S[q] = fmaf(g, B[q], S[q]);  // Eq. 8
+    for (int q = 0; q < NLM; ++q) S[h][q] = 0.f;
   }
-  float* so = Sout + ((size_t)i * C::NQA + n) * NLM;
+  const int P0 = off[min(i0, N)], P1 = off[min(i0 + M::NA, N)];
+  const int pa0 = ok ? off[i] : 0, pa1 = ok ? off[i + 1] : 0;
+  for (int cs = P0; cs < P1; cs += CH) {
+    const int ce = min(cs + CH, P1);
+    const int p = cs + tid;
+    if (p < ce) {
+      const float4 r = rij[p];
+      const float rr = sqrtf(r.x * r.x + r.y * r.y + r.z * r.z);
+      const float ri = 1.f / rr;
+      float f[C::KA];
+      radial_basis<C::KA>(rr, dm.rca_inv, f);
 #pragma unroll
-  for (int q = 0; q < NLM; ++q) so[q] = S[q];
-  float* gi = G + (size_t)i * C::NDES;
+      for (int k = 0; k < C::KA; ++k) sf[k][tid] = f[k];
+      float B[NLM];
+      harmonics(r.x * ri, r.y * ri, r.z * ri, B);
 #pragma unroll
-  for (int l = 1; l <= 4; ++l) {
-    float q = 0.f;  // Eq. 7
+      for (int q = 0; q < NLM; ++q) sB[q][tid] = B[q];
+      sJ[tid] = (int)r.w;
+    }
+    __syncthreads();
+    const int q0 = max(pa0, cs), q1 = min(pa1, ce);
+    for (int pp = q0; pp < q1; ++pp) {
+      const int sl = pp - cs;
+      const int J = sJ[sl];
+      float f[C::KA];
 #pragma unroll
-    for (int lm = l * l - 1; lm < (l + 1) * (l + 1) - 1; ++lm) q = fmaf(kClm[lm] * S[lm], S[lm], q);
-    gi[C::vang(n, l)] = q;
+      for (int k = 0; k < C::KA; ++k) f[k] = sf[k][sl];
+      float g[NPT];
+#pragma unroll
+      for (int h = 0; h < NPT; ++h) g[h] = dot_row<C::NS, C::KA>(c[h], J, f);  // Eq. 6
+#pragma unroll
+      for (int q = 0; q < NLM; ++q) {
+        const float b = sB[q][sl];
+#pragma unroll
+        for (int h = 0; h < NPT; ++h) S[h][q] = fmaf(g[h], b, S[h][q]);  // Eq. 8
+      }
+    }
+    __syncthreads();
   }
-  if (C::FB) gi[C::v4b(n)] = q4_value(&S[3]);
-}
-
-// ------------------------------------------------------------- network
-
-// Network forward per atom (D1.1-D1.5): z = W0 (s.G) + b0, x = tanh z,
-// E = w1.x + b1, E' = s . (W0^T (w1 (1 - x^2))).  Weights of all species in smem.
-template <class C>
-__global__ void __launch_bounds__(128) k_mlp_fwd(int N, DevModel dm, const int* __restrict__ type,
-                                                 const float* __restrict__ G, float* __restrict__ X,
-                                                 float* __restrict__ Ep, float* __restrict__ Eatom) {
-  extern __shared__ float sm[];
-  const int H = dm.H;
-  for (int q = threadIdx.x; q < C::NS * dm.net_size; q += blockDim.x) sm[q] = dm.params[q];
-  __syncthreads();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  const int e = type[i];
-  const float* W0 = sm + e * dm.net_size;
-  const float* b0 = W0 + C::NDES * H;
-  const float* w1 = b0 + H;
-  float g[C::NDES], ep[C::NDES];
+  if (!ok) return;
 #pragma unroll
-  for (int v = 0; v < C::NDES; ++v) {
-    g[v] = dm.scale[v] * G[(size_t)i * C::NDES + v];
-    ep[v] = 0.f;
+  for (int h = 0; h < NPT; ++h) {
+    const int n = tq * NPT + h;
+    if (n >= C::NQA) continue;
+    float* so = Sout + ((size_t)i * C::NQA + n) * NLM;
+#pragma unroll
+    for (int q = 0; q < NLM; ++q) so[q] = S[h][q];
+    float* gi = G + (size_t)i * C::NDES;
+#pragma unroll
+    for (int l = 1; l <= 4; ++l) {
+      float q = 0.f;  // Eq. 7
+#pragma unroll
+      for (int lm = l * l - 1; lm < (l + 1) * (l + 1) - 1; ++lm) q = fmaf(kClm[lm] * S[h][lm], S[h][lm], q);
+      gi[C::vang(n, l)] = q;
+    }
+    if (C::FB) gi[C::v4b(n)] = q4_value(&S[h][3]);
   }
-  float E = w1[H];
-  for (int mu = 0; mu < H; ++mu) {
-    const float* w = W0 + mu * C::NDES;
-    float z = b0[mu];
-#pragma unroll
-    for (int v = 0; v < C::NDES; ++v) z = fmaf(w[v], g[v], z);
-    const float x = tanhf(z);
-    X[(size_t)i * H + mu] = x;
-    E = fmaf(w1[mu], x, E);
-    const float beta = w1[mu] * (1.f - x * x);
-#pragma unroll
-    for (int v = 0; v < C::NDES; ++v) ep[v] = fmaf(beta, w[v], ep[v]);
-  }
-#pragma unroll
-  for (int v = 0; v < C::NDES; ++v) Ep[(size_t)i * C::NDES + v] = ep[v] * dm.scale[v];
-  Eatom[i] = E;
 }
 
 // ------------------------------------------------------------- sweep 2
 
-// dE_i/dS_nlm = E'_nl 2 C_lm S_nlm (+ E'_4b,n dq4/dS_n2m), one thread per (atom, n).
+// Angular pairs, one thread per pair, NAF atoms per block with
+// Shat_nlm = dE_i/dS_nlm = E'_nl 2 C_lm S_nlm (+ E'_4b,n dq4/dS_n2m) in shared memory:
+//   dE_i/dr_ij = sum_n [g_n' (Shat_n . B) u + g_n Shat_n . grad B]       (C2.1, C2.3, C3.6)
+//             = (sum_lm ghat'_lm B_lm) u + (I - u u^T)(sum_lm ghat_lm grad p_lm) / r,
+//   ghat_lm = sum_n g_n Shat_nlm, ghat'_lm = sum_n g_n' Shat_nlm.
+constexpr int NAF = 16;
 template <class C>
-__global__ void __launch_bounds__(128) k_shat(int N, const float* __restrict__ Sang, const float* __restrict__ Ep,
-                                              float* __restrict__ Shat) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i = t / C::NQA, n = t - i * C::NQA;
-  if (i >= N) return;
-  const float* S = Sang + ((size_t)i * C::NQA + n) * NLM;
-  const float* ep = Ep + (size_t)i * C::NDES;
-  float* o = Shat + ((size_t)i * C::NQA + n) * NLM;
-  float s[NLM];
+__global__ void __launch_bounds__(128) k_force_angular(int N, DevModel dm, const int* __restrict__ type,
+                                                       const int* __restrict__ off, const int* __restrict__ own,
+                                                       const float4* __restrict__ rij, const float* __restrict__ Sang,
+                                                       const float* __restrict__ Ep, float4* __restrict__ dA) {
+  __shared__ float cA[C::NCA];
+  __shared__ float sh[NAF][C::NQA][NLM];
+  const int i0 = blockIdx.x * NAF;
+  for (int q = threadIdx.x; q < C::NCA; q += blockDim.x) cA[q] = dm.params[dm.off_cA + q];
+  for (int t = threadIdx.x; t < NAF * C::NQA; t += blockDim.x) {
+    const int a = t / C::NQA, n = t % C::NQA, i = i0 + a;
+    if (i >= N) continue;
+    const float* S = Sang + ((size_t)i * C::NQA + n) * NLM;
+    const float* ep = Ep + (size_t)i * C::NDES;
+    float s[NLM];
 #pragma unroll
-  for (int q = 0; q < NLM; ++q) s[q] = S[q];
+    for (int q = 0; q < NLM; ++q) s[q] = S[q];
 #pragma unroll
-  for (int lm = 0; lm < NLM; ++lm) o[lm] = 2.f * kClm[lm] * ep[C::vang(n, lm_l(lm))] * s[lm];
-  if (C::FB) {
-    float g4[5];
-    q4_grad(&s[3], g4);
-    const float e4 = ep[C::v4b(n)];
+    for (int lm = 0; lm < NLM; ++lm) sh[a][n][lm] = 2.f * kClm[lm] * ep[C::vang(n, lm_l(lm))] * s[lm];
+    if (C::FB) {
+      float g4[5];
+      q4_grad(&s[3], g4);
+      const float e4 = ep[C::v4b(n)];
 #pragma unroll
-    for (int m = 0; m < 5; ++m) o[3 + m] = fmaf(e4, g4[m], o[3 + m]);
+      for (int m = 0; m < 5; ++m) sh[a][n][3 + m] = fmaf(e4, g4[m], sh[a][n][3 + m]);
+    }
+  }
+  __syncthreads();
+  const int P0 = off[min(i0, N)], P1 = off[min(i0 + NAF, N)];
+  for (int p = P0 + threadIdx.x; p < P1; p += blockDim.x) {
+    const int i = own[p];
+    const int a = i - i0;
+    const int I = type[i];
+    const float4 r = rij[p];
+    const int J = (int)r.w;
+    const float rr = sqrtf(r.x * r.x + r.y * r.y + r.z * r.z);
+    const float ri = 1.f / rr;
+    const float ux = r.x * ri, uy = r.y * ri, uz = r.z * ri;
+    float f[C::KA], fp[C::KA];
+    radial_basis_d<C::KA>(rr, dm.rca_inv, f, fp);
+    const float* cIJ = cA + (I * C::NS + J) * C::NQA * C::KA;
+    float g[C::NQA], gp[C::NQA];
+#pragma unroll
+    for (int n = 0; n < C::NQA; ++n) {
+      float a1 = 0.f, a2 = 0.f;
+#pragma unroll
+      for (int k = 0; k < C::KA; ++k) {
+        a1 = fmaf(cIJ[n * C::KA + k], f[k], a1);
+        a2 = fmaf(cIJ[n * C::KA + k], fp[k], a2);
+      }
+      g[n] = a1;
+      gp[n] = a2;
+    }
+    float B[NLM], gx[NLM], gy[NLM], gz[NLM];
+    harmonics_grad(ux, uy, uz, 1.f, B, gx, gy, gz);
+    float P = 0.f, vx = 0.f, vy = 0.f, vz = 0.f;
+#pragma unroll
+    for (int q = 0; q < NLM; ++q) {
+      float gh = 0.f, ghp = 0.f;
+#pragma unroll
+      for (int n = 0; n < C::NQA; ++n) {
+        const float s = sh[a][n][q];
+        gh = fmaf(g[n], s, gh);
+        ghp = fmaf(gp[n], s, ghp);
+      }
+      P = fmaf(ghp, B[q], P);
+      vx = fmaf(gh, gx[q], vx);
+      vy = fmaf(gh, gy[q], vy);
+      vz = fmaf(gh, gz[q], vz);
+    }
+    dA[p] = make_float4(P * ux + vx * ri, P * uy + vy * ri, P * uz + vz * ri, 0.f);
   }
 }
 
-// Radial pairs: dE_i/dr_ij = (sum_k chat_k^J f_k'(r)) r_ij / r with the per-atom
-// contraction chat_k^J = sum_n E'_n c^R_nk^{IJ}  (C1.1, C3.6).
+// Forces and per-atom virials, RL lanes per atom.
+//   radial pairs: d_ij - d_ji = (chat_i[J] . f'(r) + chat_j[I] . f'(r)) r_ij / r
+//                 (C1.1, C3.6 with the per-atom contraction chat = sum_n E'_n c^R_n)
+//   angular pairs: d_ij - d_rev(ij) from the pair forces of k_force_angular (Eq. 3)
+//   virial: -sum_j r_ij (x) d_ij, symmetrised (Eq. 4 summed over atoms).
 template <class C>
-__global__ void __launch_bounds__(128) k_force_radial(int N, DevModel dm, const int* __restrict__ type,
-                                                      const int* __restrict__ off, const float4* __restrict__ rij,
-                                                      const float* __restrict__ Ep, float4* __restrict__ dR) {
-  __shared__ float cR[C::NCR];
-  for (int q = threadIdx.x; q < C::NCR; q += blockDim.x) cR[q] = dm.params[dm.off_cR + q];
-  __syncthreads();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  const int I = type[i];
-  float ch[C::NS][C::KR];
-#pragma unroll
-  for (int s = 0; s < C::NS; ++s)
-#pragma unroll
-    for (int k = 0; k < C::KR; ++k) ch[s][k] = 0.f;
-#pragma unroll
-  for (int n = 0; n < C::NQR; ++n) {
-    const float e = Ep[(size_t)i * C::NDES + n];
+__global__ void __launch_bounds__(128) k_force_atoms(int N, DevModel dm, const int* __restrict__ type,
+                                                     const int* __restrict__ offR, const int* __restrict__ jR,
+                                                     const float4* __restrict__ rijR, const float* __restrict__ chat,
+                                                     const int* __restrict__ offA, const int* __restrict__ revA,
+                                                     const float4* __restrict__ rijA, const float4* __restrict__ dA,
+                                                     float* __restrict__ F, float* __restrict__ Wat) {
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = gt / RL, lane = gt % RL;
+  const bool ok = i < N;
+  float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // F (3), W (6)
+  if (ok) {
+    const int I = type[i];
+    float ci[C::NS][C::KR];
 #pragma unroll
     for (int s = 0; s < C::NS; ++s)
 #pragma unroll
-      for (int k = 0; k < C::KR; ++k) ch[s][k] = fmaf(e, cR[((I * C::NS + s) * C::NQR + n) * C::KR + k], ch[s][k]);
-  }
-  const int p1 = off[i + 1];
-  for (int p = off[i]; p < p1; ++p) {
-    const float4 r = rij[p];
-    const float rr = sqrtf(r.x * r.x + r.y * r.y + r.z * r.z);
-    float f[C::KR], fp[C::KR];
-    radial_basis_d<C::KR>(rr, dm.rcr_inv, f, fp);
-    const float ds = dot_row<C::NS, C::KR>(ch, (int)r.w, fp) / rr;
-    dR[p] = make_float4(ds * r.x, ds * r.y, ds * r.z, 0.f);
-  }
-}
-
-// Angular pairs, one thread per pair: dE_i/dr_ij = sum_n [g_n' (Shat_n . B) u + g_n Shat_n . grad B]
-// (C2.1, C2.3, C3.6 and the 4-body term through Shat).
-template <class C>
-__global__ void __launch_bounds__(128) k_force_angular(int64_t P, DevModel dm, const int* __restrict__ type,
-                                                       const int* __restrict__ own, const float4* __restrict__ rij,
-                                                       const float* __restrict__ Shat, float4* __restrict__ dA) {
-  __shared__ float cA[C::NCA];
-  for (int q = threadIdx.x; q < C::NCA; q += blockDim.x) cA[q] = dm.params[dm.off_cA + q];
-  __syncthreads();
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= P) return;
-  const int i = own[p];
-  const int I = type[i];
-  const float4 r = rij[p];
-  const int J = (int)r.w;
-  const float rr = sqrtf(r.x * r.x + r.y * r.y + r.z * r.z);
-  const float ri = 1.f / rr;
-  const float ux = r.x * ri, uy = r.y * ri, uz = r.z * ri;
-  float f[C::KA], fp[C::KA];
-  radial_basis_d<C::KA>(rr, dm.rca_inv, f, fp);
-  float B[NLM], gx[NLM], gy[NLM], gz[NLM];
-  harmonics_grad(ux, uy, uz, ri, B, gx, gy, gz);
-  const float* cIJ = cA + (I * C::NS + J) * C::NQA * C::KA;
-  float dx = 0.f, dy = 0.f, dz = 0.f;
-  for (int n = 0; n < C::NQA; ++n) {
-    float g = 0.f, gp = 0.f;
+      for (int k = 0; k < C::KR; ++k) ci[s][k] = chat[((size_t)i * C::NS + s) * C::KR + k];
+    const int p1 = offR[i + 1];
+    for (int p = offR[i] + lane; p < p1; p += RL) {
+      const float4 r = rijR[p];
+      const int j = jR[p];
+      const float rr = sqrtf(r.x * r.x + r.y * r.y + r.z * r.z);
+      float f[C::KR], fp[C::KR];
+      radial_basis_d<C::KR>(rr, dm.rcr_inv, f, fp);
+      const float dij = dot_row<C::NS, C::KR>(ci, (int)r.w, fp);
+      const float* cj = chat + ((size_t)j * C::NS + I) * C::KR;
+      float dji = 0.f;
 #pragma unroll
-    for (int k = 0; k < C::KA; ++k) {
-      g = fmaf(cIJ[n * C::KA + k], f[k], g);
-      gp = fmaf(cIJ[n * C::KA + k], fp[k], gp);
+      for (int k = 0; k < C::KR; ++k) dji = fmaf(cj[k], fp[k], dji);
+      const float s1 = (dij + dji) / rr, s0 = dij / rr;
+      v[0] += s1 * r.x;
+      v[1] += s1 * r.y;
+      v[2] += s1 * r.z;
+      v[3] -= s0 * r.x * r.x;
+      v[4] -= s0 * r.y * r.y;
+      v[5] -= s0 * r.z * r.z;
+      v[6] -= s0 * r.x * r.y;
+      v[7] -= s0 * r.y * r.z;
+      v[8] -= s0 * r.z * r.x;
     }
-    const float* sh = Shat + ((size_t)i * C::NQA + n) * NLM;
-    float pb = 0.f, vx = 0.f, vy = 0.f, vz = 0.f;
-#pragma unroll
-    for (int q = 0; q < NLM; ++q) {
-      const float s = sh[q];
-      pb = fmaf(s, B[q], pb);
-      vx = fmaf(s, gx[q], vx);
-      vy = fmaf(s, gy[q], vy);
-      vz = fmaf(s, gz[q], vz);
-    }
-    const float a = gp * pb;
-    dx += a * ux + g * vx;
-    dy += a * uy + g * vy;
-    dz += a * uz + g * vz;
-  }
-  dA[p] = make_float4(dx, dy, dz, 0.f);
-}
-
-}  // namespace
-
-// F_i = sum_j (d_ij - d_{rev(ij)}) over both lists (Eq. 3); per-atom virial
-// -sum_j r_ij (x) d_ij, symmetrised (Eq. 4 summed over atoms gives the total).
-__global__ void __launch_bounds__(128) k_force_gather(int N, const int* __restrict__ offR, const int* __restrict__ revR,
-                                                      const float4* __restrict__ rijR, const float4* __restrict__ dR,
-                                                      const int* __restrict__ offA, const int* __restrict__ revA,
-                                                      const float4* __restrict__ rijA, const float4* __restrict__ dA,
-                                                      float* __restrict__ F, float* __restrict__ Wat) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  float fx = 0.f, fy = 0.f, fz = 0.f;
-  float w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  for (int L = 0; L < 2; ++L) {
-    const int* off = L ? offA : offR;
-    const int* rev = L ? revA : revR;
-    const float4* rij = L ? rijA : rijR;
-    const float4* d = L ? dA : dR;
-    const int p1 = off[i + 1];
-    for (int p = off[i]; p < p1; ++p) {
-      const float4 a = d[p], b = d[rev[p]], r = rij[p];
-      fx += a.x - b.x;
-      fy += a.y - b.y;
-      fz += a.z - b.z;
-      w[0] -= r.x * a.x;
-      w[1] -= r.y * a.y;
-      w[2] -= r.z * a.z;
-      w[3] -= 0.5f * (r.x * a.y + r.y * a.x);
-      w[4] -= 0.5f * (r.y * a.z + r.z * a.y);
-      w[5] -= 0.5f * (r.z * a.x + r.x * a.z);
+    const int q1 = offA[i + 1];
+    for (int p = offA[i] + lane; p < q1; p += RL) {
+      const float4 d = dA[p], b = dA[revA[p]], r = rijA[p];
+      v[0] += d.x - b.x;
+      v[1] += d.y - b.y;
+      v[2] += d.z - b.z;
+      v[3] -= r.x * d.x;
+      v[4] -= r.y * d.y;
+      v[5] -= r.z * d.z;
+      v[6] -= 0.5f * (r.x * d.y + r.y * d.x);
+      v[7] -= 0.5f * (r.y * d.z + r.z * d.y);
+      v[8] -= 0.5f * (r.z * d.x + r.x * d.z);
     }
   }
-  F[3 * (size_t)i] = fx;
-  F[3 * (size_t)i + 1] = fy;
-  F[3 * (size_t)i + 2] = fz;
 #pragma unroll
-  for (int q = 0; q < 6; ++q) Wat[6 * (size_t)i + q] = w[q];
+  for (int o = 1; o < RL; o <<= 1)
+#pragma unroll
+    for (int q = 0; q < 9; ++q) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+  if (!ok || lane != 0) return;
+  F[3 * (size_t)i] = v[0];
+  F[3 * (size_t)i + 1] = v[1];
+  F[3 * (size_t)i + 2] = v[2];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) Wat[6 * (size_t)i + q] = v[3 + q];
 }
 
 // E_s = sum_i E_i and W_s = sum_i w_i in FP64, one block per structure.
@@ -372,11 +428,10 @@ __global__ void __launch_bounds__(128) k_struct_sum(const int* __restrict__ soff
   }
 }
 
-namespace {
-
 // ------------------------------------------------------------- sweep 3
 
-// Radial tangent: qdot_n = sum_J sum_k c^R_nk^{IJ} sum_{j in J} f_k'(r_ij) (u_hat . u_ij).
+// Radial tangent: FRd[J][k] = sum_{j in J} f_k'(r_ij) (u_hat . u_ij),
+// qdot_n = sum_J sum_k c^R_nk^{IJ} FRd[J][k].
 template <class C>
 __global__ void __launch_bounds__(128) k_tangent_radial(int N, DevModel dm, const int* __restrict__ type,
                                                         const int* __restrict__ atom_struct, const int* __restrict__ off,
@@ -386,37 +441,44 @@ __global__ void __launch_bounds__(128) k_tangent_radial(int N, DevModel dm, cons
   __shared__ float cR[C::NCR];
   for (int q = threadIdx.x; q < C::NCR; q += blockDim.x) cR[q] = dm.params[dm.off_cR + q];
   __syncthreads();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  const float4 ai = a[i];
-  float b[6];
-#pragma unroll
-  for (int q = 0; q < 6; ++q) b[q] = Bs[6 * atom_struct[i] + q];
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = gt / RL, lane = gt % RL;
+  const bool ok = i < N;
   float acc[C::NS][C::KR];
 #pragma unroll
   for (int s = 0; s < C::NS; ++s)
 #pragma unroll
     for (int k = 0; k < C::KR; ++k) acc[s][k] = 0.f;
-  const int p1 = off[i + 1];
-  for (int p = off[i]; p < p1; ++p) {
-    const float4 r = rij[p];
-    const float4 aj = a[jj[p]];
-    const float3 br = sym_apply(b, make_float3(r.x, r.y, r.z));
-    const float ux = aj.x - ai.x + br.x, uy = aj.y - ai.y + br.y, uz = aj.z - ai.z + br.z;
-    const float rr = sqrtf(r.x * r.x + r.y * r.y + r.z * r.z);
-    const float ru = (r.x * ux + r.y * uy + r.z * uz) / rr;
-    float f[C::KR], fp[C::KR];
-    radial_basis_d<C::KR>(rr, dm.rcr_inv, f, fp);
-    acc_row<C::NS, C::KR>(acc, (int)r.w, fp, ru);
+  if (ok) {
+    const float4 ai = a[i];
+    float b[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) b[q] = Bs[6 * atom_struct[i] + q];
+    const int p1 = off[i + 1];
+    for (int p = off[i] + lane; p < p1; p += RL) {
+      const float4 r = rij[p];
+      const float4 aj = a[jj[p]];
+      const float3 br = sym_apply(b, make_float3(r.x, r.y, r.z));
+      const float ux = aj.x - ai.x + br.x, uy = aj.y - ai.y + br.y, uz = aj.z - ai.z + br.z;
+      const float rr = sqrtf(r.x * r.x + r.y * r.y + r.z * r.z);
+      const float ru = (r.x * ux + r.y * uy + r.z * uz) / rr;
+      float f[C::KR], fp[C::KR];
+      radial_basis_d<C::KR>(rr, dm.rcr_inv, f, fp);
+      acc_row<C::NS, C::KR>(acc, (int)r.w, fp, ru);
+    }
   }
+  lane_reduce(acc);
+  if (!ok) return;
   float* fr = FRd + (size_t)i * C::NS * C::KR;
 #pragma unroll
   for (int s = 0; s < C::NS; ++s)
 #pragma unroll
-    for (int k = 0; k < C::KR; ++k) fr[s * C::KR + k] = acc[s][k];
+    for (int k = 0; k < C::KR; ++k)
+      if ((s * C::KR + k) % RL == lane) fr[s * C::KR + k] = acc[s][k];
   const int I = type[i];
 #pragma unroll
   for (int n = 0; n < C::NQR; ++n) {
+    if (n % RL != lane) continue;
     float q = 0.f;
 #pragma unroll
     for (int s = 0; s < C::NS; ++s)
@@ -426,230 +488,295 @@ __global__ void __launch_bounds__(128) k_tangent_radial(int N, DevModel dm, cons
   }
 }
 
-// Angular tangent, one thread per (atom, n):
-// Sdot_nlm = sum_j [g_n' (u_hat . u) B_lm + g_n grad B_lm . u],
-// qdot_nl = 2 sum_m C_lm S_nlm Sdot_nlm, qdot4_n = dq4/dS . Sdot.
+// Angular geometry for the tangent and c-gradient sweeps, one pair per thread:
+// basis f_k, fu_k = f_k' (u_hat . u_ij), harmonics B_lm and D_lm = grad B_lm . u_ij.
 template <class C>
-__global__ void __launch_bounds__(128) k_tangent_angular(int N, DevModel dm, const int* __restrict__ type,
-                                                         const int* __restrict__ atom_struct, const int* __restrict__ off,
-                                                         const int* __restrict__ jj, const float4* __restrict__ rij,
-                                                         const float4* __restrict__ a, const float* __restrict__ Bs,
-                                                         const float* __restrict__ Sang, float* __restrict__ Sd,
-                                                         float* __restrict__ Gd) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i = t / C::NQA, n = t - i * C::NQA;
-  if (i >= N) return;
-  const int I = type[i];
-  float c[C::NS][C::KA];
+struct AngGeo {
+  float f[C::KA][CH];
+  float fu[C::KA][CH];
+  float B[NLM][CH];
+  float D[NLM][CH];
+  int J[CH];
+};
+
+template <class C>
+__device__ __forceinline__ void angular_geometry(AngGeo<C>& g, int slot, int p, const DevModel& dm,
+                                                 const int* __restrict__ own, const int* __restrict__ atom_struct,
+                                                 const int* __restrict__ jj, const float4* __restrict__ rij,
+                                                 const float4* __restrict__ a, const float* __restrict__ Bs) {
+  const float4 r = rij[p];
+  const int i = own[p];
+  const float4 ai = a[i], aj = a[jj[p]];
+  const float* b = Bs + 6 * atom_struct[i];
+  const float bb[6] = {b[0], b[1], b[2], b[3], b[4], b[5]};
+  const float3 br = sym_apply(bb, make_float3(r.x, r.y, r.z));
+  const float wx = aj.x - ai.x + br.x, wy = aj.y - ai.y + br.y, wz = aj.z - ai.z + br.z;
+  const float rr = sqrtf(r.x * r.x + r.y * r.y + r.z * r.z);
+  const float ri = 1.f / rr;
+  const float ux = r.x * ri, uy = r.y * ri, uz = r.z * ri;
+  const float ru = ux * wx + uy * wy + uz * wz;
+  float f[C::KA], fp[C::KA];
+  radial_basis_d<C::KA>(rr, dm.rca_inv, f, fp);
 #pragma unroll
-  for (int s = 0; s < C::NS; ++s)
-#pragma unroll
-    for (int k = 0; k < C::KA; ++k) c[s][k] = dm.params[dm.off_cA + ((I * C::NS + s) * C::NQA + n) * C::KA + k];
-  const float4 ai = a[i];
-  float b[6];
-#pragma unroll
-  for (int q = 0; q < 6; ++q) b[q] = Bs[6 * atom_struct[i] + q];
-  float sd[NLM];
-#pragma unroll
-  for (int q = 0; q < NLM; ++q) sd[q] = 0.f;
-  const int p1 = off[i + 1];
-  for (int p = off[i]; p < p1; ++p) {
-    const float4 r = rij[p];
-    const float4 aj = a[jj[p]];
-    const float3 br = sym_apply(b, make_float3(r.x, r.y, r.z));
-    const float vx = aj.x - ai.x + br.x, vy = aj.y - ai.y + br.y, vz = aj.z - ai.z + br.z;
-    const float rr = sqrtf(r.x * r.x + r.y * r.y + r.z * r.z);
-    const float ri = 1.f / rr;
-    const float ux = r.x * ri, uy = r.y * ri, uz = r.z * ri;
-    float f[C::KA], fp[C::KA];
-    radial_basis_d<C::KA>(rr, dm.rca_inv, f, fp);
-    float g = 0.f, gp = 0.f;
-    {
-      const int J = (int)r.w;
-#pragma unroll
-      for (int s = 0; s < C::NS; ++s) {
-        float tg = 0.f, tp = 0.f;
-#pragma unroll
-        for (int k = 0; k < C::KA; ++k) {
-          tg = fmaf(c[s][k], f[k], tg);
-          tp = fmaf(c[s][k], fp[k], tp);
-        }
-        g = (s == J) ? tg : g;
-        gp = (s == J) ? tp : gp;
-      }
-    }
-    float B[NLM], gx[NLM], gy[NLM], gz[NLM];
-    harmonics_grad(ux, uy, uz, ri, B, gx, gy, gz);
-    const float a1 = gp * (ux * vx + uy * vy + uz * vz);
-#pragma unroll
-    for (int q = 0; q < NLM; ++q) sd[q] += a1 * B[q] + g * (gx[q] * vx + gy[q] * vy + gz[q] * vz);
+  for (int k = 0; k < C::KA; ++k) {
+    g.f[k][slot] = f[k];
+    g.fu[k][slot] = fp[k] * ru;
   }
-  float* so = Sd + ((size_t)i * C::NQA + n) * NLM;
+  float B[NLM], Dd[NLM];
+  harmonics_dir(ux, uy, uz, ri, wx, wy, wz, B, Dd);
 #pragma unroll
-  for (int q = 0; q < NLM; ++q) so[q] = sd[q];
-  const float* S = Sang + ((size_t)i * C::NQA + n) * NLM;
-  float s[NLM];
-#pragma unroll
-  for (int q = 0; q < NLM; ++q) s[q] = S[q];
-  float* gi = Gd + (size_t)i * C::NDES;
-#pragma unroll
-  for (int l = 1; l <= 4; ++l) {
-    float q = 0.f;
-#pragma unroll
-    for (int lm = l * l - 1; lm < (l + 1) * (l + 1) - 1; ++lm) q = fmaf(2.f * kClm[lm] * s[lm], sd[lm], q);
-    gi[C::vang(n, l)] = q;
+  for (int q = 0; q < NLM; ++q) {
+    g.B[q][slot] = B[q];
+    g.D[q][slot] = Dd[q];
   }
-  if (C::FB) {
-    float g4[5];
-    q4_grad(&s[3], g4);
-    float q = 0.f;
-#pragma unroll
-    for (int m = 0; m < 5; ++m) q = fmaf(g4[m], sd[3 + m], q);
-    gi[C::v4b(n)] = q;
-  }
+  g.J[slot] = (int)r.w;
 }
 
-// Network tangent and reverse pass per atom.  With psi_i = E'_i . Gdot_i and the
-// energy residual weight e_i (= dL/dE_i):
-//   zdot = W0 (s.Gdot), beta = w1 (1 - x^2), alpha = e_i beta + 2 x beta zdot,
-//   Gbar = s . (W0^T alpha)                        (dL/dG_i, the c-gradient adjoint)
-//   dL/db0 += alpha, dL/dw1 += e_i x - (1 - x^2) zdot, dL/db1 += e_i,
-//   dL/dW0 += alpha (s.G)^T - beta (s.Gdot)^T     (reduced over atoms later).
-template <class C>
-__global__ void __launch_bounds__(128) k_mlp_bwd(int N, DevModel dm, const int* __restrict__ type,
-                                                 const int* __restrict__ atom_struct, const float* __restrict__ es,
-                                                 const float* __restrict__ Gd, const float* __restrict__ X,
-                                                 float* __restrict__ Gb, float* __restrict__ alpha,
-                                                 float* __restrict__ betaO, float* __restrict__ q1,
-                                                 float* __restrict__ eatom) {
-  extern __shared__ float sm[];
-  const int H = dm.H;
-  for (int q = threadIdx.x; q < C::NS * dm.net_size; q += blockDim.x) sm[q] = dm.params[q];
-  __syncthreads();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  const int e = type[i];
-  const float* W0 = sm + e * dm.net_size;
-  const float* w1 = W0 + C::NDES * H + H;
-  const float ei = es[atom_struct[i]];
-  eatom[i] = ei;
-  float gd[C::NDES], gb[C::NDES];
+// Angular tangent: Sdot_nlm = sum_j [g_n' (u_hat . u) B_lm + g_n grad B_lm . u],
+// qdot_nl = 2 sum_m C_lm S_nlm Sdot_nlm, qdot4_n = dq4/dS . Sdot.
+template <class C, int NPT>
+__global__ void __launch_bounds__(128) k_tangent_angular(int N, DevModel dm, const int* __restrict__ type,
+                                                         const int* __restrict__ atom_struct, const int* __restrict__ off,
+                                                         const int* __restrict__ own, const int* __restrict__ jj,
+                                                         const float4* __restrict__ rij, const float4* __restrict__ a,
+                                                         const float* __restrict__ Bs, const float* __restrict__ Sang,
+                                                         float* __restrict__ Sd, float* __restrict__ Gd) {
+  using M = AMap<C::NQA, NPT>;
+  __shared__ AngGeo<C> geo;
+  const int tid = threadIdx.x;
+  const int i0 = blockIdx.x * M::NA;
+  const int at = tid / M::TPA, tq = tid % M::TPA;
+  const int i = i0 + at;
+  const bool ok = at < M::NA && i < N;
+  float c[NPT][C::NS][C::KA];
+  float sd[NPT][NLM];
+  const int I = ok ? type[i] : 0;
 #pragma unroll
-  for (int v = 0; v < C::NDES; ++v) {
-    gd[v] = dm.scale[v] * Gd[(size_t)i * C::NDES + v];
-    gb[v] = 0.f;
+  for (int h = 0; h < NPT; ++h) {
+    const int n = tq * NPT + h;
+#pragma unroll
+    for (int s = 0; s < C::NS; ++s)
+#pragma unroll
+      for (int k = 0; k < C::KA; ++k)
+        c[h][s][k] = (ok && n < C::NQA) ? dm.params[dm.off_cA + ((I * C::NS + s) * C::NQA + n) * C::KA + k] : 0.f;
+#pragma unroll
+    for (int q = 0; q < NLM; ++q) sd[h][q] = 0.f;
   }
-  for (int mu = 0; mu < H; ++mu) {
-    const float* w = W0 + mu * C::NDES;
-    float zd = 0.f;
+  const int P0 = off[min(i0, N)], P1 = off[min(i0 + M::NA, N)];
+  const int pa0 = ok ? off[i] : 0, pa1 = ok ? off[i + 1] : 0;
+  for (int cs = P0; cs < P1; cs += CH) {
+    const int ce = min(cs + CH, P1);
+    if (cs + tid < ce) angular_geometry<C>(geo, tid, cs + tid, dm, own, atom_struct, jj, rij, a, Bs);
+    __syncthreads();
+    const int q0 = max(pa0, cs), q1 = min(pa1, ce);
+    for (int pp = q0; pp < q1; ++pp) {
+      const int sl = pp - cs;
+      const int J = geo.J[sl];
+      float f[C::KA], fu[C::KA];
 #pragma unroll
-    for (int v = 0; v < C::NDES; ++v) zd = fmaf(w[v], gd[v], zd);
-    const float x = X[(size_t)i * H + mu];
-    const float t1 = 1.f - x * x;
-    const float beta = w1[mu] * t1;
-    const float al = ei * beta + 2.f * x * beta * zd;
+      for (int k = 0; k < C::KA; ++k) {
+        f[k] = geo.f[k][sl];
+        fu[k] = geo.fu[k][sl];
+      }
+      float g[NPT], ga[NPT];
 #pragma unroll
-    for (int v = 0; v < C::NDES; ++v) gb[v] = fmaf(al, w[v], gb[v]);
-    alpha[(size_t)i * H + mu] = al;
-    betaO[(size_t)i * H + mu] = beta;
-    q1[(size_t)i * H + mu] = ei * x - t1 * zd;
+      for (int h = 0; h < NPT; ++h) {
+        g[h] = dot_row<C::NS, C::KA>(c[h], J, f);
+        ga[h] = dot_row<C::NS, C::KA>(c[h], J, fu);
+      }
+#pragma unroll
+      for (int q = 0; q < NLM; ++q) {
+        const float b = geo.B[q][sl], d = geo.D[q][sl];
+#pragma unroll
+        for (int h = 0; h < NPT; ++h) sd[h][q] = fmaf(ga[h], b, fmaf(g[h], d, sd[h][q]));
+      }
+    }
+    __syncthreads();
   }
+  if (!ok) return;
 #pragma unroll
-  for (int v = 0; v < C::NDES; ++v) Gb[(size_t)i * C::NDES + v] = gb[v] * dm.scale[v];
+  for (int h = 0; h < NPT; ++h) {
+    const int n = tq * NPT + h;
+    if (n >= C::NQA) continue;
+    float* so = Sd + ((size_t)i * C::NQA + n) * NLM;
+#pragma unroll
+    for (int q = 0; q < NLM; ++q) so[q] = sd[h][q];
+    const float* S = Sang + ((size_t)i * C::NQA + n) * NLM;
+    float s[NLM];
+#pragma unroll
+    for (int q = 0; q < NLM; ++q) s[q] = S[q];
+    float* gi = Gd + (size_t)i * C::NDES;
+#pragma unroll
+    for (int l = 1; l <= 4; ++l) {
+      float q = 0.f;
+#pragma unroll
+      for (int lm = l * l - 1; lm < (l + 1) * (l + 1) - 1; ++lm) q = fmaf(2.f * kClm[lm] * s[lm], sd[h][lm], q);
+      gi[C::vang(n, l)] = q;
+    }
+    if (C::FB) {
+      float g4[5];
+      q4_grad(&s[3], g4);
+      float q = 0.f;
+#pragma unroll
+      for (int m = 0; m < 5; ++m) q = fmaf(g4[m], sd[h][3 + m], q);
+      gi[C::v4b(n)] = q;
+    }
+  }
 }
 
 // ------------------------------------------------------------- sweep 4
 
-// Per-atom contributions to dL/dc^A_nk^{IJ}, one thread per (atom, n):
-//   Sbar_nlm  = Gbar_nl 2C S_nlm - E'_nl 2C Sdot_nlm  (+ 4-body terms)
-//   Sdbar_nlm = -E'_nl 2C S_nlm                        (+ 4-body term)
-//   per pair: P = sum_lm Sbar B + Sdbar grad B . u,  R = sum_lm Sdbar B,
-//   acc[J][k] += P f_k + R f_k' (u_hat . u).
+// dL/dc, one thread per (atom, channel n), persistent blocks over atom tiles.
+//   radial:  dL/dc^R_nk^{IJ} += Gbar_n FR[J][k] - E'_n FRd[J][k]
+//   angular: Sbar_nlm  = Gbar_nl 2C S_nlm - E'_nl 2C Sdot_nlm  (+ 4-body terms)
+//            Sdbar_nlm = -E'_nl 2C S_nlm                        (+ 4-body term)
+//            per pair: P = sum_lm Sbar B + Sdbar D,  R = sum_lm Sdbar B,
+//            dL/dc^A_nk^{IJ} += P f_k + R fu_k.
+// Each tile's per-thread sums are folded into a block accumulator in a fixed
+// order; the block writes cpart[block][c^R..., c^A...] once.
 template <class C>
-__global__ void __launch_bounds__(128) k_cgrad_angular(int N, DevModel dm, const int* __restrict__ atom_struct,
-                                                       const int* __restrict__ off, const int* __restrict__ jj,
-                                                       const float4* __restrict__ rij, const float4* __restrict__ a,
-                                                       const float* __restrict__ Bs, const float* __restrict__ Sang,
-                                                       const float* __restrict__ Sdd, const float* __restrict__ Gb,
-                                                       const float* __restrict__ Ep, float* __restrict__ dcA) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i = t / C::NQA, n = t - i * C::NQA;
-  if (i >= N) return;
-  float sb[NLM], sdb[NLM];
-  {
-    const float* S = Sang + ((size_t)i * C::NQA + n) * NLM;
-    const float* D = Sdd + ((size_t)i * C::NQA + n) * NLM;
-    const float* gb = Gb + (size_t)i * C::NDES;
-    const float* ep = Ep + (size_t)i * C::NDES;
-    float s[NLM], d[NLM];
+__global__ void __launch_bounds__(128) k_cgrad(int N, int ntile, DevModel dm, const int* __restrict__ type,
+                                               const int* __restrict__ atom_struct, const int* __restrict__ off,
+                                               const int* __restrict__ own, const int* __restrict__ jj,
+                                               const float4* __restrict__ rij, const float4* __restrict__ a,
+                                               const float* __restrict__ Bs, const float* __restrict__ Sang,
+                                               const float* __restrict__ Sdd, const float* __restrict__ Gb,
+                                               const float* __restrict__ Ep, const float* __restrict__ FR,
+                                               const float* __restrict__ FRd, float* __restrict__ cpart) {
+  using M = AMap<C::NQ, 1>;
+  constexpr int NCR = C::NCR, NCA = C::NCA;
+  constexpr int RA = C::NS * C::KR, AA = C::NS * C::KA;  // per-thread radial / angular sums
+  // the per-tile sums are only used after the chunk loop: overlay them on the geometry
+  union Smem {
+    AngGeo<C> geo;
+    float tsum[M::NA][C::NQ][RA + AA];
+  };
+  __shared__ Smem smu;
+  AngGeo<C>& geo = smu.geo;
+  auto& tsum = smu.tsum;
+  __shared__ float bacc[NCR + NCA];
+  __shared__ int ttype[M::NA];
+  const int tid = threadIdx.x;
+  const int at = tid / M::TPA, n = tid % M::TPA;
+  for (int q = tid; q < NCR + NCA; q += blockDim.x) bacc[q] = 0.f;
+
+  for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+    const int i0 = tile * M::NA;
+    const int i = i0 + at;
+    const bool ok = at < M::NA && i < N;
+    const bool okA = ok && n < C::NQA, okR = ok && n < C::NQR;
+    __syncthreads();
+    if (tid < M::NA) ttype[tid] = (i0 + tid < N) ? type[i0 + tid] : -1;
+    float accA[C::NS][C::KA];
 #pragma unroll
-    for (int q = 0; q < NLM; ++q) { s[q] = S[q]; d[q] = D[q]; }
+    for (int s = 0; s < C::NS; ++s)
 #pragma unroll
-    for (int lm = 0; lm < NLM; ++lm) {
-      const int v = C::vang(n, lm_l(lm));
-      const float c2 = 2.f * kClm[lm];
-      sb[lm] = c2 * (gb[v] * s[lm] - ep[v] * d[lm]);
-      sdb[lm] = -c2 * ep[v] * s[lm];
-    }
-    if (C::FB) {
-      float g4[5], h4[5];
-      q4_grad(&s[3], g4);
-      q4_hvp(&s[3], &d[3], h4);
-      const float gb4 = gb[C::v4b(n)], ep4 = ep[C::v4b(n)];
+      for (int k = 0; k < C::KA; ++k) accA[s][k] = 0.f;
+    float sb[NLM], sdb[NLM];
 #pragma unroll
-      for (int m = 0; m < 5; ++m) {
-        sb[3 + m] += gb4 * g4[m] - ep4 * h4[m];
-        sdb[3 + m] -= ep4 * g4[m];
+    for (int q = 0; q < NLM; ++q) sb[q] = sdb[q] = 0.f;
+    if (okA) {
+      const float* S = Sang + ((size_t)i * C::NQA + n) * NLM;
+      const float* Dd = Sdd + ((size_t)i * C::NQA + n) * NLM;
+      const float* gb = Gb + (size_t)i * C::NDES;
+      const float* ep = Ep + (size_t)i * C::NDES;
+      float s[NLM], d[NLM];
+#pragma unroll
+      for (int q = 0; q < NLM; ++q) { s[q] = S[q]; d[q] = Dd[q]; }
+#pragma unroll
+      for (int lm = 0; lm < NLM; ++lm) {
+        const int v = C::vang(n, lm_l(lm));
+        const float c2 = 2.f * kClm[lm];
+        sb[lm] = c2 * (gb[v] * s[lm] - ep[v] * d[lm]);
+        sdb[lm] = -c2 * ep[v] * s[lm];
+      }
+      if (C::FB) {
+        float g4[5], h4[5];
+        q4_grad(&s[3], g4);
+        q4_hvp(&s[3], &d[3], h4);
+        const float gb4 = gb[C::v4b(n)], ep4 = ep[C::v4b(n)];
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+          sb[3 + m] += gb4 * g4[m] - ep4 * h4[m];
+          sdb[3 + m] -= ep4 * g4[m];
+        }
       }
     }
-  }
-  const float4 ai = a[i];
-  float b[6];
+    const int P0 = off[min(i0, N)], P1 = off[min(i0 + M::NA, N)];
+    const int pa0 = okA ? off[i] : 0, pa1 = okA ? off[i + 1] : 0;
+    for (int cs = P0; cs < P1; cs += CH) {
+      const int ce = min(cs + CH, P1);
+      __syncthreads();
+      if (cs + tid < ce) angular_geometry<C>(geo, tid, cs + tid, dm, own, atom_struct, jj, rij, a, Bs);
+      __syncthreads();
+      const int q0 = max(pa0, cs), q1 = min(pa1, ce);
+      for (int pp = q0; pp < q1; ++pp) {
+        const int sl = pp - cs;
+        float P = 0.f, R = 0.f;
 #pragma unroll
-  for (int q = 0; q < 6; ++q) b[q] = Bs[6 * atom_struct[i] + q];
-  float acc[C::NS][C::KA];
+        for (int q = 0; q < NLM; ++q) {
+          const float b = geo.B[q][sl], d = geo.D[q][sl];
+          P = fmaf(sb[q], b, fmaf(sdb[q], d, P));
+          R = fmaf(sdb[q], b, R);
+        }
+        const int J = geo.J[sl];
 #pragma unroll
-  for (int s = 0; s < C::NS; ++s)
+        for (int s = 0; s < C::NS; ++s) {
+          const float wP = (s == J) ? P : 0.f, wR = (s == J) ? R : 0.f;
 #pragma unroll
-    for (int k = 0; k < C::KA; ++k) acc[s][k] = 0.f;
-  const int p1 = off[i + 1];
-  for (int p = off[i]; p < p1; ++p) {
-    const float4 r = rij[p];
-    const float4 aj = a[jj[p]];
-    const float3 br = sym_apply(b, make_float3(r.x, r.y, r.z));
-    const float vx = aj.x - ai.x + br.x, vy = aj.y - ai.y + br.y, vz = aj.z - ai.z + br.z;
-    const float rr = sqrtf(r.x * r.x + r.y * r.y + r.z * r.z);
-    const float ri = 1.f / rr;
-    const float ux = r.x * ri, uy = r.y * ri, uz = r.z * ri;
-    float f[C::KA], fp[C::KA];
-    radial_basis_d<C::KA>(rr, dm.rca_inv, f, fp);
-    float B[NLM], gx[NLM], gy[NLM], gz[NLM];
-    harmonics_grad(ux, uy, uz, ri, B, gx, gy, gz);
-    float P = 0.f, R = 0.f;
-#pragma unroll
-    for (int q = 0; q < NLM; ++q) {
-      P = fmaf(sb[q], B[q], P);
-      P = fmaf(sdb[q], gx[q] * vx + gy[q] * vy + gz[q] * vz, P);
-      R = fmaf(sdb[q], B[q], R);
+          for (int k = 0; k < C::KA; ++k) accA[s][k] = fmaf(wP, geo.f[k][sl], fmaf(wR, geo.fu[k][sl], accA[s][k]));
+        }
+      }
     }
-    const float Rr = R * (ux * vx + uy * vy + uz * vz);
-    const int J = (int)r.w;
+    // fold this tile into the block accumulator in atom order
+    __syncthreads();
+    if (at < M::NA && n < C::NQ) {
+      const float gbn = okR ? Gb[(size_t)i * C::NDES + n] : 0.f, epn = okR ? Ep[(size_t)i * C::NDES + n] : 0.f;
 #pragma unroll
-    for (int s = 0; s < C::NS; ++s) {
-      const float wP = (s == J) ? P : 0.f, wR = (s == J) ? Rr : 0.f;
+      for (int s = 0; s < C::NS; ++s) {
 #pragma unroll
-      for (int k = 0; k < C::KA; ++k) acc[s][k] = fmaf(wP, f[k], fmaf(wR, fp[k], acc[s][k]));
+        for (int k = 0; k < C::KR; ++k)
+          tsum[at][n][s * C::KR + k] =
+              okR ? gbn * FR[((size_t)i * C::NS + s) * C::KR + k] - epn * FRd[((size_t)i * C::NS + s) * C::KR + k] : 0.f;
+#pragma unroll
+        for (int k = 0; k < C::KA; ++k) tsum[at][n][RA + s * C::KA + k] = accA[s][k];
+      }
+    }
+    __syncthreads();
+    for (int q = tid; q < NCR + NCA; q += blockDim.x) {
+      int I, J, nn, k, col;
+      if (q < NCR) {
+        I = q / (C::NS * C::NQR * C::KR);
+        const int r = q % (C::NS * C::NQR * C::KR);
+        J = r / (C::NQR * C::KR);
+        nn = (r / C::KR) % C::NQR;
+        k = r % C::KR;
+        col = J * C::KR + k;
+      } else {
+        const int qa = q - NCR;
+        I = qa / (C::NS * C::NQA * C::KA);
+        const int r = qa % (C::NS * C::NQA * C::KA);
+        J = r / (C::NQA * C::KA);
+        nn = (r / C::KA) % C::NQA;
+        k = r % C::KA;
+        col = RA + J * C::KA + k;
+      }
+      float s = 0.f;
+      for (int t = 0; t < M::NA; ++t)
+        if (ttype[t] == I) s += tsum[t][nn][col];
+      bacc[q] += s;
     }
   }
-  // layout [atom][n][J][k] so that a column sum over atoms of species I gives c^A[I][J][n][k]
-  float* o = dcA + ((size_t)i * C::NQA + n) * C::NS * C::KA;
-#pragma unroll
-  for (int s = 0; s < C::NS; ++s)
-#pragma unroll
-    for (int k = 0; k < C::KA; ++k) o[s * C::KA + k] = acc[s][k];
+  __syncthreads();
+  for (int q = tid; q < NCR + NCA; q += blockDim.x) cpart[(size_t)blockIdx.x * (NCR + NCA) + q] = bacc[q];
 }
 
 // ------------------------------------------------------------- launchers
+
+namespace {
+
+constexpr int kNptDesc = 2;     // channels per thread, descriptor sweep
+constexpr int kNptTangent = 2;  // channels per thread, tangent sweep
 
 template <class C>
 struct Runner {
@@ -660,17 +787,23 @@ struct Runner {
     const DevModel dm = m->dev();
     const int N = nl->n_atoms;
     if (N == 0) return GNEP_OK;
-    k_desc_radial<C><<<blocks_for(N, 128), 128, 0, A.st>>>(N, dm, nl->type, nl->L[0].off, nl->L[0].rij, w.FR, w.G);
+    k_desc_radial<C><<<blocks_for((int64_t)N * RL, 128), 128, 0, A.st>>>(N, dm, nl->type, nl->L[0].off,
+                                                                          nl->L[0].rij, w.FR, w.G);
     stage("desc_radial");
-    k_desc_angular<C><<<blocks_for((int64_t)N * C::NQA, 128), 128, 0, A.st>>>(N, dm, nl->type, nl->L[1].off,
-                                                                                nl->L[1].rij, w.S, w.G);
+    using MA = AMap<C::NQA, kNptDesc>;
+    k_desc_angular<C, kNptDesc><<<blocks_for(N, MA::NA), 128, 0, A.st>>>(N, dm, nl->type, nl->L[1].off,
+                                                                          nl->L[1].rij, w.S, w.G);
     stage("desc_angular");
     GNEP_CHECK_LAUNCH("descriptor sweep");
     if (with_mlp) {
-      const size_t smem = sizeof(float) * C::NS * m->net_size;
-      k_mlp_fwd<C><<<blocks_for(N, 128), 128, smem, A.st>>>(N, dm, nl->type, w.G, w.X, w.Ep, w.Eatom);
+      int rc;
+      switch (hidden_pad(m->shape.H)) {
+        case 32: rc = mlp_forward<C::NDES, 32, C::NS, C::NQR, C::KR>(m, nl, A.st); break;
+        case 64: rc = mlp_forward<C::NDES, 64, C::NS, C::NQR, C::KR>(m, nl, A.st); break;
+        default: rc = mlp_forward<C::NDES, 128, C::NS, C::NQR, C::KR>(m, nl, A.st); break;
+      }
+      if (rc) return rc;
       stage("mlp_fwd");
-      GNEP_CHECK_LAUNCH("k_mlp_fwd");
     }
     return GNEP_OK;
   }
@@ -682,17 +815,15 @@ struct Runner {
     const DevModel dm = m->dev();
     const int N = nl->n_atoms;
     if (N == 0) return GNEP_OK;
-    k_shat<C><<<blocks_for((int64_t)N * C::NQA, 128), 128, 0, A.st>>>(N, w.S, w.Ep, w.Shat);
-    stage("shat");
-    k_force_radial<C><<<blocks_for(N, 128), 128, 0, A.st>>>(N, dm, nl->type, nl->L[0].off, nl->L[0].rij, w.Ep, w.dR);
-    stage("force_radial");
-    if (nl->L[1].n > 0)
-      k_force_angular<C><<<blocks_for(nl->L[1].n, 128), 128, 0, A.st>>>(nl->L[1].n, dm, nl->type, nl->L[1].owner,
-                                                                         nl->L[1].rij, w.Shat, w.dA);
-    stage("force_angular");
-    k_force_gather<<<blocks_for(N, 128), 128, 0, A.st>>>(N, nl->L[0].off, nl->L[0].rev, nl->L[0].rij, w.dR,
-                                                         nl->L[1].off, nl->L[1].rev, nl->L[1].rij, w.dA, w.F, w.Wat);
-    stage("force_gather");
+    if (nl->L[1].n > 0) {
+      k_force_angular<C><<<blocks_for(N, NAF), 128, 0, A.st>>>(N, dm, nl->type, nl->L[1].off, nl->L[1].owner,
+                                                               nl->L[1].rij, w.S, w.Ep, w.dA);
+      stage("force_angular");
+    }
+    k_force_atoms<C><<<blocks_for((int64_t)N * RL, 128), 128, 0, A.st>>>(
+        N, dm, nl->type, nl->L[0].off, nl->L[0].j, nl->L[0].rij, w.chat, nl->L[1].off, nl->L[1].rev, nl->L[1].rij,
+        w.dA, w.F, w.Wat);
+    stage("force_atoms");
     k_struct_sum<<<nl->n_struct, 128, 0, A.st>>>(nl->struct_off, w.Eatom, w.Wat, w.Es, w.Ws);
     stage("struct_sum");
     GNEP_CHECK_LAUNCH("force sweep");
@@ -706,19 +837,28 @@ struct Runner {
     const DevModel dm = m->dev();
     const int N = nl->n_atoms;
     if (N == 0) return GNEP_OK;
-    k_tangent_radial<C><<<blocks_for(N, 128), 128, 0, A.st>>>(N, dm, nl->type, nl->atom_struct, nl->L[0].off,
-                                                              nl->L[0].j, nl->L[0].rij, w.a, w.Bs, w.FRd, w.Gd);
+    k_tangent_radial<C><<<blocks_for((int64_t)N * RL, 128), 128, 0, A.st>>>(
+        N, dm, nl->type, nl->atom_struct, nl->L[0].off, nl->L[0].j, nl->L[0].rij, w.a, w.Bs, w.FRd, w.Gd);
     stage("tangent_radial");
-    k_tangent_angular<C><<<blocks_for((int64_t)N * C::NQA, 128), 128, 0, A.st>>>(
-        N, dm, nl->type, nl->atom_struct, nl->L[1].off, nl->L[1].j, nl->L[1].rij, w.a, w.Bs, w.S, w.Sd, w.Gd);
+    using MT = AMap<C::NQA, kNptTangent>;
+    k_tangent_angular<C, kNptTangent><<<blocks_for(N, MT::NA), 128, 0, A.st>>>(
+        N, dm, nl->type, nl->atom_struct, nl->L[1].off, nl->L[1].owner, nl->L[1].j, nl->L[1].rij, w.a, w.Bs, w.S,
+        w.Sd, w.Gd);
     stage("tangent_angular");
-    const size_t smem = sizeof(float) * C::NS * m->net_size;
-    k_mlp_bwd<C><<<blocks_for(N, 128), 128, smem, A.st>>>(N, dm, nl->type, nl->atom_struct, w.es, w.Gd, w.X, w.Gb,
-                                                          w.alpha, w.beta, w.q1, w.eatom);
+    int rc;
+    switch (hidden_pad(m->shape.H)) {
+      case 32: rc = mlp_backward<C::NDES, 32>(m, nl, A.st); break;
+      case 64: rc = mlp_backward<C::NDES, 64>(m, nl, A.st); break;
+      default: rc = mlp_backward<C::NDES, 128>(m, nl, A.st); break;
+    }
+    if (rc) return rc;
     stage("mlp_bwd");
-    k_cgrad_angular<C><<<blocks_for((int64_t)N * C::NQA, 128), 128, 0, A.st>>>(
-        N, dm, nl->atom_struct, nl->L[1].off, nl->L[1].j, nl->L[1].rij, w.a, w.Bs, w.S, w.Sd, w.Gb, w.Ep, w.dcA);
-    stage("cgrad_angular");
+    using MC = AMap<C::NQ, 1>;
+    const int ntile = blocks_for(N, MC::NA);
+    k_cgrad<C><<<ntile < kCgBlocks ? ntile : kCgBlocks, 128, 0, A.st>>>(
+        N, ntile, dm, nl->type, nl->atom_struct, nl->L[1].off, nl->L[1].owner, nl->L[1].j, nl->L[1].rij, w.a, w.Bs,
+        w.S, w.Sd, w.Gb, w.Ep, w.FR, w.FRd, w.cpart);
+    stage("cgrad");
     GNEP_CHECK_LAUNCH("backward sweeps");
     return GNEP_OK;
   }
@@ -732,11 +872,12 @@ struct Runner {
   X(2, 9, 13, 9, 13, true)        \
   X(2, 9, 13, 9, 13, false)
 
+#define GNEP_MATCH(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB) \
+  (s.ns == P_NS && s.nqr == P_NQR && s.kr == P_KR && s.nqa == P_NQA && s.ka == P_KA && (s.fb != 0) == P_FB)
+
 bool shape_supported(const Shape& s) {
-#define X(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB)                                                                    \
-  if (s.ns == P_NS && s.nqr == P_NQR && s.kr == P_KR && s.nqa == P_NQA && s.ka == P_KA && (s.fb != 0) == P_FB && \
-      s.lmax == 4)                                                                                     \
-    return true;
+#define X(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB) \
+  if (GNEP_MATCH(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB) && s.lmax == 4) return true;
   GNEP_SHAPES(X)
 #undef X
   return false;
@@ -745,16 +886,16 @@ bool shape_supported(const Shape& s) {
 namespace {
 template <class C>
 int setup_shape() {
-  GNEP_CUDA(cudaFuncSetAttribute(k_mlp_fwd<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-  GNEP_CUDA(cudaFuncSetAttribute(k_mlp_bwd<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-  return GNEP_OK;
+  int rc = mlp_setup<C::NDES, 32, C::NS, C::NQR, C::KR>();
+  if (!rc) rc = mlp_setup<C::NDES, 64, C::NS, C::NQR, C::KR>();
+  if (!rc) rc = mlp_setup<C::NDES, 128, C::NS, C::NQR, C::KR>();
+  return rc;
 }
 }  // namespace
 
 int shape_setup(const Shape& s) {
-#define X(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB)                                                                    \
-  if (s.ns == P_NS && s.nqr == P_NQR && s.kr == P_KR && s.nqa == P_NQA && s.ka == P_KA && (s.fb != 0) == P_FB) \
-    return setup_shape<Sh<P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB>>();
+#define X(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB) \
+  if (GNEP_MATCH(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB)) return setup_shape<Sh<P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB>>();
   GNEP_SHAPES(X)
 #undef X
   return set_error(GNEP_ERR_UNSUPPORTED, "no kernel for this shape");
@@ -762,8 +903,8 @@ int shape_setup(const Shape& s) {
 
 int run_descriptors(const StepArgs& A, bool with_mlp) {
   const Shape& s = A.m->shape;
-#define X(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB)                                                                    \
-  if (s.ns == P_NS && s.nqr == P_NQR && s.kr == P_KR && s.nqa == P_NQA && s.ka == P_KA && (s.fb != 0) == P_FB) \
+#define X(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB) \
+  if (GNEP_MATCH(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB)) \
     return Runner<Sh<P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB>>::descriptors(A, with_mlp);
   GNEP_SHAPES(X)
 #undef X
@@ -772,9 +913,8 @@ int run_descriptors(const StepArgs& A, bool with_mlp) {
 
 int run_forward(const StepArgs& A) {
   const Shape& s = A.m->shape;
-#define X(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB)                                                                    \
-  if (s.ns == P_NS && s.nqr == P_NQR && s.kr == P_KR && s.nqa == P_NQA && s.ka == P_KA && (s.fb != 0) == P_FB) \
-    return Runner<Sh<P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB>>::forward(A);
+#define X(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB) \
+  if (GNEP_MATCH(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB)) return Runner<Sh<P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB>>::forward(A);
   GNEP_SHAPES(X)
 #undef X
   return set_error(GNEP_ERR_UNSUPPORTED, "no kernel for this shape");
@@ -782,12 +922,18 @@ int run_forward(const StepArgs& A) {
 
 int run_backward(const StepArgs& A) {
   const Shape& s = A.m->shape;
-#define X(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB)                                                                    \
-  if (s.ns == P_NS && s.nqr == P_NQR && s.kr == P_KR && s.nqa == P_NQA && s.ka == P_KA && (s.fb != 0) == P_FB) \
-    return Runner<Sh<P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB>>::backward(A);
+#define X(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB) \
+  if (GNEP_MATCH(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB)) return Runner<Sh<P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB>>::backward(A);
   GNEP_SHAPES(X)
 #undef X
   return set_error(GNEP_ERR_UNSUPPORTED, "no kernel for this shape");
+}
+
+int cgrad_blocks(int n_atoms, const Shape& s) {
+  const int tpa = s.nqr > s.nqa ? s.nqr : s.nqa;
+  const int na = 128 / tpa;
+  const int ntile = (n_atoms + na - 1) / na;
+  return ntile < kCgBlocks ? (ntile > 0 ? ntile : 1) : kCgBlocks;
 }
 
 }  // namespace gnep
@@ -848,10 +994,11 @@ int descriptors_static(const StepArgs& A, float* G) {
   const DevModel dm = m->dev();
   // Both kernels overwrite every scratch element they later read, so the
   // array needs no clearing between calls.
-  k_desc_radial<C><<<blocks_for(N, 128), 128, 0, A.st>>>((int)N, dm, nl->type, nl->L[0].off, nl->L[0].rij,
-                                                         scratch, G);
-  k_desc_angular<C><<<blocks_for(N * C::NQA, 128), 128, 0, A.st>>>((int)N, dm, nl->type, nl->L[1].off,
-                                                                    nl->L[1].rij, scratch + fr_padded, G);
+  k_desc_radial<C><<<blocks_for(N * RL, 128), 128, 0, A.st>>>((int)N, dm, nl->type, nl->L[0].off, nl->L[0].rij,
+                                                              scratch, G);
+  using MA = AMap<C::NQA, 2>;
+  k_desc_angular<C, 2><<<blocks_for(N, MA::NA), 128, 0, A.st>>>((int)N, dm, nl->type, nl->L[1].off, nl->L[1].rij,
+                                                                 scratch + fr_padded, G);
   GNEP_CHECK_LAUNCH("descriptor sweep (static scratch)");
   return GNEP_OK;
 }
@@ -860,9 +1007,8 @@ int descriptors_static(const StepArgs& A, float* G) {
 
 int run_descriptors_static(const StepArgs& A, float* G) {
   const Shape& s = A.m->shape;
-#define X(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB)                                                       \
-  if (s.ns == P_NS && s.nqr == P_NQR && s.kr == P_KR && s.nqa == P_NQA && s.ka == P_KA && (s.fb != 0) == P_FB) \
-    return descriptors_static<Sh<P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB>>(A, G);
+#define X(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB) \
+  if (GNEP_MATCH(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB)) return descriptors_static<Sh<P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB>>(A, G);
   GNEP_SHAPES(X)
 #undef X
   return set_error(GNEP_ERR_UNSUPPORTED, "no kernel for this shape");

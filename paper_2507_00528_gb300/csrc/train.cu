@@ -3,11 +3,11 @@
 // and the species-grouped atom order.  Every cross-atom sum is FP64 in a fixed
 // order, so a step is bit-reproducible.
 #include "gnep_internal.h"
+#include "network.cuh"
 
 namespace gnep {
 
 constexpr int kRedBlocks = 512;  // partial sums per loss term
-constexpr int kChunk = 256;      // atoms per gradient partial
 
 namespace {
 
@@ -129,126 +129,29 @@ __global__ void k_residual_struct(int S, const int* __restrict__ soff, const dou
 
 // ---------------------------------------------------------- gradient sums
 
-struct Operand {
-  const float* p;
-  int ld, col0;
-  const float* colscale;  // optional per-column factor
-};
-
-struct ChunkMap {
-  const int* perm;
-  int soff[9];     // species offsets in perm
-  int nchunk[8];   // chunks per species
-  int cmax;        // max chunks over species
-  int local_size;  // partial row length per species (= n_params / ns)
-  int ns;
-};
-
-__device__ __forceinline__ bool chunk_range(const ChunkMap& cm, int e, int c, int& b, int& en) {
-  if (c >= cm.nchunk[e]) return false;
-  b = cm.soff[e] + c * kChunk;
-  en = min(b + kChunk, cm.soff[e + 1]);
-  return b < en;
-}
-
-// out[a][b] += sum_i X1(i,a) Y1(i,b) + sgn X2(i,a) Y2(i,b) over one chunk of one
-// species; 32 x 32 output tile per block, 256 threads x 4 outputs.
-__global__ void __launch_bounds__(256) k_outer_reduce(ChunkMap cm, Operand x1, Operand y1, Operand x2,
-                                                      Operand y2, float sgn, int A, int B, int out_off,
-                                                      float* __restrict__ part) {
-  const int tilesB = (B + 31) / 32;
-  const int ta = blockIdx.x / tilesB, tb = blockIdx.x % tilesB;
-  const int c = blockIdx.y, e = blockIdx.z;
-  int i0, i1;
-  if (!chunk_range(cm, e, c, i0, i1)) return;
-  __shared__ float sx1[32][33], sy1[32][33], sx2[32][33], sy2[32][33];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 x 16 threads, 2 x 2 outputs each
-  float acc[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
-  for (int base = i0; base < i1; base += 32) {
-    for (int q = threadIdx.x; q < 32 * 32; q += 256) {
-      const int r = q >> 5, col = q & 31;
-      const int ii = base + r;
-      float vx1 = 0.f, vy1 = 0.f, vx2 = 0.f, vy2 = 0.f;
-      if (ii < i1) {
-        const int at = cm.perm[ii];
-        const int a = ta * 32 + col, b = tb * 32 + col;
-        if (a < A) {
-          vx1 = x1.p[(size_t)at * x1.ld + x1.col0 + a];
-          if (x2.p) vx2 = x2.p[(size_t)at * x2.ld + x2.col0 + a];
-        }
-        if (b < B) {
-          vy1 = y1.p[(size_t)at * y1.ld + y1.col0 + b];
-          if (y1.colscale) vy1 *= y1.colscale[y1.col0 + b];
-          if (y2.p) {
-            vy2 = y2.p[(size_t)at * y2.ld + y2.col0 + b];
-            if (y2.colscale) vy2 *= y2.colscale[y2.col0 + b];
-          }
-        }
-      }
-      sx1[r][col] = vx1;
-      sy1[r][col] = vy1;
-      sx2[r][col] = vx2;
-      sy2[r][col] = sgn * vy2;
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int r = 0; r < 32; ++r) {
-#pragma unroll
-      for (int u = 0; u < 2; ++u)
-#pragma unroll
-        for (int w = 0; w < 2; ++w) {
-          acc[u][w] = fmaf(sx1[r][ty * 2 + u], sy1[r][tx * 2 + w], acc[u][w]);
-          acc[u][w] = fmaf(sx2[r][ty * 2 + u], sy2[r][tx * 2 + w], acc[u][w]);
-        }
-    }
-    __syncthreads();
-  }
-  float* out = part + ((size_t)c * cm.ns + e) * cm.local_size + out_off;
-#pragma unroll
-  for (int u = 0; u < 2; ++u)
-#pragma unroll
-    for (int w = 0; w < 2; ++w) {
-      const int a = ta * 32 + ty * 2 + u, b = tb * 32 + tx * 2 + w;
-      if (a < A && b < B) out[a * B + b] = acc[u][w];
-    }
-}
-
-// out[q] = sum_i Z(i, q) over one chunk of one species.
-__global__ void __launch_bounds__(256) k_col_reduce(ChunkMap cm, Operand z, int Q, int out_off,
-                                                    float* __restrict__ part) {
-  const int c = blockIdx.y, e = blockIdx.z;
-  int i0, i1;
-  if (!chunk_range(cm, e, c, i0, i1)) return;
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= Q) return;
-  float s = 0.f;
-  for (int ii = i0; ii < i1; ++ii) s += z.p[(size_t)cm.perm[ii] * z.ld + z.col0 + q];
-  part[((size_t)c * cm.ns + e) * cm.local_size + out_off + q] = s;
-}
-
-// grad[q] = sum over chunks (FP64) + 2 lambda_l2 theta_q / N_par.
-__global__ void k_grad_final(DevModel dm, int cmax, int ns, int local_size, const float* __restrict__ part,
-                             double l2coef, double* __restrict__ grad) {
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// grad[q] = sum over block partials (FP64, one warp per parameter, fixed order)
+//           + 2 lambda_l2 theta_q / N_par.
+// Network parameters come from the network backward pass (net_part), the
+// coefficients from the c-gradient sweep (cpart).
+__global__ void __launch_bounds__(256) k_grad_final(DevModel dm, int ns, int nb_net, int nb_cg,
+                                                    const float* __restrict__ net_part,
+                                                    const float* __restrict__ cpart, double l2coef,
+                                                    double* __restrict__ grad) {
+  const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (q >= dm.n_params) return;
-  int e, l;
-  if (q < (int64_t)ns * dm.net_size) {
-    e = (int)(q / dm.net_size);
-    l = (int)(q % dm.net_size);
-  } else if (q < dm.off_cA) {
-    const int r = (int)(q - dm.off_cR), blk = ns * dm.nqr * dm.kr;
-    e = r / blk;
-    const int rem = r % blk, J = rem / (dm.nqr * dm.kr), n = (rem / dm.kr) % dm.nqr, k = rem % dm.kr;
-    l = dm.net_size + n * ns * dm.kr + J * dm.kr + k;
-  } else {
-    const int r = (int)(q - dm.off_cA), blk = ns * dm.nqa * dm.ka;
-    e = r / blk;
-    const int rem = r % blk, J = rem / (dm.nqa * dm.ka), n = (rem / dm.ka) % dm.nqa, k = rem % dm.ka;
-    l = dm.net_size + dm.nqr * ns * dm.kr + n * ns * dm.ka + J * dm.ka + k;
-  }
   double s = 0.0;
-  for (int c = 0; c < cmax; ++c) s += (double)part[((size_t)c * ns + e) * local_size + l];
-  grad[q] = s + l2coef * (double)dm.params[q];
+  if (q < (int64_t)ns * dm.net_size) {
+    const int e = (int)(q / dm.net_size), l = (int)(q % dm.net_size);
+    for (int b = lane; b < nb_net; b += 32) s += (double)net_part[((size_t)b * ns + e) * dm.net_size + l];
+  } else {
+    const int64_t nc = dm.n_params - (int64_t)ns * dm.net_size;
+    const int64_t c = q - dm.off_cR;
+    for (int b = lane; b < nb_cg; b += 32) s += (double)cpart[(size_t)b * nc + c];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) grad[q] = s + l2coef * (double)dm.params[q];
 }
 
 // ---------------------------------------------------------- Adam, Eq. 17
@@ -344,27 +247,8 @@ __global__ void __launch_bounds__(1024) k_species_perm(int N, int ns, const int*
   if (threadIdx.x == 0) soff[ns] = base;
 }
 
-ChunkMap make_chunk_map(const gnep_model* m, const gnep_nlist* nl) {
-  ChunkMap cm;
-  cm.perm = nl->perm;
-  cm.ns = m->shape.ns;
-  cm.cmax = 0;
-  for (int e = 0; e <= cm.ns; ++e) cm.soff[e] = nl->species_off[e];
-  for (int e = 0; e < cm.ns; ++e) {
-    const int ne = nl->species_off[e + 1] - nl->species_off[e];
-    cm.nchunk[e] = (ne + kChunk - 1) / kChunk;
-    if (cm.nchunk[e] > cm.cmax) cm.cmax = cm.nchunk[e];
-  }
-  cm.local_size = (int)(m->n_params / cm.ns);
-  return cm;
-}
-
 }  // namespace
 
-int64_t grad_partial_floats(const gnep_model* m, int n_atoms) {
-  const int cmax = (n_atoms + kChunk - 1) / kChunk + 1;
-  return (int64_t)cmax * m->n_params;
-}
 int64_t loss_partial_doubles() { return 3LL * kRedBlocks; }
 
 int run_species_perm(gnep_nlist* nl, cudaStream_t st) {
@@ -398,51 +282,14 @@ int run_loss_impl(const gnep_model* m, gnep_nlist* nl, const double* le, const f
 }
 
 int run_grad_reduce_impl(const gnep_model* m, gnep_nlist* nl, double lambda_l2, cudaStream_t st) {
-  Workspace& w = nl->ws;
-  const Shape& sh = m->shape;
-  const ChunkMap cm = make_chunk_map(m, nl);
   const DevModel dm = m->dev();
-  const int H = sh.H, D = sh.ndes, ns = sh.ns;
-  const size_t part_bytes = sizeof(float) * (size_t)(cm.cmax > 0 ? cm.cmax : 1) * ns * cm.local_size;
-  GNEP_CUDA(cudaMemsetAsync(w.part, 0, part_bytes, st));
-  stage("memset_partials");
-  if (cm.cmax > 0) {
-    // dL/dW0 = sum_i alpha (s.G)^T - beta (s.Gdot)^T
-    {
-      Operand x1{w.alpha, H, 0, nullptr}, y1{w.G, D, 0, m->scale}, x2{w.beta, H, 0, nullptr},
-          y2{w.Gd, D, 0, m->scale};
-      dim3 grid(((H + 31) / 32) * ((D + 31) / 32), cm.cmax, ns);
-      k_outer_reduce<<<grid, 256, 0, st>>>(cm, x1, y1, x2, y2, -1.f, H, D, 0, w.part);
-      stage("reduce_W0");
-    }
-    // dL/dc^R = sum_i Gbar_n FR_Jk - E'_n FRdot_Jk
-    {
-      Operand x1{w.Gb, D, 0, nullptr}, y1{w.FR, ns * sh.kr, 0, nullptr}, x2{w.Ep, D, 0, nullptr},
-          y2{w.FRd, ns * sh.kr, 0, nullptr};
-      const int B = ns * sh.kr;
-      dim3 grid(((sh.nqr + 31) / 32) * ((B + 31) / 32), cm.cmax, ns);
-      k_outer_reduce<<<grid, 256, 0, st>>>(cm, x1, y1, x2, y2, -1.f, sh.nqr, B, m->net_size, w.part);
-      stage("reduce_cR");
-    }
-    // b0, w1, b1, c^A column sums
-    {
-      dim3 g1((H + 255) / 256, cm.cmax, ns);
-      k_col_reduce<<<g1, 256, 0, st>>>(cm, Operand{w.alpha, H, 0, nullptr}, H, D * H, w.part);
-      stage("reduce_b0");
-      k_col_reduce<<<g1, 256, 0, st>>>(cm, Operand{w.q1, H, 0, nullptr}, H, D * H + H, w.part);
-      stage("reduce_w1");
-      dim3 g2(1, cm.cmax, ns);
-      k_col_reduce<<<g2, 256, 0, st>>>(cm, Operand{w.eatom, 1, 0, nullptr}, 1, D * H + 2 * H, w.part);
-      stage("reduce_b1");
-      const int QA = sh.nqa * ns * sh.ka;
-      dim3 g3((QA + 255) / 256, cm.cmax, ns);
-      k_col_reduce<<<g3, 256, 0, st>>>(cm, Operand{w.dcA, QA, 0, nullptr}, QA,
-                                       m->net_size + sh.nqr * ns * sh.kr, w.part);
-      stage("reduce_cA");
-    }
-  }
-  k_grad_final<<<blocks_for(m->n_params, 256), 256, 0, st>>>(dm, cm.cmax, ns, cm.local_size, w.part,
-                                                             2.0 * lambda_l2 / (double)m->n_params, m->grad);
+  const int ns = m->shape.ns;
+  const Tiles T = make_tiles(nl, ns);
+  const int nb_net = T.tbase[ns] < kNetBlocks ? T.tbase[ns] : kNetBlocks;
+  const int nb_cg = nl->n_atoms > 0 ? cgrad_blocks(nl->n_atoms, m->shape) : 0;
+  k_grad_final<<<blocks_for(m->n_params * 32, 256), 256, 0, st>>>(dm, ns, nb_net, nb_cg, nl->ws.net_part,
+                                                                  nl->ws.cpart, 2.0 * lambda_l2 / (double)m->n_params,
+                                                                  m->grad);
   stage("grad_final");
   GNEP_CHECK_LAUNCH("gradient reduction");
   return GNEP_OK;
