@@ -74,13 +74,14 @@ int alloc_workspace(gnep_model* m, gnep_nlist* nl) {
   const Shape& s = m->shape;
   const size_t N = nl->n_atoms > 0 ? nl->n_atoms : 1, S = nl->n_struct;
   const size_t PR = nl->L[0].n > 0 ? nl->L[0].n : 1, PA = nl->L[1].n > 0 ? nl->L[1].n : 1;
-  const size_t D = s.ndes, H = s.H, A24 = (size_t)s.nqa * 24, FRn = (size_t)s.ns * s.kr;
+  const size_t D = s.ndes, A24 = (size_t)s.nqa * 24, FRn = (size_t)s.ns * s.kr;
+  const size_t HPad = (size_t)hidden_pad(s.H);  // row pitch of the hidden activations
   struct Item { void** p; size_t bytes; };
   Workspace& w = nl->ws;
   w.red_len = loss_partial_doubles();
   const size_t NC = (size_t)(m->n_params - (int64_t)s.ns * m->net_size);
   std::vector<Item> items = {
-      {(void**)&w.G, 4 * N * D},        {(void**)&w.Ep, 4 * N * D},       {(void**)&w.X, 4 * N * H},
+      {(void**)&w.G, 4 * N * D},        {(void**)&w.Ep, 4 * N * D},       {(void**)&w.X, 4 * N * HPad},
       {(void**)&w.Eatom, 4 * N},        {(void**)&w.S, 4 * N * A24},      {(void**)&w.FR, 4 * N * FRn},
       {(void**)&w.chat, 4 * N * FRn},   {(void**)&w.dA, 16 * PA},         {(void**)&w.F, 12 * N},
       {(void**)&w.Wat, 24 * N},         {(void**)&w.Es, 8 * S},           {(void**)&w.Ws, 48 * S},
@@ -268,11 +269,40 @@ static int load_batch(gnep_model* m, const gnep_batch* b, gnep_nlist* nl, cudaSt
   return GNEP_OK;
 }
 
+// Greedy tiles of consecutive atoms with at most na atoms and ch angular pairs.
+static int build_angular_tiles(gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
+  const int N = nl->n_atoms;
+  std::vector<int> off(N + 1);
+  GNEP_CUDA(cudaMemcpyAsync(off.data(), nl->L[1].off, sizeof(int) * (N + 1), cudaMemcpyDeviceToHost, st));
+  GNEP_CUDA(cudaStreamSynchronize(st));
+  for (int which = 0; which < 2; ++which) {
+    int na = 0, ch = 0;
+    angular_tile_limits(m->shape, which, &na, &ch);
+    std::vector<int> t;
+    int i = 0;
+    while (i < N) {
+      t.push_back(i);
+      int j = i + 1;
+      while (j < N && j - i < na && off[j + 1] - off[i] <= ch) ++j;
+      i = j;
+    }
+    t.push_back(N);
+    cudaFree(nl->atile[which]);
+    nl->atile[which] = nullptr;
+    GNEP_CUDA(cudaMalloc(&nl->atile[which], sizeof(int) * t.size()));
+    GNEP_CUDA(cudaMemcpyAsync(nl->atile[which], t.data(), sizeof(int) * t.size(), cudaMemcpyHostToDevice, st));
+    nl->natile[which] = (int)t.size() - 1;
+  }
+  GNEP_CUDA(cudaStreamSynchronize(st));
+  return GNEP_OK;
+}
+
 static int finish_build(gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
   int rc;
   if (nl->n_atoms > 0) {
     if ((rc = build_lists(m, nl, st))) return rc;
     if ((rc = run_species_perm(nl, st))) return rc;
+    if ((rc = build_angular_tiles(m, nl, st))) return rc;
   } else {
     for (int e = 0; e <= m->shape.ns; ++e) nl->species_off[e] = 0;
     for (int L = 0; L < 2; ++L) {
@@ -290,6 +320,7 @@ int gnep_nlist_destroy(gnep_nlist* nl) {
   if (!nl) return GNEP_OK;
   cudaFree(nl->struct_off); cudaFree(nl->type); cudaFree(nl->pos); cudaFree(nl->cell);
   cudaFree(nl->atom_struct); cudaFree(nl->perm);
+  cudaFree(nl->atile[0]); cudaFree(nl->atile[1]);
   for (int L = 0; L < 2; ++L) {
     PairList& P = nl->L[L];
     cudaFree(P.off); cudaFree(P.j); cudaFree(P.owner); cudaFree(P.rev); cudaFree(P.rij); cudaFree(P.shift);

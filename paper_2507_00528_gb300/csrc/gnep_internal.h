@@ -81,6 +81,11 @@ struct gnep_nlist {
   int* perm = nullptr;         // device [N] atoms grouped by species
   int species_off[9] = {0};    // host [ns+1]
   gnep::PairList L[2];         // radial, angular
+  // Atom tiles for the angular sweeps: consecutive atoms, at most NA atoms and
+  // CH angular pairs per tile (a single atom above CH pairs gets its own tile).
+  // [0] wide tiles (descriptor sweep), [1] narrow tiles (force, tangent, c-gradient).
+  int* atile[2] = {nullptr, nullptr};
+  int natile[2] = {0, 0};
   gnep::Workspace ws;
   void* ws_mem = nullptr;      // one allocation carved into the workspace
   int64_t ws_pairs[2] = {-1, -1};  // pair counts the workspace was sized for
@@ -146,7 +151,8 @@ int run_backward(const StepArgs& a);
 
 int shape_setup(const Shape& s);
 int run_descriptors_static(const StepArgs& a, float* G);
-int cgrad_blocks(int n_atoms, const Shape& s);
+int cgrad_blocks(int ntiles);
+void angular_tile_limits(const Shape& s, int which, int* na, int* ch);
 constexpr int kCgBlocksMax = 608;
 
 // train.cu

@@ -28,7 +28,9 @@ __global__ void k_atom_struct(const int* __restrict__ off, int S, int N, int* __
 }
 
 // Images needed per cell direction: floor(rc / w) + 1, w = V / |b x c| etc.
-__global__ void k_image_range(const double* __restrict__ cell, int S, double rc, int* __restrict__ kr) {
+// tw[s][x] = rc / w_x bounds |df_x + n_x| for any pair within rc.
+__global__ void k_image_range(const double* __restrict__ cell, int S, double rc, int* __restrict__ kr,
+                              float* __restrict__ tw) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= S) return;
   const double* a = cell + 9 * s;
@@ -39,7 +41,29 @@ __global__ void k_image_range(const double* __restrict__ cell, int S, double rc,
   const double ab[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
   const double vol = fabs(a[0] * bc[0] + a[1] * bc[1] + a[2] * bc[2]);
   const double n[3] = {norm3d(bc[0], bc[1], bc[2]), norm3d(ca[0], ca[1], ca[2]), norm3d(ab[0], ab[1], ab[2])};
-  for (int x = 0; x < 3; ++x) kr[3 * s + x] = (int)floor(rc / (vol / n[x])) + 1;
+  for (int x = 0; x < 3; ++x) {
+    kr[3 * s + x] = (int)floor(rc / (vol / n[x])) + 1;
+    tw[3 * s + x] = (float)(rc / (vol / n[x]));
+  }
+}
+
+// Fractional coordinates f = r H^-1 (FP32; only used to bound image shifts).
+__global__ void k_fractional(int N, const int* __restrict__ atom_struct, const double* __restrict__ pos,
+                             const double* __restrict__ cell, float4* __restrict__ frac) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double* H = cell + 9 * atom_struct[i];
+  const double det = H[0] * (H[4] * H[8] - H[5] * H[7]) - H[1] * (H[3] * H[8] - H[5] * H[6]) +
+                     H[2] * (H[3] * H[7] - H[4] * H[6]);
+  const double inv[9] = {(H[4] * H[8] - H[5] * H[7]) / det, (H[2] * H[7] - H[1] * H[8]) / det,
+                         (H[1] * H[5] - H[2] * H[4]) / det, (H[5] * H[6] - H[3] * H[8]) / det,
+                         (H[0] * H[8] - H[2] * H[6]) / det, (H[2] * H[3] - H[0] * H[5]) / det,
+                         (H[3] * H[7] - H[4] * H[6]) / det, (H[1] * H[6] - H[0] * H[7]) / det,
+                         (H[0] * H[4] - H[1] * H[3]) / det};
+  const double* p = pos + 3 * (size_t)i;
+  double f[3];
+  for (int x = 0; x < 3; ++x) f[x] = p[0] * inv[x] + p[1] * inv[3 + x] + p[2] * inv[6 + x];
+  frac[i] = make_float4((float)f[0], (float)f[1], (float)f[2], 0.f);
 }
 
 __device__ __forceinline__ double pair_d2_exact(const double* H, const double* pi, const double* pj,
@@ -64,6 +88,7 @@ template <bool kFill>
 __global__ void __launch_bounds__(128) k_pairs(
     int N, const int* __restrict__ struct_off, const int* __restrict__ atom_struct,
     const double* __restrict__ pos, const double* __restrict__ cell, const int* __restrict__ krange,
+    const float* __restrict__ tw, const float4* __restrict__ frac,
     const int* __restrict__ type, ListParams lp, int* __restrict__ cnt0, int* __restrict__ cnt1,
     const long long* __restrict__ off0, const long long* __restrict__ off1,
     int* __restrict__ j0, int* __restrict__ own0, float4* __restrict__ r0, char4* __restrict__ sh0,
@@ -98,13 +123,22 @@ __global__ void __launch_bounds__(128) k_pairs(
   }
   int c0 = 0, c1 = 0;
   long long w0 = kFill ? off0[i] : 0, w1 = kFill ? off1[i] : 0;
+  // |r_j + n.H - r_i| >= |df_x + n_x| w_x, so only shifts with |df_x + n_x| < rc / w_x
+  // (with a margin far above FP32 rounding) can pass the exact test below.
+  const float4 fi = frac[i];
+  const float t0 = tw[3 * s] + 1e-3f, t1 = tw[3 * s + 1] + 1e-3f, t2 = tw[3 * s + 2] + 1e-3f;
   for (int j = a0; j < a1; ++j) {
     const double pj[3] = {pos[3 * j], pos[3 * j + 1], pos[3 * j + 2]};
     const float dj[3] = {(float)pj[0] - pif[0], (float)pj[1] - pif[1], (float)pj[2] - pif[2]};
     const int tj = type[j];
-    for (int na = -ka; na <= ka; ++na)
-      for (int nb = -kb; nb <= kb; ++nb)
-        for (int nc = -kc; nc <= kc; ++nc) {
+    const float4 fj = frac[j];
+    const float dfa = fj.x - fi.x, dfb = fj.y - fi.y, dfc = fj.z - fi.z;
+    const int alo = max(-ka, (int)ceilf(-t0 - dfa)), ahi = min(ka, (int)floorf(t0 - dfa));
+    const int blo = max(-kb, (int)ceilf(-t1 - dfb)), bhi = min(kb, (int)floorf(t1 - dfb));
+    const int clo = max(-kc, (int)ceilf(-t2 - dfc)), chi = min(kc, (int)floorf(t2 - dfc));
+    for (int na = alo; na <= ahi; ++na)
+      for (int nb = blo; nb <= bhi; ++nb)
+        for (int nc = clo; nc <= chi; ++nc) {
           if (j == i && na == 0 && nb == 0 && nc == 0) continue;
           const float fx = dj[0] + ((float)na * Hf[0] + (float)nb * Hf[3] + (float)nc * Hf[6]);
           const float fy = dj[1] + ((float)na * Hf[1] + (float)nb * Hf[4] + (float)nc * Hf[7]);
@@ -214,18 +248,25 @@ int build_lists(gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
     for (auto p : tmp) cudaFreeAsync(p, st);
   };
   int *cnt = nullptr, *kr = nullptr;
+  float* tw = nullptr;
+  float4* frac = nullptr;
   long long* offs = nullptr;
   GNEP_CUDA(cudaMallocAsync(&cnt, sizeof(int) * 2 * (size_t)(N + 1), st));
   GNEP_CUDA(cudaMallocAsync(&kr, sizeof(int) * 3 * (size_t)S, st));
   GNEP_CUDA(cudaMallocAsync(&offs, sizeof(long long) * 2 * (size_t)(N + 1), st));
+  GNEP_CUDA(cudaMallocAsync(&tw, sizeof(float) * 3 * (size_t)S, st));
+  GNEP_CUDA(cudaMallocAsync(&frac, sizeof(float4) * (size_t)N, st));
   tmp.push_back(cnt);
   tmp.push_back(kr);
+  tmp.push_back(tw);
+  tmp.push_back(frac);
   tmp.push_back(offs);
   GNEP_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * 2 * (size_t)(N + 1), st));
 
   k_atom_struct<<<blocks_for(N, 256), 256, 0, st>>>(nl->struct_off, S, N, nl->atom_struct);
   const double rcmax = nl->rcr > nl->rca ? nl->rcr : nl->rca;
-  k_image_range<<<blocks_for(S, 128), 128, 0, st>>>(nl->cell, S, rcmax, kr);
+  k_image_range<<<blocks_for(S, 128), 128, 0, st>>>(nl->cell, S, rcmax, kr, tw);
+  k_fractional<<<blocks_for(N, 256), 256, 0, st>>>(N, nl->atom_struct, nl->pos, nl->cell, frac);
   GNEP_CHECK_LAUNCH("k_image_range");
 
   ListParams lp;
@@ -236,7 +277,7 @@ int build_lists(gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
   int* cnt0 = cnt;
   int* cnt1 = cnt + (N + 1);
   k_pairs<false><<<blocks_for(N, 128), 128, 0, st>>>(
-      N, nl->struct_off, nl->atom_struct, nl->pos, nl->cell, kr, nl->type, lp, cnt0, cnt1, nullptr,
+      N, nl->struct_off, nl->atom_struct, nl->pos, nl->cell, kr, tw, frac, nl->type, lp, cnt0, cnt1, nullptr,
       nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, m->err);
   GNEP_CHECK_LAUNCH("k_pairs<count>");
 
@@ -280,7 +321,7 @@ int build_lists(gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
     k_to_int<<<blocks_for(N + 1, 256), 256, 0, st>>>(L == 0 ? off0 : off1, N + 1, P.off);
   }
   k_pairs<true><<<blocks_for(N, 128), 128, 0, st>>>(
-      N, nl->struct_off, nl->atom_struct, nl->pos, nl->cell, kr, nl->type, lp, nullptr, nullptr, off0,
+      N, nl->struct_off, nl->atom_struct, nl->pos, nl->cell, kr, tw, frac, nl->type, lp, nullptr, nullptr, off0,
       off1, nl->L[0].j, nl->L[0].owner, nl->L[0].rij, nl->L[0].shift, nl->L[1].j, nl->L[1].owner,
       nl->L[1].rij, nl->L[1].shift, m->err);
   GNEP_CHECK_LAUNCH("k_pairs<fill>");

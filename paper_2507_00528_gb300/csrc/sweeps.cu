@@ -159,19 +159,20 @@ __global__ void __launch_bounds__(128) k_desc_radial(int N, DevModel dm, const i
 }
 
 // Angular descriptors S_nlm = sum_j g_n(r_ij) B_lm (Eq. 8), q_nl (Eq. 7), q4_n.
-template <class C, int NPT>
-__global__ void __launch_bounds__(128) k_desc_angular(int N, DevModel dm, const int* __restrict__ type,
-                                                      const int* __restrict__ off, const float4* __restrict__ rij,
-                                                      float* __restrict__ Sout, float* __restrict__ G) {
+template <class C, int NPT, int CHD>
+__global__ void __launch_bounds__(128) k_desc_angular(int N, DevModel dm, const int* __restrict__ tiles,
+                                                      const int* __restrict__ type, const int* __restrict__ off,
+                                                      const float4* __restrict__ rij, float* __restrict__ Sout,
+                                                      float* __restrict__ G) {
   using M = AMap<C::NQA, NPT>;
-  __shared__ float sf[C::KA][CH];
-  __shared__ float sB[NLM][CH];
-  __shared__ int sJ[CH];
+  __shared__ float sf[C::KA][CHD];
+  __shared__ float sB[NLM][CHD];
+  __shared__ int sJ[CHD];
   const int tid = threadIdx.x;
-  const int i0 = blockIdx.x * M::NA;
+  const int i0 = tiles[blockIdx.x], i1 = tiles[blockIdx.x + 1];
   const int a = tid / M::TPA, tq = tid % M::TPA;
   const int i = i0 + a;
-  const bool ok = a < M::NA && i < N;
+  const bool ok = a < M::NA && i < i1;
   float c[NPT][C::NS][C::KA];
   float S[NPT][NLM];
   const int I = ok ? type[i] : 0;
@@ -186,24 +187,24 @@ __global__ void __launch_bounds__(128) k_desc_angular(int N, DevModel dm, const 
 #pragma unroll
     for (int q = 0; q < NLM; ++q) S[h][q] = 0.f;
   }
-  const int P0 = off[min(i0, N)], P1 = off[min(i0 + M::NA, N)];
+  const int P0 = off[i0], P1 = off[i1];
   const int pa0 = ok ? off[i] : 0, pa1 = ok ? off[i + 1] : 0;
-  for (int cs = P0; cs < P1; cs += CH) {
-    const int ce = min(cs + CH, P1);
-    const int p = cs + tid;
-    if (p < ce) {
+  for (int cs = P0; cs < P1; cs += CHD) {
+    const int ce = min(cs + CHD, P1);
+    for (int p = cs + tid; p < ce; p += blockDim.x) {
+      const int sl = p - cs;
       const float4 r = rij[p];
       const float rr = sqrtf(r.x * r.x + r.y * r.y + r.z * r.z);
       const float ri = 1.f / rr;
       float f[C::KA];
       radial_basis<C::KA>(rr, dm.rca_inv, f);
 #pragma unroll
-      for (int k = 0; k < C::KA; ++k) sf[k][tid] = f[k];
+      for (int k = 0; k < C::KA; ++k) sf[k][sl] = f[k];
       float B[NLM];
       harmonics(r.x * ri, r.y * ri, r.z * ri, B);
 #pragma unroll
-      for (int q = 0; q < NLM; ++q) sB[q][tid] = B[q];
-      sJ[tid] = (int)r.w;
+      for (int q = 0; q < NLM; ++q) sB[q][sl] = B[q];
+      sJ[sl] = (int)r.w;
     }
     __syncthreads();
     const int q0 = max(pa0, cs), q1 = min(pa1, ce);
@@ -252,19 +253,20 @@ __global__ void __launch_bounds__(128) k_desc_angular(int N, DevModel dm, const 
 //   dE_i/dr_ij = sum_n [g_n' (Shat_n . B) u + g_n Shat_n . grad B]       (C2.1, C2.3, C3.6)
 //             = (sum_lm ghat'_lm B_lm) u + (I - u u^T)(sum_lm ghat_lm grad p_lm) / r,
 //   ghat_lm = sum_n g_n Shat_nlm, ghat'_lm = sum_n g_n' Shat_nlm.
-constexpr int NAF = 16;
 template <class C>
-__global__ void __launch_bounds__(128) k_force_angular(int N, DevModel dm, const int* __restrict__ type,
-                                                       const int* __restrict__ off, const int* __restrict__ own,
-                                                       const float4* __restrict__ rij, const float* __restrict__ Sang,
-                                                       const float* __restrict__ Ep, float4* __restrict__ dA) {
+__global__ void __launch_bounds__(128) k_force_angular(int N, DevModel dm, const int* __restrict__ tiles,
+                                                       const int* __restrict__ type, const int* __restrict__ off,
+                                                       const int* __restrict__ own, const float4* __restrict__ rij,
+                                                       const float* __restrict__ Sang, const float* __restrict__ Ep,
+                                                       float4* __restrict__ dA) {
+  constexpr int NAF = AMap<C::NQ, 1>::NA;
   __shared__ float cA[C::NCA];
   __shared__ float sh[NAF][C::NQA][NLM];
-  const int i0 = blockIdx.x * NAF;
+  const int i0 = tiles[blockIdx.x], i1 = tiles[blockIdx.x + 1];
   for (int q = threadIdx.x; q < C::NCA; q += blockDim.x) cA[q] = dm.params[dm.off_cA + q];
   for (int t = threadIdx.x; t < NAF * C::NQA; t += blockDim.x) {
     const int a = t / C::NQA, n = t % C::NQA, i = i0 + a;
-    if (i >= N) continue;
+    if (i >= i1) continue;
     const float* S = Sang + ((size_t)i * C::NQA + n) * NLM;
     const float* ep = Ep + (size_t)i * C::NDES;
     float s[NLM];
@@ -281,7 +283,7 @@ __global__ void __launch_bounds__(128) k_force_angular(int N, DevModel dm, const
     }
   }
   __syncthreads();
-  const int P0 = off[min(i0, N)], P1 = off[min(i0 + NAF, N)];
+  const int P0 = off[i0], P1 = off[i1];
   for (int p = P0 + threadIdx.x; p < P1; p += blockDim.x) {
     const int i = own[p];
     const int a = i - i0;
@@ -535,7 +537,8 @@ __device__ __forceinline__ void angular_geometry(AngGeo<C>& g, int slot, int p, 
 // Angular tangent: Sdot_nlm = sum_j [g_n' (u_hat . u) B_lm + g_n grad B_lm . u],
 // qdot_nl = 2 sum_m C_lm S_nlm Sdot_nlm, qdot4_n = dq4/dS . Sdot.
 template <class C, int NPT>
-__global__ void __launch_bounds__(128) k_tangent_angular(int N, DevModel dm, const int* __restrict__ type,
+__global__ void __launch_bounds__(128) k_tangent_angular(int N, DevModel dm, const int* __restrict__ tiles,
+                                                         const int* __restrict__ type,
                                                          const int* __restrict__ atom_struct, const int* __restrict__ off,
                                                          const int* __restrict__ own, const int* __restrict__ jj,
                                                          const float4* __restrict__ rij, const float4* __restrict__ a,
@@ -544,10 +547,10 @@ __global__ void __launch_bounds__(128) k_tangent_angular(int N, DevModel dm, con
   using M = AMap<C::NQA, NPT>;
   __shared__ AngGeo<C> geo;
   const int tid = threadIdx.x;
-  const int i0 = blockIdx.x * M::NA;
+  const int i0 = tiles[blockIdx.x], i1 = tiles[blockIdx.x + 1];
   const int at = tid / M::TPA, tq = tid % M::TPA;
   const int i = i0 + at;
-  const bool ok = at < M::NA && i < N;
+  const bool ok = at < M::NA && i < i1;
   float c[NPT][C::NS][C::KA];
   float sd[NPT][NLM];
   const int I = ok ? type[i] : 0;
@@ -562,7 +565,7 @@ __global__ void __launch_bounds__(128) k_tangent_angular(int N, DevModel dm, con
 #pragma unroll
     for (int q = 0; q < NLM; ++q) sd[h][q] = 0.f;
   }
-  const int P0 = off[min(i0, N)], P1 = off[min(i0 + M::NA, N)];
+  const int P0 = off[i0], P1 = off[i1];
   const int pa0 = ok ? off[i] : 0, pa1 = ok ? off[i + 1] : 0;
   for (int cs = P0; cs < P1; cs += CH) {
     const int ce = min(cs + CH, P1);
@@ -635,7 +638,8 @@ __global__ void __launch_bounds__(128) k_tangent_angular(int N, DevModel dm, con
 // Each tile's per-thread sums are folded into a block accumulator in a fixed
 // order; the block writes cpart[block][c^R..., c^A...] once.
 template <class C>
-__global__ void __launch_bounds__(128) k_cgrad(int N, int ntile, DevModel dm, const int* __restrict__ type,
+__global__ void __launch_bounds__(128) k_cgrad(int N, int ntile, const int* __restrict__ tiles, DevModel dm,
+                                               const int* __restrict__ type,
                                                const int* __restrict__ atom_struct, const int* __restrict__ off,
                                                const int* __restrict__ own, const int* __restrict__ jj,
                                                const float4* __restrict__ rij, const float4* __restrict__ a,
@@ -661,12 +665,12 @@ __global__ void __launch_bounds__(128) k_cgrad(int N, int ntile, DevModel dm, co
   for (int q = tid; q < NCR + NCA; q += blockDim.x) bacc[q] = 0.f;
 
   for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
-    const int i0 = tile * M::NA;
+    const int i0 = tiles[tile], i1 = tiles[tile + 1];
     const int i = i0 + at;
-    const bool ok = at < M::NA && i < N;
+    const bool ok = at < M::NA && i < i1;
     const bool okA = ok && n < C::NQA, okR = ok && n < C::NQR;
     __syncthreads();
-    if (tid < M::NA) ttype[tid] = (i0 + tid < N) ? type[i0 + tid] : -1;
+    if (tid < M::NA) ttype[tid] = (i0 + tid < i1) ? type[i0 + tid] : -1;
     float accA[C::NS][C::KA];
 #pragma unroll
     for (int s = 0; s < C::NS; ++s)
@@ -702,7 +706,7 @@ __global__ void __launch_bounds__(128) k_cgrad(int N, int ntile, DevModel dm, co
         }
       }
     }
-    const int P0 = off[min(i0, N)], P1 = off[min(i0 + M::NA, N)];
+    const int P0 = off[i0], P1 = off[i1];
     const int pa0 = okA ? off[i] : 0, pa1 = okA ? off[i + 1] : 0;
     for (int cs = P0; cs < P1; cs += CH) {
       const int ce = min(cs + CH, P1);
@@ -776,7 +780,8 @@ __global__ void __launch_bounds__(128) k_cgrad(int N, int ntile, DevModel dm, co
 namespace {
 
 constexpr int kNptDesc = 2;     // channels per thread, descriptor sweep
-constexpr int kNptTangent = 2;  // channels per thread, tangent sweep
+constexpr int kChDesc = 256;    // pairs per geometry chunk, descriptor sweep
+constexpr int kNptTangent = 1;  // channels per thread, tangent sweep
 
 template <class C>
 struct Runner {
@@ -790,9 +795,8 @@ struct Runner {
     k_desc_radial<C><<<blocks_for((int64_t)N * RL, 128), 128, 0, A.st>>>(N, dm, nl->type, nl->L[0].off,
                                                                           nl->L[0].rij, w.FR, w.G);
     stage("desc_radial");
-    using MA = AMap<C::NQA, kNptDesc>;
-    k_desc_angular<C, kNptDesc><<<blocks_for(N, MA::NA), 128, 0, A.st>>>(N, dm, nl->type, nl->L[1].off,
-                                                                          nl->L[1].rij, w.S, w.G);
+    k_desc_angular<C, kNptDesc, kChDesc><<<nl->natile[0], 128, 0, A.st>>>(N, dm, nl->atile[0], nl->type,
+                                                                           nl->L[1].off, nl->L[1].rij, w.S, w.G);
     stage("desc_angular");
     GNEP_CHECK_LAUNCH("descriptor sweep");
     if (with_mlp) {
@@ -816,8 +820,8 @@ struct Runner {
     const int N = nl->n_atoms;
     if (N == 0) return GNEP_OK;
     if (nl->L[1].n > 0) {
-      k_force_angular<C><<<blocks_for(N, NAF), 128, 0, A.st>>>(N, dm, nl->type, nl->L[1].off, nl->L[1].owner,
-                                                               nl->L[1].rij, w.S, w.Ep, w.dA);
+      k_force_angular<C><<<nl->natile[1], 128, 0, A.st>>>(N, dm, nl->atile[1], nl->type, nl->L[1].off,
+                                                           nl->L[1].owner, nl->L[1].rij, w.S, w.Ep, w.dA);
       stage("force_angular");
     }
     k_force_atoms<C><<<blocks_for((int64_t)N * RL, 128), 128, 0, A.st>>>(
@@ -840,10 +844,9 @@ struct Runner {
     k_tangent_radial<C><<<blocks_for((int64_t)N * RL, 128), 128, 0, A.st>>>(
         N, dm, nl->type, nl->atom_struct, nl->L[0].off, nl->L[0].j, nl->L[0].rij, w.a, w.Bs, w.FRd, w.Gd);
     stage("tangent_radial");
-    using MT = AMap<C::NQA, kNptTangent>;
-    k_tangent_angular<C, kNptTangent><<<blocks_for(N, MT::NA), 128, 0, A.st>>>(
-        N, dm, nl->type, nl->atom_struct, nl->L[1].off, nl->L[1].owner, nl->L[1].j, nl->L[1].rij, w.a, w.Bs, w.S,
-        w.Sd, w.Gd);
+    k_tangent_angular<C, kNptTangent><<<nl->natile[1], 128, 0, A.st>>>(
+        N, dm, nl->atile[1], nl->type, nl->atom_struct, nl->L[1].off, nl->L[1].owner, nl->L[1].j, nl->L[1].rij, w.a,
+        w.Bs, w.S, w.Sd, w.Gd);
     stage("tangent_angular");
     int rc;
     switch (hidden_pad(m->shape.H)) {
@@ -853,11 +856,9 @@ struct Runner {
     }
     if (rc) return rc;
     stage("mlp_bwd");
-    using MC = AMap<C::NQ, 1>;
-    const int ntile = blocks_for(N, MC::NA);
-    k_cgrad<C><<<ntile < kCgBlocks ? ntile : kCgBlocks, 128, 0, A.st>>>(
-        N, ntile, dm, nl->type, nl->atom_struct, nl->L[1].off, nl->L[1].owner, nl->L[1].j, nl->L[1].rij, w.a, w.Bs,
-        w.S, w.Sd, w.Gb, w.Ep, w.FR, w.FRd, w.cpart);
+    k_cgrad<C><<<cgrad_blocks(nl->natile[1]), 128, 0, A.st>>>(
+        N, nl->natile[1], nl->atile[1], dm, nl->type, nl->atom_struct, nl->L[1].off, nl->L[1].owner, nl->L[1].j,
+        nl->L[1].rij, w.a, w.Bs, w.S, w.Sd, w.Gb, w.Ep, w.FR, w.FRd, w.cpart);
     stage("cgrad");
     GNEP_CHECK_LAUNCH("backward sweeps");
     return GNEP_OK;
@@ -929,11 +930,20 @@ int run_backward(const StepArgs& A) {
   return set_error(GNEP_ERR_UNSUPPORTED, "no kernel for this shape");
 }
 
-int cgrad_blocks(int n_atoms, const Shape& s) {
-  const int tpa = s.nqr > s.nqa ? s.nqr : s.nqa;
-  const int na = 128 / tpa;
-  const int ntile = (n_atoms + na - 1) / na;
-  return ntile < kCgBlocks ? (ntile > 0 ? ntile : 1) : kCgBlocks;
+int cgrad_blocks(int ntiles) { return ntiles < kCgBlocks ? (ntiles > 0 ? ntiles : 1) : kCgBlocks; }
+
+// Tile limits of the angular sweeps: [0] descriptor sweep (kNptDesc channels
+// per thread, kChDesc pairs), [1] force, tangent and c-gradient sweeps (one
+// channel per thread, CH pairs).
+void angular_tile_limits(const Shape& s, int which, int* na, int* ch) {
+  const int nq = s.nqr > s.nqa ? s.nqr : s.nqa;
+  if (which == 0) {
+    *na = 128 / ((s.nqa + kNptDesc - 1) / kNptDesc);
+    *ch = kChDesc;
+  } else {
+    *na = 128 / nq;
+    *ch = CH;
+  }
 }
 
 }  // namespace gnep
@@ -996,9 +1006,9 @@ int descriptors_static(const StepArgs& A, float* G) {
   // array needs no clearing between calls.
   k_desc_radial<C><<<blocks_for(N * RL, 128), 128, 0, A.st>>>((int)N, dm, nl->type, nl->L[0].off, nl->L[0].rij,
                                                               scratch, G);
-  using MA = AMap<C::NQA, 2>;
-  k_desc_angular<C, 2><<<blocks_for(N, MA::NA), 128, 0, A.st>>>((int)N, dm, nl->type, nl->L[1].off, nl->L[1].rij,
-                                                                 scratch + fr_padded, G);
+  k_desc_angular<C, kNptDesc, kChDesc><<<nl->natile[0], 128, 0, A.st>>>((int)N, dm, nl->atile[0], nl->type,
+                                                                         nl->L[1].off, nl->L[1].rij,
+                                                                         scratch + fr_padded, G);
   GNEP_CHECK_LAUNCH("descriptor sweep (static scratch)");
   return GNEP_OK;
 }

@@ -272,7 +272,9 @@ class TrainGraph:
         self.h = h
 
     def launch(self, stream=None):
-        s = stream or self.stream
+        """Replay the step on `stream` (default: torch's current stream, so the
+        replay is ordered with the caller's subsequent torch operations)."""
+        s = stream if stream is not None else torch.cuda.current_stream()
         check(_lib.load().gnep_graph_launch(self.h, C.c_void_p(s.cuda_stream)))
 
     def close(self):
