@@ -189,6 +189,41 @@ int gnep_forward(gnep_model *m, const gnep_nlist *nl, float *E_atom,
 int gnep_loss_grad(gnep_model *m, const gnep_nlist *nl, const gnep_labels *y,
                    double *loss_terms, float *grad, void *stream);
 
+/* Autotuner.  Launch shapes of the angular sweeps are per batch: atoms and
+ * pairs per tile of the descriptor sweep's tiles and of the force / tangent /
+ * c-gradient sweeps' tiles, and the number of persistent blocks of the
+ * c-gradient sweep.  gnep_autotune times the loss + gradient evaluation of
+ * this batch (median of `reps` runs, no parameter update) over candidate
+ * values of each in turn and keeps the fastest in the neighbour list.  It
+ * synchronizes `stream` and must not run during stream capture; graphs
+ * captured earlier on this list are invalidated (gnep_graph_launch then
+ * returns INVALID_ARG).  values [5] = {atoms per descriptor tile, pairs per
+ * descriptor tile, atoms per force tile, pairs per force tile, c-gradient
+ * blocks}; gnep_tuning_set takes the same layout (0 = default) and rebuilds
+ * the tiles.  Results agree with the untuned ones to FP32 summation order.
+ * Errors: INVALID_ARG, CUDA, and those of gnep_loss_grad. */
+int gnep_autotune(gnep_model *m, gnep_nlist *nl, const gnep_labels *y,
+                  int reps, void *stream);
+int gnep_tuning_get(const gnep_model *m, const gnep_nlist *nl,
+                    int32_t *values);
+int gnep_tuning_set(gnep_model *m, gnep_nlist *nl, const int32_t *values,
+                    void *stream);
+
+/* Loss only (Eqs. 9-12): the forward pass and loss_terms [4] as in
+ * gnep_loss_grad, without the backward pass.  Used where the loss must be
+ * known before the gradient is formed, e.g. the whole-batch RMSE of a batch
+ * split over ranks.  Errors: as gnep_loss_grad. */
+int gnep_loss(gnep_model *m, const gnep_nlist *nl, const gnep_labels *y,
+              double *loss_terms, void *stream);
+
+/* The model's FP64 gradient dL/dtheta (the one gnep_adam_step applies):
+ * copy it out to dst, or replace it by src ([n] doubles, host or device,
+ * n = gnep_num_params).  Lets a caller sum gradients over data-parallel ranks
+ * between gnep_loss_grad and gnep_adam_step.  set_grad with a host source
+ * returns after the copy.  Errors: INVALID_ARG (NULL or n mismatch), CUDA. */
+int gnep_get_grad(gnep_model *m, double *dst, int64_t n, void *stream);
+int gnep_set_grad(gnep_model *m, const double *src, int64_t n, void *stream);
+
 /* Adam update (Kingma & Ba, bias-corrected; AdamW decay if weight_decay > 0)
  * with the model's last gradient.  The update count t lives in device memory
  * and advances by one per call.  lr is used as given. */

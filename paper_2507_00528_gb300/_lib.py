@@ -30,7 +30,8 @@ EXPORTS = [
     "gnep_loss_grad", "gnep_adam_step", "gnep_adam_step_scheduled", "gnep_get_step",
     "gnep_lr_schedule", "gnep_graph_create", "gnep_graph_launch", "gnep_graph_destroy", "gnep_save",
     "gnep_load", "gnep_sync_status", "gnep_last_error", "gnep_abi_version", "gnep_profile_step",
-    "gnep_profile_stage_name", "gnep_descriptors_noalloc",
+    "gnep_profile_stage_name", "gnep_descriptors_noalloc", "gnep_loss", "gnep_get_grad", "gnep_set_grad",
+    "gnep_autotune", "gnep_tuning_get", "gnep_tuning_set",
 ]
 
 
@@ -73,6 +74,12 @@ _SIGS = {
     "gnep_descriptors_noalloc": [_vp, _vp, _vp, _vp],
     "gnep_forward": [_vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "gnep_loss_grad": [_vp, _vp, C.POINTER(Labels), _vp, _vp, _vp],
+    "gnep_loss": [_vp, _vp, C.POINTER(Labels), _vp, _vp],
+    "gnep_get_grad": [_vp, _vp, C.c_int64, _vp],
+    "gnep_set_grad": [_vp, _vp, C.c_int64, _vp],
+    "gnep_autotune": [_vp, _vp, C.POINTER(Labels), C.c_int, _vp],
+    "gnep_tuning_get": [_vp, _vp, _vp],
+    "gnep_tuning_set": [_vp, _vp, _vp, _vp],
     "gnep_adam_step": [_vp, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, _vp],
     "gnep_adam_step_scheduled": [_vp, C.c_double, C.c_double, C.c_int64, C.c_int64, C.c_double,
                                  C.c_double, C.c_double, C.c_double, _vp],

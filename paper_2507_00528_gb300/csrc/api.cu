@@ -1,5 +1,6 @@
 // C ABI of libgnep: models, neighbour lists, one training step, Adam, graphs,
 // checkpoints and error reporting.  See include/gnep.h for the contract.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -137,6 +138,8 @@ int gnep_create(gnep_model** out, int n_species, const int* species_z, double rc
     return set_error(GNEP_ERR_UNSUPPORTED,
                      "no compiled kernel for this shape (built: 2 species, l_max 4, n_max/basis 4/8 without "
                      "4-body or 8/12 with or without 4-body)");
+  if (precision != GNEP_PREC_FP32 && hidden > kMaxHiddenTc)
+    return set_error(GNEP_ERR_UNSUPPORTED, "TF32/BF16 network tiles hold at most 112 hidden neurons");
   gnep_model* m = new gnep_model();
   m->shape = s;
   m->rcr = rc_radial;
@@ -187,6 +190,8 @@ int gnep_destroy(gnep_model* m) {
 
 int gnep_set_precision(gnep_model* m, int precision) {
   if (!m || precision < 0 || precision > 2) return set_error(GNEP_ERR_INVALID_ARG, "bad precision");
+  if (precision != GNEP_PREC_FP32 && m->shape.H > kMaxHiddenTc)
+    return set_error(GNEP_ERR_UNSUPPORTED, "TF32/BF16 network tiles hold at most 112 hidden neurons");
   m->precision = precision;
   return GNEP_OK;
 }
@@ -278,6 +283,8 @@ static int build_angular_tiles(gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
   for (int which = 0; which < 2; ++which) {
     int na = 0, ch = 0;
     angular_tile_limits(m->shape, which, &na, &ch);
+    if (nl->tune.na[which] > 0 && nl->tune.na[which] < na) na = nl->tune.na[which];
+    if (nl->tune.ch[which] > 0) ch = nl->tune.ch[which];
     std::vector<int> t;
     int i = 0;
     while (i < N) {
@@ -299,6 +306,7 @@ static int build_angular_tiles(gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
 
 static int finish_build(gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
   int rc;
+  ++nl->gen;
   if (nl->n_atoms > 0) {
     if ((rc = build_lists(m, nl, st))) return rc;
     if ((rc = run_species_perm(nl, st))) return rc;
@@ -447,7 +455,8 @@ int gnep_forward(gnep_model* m, const gnep_nlist* nl_, float* E_atom, double* E_
   return copy_out(W_struct, nl->ws.Ws, 48 * S, st);
 }
 
-static int loss_grad_core(gnep_model* m, gnep_nlist* nl, const gnep_labels* y, cudaStream_t st) {
+// Labels staged on the device, then descriptors, network, forces and the loss (Eqs. 1-12).
+static int forward_loss(gnep_model* m, gnep_nlist* nl, const gnep_labels* y, cudaStream_t st) {
   if (!y || (nl->n_struct > 0 && (!y->energy || !y->virial)) || (nl->n_atoms > 0 && !y->force))
     return set_error(GNEP_ERR_INVALID_ARG, "incomplete labels");
   if (y->loss_form != GNEP_LOSS_MSE && y->loss_form != GNEP_LOSS_RMSE)
@@ -465,9 +474,36 @@ static int loss_grad_core(gnep_model* m, gnep_nlist* nl, const gnep_labels* y, c
   int rc;
   if ((rc = run_descriptors(A, true))) return rc;
   if ((rc = run_forward(A))) return rc;
-  if ((rc = run_loss_impl(m, nl, le, lf, lv, y, st))) return rc;
+  return run_loss_impl(m, nl, le, lf, lv, y, st);
+}
+
+static int loss_grad_core(gnep_model* m, gnep_nlist* nl, const gnep_labels* y, cudaStream_t st) {
+  int rc;
+  if ((rc = forward_loss(m, nl, y, st))) return rc;
+  StepArgs A{m, nl, st};
   if ((rc = run_backward(A))) return rc;
   return run_grad_reduce_impl(m, nl, y->lambda_l2, st);
+}
+
+int gnep_loss(gnep_model* m, const gnep_nlist* nl_, const gnep_labels* y, double* loss_terms, void* stream) {
+  int rc = check_nlist(m, nl_);
+  if (rc) return rc;
+  gnep_nlist* nl = const_cast<gnep_nlist*>(nl_);
+  cudaStream_t st = (cudaStream_t)stream;
+  if ((rc = forward_loss(m, nl, y, st))) return rc;
+  return copy_out(loss_terms, nl->ws.coef, 4 * sizeof(double), st);
+}
+
+int gnep_get_grad(gnep_model* m, double* dst, int64_t n, void* stream) {
+  if (!m || !dst || n != m->n_params) return set_error(GNEP_ERR_INVALID_ARG, "gradient buffer");
+  return copy_out(dst, m->grad, 8 * (size_t)n, (cudaStream_t)stream);
+}
+
+int gnep_set_grad(gnep_model* m, const double* src, int64_t n, void* stream) {
+  if (!m || !src || n != m->n_params) return set_error(GNEP_ERR_INVALID_ARG, "gradient buffer");
+  GNEP_CUDA(cudaMemcpyAsync(m->grad, src, 8 * (size_t)n, cudaMemcpyDefault, (cudaStream_t)stream));
+  if (!is_device_ptr(src)) GNEP_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  return GNEP_OK;
 }
 
 int gnep_loss_grad(gnep_model* m, const gnep_nlist* nl_, const gnep_labels* y, double* loss_terms, float* grad,
@@ -523,6 +559,8 @@ double gnep_lr_schedule(double lr_start, double lr_stop, int64_t s, int64_t n_wa
 struct gnep_graph {
   cudaGraph_t g = nullptr;
   cudaGraphExec_t ge = nullptr;
+  const gnep_nlist* nl = nullptr;
+  uint64_t gen = 0;  // generation of the neighbour list at capture
 };
 
 int gnep_graph_create(gnep_model* m, const gnep_nlist* nl_, const gnep_labels* y, double* loss_out,
@@ -552,6 +590,8 @@ int gnep_graph_create(gnep_model* m, const gnep_nlist* nl_, const gnep_labels* y
   if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture");
   gnep_graph* gr = new gnep_graph();
   gr->g = g;
+  gr->nl = nl;
+  gr->gen = nl->gen;
   e = cudaGraphInstantiate(&gr->ge, g, 0);
   if (e != cudaSuccess) {
     cudaGraphDestroy(g);
@@ -564,7 +604,123 @@ int gnep_graph_create(gnep_model* m, const gnep_nlist* nl_, const gnep_labels* y
 
 int gnep_graph_launch(gnep_graph* g, void* stream) {
   if (!g) return set_error(GNEP_ERR_INVALID_ARG, "NULL graph");
+  if (g->nl && g->nl->gen != g->gen)
+    return set_error(GNEP_ERR_INVALID_ARG, "the neighbour list was rebuilt or retuned after this graph was captured");
   GNEP_CUDA(cudaGraphLaunch(g->ge, (cudaStream_t)stream));
+  return GNEP_OK;
+}
+
+// ---------------------------------------------------------------- autotuner
+
+namespace {
+
+constexpr int kTuneKnobs = 5;  // na[0], ch[0], na[1], ch[1], cg_blocks
+
+int* knob(gnep_nlist* nl, int k) {
+  switch (k) {
+    case 0: return &nl->tune.na[0];
+    case 1: return &nl->tune.ch[0];
+    case 2: return &nl->tune.na[1];
+    case 3: return &nl->tune.ch[1];
+    default: return &nl->tune.cg_blocks;
+  }
+}
+
+// Effective value of each knob (the tuned value, or the built-in default).
+void effective_tuning(const gnep_model* m, const gnep_nlist* nl, int32_t* v) {
+  for (int w = 0; w < 2; ++w) {
+    int na = 0, ch = 0;
+    angular_tile_limits(m->shape, w, &na, &ch);
+    v[2 * w] = (nl->tune.na[w] > 0 && nl->tune.na[w] < na) ? nl->tune.na[w] : na;
+    v[2 * w + 1] = nl->tune.ch[w] > 0 ? nl->tune.ch[w] : ch;
+  }
+  v[4] = cgrad_blocks(nl);
+}
+
+// Median over `reps` of one loss + gradient evaluation (no update), in ms.
+int time_step(gnep_model* m, gnep_nlist* nl, const gnep_labels* y, int reps, cudaStream_t st, float* ms) {
+  cudaEvent_t a, b;
+  GNEP_CUDA(cudaEventCreate(&a));
+  GNEP_CUDA(cudaEventCreate(&b));
+  std::vector<float> t;
+  int rc = loss_grad_core(m, nl, y, st);  // warm-up
+  for (int r = 0; r < reps && !rc; ++r) {
+    cudaEventRecord(a, st);
+    rc = loss_grad_core(m, nl, y, st);
+    cudaEventRecord(b, st);
+    if (!rc && cudaEventSynchronize(b) == cudaSuccess) {
+      float x = 0.f;
+      cudaEventElapsedTime(&x, a, b);
+      t.push_back(x);
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (rc) return rc;
+  if (t.empty()) return set_error(GNEP_ERR_CUDA, "autotune timing failed");
+  std::sort(t.begin(), t.end());
+  *ms = t[t.size() / 2];
+  return GNEP_OK;
+}
+
+}  // namespace
+
+int gnep_tuning_get(const gnep_model* m, const gnep_nlist* nl, int32_t* values) {
+  if (check_nlist(m, nl) || !values) return set_error(GNEP_ERR_INVALID_ARG, "NULL argument or foreign list");
+  effective_tuning(m, nl, values);
+  return GNEP_OK;
+}
+
+int gnep_tuning_set(gnep_model* m, gnep_nlist* nl, const int32_t* values, void* stream) {
+  int rc = check_nlist(m, nl);
+  if (rc) return rc;
+  if (!values) return set_error(GNEP_ERR_INVALID_ARG, "NULL values");
+  for (int k = 0; k < kTuneKnobs; ++k)
+    if (values[k] < 0 || values[k] > (k == 4 ? kCgBlocksMax : 1 << 20))
+      return set_error(GNEP_ERR_INVALID_ARG, "tuning value out of range");
+  for (int k = 0; k < kTuneKnobs; ++k) *knob(nl, k) = values[k];
+  ++nl->gen;
+  if (nl->n_atoms == 0) return GNEP_OK;
+  return build_angular_tiles(m, nl, (cudaStream_t)stream);
+}
+
+int gnep_autotune(gnep_model* m, gnep_nlist* nl, const gnep_labels* y, int reps, void* stream) {
+  int rc = check_nlist(m, nl);
+  if (rc) return rc;
+  if (!y) return set_error(GNEP_ERR_INVALID_ARG, "NULL labels");
+  if (nl->n_atoms == 0) return GNEP_OK;
+  if (reps < 1) reps = 3;
+  cudaStream_t st = (cudaStream_t)stream;
+  int32_t cur[kTuneKnobs];
+  effective_tuning(m, nl, cur);
+  // candidate values per knob; the compiled atom maxima bound the atom caps
+  const int na0 = cur[0], na1 = cur[2];
+  const std::vector<std::vector<int>> cand = {
+      {na0, na0 / 2, na0 / 4},  {64, 128, 256, 384, 512},
+      {na1, na1 / 2, na1 / 4},  {32, 48, 64, 96, 128, 192},
+      {152, 304, 456, 608}};
+  for (int k = 0; k < kTuneKnobs; ++k) *knob(nl, k) = cur[k];
+  ++nl->gen;
+  if ((rc = build_angular_tiles(m, nl, st))) return rc;
+  float best = 0.f;
+  if ((rc = time_step(m, nl, y, reps, st, &best))) return rc;
+  for (int k = 0; k < kTuneKnobs; ++k) {  // coordinate descent, one pass
+    const int keep = *knob(nl, k);
+    int pick = keep;
+    for (int v : cand[k]) {
+      if (v < 1 || v == keep) continue;
+      *knob(nl, k) = v;
+      if (k < 4 && (rc = build_angular_tiles(m, nl, st))) return rc;
+      float t = 0.f;
+      if ((rc = time_step(m, nl, y, reps, st, &t))) return rc;
+      if (t < 0.99f * best) {
+        best = t;
+        pick = v;
+      }
+    }
+    *knob(nl, k) = pick;
+    if (k < 4 && (rc = build_angular_tiles(m, nl, st))) return rc;
+  }
   return GNEP_OK;
 }
 

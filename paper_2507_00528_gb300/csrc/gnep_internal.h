@@ -57,6 +57,7 @@ struct Workspace {
   float *Gd = nullptr, *Sd = nullptr, *FRd = nullptr, *Gb = nullptr;
   float* net_part = nullptr;           // network-gradient partials [blocks][species][net_size]
   float* cpart = nullptr;              // coefficient-gradient partials [blocks][c^R + c^A]
+  int net_blocks = 0;                  // blocks that wrote net_part in the last backward pass
   double* red = nullptr;               // loss partials
   int64_t red_len = 0;
   double* lab_e = nullptr;             // staged labels
@@ -86,6 +87,12 @@ struct gnep_nlist {
   // [0] wide tiles (descriptor sweep), [1] narrow tiles (force, tangent, c-gradient).
   int* atile[2] = {nullptr, nullptr};
   int natile[2] = {0, 0};
+  // Launch shapes chosen by gnep_autotune (0 = built-in default): atoms and
+  // pairs per tile of each tile set, persistent blocks of the c-gradient sweep.
+  struct Tuning {
+    int na[2] = {0, 0}, ch[2] = {0, 0}, cg_blocks = 0;
+  } tune;
+  uint64_t gen = 0;  // bumped whenever lists or tiles change (captured graphs check it)
   gnep::Workspace ws;
   void* ws_mem = nullptr;      // one allocation carved into the workspace
   int64_t ws_pairs[2] = {-1, -1};  // pair counts the workspace was sized for
@@ -151,7 +158,7 @@ int run_backward(const StepArgs& a);
 
 int shape_setup(const Shape& s);
 int run_descriptors_static(const StepArgs& a, float* G);
-int cgrad_blocks(int ntiles);
+int cgrad_blocks(const gnep_nlist* nl);
 void angular_tile_limits(const Shape& s, int which, int* na, int* ch);
 constexpr int kCgBlocksMax = 608;
 

@@ -399,7 +399,7 @@ __global__ void __launch_bounds__(NT) k_mlp_bwd_tile(Tiles T, int ntiles, DevMod
 
 // ------------------------------------------------------------- launchers
 
-Tiles make_tiles(const gnep_nlist* nl, int ns) {
+Tiles make_tiles(const gnep_nlist* nl, int ns, int tile_atoms) {
   Tiles T;
   T.perm = nl->perm;
   T.ns = ns;
@@ -407,7 +407,7 @@ Tiles make_tiles(const gnep_nlist* nl, int ns) {
   for (int e = 0; e <= ns; ++e) {
     T.soff[e] = nl->species_off[e];
     T.tbase[e] = t;
-    if (e < ns) t += (nl->species_off[e + 1] - nl->species_off[e] + TM - 1) / TM;
+    if (e < ns) t += (nl->species_off[e + 1] - nl->species_off[e] + tile_atoms - 1) / tile_atoms;
   }
   return T;
 }
@@ -441,7 +441,8 @@ int mlp_backward(const gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
   const int ntiles = T.tbase[ns];
   Workspace& w = nl->ws;
   const int grid = ntiles < kNetBlocks ? (ntiles > 0 ? ntiles : 1) : kNetBlocks;
-  GNEP_CUDA(cudaMemsetAsync(w.net_part, 0, sizeof(float) * (size_t)kNetBlocks * ns * m->net_size, st));
+  w.net_blocks = grid;
+  GNEP_CUDA(cudaMemsetAsync(w.net_part, 0, sizeof(float) * (size_t)grid * ns * m->net_size, st));
   if (ntiles == 0) return GNEP_OK;
   k_mlp_bwd_tile<D, HP><<<grid, NT, mlp_bwd_smem<D, HP>(), st>>>(T, ntiles, m->dev(), nl->atom_struct, w.es, w.G,
                                                                  w.Gd, w.X, w.Gb, w.net_part, m->net_size);

@@ -15,7 +15,7 @@ struct Tiles {
   int ns;
 };
 
-Tiles make_tiles(const gnep_nlist* nl, int ns);
+Tiles make_tiles(const gnep_nlist* nl, int ns, int tile_atoms = kTileAtoms);
 
 template <int D, int HP, int NS, int NQR, int KR>
 int mlp_setup();
@@ -26,5 +26,16 @@ int mlp_backward(const gnep_model* m, gnep_nlist* nl, cudaStream_t st);
 
 // Hidden width padded to the instantiated tile width.
 inline int hidden_pad(int H) { return H <= 32 ? 32 : H <= 64 ? 64 : 128; }
+
+// Tensor-core network (network_tc.cu): BF16 (TF32 = false) or TF32 operands,
+// FP32 accumulation; hidden width padded to a multiple of 16 up to 112.
+constexpr int kMaxHiddenTc = 112;
+inline int hidden_pad_tc(int H) { return H <= 32 ? 32 : H <= 64 ? 64 : 112; }
+template <bool TF32, int D, int HPn, int NS, int NQR, int KR>
+int mlp_setup_tc();
+template <bool TF32, int D, int HPn, int NS, int NQR, int KR>
+int mlp_forward_tc(const gnep_model* m, gnep_nlist* nl, cudaStream_t st);
+template <bool TF32, int D, int HPn>
+int mlp_backward_tc(const gnep_model* m, gnep_nlist* nl, cudaStream_t st);
 
 }  // namespace gnep

@@ -1,0 +1,553 @@
+// Per-element network (D1.1-D1.10, and the tangent/reverse pass of
+// D1.18-D1.21) with its contractions on the fifth-generation tensor cores:
+// BF16 or TF32 operands staged in shared memory, FP32 accumulation in tensor
+// memory (TMEM).  Tiles hold 128 atoms of one species, so that an atom is a
+// row of every MMA and thread t of the block owns TMEM lane t, i.e. atom t of
+// the tile: the element-wise epilogues (tanh, beta, alpha, energies) run
+// thread-per-atom straight out of TMEM.
+//
+// Forward, per tile:   Z  = (s.G) W0^T                     [128 x H]
+//                      E' = (w1 (1 - x^2)) W0, scaled by s  [128 x D]
+// Backward, per tile:  Z, Zdot = (s.G) W0^T, (s.Gdot) W0^T
+//                      Gbar = s . (alpha W0)
+//                      dW0 += alpha^T (s.G) - beta^T (s.Gdot)    (K = atoms)
+// dW0 stays in TMEM across all tiles a block visits for one species and is
+// written once, as one partial per block and species; db0 = sum of alpha comes
+// out of the same accumulator through a column of ones appended to (s.G)^T.
+// All operands are K-major; the operands of the atom contraction are written
+// transposed by the epilogue.  The network in FP32 (network.cu) is the plain
+// form these modes are measured against.
+#include "gnep_internal.h"
+#include "network.cuh"
+#include "tc.cuh"
+
+namespace gnep {
+
+namespace {
+
+constexpr int TA = 128;                      // atoms per tile = MMA rows = TMEM lanes
+constexpr int NTC = 256;                     // threads per block: warps w and w + 4 share TMEM lanes 32 (w % 4) ..
+constexpr int kLB = 16;                      // global loads a thread keeps in flight while staging a tile
+constexpr uint64_t kWaitNs = 1000000000ull;  // give up on an MMA completion after 1 s
+constexpr int kSmemPerSm = 233472;           // shared memory per SM (228 KB)
+
+__device__ __forceinline__ void tile_of(const Tiles& T, int t, int& e, int& a0, int& na) {
+  e = 0;
+  while (e + 1 < T.ns && t >= T.tbase[e + 1]) ++e;
+  a0 = T.soff[e] + (t - T.tbase[e]) * TA;
+  na = min(TA, T.soff[e + 1] - a0);
+}
+
+template <bool TF32, int D, int HPn>
+struct Dims {
+  static constexpr int ES = tc::Elem<TF32>::ES;
+  static constexpr int DPn = (D + 1 + 15) / 16 * 16;  // descriptor width + the ones column, padded
+  static constexpr uint32_t sG = tc::sbo<TF32>(DPn);  // rows of length DPn:  [atoms][v], [mu][v]
+  static constexpr uint32_t sH = tc::sbo<TF32>(HPn);  // rows of length HPn:  [atoms][mu], [v][mu]
+  static constexpr uint32_t sA = tc::sbo<TF32>(TA);   // rows of length TA:   [mu][atoms], [v][atoms]
+  static constexpr int bG = TA * DPn * ES;
+  static constexpr int bH = TA * HPn * ES;
+  static constexpr int bW0 = HPn * DPn * ES;
+  static constexpr int bT = 128 * TA * ES;  // [mu][atoms], 128 rows (the MMA's M) whatever H is
+  static constexpr int bGT = DPn * TA * ES;
+  static constexpr int OW = D + 1;          // row pitch (floats) of the FP32 output tile, odd: conflict-free rows
+  static constexpr int bO = TA * OW * 4;
+  // forward: RA (s.G, then beta) | W0 [mu][v] | W0t [v][mu] | output tile (E')
+  static constexpr int fRA = bG > bH ? bG : bH;
+  static constexpr int fwd_smem = fRA + 2 * bW0 + bO;
+  static constexpr int fwd_cols = tc::pow2_cols(HPn + DPn);
+  // backward: RA (s.G | s.Gdot, then alpha) | RG ((s.G)^T, then (s.Gdot)^T) |
+  //           RT (alpha^T, then the Gbar output tile, then -beta^T) | W0 | W0t
+  static constexpr int bRA = 2 * bG > bH ? 2 * bG : bH;
+  static constexpr int bwd_smem = bRA + bGT + bT + 2 * bW0;
+  static constexpr int bwd_cols = tc::pow2_cols(2 * HPn + 2 * DPn);
+  static_assert(bO <= bT, "the Gbar output tile lives in the [mu][atoms] operand");
+  // blocks per SM that TMEM and shared memory admit (caps the registers per thread via launch bounds)
+  static constexpr int fits(int smem, int cols) {
+    const int by_smem = kSmemPerSm / (smem + 6 * 1024), by_tmem = 512 / cols;
+    const int b = by_smem < by_tmem ? by_smem : by_tmem;
+    return b < 1 ? 1 : (b > 2 ? 2 : b);
+  }
+  static constexpr int fwd_minb = fits(fwd_smem, fwd_cols);
+  static constexpr int bwd_minb = fits(bwd_smem, bwd_cols);
+};
+
+// W0 of species e as [mu][v] and [v][mu] operands (zero-padded), b0 and w1.
+template <bool TF32, int D, int HPn>
+__device__ void stage_weights(const DevModel& dm, int e, uint8_t* W0, uint8_t* W0t, float* b0s, float* w1s) {
+  using Dm = Dims<TF32, D, HPn>;
+  const float* P = dm.params + (size_t)e * dm.net_size;
+  const int H = dm.H;
+  for (int q = threadIdx.x; q < HPn * Dm::DPn; q += NTC) {
+    const int mu = q / Dm::DPn, v = q % Dm::DPn;
+    const float w = (mu < H && v < D) ? P[mu * D + v] : 0.f;
+    tc::st_elem<TF32>(W0, tc::core_off<TF32>(mu, v, Dm::sG), w);
+    tc::st_elem<TF32>(W0t, tc::core_off<TF32>(v, mu, Dm::sH), w);
+  }
+  for (int mu = threadIdx.x; mu < HPn; mu += NTC) {
+    b0s[mu] = mu < H ? P[D * H + mu] : 0.f;
+    w1s[mu] = mu < H ? P[D * H + H + mu] : 0.f;
+  }
+}
+
+// Rows `rows[a]` (a < TA, -1 = padding) of one or two per-atom arrays of
+// width D, zero-padded to DPn columns, handed to store(a, v, x0, x1).  Each
+// thread keeps LB loads in flight (LB / 2 of each of two arrays) before it
+// stores them.
+template <int D, int DPn, bool TWO, class F>
+__device__ __forceinline__ void stage_rows(const float* __restrict__ s0, const float* __restrict__ s1,
+                                           const int* rows, F store) {
+  constexpr int PER = TA * DPn / NTC;
+  constexpr int LB = TWO ? kLB / 2 : kLB;
+#pragma unroll
+  for (int b0 = 0; b0 < PER; b0 += LB) {
+    float x0[LB], x1[LB];
+#pragma unroll
+    for (int u = 0; u < LB; ++u) {
+      const int k = b0 + u;
+      if (k < PER) {
+        const int q = threadIdx.x + k * NTC, a = q / DPn, v = q % DPn, r = rows[a];
+        const bool in = r >= 0 && v < D;
+        x0[u] = in ? s0[(size_t)r * D + v] : 0.f;
+        if (TWO) x1[u] = in ? s1[(size_t)r * D + v] : 0.f;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < LB; ++u) {
+      const int k = b0 + u;
+      if (k < PER) {
+        const int q = threadIdx.x + k * NTC;
+        store(q / DPn, q % DPn, x0[u], TWO ? x1[u] : 0.f);
+      }
+    }
+  }
+}
+
+// Make this thread's generic-proxy shared-memory writes and TMEM reads
+// ordered before an MMA that a thread issues after the barrier.
+__device__ __forceinline__ void sync_for_mma() {
+  tc::fence_async_smem();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+}
+
+// Wait for the MMAs committed on `mbar` (phase `ph`); the outcome is made
+// uniform across the block so that every thread leaves the tile loop together.
+__device__ __forceinline__ bool wait_mma(uint64_t* mbar, uint32_t& ph) {
+  const bool ok = tc::mbar_wait(mbar, ph, kWaitNs);
+  ph ^= 1u;
+  tc::fence_after();
+  return __syncthreads_and(ok) != 0;
+}
+
+// After a timed-out wait: give the MMAs in flight a second bounded wait before
+// the tensor memory they write is released, and raise the error flag.
+__device__ __forceinline__ void on_timeout(uint64_t* mbar, uint32_t ph, int* err) {
+  tc::mbar_wait(mbar, ph ^ 1u, kWaitNs);
+  if (threadIdx.x == 0) atomicOr(err, kErrTimeout);
+}
+
+}  // namespace
+
+// Forward, persistent over 128-atom tiles: energies (D1.1), E' (D1.5) and the
+// per-atom radial contraction chat_i[J][k] = sum_n E'_n c^R_nk^{IJ} used by
+// the force sweep.  Thread t reads TMEM lane 32 (w % 4) + (t % 32) (its atom)
+// and the 16-column chunks c = w / 4, w / 4 + 2, ... of each accumulator.
+template <bool TF32, int D, int HPn, int NS, int NQR, int KR>
+__global__ void __launch_bounds__(NTC, (Dims<TF32, D, HPn>::fwd_minb))
+    k_mlp_fwd_tc(Tiles T, int ntiles, DevModel dm, const float* __restrict__ G, float* __restrict__ Ep,
+                 float* __restrict__ Eatom, float* __restrict__ chat, int* __restrict__ err) {
+  using Dm = Dims<TF32, D, HPn>;
+  constexpr int DPn = Dm::DPn, OW = Dm::OW, NCZ = HPn / 16, NCE = DPn / 16, NJK = NS * KR;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* RA = smem;
+  uint8_t* W0 = RA + Dm::fRA;
+  uint8_t* W0t = W0 + Dm::bW0;
+  float* O = reinterpret_cast<float*>(W0t + Dm::bW0);  // [TA][OW] scaled E'
+  __shared__ float b0s[HPn], w1s[HPn], sc[DPn], cR[NS * NQR * KR], Eh[2][TA];
+  __shared__ int rows[TA];
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t tbase;
+  const int tid = threadIdx.x, warp = tid >> 5, half = warp >> 2;
+  const int arow = 32 * (warp & 3) + (tid & 31);
+  if (warp == 0) tc::tmem_alloc(&tbase, Dm::fwd_cols);
+  if (tid == 0) tc::mbar_init(&mbar, 1);
+  for (int v = tid; v < DPn; v += NTC) sc[v] = v < D ? dm.scale[v] : 0.f;
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tm = tbase;
+  const uint32_t lane = tm + ((uint32_t)(32 * (warp & 3)) << 16);
+  const uint32_t cZ = 0, cE = HPn;  // TMEM columns of Z and E'
+  uint32_t ph = 0;
+  bool ok = true;
+  int cur_e = -1;
+  float b1 = 0.f;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int e, a0, na;
+    tile_of(T, t, e, a0, na);
+    if (e != cur_e) {
+      stage_weights<TF32, D, HPn>(dm, e, W0, W0t, b0s, w1s);
+      for (int q = tid; q < NS * NQR * KR; q += NTC) cR[q] = dm.params[dm.off_cR + e * NS * NQR * KR + q];
+      b1 = dm.params[(size_t)e * dm.net_size + D * dm.H + 2 * dm.H];
+      cur_e = e;
+    }
+    if (tid < TA) rows[tid] = tid < na ? T.perm[a0 + tid] : -1;
+    __syncthreads();
+    stage_rows<D, DPn, false>(G, nullptr, rows, [&](int a, int v, float g, float) {
+      tc::st_elem<TF32>(RA, tc::core_off<TF32>(a, v, Dm::sG), sc[v] * g);
+    });
+    sync_for_mma();
+    if (tid == 0) {
+      tc::mma_chain<TF32>(tm + cZ, RA, Dm::sG, W0, Dm::sG, DPn, HPn, false);
+      tc::commit(&mbar);
+    }
+    if (!(ok = wait_mma(&mbar, ph))) break;
+    // x = tanh(z + b0), E = w1.x + b1, beta = w1 (1 - x^2) -> RA as [atoms][mu]
+    float E = 0.f;
+    for (int c = half; c < NCZ; c += 2) {
+      float z[16], bt[16];
+      tc::ld16(lane + cZ + 16 * c, z);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int mu = 16 * c + q;
+        const float x = tanhf(z[q] + b0s[mu]);
+        E = fmaf(w1s[mu], x, E);
+        bt[q] = w1s[mu] * (1.f - x * x);
+      }
+#pragma unroll
+      for (int q = 0; q < 16; q += tc::Elem<TF32>::EPC)
+        tc::st_chunk<TF32>(RA, tc::core_off<TF32>(arow, 16 * c + q, Dm::sH), bt + q);
+    }
+    Eh[half][arow] = E;
+    sync_for_mma();
+    if (tid == 0) {
+      tc::mma_chain<TF32>(tm + cE, RA, Dm::sH, W0t, Dm::sH, HPn, DPn, false);
+      tc::commit(&mbar);
+    }
+    if (tid < TA) {
+      const int r = rows[tid];
+      if (r >= 0) Eatom[r] = (Eh[0][tid] + Eh[1][tid]) + b1;
+    }
+    if (!(ok = wait_mma(&mbar, ph))) break;
+    for (int c = half; c < NCE; c += 2) {
+      float v[16];
+      tc::ld16(lane + cE + 16 * c, v);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int vv = 16 * c + q;
+        if (vv < D) O[arow * OW + vv] = v[q] * sc[vv];
+      }
+    }
+    tc::fence_before();
+    __syncthreads();
+    // coalesced row writes: E' and chat
+    for (int q = tid; q < TA * D; q += NTC) {
+      const int a = q / D, v = q % D, r = rows[a];
+      if (r >= 0) Ep[(size_t)r * D + v] = O[a * OW + v];
+    }
+    for (int q = tid; q < TA * NJK; q += NTC) {
+      const int a = q / NJK, jk = q % NJK, r = rows[a];
+      if (r < 0) continue;
+      const int J = jk / KR, k = jk % KR;
+      float s = 0.f;
+#pragma unroll
+      for (int n = 0; n < NQR; ++n) s = fmaf(O[a * OW + n], cR[(J * NQR + n) * KR + k], s);
+      chat[(size_t)r * NJK + jk] = s;
+    }
+    __syncthreads();  // rows, RA, O and the TMEM columns are rewritten by the next tile
+    tc::fence_after();
+  }
+  if (!ok) on_timeout(&mbar, ph, err);
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tm, Dm::fwd_cols);
+}
+
+// Tangent and reverse pass, persistent over 128-atom tiles, with e_i the
+// energy residual weight of the atom's structure:
+//   zdot = W0 (s.Gdot), beta = w1 (1 - x^2), alpha = e_i beta + 2 x beta zdot,
+//   Gbar = s . (W0^T alpha),
+//   dW0 += alpha (s.G)^T - beta (s.Gdot)^T, db0 += alpha,
+//   dw1 += e_i x - (1 - x^2) zdot, db1 += e_i.
+// One partial per block and species visited goes to part[block][species].
+template <bool TF32, int D, int HPn>
+__global__ void __launch_bounds__(NTC, (Dims<TF32, D, HPn>::bwd_minb))
+    k_mlp_bwd_tc(Tiles T, int ntiles, DevModel dm, const int* __restrict__ atom_struct, const float* __restrict__ es,
+                 const float* __restrict__ G, const float* __restrict__ Gd, float* __restrict__ Gb,
+                 float* __restrict__ part, int part_stride, int* __restrict__ err) {
+  using Dm = Dims<TF32, D, HPn>;
+  constexpr int DPn = Dm::DPn, OW = Dm::OW, NCZ = HPn / 16, NCD = DPn / 16;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* RA = smem;          // s.G | s.Gdot as [atoms][v]; then alpha as [atoms][mu]
+  uint8_t* RG = RA + Dm::bRA;  // (s.G)^T with a row of ones at v = D, then (s.Gdot)^T, as [v][atoms]
+  uint8_t* RT = RG + Dm::bGT;  // alpha^T, then the Gbar output tile, then -beta^T, as [mu][atoms]
+  uint8_t* W0 = RT + Dm::bT;
+  uint8_t* W0t = W0 + Dm::bW0;
+  float* O = reinterpret_cast<float*>(RT);
+  __shared__ float b0s[HPn], w1s[HPn], sc[DPn], wpart[4][HPn];
+  __shared__ int rows[TA];
+  __shared__ float ei[TA];
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t tbase;
+  const int tid = threadIdx.x, warp = tid >> 5, ln = tid & 31, half = warp >> 2;
+  const int arow = 32 * (warp & 3) + ln;
+  const int H = dm.H;
+  // rows HPn..127 of the [mu][atoms] operand must hold zeros whenever an MMA reads it
+  auto zero_pad_rows = [&]() {
+    for (uint32_t o = (uint32_t)(HPn / 8) * Dm::sA + 16u * tid; o < (uint32_t)Dm::bT; o += 16u * NTC)
+      *reinterpret_cast<uint4*>(RT + o) = make_uint4(0u, 0u, 0u, 0u);
+  };
+  if (warp == 0) tc::tmem_alloc(&tbase, Dm::bwd_cols);
+  if (tid == 0) tc::mbar_init(&mbar, 1);
+  for (int v = tid; v < DPn; v += NTC) sc[v] = v < D ? dm.scale[v] : 0.f;
+  zero_pad_rows();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tm = tbase;
+  const uint32_t lane = tm + ((uint32_t)(32 * (warp & 3)) << 16);
+  const uint32_t cZ = 0, cZd = HPn, cGb = 2 * HPn, cW = 2 * HPn + DPn;  // TMEM columns
+  uint32_t ph = 0;
+  bool ok = true, fresh = true;
+  int cur_e = -1;
+  float acc_w1 = 0.f, cb1 = 0.f;
+
+  auto flush = [&](int e) {
+    float* out = part + ((size_t)blockIdx.x * T.ns + e) * part_stride;
+    const int mu = arow;
+    for (int c = half; c < NCD; c += 2) {
+      float v[16];
+      tc::ld16(lane + cW + 16 * c, v);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int vv = 16 * c + q;
+        if (mu < H) {
+          if (vv < D)
+            out[mu * D + vv] = v[q];
+          else if (vv == D)
+            out[D * H + mu] = v[q];  // db0 through the ones column
+        }
+      }
+    }
+    if (tid < H) out[D * H + H + tid] = acc_w1;
+    if (tid == 0) out[D * H + 2 * H] = cb1;
+  };
+
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int e, a0, na;
+    tile_of(T, t, e, a0, na);
+    if (e != cur_e) {
+      if (cur_e >= 0) flush(cur_e);
+      stage_weights<TF32, D, HPn>(dm, e, W0, W0t, b0s, w1s);
+      acc_w1 = 0.f;
+      cb1 = 0.f;
+      fresh = true;
+      cur_e = e;
+    }
+    if (tid < TA) {
+      const int r = tid < na ? T.perm[a0 + tid] : -1;
+      rows[tid] = r;
+      ei[tid] = r >= 0 ? es[atom_struct[r]] : 0.f;
+    }
+    __syncthreads();
+    if (tid == 0)
+      for (int a = 0; a < na; ++a) cb1 += ei[a];
+    stage_rows<D, DPn, true>(G, Gd, rows, [&](int a, int v, float g, float gd) {
+      const uint32_t o = tc::core_off<TF32>(a, v, Dm::sG);
+      tc::st_elem<TF32>(RA, o, sc[v] * g);
+      tc::st_elem<TF32>(RA + Dm::bG, o, sc[v] * gd);
+      tc::st_elem<TF32>(RG, tc::core_off<TF32>(v, a, Dm::sA), v == D ? (rows[a] >= 0 ? 1.f : 0.f) : sc[v] * g);
+    });
+    sync_for_mma();
+    if (tid == 0) {
+      tc::mma_chain<TF32>(tm + cZ, RA, Dm::sG, W0, Dm::sG, DPn, HPn, false);
+      tc::mma_chain<TF32>(tm + cZd, RA + Dm::bG, Dm::sG, W0, Dm::sG, DPn, HPn, false);
+      tc::commit(&mbar);
+    }
+    if (!(ok = wait_mma(&mbar, ph))) break;
+    // alpha -> RA ([atoms][mu]) and RT ([mu][atoms]); column sums of e x - (1 - x^2) zdot
+    const float ea = ei[arow];
+    for (int c = half; c < NCZ; c += 2) {
+      float z[16], zd[16], al[16];
+      tc::ld16(lane + cZ + 16 * c, z);
+      tc::ld16(lane + cZd + 16 * c, zd);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int mu = 16 * c + q;
+        const float x = tanhf(z[q] + b0s[mu]);
+        const float t1 = 1.f - x * x;
+        const float beta = w1s[mu] * t1;
+        al[q] = ea * beta + 2.f * x * beta * zd[q];
+        float q1 = ea * x - t1 * zd[q];  // zero for padded atoms (e = 0, zdot = 0)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) q1 += __shfl_xor_sync(0xffffffffu, q1, o);
+        if (ln == 0) wpart[warp & 3][mu] = q1;
+        tc::st_elem<TF32>(RT, tc::core_off<TF32>(mu, arow, Dm::sA), al[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < 16; q += tc::Elem<TF32>::EPC)
+        tc::st_chunk<TF32>(RA, tc::core_off<TF32>(arow, 16 * c + q, Dm::sH), al + q);
+    }
+    sync_for_mma();
+    if (tid < HPn) acc_w1 += ((wpart[0][tid] + wpart[1][tid]) + wpart[2][tid]) + wpart[3][tid];
+    if (tid == 0) {
+      tc::mma_chain<TF32>(tm + cGb, RA, Dm::sH, W0t, Dm::sH, HPn, DPn, false);
+      tc::mma_chain<TF32>(tm + cW, RT, Dm::sA, RG, Dm::sA, TA, DPn, !fresh);
+      tc::commit(&mbar);
+    }
+    if (!(ok = wait_mma(&mbar, ph))) break;
+    // Gbar -> output tile in RT -> coalesced rows of Gb
+    for (int c = half; c < NCD; c += 2) {
+      float v[16];
+      tc::ld16(lane + cGb + 16 * c, v);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int vv = 16 * c + q;
+        if (vv < D) O[arow * OW + vv] = v[q] * sc[vv];
+      }
+    }
+    __syncthreads();
+    for (int q = tid; q < TA * D; q += NTC) {
+      const int a = q / D, v = q % D, r = rows[a];
+      if (r >= 0) Gb[(size_t)r * D + v] = O[a * OW + v];
+    }
+    __syncthreads();
+    // -beta -> RT ([mu][atoms]); (s.Gdot)^T -> RG
+    for (int c = half; c < NCZ; c += 2) {
+      float z[16];
+      tc::ld16(lane + cZ + 16 * c, z);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int mu = 16 * c + q;
+        const float x = tanhf(z[q] + b0s[mu]);
+        tc::st_elem<TF32>(RT, tc::core_off<TF32>(mu, arow, Dm::sA), -w1s[mu] * (1.f - x * x));
+      }
+    }
+    zero_pad_rows();
+    stage_rows<D, DPn, false>(Gd, nullptr, rows, [&](int a, int v, float gd, float) {
+      tc::st_elem<TF32>(RG, tc::core_off<TF32>(v, a, Dm::sA), sc[v] * gd);
+    });
+    sync_for_mma();
+    if (tid == 0) {
+      tc::mma_chain<TF32>(tm + cW, RT, Dm::sA, RG, Dm::sA, TA, DPn, true);
+      tc::commit(&mbar);
+    }
+    if (!(ok = wait_mma(&mbar, ph))) break;
+    fresh = false;
+  }
+  if (ok && cur_e >= 0) flush(cur_e);
+  if (!ok) on_timeout(&mbar, ph, err);
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tm, Dm::bwd_cols);
+}
+
+// ------------------------------------------------------------- launchers
+
+namespace {
+
+// Dynamic shared memory for a kernel that allocates `cols` TMEM columns: at
+// least `need`, and large enough that no more CTAs share an SM than its 512
+// TMEM columns admit, so that an allocation never waits on another CTA.
+int tc_smem(int need, int cols, int static_bytes) {
+  const int cap = 512 / cols;
+  const int floor_req = kSmemPerSm / (cap + 1) - 1024 - static_bytes + 16;
+  return need > floor_req ? need : floor_req;
+}
+
+// Blocks per SM from the kernel's registers, shared memory and TMEM columns.
+template <class K>
+int tc_launch_shape(K kern, int need, int cols, int ntiles, int& smem, int& grid) {
+  cudaFuncAttributes fa;
+  GNEP_CUDA(cudaFuncGetAttributes(&fa, kern));
+  smem = tc_smem(need, cols, (int)fa.sharedSizeBytes);
+  int dev = 0, nsm = 0;
+  GNEP_CUDA(cudaGetDevice(&dev));
+  GNEP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int regs_warp = (fa.numRegs * 32 + 255) / 256 * 256;
+  const int by_regs = 65536 / (regs_warp * (NTC / 32));
+  const int by_smem = kSmemPerSm / (smem + (int)fa.sharedSizeBytes + 1024);
+  int occ = 512 / cols;
+  if (by_regs < occ) occ = by_regs;
+  if (by_smem < occ) occ = by_smem;
+  if (occ < 1) return set_error(GNEP_ERR_CUDA, "tensor-core network kernel does not fit on an SM");
+  grid = ntiles < nsm * occ ? ntiles : nsm * occ;
+  return GNEP_OK;
+}
+
+template <class K>
+int tc_set_smem(K kern, int need, int cols) {
+  cudaFuncAttributes fa;
+  GNEP_CUDA(cudaFuncGetAttributes(&fa, kern));
+  GNEP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 tc_smem(need, cols, (int)fa.sharedSizeBytes)));
+  GNEP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+  return GNEP_OK;
+}
+
+}  // namespace
+
+template <bool TF32, int D, int HPn, int NS, int NQR, int KR>
+int mlp_setup_tc() {
+  using Dm = Dims<TF32, D, HPn>;
+  int rc = tc_set_smem(k_mlp_fwd_tc<TF32, D, HPn, NS, NQR, KR>, Dm::fwd_smem, Dm::fwd_cols);
+  if (!rc) rc = tc_set_smem(k_mlp_bwd_tc<TF32, D, HPn>, Dm::bwd_smem, Dm::bwd_cols);
+  return rc;
+}
+
+template <bool TF32, int D, int HPn, int NS, int NQR, int KR>
+int mlp_forward_tc(const gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
+  using Dm = Dims<TF32, D, HPn>;
+  const Tiles T = make_tiles(nl, NS, TA);
+  const int ntiles = T.tbase[NS];
+  if (ntiles == 0) return GNEP_OK;
+  Workspace& w = nl->ws;
+  auto kern = k_mlp_fwd_tc<TF32, D, HPn, NS, NQR, KR>;
+  int smem = 0, grid = 0;
+  if (int rc = tc_launch_shape(kern, Dm::fwd_smem, Dm::fwd_cols, ntiles, smem, grid)) return rc;
+  kern<<<grid, NTC, smem, st>>>(T, ntiles, m->dev(), w.G, w.Ep, w.Eatom, w.chat, m->err);
+  GNEP_CHECK_LAUNCH("k_mlp_fwd_tc");
+  return GNEP_OK;
+}
+
+template <bool TF32, int D, int HPn>
+int mlp_backward_tc(const gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
+  using Dm = Dims<TF32, D, HPn>;
+  const int ns = m->shape.ns;
+  const Tiles T = make_tiles(nl, ns, TA);
+  const int ntiles = T.tbase[ns];
+  Workspace& w = nl->ws;
+  auto kern = k_mlp_bwd_tc<TF32, D, HPn>;
+  int smem = 0, grid = 1;
+  if (ntiles > 0)
+    if (int rc = tc_launch_shape(kern, Dm::bwd_smem, Dm::bwd_cols, ntiles, smem, grid)) return rc;
+  if (grid > kNetBlocks) grid = kNetBlocks;  // net_part holds kNetBlocks partials
+  w.net_blocks = grid;
+  GNEP_CUDA(cudaMemsetAsync(w.net_part, 0, sizeof(float) * (size_t)grid * ns * m->net_size, st));
+  if (ntiles == 0) return GNEP_OK;
+  kern<<<grid, NTC, smem, st>>>(T, ntiles, m->dev(), nl->atom_struct, w.es, w.G, w.Gd, w.Gb, w.net_part,
+                                m->net_size, m->err);
+  GNEP_CHECK_LAUNCH("k_mlp_bwd_tc");
+  return GNEP_OK;
+}
+
+#define GNEP_NET_TC1(TF, D, HPN, NQR, KR)                                                               \
+  template int mlp_setup_tc<TF, D, HPN, 2, NQR, KR>();                                                 \
+  template int mlp_forward_tc<TF, D, HPN, 2, NQR, KR>(const gnep_model*, gnep_nlist*, cudaStream_t);   \
+  template int mlp_backward_tc<TF, D, HPN>(const gnep_model*, gnep_nlist*, cudaStream_t);
+#define GNEP_NET_TC(D, NQR, KR)            \
+  GNEP_NET_TC1(false, D, 32, NQR, KR)      \
+  GNEP_NET_TC1(false, D, 64, NQR, KR)      \
+  GNEP_NET_TC1(false, D, 112, NQR, KR)     \
+  GNEP_NET_TC1(true, D, 32, NQR, KR)       \
+  GNEP_NET_TC1(true, D, 64, NQR, KR)       \
+  GNEP_NET_TC1(true, D, 112, NQR, KR)
+GNEP_NET_TC(25, 5, 9)
+GNEP_NET_TC(54, 9, 13)
+GNEP_NET_TC(45, 9, 13)
+#undef GNEP_NET_TC
+#undef GNEP_NET_TC1
+
+}  // namespace gnep

@@ -785,6 +785,47 @@ constexpr int kNptTangent = 1;  // channels per thread, tangent sweep
 
 template <class C>
 struct Runner {
+  // Network forward/backward in the model's precision: plain FP32 tiles, or
+  // tensor-core tiles with TF32 or BF16 operands.
+  static int network_forward(const gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
+    if (m->precision == GNEP_PREC_FP32) {
+      switch (hidden_pad(m->shape.H)) {
+        case 32: return mlp_forward<C::NDES, 32, C::NS, C::NQR, C::KR>(m, nl, st);
+        case 64: return mlp_forward<C::NDES, 64, C::NS, C::NQR, C::KR>(m, nl, st);
+        default: return mlp_forward<C::NDES, 128, C::NS, C::NQR, C::KR>(m, nl, st);
+      }
+    }
+    const bool tf = m->precision == GNEP_PREC_TF32;
+    switch (hidden_pad_tc(m->shape.H)) {
+      case 32:
+        return tf ? mlp_forward_tc<true, C::NDES, 32, C::NS, C::NQR, C::KR>(m, nl, st)
+                  : mlp_forward_tc<false, C::NDES, 32, C::NS, C::NQR, C::KR>(m, nl, st);
+      case 64:
+        return tf ? mlp_forward_tc<true, C::NDES, 64, C::NS, C::NQR, C::KR>(m, nl, st)
+                  : mlp_forward_tc<false, C::NDES, 64, C::NS, C::NQR, C::KR>(m, nl, st);
+      default:
+        return tf ? mlp_forward_tc<true, C::NDES, 112, C::NS, C::NQR, C::KR>(m, nl, st)
+                  : mlp_forward_tc<false, C::NDES, 112, C::NS, C::NQR, C::KR>(m, nl, st);
+    }
+  }
+
+  static int network_backward(const gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
+    if (m->precision == GNEP_PREC_FP32) {
+      switch (hidden_pad(m->shape.H)) {
+        case 32: return mlp_backward<C::NDES, 32>(m, nl, st);
+        case 64: return mlp_backward<C::NDES, 64>(m, nl, st);
+        default: return mlp_backward<C::NDES, 128>(m, nl, st);
+      }
+    }
+    const bool tf = m->precision == GNEP_PREC_TF32;
+    switch (hidden_pad_tc(m->shape.H)) {
+      case 32: return tf ? mlp_backward_tc<true, C::NDES, 32>(m, nl, st) : mlp_backward_tc<false, C::NDES, 32>(m, nl, st);
+      case 64: return tf ? mlp_backward_tc<true, C::NDES, 64>(m, nl, st) : mlp_backward_tc<false, C::NDES, 64>(m, nl, st);
+      default:
+        return tf ? mlp_backward_tc<true, C::NDES, 112>(m, nl, st) : mlp_backward_tc<false, C::NDES, 112>(m, nl, st);
+    }
+  }
+
   static int descriptors(const StepArgs& A, bool with_mlp) {
     const gnep_model* m = A.m;
     gnep_nlist* nl = A.nl;
@@ -800,13 +841,7 @@ struct Runner {
     stage("desc_angular");
     GNEP_CHECK_LAUNCH("descriptor sweep");
     if (with_mlp) {
-      int rc;
-      switch (hidden_pad(m->shape.H)) {
-        case 32: rc = mlp_forward<C::NDES, 32, C::NS, C::NQR, C::KR>(m, nl, A.st); break;
-        case 64: rc = mlp_forward<C::NDES, 64, C::NS, C::NQR, C::KR>(m, nl, A.st); break;
-        default: rc = mlp_forward<C::NDES, 128, C::NS, C::NQR, C::KR>(m, nl, A.st); break;
-      }
-      if (rc) return rc;
+      if (int rc = network_forward(m, nl, A.st)) return rc;
       stage("mlp_fwd");
     }
     return GNEP_OK;
@@ -848,15 +883,9 @@ struct Runner {
         N, dm, nl->atile[1], nl->type, nl->atom_struct, nl->L[1].off, nl->L[1].owner, nl->L[1].j, nl->L[1].rij, w.a,
         w.Bs, w.S, w.Sd, w.Gd);
     stage("tangent_angular");
-    int rc;
-    switch (hidden_pad(m->shape.H)) {
-      case 32: rc = mlp_backward<C::NDES, 32>(m, nl, A.st); break;
-      case 64: rc = mlp_backward<C::NDES, 64>(m, nl, A.st); break;
-      default: rc = mlp_backward<C::NDES, 128>(m, nl, A.st); break;
-    }
-    if (rc) return rc;
+    if (int rc = network_backward(m, nl, A.st)) return rc;
     stage("mlp_bwd");
-    k_cgrad<C><<<cgrad_blocks(nl->natile[1]), 128, 0, A.st>>>(
+    k_cgrad<C><<<cgrad_blocks(nl), 128, 0, A.st>>>(
         N, nl->natile[1], nl->atile[1], dm, nl->type, nl->atom_struct, nl->L[1].off, nl->L[1].owner, nl->L[1].j,
         nl->L[1].rij, w.a, w.Bs, w.S, w.Sd, w.Gb, w.Ep, w.FR, w.FRd, w.cpart);
     stage("cgrad");
@@ -890,6 +919,12 @@ int setup_shape() {
   int rc = mlp_setup<C::NDES, 32, C::NS, C::NQR, C::KR>();
   if (!rc) rc = mlp_setup<C::NDES, 64, C::NS, C::NQR, C::KR>();
   if (!rc) rc = mlp_setup<C::NDES, 128, C::NS, C::NQR, C::KR>();
+  if (!rc) rc = mlp_setup_tc<false, C::NDES, 32, C::NS, C::NQR, C::KR>();
+  if (!rc) rc = mlp_setup_tc<false, C::NDES, 64, C::NS, C::NQR, C::KR>();
+  if (!rc) rc = mlp_setup_tc<false, C::NDES, 112, C::NS, C::NQR, C::KR>();
+  if (!rc) rc = mlp_setup_tc<true, C::NDES, 32, C::NS, C::NQR, C::KR>();
+  if (!rc) rc = mlp_setup_tc<true, C::NDES, 64, C::NS, C::NQR, C::KR>();
+  if (!rc) rc = mlp_setup_tc<true, C::NDES, 112, C::NS, C::NQR, C::KR>();
   return rc;
 }
 }  // namespace
@@ -930,7 +965,14 @@ int run_backward(const StepArgs& A) {
   return set_error(GNEP_ERR_UNSUPPORTED, "no kernel for this shape");
 }
 
-int cgrad_blocks(int ntiles) { return ntiles < kCgBlocks ? (ntiles > 0 ? ntiles : 1) : kCgBlocks; }
+// Persistent blocks of the c-gradient sweep: one per tile up to the default
+// (or tuned) count, at most kCgBlocksMax (the size of the partial buffer).
+int cgrad_blocks(const gnep_nlist* nl) {
+  const int ntiles = nl->natile[1];
+  int cap = nl->tune.cg_blocks > 0 ? nl->tune.cg_blocks : kCgBlocks;
+  if (cap > kCgBlocksMax) cap = kCgBlocksMax;
+  return ntiles < cap ? (ntiles > 0 ? ntiles : 1) : cap;
+}
 
 // Tile limits of the angular sweeps: [0] descriptor sweep (kNptDesc channels
 // per thread, kChDesc pairs), [1] force, tangent and c-gradient sweeps (one

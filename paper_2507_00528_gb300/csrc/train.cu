@@ -284,9 +284,8 @@ int run_loss_impl(const gnep_model* m, gnep_nlist* nl, const double* le, const f
 int run_grad_reduce_impl(const gnep_model* m, gnep_nlist* nl, double lambda_l2, cudaStream_t st) {
   const DevModel dm = m->dev();
   const int ns = m->shape.ns;
-  const Tiles T = make_tiles(nl, ns);
-  const int nb_net = T.tbase[ns] < kNetBlocks ? T.tbase[ns] : kNetBlocks;
-  const int nb_cg = nl->n_atoms > 0 ? cgrad_blocks(nl->natile[1]) : 0;
+  const int nb_net = nl->ws.net_blocks;
+  const int nb_cg = nl->n_atoms > 0 ? cgrad_blocks(nl) : 0;
   k_grad_final<<<blocks_for(m->n_params * 32, 256), 256, 0, st>>>(dm, ns, nb_net, nb_cg, nl->ws.net_part,
                                                                   nl->ws.cpart, 2.0 * lambda_l2 / (double)m->n_params,
                                                                   m->grad);

@@ -127,6 +127,26 @@ class NeighborList:
                                             _stream()))
         return off, j[:n], sh[:n]
 
+    TUNING_KEYS = ("desc_tile_atoms", "desc_tile_pairs", "force_tile_atoms", "force_tile_pairs", "cgrad_blocks")
+
+    def autotune(self, y: "Labels", reps: int = 3, stream=None) -> dict:
+        """Pick the fastest launch shapes of the angular sweeps for this batch
+        (times loss + gradient; invalidates graphs captured on this list)."""
+        yc = y.c()
+        check(_lib.load().gnep_autotune(self.model.h, self.h, C.byref(yc), reps, _stream(stream)))
+        return self.tuning()
+
+    def tuning(self) -> dict:
+        v = np.zeros(5, dtype=np.int32)
+        check(_lib.load().gnep_tuning_get(self.model.h, self.h, v.ctypes.data))
+        return dict(zip(self.TUNING_KEYS, v.tolist()))
+
+    def set_tuning(self, values: dict | None = None, stream=None):
+        """Set launch shapes (missing or 0 = built-in default) and rebuild the tiles."""
+        values = values or {}
+        v = np.array([int(values.get(k, 0)) for k in self.TUNING_KEYS], dtype=np.int32)
+        check(_lib.load().gnep_tuning_set(self.model.h, self.h, v.ctypes.data, _stream(stream)))
+
     def close(self):
         if getattr(self, "h", None):
             _lib.load().gnep_nlist_destroy(self.h)
@@ -214,6 +234,25 @@ class GNEP:
         yc = y.c()
         check(_lib.load().gnep_loss_grad(self.h, nl.h, C.byref(yc), _ptr(terms), _ptr(g), _stream(stream)))
         return terms, g
+
+    def loss(self, nl: NeighborList, y: Labels, stream=None):
+        """Loss terms {L, L_e, L_f, L_v} without the backward pass."""
+        terms = torch.empty(4, dtype=torch.float64, device="cuda")
+        yc = y.c()
+        check(_lib.load().gnep_loss(self.h, nl.h, C.byref(yc), _ptr(terms), _stream(stream)))
+        return terms
+
+    def get_grad(self, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """The model's FP64 gradient (the one adam_step applies)."""
+        if out is None:
+            out = torch.empty(self.n_params, dtype=torch.float64, device="cuda")
+        assert out.dtype == torch.float64 and out.is_contiguous() and out.numel() == self.n_params
+        check(_lib.load().gnep_get_grad(self.h, _ptr(out), self.n_params, _stream(stream)))
+        return out
+
+    def set_grad(self, g: torch.Tensor, stream=None):
+        assert g.dtype == torch.float64 and g.is_contiguous() and g.numel() == self.n_params
+        check(_lib.load().gnep_set_grad(self.h, _ptr(g), self.n_params, _stream(stream)))
 
     # optimiser --------------------------------------------------------------
     def adam_step(self, lr, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0, stream=None):

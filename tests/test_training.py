@@ -1,7 +1,8 @@
-"""Training with the library's own kernels: 100 Adam steps (Eq. 17 schedule)
-on the RMSE + L2 loss move a random student toward a random teacher, and the
-trained network predicts energies better than the method without a network
-(a ridge fit of per-atom energy on the structure-averaged descriptors)."""
+"""Training with the library's own kernels: 300 Adam steps (Eq. 17 schedule)
+on the RMSE + L2 loss move a random student toward a random teacher.  On
+held-out structures the trained network beats the predictors that have no
+network: the best linear fit of per-atom energy on the structure-averaged
+descriptors (ridge, fitted on the training energies), and the zero force."""
 import numpy as np
 import pytest
 import torch
@@ -56,26 +57,27 @@ def test_adam_training_converges_and_beats_no_network_baseline():
     ridge = _ridge_baseline(student, nl_tr, y_tr, train.sizes(), nl_te, y_te, test.sizes())
 
     losses = []
-    steps = 100
-    g = gnep.TrainGraph(student, nl_tr, y_tr, 2e-3, 2e-5, 10, steps)
+    steps = 300
+    g = gnep.TrainGraph(student, nl_tr, y_tr, 5e-3, 5e-5, 10, steps)
     for _ in range(steps):
         g.launch()
         losses.append(g.loss.cpu().numpy()[0])  # ordered after the replay on the current stream
     student.sync_status()
     losses = np.array(losses)
     assert np.all(np.isfinite(losses))
-    # converges toward the teacher: window averages fall and the end is well below the start
-    w = losses.reshape(10, 10).mean(1)
+    # converges toward the teacher: window averages fall and the end is far below the start
+    w = losses.reshape(10, 30).mean(1)
     assert np.sum(np.diff(w) < 0) >= 8, w
-    assert w[-1] < 0.75 * losses[0], (losses[0], w)
+    assert w[-1] < 0.25 * losses[0], (losses[0], w)
 
     rmse_e = _energy_rmse(student, nl_te, y_te, test.sizes())
     _, _, F1, _ = (t.cpu().numpy() for t in student.forward(nl_te))
     Fte = y_te.force.cpu().numpy()
     rmse_f0 = np.sqrt(np.mean((F0 - Fte) ** 2))
     rmse_f1 = np.sqrt(np.mean((F1 - Fte) ** 2))
+    rmse_f_zero = np.sqrt(np.mean(Fte ** 2))
     print(f"energy RMSE test: untrained {rmse_e0:.4g}, ridge on descriptors {ridge:.4g}, trained {rmse_e:.4g}; "
-          f"force RMSE {rmse_f0:.4g} -> {rmse_f1:.4g}; loss {losses[0]:.4g} -> {losses[-1]:.4g}")
-    assert rmse_e < rmse_e0, (rmse_e, rmse_e0)
-    assert rmse_f1 < 0.8 * rmse_f0, (rmse_f1, rmse_f0)
-    assert rmse_e < ridge, (rmse_e, ridge)
+          f"force RMSE: zero {rmse_f_zero:.4g}, untrained {rmse_f0:.4g}, trained {rmse_f1:.4g}; "
+          f"loss {losses[0]:.4g} -> {losses[-1]:.4g}")
+    assert rmse_e < 0.5 * ridge, (rmse_e, ridge)
+    assert rmse_f1 < 0.3 * rmse_f_zero and rmse_f1 < 0.3 * rmse_f0, (rmse_f1, rmse_f_zero, rmse_f0)
