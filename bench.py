@@ -429,6 +429,181 @@ def run_e2e(student, nl, batch, y, args, gnep, torch):
             "includes": "H2D structures+labels (pinned), neighbour rebuild, loss+gradient, Adam, D2H loss"}
 
 
+# ----------------------------------------------------------- workload reports
+#
+# Two further measurements, outside the headline line:
+#   --report precision  the 4,000-structure workload (100-300 atoms, n_max 8/8,
+#                       basis 12/12, 3-body, 100 hidden neurons): E/F/V and
+#                       gradient errors of each network mode against the FP64
+#                       oracle on sampled structures, and training throughput
+#                       of each mode over one pass of 256-structure batches.
+#   --report epoch      the 10,000-structure workload (64-512 atoms, 4-body,
+#                       100 hidden): graph-captured epochs of 256-structure
+#                       batches in FP32 and BF16, with the force and energy
+#                       RMSE on a held-out batch after each epoch.
+
+CFG4_KW = dict(n_max=(8, 8), basis=(12, 12), hidden=100, four_body=False)
+CFG5_KW = dict(n_max=(8, 8), basis=(12, 12), hidden=100, four_body=True)
+
+
+def _chunks_parallel(cfg_id, idx):
+    """Workload chunks from a spawn pool (started before any CUDA use)."""
+    import multiprocessing as mp
+    from paper_2507_00528_gb300 import synth
+    idx = list(idx)
+    workers = max(1, min(len(idx), (os.cpu_count() or 2) - 1, 32))
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return pool.starmap(synth.config_chunk, [(cfg_id, c) for c in idx])
+
+
+def _gpu_ident(torch, dev=0):
+    props = torch.cuda.get_device_properties(dev)
+    uuid = str(getattr(props, "uuid", "") or "")
+    return ("GPU-" + uuid) if uuid and not uuid.startswith("GPU-") else (uuid or str(dev))
+
+
+def report_precision(args):
+    from paper_2507_00528_gb300 import synth
+    t_gen = time.perf_counter()
+    chunks = _chunks_parallel(4, range(synth.n_chunks(4)))
+    t_gen = time.perf_counter() - t_gen
+    import torch
+    import oracle as O
+    from paper_2507_00528_gb300 import build as gbuild
+    gbuild.build()
+    from paper_2507_00528_gb300 import gnep
+    cfg = O.Cfg(nq_r=9, nq_a=9, k_r=13, k_a=13, hidden=100, four_body=False)
+    T = synth.uniform_params(cfg.n_params, 12)
+    P = synth.uniform_params(cfg.n_params, 11)
+    teacher = gnep.GNEP(**CFG4_KW, seed=12)
+    teacher.set_params(torch.from_numpy(T))
+    nls = [teacher.neighbors(gnep.DeviceBatch.from_host(b)) for b in chunks]
+    teacher.compute_scale(nls[0])
+    scale = teacher.get_scale().cpu().numpy()
+    s64, T64, P64 = scale.astype(np.float64), T.astype(np.float64), P.astype(np.float64)
+    # oracle sample: forward on 4 structures, gradient on 2
+    sample_f = chunks[0].subset([0, 1, 2, 3])
+    sample_g = chunks[0].subset([0, 1])
+    t0 = time.perf_counter()
+    ref_f = O.forward(cfg, P64, s64, sample_f)
+    y_g = O.teacher_labels(cfg, T64, s64, sample_g, **LAMBDAS)
+    y_g.force = y_g.force.astype(np.float32).astype(np.float64)
+    _, ref_g = O.loss_grad(cfg, P64, s64, sample_g, y_g)
+    t_oracle = time.perf_counter() - t0
+    student = gnep.GNEP(**CFG4_KW, seed=11)
+    student.set_params(torch.from_numpy(P))
+    student.set_scale(torch.from_numpy(scale))
+    nl_f = student.neighbors(gnep.DeviceBatch.from_host(sample_f))
+    nl_g = student.neighbors(gnep.DeviceBatch.from_host(sample_g))
+    yg = gnep.Labels(torch.tensor(y_g.energy, device="cuda"),
+                     torch.tensor(y_g.force, dtype=torch.float32, device="cuda").contiguous(),
+                     torch.tensor(y_g.virial, device="cuda").contiguous(), **LAMBDAS)
+    rel = lambda a, b: float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+    errors = {}
+    for mode in ("fp32", "tf32", "bf16"):
+        student.set_precision(mode)
+        Ea, Es, F, W = (t.double().cpu().numpy() for t in student.forward(nl_f))
+        _, g = student.loss_grad(nl_g, yg)
+        g = g.double().cpu().numpy()
+        errors[mode] = {"energy_per_atom_rel_l2": rel(Ea, ref_f[0]), "force_rel_rms": rel(F, ref_f[2]),
+                        "virial_rel_rms": rel(W, ref_f[3]), "gradient_rel_l2": rel(g, ref_g),
+                        "gradient_max_abs_over_max": float(np.abs(g - ref_g).max() / np.abs(ref_g).max())}
+    # throughput: one pass over all 256-structure batches per mode, labels from the teacher
+    ys = [teacher.teacher_labels(nl, b.sizes(), **LAMBDAS) for nl, b in zip(nls, chunks)]
+    n_atoms = sum(b.n_atoms for b in chunks)
+    thr, pass_ms = {}, {}
+    clk_all = {}
+    for mode in ("fp32", "tf32", "bf16"):
+        student.set_precision(mode)
+        student.set_params(torch.from_numpy(P))
+        graphs = [gnep.TrainGraph(student, nl, y, 1e-3, 1e-5, len(nls), 4 * len(nls)) for nl, y in zip(nls, ys)]
+        for gr in graphs:  # warm-up pass
+            gr.launch()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(_gpu_ident(torch)) as clk:
+            e0.record()
+            for _ in range(3):
+                for gr in graphs:
+                    gr.launch()
+            e1.record()
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 3
+        pass_ms[mode] = ms
+        thr[mode] = n_atoms / (ms / 1e3)
+        clk_all[mode] = clk.summary()
+        student.sync_status()
+        del graphs
+    line = {"report": "precision", "workload": "sbte_4000_structures_100-300_atoms_nmax8_basis12_lmax4_h100",
+            "n_struct": sum(b.n_struct for b in chunks), "n_atoms": n_atoms, "batches": len(chunks),
+            "errors_vs_fp64_oracle": errors,
+            "oracle_sample": {"forward": f"4 structures ({sample_f.n_atoms} atoms)",
+                              "gradient": f"2 structures ({sample_g.n_atoms} atoms)", "seconds": round(t_oracle, 1)},
+            "train_pass_ms": pass_ms, "atoms_per_s": thr, "clocks": clk_all,
+            "generation_s": round(t_gen, 1), "source_sha": csrc_sha()}
+    print(json.dumps(line), flush=True)
+
+
+def report_epoch(args):
+    from paper_2507_00528_gb300 import synth
+    t_gen = time.perf_counter()
+    chunks = _chunks_parallel(5, range(synth.n_chunks(5)))
+    t_gen = time.perf_counter() - t_gen
+    import torch
+    from paper_2507_00528_gb300 import build as gbuild
+    gbuild.build()
+    from paper_2507_00528_gb300 import gnep
+    teacher = gnep.GNEP(**CFG5_KW, seed=12)
+    t0 = time.perf_counter()
+    nls = [teacher.neighbors(gnep.DeviceBatch.from_host(b)) for b in chunks]
+    torch.cuda.synchronize()
+    t_nl = time.perf_counter() - t0
+    teacher.compute_scale(nls[0])
+    scale = teacher.get_scale()
+    ys = [teacher.teacher_labels(nl, b.sizes(), **LAMBDAS) for nl, b in zip(nls, chunks)]
+    train = list(range(len(chunks) - 1))  # the last batch is held out
+    test = len(chunks) - 1
+    n_train_atoms = sum(chunks[c].n_atoms for c in train)
+    epochs = args.epochs
+    F_test = ys[test].force.double().cpu().numpy()
+    E_test = ys[test].energy.cpu().numpy()
+    sizes_test = chunks[test].sizes()
+    out = {}
+    for mode in ("fp32", "bf16"):
+        student = gnep.GNEP(**CFG5_KW, seed=11, precision=mode)
+        student.set_scale(scale)
+        graphs = [gnep.TrainGraph(student, nls[c], ys[c], 2e-3, 2e-5, len(train), epochs * len(train))
+                  for c in train]
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(epochs)]
+        frmse, ermse = [], []
+        torch.cuda.synchronize()
+        with ClockSampler(_gpu_ident(torch)) as clk:
+            for k in range(epochs):
+                ev[k][0].record()
+                for gr in graphs:
+                    gr.launch()
+                ev[k][1].record()
+                _, Es, F, _ = student.forward(nls[test])
+                frmse.append(float(np.sqrt(np.mean((F.double().cpu().numpy() - F_test) ** 2))))
+                ermse.append(float(np.sqrt(np.mean((Es.cpu().numpy() / sizes_test - E_test) ** 2))))
+            torch.cuda.synchronize()
+        student.sync_status()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        med = statistics.median(ms)
+        out[mode] = {"epoch_ms": [round(x, 3) for x in ms], "epoch_ms_median": med,
+                     "atoms_per_s": n_train_atoms / (med / 1e3),
+                     "force_rmse_test_per_epoch": frmse, "energy_rmse_test_per_epoch": ermse,
+                     "clocks": clk.summary()}
+        del graphs
+    line = {"report": "epoch", "workload": "sbte_10000_structures_64-512_atoms_nmax8_basis12_lmax4_4body_h100",
+            "n_struct": sum(b.n_struct for b in chunks), "n_atoms": sum(b.n_atoms for b in chunks),
+            "batches": len(chunks), "train_batches": len(train), "train_atoms_per_epoch": n_train_atoms,
+            "held_out": f"batch {test} ({chunks[test].n_struct} structures, {chunks[test].n_atoms} atoms)",
+            "epochs": epochs, "lr": "Eq. 17, 2e-3 -> 2e-5, warm-up one epoch", "modes": out,
+            "neighbor_build_s": round(t_nl, 2), "generation_s": round(t_gen, 1), "source_sha": csrc_sha()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -438,10 +613,17 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--report", choices=["precision", "epoch"], default=None,
+                    help="a workload report instead of the headline line")
+    ap.add_argument("--epochs", type=int, default=20)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.report == "precision":
+        report_precision(args)
+    elif args.report == "epoch":
+        report_epoch(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gnep(args)

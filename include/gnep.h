@@ -225,8 +225,11 @@ int gnep_get_grad(gnep_model *m, double *dst, int64_t n, void *stream);
 int gnep_set_grad(gnep_model *m, const double *src, int64_t n, void *stream);
 
 /* Adam update (Kingma & Ba, bias-corrected; AdamW decay if weight_decay > 0)
- * with the model's last gradient.  The update count t lives in device memory
- * and advances by one per call.  lr is used as given. */
+ * with the model's last gradient, in FP32 (parameters and moments are FP32).
+ * The update count t lives in device memory and advances by one per call.  lr
+ * is used as given.  If the last loss was not finite the update is skipped
+ * and t does not advance.  Errors: INVALID_ARG unless 0 < beta1, beta2 < 1
+ * and eps > 0. */
 int gnep_adam_step(gnep_model *m, double lr, double beta1, double beta2,
                    double eps, double weight_decay, void *stream);
 /* Same, with the learning rate of Eq. 17 evaluated on the device from the

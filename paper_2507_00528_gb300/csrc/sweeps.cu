@@ -402,12 +402,15 @@ __global__ void __launch_bounds__(128) k_force_atoms(int N, DevModel dm, const i
 }
 
 // E_s = sum_i E_i and W_s = sum_i w_i in FP64, one block per structure.
+// Per-structure energy and virial (Eqs. 1, 4): each thread sums its few atoms
+// (at most 4 for structures of 512 atoms) in FP32, the 128 thread sums are
+// combined in FP64 by a fixed tree.
 __global__ void __launch_bounds__(128) k_struct_sum(const int* __restrict__ soff, const float* __restrict__ Eatom,
                                                     const float* __restrict__ Wat, double* __restrict__ Es,
                                                     double* __restrict__ Ws) {
   const int s = blockIdx.x;
   const int a0 = soff[s], a1 = soff[s + 1];
-  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
     acc[0] += Eatom[i];
 #pragma unroll
@@ -415,7 +418,7 @@ __global__ void __launch_bounds__(128) k_struct_sum(const int* __restrict__ soff
   }
   __shared__ double sh[7][128];
 #pragma unroll
-  for (int q = 0; q < 7; ++q) sh[q][threadIdx.x] = acc[q];
+  for (int q = 0; q < 7; ++q) sh[q][threadIdx.x] = (double)acc[q];
   __syncthreads();
   for (int o = 64; o > 0; o >>= 1) {
     if (threadIdx.x < o)
@@ -423,10 +426,11 @@ __global__ void __launch_bounds__(128) k_struct_sum(const int* __restrict__ soff
       for (int q = 0; q < 7; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    Es[s] = sh[0][0];
-#pragma unroll
-    for (int q = 0; q < 6; ++q) Ws[6 * s + q] = sh[1 + q][0];
+  if (threadIdx.x < 7) {
+    if (threadIdx.x == 0)
+      Es[s] = sh[0][0];
+    else
+      Ws[6 * s + threadIdx.x - 1] = sh[threadIdx.x][0];
   }
 }
 
@@ -638,7 +642,7 @@ __global__ void __launch_bounds__(128) k_tangent_angular(int N, DevModel dm, con
 // Each tile's per-thread sums are folded into a block accumulator in a fixed
 // order; the block writes cpart[block][c^R..., c^A...] once.
 template <class C>
-__global__ void __launch_bounds__(128) k_cgrad(int N, int ntile, const int* __restrict__ tiles, DevModel dm,
+__global__ void __launch_bounds__(128, 4) k_cgrad(int N, int ntile, const int* __restrict__ tiles, DevModel dm,
                                                const int* __restrict__ type,
                                                const int* __restrict__ atom_struct, const int* __restrict__ off,
                                                const int* __restrict__ own, const int* __restrict__ jj,

@@ -2,55 +2,82 @@
 // (Eqs. 13-16, D1.18-D1.21), Adam with the Eq. 17 schedule, descriptor scale
 // and the species-grouped atom order.  Every cross-atom sum is FP64 in a fixed
 // order, so a step is bit-reproducible.
+#include <cmath>
+
 #include "gnep_internal.h"
 #include "network.cuh"
 
 namespace gnep {
 
-constexpr int kRedBlocks = 512;  // partial sums per loss term
+constexpr int kRedBlocks = 304;  // partial sums per loss term (2 blocks per SM)
 
 namespace {
 
-__device__ __forceinline__ double block_sum(double v, double* sh) {
-  sh[threadIdx.x] = v;
+// Block sums of K values per thread, in a fixed order (xor butterflies within
+// warps, then warps in order); the sums are valid in threads 0..K-1 (thread k
+// holds sum k).  sh holds 32 K doubles.
+template <int K>
+__device__ __forceinline__ double block_sums(double (&v)[K], double* sh) {
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) sh[warp * K + k] = v[k];
   __syncthreads();
-  for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
-    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-    __syncthreads();
-  }
-  const double r = sh[0];
-  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x < K)
+    for (int w = 0; w < nw; ++w) r += sh[w * K + threadIdx.x];
   return r;
 }
 
-// Partial sums of the squared residuals of Eqs. 10-12 (fixed grid, fixed order).
+// Partial sums of the squared residuals of Eqs. 10-12 (fixed grid, fixed
+// order).  The leaves of the reduction (a thread's few terms, then the 32
+// lanes of a warp) are summed in FP32; warps and blocks are combined in FP64.
 __global__ void __launch_bounds__(256) k_loss_partials(int N, int S, const int* __restrict__ soff,
                                                        const double* __restrict__ Es, const double* __restrict__ Ws,
                                                        const float* __restrict__ F, const double* __restrict__ le,
                                                        const float* __restrict__ lf, const double* __restrict__ lv,
                                                        double* __restrict__ red) {
-  __shared__ double sh[256];
-  double se = 0, sf = 0, sv = 0;
+  __shared__ double sh[8][3];
+  float sf = 0.f;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < 3LL * N; q += (int64_t)gridDim.x * blockDim.x) {
-    const double d = (double)F[q] - (double)lf[q];
-    sf += d * d;
+    const float d = F[q] - lf[q];
+    sf = fmaf(d, d, sf);
   }
+  double se = 0.0, sv = 0.0;  // structures: few terms per block, kept in FP64
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S; s += gridDim.x * blockDim.x) {
-    const double ns = soff[s + 1] - soff[s];
-    const double de = Es[s] / ns - le[s];
+    const double inv = 1.0 / (double)(soff[s + 1] - soff[s]);
+    const double de = Es[s] * inv - le[s];
     se += de * de;
     for (int c = 0; c < 6; ++c) {
-      const double dv = Ws[6 * s + c] / ns - lv[6 * s + c];
+      const double dv = Ws[6 * s + c] * inv - lv[6 * s + c];
       sv += dv * dv;
     }
   }
-  se = block_sum(se, sh);
-  sf = block_sum(sf, sh);
-  sv = block_sum(sv, sh);
-  if (threadIdx.x == 0) {
-    red[3 * blockIdx.x] = se;
-    red[3 * blockIdx.x + 1] = sf;
-    red[3 * blockIdx.x + 2] = sv;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sf += __shfl_xor_sync(0xffffffffu, sf, o);
+  const unsigned any_s = __ballot_sync(0xffffffffu, se != 0.0 || sv != 0.0);
+  if (any_s) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      se += __shfl_xor_sync(0xffffffffu, se, o);
+      sv += __shfl_xor_sync(0xffffffffu, sv, o);
+    }
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    sh[w][0] = se;
+    sh[w][1] = (double)sf;
+    sh[w][2] = sv;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double t = 0.0;
+    for (int k = 0; k < 8; ++k) t += sh[k][threadIdx.x];
+    red[3 * blockIdx.x + threadIdx.x] = t;
   }
 }
 
@@ -59,6 +86,7 @@ struct LossArgs {
   double le, lf, lv, l2;
   int form;
   int64_t n_params;
+  double inv_S, inv_3N, inv_6S, inv_np;  // reciprocal normalisers (0 for empty sets), formed on the host
 };
 
 // Loss terms and the scalar weights of the residuals:
@@ -68,23 +96,24 @@ struct LossArgs {
 __global__ void __launch_bounds__(256) k_loss_final(LossArgs a, int nred, const double* __restrict__ red,
                                                     const float* __restrict__ params, double* __restrict__ coef,
                                                     int* __restrict__ err) {
-  __shared__ double sh[256];
-  double se = 0, sf = 0, sv = 0, l2 = 0;
+  __shared__ double sh[32 * 4];
+  __shared__ double tot[4];
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
   for (int b = threadIdx.x; b < nred; b += blockDim.x) {
-    se += red[3 * b];
-    sf += red[3 * b + 1];
-    sv += red[3 * b + 2];
+    v[0] += red[3 * b];
+    v[1] += red[3 * b + 1];
+    v[2] += red[3 * b + 2];
   }
-  for (int64_t q = threadIdx.x; q < a.n_params; q += blockDim.x) l2 += (double)params[q] * params[q];
-  se = block_sum(se, sh);
-  sf = block_sum(sf, sh);
-  sv = block_sum(sv, sh);
-  l2 = block_sum(l2, sh);
+  for (int64_t q = threadIdx.x; q < a.n_params; q += blockDim.x) v[3] += (double)params[q] * params[q];
+  const double r = block_sums<4>(v, sh);
+  if (threadIdx.x < 4) tot[threadIdx.x] = r;
+  __syncthreads();
   if (threadIdx.x != 0) return;
-  const double Le = a.S > 0 ? se / a.S : 0.0;           // Eq. 10
-  const double Lf = a.N > 0 ? sf / (3.0 * a.N) : 0.0;   // Eq. 11
-  const double Lv = a.S > 0 ? sv / (6.0 * a.S) : 0.0;   // Eq. 12
-  const double reg = a.l2 * l2 / (double)a.n_params;
+  const double se = tot[0], sf = tot[1], sv = tot[2], l2 = tot[3];
+  const double Le = se * a.inv_S;   // Eq. 10
+  const double Lf = sf * a.inv_3N;  // Eq. 11
+  const double Lv = sv * a.inv_6S;  // Eq. 12
+  const double reg = a.l2 * l2 * a.inv_np;
   double L, ke = 1, kf = 1, kv = 1;
   if (a.form == GNEP_LOSS_RMSE) {
     L = a.le * sqrt(Le) + a.lf * sqrt(Lf) + a.lv * sqrt(Lv) + reg;
@@ -98,94 +127,110 @@ __global__ void __launch_bounds__(256) k_loss_final(LossArgs a, int nred, const 
   coef[1] = Le;
   coef[2] = Lf;
   coef[3] = Lv;
-  coef[4] = a.N > 0 ? a.lf * kf * 2.0 / (3.0 * a.N) : 0.0;  // Eq. 15
-  coef[5] = a.S > 0 ? a.le * ke * 2.0 / a.S : 0.0;          // Eq. 14
-  coef[6] = a.S > 0 ? a.lv * kv * 2.0 / (6.0 * a.S) : 0.0;  // Eq. 16
+  coef[4] = 2.0 * a.lf * kf * a.inv_3N;  // Eq. 15
+  coef[5] = 2.0 * a.le * ke * a.inv_S;   // Eq. 14
+  coef[6] = 2.0 * a.lv * kv * a.inv_6S;  // Eq. 16
   if (!isfinite(L)) atomicOr(err, kErrNonFinite);
 }
 
-__global__ void k_residual_atoms(int N, const float* __restrict__ F, const float* __restrict__ lf,
-                                 const double* __restrict__ coef, float4* __restrict__ a) {
+// Residual weights of the loss gradient: a_i for atoms i < N, then e_s and
+// B_s (off-diagonals halved) for structures s = i - N (Eqs. 14-16).
+__global__ void k_residuals(int N, int S, const float* __restrict__ F, const float* __restrict__ lf,
+                            const int* __restrict__ soff, const double* __restrict__ Es,
+                            const double* __restrict__ Ws, const double* __restrict__ le,
+                            const double* __restrict__ lv, const double* __restrict__ coef,
+                            float4* __restrict__ a, float* __restrict__ es, float* __restrict__ Bs) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  const float cf = (float)coef[4];
-  a[i] = make_float4(cf * (F[3 * i] - lf[3 * i]), cf * (F[3 * i + 1] - lf[3 * i + 1]),
-                     cf * (F[3 * i + 2] - lf[3 * i + 2]), 0.f);
-}
-
-__global__ void k_residual_struct(int S, const int* __restrict__ soff, const double* __restrict__ Es,
-                                  const double* __restrict__ Ws, const double* __restrict__ le,
-                                  const double* __restrict__ lv, const double* __restrict__ coef,
-                                  float* __restrict__ es, float* __restrict__ Bs) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) {
+    const float cf = (float)coef[4];
+    a[i] = make_float4(cf * (F[3 * i] - lf[3 * i]), cf * (F[3 * i + 1] - lf[3 * i + 1]),
+                       cf * (F[3 * i + 2] - lf[3 * i + 2]), 0.f);
+    return;
+  }
+  const int s = i - N;
   if (s >= S) return;
-  const double ns = soff[s + 1] - soff[s];
-  es[s] = (float)(coef[5] * (Es[s] / ns - le[s]) / ns);
+  const double inv = 1.0 / (double)(soff[s + 1] - soff[s]);
+  es[s] = (float)(coef[5] * (Es[s] * inv - le[s]) * inv);
   for (int c = 0; c < 6; ++c) {
-    const double g = coef[6] * (Ws[6 * s + c] / ns - lv[6 * s + c]) / ns;
+    const double g = coef[6] * (Ws[6 * s + c] * inv - lv[6 * s + c]) * inv;
     Bs[6 * s + c] = (float)(c < 3 ? g : 0.5 * g);
   }
 }
 
 // ---------------------------------------------------------- gradient sums
 
-// grad[q] = sum over block partials (FP64, one warp per parameter, fixed order)
-//           + 2 lambda_l2 theta_q / N_par.
-// Network parameters come from the network backward pass (net_part), the
-// coefficients from the c-gradient sweep (cpart).
+// grad[q] = sum over block partials + 2 lambda_l2 theta_q / N_par, one warp
+// per parameter.  Lane l sums the partials of blocks l, l + 32, ... in FP32
+// (at most a few tens of terms); the 32 lane sums are added in FP64 in lane
+// order.  Network parameters come from the network backward pass (net_part),
+// the coefficients from the c-gradient sweep (cpart).
 __global__ void __launch_bounds__(256) k_grad_final(DevModel dm, int ns, int nb_net, int nb_cg,
                                                     const float* __restrict__ net_part,
                                                     const float* __restrict__ cpart, double l2coef,
                                                     double* __restrict__ grad) {
+  __shared__ double sh[8][32];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (q >= dm.n_params) return;
-  double s = 0.0;
-  if (q < (int64_t)ns * dm.net_size) {
-    const int e = (int)(q / dm.net_size), l = (int)(q % dm.net_size);
-    for (int b = lane; b < nb_net; b += 32) s += (double)net_part[((size_t)b * ns + e) * dm.net_size + l];
-  } else {
-    const int64_t nc = dm.n_params - (int64_t)ns * dm.net_size;
-    const int64_t c = q - dm.off_cR;
-    for (int b = lane; b < nb_cg; b += 32) s += (double)cpart[(size_t)b * nc + c];
+  float s = 0.f;
+  if (q < dm.n_params) {
+    if (q < (int64_t)ns * dm.net_size) {
+      const int e = (int)(q / dm.net_size), l = (int)(q % dm.net_size);
+      for (int b = lane; b < nb_net; b += 32) s += net_part[((size_t)b * ns + e) * dm.net_size + l];
+    } else {
+      const int64_t nc = dm.n_params - (int64_t)ns * dm.net_size;
+      const int64_t c = q - dm.off_cR;
+      for (int b = lane; b < nb_cg; b += 32) s += cpart[(size_t)b * nc + c];
+    }
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) grad[q] = s + l2coef * (double)dm.params[q];
+  sh[w][lane] = (double)s;
+  __syncwarp();
+  if (lane == 0 && q < dm.n_params) {
+    double t = 0.0;
+    for (int k = 0; k < 32; ++k) t += sh[w][k];
+    grad[q] = t + l2coef * (double)dm.params[q];
+  }
 }
 
 // ---------------------------------------------------------- Adam, Eq. 17
 
 struct AdamArgs {
-  double lr, b1, b2, eps, wd;
+  float lr, b1, b2, eps, wd;
+  float lb1, lb2;  // log(beta1), log(beta2), formed on the host in double
   int scheduled;
-  double lr_start, lr_stop;
+  float lr_start, lr_stop;
   long long nw, nt;
 };
 
-__device__ double lr_eq17(const AdamArgs& a, long long s) {
-  if (s < a.nw) return a.lr_stop + (double)s / (double)a.nw * (a.lr_start - a.lr_stop);
+// Eq. 17: linear warm-up from lr_stop to lr_start over nw steps, then a cosine
+// decay back to lr_stop at step nt.
+__device__ float lr_eq17(const AdamArgs& a, long long s) {
+  if (s < a.nw) return a.lr_stop + (float)s / (float)a.nw * (a.lr_start - a.lr_stop);
   if (s > a.nt) s = a.nt;
-  const double span = (double)(a.nt - a.nw);
-  const double frac = span > 0 ? (double)(s - a.nw) / span : 1.0;
-  return a.lr_stop + (a.lr_start - a.lr_stop) * 0.5 * (1.0 + cospi(frac));
+  const long long span = a.nt - a.nw;
+  const float frac = span > 0 ? (float)(s - a.nw) / (float)span : 1.f;
+  return a.lr_stop + (a.lr_start - a.lr_stop) * 0.5f * (1.f + cospif(frac));
 }
 
+// Adam (Kingma-Ba bias correction, optional decoupled weight decay) with the
+// step size of Eq. 17 when scheduled, in FP32 (moments are FP32).  The bias
+// corrections 1 - beta^t are formed as -expm1(t log beta), accurate also when
+// beta^t is close to 1.
 __global__ void k_adam(int64_t n, float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
                        const double* __restrict__ g, const long long* __restrict__ step,
                        const int* __restrict__ err, AdamArgs a) {
-  if (*err & kErrNonFinite) return;  // the step is skipped
-  const long long t = *step + 1;
-  const double lr = a.scheduled ? lr_eq17(a, *step) : a.lr;
-  const double c1 = 1.0 - pow(a.b1, (double)t), c2 = 1.0 - pow(a.b2, (double)t);
+  if (*err & kErrNonFinite) return;  // the step is skipped (uniform over the grid)
+  const long long s = *step;
+  const float tf = (float)(s + 1);
+  const float lr = a.scheduled ? lr_eq17(a, s) : a.lr;
+  const float ic1 = -1.f / expm1f(tf * a.lb1), ic2 = -1.f / expm1f(tf * a.lb2);
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
-    const double gq = g[q];
-    const double mq = a.b1 * m[q] + (1.0 - a.b1) * gq;
-    const double vq = a.b2 * v[q] + (1.0 - a.b2) * gq * gq;
-    m[q] = (float)mq;
-    v[q] = (float)vq;
-    const double upd = (mq / c1) / (sqrt(vq / c2) + a.eps) + a.wd * p[q];
-    p[q] = (float)(p[q] - lr * upd);
+    const float gq = (float)g[q];
+    const float mq = fmaf(a.b1, m[q], (1.f - a.b1) * gq);
+    const float vq = fmaf(a.b2, v[q], (1.f - a.b2) * gq * gq);
+    m[q] = mq;
+    v[q] = vq;
+    const float upd = (mq * ic1) / (sqrtf(vq * ic2) + a.eps) + a.wd * p[q];
+    p[q] = p[q] - lr * upd;
   }
 }
 
@@ -271,12 +316,16 @@ int run_loss_impl(const gnep_model* m, gnep_nlist* nl, const double* le, const f
   LossArgs a;
   a.N = N; a.S = S; a.le = y->lambda_e; a.lf = y->lambda_f; a.lv = y->lambda_v; a.l2 = y->lambda_l2;
   a.form = y->loss_form; a.n_params = m->n_params;
+  a.inv_S = S > 0 ? 1.0 / S : 0.0;
+  a.inv_3N = N > 0 ? 1.0 / (3.0 * N) : 0.0;
+  a.inv_6S = S > 0 ? 1.0 / (6.0 * S) : 0.0;
+  a.inv_np = 1.0 / (double)m->n_params;
   k_loss_final<<<1, 256, 0, st>>>(a, kRedBlocks, w.red, m->params, w.coef, m->err);
   stage("loss_final");
-  if (N > 0) k_residual_atoms<<<blocks_for(N, 256), 256, 0, st>>>(N, w.F, lf, w.coef, w.a);
-  stage("residual_atoms");
-  k_residual_struct<<<blocks_for(S, 128), 128, 0, st>>>(S, nl->struct_off, w.Es, w.Ws, le, lv, w.coef, w.es, w.Bs);
-  stage("residual_struct");
+  if (N + S > 0)
+    k_residuals<<<blocks_for(N + S, 256), 256, 0, st>>>(N, S, w.F, lf, nl->struct_off, w.Es, w.Ws, le, lv, w.coef,
+                                                         w.a, w.es, w.Bs);
+  stage("residuals");
   GNEP_CHECK_LAUNCH("loss");
   return GNEP_OK;
 }
@@ -296,10 +345,13 @@ int run_grad_reduce_impl(const gnep_model* m, gnep_nlist* nl, double lambda_l2, 
 
 int run_adam(gnep_model* m, const double*, double lr, double b1, double b2, double eps, double wd, bool scheduled,
              double lr_start, double lr_stop, int64_t nw, int64_t nt, cudaStream_t st) {
+  if (!(b1 > 0.0 && b1 < 1.0 && b2 > 0.0 && b2 < 1.0 && eps > 0.0))
+    return set_error(GNEP_ERR_INVALID_ARG, "Adam needs 0 < beta1, beta2 < 1 and eps > 0");
   AdamArgs a;
-  a.lr = lr; a.b1 = b1; a.b2 = b2; a.eps = eps; a.wd = wd;
+  a.lr = (float)lr; a.b1 = (float)b1; a.b2 = (float)b2; a.eps = (float)eps; a.wd = (float)wd;
+  a.lb1 = (float)std::log(b1); a.lb2 = (float)std::log(b2);
   a.scheduled = scheduled ? 1 : 0;
-  a.lr_start = lr_start; a.lr_stop = lr_stop; a.nw = nw; a.nt = nt;
+  a.lr_start = (float)lr_start; a.lr_stop = (float)lr_stop; a.nw = nw; a.nt = nt;
   const int nb = blocks_for(m->n_params, 256);
   k_adam<<<nb < 1 ? 1 : nb, 256, 0, st>>>(m->n_params, m->params, m->adam_m, m->adam_v, m->grad, m->step, m->err, a);
   stage("adam");

@@ -208,6 +208,27 @@ def make_config(cfg_id: int, n_struct: int | None = None,
     return make_batch(sizes, phases, rng)
 
 
+def config_chunk(cfg_id: int, chunk: int, chunk_size: int = 256) -> Batch:
+    """Structures chunk*chunk_size .. of workload ``cfg_id`` for per-batch
+    training steps.  Sizes and phases are those of the whole workload (drawn
+    as in make_config); positions come from a generator seeded by (workload,
+    chunk), so chunks can be generated independently and in parallel."""
+    c = CONFIGS[cfg_id]
+    rng = np.random.default_rng(SEED_BASE + cfg_id)
+    total = c["n_struct"]
+    lo, hi = c["size"]
+    sizes = rng.integers(lo, hi + 1, size=total)
+    phases = (np.arange(total) % 3) if c["mix"] else np.zeros(total, dtype=int)
+    s0, s1 = chunk * chunk_size, min(total, (chunk + 1) * chunk_size)
+    if s0 >= s1:
+        raise ValueError(f"workload {cfg_id} has no chunk {chunk}")
+    return make_batch(sizes[s0:s1], phases[s0:s1], np.random.default_rng([SEED_BASE + cfg_id, chunk]))
+
+
+def n_chunks(cfg_id: int, chunk_size: int = 256) -> int:
+    return (CONFIGS[cfg_id]["n_struct"] + chunk_size - 1) // chunk_size
+
+
 def uniform_params(n: int, seed: int, lo: float = -0.5, hi: float = 0.5) -> np.ndarray:
     """Parameter vector with entries U(lo, hi), rounded to float32."""
     rng = np.random.default_rng(seed)
