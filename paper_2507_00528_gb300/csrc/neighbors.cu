@@ -2,11 +2,15 @@
 // over every periodic image n, for the radial (r_c^R) and angular (r_c^A)
 // cut-offs, in canonical order (j ascending, then image shift lexicographic).
 //
-// The accept/reject decision is made in FP64 with explicitly rounded operations
+// The accept/reject decision is that of FP64 with explicitly rounded operations
 // (no fused multiply-add) in the fixed order
 //   s = (na a + nb b) + nc c,  d = (r_j + s) - r_i,  d2 = (dx^2 + dy^2) + dz^2,
 // so the list equals that of any plain FP64 evaluation of the same expression.
-// An FP32 prefilter only discards candidates far outside the larger cut-off.
+// FP64 arithmetic is slow on this GPU, so candidates are first measured in
+// FP32; only those whose FP32 d2 lies within a relative 2e-3 of a cut-off (far
+// above the FP32 error of d2 for coordinates below 10^4 A) take the FP64 test.
+// The stored r_ij is formed in float-float arithmetic (about 44 bits) and
+// rounded to FP32.
 #include <cstdio>
 #include <vector>
 
@@ -28,11 +32,27 @@ __global__ void k_atom_struct(const int* __restrict__ off, int S, int N, int* __
 }
 
 // Images needed per cell direction: floor(rc / w) + 1, w = V / |b x c| etc.
-// tw[s][x] = rc / w_x bounds |df_x + n_x| for any pair within rc.
+// tw[s][x] = rc / w_x bounds |df_x + n_x| for any pair within rc.  Also the
+// inverse cell (FP64) and the cell split into FP32 high and low parts.
 __global__ void k_image_range(const double* __restrict__ cell, int S, double rc, int* __restrict__ kr,
-                              float* __restrict__ tw) {
+                              float* __restrict__ tw, double* __restrict__ hinv, float* __restrict__ hsplit) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= S) return;
+  const double* H = cell + 9 * s;
+  const double det = H[0] * (H[4] * H[8] - H[5] * H[7]) - H[1] * (H[3] * H[8] - H[5] * H[6]) +
+                     H[2] * (H[3] * H[7] - H[4] * H[6]);
+  const double id = 1.0 / det;
+  const double inv[9] = {(H[4] * H[8] - H[5] * H[7]) * id, (H[2] * H[7] - H[1] * H[8]) * id,
+                         (H[1] * H[5] - H[2] * H[4]) * id, (H[5] * H[6] - H[3] * H[8]) * id,
+                         (H[0] * H[8] - H[2] * H[6]) * id, (H[2] * H[3] - H[0] * H[5]) * id,
+                         (H[3] * H[7] - H[4] * H[6]) * id, (H[1] * H[6] - H[0] * H[7]) * id,
+                         (H[0] * H[4] - H[1] * H[3]) * id};
+  for (int q = 0; q < 9; ++q) {
+    hinv[9 * s + q] = inv[q];
+    const float hi = (float)H[q];
+    hsplit[18 * s + q] = hi;
+    hsplit[18 * s + 9 + q] = (float)(H[q] - (double)hi);
+  }
   const double* a = cell + 9 * s;
   const double* b = a + 3;
   const double* c = a + 6;
@@ -47,23 +67,60 @@ __global__ void k_image_range(const double* __restrict__ cell, int S, double rc,
   }
 }
 
-// Fractional coordinates f = r H^-1 (FP32; only used to bound image shifts).
-__global__ void k_fractional(int N, const int* __restrict__ atom_struct, const double* __restrict__ pos,
-                             const double* __restrict__ cell, float4* __restrict__ frac) {
+// Per atom: fractional coordinates f = r H^-1 (FP32; only used to bound image
+// shifts, and checked to lie in [0, 1)), and the position split into FP32
+// high and low parts (w of the high part carries the species).
+__global__ void k_atom_prep(int N, const int* __restrict__ atom_struct, const double* __restrict__ pos,
+                            const int* __restrict__ type, const double* __restrict__ hinv,
+                            float4* __restrict__ frac, float4* __restrict__ phi, float4* __restrict__ plo,
+                            int* __restrict__ err) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  const double* H = cell + 9 * atom_struct[i];
-  const double det = H[0] * (H[4] * H[8] - H[5] * H[7]) - H[1] * (H[3] * H[8] - H[5] * H[6]) +
-                     H[2] * (H[3] * H[7] - H[4] * H[6]);
-  const double inv[9] = {(H[4] * H[8] - H[5] * H[7]) / det, (H[2] * H[7] - H[1] * H[8]) / det,
-                         (H[1] * H[5] - H[2] * H[4]) / det, (H[5] * H[6] - H[3] * H[8]) / det,
-                         (H[0] * H[8] - H[2] * H[6]) / det, (H[2] * H[3] - H[0] * H[5]) / det,
-                         (H[3] * H[7] - H[4] * H[6]) / det, (H[1] * H[6] - H[0] * H[7]) / det,
-                         (H[0] * H[4] - H[1] * H[3]) / det};
+  const double* inv = hinv + 9 * atom_struct[i];
   const double* p = pos + 3 * (size_t)i;
   double f[3];
-  for (int x = 0; x < 3; ++x) f[x] = p[0] * inv[x] + p[1] * inv[3 + x] + p[2] * inv[6 + x];
+  bool wrapped = true;
+  for (int x = 0; x < 3; ++x) {
+    f[x] = p[0] * inv[x] + p[1] * inv[3 + x] + p[2] * inv[6 + x];
+    wrapped = wrapped && f[x] > -1e-9 && f[x] < 1.0 + 1e-9;
+  }
+  if (!wrapped) atomicOr(err, kErrUnwrapped);
   frac[i] = make_float4((float)f[0], (float)f[1], (float)f[2], 0.f);
+  const float hx = (float)p[0], hy = (float)p[1], hz = (float)p[2];
+  phi[i] = make_float4(hx, hy, hz, (float)type[i]);
+  plo[i] = make_float4((float)(p[0] - (double)hx), (float)(p[1] - (double)hy), (float)(p[2] - (double)hz), 0.f);
+}
+
+// Error-free transformations for float-float arithmetic.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = a * b;
+  e = fmaf(a, b, -p);
+}
+
+// r_j + n.H - r_i in float-float (about 44 significant bits), rounded to FP32.
+__device__ __forceinline__ float pair_component(float pjh, float pjl, float pih, float pil, int na, int nb, int nc,
+                                                float ah, float al, float bh, float bl, float ch, float cl) {
+  float h, e, t, u;
+  two_sum(pjh, -pih, h, e);
+  float lo = e + (pjl - pil);
+  two_prod((float)na, ah, t, u);
+  lo += u + (float)na * al;
+  two_sum(h, t, h, e);
+  lo += e;
+  two_prod((float)nb, bh, t, u);
+  lo += u + (float)nb * bl;
+  two_sum(h, t, h, e);
+  lo += e;
+  two_prod((float)nc, ch, t, u);
+  lo += u + (float)nc * cl;
+  two_sum(h, t, h, e);
+  lo += e;
+  return h + lo;
 }
 
 __device__ __forceinline__ double pair_d2_exact(const double* H, const double* pi, const double* pj,
@@ -79,58 +136,44 @@ __device__ __forceinline__ double pair_d2_exact(const double* H, const double* p
 
 struct ListParams {
   double rc2[2];     // exact squared cut-offs (radial, angular)
-  float reject2;     // FP32 prefilter bound above max(rc2)
+  float lo2[2];      // FP32 d2 below: inside (FP32 decision)
+  float hi2[2];      // FP32 d2 above: outside (FP32 decision)
+  float reject2;     // max(hi2): candidates above it are outside both
 };
 
 // One thread per central atom walks every (j, image) of its structure in
-// canonical order.  Pass 0 counts, pass 1 writes.
+// canonical order.  Pass 0 counts, pass 1 writes; both take the same
+// decisions (FP32 away from the cut-offs, FP64 within the band).
 template <bool kFill>
 __global__ void __launch_bounds__(128) k_pairs(
     int N, const int* __restrict__ struct_off, const int* __restrict__ atom_struct,
     const double* __restrict__ pos, const double* __restrict__ cell, const int* __restrict__ krange,
-    const float* __restrict__ tw, const float4* __restrict__ frac,
-    const int* __restrict__ type, ListParams lp, int* __restrict__ cnt0, int* __restrict__ cnt1,
-    const long long* __restrict__ off0, const long long* __restrict__ off1,
+    const float* __restrict__ tw, const float* __restrict__ hsplit, const float4* __restrict__ frac,
+    const float4* __restrict__ phi, const float4* __restrict__ plo, ListParams lp, int* __restrict__ cnt0,
+    int* __restrict__ cnt1, const long long* __restrict__ off0, const long long* __restrict__ off1,
     int* __restrict__ j0, int* __restrict__ own0, float4* __restrict__ r0, char4* __restrict__ sh0,
-    int* __restrict__ j1, int* __restrict__ own1, float4* __restrict__ r1, char4* __restrict__ sh1,
-    int* __restrict__ err) {
+    int* __restrict__ j1, int* __restrict__ own1, float4* __restrict__ r1, char4* __restrict__ sh1) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const int s = atom_struct[i];
   const int a0 = struct_off[s], a1 = struct_off[s + 1];
-  double H[9];
+  float Hh[9], Hl[9];
 #pragma unroll
-  for (int q = 0; q < 9; ++q) H[q] = cell[9 * s + q];
-  float Hf[9];
-#pragma unroll
-  for (int q = 0; q < 9; ++q) Hf[q] = (float)H[q];
-  const double pi[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
-  const float pif[3] = {(float)pi[0], (float)pi[1], (float)pi[2]};
-  const int ka = krange[3 * s], kb = krange[3 * s + 1], kc = krange[3 * s + 2];
-  if (!kFill) {
-    // fractional coordinates must lie in [0, 1) up to rounding
-    const double det = H[0] * (H[4] * H[8] - H[5] * H[7]) - H[1] * (H[3] * H[8] - H[5] * H[6]) +
-                       H[2] * (H[3] * H[7] - H[4] * H[6]);
-    const double inv[9] = {(H[4] * H[8] - H[5] * H[7]) / det, (H[2] * H[7] - H[1] * H[8]) / det,
-                           (H[1] * H[5] - H[2] * H[4]) / det, (H[5] * H[6] - H[3] * H[8]) / det,
-                           (H[0] * H[8] - H[2] * H[6]) / det, (H[2] * H[3] - H[0] * H[5]) / det,
-                           (H[3] * H[7] - H[4] * H[6]) / det, (H[1] * H[6] - H[0] * H[7]) / det,
-                           (H[0] * H[4] - H[1] * H[3]) / det};
-    for (int x = 0; x < 3; ++x) {
-      const double f = pi[0] * inv[x] + pi[1] * inv[3 + x] + pi[2] * inv[6 + x];
-      if (!(f > -1e-9 && f < 1.0 + 1e-9)) atomicOr(err, kErrUnwrapped);
-    }
+  for (int q = 0; q < 9; ++q) {
+    Hh[q] = hsplit[18 * s + q];
+    Hl[q] = hsplit[18 * s + 9 + q];
   }
+  const float4 pih = phi[i], pil = plo[i];
+  const int ka = krange[3 * s], kb = krange[3 * s + 1], kc = krange[3 * s + 2];
   int c0 = 0, c1 = 0;
   long long w0 = kFill ? off0[i] : 0, w1 = kFill ? off1[i] : 0;
   // |r_j + n.H - r_i| >= |df_x + n_x| w_x, so only shifts with |df_x + n_x| < rc / w_x
-  // (with a margin far above FP32 rounding) can pass the exact test below.
+  // (with a margin far above FP32 rounding) can pass the test below.
   const float4 fi = frac[i];
   const float t0 = tw[3 * s] + 1e-3f, t1 = tw[3 * s + 1] + 1e-3f, t2 = tw[3 * s + 2] + 1e-3f;
   for (int j = a0; j < a1; ++j) {
-    const double pj[3] = {pos[3 * j], pos[3 * j + 1], pos[3 * j + 2]};
-    const float dj[3] = {(float)pj[0] - pif[0], (float)pj[1] - pif[1], (float)pj[2] - pif[2]};
-    const int tj = type[j];
+    const float4 pjh = phi[j];
+    const float dj[3] = {pjh.x - pih.x, pjh.y - pih.y, pjh.z - pih.z};
     const float4 fj = frac[j];
     const float dfa = fj.x - fi.x, dfb = fj.y - fi.y, dfc = fj.z - fi.z;
     const int alo = max(-ka, (int)ceilf(-t0 - dfa)), ahi = min(ka, (int)floorf(t0 - dfa));
@@ -140,15 +183,30 @@ __global__ void __launch_bounds__(128) k_pairs(
       for (int nb = blo; nb <= bhi; ++nb)
         for (int nc = clo; nc <= chi; ++nc) {
           if (j == i && na == 0 && nb == 0 && nc == 0) continue;
-          const float fx = dj[0] + ((float)na * Hf[0] + (float)nb * Hf[3] + (float)nc * Hf[6]);
-          const float fy = dj[1] + ((float)na * Hf[1] + (float)nb * Hf[4] + (float)nc * Hf[7]);
-          const float fz = dj[2] + ((float)na * Hf[2] + (float)nb * Hf[5] + (float)nc * Hf[8]);
-          if (fx * fx + fy * fy + fz * fz > lp.reject2) continue;
-          double d[3];
-          const double d2 = pair_d2_exact(H, pi, pj, na, nb, nc, d);
-          const bool in0 = d2 < lp.rc2[0], in1 = d2 < lp.rc2[1];
+          const float fx = dj[0] + ((float)na * Hh[0] + (float)nb * Hh[3] + (float)nc * Hh[6]);
+          const float fy = dj[1] + ((float)na * Hh[1] + (float)nb * Hh[4] + (float)nc * Hh[7]);
+          const float fz = dj[2] + ((float)na * Hh[2] + (float)nb * Hh[5] + (float)nc * Hh[8]);
+          const float d2f = fx * fx + fy * fy + fz * fz;
+          if (d2f > lp.reject2) continue;
+          bool in0 = d2f < lp.lo2[0], in1 = d2f < lp.lo2[1];
+          const bool band0 = !in0 && d2f <= lp.hi2[0], band1 = !in1 && d2f <= lp.hi2[1];
+          if (band0 || band1) {  // near a cut-off: the FP64 decision
+            const double* Hd = cell + 9 * s;
+            const double H[9] = {Hd[0], Hd[1], Hd[2], Hd[3], Hd[4], Hd[5], Hd[6], Hd[7], Hd[8]};
+            const double pi[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
+            const double pj[3] = {pos[3 * j], pos[3 * j + 1], pos[3 * j + 2]};
+            double d[3];
+            const double d2 = pair_d2_exact(H, pi, pj, na, nb, nc, d);
+            if (band0) in0 = d2 < lp.rc2[0];
+            if (band1) in1 = d2 < lp.rc2[1];
+          }
+          if (!in0 && !in1) continue;
           if (kFill) {
-            const float4 rv = make_float4((float)d[0], (float)d[1], (float)d[2], (float)tj);
+            const float4 pjl = plo[j];
+            const float rx = pair_component(pjh.x, pjl.x, pih.x, pil.x, na, nb, nc, Hh[0], Hl[0], Hh[3], Hl[3], Hh[6], Hl[6]);
+            const float ry = pair_component(pjh.y, pjl.y, pih.y, pil.y, na, nb, nc, Hh[1], Hl[1], Hh[4], Hl[4], Hh[7], Hl[7]);
+            const float rz = pair_component(pjh.z, pjl.z, pih.z, pil.z, na, nb, nc, Hh[2], Hl[2], Hh[5], Hl[5], Hh[8], Hl[8]);
+            const float4 rv = make_float4(rx, ry, rz, pjh.w);
             const char4 sv = make_char4((signed char)na, (signed char)nb, (signed char)nc, 0);
             if (in0) { j0[w0] = j; own0[w0] = i; r0[w0] = rv; sh0[w0] = sv; ++w0; }
             if (in1) { j1[w1] = j; own1[w1] = i; r1[w1] = rv; sh1[w1] = sv; ++w1; }
@@ -248,37 +306,44 @@ int build_lists(gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
     for (auto p : tmp) cudaFreeAsync(p, st);
   };
   int *cnt = nullptr, *kr = nullptr;
-  float* tw = nullptr;
-  float4* frac = nullptr;
+  float *tw = nullptr, *hsplit = nullptr;
+  double* hinv = nullptr;
+  float4 *frac = nullptr, *phi = nullptr, *plo = nullptr;
   long long* offs = nullptr;
   GNEP_CUDA(cudaMallocAsync(&cnt, sizeof(int) * 2 * (size_t)(N + 1), st));
   GNEP_CUDA(cudaMallocAsync(&kr, sizeof(int) * 3 * (size_t)S, st));
   GNEP_CUDA(cudaMallocAsync(&offs, sizeof(long long) * 2 * (size_t)(N + 1), st));
   GNEP_CUDA(cudaMallocAsync(&tw, sizeof(float) * 3 * (size_t)S, st));
-  GNEP_CUDA(cudaMallocAsync(&frac, sizeof(float4) * (size_t)N, st));
-  tmp.push_back(cnt);
-  tmp.push_back(kr);
-  tmp.push_back(tw);
-  tmp.push_back(frac);
-  tmp.push_back(offs);
+  GNEP_CUDA(cudaMallocAsync(&hsplit, sizeof(float) * 18 * (size_t)S, st));
+  GNEP_CUDA(cudaMallocAsync(&hinv, sizeof(double) * 9 * (size_t)S, st));
+  GNEP_CUDA(cudaMallocAsync(&frac, sizeof(float4) * 3 * (size_t)N, st));
+  phi = frac + N;
+  plo = frac + 2 * (size_t)N;
+  for (void* p : {(void*)cnt, (void*)kr, (void*)tw, (void*)hsplit, (void*)hinv, (void*)frac, (void*)offs})
+    tmp.push_back(p);
   GNEP_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * 2 * (size_t)(N + 1), st));
 
   k_atom_struct<<<blocks_for(N, 256), 256, 0, st>>>(nl->struct_off, S, N, nl->atom_struct);
   const double rcmax = nl->rcr > nl->rca ? nl->rcr : nl->rca;
-  k_image_range<<<blocks_for(S, 128), 128, 0, st>>>(nl->cell, S, rcmax, kr, tw);
-  k_fractional<<<blocks_for(N, 256), 256, 0, st>>>(N, nl->atom_struct, nl->pos, nl->cell, frac);
+  k_image_range<<<blocks_for(S, 128), 128, 0, st>>>(nl->cell, S, rcmax, kr, tw, hinv, hsplit);
+  k_atom_prep<<<blocks_for(N, 256), 256, 0, st>>>(N, nl->atom_struct, nl->pos, nl->type, hinv, frac, phi, plo,
+                                                   m->err);
   GNEP_CHECK_LAUNCH("k_image_range");
 
   ListParams lp;
   lp.rc2[0] = nl->rcr * nl->rcr;
   lp.rc2[1] = nl->rca * nl->rca;
-  lp.reject2 = (float)(rcmax * rcmax * 1.001 + 0.05);
+  for (int L = 0; L < 2; ++L) {
+    lp.lo2[L] = (float)(lp.rc2[L] * (1.0 - 2e-3));
+    lp.hi2[L] = (float)(lp.rc2[L] * (1.0 + 2e-3));
+  }
+  lp.reject2 = lp.hi2[0] > lp.hi2[1] ? lp.hi2[0] : lp.hi2[1];
 
   int* cnt0 = cnt;
   int* cnt1 = cnt + (N + 1);
   k_pairs<false><<<blocks_for(N, 128), 128, 0, st>>>(
-      N, nl->struct_off, nl->atom_struct, nl->pos, nl->cell, kr, tw, frac, nl->type, lp, cnt0, cnt1, nullptr,
-      nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, m->err);
+      N, nl->struct_off, nl->atom_struct, nl->pos, nl->cell, kr, tw, hsplit, frac, phi, plo, lp, cnt0, cnt1,
+      nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
   GNEP_CHECK_LAUNCH("k_pairs<count>");
 
   long long* off0 = offs;
@@ -321,9 +386,9 @@ int build_lists(gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
     k_to_int<<<blocks_for(N + 1, 256), 256, 0, st>>>(L == 0 ? off0 : off1, N + 1, P.off);
   }
   k_pairs<true><<<blocks_for(N, 128), 128, 0, st>>>(
-      N, nl->struct_off, nl->atom_struct, nl->pos, nl->cell, kr, tw, frac, nl->type, lp, nullptr, nullptr, off0,
-      off1, nl->L[0].j, nl->L[0].owner, nl->L[0].rij, nl->L[0].shift, nl->L[1].j, nl->L[1].owner,
-      nl->L[1].rij, nl->L[1].shift, m->err);
+      N, nl->struct_off, nl->atom_struct, nl->pos, nl->cell, kr, tw, hsplit, frac, phi, plo, lp, nullptr, nullptr,
+      off0, off1, nl->L[0].j, nl->L[0].owner, nl->L[0].rij, nl->L[0].shift, nl->L[1].j, nl->L[1].owner,
+      nl->L[1].rij, nl->L[1].shift);
   GNEP_CHECK_LAUNCH("k_pairs<fill>");
   for (int L = 0; L < 2; ++L) {
     PairList& P = nl->L[L];

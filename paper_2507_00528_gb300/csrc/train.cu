@@ -265,31 +265,60 @@ __global__ void __launch_bounds__(256) k_scale(int N, int ndes, const float* __r
   }
 }
 
-// Stable grouping of atoms by species: perm = atoms of species 0 in order, then 1, ...
-__global__ void __launch_bounds__(1024) k_species_perm(int N, int ns, const int* __restrict__ type,
-                                                       int* __restrict__ perm, int* __restrict__ soff) {
-  __shared__ int sh[1024];
+// Stable grouping of atoms by species: perm = atoms of species 0 in order,
+// then 1, ...  Three steps over blocks of 1024 atoms: per-block species counts;
+// block offsets (one small block, exclusive scan in block order); scatter with
+// ranks inside the block from warp ballots.
+constexpr int kPermBlock = 1024;
+
+__global__ void __launch_bounds__(kPermBlock) k_species_count(int N, int ns, const int* __restrict__ type,
+                                                              int* __restrict__ bcount) {
+  __shared__ int c[8];
+  if (threadIdx.x < 8) c[threadIdx.x] = 0;
+  __syncthreads();
+  const int i = blockIdx.x * kPermBlock + threadIdx.x;
+  const int t = i < N ? type[i] : -1;
+  for (int e = 0; e < ns; ++e) {
+    const unsigned b = __ballot_sync(0xffffffffu, t == e);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(&c[e], __popc(b));  // integer: order-free
+  }
+  __syncthreads();
+  if (threadIdx.x < ns) bcount[(size_t)blockIdx.x * ns + threadIdx.x] = c[threadIdx.x];
+}
+
+// bcount[b][e] -> exclusive offsets boff[b][e] of the grouped order; soff[e] = species starts.
+__global__ void __launch_bounds__(256) k_species_offsets(int nb, int ns, const int* __restrict__ bcount,
+                                                         int* __restrict__ boff, int* __restrict__ soff) {
+  if (threadIdx.x != 0) return;
   int base = 0;
   for (int e = 0; e < ns; ++e) {
-    if (threadIdx.x == 0) soff[e] = base;
-    for (int c = 0; c < N; c += 1024) {
-      const int i = c + threadIdx.x;
-      const int f = (i < N && type[i] == e) ? 1 : 0;
-      sh[threadIdx.x] = f;
-      __syncthreads();
-      for (int o = 1; o < 1024; o <<= 1) {
-        const int t = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
-        __syncthreads();
-        sh[threadIdx.x] += t;
-        __syncthreads();
-      }
-      if (f) perm[base + sh[threadIdx.x] - 1] = i;
-      const int tot = sh[1023];
-      __syncthreads();
-      base += tot;
+    soff[e] = base;
+    for (int b = 0; b < nb; ++b) {
+      boff[(size_t)b * ns + e] = base;
+      base += bcount[(size_t)b * ns + e];
     }
   }
-  if (threadIdx.x == 0) soff[ns] = base;
+  soff[ns] = base;
+}
+
+__global__ void __launch_bounds__(kPermBlock) k_species_scatter(int N, int ns, const int* __restrict__ type,
+                                                                const int* __restrict__ boff, int* __restrict__ perm) {
+  __shared__ int wc[8][kPermBlock / 32];
+  const int i = blockIdx.x * kPermBlock + threadIdx.x;
+  const int t = i < N ? type[i] : -1;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  unsigned mine = 0;
+  for (int e = 0; e < ns; ++e) {
+    const unsigned b = __ballot_sync(0xffffffffu, t == e);
+    if (lane == 0) wc[e][w] = __popc(b);
+    if (t == e) mine = b;
+  }
+  __syncthreads();
+  if (t < 0) return;
+  int r = __popc(mine & lt);
+  for (int k = 0; k < w; ++k) r += wc[t][k];
+  perm[boff[(size_t)blockIdx.x * ns + t] + r] = i;
 }
 
 }  // namespace
@@ -299,8 +328,18 @@ int64_t loss_partial_doubles() { return 3LL * kRedBlocks; }
 int run_species_perm(gnep_nlist* nl, cudaStream_t st) {
   int* soff_dev = nullptr;
   GNEP_CUDA(cudaMallocAsync(&soff_dev, sizeof(int) * 9, st));
-  k_species_perm<<<1, 1024, 0, st>>>(nl->n_atoms, nl->shape.ns, nl->type, nl->perm, soff_dev);
-  GNEP_CHECK_LAUNCH("k_species_perm");
+  const int N = nl->n_atoms, ns = nl->shape.ns, nb = (N + kPermBlock - 1) / kPermBlock;
+  int* tmp = nullptr;
+  GNEP_CUDA(cudaMallocAsync(&tmp, sizeof(int) * 2 * (size_t)(nb > 0 ? nb : 1) * ns, st));
+  if (nb > 0) {
+    k_species_count<<<nb, kPermBlock, 0, st>>>(N, ns, nl->type, tmp);
+    k_species_offsets<<<1, 32, 0, st>>>(nb, ns, tmp, tmp + (size_t)nb * ns, soff_dev);
+    k_species_scatter<<<nb, kPermBlock, 0, st>>>(N, ns, nl->type, tmp + (size_t)nb * ns, nl->perm);
+  } else {
+    GNEP_CUDA(cudaMemsetAsync(soff_dev, 0, sizeof(int) * 9, st));
+  }
+  GNEP_CHECK_LAUNCH("species grouping");
+  GNEP_CUDA(cudaFreeAsync(tmp, st));
   GNEP_CUDA(cudaMemcpyAsync(nl->species_off, soff_dev, sizeof(int) * (nl->shape.ns + 1), cudaMemcpyDeviceToHost, st));
   GNEP_CUDA(cudaFreeAsync(soff_dev, st));
   GNEP_CUDA(cudaStreamSynchronize(st));
