@@ -604,6 +604,63 @@ def report_epoch(args):
     print(json.dumps(line), flush=True)
 
 
+def report_batch_size(args):
+    """Batch-size / epoch-budget study (the paper's experimental axis, on
+    synthetic data): the same student trained for a fixed number of epochs over
+    the 256-structure workload split into batches of B structures, with the
+    Eq. 17 schedule over the whole run; final training loss, held-out force and
+    energy RMSE, and wall time per B."""
+    from paper_2507_00528_gb300 import synth
+    import torch
+    from paper_2507_00528_gb300 import build as gbuild
+    gbuild.build()
+    from paper_2507_00528_gb300 import gnep
+    train = synth.make_config(2)
+    test = synth.make_config(2, seed=20250702 + 7, n_struct=32)
+    teacher = gnep.GNEP(**MODEL_KW, seed=12)
+    nl_all = teacher.neighbors(gnep.DeviceBatch.from_host(train))
+    teacher.compute_scale(nl_all)
+    scale = teacher.get_scale()
+    nl_te = teacher.neighbors(gnep.DeviceBatch.from_host(test))
+    y_te = teacher.teacher_labels(nl_te, test.sizes(), **LAMBDAS)
+    F_te = y_te.force.double().cpu().numpy()
+    E_te = y_te.energy.cpu().numpy()
+    order = np.random.default_rng(5).permutation(train.n_struct)  # fixed batch composition
+    epochs = args.epochs
+    out = {}
+    for B in (1, 4, 16, 64, 256):
+        groups = [order[k:k + B] for k in range(0, train.n_struct, B)]
+        subs = [train.subset(sorted(g)) for g in groups]
+        nls = [teacher.neighbors(gnep.DeviceBatch.from_host(b)) for b in subs]
+        ys = [teacher.teacher_labels(nl, b.sizes(), **LAMBDAS) for nl, b in zip(nls, subs)]
+        student = gnep.GNEP(**MODEL_KW, seed=11, precision=args.precision)
+        student.set_scale(scale)
+        n_steps = epochs * len(nls)
+        graphs = [gnep.TrainGraph(student, nl, y, 2e-3, 2e-5, len(nls), n_steps) for nl, y in zip(nls, ys)]
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(epochs):
+            for gr in graphs:
+                gr.launch()
+        e1.record()
+        torch.cuda.synchronize()
+        student.sync_status()
+        ms = e0.elapsed_time(e1)
+        full = student.loss(nl_all, teacher.teacher_labels(nl_all, train.sizes(), **LAMBDAS)).cpu().numpy()
+        _, Es, F, _ = student.forward(nl_te)
+        out[str(B)] = {"steps": n_steps, "train_ms": round(ms, 2), "ms_per_step": round(ms / n_steps, 4),
+                       "train_loss_full_batch": float(full[0]),
+                       "test_force_rmse": float(np.sqrt(np.mean((F.double().cpu().numpy() - F_te) ** 2))),
+                       "test_energy_rmse": float(np.sqrt(np.mean((Es.cpu().numpy() / test.sizes() - E_te) ** 2)))}
+        del graphs, nls, ys
+    line = {"report": "batch-size", "workload": WORKLOAD["workload"], "epochs": epochs,
+            "precision": args.precision, "lr": "Eq. 17, 2e-3 -> 2e-5, warm-up one epoch",
+            "held_out": f"{test.n_struct} structures ({test.n_atoms} atoms) from another seed",
+            "by_batch_structures": out, "source_sha": csrc_sha()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -613,7 +670,7 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--report", choices=["precision", "epoch"], default=None,
+    ap.add_argument("--report", choices=["precision", "epoch", "batch-size"], default=None,
                     help="a workload report instead of the headline line")
     ap.add_argument("--epochs", type=int, default=20)
     args = ap.parse_args()
@@ -623,6 +680,8 @@ def main():
         report_precision(args)
     elif args.report == "epoch":
         report_epoch(args)
+    elif args.report == "batch-size":
+        report_batch_size(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

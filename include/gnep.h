@@ -181,6 +181,24 @@ int gnep_descriptors_noalloc(gnep_model *m, const gnep_nlist *nl, float *G,
 int gnep_forward(gnep_model *m, const gnep_nlist *nl, float *E_atom,
                  double *E_struct, float *F, double *W_struct, void *stream);
 
+/* One velocity-Verlet step of molecular dynamics (NVE) with the model's
+ * forces (forward-only inference, Eqs. 1 and 3; NEXT use of a trained model
+ * for EOS / RDF-style sampling).  Units A, fs, amu, eV.
+ * pos [n_atoms*3] FP64 and vel [n_atoms*3] FP64 (A/fs): device arrays of this
+ *   list's batch, updated in place; positions are wrapped back into their
+ *   cell after the drift and the neighbour list is rebuilt from them.
+ * inv_mass [n_atoms] FP64 device, 1/amu.
+ * F [n_atoms*3] FP32 device: forces at pos on entry (from gnep_forward) and at
+ *   the new positions on return.
+ * E_struct [n_struct] FP64 (optional, host or device): potential energies at
+ *   the new positions.
+ * The cells stay fixed.  Graphs captured on this list are invalidated (the
+ * lists are rebuilt).  Errors: INVALID_ARG (host arrays, dt <= 0), and those
+ * of gnep_rebuild_neighbors and gnep_forward. */
+int gnep_md_verlet(gnep_model *m, gnep_nlist *nl, double *pos, double *vel,
+                   const double *inv_mass, float *F, double dt,
+                   double *E_struct, void *stream);
+
 /* Loss and exact parameter gradient of one training step (Eqs. 9-16,
  * D1.18-D1.21).  loss_terms [4] = {L, L_e, L_f, L_v} (L_x are Eqs. 10-12, L the
  * weighted total); grad [n_params] (may be NULL: the gradient stays in the

@@ -31,7 +31,7 @@ EXPORTS = [
     "gnep_lr_schedule", "gnep_graph_create", "gnep_graph_launch", "gnep_graph_destroy", "gnep_save",
     "gnep_load", "gnep_sync_status", "gnep_last_error", "gnep_abi_version", "gnep_profile_step",
     "gnep_profile_stage_name", "gnep_descriptors_noalloc", "gnep_loss", "gnep_get_grad", "gnep_set_grad",
-    "gnep_autotune", "gnep_tuning_get", "gnep_tuning_set",
+    "gnep_autotune", "gnep_tuning_get", "gnep_tuning_set", "gnep_md_verlet",
 ]
 
 
@@ -78,6 +78,7 @@ _SIGS = {
     "gnep_get_grad": [_vp, _vp, C.c_int64, _vp],
     "gnep_set_grad": [_vp, _vp, C.c_int64, _vp],
     "gnep_autotune": [_vp, _vp, C.POINTER(Labels), C.c_int, _vp],
+    "gnep_md_verlet": [_vp, _vp, _vp, _vp, _vp, _vp, C.c_double, _vp, _vp],
     "gnep_tuning_get": [_vp, _vp, _vp],
     "gnep_tuning_set": [_vp, _vp, _vp, _vp],
     "gnep_adam_step": [_vp, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, _vp],

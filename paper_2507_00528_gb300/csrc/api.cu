@@ -455,6 +455,26 @@ int gnep_forward(gnep_model* m, const gnep_nlist* nl_, float* E_atom, double* E_
   return copy_out(W_struct, nl->ws.Ws, 48 * S, st);
 }
 
+int gnep_md_verlet(gnep_model* m, gnep_nlist* nl, double* pos, double* vel, const double* inv_mass, float* F,
+                   double dt, double* E_struct, void* stream) {
+  int rc = check_nlist(m, nl);
+  if (rc) return rc;
+  if (nl->n_atoms > 0 && (!is_device_ptr(pos) || !is_device_ptr(vel) || !is_device_ptr(inv_mass) || !is_device_ptr(F)))
+    return set_error(GNEP_ERR_INVALID_ARG, "md: pos, vel, inv_mass and F must be device arrays");
+  if (!(dt > 0.0)) return set_error(GNEP_ERR_INVALID_ARG, "md: dt must be positive");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t N = nl->n_atoms;
+  if ((rc = md_kick_drift(nl, pos, vel, inv_mass, F, dt, st))) return rc;
+  if (N > 0) GNEP_CUDA(cudaMemcpyAsync(nl->pos, pos, 24 * N, cudaMemcpyDeviceToDevice, st));
+  if ((rc = finish_build(m, nl, st))) return rc;  // lists for the new positions
+  StepArgs A{m, nl, st};
+  if ((rc = run_descriptors(A, true))) return rc;
+  if ((rc = run_forward(A))) return rc;
+  if (N > 0) GNEP_CUDA(cudaMemcpyAsync(F, nl->ws.F, 12 * N, cudaMemcpyDeviceToDevice, st));
+  if ((rc = md_kick(nl, vel, inv_mass, F, dt, st))) return rc;
+  return copy_out(E_struct, nl->ws.Es, 8 * (size_t)nl->n_struct, st);
+}
+
 // Labels staged on the device, then descriptors, network, forces and the loss (Eqs. 1-12).
 static int forward_loss(gnep_model* m, gnep_nlist* nl, const gnep_labels* y, cudaStream_t st) {
   if (!y || (nl->n_struct > 0 && (!y->energy || !y->virial)) || (nl->n_atoms > 0 && !y->force))

@@ -158,6 +158,9 @@ int run_backward(const StepArgs& a);
 
 int shape_setup(const Shape& s);
 int run_descriptors_static(const StepArgs& a, float* G);
+int md_kick_drift(const gnep_nlist* nl, double* pos, double* vel, const double* inv_mass, const float* F, double dt,
+                  cudaStream_t st);
+int md_kick(const gnep_nlist* nl, double* vel, const double* inv_mass, const float* F, double dt, cudaStream_t st);
 int cgrad_blocks(const gnep_nlist* nl);
 void angular_tile_limits(const Shape& s, int which, int* na, int* ch);
 constexpr int kCgBlocksMax = 608;
