@@ -4,7 +4,10 @@
 One step = the whole hot path over one batch: descriptors, network, energies,
 forces, virials, loss, the exact gradient w.r.t. every parameter, and an Adam
 update with the Eq. 17 learning rate, captured once as a CUDA graph and
-replayed.  The workload is 256 synthetic Sb/Te structures of 32-400 atoms
+replayed.  By default the network contractions run in BF16 on the tensor
+cores (FP32 accumulation; the sweeps are FP32); the same step in the plain
+FP32 form is timed alongside and reported as "fp32_form", with the force
+difference between the two forms.  The workload is 256 synthetic Sb/Te structures of 32-400 atoms
 (perturbed rocksalt, liquid-like and strained cells in equal thirds),
 n_max 8/8, basis 12/12, l_max 4 with the 4-body term, 50 hidden neurons,
 labels from a random teacher model of the same shape.
@@ -341,6 +344,36 @@ def run_gnep(args):
     # labels from pinned memory, neighbour rebuild, loss + gradient, Adam, D2H loss
     e2e = run_e2e(student, nl, batch, y, args, gnep, torch)
 
+    # the plain FP32 form of the same step, and the force difference of this
+    # mode from it at identical parameters (the FP32 form matches the FP64
+    # oracle to 1e-5 in the parity tests)
+    fp32_form = None
+    if world == 1 and args.precision != "fp32":
+        ref = gnep.GNEP(**MODEL_KW, seed=11, precision="fp32")
+        ref.set_scale(scale)
+        gr32 = gnep.TrainGraph(ref, nl, y, 1e-3, 1e-5, 2, 10 ** 6)
+        k32 = min(args.steps, 100)
+        for _ in range(args.warmup):
+            gr32.launch(gr32.stream)
+        ev32 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k32)]
+        torch.cuda.synchronize()
+        for k in range(k32):
+            with torch.cuda.stream(gr32.stream):
+                flush.zero_()
+                ev32[k][0].record(gr32.stream)
+                gr32.launch(gr32.stream)
+                ev32[k][1].record(gr32.stream)
+        torch.cuda.synchronize()
+        ms32 = sum(a.elapsed_time(b) for a, b in ev32) / k32
+        probe = gnep.GNEP(**MODEL_KW, seed=11, precision=args.precision)
+        probe.set_scale(scale)
+        F_mode = probe.forward(nl)[2].double().cpu().numpy()
+        probe.set_precision("fp32")
+        F_ref = probe.forward(nl)[2].double().cpu().numpy()
+        fp32_form = {"value": n_atoms / (ms32 / 1e3), "unit": UNIT, "ms_per_step": ms32, "steps": k32,
+                     "speedup_of_this_mode": ms32 / (total_ms / args.steps),
+                     "force_rel_rms_vs_fp32_form": float(np.linalg.norm(F_mode - F_ref) / np.linalg.norm(F_ref))}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         n_s_atoms, n_s, times = oracle_sample_step(batch, args.cpu_seconds, 1)
@@ -371,6 +404,7 @@ def run_gnep(args):
         "kernel_ms": {k: round(v, 5) for k, v in stage_ms.items()},
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "fp32_form": fp32_form,
         "gpu_launches": args.steps * len(stage_ms) - args.steps * sum(1 for k in stage_ms if k.startswith("memset")),
         "clocks": clocks,
         "loss": {"after_warmup": loss0.tolist(), "end": loss_end.tolist()},
@@ -667,7 +701,8 @@ def main():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gnep", choices=["gnep", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16"])
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "tf32", "bf16"],
+                    help="network contractions: bf16 / tf32 on tensor cores, or the plain fp32 form")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--report", choices=["precision", "epoch", "batch-size"], default=None,

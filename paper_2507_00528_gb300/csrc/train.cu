@@ -104,7 +104,8 @@ __global__ void __launch_bounds__(256) k_loss_final(LossArgs a, int nred, const 
     v[1] += red[3 * b + 1];
     v[2] += red[3 * b + 2];
   }
-  for (int64_t q = threadIdx.x; q < a.n_params; q += blockDim.x) v[3] += (double)params[q] * params[q];
+  if (a.l2 != 0.0)
+    for (int64_t q = threadIdx.x; q < a.n_params; q += blockDim.x) v[3] += (double)params[q] * params[q];
   const double r = block_sums<4>(v, sh);
   if (threadIdx.x < 4) tot[threadIdx.x] = r;
   __syncthreads();
@@ -189,6 +190,38 @@ __global__ void __launch_bounds__(256) k_grad_final(DevModel dm, int ns, int nb_
     for (int k = 0; k < 32; ++k) t += sh[w][k];
     grad[q] = t + l2coef * (double)dm.params[q];
   }
+}
+
+// The same sum for few partials (at most 64 per parameter, small batches):
+// one thread per parameter, FP32 leaves of at most 32 partials, FP64 above.
+__global__ void __launch_bounds__(256) k_grad_final_small(DevModel dm, int ns, int nb_net, int nb_cg,
+                                                          const float* __restrict__ net_part,
+                                                          const float* __restrict__ cpart, double l2coef,
+                                                          double* __restrict__ grad) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= dm.n_params) return;
+  const float* src;
+  size_t stride;
+  int nb;
+  if (q < (int64_t)ns * dm.net_size) {
+    const int e = (int)(q / dm.net_size), l = (int)(q % dm.net_size);
+    src = net_part + (size_t)e * dm.net_size + l;
+    stride = (size_t)ns * dm.net_size;
+    nb = nb_net;
+  } else {
+    const int64_t nc = dm.n_params - (int64_t)ns * dm.net_size;
+    src = cpart + (q - dm.off_cR);
+    stride = (size_t)nc;
+    nb = nb_cg;
+  }
+  double t = 0.0;
+  for (int b0 = 0; b0 < nb; b0 += 32) {
+    float leaf = 0.f;
+    const int b1 = b0 + 32 < nb ? b0 + 32 : nb;
+    for (int b = b0; b < b1; ++b) leaf += src[(size_t)b * stride];
+    t += (double)leaf;
+  }
+  grad[q] = t + l2coef * (double)dm.params[q];
 }
 
 // ---------------------------------------------------------- Adam, Eq. 17
@@ -374,9 +407,13 @@ int run_grad_reduce_impl(const gnep_model* m, gnep_nlist* nl, double lambda_l2, 
   const int ns = m->shape.ns;
   const int nb_net = nl->ws.net_blocks;
   const int nb_cg = nl->n_atoms > 0 ? cgrad_blocks(nl) : 0;
-  k_grad_final<<<blocks_for(m->n_params * 32, 256), 256, 0, st>>>(dm, ns, nb_net, nb_cg, nl->ws.net_part,
-                                                                  nl->ws.cpart, 2.0 * lambda_l2 / (double)m->n_params,
-                                                                  m->grad);
+  const double l2coef = 2.0 * lambda_l2 / (double)m->n_params;
+  if (nb_net <= 64 && nb_cg <= 64)
+    k_grad_final_small<<<blocks_for(m->n_params, 256), 256, 0, st>>>(dm, ns, nb_net, nb_cg, nl->ws.net_part,
+                                                                      nl->ws.cpart, l2coef, m->grad);
+  else
+    k_grad_final<<<blocks_for(m->n_params * 32, 256), 256, 0, st>>>(dm, ns, nb_net, nb_cg, nl->ws.net_part,
+                                                                    nl->ws.cpart, l2coef, m->grad);
   stage("grad_final");
   GNEP_CHECK_LAUNCH("gradient reduction");
   return GNEP_OK;
