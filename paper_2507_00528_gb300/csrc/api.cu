@@ -74,7 +74,8 @@ int alloc_workspace(gnep_model* m, gnep_nlist* nl) {
   free_workspace(nl);
   const Shape& s = m->shape;
   const size_t N = nl->n_atoms > 0 ? nl->n_atoms : 1, S = nl->n_struct;
-  const size_t PR = nl->L[0].n > 0 ? nl->L[0].n : 1, PA = nl->L[1].n > 0 ? nl->L[1].n : 1;
+  // pair-sized buffers get headroom so that rebuilds with a few more pairs (MD) do not reallocate
+  const size_t PR = nl->L[0].n + nl->L[0].n / 8 + 64, PA = nl->L[1].n + nl->L[1].n / 8 + 64;
   const size_t D = s.ndes, A24 = (size_t)s.nqa * 24, FRn = (size_t)s.ns * s.kr;
   const size_t HPad = (size_t)hidden_pad(s.H);  // row pitch of the hidden activations
   struct Item { void** p; size_t bytes; };
@@ -106,8 +107,8 @@ int alloc_workspace(gnep_model* m, gnep_nlist* nl) {
     off += align256(it.bytes);
   }
   nl->ws_mem = base;
-  nl->ws_pairs[0] = nl->L[0].n;
-  nl->ws_pairs[1] = nl->L[1].n;
+  nl->ws_pairs[0] = (int64_t)PR;
+  nl->ws_pairs[1] = (int64_t)PA;
   return GNEP_OK;
 }
 
@@ -294,9 +295,12 @@ static int build_angular_tiles(gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
       i = j;
     }
     t.push_back(N);
-    cudaFree(nl->atile[which]);
-    nl->atile[which] = nullptr;
-    GNEP_CUDA(cudaMalloc(&nl->atile[which], sizeof(int) * t.size()));
+    if (!nl->atile[which] || nl->atile_cap[which] < (int64_t)t.size()) {  // at most N + 1 bounds
+      cudaFree(nl->atile[which]);
+      nl->atile[which] = nullptr;
+      GNEP_CUDA(cudaMalloc(&nl->atile[which], sizeof(int) * (size_t)(N + 1)));
+      nl->atile_cap[which] = N + 1;
+    }
     GNEP_CUDA(cudaMemcpyAsync(nl->atile[which], t.data(), sizeof(int) * t.size(), cudaMemcpyHostToDevice, st));
     nl->natile[which] = (int)t.size() - 1;
   }

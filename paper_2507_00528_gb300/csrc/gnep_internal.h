@@ -87,6 +87,7 @@ struct gnep_nlist {
   // [0] wide tiles (descriptor sweep), [1] narrow tiles (force, tangent, c-gradient).
   int* atile[2] = {nullptr, nullptr};
   int natile[2] = {0, 0};
+  int64_t atile_cap[2] = {0, 0};  // allocated tile-bound slots
   // Launch shapes chosen by gnep_autotune (0 = built-in default): atoms and
   // pairs per tile of each tile set, persistent blocks of the c-gradient sweep.
   struct Tuning {

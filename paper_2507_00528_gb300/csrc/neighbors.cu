@@ -373,7 +373,7 @@ int build_lists(gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
     PairList& P = nl->L[L];
     if (tot[L] > P.cap) {
       cudaFree(P.j); cudaFree(P.owner); cudaFree(P.rev); cudaFree(P.rij); cudaFree(P.shift);
-      const int64_t cap = tot[L] > 0 ? tot[L] : 1;
+      const int64_t cap = tot[L] > 0 ? tot[L] + tot[L] / 8 + 64 : 64;  // headroom for rebuilds (MD)
       GNEP_CUDA(cudaMalloc(&P.j, sizeof(int) * cap));
       GNEP_CUDA(cudaMalloc(&P.owner, sizeof(int) * cap));
       GNEP_CUDA(cudaMalloc(&P.rev, sizeof(int) * cap));

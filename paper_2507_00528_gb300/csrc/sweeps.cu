@@ -541,7 +541,7 @@ __device__ __forceinline__ void angular_geometry(AngGeo<C>& g, int slot, int p, 
 // Angular tangent: Sdot_nlm = sum_j [g_n' (u_hat . u) B_lm + g_n grad B_lm . u],
 // qdot_nl = 2 sum_m C_lm S_nlm Sdot_nlm, qdot4_n = dq4/dS . Sdot.
 template <class C, int NPT>
-__global__ void __launch_bounds__(128, 3) k_tangent_angular(int N, DevModel dm, const int* __restrict__ tiles,
+__global__ void __launch_bounds__(128) k_tangent_angular(int N, DevModel dm, const int* __restrict__ tiles,
                                                          const int* __restrict__ type,
                                                          const int* __restrict__ atom_struct, const int* __restrict__ off,
                                                          const int* __restrict__ own, const int* __restrict__ jj,
@@ -785,7 +785,7 @@ namespace {
 
 constexpr int kNptDesc = 2;     // channels per thread, descriptor sweep
 constexpr int kChDesc = 256;    // pairs per geometry chunk, descriptor sweep
-constexpr int kNptTangent = 2;  // channels per thread, tangent sweep (descriptor tiles)
+constexpr int kNptTangent = 1;  // channels per thread, tangent sweep
 
 template <class C>
 struct Runner {
@@ -883,8 +883,8 @@ struct Runner {
     k_tangent_radial<C><<<blocks_for((int64_t)N * RL, 128), 128, 0, A.st>>>(
         N, dm, nl->type, nl->atom_struct, nl->L[0].off, nl->L[0].j, nl->L[0].rij, w.a, w.Bs, w.FRd, w.Gd);
     stage("tangent_radial");
-    k_tangent_angular<C, kNptTangent><<<nl->natile[0], 128, 0, A.st>>>(
-        N, dm, nl->atile[0], nl->type, nl->atom_struct, nl->L[1].off, nl->L[1].owner, nl->L[1].j, nl->L[1].rij, w.a,
+    k_tangent_angular<C, kNptTangent><<<nl->natile[1], 128, 0, A.st>>>(
+        N, dm, nl->atile[1], nl->type, nl->atom_struct, nl->L[1].off, nl->L[1].owner, nl->L[1].j, nl->L[1].rij, w.a,
         w.Bs, w.S, w.Sd, w.Gd);
     stage("tangent_angular");
     if (int rc = network_backward(m, nl, A.st)) return rc;
