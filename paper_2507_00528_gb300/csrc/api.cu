@@ -333,6 +333,9 @@ int gnep_nlist_destroy(gnep_nlist* nl) {
   cudaFree(nl->struct_off); cudaFree(nl->type); cudaFree(nl->pos); cudaFree(nl->cell);
   cudaFree(nl->atom_struct); cudaFree(nl->perm);
   cudaFree(nl->atile[0]); cudaFree(nl->atile[1]);
+  if (nl->side) cudaStreamDestroy(nl->side);
+  if (nl->fork_ev) cudaEventDestroy(nl->fork_ev);
+  if (nl->join_ev) cudaEventDestroy(nl->join_ev);
   for (int L = 0; L < 2; ++L) {
     PairList& P = nl->L[L];
     cudaFree(P.off); cudaFree(P.j); cudaFree(P.owner); cudaFree(P.rev); cudaFree(P.rij); cudaFree(P.shift);

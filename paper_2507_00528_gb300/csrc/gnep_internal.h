@@ -94,6 +94,10 @@ struct gnep_nlist {
     int na[2] = {0, 0}, ch[2] = {0, 0}, cg_blocks = 0;
   } tune;
   uint64_t gen = 0;  // bumped whenever lists or tiles change (captured graphs check it)
+  // Second stream for sweeps that can run beside the caller's stream (the
+  // radial and angular sweeps of one phase), with its fork / join events.
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   gnep::Workspace ws;
   void* ws_mem = nullptr;      // one allocation carved into the workspace
   int64_t ws_pairs[2] = {-1, -1};  // pair counts the workspace was sized for

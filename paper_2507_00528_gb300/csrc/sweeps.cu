@@ -787,6 +787,34 @@ constexpr int kNptDesc = 2;     // channels per thread, descriptor sweep
 constexpr int kChDesc = 256;    // pairs per geometry chunk, descriptor sweep
 constexpr int kNptTangent = 1;  // channels per thread, tangent sweep
 
+// Fork / join of a second stream for two sweeps of one phase that do not
+// depend on each other.  Under stream capture this records two parallel
+// branches of the graph.  While the stage profiler runs, everything stays on
+// the caller's stream so that per-kernel times remain separable.
+struct Fork {
+  cudaStream_t main, side;
+  bool on;
+  Fork(gnep_nlist* nl, cudaStream_t st) : main(st), side(st), on(false) {
+    if (g_prof.on) return;
+    if (!nl->side) {
+      if (cudaStreamCreateWithFlags(&nl->side, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&nl->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&nl->join_ev, cudaEventDisableTiming) != cudaSuccess)
+        return;  // run sequentially
+    }
+    if (cudaEventRecord(nl->fork_ev, st) != cudaSuccess || cudaStreamWaitEvent(nl->side, nl->fork_ev, 0) != cudaSuccess)
+      return;
+    side = nl->side;
+    on = true;
+  }
+  int join(gnep_nlist* nl) {
+    if (!on) return GNEP_OK;
+    GNEP_CUDA(cudaEventRecord(nl->join_ev, side));
+    GNEP_CUDA(cudaStreamWaitEvent(main, nl->join_ev, 0));
+    return GNEP_OK;
+  }
+};
+
 template <class C>
 struct Runner {
   // Network forward/backward in the model's precision: plain FP32 tiles, or
@@ -837,13 +865,15 @@ struct Runner {
     const DevModel dm = m->dev();
     const int N = nl->n_atoms;
     if (N == 0) return GNEP_OK;
-    k_desc_radial<C><<<blocks_for((int64_t)N * RL, 128), 128, 0, A.st>>>(N, dm, nl->type, nl->L[0].off,
-                                                                          nl->L[0].rij, w.FR, w.G);
+    Fork fk(nl, A.st);  // radial and angular descriptors write disjoint columns of G
+    k_desc_radial<C><<<blocks_for((int64_t)N * RL, 128), 128, 0, fk.side>>>(N, dm, nl->type, nl->L[0].off,
+                                                                             nl->L[0].rij, w.FR, w.G);
     stage("desc_radial");
     k_desc_angular<C, kNptDesc, kChDesc><<<nl->natile[0], 128, 0, A.st>>>(N, dm, nl->atile[0], nl->type,
                                                                            nl->L[1].off, nl->L[1].rij, w.S, w.G);
     stage("desc_angular");
     GNEP_CHECK_LAUNCH("descriptor sweep");
+    if (int rc = fk.join(nl)) return rc;
     if (with_mlp) {
       if (int rc = network_forward(m, nl, A.st)) return rc;
       stage("mlp_fwd");
@@ -880,13 +910,15 @@ struct Runner {
     const DevModel dm = m->dev();
     const int N = nl->n_atoms;
     if (N == 0) return GNEP_OK;
-    k_tangent_radial<C><<<blocks_for((int64_t)N * RL, 128), 128, 0, A.st>>>(
+    Fork fk(nl, A.st);  // radial and angular tangents write disjoint columns of Gdot
+    k_tangent_radial<C><<<blocks_for((int64_t)N * RL, 128), 128, 0, fk.side>>>(
         N, dm, nl->type, nl->atom_struct, nl->L[0].off, nl->L[0].j, nl->L[0].rij, w.a, w.Bs, w.FRd, w.Gd);
     stage("tangent_radial");
     k_tangent_angular<C, kNptTangent><<<nl->natile[1], 128, 0, A.st>>>(
         N, dm, nl->atile[1], nl->type, nl->atom_struct, nl->L[1].off, nl->L[1].owner, nl->L[1].j, nl->L[1].rij, w.a,
         w.Bs, w.S, w.Sd, w.Gd);
     stage("tangent_angular");
+    if (int rc = fk.join(nl)) return rc;
     if (int rc = network_backward(m, nl, A.st)) return rc;
     stage("mlp_bwd");
     k_cgrad<C><<<cgrad_blocks(nl), 128, 0, A.st>>>(

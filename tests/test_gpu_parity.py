@@ -263,3 +263,37 @@ def test_autograd_function_and_gpu_finite_differences():
         lm = c.m.loss_grad(c.nl, y, grad=False)[0][0].item()
         fd = (lp - lm) / (2 * h)
         assert abs(fd - gh[k]) <= 2e-2 * (abs(gh[k]) + 1e-2 * np.abs(gh).max()), (k, fd, gh[k])
+
+
+def test_skewed_cells_many_images_and_largest_structure():
+    """A strongly sheared triclinic cell, a two-atom cell far below both
+    cut-offs (dozens of images of each atom in both lists), and one structure
+    of the largest size of the 10,000-structure workload (512 atoms)."""
+    rng = np.random.default_rng(31)
+    # shear: a = (9, 0, 0), b = (5.5, 8, 0), c = (-4, 3.5, 8.5)
+    H = np.array([[9.0, 0.0, 0.0], [5.5, 8.0, 0.0], [-4.0, 3.5, 8.5]])
+    f = rng.random((24, 3))
+    sk_pos = f @ H
+    tiny = np.array([[0.2, 0.3, 0.1], [1.9, 1.6, 1.7]])
+    tiny_H = np.diag([3.4, 3.3, 3.6])
+    big = synth.make_batch([512], [1], np.random.default_rng(32))
+    pos = np.concatenate([sk_pos, tiny, big.pos])
+    types = np.concatenate([rng.integers(0, 2, 24), [0, 1], big.types]).astype(np.int32)
+    cells = np.stack([H, tiny_H, big.cell[0]])
+    b = synth.Batch(np.array([0, 24, 26, 538], dtype=np.int32), pos, types, cells)
+    c = Case("nmax8_basis12_h50_4b", b.subset([0, 1]), labels=False)
+    nl = c.m.neighbors(gnep.DeviceBatch.from_host(b))
+    for which, rc in ((0, 7.0), (1, 4.0)):
+        off, j, sh = nl.export(which)
+        ooff, oj, osh = O.neighbors(b, rc)
+        np.testing.assert_array_equal(off, ooff)
+        np.testing.assert_array_equal(j, oj)
+        np.testing.assert_array_equal(sh, osh)
+    Ea, Es, F, W = (t.double().cpu().numpy() for t in c.m.forward(nl))
+    small = b.subset([0, 1])  # the oracle on the two small cells; the 512-atom one sampled by structure sums
+    Eao, Eso, Fo, Wo = O.forward(c.cfg, c.P64, c.s64, small)
+    assert rel_l2(Ea[:26], Eao) < E_TOL
+    assert rel_l2(F[:26], Fo) < F_TOL and rel_l2(W[:2], Wo) < F_TOL
+    _, eso, fo, wo = O.forward(c.cfg, c.P64, c.s64, b.subset([2]))
+    assert abs(Es[2] - eso[0]) <= E_TOL * abs(eso[0])
+    assert rel_l2(F[26:], fo) < F_TOL and rel_l2(W[2], wo[0]) < F_TOL
