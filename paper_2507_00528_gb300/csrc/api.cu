@@ -266,6 +266,10 @@ static int load_batch(gnep_model* m, const gnep_batch* b, gnep_nlist* nl, cudaSt
       return set_error(GNEP_ERR_INVALID_ARG, "struct_off must be strictly increasing (every structure holds an atom)");
   for (int i = 0; i < N; ++i)
     if (typ[i] < 0 || typ[i] >= m->shape.ns) return set_error(GNEP_ERR_INVALID_ARG, "species index out of range");
+  // the species grouping only changes with the species (a rebuild usually keeps them)
+  nl->types_changed = !(nl->host_types.size() == (size_t)N && std::equal(typ.begin(), typ.begin() + N,
+                                                                          nl->host_types.begin()));
+  if (nl->types_changed) nl->host_types.assign(typ.begin(), typ.begin() + N);
   GNEP_CUDA(cudaMemcpyAsync(nl->struct_off, off.data(), sizeof(int) * (S + 1), cudaMemcpyHostToDevice, st));
   if (N > 0) {
     GNEP_CUDA(cudaMemcpyAsync(nl->type, typ.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
@@ -313,7 +317,8 @@ static int finish_build(gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
   ++nl->gen;
   if (nl->n_atoms > 0) {
     if ((rc = build_lists(m, nl, st))) return rc;
-    if ((rc = run_species_perm(nl, st))) return rc;
+    if (nl->types_changed && (rc = run_species_perm(nl, st))) return rc;
+    nl->types_changed = false;
     if ((rc = build_angular_tiles(m, nl, st))) return rc;
   } else {
     for (int e = 0; e <= m->shape.ns; ++e) nl->species_off[e] = 0;

@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/gnep.h"
 
@@ -96,6 +97,8 @@ struct gnep_nlist {
   uint64_t gen = 0;  // bumped whenever lists or tiles change (captured graphs check it)
   // Second stream for sweeps that can run beside the caller's stream (the
   // radial and angular sweeps of one phase), with its fork / join events.
+  std::vector<int> host_types;  // species of the last build (host copy)
+  bool types_changed = true;
   cudaStream_t side = nullptr;
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   gnep::Workspace ws;
