@@ -151,6 +151,13 @@ int gnep_create(gnep_model** out, int n_species, const int* species_z, double rc
   m->off_cA = m->off_cR + s.ns * s.ns * s.nqr * s.kr;
   m->n_params = (int64_t)m->off_cA + (int64_t)s.ns * s.ns * s.nqa * s.ka;
   cudaGetDevice(&m->device);
+  {  // keep stream-ordered scratch (neighbour builds) in the pool between builds
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, m->device) == cudaSuccess) {
+      uint64_t keep = 8ull << 30;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+  }
   int rc = shape_setup(s);
   if (rc) { delete m; return rc; }
   const size_t n = (size_t)m->n_params;

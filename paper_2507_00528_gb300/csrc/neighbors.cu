@@ -142,9 +142,19 @@ struct ListParams {
 };
 
 // One thread per central atom walks every (j, image) of its structure in
-// canonical order.  Pass 0 counts, pass 1 writes; both take the same
-// decisions (FP32 away from the cut-offs, FP64 within the band).
-template <bool kFill>
+// canonical order.  kMode 0 counts; kMode 1 writes the CSR lists at the
+// scanned offsets; kMode 2 counts and writes each atom's first cap entries
+// into fixed per-atom slots (one pass; the slots are then compacted).  All
+// modes take the same decisions (FP32 away from the cut-offs, FP64 within the
+// band).
+struct Slots {
+  int cap[2];
+  int* j[2];
+  float4* r[2];
+  char4* sh[2];
+};
+
+template <int kMode>
 __global__ void __launch_bounds__(128) k_pairs(
     int N, const int* __restrict__ struct_off, const int* __restrict__ atom_struct,
     const double* __restrict__ pos, const double* __restrict__ cell, const int* __restrict__ krange,
@@ -152,7 +162,9 @@ __global__ void __launch_bounds__(128) k_pairs(
     const float4* __restrict__ phi, const float4* __restrict__ plo, ListParams lp, int* __restrict__ cnt0,
     int* __restrict__ cnt1, const long long* __restrict__ off0, const long long* __restrict__ off1,
     int* __restrict__ j0, int* __restrict__ own0, float4* __restrict__ r0, char4* __restrict__ sh0,
-    int* __restrict__ j1, int* __restrict__ own1, float4* __restrict__ r1, char4* __restrict__ sh1) {
+    int* __restrict__ j1, int* __restrict__ own1, float4* __restrict__ r1, char4* __restrict__ sh1, Slots sl) {
+  constexpr bool kFill = kMode == 1;
+  constexpr bool kStage = kMode == 2;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const int s = atom_struct[i];
@@ -201,15 +213,28 @@ __global__ void __launch_bounds__(128) k_pairs(
             if (band1) in1 = d2 < lp.rc2[1];
           }
           if (!in0 && !in1) continue;
-          if (kFill) {
+          if (kFill || kStage) {
             const float4 pjl = plo[j];
             const float rx = pair_component(pjh.x, pjl.x, pih.x, pil.x, na, nb, nc, Hh[0], Hl[0], Hh[3], Hl[3], Hh[6], Hl[6]);
             const float ry = pair_component(pjh.y, pjl.y, pih.y, pil.y, na, nb, nc, Hh[1], Hl[1], Hh[4], Hl[4], Hh[7], Hl[7]);
             const float rz = pair_component(pjh.z, pjl.z, pih.z, pil.z, na, nb, nc, Hh[2], Hl[2], Hh[5], Hl[5], Hh[8], Hl[8]);
             const float4 rv = make_float4(rx, ry, rz, pjh.w);
             const char4 sv = make_char4((signed char)na, (signed char)nb, (signed char)nc, 0);
-            if (in0) { j0[w0] = j; own0[w0] = i; r0[w0] = rv; sh0[w0] = sv; ++w0; }
-            if (in1) { j1[w1] = j; own1[w1] = i; r1[w1] = rv; sh1[w1] = sv; ++w1; }
+            if (kFill) {
+              if (in0) { j0[w0] = j; own0[w0] = i; r0[w0] = rv; sh0[w0] = sv; ++w0; }
+              if (in1) { j1[w1] = j; own1[w1] = i; r1[w1] = rv; sh1[w1] = sv; ++w1; }
+            } else {
+              if (in0 && c0 < sl.cap[0]) {
+                const size_t q = (size_t)i * sl.cap[0] + c0;
+                sl.j[0][q] = j; sl.r[0][q] = rv; sl.sh[0][q] = sv;
+              }
+              if (in1 && c1 < sl.cap[1]) {
+                const size_t q = (size_t)i * sl.cap[1] + c1;
+                sl.j[1][q] = j; sl.r[1][q] = rv; sl.sh[1][q] = sv;
+              }
+              c0 += in0;
+              c1 += in1;
+            }
           } else {
             c0 += in0;
             c1 += in1;
@@ -220,6 +245,21 @@ __global__ void __launch_bounds__(128) k_pairs(
     cnt0[i] = c0;
     cnt1[i] = c1;
   }
+}
+
+// Copies the per-atom slots into the CSR lists (thread per atom and slot).
+__global__ void k_compact(int N, int cap, const int* __restrict__ cnt, const long long* __restrict__ off,
+                          const int* __restrict__ sj, const float4* __restrict__ sr, const char4* __restrict__ ssh,
+                          int* __restrict__ j, int* __restrict__ own, float4* __restrict__ r, char4* __restrict__ sh) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= (int64_t)N * cap) return;
+  const int i = (int)(g / cap), c = (int)(g % cap);
+  if (c >= cnt[i]) return;
+  const long long d = off[i] + c;
+  j[d] = sj[g];
+  own[d] = i;
+  r[d] = sr[g];
+  sh[d] = ssh[g];
 }
 
 // Exclusive scan of int counts into int64 offsets: one block per 1024 items,
@@ -246,6 +286,24 @@ __global__ void k_scan_add(long long* __restrict__ out, int64_t n, const long lo
   const int64_t g = (int64_t)blockIdx.x * 1024 + threadIdx.x;
   if (g < n) out[g] += add[blockIdx.x];
 }
+
+// Largest neighbour count per list (integer maxima: order-free).
+__global__ void k_max2(int N, const int* __restrict__ c0, const int* __restrict__ c1, int* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int a = i < N ? c0[i] : 0, b = i < N ? c1[i] : 0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a = max(a, __shfl_xor_sync(0xffffffffu, a, o));
+    b = max(b, __shfl_xor_sync(0xffffffffu, b, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&out[0], a);
+    atomicMax(&out[1], b);
+  }
+}
+
+constexpr int kSlotsRadial = 96;   // per-atom slots of the one-pass build (radial list)
+constexpr int kSlotsAngular = 32;  // (angular list)
 
 __global__ void k_to_int(const long long* __restrict__ in, int64_t n, int* __restrict__ out) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -341,10 +399,32 @@ int build_lists(gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
 
   int* cnt0 = cnt;
   int* cnt1 = cnt + (N + 1);
-  k_pairs<false><<<blocks_for(N, 128), 128, 0, st>>>(
+  // one pass into per-atom slots (cap entries per atom and list); atoms with
+  // more neighbours than that fall back to a second, writing pass
+  Slots sl;
+  sl.cap[0] = kSlotsRadial;
+  sl.cap[1] = kSlotsAngular;
+  {
+    const size_t n0 = (size_t)N * sl.cap[0], n1 = (size_t)N * sl.cap[1];
+    char* slots = nullptr;
+    GNEP_CUDA(cudaMallocAsync(&slots, (n0 + n1) * (sizeof(int) + sizeof(float4) + sizeof(char4)), st));
+    tmp.push_back(slots);
+    sl.r[0] = reinterpret_cast<float4*>(slots);
+    sl.r[1] = sl.r[0] + n0;
+    sl.j[0] = reinterpret_cast<int*>(sl.r[1] + n1);
+    sl.j[1] = sl.j[0] + n0;
+    sl.sh[0] = reinterpret_cast<char4*>(sl.j[1] + n1);
+    sl.sh[1] = sl.sh[0] + n0;
+  }
+  k_pairs<2><<<blocks_for(N, 128), 128, 0, st>>>(
       N, nl->struct_off, nl->atom_struct, nl->pos, nl->cell, kr, tw, hsplit, frac, phi, plo, lp, cnt0, cnt1,
-      nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
-  GNEP_CHECK_LAUNCH("k_pairs<count>");
+      nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, sl);
+  GNEP_CHECK_LAUNCH("k_pairs<stage>");
+  int* maxc = nullptr;
+  GNEP_CUDA(cudaMallocAsync(&maxc, sizeof(int) * 2, st));
+  tmp.push_back(maxc);
+  GNEP_CUDA(cudaMemsetAsync(maxc, 0, sizeof(int) * 2, st));
+  k_max2<<<blocks_for(N, 256), 256, 0, st>>>(N, cnt0, cnt1, maxc);
 
   long long* off0 = offs;
   long long* off1 = offs + (N + 1);
@@ -353,8 +433,10 @@ int build_lists(gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
   rc = scan_rec(nullptr, cnt1, N + 1, off1, tmp, st);
   if (rc) { cleanup(); return rc; }
   long long tot[2];
+  int hmax[2] = {0, 0};
   GNEP_CUDA(cudaMemcpyAsync(&tot[0], off0 + N, sizeof(long long), cudaMemcpyDeviceToHost, st));
   GNEP_CUDA(cudaMemcpyAsync(&tot[1], off1 + N, sizeof(long long), cudaMemcpyDeviceToHost, st));
+  GNEP_CUDA(cudaMemcpyAsync(hmax, maxc, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
   int herr = 0;
   GNEP_CUDA(cudaMemcpyAsync(&herr, m->err, sizeof(int), cudaMemcpyDeviceToHost, st));
   GNEP_CUDA(cudaStreamSynchronize(st));
@@ -385,11 +467,23 @@ int build_lists(gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
     P.n = tot[L];
     k_to_int<<<blocks_for(N + 1, 256), 256, 0, st>>>(L == 0 ? off0 : off1, N + 1, P.off);
   }
-  k_pairs<true><<<blocks_for(N, 128), 128, 0, st>>>(
-      N, nl->struct_off, nl->atom_struct, nl->pos, nl->cell, kr, tw, hsplit, frac, phi, plo, lp, nullptr, nullptr,
-      off0, off1, nl->L[0].j, nl->L[0].owner, nl->L[0].rij, nl->L[0].shift, nl->L[1].j, nl->L[1].owner,
-      nl->L[1].rij, nl->L[1].shift);
-  GNEP_CHECK_LAUNCH("k_pairs<fill>");
+  if (hmax[0] <= sl.cap[0] && hmax[1] <= sl.cap[1]) {
+    for (int L = 0; L < 2; ++L) {
+      PairList& P = nl->L[L];
+      const int64_t nt = (int64_t)N * sl.cap[L];
+      if (nt > 0)
+        k_compact<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(N, sl.cap[L], L == 0 ? cnt0 : cnt1,
+                                                                L == 0 ? off0 : off1, sl.j[L], sl.r[L], sl.sh[L],
+                                                                P.j, P.owner, P.rij, P.shift);
+    }
+    GNEP_CHECK_LAUNCH("k_compact");
+  } else {
+    k_pairs<1><<<blocks_for(N, 128), 128, 0, st>>>(
+        N, nl->struct_off, nl->atom_struct, nl->pos, nl->cell, kr, tw, hsplit, frac, phi, plo, lp, nullptr, nullptr,
+        off0, off1, nl->L[0].j, nl->L[0].owner, nl->L[0].rij, nl->L[0].shift, nl->L[1].j, nl->L[1].owner,
+        nl->L[1].rij, nl->L[1].shift, sl);
+    GNEP_CHECK_LAUNCH("k_pairs<fill>");
+  }
   for (int L = 0; L < 2; ++L) {
     PairList& P = nl->L[L];
     if (P.n > 0)
