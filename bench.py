@@ -205,6 +205,38 @@ def oracle_sample_step(batch, seconds: float, steps: int = 1):
     return sb.n_atoms, len(idx), times
 
 
+def _oracle_structure_step(sb):
+    """Worker: one oracle loss + gradient on the one-structure batch sb;
+    returns (atoms, seconds of the gradient evaluation)."""
+    import oracle as O
+    from paper_2507_00528_gb300 import synth
+    cfg = O.Cfg(nq_r=9, nq_a=9, k_r=13, k_a=13, hidden=50, four_body=True)
+    T = synth.uniform_params(cfg.n_params, 12).astype(np.float64)
+    P = synth.uniform_params(cfg.n_params, 11).astype(np.float64)
+    sc = O.descriptor_scale(cfg, T, sb)
+    y = O.teacher_labels(cfg, T, sc, sb, **LAMBDAS)
+    t0 = time.perf_counter()
+    O.loss_grad(cfg, P, sc, sb, y)
+    return sb.n_atoms, time.perf_counter() - t0
+
+
+def oracle_all_cores(batch):
+    """The oracle on every host core at once (a spawn pool, one structure per
+    process: the smallest structures, one per core).  The evaluations run
+    concurrently, so the sample's wall time is the slowest one; atoms/s is the
+    sample's atoms over that time."""
+    import multiprocessing as mp
+    ncores = os.cpu_count() or 1
+    subs = [batch.subset([int(s)]) for s in np.argsort(batch.sizes())[:ncores]]
+    with mp.get_context("spawn").Pool(ncores) as pool:
+        res = pool.map(_oracle_structure_step, subs, chunksize=1)
+    atoms = sum(r[0] for r in res)
+    wall = max(r[1] for r in res)
+    return {"value": atoms / wall, "unit": UNIT, "cores": ncores, "kind": "oracle",
+            "sample": f"{len(subs)} smallest structures ({atoms} atoms), one per process, loss + explicit-route "
+                      f"gradient, {wall:.1f} s for the slowest"}
+
+
 def run_reference(args):
     from paper_2507_00528_gb300 import synth
     rank = int(os.environ.get("RANK", "0"))
@@ -228,6 +260,7 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": dict(WORKLOAD),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_all_cores": oracle_all_cores(batch),
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -379,7 +412,8 @@ def run_gnep(args):
         n_s_atoms, n_s, times = oracle_sample_step(batch, args.cpu_seconds, 1)
         cpu = {"value": n_s_atoms / times[0], "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{n_s} smallest structures of the workload ({n_s_atoms} atoms), one full step "
-                         f"(FP64 loss + explicit-route gradient + Adam), {times[0]:.1f} s"}
+                         f"(FP64 loss + explicit-route gradient + Adam), {times[0]:.1f} s",
+               "all_cores": oracle_all_cores(batch)}
 
     if rank != 0:
         return

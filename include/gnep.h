@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define GNEP_ABI_VERSION 1
+#define GNEP_ABI_VERSION 2
 
 typedef enum {
   GNEP_OK = 0,
