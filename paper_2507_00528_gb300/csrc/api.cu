@@ -80,7 +80,7 @@ int alloc_workspace(gnep_model* m, gnep_nlist* nl) {
   const size_t HPad = (size_t)hidden_pad(s.H);  // row pitch of the hidden activations
   struct Item { void** p; size_t bytes; };
   Workspace& w = nl->ws;
-  w.red_len = loss_partial_doubles();
+  w.red_len = loss_partial_doubles(nl->n_struct);
   const size_t NC = (size_t)(m->n_params - (int64_t)s.ns * m->net_size);
   std::vector<Item> items = {
       {(void**)&w.G, 4 * N * D},        {(void**)&w.Ep, 4 * N * D},       {(void**)&w.X, 4 * N * HPad},
@@ -172,7 +172,7 @@ int gnep_create(gnep_model** out, int n_species, const int* species_z, double rc
   if ((e = cudaMalloc(&m->adam_v, 4 * n)) != cudaSuccess) return fail(e, "cudaMalloc adam");
   if ((e = cudaMalloc(&m->grad, 8 * n)) != cudaSuccess) return fail(e, "cudaMalloc grad");
   if ((e = cudaMalloc(&m->step, sizeof(long long))) != cudaSuccess) return fail(e, "cudaMalloc step");
-  if ((e = cudaMalloc(&m->err, sizeof(int))) != cudaSuccess) return fail(e, "cudaMalloc err");
+  if ((e = cudaMalloc(&m->err, 2 * sizeof(int))) != cudaSuccess) return fail(e, "cudaMalloc err");
   std::vector<float> h(n);
   uint64_t st = seed;
   for (size_t q = 0; q < n; ++q) h[q] = (float)((double)(splitmix64(st) >> 11) * 0x1.0p-53 - 0.5);
@@ -183,7 +183,7 @@ int gnep_create(gnep_model** out, int n_species, const int* species_z, double rc
   cudaMemset(m->adam_v, 0, 4 * n);
   cudaMemset(m->grad, 0, 8 * n);
   cudaMemset(m->step, 0, sizeof(long long));
-  if ((e = cudaMemset(m->err, 0, sizeof(int))) != cudaSuccess) return fail(e, "init");
+  if ((e = cudaMemset(m->err, 0, 2 * sizeof(int))) != cudaSuccess) return fail(e, "init");
   *out = m;
   return GNEP_OK;
 }
@@ -510,6 +510,7 @@ static int forward_loss(gnep_model* m, gnep_nlist* nl, const gnep_labels* y, cud
   if (!is_device_ptr(lv)) { GNEP_CUDA(cudaMemcpyAsync(w.lab_v, lv, 48 * S, cudaMemcpyDefault, st)); lv = w.lab_v; }
   if (N == 0) lf = w.lab_f;
   StepArgs A{m, nl, st};
+  A.loss_follows = true;
   int rc;
   if ((rc = run_descriptors(A, true))) return rc;
   if ((rc = run_forward(A))) return rc;

@@ -119,7 +119,7 @@ struct gnep_model {
   float* adam_v = nullptr;
   double* grad = nullptr;   // device [n_params]
   long long* step = nullptr;  // device update count
-  int* err = nullptr;       // device error flag
+  int* err = nullptr;       // device error flag, then a block counter of the Adam kernel (err[1])
   gnep::DevModel dev() const {
     gnep::DevModel d;
     d.ns = shape.ns; d.nqr = shape.nqr; d.kr = shape.kr; d.nqa = shape.nqa; d.ka = shape.ka;
@@ -158,6 +158,7 @@ struct StepArgs {
   const gnep_model* m;
   gnep_nlist* nl;
   cudaStream_t st;
+  bool loss_follows = false;  // the loss kernel forms the per-structure sums (fused)
 };
 bool shape_supported(const Shape& s);
 int run_descriptors(const StepArgs& a, bool with_mlp);
@@ -174,7 +175,7 @@ void angular_tile_limits(const Shape& s, int which, int* na, int* ch);
 constexpr int kCgBlocksMax = 608;
 
 // train.cu
-int64_t loss_partial_doubles();
+int64_t loss_partial_doubles(int n_struct);
 int run_loss_impl(const gnep_model* m, gnep_nlist* nl, const double* le, const float* lf, const double* lv,
                   const gnep_labels* y, cudaStream_t st);
 int run_grad_reduce_impl(const gnep_model* m, gnep_nlist* nl, double lambda_l2, cudaStream_t st);

@@ -897,8 +897,10 @@ struct Runner {
         N, dm, nl->type, nl->L[0].off, nl->L[0].j, nl->L[0].rij, w.chat, nl->L[1].off, nl->L[1].rev, nl->L[1].rij,
         w.dA, w.F, w.Wat);
     stage("force_atoms");
-    k_struct_sum<<<nl->n_struct, 128, 0, A.st>>>(nl->struct_off, w.Eatom, w.Wat, w.Es, w.Ws);
-    stage("struct_sum");
+    if (!A.loss_follows) {  // otherwise the loss kernel forms these sums
+      k_struct_sum<<<nl->n_struct, 128, 0, A.st>>>(nl->struct_off, w.Eatom, w.Wat, w.Es, w.Ws);
+      stage("struct_sum");
+    }
     GNEP_CHECK_LAUNCH("force sweep");
     return GNEP_OK;
   }

@@ -9,7 +9,6 @@
 
 namespace gnep {
 
-constexpr int kRedBlocks = 304;  // partial sums per loss term (2 blocks per SM)
 
 namespace {
 
@@ -33,52 +32,53 @@ __device__ __forceinline__ double block_sums(double (&v)[K], double* sh) {
   return r;
 }
 
-// Partial sums of the squared residuals of Eqs. 10-12 (fixed grid, fixed
-// order).  The leaves of the reduction (a thread's few terms, then the 32
-// lanes of a warp) are summed in FP32; warps and blocks are combined in FP64.
-__global__ void __launch_bounds__(256) k_loss_partials(int N, int S, const int* __restrict__ soff,
-                                                       const double* __restrict__ Es, const double* __restrict__ Ws,
-                                                       const float* __restrict__ F, const double* __restrict__ le,
-                                                       const float* __restrict__ lf, const double* __restrict__ lv,
-                                                       double* __restrict__ red) {
-  __shared__ double sh[8][3];
-  float sf = 0.f;
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < 3LL * N; q += (int64_t)gridDim.x * blockDim.x) {
-    const float d = F[q] - lf[q];
-    sf = fmaf(d, d, sf);
-  }
-  double se = 0.0, sv = 0.0;  // structures: few terms per block, kept in FP64
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S; s += gridDim.x * blockDim.x) {
-    const double inv = 1.0 / (double)(soff[s + 1] - soff[s]);
-    const double de = Es[s] * inv - le[s];
-    se += de * de;
-    for (int c = 0; c < 6; ++c) {
-      const double dv = Ws[6 * s + c] * inv - lv[6 * s + c];
-      sv += dv * dv;
+// Per structure s (one block of 128 threads): the sums E_s and W_s (Eqs. 1, 4)
+// and the structure's squared residuals of Eqs. 10-12 (energy, virial, and the
+// force term over its atoms).  Each thread sums its few atoms in FP32; the 128
+// thread sums are combined in FP64 by a fixed tree.
+__global__ void __launch_bounds__(128) k_struct_loss(const int* __restrict__ soff, const float* __restrict__ Eatom,
+                                                     const float* __restrict__ Wat, const float* __restrict__ F,
+                                                     const double* __restrict__ le, const float* __restrict__ lf,
+                                                     const double* __restrict__ lv, double* __restrict__ Es,
+                                                     double* __restrict__ Ws, double* __restrict__ red) {
+  const int s = blockIdx.x;
+  const int a0 = soff[s], a1 = soff[s + 1];
+  float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
+    acc[0] += Eatom[i];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) acc[1 + q] += Wat[6 * (size_t)i + q];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float d = F[3 * (size_t)i + c] - lf[3 * (size_t)i + c];
+      acc[7] = fmaf(d, d, acc[7]);
     }
   }
+  __shared__ double sh[8][128];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) sf += __shfl_xor_sync(0xffffffffu, sf, o);
-  const unsigned any_s = __ballot_sync(0xffffffffu, se != 0.0 || sv != 0.0);
-  if (any_s) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      se += __shfl_xor_sync(0xffffffffu, se, o);
-      sv += __shfl_xor_sync(0xffffffffu, sv, o);
-    }
-  }
-  const int w = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) {
-    sh[w][0] = se;
-    sh[w][1] = (double)sf;
-    sh[w][2] = sv;
-  }
+  for (int q = 0; q < 8; ++q) sh[q][threadIdx.x] = (double)acc[q];
   __syncthreads();
-  if (threadIdx.x < 3) {
-    double t = 0.0;
-    for (int k = 0; k < 8; ++k) t += sh[k][threadIdx.x];
-    red[3 * blockIdx.x + threadIdx.x] = t;
+  for (int o = 64; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + o];
+    __syncthreads();
   }
+  if (threadIdx.x != 0) return;
+  const double inv = 1.0 / (double)(a1 - a0);
+  const double E = sh[0][0];
+  Es[s] = E;
+  const double de = E * inv - le[s];
+  double sv = 0.0;
+  for (int c = 0; c < 6; ++c) {
+    const double w = sh[1 + c][0];
+    Ws[6 * s + c] = w;
+    const double dv = w * inv - lv[6 * s + c];
+    sv += dv * dv;
+  }
+  red[3 * s] = de * de;
+  red[3 * s + 1] = sh[7][0];
+  red[3 * s + 2] = sv;
 }
 
 struct LossArgs {
@@ -249,8 +249,8 @@ __device__ float lr_eq17(const AdamArgs& a, long long s) {
 // corrections 1 - beta^t are formed as -expm1(t log beta), accurate also when
 // beta^t is close to 1.
 __global__ void k_adam(int64_t n, float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
-                       const double* __restrict__ g, const long long* __restrict__ step,
-                       const int* __restrict__ err, AdamArgs a) {
+                       const double* __restrict__ g, long long* __restrict__ step, int* __restrict__ err,
+                       AdamArgs a) {
   if (*err & kErrNonFinite) return;  // the step is skipped (uniform over the grid)
   const long long s = *step;
   const float tf = (float)(s + 1);
@@ -265,10 +265,15 @@ __global__ void k_adam(int64_t n, float* __restrict__ p, float* __restrict__ m, 
     const float upd = (mq * ic1) / (sqrtf(vq * ic2) + a.eps) + a.wd * p[q];
     p[q] = p[q] - lr * upd;
   }
-}
-
-__global__ void k_step_inc(long long* step, const int* err) {
-  if (!(*err & kErrNonFinite)) *step += 1;
+  // the last block to finish advances the update count (every block has read it)
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(err + 1, 1) == (int)gridDim.x - 1) {
+      *step += 1;
+      err[1] = 0;
+    }
+  }
 }
 
 // ---------------------------------------------------------- scale, perm
@@ -356,7 +361,7 @@ __global__ void __launch_bounds__(kPermBlock) k_species_scatter(int N, int ns, c
 
 }  // namespace
 
-int64_t loss_partial_doubles() { return 3LL * kRedBlocks; }
+int64_t loss_partial_doubles(int n_struct) { return 3LL * (n_struct > 0 ? n_struct : 1); }
 
 int run_species_perm(gnep_nlist* nl, cudaStream_t st) {
   int* soff_dev = nullptr;
@@ -383,8 +388,9 @@ int run_loss_impl(const gnep_model* m, gnep_nlist* nl, const double* le, const f
                   const gnep_labels* y, cudaStream_t st) {
   Workspace& w = nl->ws;
   const int N = nl->n_atoms, S = nl->n_struct;
-  k_loss_partials<<<kRedBlocks, 256, 0, st>>>(N, S, nl->struct_off, w.Es, w.Ws, w.F, le, lf, lv, w.red);
-  stage("loss_partials");
+  if (S > 0)
+    k_struct_loss<<<S, 128, 0, st>>>(nl->struct_off, w.Eatom, w.Wat, w.F, le, lf, lv, w.Es, w.Ws, w.red);
+  stage("struct_loss");
   LossArgs a;
   a.N = N; a.S = S; a.le = y->lambda_e; a.lf = y->lambda_f; a.lv = y->lambda_v; a.l2 = y->lambda_l2;
   a.form = y->loss_form; a.n_params = m->n_params;
@@ -392,7 +398,7 @@ int run_loss_impl(const gnep_model* m, gnep_nlist* nl, const double* le, const f
   a.inv_3N = N > 0 ? 1.0 / (3.0 * N) : 0.0;
   a.inv_6S = S > 0 ? 1.0 / (6.0 * S) : 0.0;
   a.inv_np = 1.0 / (double)m->n_params;
-  k_loss_final<<<1, 256, 0, st>>>(a, kRedBlocks, w.red, m->params, w.coef, m->err);
+  k_loss_final<<<1, 256, 0, st>>>(a, S, w.red, m->params, w.coef, m->err);
   stage("loss_final");
   if (N + S > 0)
     k_residuals<<<blocks_for(N + S, 256), 256, 0, st>>>(N, S, w.F, lf, nl->struct_off, w.Es, w.Ws, le, lv, w.coef,
@@ -431,8 +437,6 @@ int run_adam(gnep_model* m, const double*, double lr, double b1, double b2, doub
   const int nb = blocks_for(m->n_params, 256);
   k_adam<<<nb < 1 ? 1 : nb, 256, 0, st>>>(m->n_params, m->params, m->adam_m, m->adam_v, m->grad, m->step, m->err, a);
   stage("adam");
-  k_step_inc<<<1, 1, 0, st>>>(m->step, m->err);
-  stage("step_inc");
   GNEP_CHECK_LAUNCH("adam");
   return GNEP_OK;
 }
