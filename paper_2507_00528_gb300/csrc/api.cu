@@ -89,7 +89,7 @@ int alloc_workspace(gnep_model* m, gnep_nlist* nl) {
       {(void**)&w.Wat, 24 * N},         {(void**)&w.Es, 8 * S},           {(void**)&w.Ws, 48 * S},
       {(void**)&w.a, 16 * N},           {(void**)&w.es, 4 * S},           {(void**)&w.Bs, 24 * S},
       {(void**)&w.Gd, 4 * N * D},       {(void**)&w.Sd, 4 * N * A24},     {(void**)&w.FRd, 4 * N * FRn},
-      {(void**)&w.Gb, 4 * N * D},
+      {(void**)&w.Gb, 4 * N * D},       {(void**)&w.wij, 16 * PA},
       {(void**)&w.net_part, 4 * (size_t)kNetBlocks * s.ns * m->net_size},
       {(void**)&w.cpart, 4 * (size_t)kCgBlocksMax * NC},
       {(void**)&w.red, 8 * (size_t)w.red_len},

@@ -56,6 +56,7 @@ struct Workspace {
   float4* a = nullptr;                 // force residual coefficients a_i
   float *es = nullptr, *Bs = nullptr;  // energy and virial residual coefficients
   float *Gd = nullptr, *Sd = nullptr, *FRd = nullptr, *Gb = nullptr;
+  float4* wij = nullptr;               // per angular pair: tangent direction (a_j - a_i) + B_s r_ij
   float* net_part = nullptr;           // network-gradient partials [blocks][species][net_size]
   float* cpart = nullptr;              // coefficient-gradient partials [blocks][c^R + c^A]
   int net_blocks = 0;                  // blocks that wrote net_part in the last backward pass

@@ -30,6 +30,7 @@
 #include "device_math.cuh"
 #include "gnep_internal.h"
 #include "network.cuh"
+#include "warp_mma.cuh"
 
 namespace gnep {
 
@@ -47,7 +48,7 @@ struct Sh {
 
 constexpr int RL = 4;           // lanes per atom in radial sweeps
 constexpr int CH = 128;         // pairs per geometry chunk
-constexpr int kCgBlocks = kCgBlocksMax;  // persistent blocks of the c-gradient sweep (4 per SM)
+constexpr int kCgBlocks = 2 * 152;  // persistent blocks of the c-gradient sweep (2 per SM of 152)
 
 // Angular thread map: TPA threads per atom, NPT channels per thread.
 template <int NQ, int NPT>
@@ -505,22 +506,37 @@ struct AngGeo {
   int J[CH];
 };
 
+// The same geometry with rows padded for warp-level MMA fragments (c-gradient
+// sweep): B and D rows 8 mod 32 words apart, f and fu rows 4 mod 32, so that the
+// fragment loads of one warp touch 32 different banks.
 template <class C>
-__device__ __forceinline__ void angular_geometry(AngGeo<C>& g, int slot, int p, const DevModel& dm,
-                                                 const int* __restrict__ own, const int* __restrict__ atom_struct,
-                                                 const int* __restrict__ jj, const float4* __restrict__ rij,
-                                                 const float4* __restrict__ a, const float* __restrict__ Bs) {
-  const float4 r = rij[p];
+struct MGeo {
+  static constexpr int SBD = CH + 8, SF = CH + 4;
+  float B[NLM][SBD];
+  float D[NLM][SBD];
+  float f[C::KA][SF];
+  float fu[C::KA][SF];
+  int J[CH];
+};
+
+// Direction of the tangent for pair p: w_ij = (a_j - a_i) + B_s r_ij.
+__device__ __forceinline__ float3 tangent_dir(int p, float4 r, const int* __restrict__ own,
+                                              const int* __restrict__ atom_struct, const int* __restrict__ jj,
+                                              const float4* __restrict__ a, const float* __restrict__ Bs) {
   const int i = own[p];
   const float4 ai = a[i], aj = a[jj[p]];
   const float* b = Bs + 6 * atom_struct[i];
   const float bb[6] = {b[0], b[1], b[2], b[3], b[4], b[5]};
   const float3 br = sym_apply(bb, make_float3(r.x, r.y, r.z));
-  const float wx = aj.x - ai.x + br.x, wy = aj.y - ai.y + br.y, wz = aj.z - ai.z + br.z;
+  return make_float3(aj.x - ai.x + br.x, aj.y - ai.y + br.y, aj.z - ai.z + br.z);
+}
+
+template <class C, class Geo>
+__device__ __forceinline__ void pair_geometry(Geo& g, int slot, float4 r, float3 w, const DevModel& dm) {
   const float rr = sqrtf(r.x * r.x + r.y * r.y + r.z * r.z);
   const float ri = 1.f / rr;
   const float ux = r.x * ri, uy = r.y * ri, uz = r.z * ri;
-  const float ru = ux * wx + uy * wy + uz * wz;
+  const float ru = ux * w.x + uy * w.y + uz * w.z;
   float f[C::KA], fp[C::KA];
   radial_basis_d<C::KA>(rr, dm.rca_inv, f, fp);
 #pragma unroll
@@ -529,7 +545,7 @@ __device__ __forceinline__ void angular_geometry(AngGeo<C>& g, int slot, int p, 
     g.fu[k][slot] = fp[k] * ru;
   }
   float B[NLM], Dd[NLM];
-  harmonics_dir(ux, uy, uz, ri, wx, wy, wz, B, Dd);
+  harmonics_dir(ux, uy, uz, ri, w.x, w.y, w.z, B, Dd);
 #pragma unroll
   for (int q = 0; q < NLM; ++q) {
     g.B[q][slot] = B[q];
@@ -547,7 +563,8 @@ __global__ void __launch_bounds__(128) k_tangent_angular(int N, DevModel dm, con
                                                          const int* __restrict__ own, const int* __restrict__ jj,
                                                          const float4* __restrict__ rij, const float4* __restrict__ a,
                                                          const float* __restrict__ Bs, const float* __restrict__ Sang,
-                                                         float* __restrict__ Sd, float* __restrict__ Gd) {
+                                                         float* __restrict__ Sd, float* __restrict__ Gd,
+                                                         float4* __restrict__ wij) {
   using M = AMap<C::NQA, NPT>;
   __shared__ AngGeo<C> geo;
   const int tid = threadIdx.x;
@@ -573,7 +590,13 @@ __global__ void __launch_bounds__(128) k_tangent_angular(int N, DevModel dm, con
   const int pa0 = ok ? off[i] : 0, pa1 = ok ? off[i + 1] : 0;
   for (int cs = P0; cs < P1; cs += CH) {
     const int ce = min(cs + CH, P1);
-    if (cs + tid < ce) angular_geometry<C>(geo, tid, cs + tid, dm, own, atom_struct, jj, rij, a, Bs);
+    if (cs + tid < ce) {
+      const int p = cs + tid;
+      const float4 r = rij[p];
+      const float3 w = tangent_dir(p, r, own, atom_struct, jj, a, Bs);
+      wij[p] = make_float4(w.x, w.y, w.z, 0.f);  // reused by the c-gradient sweep
+      pair_geometry<C>(geo, tid, r, w, dm);
+    }
     __syncthreads();
     const int q0 = max(pa0, cs), q1 = min(pa1, ce);
     for (int pp = q0; pp < q1; ++pp) {
@@ -633,150 +656,283 @@ __global__ void __launch_bounds__(128) k_tangent_angular(int N, DevModel dm, con
 
 // ------------------------------------------------------------- sweep 4
 
-// dL/dc, one thread per (atom, channel n), persistent blocks over atom tiles.
-//   radial:  dL/dc^R_nk^{IJ} += Gbar_n FR[J][k] - E'_n FRd[J][k]
-//   angular: Sbar_nlm  = Gbar_nl 2C S_nlm - E'_nl 2C Sdot_nlm  (+ 4-body terms)
-//            Sdbar_nlm = -E'_nl 2C S_nlm                        (+ 4-body term)
-//            per pair: P = sum_lm Sbar B + Sdbar D,  R = sum_lm Sdbar B,
-//            dL/dc^A_nk^{IJ} += P f_k + R fu_k.
-// Each tile's per-thread sums are folded into a block accumulator in a fixed
-// order; the block writes cpart[block][c^R..., c^A...] once.
-template <class C>
-__global__ void __launch_bounds__(128, 4) k_cgrad(int N, int ntile, const int* __restrict__ tiles, DevModel dm,
-                                               const int* __restrict__ type,
-                                               const int* __restrict__ atom_struct, const int* __restrict__ off,
-                                               const int* __restrict__ own, const int* __restrict__ jj,
-                                               const float4* __restrict__ rij, const float4* __restrict__ a,
-                                               const float* __restrict__ Bs, const float* __restrict__ Sang,
-                                               const float* __restrict__ Sdd, const float* __restrict__ Gb,
-                                               const float* __restrict__ Ep, const float* __restrict__ FR,
-                                               const float* __restrict__ FRd, float* __restrict__ cpart) {
-  using M = AMap<C::NQ, 1>;
-  constexpr int NCR = C::NCR, NCA = C::NCA;
-  constexpr int RA = C::NS * C::KR, AA = C::NS * C::KA;  // per-thread radial / angular sums
-  // the per-tile sums are only used after the chunk loop: overlay them on the geometry
-  union Smem {
-    AngGeo<C> geo;
-    float tsum[M::NA][C::NQ][RA + AA];
-  };
-  __shared__ Smem smu;
-  AngGeo<C>& geo = smu.geo;
-  auto& tsum = smu.tsum;
-  __shared__ float bacc[NCR + NCA];
-  __shared__ int ttype[M::NA];
-  const int tid = threadIdx.x;
-  const int at = tid / M::TPA, n = tid % M::TPA;
-  for (int q = tid; q < NCR + NCA; q += blockDim.x) bacc[q] = 0.f;
+// dL/dc.  With Sbar and Sdbar the adjoints of S and Sdot of atom i,
+//   Sbar_nlm  = Gbar_nl 2C S_nlm - E'_nl 2C Sdot_nlm  (+ 4-body terms)
+//   Sdbar_nlm = -E'_nl 2C S_nlm                        (+ 4-body term),
+// each angular pair ij contributes
+//   P_n = sum_lm Sbar_nlm B_lm + Sdbar_nlm D_lm,   R_n = sum_lm Sdbar_nlm B_lm,
+//   dL/dc^A_nk^{IJ} += P_n f_k + R_n fu_k,
+// and each atom contributes dL/dc^R_nk^{IJ} += Gbar_n FR[J][k] - E'_n FRd[J][k].
+//
+// Angular part: one warp per atom.  For 8 of the atom's pairs at a time,
+//   [P | R] = [Sbar | Sdbar] [B D; D 0 ... ]  as three products of K = 24:
+//        P = Sbar B + Sdbar D,  R = Sdbar B            (16 x 24) (24 x 8)
+//   acc^{IJ} += P_J F^T + R_J Fu^T                       (16 x 8) (8 x 16)
+// with P_J, R_J the columns of pairs whose neighbour has species J, on the
+// tensor cores (warp_mma.cuh).  The pair columns of the first products are
+// ordered so that their C fragments are, register for register, the A
+// fragments of the second: column g holds pair g/2 + 4 (g mod 2), so the C
+// columns 2t and 2t+1 of a lane are the pairs t and t+4, which are its K rows t
+// and t+4 in the second product.  Accumulators stay in registers over all of a
+// warp's atoms; the block folds its four warps in order and writes
+// cpart[block][c^A] once.
+constexpr int kAS = 2 * NLM + 4;  // row stride of [Sbar | Sdbar] (20 mod 32 words: conflict-free A fragments)
+constexpr int kCgWarps = 8;       // warps 0-3 build the pair geometry while warps 4-7 build the atom rows
 
-  for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
-    const int i0 = tiles[tile], i1 = tiles[tile + 1];
-    const int i = i0 + at;
-    const bool ok = at < M::NA && i < i1;
-    const bool okA = ok && n < C::NQA, okR = ok && n < C::NQR;
-    __syncthreads();
-    if (tid < M::NA) ttype[tid] = (i0 + tid < i1) ? type[i0 + tid] : -1;
-    float accA[C::NS][C::KA];
+template <class C>
+struct CgSmem {
+  static constexpr int NA = 128 / C::NQ;  // atoms per tile, at most (force and tangent tiling)
+  static constexpr int KT = (C::KA + 7) / 8;
+  union {
+    MGeo<C> geo;
+    float red[kCgWarps][C::NS * C::NS * KT * 128];  // per warp: [I][J][kt][lane][4] accumulator registers
+  };
+  float A[NA][C::NQA][kAS];
+  int type[NA];
+  int off[NA + 1];
+};
+
+template <class C, bool SPLIT>
+__global__ void __launch_bounds__(32 * kCgWarps, SPLIT ? 1 : 2)
+    k_cgrad_ang(int ntile, const int* __restrict__ tiles, DevModel dm, const int* __restrict__ type,
+                const int* __restrict__ off, const float4* __restrict__ rij, const float4* __restrict__ wij,
+                const float* __restrict__ Sang, const float* __restrict__ Sdd, const float* __restrict__ Gb,
+                const float* __restrict__ Ep, float* __restrict__ cpart) {
+  using SM = CgSmem<C>;
+  constexpr int NA = SM::NA, KT = SM::KT, NQA = C::NQA, KA = C::KA, NS = C::NS, KS = NLM / 8;
+  static_assert(NLM % 8 == 0 && NLM % 4 == 0 && NQA <= 16 && NA * NQA <= 128 && CH == 128, "fragment shapes");
+  extern __shared__ __align__(16) unsigned char smraw[];
+  SM& sm = *reinterpret_cast<SM*>(smraw);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int pg = (g >> 1) | ((g & 1) << 2);  // pair of B-fragment column g
+  float acc[NS][NS][KT][4];
 #pragma unroll
-    for (int s = 0; s < C::NS; ++s)
+  for (int s = 0; s < NS; ++s)
 #pragma unroll
-      for (int k = 0; k < C::KA; ++k) accA[s][k] = 0.f;
-    float sb[NLM], sdb[NLM];
+    for (int J = 0; J < NS; ++J)
 #pragma unroll
-    for (int q = 0; q < NLM; ++q) sb[q] = sdb[q] = 0.f;
-    if (okA) {
-      const float* S = Sang + ((size_t)i * C::NQA + n) * NLM;
-      const float* Dd = Sdd + ((size_t)i * C::NQA + n) * NLM;
-      const float* gb = Gb + (size_t)i * C::NDES;
-      const float* ep = Ep + (size_t)i * C::NDES;
-      float s[NLM], d[NLM];
+      for (int kt = 0; kt < KT; ++kt)
 #pragma unroll
-      for (int q = 0; q < NLM; ++q) { s[q] = S[q]; d[q] = Dd[q]; }
+        for (int r = 0; r < 4; ++r) acc[s][J][kt][r] = 0.f;
+
+  int tile = blockIdx.x;
+  int i0 = 0, i1 = 0, P0 = 0, P1 = 0;
+  if (tile < ntile) {
+    i0 = tiles[tile];
+    i1 = tiles[tile + 1];
+    P0 = off[i0];
+    P1 = off[i1];
+  }
+  for (; tile < ntile; tile += gridDim.x) {
+    const int nt = tile + gridDim.x;  // the next tile's bounds are fetched early
+    const int i0n = nt < ntile ? tiles[nt] : 0, i1n = nt < ntile ? tiles[nt + 1] : 0;
+    __syncthreads();  // the previous tile's readers are done
+    if (tid >= 128) {
+      // atom rows [Sbar | Sdbar], one thread per (atom, channel)
+      const int u = tid - 128, at = u / NQA, n = u % NQA, i = i0 + at;
+      if (at < NA && i < i1) {
+        const float4* S4 = reinterpret_cast<const float4*>(Sang + ((size_t)i * NQA + n) * NLM);
+        const float4* D4 = reinterpret_cast<const float4*>(Sdd + ((size_t)i * NQA + n) * NLM);
+        const float* gb = Gb + (size_t)i * C::NDES;
+        const float* ep = Ep + (size_t)i * C::NDES;
+        float s[NLM], d[NLM], sb[NLM], sdb[NLM];
 #pragma unroll
-      for (int lm = 0; lm < NLM; ++lm) {
-        const int v = C::vang(n, lm_l(lm));
-        const float c2 = 2.f * kClm[lm];
-        sb[lm] = c2 * (gb[v] * s[lm] - ep[v] * d[lm]);
-        sdb[lm] = -c2 * ep[v] * s[lm];
-      }
-      if (C::FB) {
-        float g4[5], h4[5];
-        q4_grad(&s[3], g4);
-        q4_hvp(&s[3], &d[3], h4);
-        const float gb4 = gb[C::v4b(n)], ep4 = ep[C::v4b(n)];
+        for (int q = 0; q < NLM / 4; ++q) {
+          const float4 x = S4[q], y = D4[q];
+          s[4 * q] = x.x; s[4 * q + 1] = x.y; s[4 * q + 2] = x.z; s[4 * q + 3] = x.w;
+          d[4 * q] = y.x; d[4 * q + 1] = y.y; d[4 * q + 2] = y.z; d[4 * q + 3] = y.w;
+        }
+        float gbl[4], epl[4];
 #pragma unroll
-        for (int m = 0; m < 5; ++m) {
-          sb[3 + m] += gb4 * g4[m] - ep4 * h4[m];
-          sdb[3 + m] -= ep4 * g4[m];
+        for (int l = 1; l <= 4; ++l) {
+          gbl[l - 1] = gb[C::vang(n, l)];
+          epl[l - 1] = ep[C::vang(n, l)];
+        }
+#pragma unroll
+        for (int lm = 0; lm < NLM; ++lm) {
+          const float c2 = 2.f * kClm[lm], gv = gbl[lm_l(lm) - 1], ev = epl[lm_l(lm) - 1];
+          sb[lm] = c2 * (gv * s[lm] - ev * d[lm]);
+          sdb[lm] = -c2 * ev * s[lm];
+        }
+        if (C::FB) {
+          float g4[5], h4[5];
+          q4_grad(&s[3], g4);
+          q4_hvp(&s[3], &d[3], h4);
+          const float gb4 = gb[C::v4b(n)], ep4 = ep[C::v4b(n)];
+#pragma unroll
+          for (int m = 0; m < 5; ++m) {
+            sb[3 + m] += gb4 * g4[m] - ep4 * h4[m];
+            sdb[3 + m] -= ep4 * g4[m];
+          }
+        }
+        float4* row = reinterpret_cast<float4*>(sm.A[at][n]);
+#pragma unroll
+        for (int q = 0; q < NLM / 4; ++q) {
+          row[q] = make_float4(sb[4 * q], sb[4 * q + 1], sb[4 * q + 2], sb[4 * q + 3]);
+          row[NLM / 4 + q] = make_float4(sdb[4 * q], sdb[4 * q + 1], sdb[4 * q + 2], sdb[4 * q + 3]);
         }
       }
+      if (u < NA) sm.type[u] = (i0 + u < i1) ? type[i0 + u] : 0;
+      if (u <= i1 - i0) sm.off[u] = off[i0 + u];
     }
-    const int P0 = off[i0], P1 = off[i1];
-    const int pa0 = okA ? off[i] : 0, pa1 = okA ? off[i + 1] : 0;
     for (int cs = P0; cs < P1; cs += CH) {
       const int ce = min(cs + CH, P1);
+      if (cs != P0) __syncthreads();  // the previous chunk's readers are done
+      if (tid < 128 && cs + tid < ce) {
+        const float4 r = rij[cs + tid], w = wij[cs + tid];
+        pair_geometry<C>(sm.geo, tid, r, make_float3(w.x, w.y, w.z), dm);
+      }
       __syncthreads();
-      if (cs + tid < ce) angular_geometry<C>(geo, tid, cs + tid, dm, own, atom_struct, jj, rij, a, Bs);
-      __syncthreads();
-      const int q0 = max(pa0, cs), q1 = min(pa1, ce);
-      for (int pp = q0; pp < q1; ++pp) {
-        const int sl = pp - cs;
-        float P = 0.f, R = 0.f;
+      for (int at = warp; at < i1 - i0; at += kCgWarps) {
+        const int q0 = max(sm.off[at], cs) - cs, q1 = min(sm.off[at + 1], ce) - cs;
+        if (q0 >= q1) continue;
+        FragA fa[2 * KS];  // [Sbar | Sdbar], k-steps of 8 columns
+        const float* Am = &sm.A[at][0][0];
 #pragma unroll
-        for (int q = 0; q < NLM; ++q) {
-          const float b = geo.B[q][sl], d = geo.D[q][sl];
-          P = fmaf(sb[q], b, fmaf(sdb[q], d, P));
-          R = fmaf(sdb[q], b, R);
+        for (int ks = 0; ks < 2 * KS; ++ks) {
+          const int c = 8 * ks + t;
+          frag_a<SPLIT>(fa[ks], g < NQA ? Am[g * kAS + c] : 0.f, g + 8 < NQA ? Am[(g + 8) * kAS + c] : 0.f,
+                        g < NQA ? Am[g * kAS + c + 4] : 0.f, g + 8 < NQA ? Am[(g + 8) * kAS + c + 4] : 0.f);
         }
-        const int J = geo.J[sl];
+        const int I = sm.type[at];
+        for (int p0 = q0; p0 < q1; p0 += 8) {
+          const int sc = p0 + pg;
+          const bool vc = sc < q1;
+          float Pb[4] = {0.f, 0.f, 0.f, 0.f}, Pd[4] = {0.f, 0.f, 0.f, 0.f}, R[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int s = 0; s < C::NS; ++s) {
-          const float wP = (s == J) ? P : 0.f, wR = (s == J) ? R : 0.f;
+          for (int ks = 0; ks < KS; ++ks) {
+            const int r0 = 8 * ks + t;
+            FragB fb, fd;
+            frag_b<SPLIT>(fb, vc ? sm.geo.B[r0][sc] : 0.f, vc ? sm.geo.B[r0 + 4][sc] : 0.f);
+            frag_b<SPLIT>(fd, vc ? sm.geo.D[r0][sc] : 0.f, vc ? sm.geo.D[r0 + 4][sc] : 0.f);
+            mma_acc<SPLIT>(Pb, fa[ks], fb);
+            mma_acc<SPLIT>(Pd, fa[KS + ks], fd);
+            mma_acc<SPLIT>(R, fa[KS + ks], fb);
+          }
+          const float P[4] = {Pb[0] + Pd[0], Pb[1] + Pd[1], Pb[2] + Pd[2], Pb[3] + Pd[3]};
+          const int s0 = p0 + t, s1 = p0 + t + 4;  // K rows t and t+4 of the second products
+          const bool v0 = s0 < q1, v1 = s1 < q1;
+          const int J0 = v0 ? sm.geo.J[s0] : -1, J1 = v1 ? sm.geo.J[s1] : -1;
+          FragB ff[KT], fu[KT];
 #pragma unroll
-          for (int k = 0; k < C::KA; ++k) accA[s][k] = fmaf(wP, geo.f[k][sl], fmaf(wR, geo.fu[k][sl], accA[s][k]));
+          for (int kt = 0; kt < KT; ++kt) {
+            const int k = 8 * kt + g;
+            const bool kv = k < KA;
+            frag_b<SPLIT>(ff[kt], (kv && v0) ? sm.geo.f[k][s0] : 0.f, (kv && v1) ? sm.geo.f[k][s1] : 0.f);
+            frag_b<SPLIT>(fu[kt], (kv && v0) ? sm.geo.fu[k][s0] : 0.f, (kv && v1) ? sm.geo.fu[k][s1] : 0.f);
+          }
+#pragma unroll
+          for (int J = 0; J < NS; ++J) {
+            const bool m0 = J0 == J, m1 = J1 == J;
+            FragA ap, ar;
+            frag_a<SPLIT>(ap, m0 ? P[0] : 0.f, m0 ? P[2] : 0.f, m1 ? P[1] : 0.f, m1 ? P[3] : 0.f);
+            frag_a<SPLIT>(ar, m0 ? R[0] : 0.f, m0 ? R[2] : 0.f, m1 ? R[1] : 0.f, m1 ? R[3] : 0.f);
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+              if (s != I) continue;
+#pragma unroll
+              for (int kt = 0; kt < KT; ++kt) {
+                mma_acc<SPLIT>(acc[s][J][kt], ap, ff[kt]);
+                mma_acc<SPLIT>(acc[s][J][kt], ar, fu[kt]);
+              }
+            }
+          }
         }
       }
     }
-    // fold this tile into the block accumulator in atom order
-    __syncthreads();
-    if (at < M::NA && n < C::NQ) {
-      const float gbn = okR ? Gb[(size_t)i * C::NDES + n] : 0.f, epn = okR ? Ep[(size_t)i * C::NDES + n] : 0.f;
-#pragma unroll
-      for (int s = 0; s < C::NS; ++s) {
-#pragma unroll
-        for (int k = 0; k < C::KR; ++k)
-          tsum[at][n][s * C::KR + k] =
-              okR ? gbn * FR[((size_t)i * C::NS + s) * C::KR + k] - epn * FRd[((size_t)i * C::NS + s) * C::KR + k] : 0.f;
-#pragma unroll
-        for (int k = 0; k < C::KA; ++k) tsum[at][n][RA + s * C::KA + k] = accA[s][k];
-      }
-    }
-    __syncthreads();
-    for (int q = tid; q < NCR + NCA; q += blockDim.x) {
-      int I, J, nn, k, col;
-      if (q < NCR) {
-        I = q / (C::NS * C::NQR * C::KR);
-        const int r = q % (C::NS * C::NQR * C::KR);
-        J = r / (C::NQR * C::KR);
-        nn = (r / C::KR) % C::NQR;
-        k = r % C::KR;
-        col = J * C::KR + k;
-      } else {
-        const int qa = q - NCR;
-        I = qa / (C::NS * C::NQA * C::KA);
-        const int r = qa % (C::NS * C::NQA * C::KA);
-        J = r / (C::NQA * C::KA);
-        nn = (r / C::KA) % C::NQA;
-        k = r % C::KA;
-        col = RA + J * C::KA + k;
-      }
-      float s = 0.f;
-      for (int t = 0; t < M::NA; ++t)
-        if (ttype[t] == I) s += tsum[t][nn][col];
-      bacc[q] += s;
+    i0 = i0n;
+    i1 = i1n;
+    if (nt < ntile) {
+      P0 = off[i0];
+      P1 = off[i1];
     }
   }
+  // fold the warps in order
   __syncthreads();
-  for (int q = tid; q < NCR + NCA; q += blockDim.x) cpart[(size_t)blockIdx.x * (NCR + NCA) + q] = bacc[q];
+#pragma unroll
+  for (int s = 0; s < NS; ++s)
+#pragma unroll
+    for (int J = 0; J < NS; ++J)
+#pragma unroll
+      for (int kt = 0; kt < KT; ++kt)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) sm.red[warp][((s * NS + J) * KT + kt) * 128 + lane * 4 + r] = acc[s][J][kt][r];
+  __syncthreads();
+  for (int q = tid; q < C::NCA; q += blockDim.x) {
+    const int k = q % KA, n = (q / KA) % NQA, sj = q / (KA * NQA);  // sj = I NS + J
+    const int kt = k / 8, kk = k % 8;
+    const int idx = (sj * KT + kt) * 128 + ((n % 8) * 4 + kk / 2) * 4 + (n / 8) * 2 + kk % 2;
+    float v = 0.f;
+#pragma unroll
+    for (int w = 0; w < kCgWarps; ++w) v += sm.red[w][idx];
+    cpart[(size_t)blockIdx.x * (C::NCR + C::NCA) + C::NCR + q] = v;
+  }
+}
+
+// Radial part: one block per contiguous range of atoms, lane = column (J, k),
+// warp r takes the range's atoms r, r + 16, ... (two per iteration, loads
+// first); the block folds its warps in order and writes cpart[block][c^R].
+constexpr int kCgRadialWarps = 16;
+
+template <class C>
+__global__ void __launch_bounds__(32 * kCgRadialWarps) k_cgrad_radial(int N, const int* __restrict__ type,
+                                                                    const float* __restrict__ Gb,
+                                                                    const float* __restrict__ Ep,
+                                                                    const float* __restrict__ FR,
+                                                                    const float* __restrict__ FRd,
+                                                                    float* __restrict__ cpart) {
+  constexpr int NCOL = C::NS * C::KR, NW = kCgRadialWarps;
+  static_assert(NCOL <= 32, "one lane per radial column");
+  __shared__ float red[NW][C::NS][C::NQR][32];
+  const int lane = threadIdx.x & 31, r = threadIdx.x >> 5;
+  const int per = (N + gridDim.x - 1) / gridDim.x;
+  const int lo = min(N, (int)blockIdx.x * per), hi = min(N, lo + per);
+  float acc[C::NS][C::NQR];
+#pragma unroll
+  for (int s = 0; s < C::NS; ++s)
+#pragma unroll
+    for (int n = 0; n < C::NQR; ++n) acc[s][n] = 0.f;
+  if (lane < NCOL) {
+    for (int i = lo + r; i < hi; i += 2 * NW) {
+      int I[2];
+      float fr[2], frd[2], gb[2][C::NQR], ep[2][C::NQR];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int iu = i + u * NW;
+        const bool ok = iu < hi;
+        I[u] = ok ? type[iu] : -1;
+        fr[u] = ok ? FR[(size_t)iu * NCOL + lane] : 0.f;
+        frd[u] = ok ? FRd[(size_t)iu * NCOL + lane] : 0.f;
+#pragma unroll
+        for (int n = 0; n < C::NQR; ++n) {
+          gb[u][n] = ok ? Gb[(size_t)iu * C::NDES + n] : 0.f;
+          ep[u][n] = ok ? Ep[(size_t)iu * C::NDES + n] : 0.f;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int n = 0; n < C::NQR; ++n) {
+          const float v = gb[u][n] * fr[u] - ep[u][n] * frd[u];
+#pragma unroll
+          for (int s = 0; s < C::NS; ++s) acc[s][n] += (s == I[u]) ? v : 0.f;
+        }
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < C::NS; ++s)
+#pragma unroll
+    for (int n = 0; n < C::NQR; ++n) red[r][s][n][lane] = acc[s][n];
+  __syncthreads();
+  for (int q = threadIdx.x; q < C::NCR; q += blockDim.x) {
+    const int k = q % C::KR, n = (q / C::KR) % C::NQR, J = (q / (C::KR * C::NQR)) % C::NS,
+              I = q / (C::KR * C::NQR * C::NS);
+    float v = 0.f;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) v += red[w][I][n][J * C::KR + k];
+    cpart[(size_t)blockIdx.x * (C::NCR + C::NCA) + q] = v;
+  }
 }
 
 // ------------------------------------------------------------- launchers
@@ -918,17 +1074,21 @@ struct Runner {
     stage("tangent_radial");
     k_tangent_angular<C, kNptTangent><<<nl->natile[1], 128, 0, A.st>>>(
         N, dm, nl->atile[1], nl->type, nl->atom_struct, nl->L[1].off, nl->L[1].owner, nl->L[1].j, nl->L[1].rij, w.a,
-        w.Bs, w.S, w.Sd, w.Gd);
+        w.Bs, w.S, w.Sd, w.Gd, w.wij);
     stage("tangent_angular");
     if (int rc = fk.join(nl)) return rc;
     if (int rc = network_backward(m, nl, A.st)) return rc;
     stage("mlp_bwd");
-    k_cgrad<C><<<cgrad_blocks(nl), 128, 0, A.st>>>(
-        N, nl->natile[1], nl->atile[1], dm, nl->type, nl->atom_struct, nl->L[1].off, nl->L[1].owner, nl->L[1].j,
-        nl->L[1].rij, w.a, w.Bs, w.S, w.Sd, w.Gb, w.Ep, w.FR, w.FRd, w.cpart);
+    const int nb = cgrad_blocks(nl);
+    Fork fc(nl, A.st);  // radial and angular parts write disjoint columns of cpart
+    k_cgrad_radial<C><<<nb, 32 * kCgRadialWarps, 0, fc.side>>>(N, nl->type, w.Gb, w.Ep, w.FR, w.FRd, w.cpart);
+    stage("cgrad_radial");
+    auto ang = m->precision == GNEP_PREC_FP32 ? k_cgrad_ang<C, true> : k_cgrad_ang<C, false>;
+    ang<<<nb, 32 * kCgWarps, sizeof(CgSmem<C>), A.st>>>(nl->natile[1], nl->atile[1], dm, nl->type, nl->L[1].off,
+                                                         nl->L[1].rij, w.wij, w.S, w.Sd, w.Gb, w.Ep, w.cpart);
     stage("cgrad");
     GNEP_CHECK_LAUNCH("backward sweeps");
-    return GNEP_OK;
+    return fc.join(nl);
   }
 };
 
@@ -954,6 +1114,12 @@ bool shape_supported(const Shape& s) {
 namespace {
 template <class C>
 int setup_shape() {
+  GNEP_CUDA(cudaFuncSetAttribute(k_cgrad_ang<C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(CgSmem<C>)));
+  GNEP_CUDA(cudaFuncSetAttribute(k_cgrad_ang<C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(CgSmem<C>)));
+  GNEP_CUDA(cudaFuncSetAttribute(k_cgrad_ang<C, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+  GNEP_CUDA(cudaFuncSetAttribute(k_cgrad_ang<C, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   int rc = mlp_setup<C::NDES, 32, C::NS, C::NQR, C::KR>();
   if (!rc) rc = mlp_setup<C::NDES, 64, C::NS, C::NQR, C::KR>();
   if (!rc) rc = mlp_setup<C::NDES, 128, C::NS, C::NQR, C::KR>();
