@@ -17,12 +17,13 @@
 // derivative tensors.
 //
 // Thread mappings.  Radial sweeps: RL consecutive lanes per atom, each taking
-// every RL-th pair, combined by warp shuffles.  Angular sweeps 1, 3, 4: a block
-// holds NA atoms; their pairs are processed in chunks of CH, the per-pair
-// geometry (basis, harmonics, directional derivatives) is computed once per
-// pair into shared memory, then consumed by one thread per (atom, channel
-// group).  Angular force: one thread per pair, with dE/dS_nlm of the block's
-// atoms in shared memory.  No float atomics anywhere: fixed summation order.
+// every RL-th pair, combined by warp shuffles.  Angular sweeps 1, 3, 4:
+// persistent blocks over tiles of atoms; the per-pair geometry (basis,
+// harmonics, directional derivatives) of a chunk of the tile's pairs is computed
+// once per pair into shared memory, then one warp per atom contracts it with
+// the atom's coefficients on the tensor cores (mma.sync TF32, warp_mma.cuh).
+// Angular force: one thread per pair, with dE/dS_nlm of the block's atoms in
+// shared memory.  No float atomics anywhere: fixed summation order.
 #include <cstdio>
 #include <mutex>
 #include <string>
@@ -156,94 +157,6 @@ __global__ void __launch_bounds__(128) k_desc_radial(int N, DevModel dm, const i
 #pragma unroll
       for (int k = 0; k < C::KR; ++k) q = fmaf(cR[((I * C::NS + s) * C::NQR + n) * C::KR + k], acc[s][k], q);
     G[(size_t)i * C::NDES + n] = q;
-  }
-}
-
-// Angular descriptors S_nlm = sum_j g_n(r_ij) B_lm (Eq. 8), q_nl (Eq. 7), q4_n.
-template <class C, int NPT, int CHD>
-__global__ void __launch_bounds__(128) k_desc_angular(int N, DevModel dm, const int* __restrict__ tiles,
-                                                      const int* __restrict__ type, const int* __restrict__ off,
-                                                      const float4* __restrict__ rij, float* __restrict__ Sout,
-                                                      float* __restrict__ G) {
-  using M = AMap<C::NQA, NPT>;
-  __shared__ float sf[C::KA][CHD];
-  __shared__ float sB[NLM][CHD];
-  __shared__ int sJ[CHD];
-  const int tid = threadIdx.x;
-  const int i0 = tiles[blockIdx.x], i1 = tiles[blockIdx.x + 1];
-  const int a = tid / M::TPA, tq = tid % M::TPA;
-  const int i = i0 + a;
-  const bool ok = a < M::NA && i < i1;
-  float c[NPT][C::NS][C::KA];
-  float S[NPT][NLM];
-  const int I = ok ? type[i] : 0;
-#pragma unroll
-  for (int h = 0; h < NPT; ++h) {
-    const int n = tq * NPT + h;
-#pragma unroll
-    for (int s = 0; s < C::NS; ++s)
-#pragma unroll
-      for (int k = 0; k < C::KA; ++k)
-        c[h][s][k] = (ok && n < C::NQA) ? dm.params[dm.off_cA + ((I * C::NS + s) * C::NQA + n) * C::KA + k] : 0.f;
-#pragma unroll
-    for (int q = 0; q < NLM; ++q) S[h][q] = 0.f;
-  }
-  const int P0 = off[i0], P1 = off[i1];
-  const int pa0 = ok ? off[i] : 0, pa1 = ok ? off[i + 1] : 0;
-  for (int cs = P0; cs < P1; cs += CHD) {
-    const int ce = min(cs + CHD, P1);
-    for (int p = cs + tid; p < ce; p += blockDim.x) {
-      const int sl = p - cs;
-      const float4 r = rij[p];
-      const float rr = sqrtf(r.x * r.x + r.y * r.y + r.z * r.z);
-      const float ri = 1.f / rr;
-      float f[C::KA];
-      radial_basis<C::KA>(rr, dm.rca_inv, f);
-#pragma unroll
-      for (int k = 0; k < C::KA; ++k) sf[k][sl] = f[k];
-      float B[NLM];
-      harmonics(r.x * ri, r.y * ri, r.z * ri, B);
-#pragma unroll
-      for (int q = 0; q < NLM; ++q) sB[q][sl] = B[q];
-      sJ[sl] = (int)r.w;
-    }
-    __syncthreads();
-    const int q0 = max(pa0, cs), q1 = min(pa1, ce);
-    for (int pp = q0; pp < q1; ++pp) {
-      const int sl = pp - cs;
-      const int J = sJ[sl];
-      float f[C::KA];
-#pragma unroll
-      for (int k = 0; k < C::KA; ++k) f[k] = sf[k][sl];
-      float g[NPT];
-#pragma unroll
-      for (int h = 0; h < NPT; ++h) g[h] = dot_row<C::NS, C::KA>(c[h], J, f);  // Eq. 6
-#pragma unroll
-      for (int q = 0; q < NLM; ++q) {
-        const float b = sB[q][sl];
-#pragma unroll
-        for (int h = 0; h < NPT; ++h) S[h][q] = fmaf(g[h], b, S[h][q]);  // Eq. 8
-      }
-    }
-    __syncthreads();
-  }
-  if (!ok) return;
-#pragma unroll
-  for (int h = 0; h < NPT; ++h) {
-    const int n = tq * NPT + h;
-    if (n >= C::NQA) continue;
-    float* so = Sout + ((size_t)i * C::NQA + n) * NLM;
-#pragma unroll
-    for (int q = 0; q < NLM; ++q) so[q] = S[h][q];
-    float* gi = G + (size_t)i * C::NDES;
-#pragma unroll
-    for (int l = 1; l <= 4; ++l) {
-      float q = 0.f;  // Eq. 7
-#pragma unroll
-      for (int lm = l * l - 1; lm < (l + 1) * (l + 1) - 1; ++lm) q = fmaf(kClm[lm] * S[h][lm], S[h][lm], q);
-      gi[C::vang(n, l)] = q;
-    }
-    if (C::FB) gi[C::v4b(n)] = q4_value(&S[h][3]);
   }
 }
 
@@ -495,20 +408,10 @@ __global__ void __launch_bounds__(128) k_tangent_radial(int N, DevModel dm, cons
   }
 }
 
-// Angular geometry for the tangent and c-gradient sweeps, one pair per thread:
-// basis f_k, fu_k = f_k' (u_hat . u_ij), harmonics B_lm and D_lm = grad B_lm . u_ij.
-template <class C>
-struct AngGeo {
-  float f[C::KA][CH];
-  float fu[C::KA][CH];
-  float B[NLM][CH];
-  float D[NLM][CH];
-  int J[CH];
-};
-
-// The same geometry with rows padded for warp-level MMA fragments (c-gradient
-// sweep): B and D rows 8 mod 32 words apart, f and fu rows 4 mod 32, so that the
-// fragment loads of one warp touch 32 different banks.
+// Angular geometry of a chunk of CH pairs for the c-gradient sweep, one pair per
+// thread: basis f_k, fu_k = f_k' (u_hat . u_ij), harmonics B_lm and
+// D_lm = grad B_lm . u_ij.  Rows of B and D are 8 mod 32 words apart, rows of f
+// and fu 4 mod 32, so that the MMA fragment loads of one warp touch 32 banks.
 template <class C>
 struct MGeo {
   static constexpr int SBD = CH + 8, SF = CH + 4;
@@ -554,106 +457,6 @@ __device__ __forceinline__ void pair_geometry(Geo& g, int slot, float4 r, float3
   g.J[slot] = (int)r.w;
 }
 
-// Angular tangent: Sdot_nlm = sum_j [g_n' (u_hat . u) B_lm + g_n grad B_lm . u],
-// qdot_nl = 2 sum_m C_lm S_nlm Sdot_nlm, qdot4_n = dq4/dS . Sdot.
-template <class C, int NPT>
-__global__ void __launch_bounds__(128) k_tangent_angular(int N, DevModel dm, const int* __restrict__ tiles,
-                                                         const int* __restrict__ type,
-                                                         const int* __restrict__ atom_struct, const int* __restrict__ off,
-                                                         const int* __restrict__ own, const int* __restrict__ jj,
-                                                         const float4* __restrict__ rij, const float4* __restrict__ a,
-                                                         const float* __restrict__ Bs, const float* __restrict__ Sang,
-                                                         float* __restrict__ Sd, float* __restrict__ Gd,
-                                                         float4* __restrict__ wij) {
-  using M = AMap<C::NQA, NPT>;
-  __shared__ AngGeo<C> geo;
-  const int tid = threadIdx.x;
-  const int i0 = tiles[blockIdx.x], i1 = tiles[blockIdx.x + 1];
-  const int at = tid / M::TPA, tq = tid % M::TPA;
-  const int i = i0 + at;
-  const bool ok = at < M::NA && i < i1;
-  float c[NPT][C::NS][C::KA];
-  float sd[NPT][NLM];
-  const int I = ok ? type[i] : 0;
-#pragma unroll
-  for (int h = 0; h < NPT; ++h) {
-    const int n = tq * NPT + h;
-#pragma unroll
-    for (int s = 0; s < C::NS; ++s)
-#pragma unroll
-      for (int k = 0; k < C::KA; ++k)
-        c[h][s][k] = (ok && n < C::NQA) ? dm.params[dm.off_cA + ((I * C::NS + s) * C::NQA + n) * C::KA + k] : 0.f;
-#pragma unroll
-    for (int q = 0; q < NLM; ++q) sd[h][q] = 0.f;
-  }
-  const int P0 = off[i0], P1 = off[i1];
-  const int pa0 = ok ? off[i] : 0, pa1 = ok ? off[i + 1] : 0;
-  for (int cs = P0; cs < P1; cs += CH) {
-    const int ce = min(cs + CH, P1);
-    if (cs + tid < ce) {
-      const int p = cs + tid;
-      const float4 r = rij[p];
-      const float3 w = tangent_dir(p, r, own, atom_struct, jj, a, Bs);
-      wij[p] = make_float4(w.x, w.y, w.z, 0.f);  // reused by the c-gradient sweep
-      pair_geometry<C>(geo, tid, r, w, dm);
-    }
-    __syncthreads();
-    const int q0 = max(pa0, cs), q1 = min(pa1, ce);
-    for (int pp = q0; pp < q1; ++pp) {
-      const int sl = pp - cs;
-      const int J = geo.J[sl];
-      float f[C::KA], fu[C::KA];
-#pragma unroll
-      for (int k = 0; k < C::KA; ++k) {
-        f[k] = geo.f[k][sl];
-        fu[k] = geo.fu[k][sl];
-      }
-      float g[NPT], ga[NPT];
-#pragma unroll
-      for (int h = 0; h < NPT; ++h) {
-        g[h] = dot_row<C::NS, C::KA>(c[h], J, f);
-        ga[h] = dot_row<C::NS, C::KA>(c[h], J, fu);
-      }
-#pragma unroll
-      for (int q = 0; q < NLM; ++q) {
-        const float b = geo.B[q][sl], d = geo.D[q][sl];
-#pragma unroll
-        for (int h = 0; h < NPT; ++h) sd[h][q] = fmaf(ga[h], b, fmaf(g[h], d, sd[h][q]));
-      }
-    }
-    __syncthreads();
-  }
-  if (!ok) return;
-#pragma unroll
-  for (int h = 0; h < NPT; ++h) {
-    const int n = tq * NPT + h;
-    if (n >= C::NQA) continue;
-    float* so = Sd + ((size_t)i * C::NQA + n) * NLM;
-#pragma unroll
-    for (int q = 0; q < NLM; ++q) so[q] = sd[h][q];
-    const float* S = Sang + ((size_t)i * C::NQA + n) * NLM;
-    float s[NLM];
-#pragma unroll
-    for (int q = 0; q < NLM; ++q) s[q] = S[q];
-    float* gi = Gd + (size_t)i * C::NDES;
-#pragma unroll
-    for (int l = 1; l <= 4; ++l) {
-      float q = 0.f;
-#pragma unroll
-      for (int lm = l * l - 1; lm < (l + 1) * (l + 1) - 1; ++lm) q = fmaf(2.f * kClm[lm] * s[lm], sd[h][lm], q);
-      gi[C::vang(n, l)] = q;
-    }
-    if (C::FB) {
-      float g4[5];
-      q4_grad(&s[3], g4);
-      float q = 0.f;
-#pragma unroll
-      for (int m = 0; m < 5; ++m) q = fmaf(g4[m], sd[h][3 + m], q);
-      gi[C::v4b(n)] = q;
-    }
-  }
-}
-
 // ------------------------------------------------------------- sweep 4
 
 // dL/dc.  With Sbar and Sdbar the adjoints of S and Sdot of atom i,
@@ -676,6 +479,14 @@ __global__ void __launch_bounds__(128) k_tangent_angular(int N, DevModel dm, con
 // and t+4 in the second product.  Accumulators stay in registers over all of a
 // warp's atoms; the block folds its four warps in order and writes
 // cpart[block][c^A] once.
+// Hint to bring [p, p + bytes) into L2 ahead of use (bulk prefetch; the range
+// is rounded inward to 16 bytes, so nothing outside it is touched).
+__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
+  const uintptr_t a = ((uintptr_t)p + 15) & ~(uintptr_t)15;
+  const uintptr_t e = ((uintptr_t)p + bytes) & ~(uintptr_t)15;
+  if (e > a) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((uint32_t)(e - a)) : "memory");
+}
+
 constexpr int kAS = 2 * NLM + 4;  // row stride of [Sbar | Sdbar] (20 mod 32 words: conflict-free A fragments)
 constexpr int kCgWarps = 8;       // warps 0-3 build the pair geometry while warps 4-7 build the atom rows
 
@@ -706,15 +517,13 @@ __global__ void __launch_bounds__(32 * kCgWarps, SPLIT ? 1 : 2)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, t = lane & 3;
   const int pg = (g >> 1) | ((g & 1) << 2);  // pair of B-fragment column g
-  float acc[NS][NS][KT][4];
+  Acc<SPLIT> acc[NS][NS][KT];
 #pragma unroll
   for (int s = 0; s < NS; ++s)
 #pragma unroll
     for (int J = 0; J < NS; ++J)
 #pragma unroll
-      for (int kt = 0; kt < KT; ++kt)
-#pragma unroll
-        for (int r = 0; r < 4; ++r) acc[s][J][kt][r] = 0.f;
+      for (int kt = 0; kt < KT; ++kt) acc[s][J][kt].zero();
 
   int tile = blockIdx.x;
   int i0 = 0, i1 = 0, P0 = 0, P1 = 0;
@@ -784,6 +593,18 @@ __global__ void __launch_bounds__(32 * kCgWarps, SPLIT ? 1 : 2)
         pair_geometry<C>(sm.geo, tid, r, make_float3(w.x, w.y, w.z), dm);
       }
       __syncthreads();
+      if (tid == 32 * kCgWarps - 1 && cs == P0 && nt < ntile) {
+        // the next tile's inputs move into L2 while this one is contracted (the
+        // last warp has the fewest atoms)
+        const int p0n = off[i0n], p1n = off[i1n];
+        const size_t na = (size_t)(i1n - i0n);
+        prefetch_l2(Sang + (size_t)i0n * NQA * NLM, na * NQA * NLM * sizeof(float));
+        prefetch_l2(Sdd + (size_t)i0n * NQA * NLM, na * NQA * NLM * sizeof(float));
+        prefetch_l2(Gb + (size_t)i0n * C::NDES, na * C::NDES * sizeof(float));
+        prefetch_l2(Ep + (size_t)i0n * C::NDES, na * C::NDES * sizeof(float));
+        prefetch_l2(rij + p0n, (size_t)(p1n - p0n) * sizeof(float4));
+        prefetch_l2(wij + p0n, (size_t)(p1n - p0n) * sizeof(float4));
+      }
       for (int at = warp; at < i1 - i0; at += kCgWarps) {
         const int q0 = max(sm.off[at], cs) - cs, q1 = min(sm.off[at + 1], ce) - cs;
         if (q0 >= q1) continue;
@@ -799,7 +620,10 @@ __global__ void __launch_bounds__(32 * kCgWarps, SPLIT ? 1 : 2)
         for (int p0 = q0; p0 < q1; p0 += 8) {
           const int sc = p0 + pg;
           const bool vc = sc < q1;
-          float Pb[4] = {0.f, 0.f, 0.f, 0.f}, Pd[4] = {0.f, 0.f, 0.f, 0.f}, R[4] = {0.f, 0.f, 0.f, 0.f};
+          Acc<SPLIT> Pb, Pd, Rc;
+          Pb.zero();
+          Pd.zero();
+          Rc.zero();
 #pragma unroll
           for (int ks = 0; ks < KS; ++ks) {
             const int r0 = 8 * ks + t;
@@ -808,9 +632,14 @@ __global__ void __launch_bounds__(32 * kCgWarps, SPLIT ? 1 : 2)
             frag_b<SPLIT>(fd, vc ? sm.geo.D[r0][sc] : 0.f, vc ? sm.geo.D[r0 + 4][sc] : 0.f);
             mma_acc<SPLIT>(Pb, fa[ks], fb);
             mma_acc<SPLIT>(Pd, fa[KS + ks], fd);
-            mma_acc<SPLIT>(R, fa[KS + ks], fb);
+            mma_acc<SPLIT>(Rc, fa[KS + ks], fb);
           }
-          const float P[4] = {Pb[0] + Pd[0], Pb[1] + Pd[1], Pb[2] + Pd[2], Pb[3] + Pd[3]};
+          float P[4], R[4];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            P[r] = Pb.get(r) + Pd.get(r);
+            R[r] = Rc.get(r);
+          }
           const int s0 = p0 + t, s1 = p0 + t + 4;  // K rows t and t+4 of the second products
           const bool v0 = s0 < q1, v1 = s1 < q1;
           const int J0 = v0 ? sm.geo.J[s0] : -1, J1 = v1 ? sm.geo.J[s1] : -1;
@@ -857,7 +686,7 @@ __global__ void __launch_bounds__(32 * kCgWarps, SPLIT ? 1 : 2)
 #pragma unroll
       for (int kt = 0; kt < KT; ++kt)
 #pragma unroll
-        for (int r = 0; r < 4; ++r) sm.red[warp][((s * NS + J) * KT + kt) * 128 + lane * 4 + r] = acc[s][J][kt][r];
+        for (int r = 0; r < 4; ++r) sm.red[warp][((s * NS + J) * KT + kt) * 128 + lane * 4 + r] = acc[s][J][kt].get(r);
   __syncthreads();
   for (int q = tid; q < C::NCA; q += blockDim.x) {
     const int k = q % KA, n = (q / KA) % NQA, sj = q / (KA * NQA);  // sj = I NS + J
@@ -935,13 +764,354 @@ __global__ void __launch_bounds__(32 * kCgRadialWarps) k_cgrad_radial(int N, con
   }
 }
 
+// ------------------------------------------------------------- warp-product sweeps 1 and 3
+
+// Angular descriptor and tangent sweeps on warp-level tensor cores, one warp
+// per atom i (species I).  For each run of 8 of its pairs (columns),
+//   G   = sum_J C^{IJ} F_J          (16 x 16) (16 x 8):  g_n(r_ij) of Eq. 6
+//   Ga  = sum_J C^{IJ} Fu_J          tangent: g_n'(r_ij) (u_hat . u)
+//   S  += G B^T                      (16 x 8) (8 x 24):   S_nlm of Eq. 8
+//   Sd += Ga B^T + G D^T             tangent: Sdot_nlm
+// where C^{IJ}[n][k] = c^A_nk^{IJ} and F_J holds f_k of the pairs whose
+// neighbour has species J (zero elsewhere).  As in the c-gradient sweep, the
+// C fragments of the first products are the A fragments of the second (column
+// g holds pair g/2 + 4 (g mod 2)).  The epilogue forms q_nl (Eq. 7) and q4_n,
+// or their tangents, from the accumulator fragments with lane shuffles.
+template <class C, bool TAN>
+struct AGeo {
+  static constexpr int CHT = 256;                   // pairs per chunk
+  static constexpr int SF = CHT + 8, SB = CHT + 4;  // f, fu rows 8 mod 32 words apart; B, D rows 4 mod 32
+  float f[C::KA][SF];
+  float fu[TAN ? C::KA : 1][SF];
+  float B[NLM][SB];
+  float D[TAN ? NLM : 1][SB];
+  int J[CHT];
+};
+constexpr int kCS = 20;            // row stride of the staged C^{IJ} blocks (conflict-free A fragments)
+constexpr int kAngWarps = 8;
+constexpr int kAngMaxAtoms = 128;  // atoms per tile, at most
+
+template <class C, bool TAN>
+struct AngSmem {
+  AGeo<C, TAN> geo;
+  float c[C::NS * C::NS][16][kCS];  // C^{IJ}[n][k], zero-padded to 16 x 16
+  float clm[NLM];
+  int off[kAngMaxAtoms + 1];
+  int type[kAngMaxAtoms];
+};
+
+// Lane (g, t) of an accumulator holds S[n][q] for n = g + 8h (h = r / 2) and
+// q = 8 nt + 2t + (r mod 2).  Sum over the lane's q of C_q x_q y_q per degree l,
+// completed over the four lanes of the row.
+__device__ __forceinline__ void lsum_rows(const float (&x)[3][4], const float (&y)[3][4], const float* clm, int t,
+                                          float (&out)[2][4]) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+#pragma unroll
+    for (int l = 0; l < 4; ++l) out[h][l] = 0.f;
+#pragma unroll
+    for (int nt = 0; nt < 3; ++nt)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int q = 8 * nt + 2 * t + e;
+        const float v = clm[q] * x[nt][2 * h + e] * y[nt][2 * h + e];
+        const int l = lm_l(q) - 1;
+#pragma unroll
+        for (int ll = 0; ll < 4; ++ll) out[h][ll] += (ll == l) ? v : 0.f;
+      }
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      out[h][l] += __shfl_xor_sync(0xffffffffu, out[h][l], 1);
+      out[h][l] += __shfl_xor_sync(0xffffffffu, out[h][l], 2);
+    }
+  }
+}
+
+__device__ __forceinline__ float pick4(const float (&v)[4], int t) {
+  return t == 0 ? v[0] : t == 1 ? v[1] : t == 2 ? v[2] : v[3];
+}
+
+// The five l = 2 moments (q = 3..7) of row half h, gathered from the lanes t = 1..3 of the row.
+__device__ __forceinline__ void gather_l2(const float (&x)[3][4], int h, int lane, float (&s)[5]) {
+  const int base = lane & ~3;
+  s[0] = __shfl_sync(0xffffffffu, x[0][2 * h + 1], base + 1);
+  s[1] = __shfl_sync(0xffffffffu, x[0][2 * h], base + 2);
+  s[2] = __shfl_sync(0xffffffffu, x[0][2 * h + 1], base + 2);
+  s[3] = __shfl_sync(0xffffffffu, x[0][2 * h], base + 3);
+  s[4] = __shfl_sync(0xffffffffu, x[0][2 * h + 1], base + 3);
+}
+
+template <class C, bool TAN, bool SPLIT>
+__global__ void __launch_bounds__(32 * kAngWarps, 2)
+    k_ang_mma(int ntile, const int* __restrict__ tiles, DevModel dm, const int* __restrict__ type,
+              const int* __restrict__ atom_struct, const int* __restrict__ off, const int* __restrict__ own,
+              const int* __restrict__ jj, const float4* __restrict__ rij, const float4* __restrict__ a,
+              const float* __restrict__ Bs, const float* __restrict__ Sin, float* __restrict__ Sout,
+              float* __restrict__ Gout, float4* __restrict__ wij) {
+  using SM = AngSmem<C, TAN>;
+  using GEO = AGeo<C, TAN>;
+  constexpr int CHT = GEO::CHT, NQA = C::NQA, KA = C::KA, NS = C::NS;
+  static_assert(NLM == 24 && NQA <= 16 && KA <= 16, "fragment shapes");
+  extern __shared__ __align__(16) unsigned char smraw[];
+  SM& sm = *reinterpret_cast<SM*>(smraw);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int pg = (g >> 1) | ((g & 1) << 2);  // pair of B-fragment column g
+  for (int q = tid; q < NS * NS * 16 * kCS; q += blockDim.x) {
+    const int ij = q / (16 * kCS), r = q % (16 * kCS), n = r / kCS, k = r % kCS;
+    sm.c[ij][n][k] = (n < NQA && k < KA) ? dm.params[dm.off_cA + (ij * NQA + n) * KA + k] : 0.f;
+  }
+  if (tid < NLM) sm.clm[tid] = kClm[tid];
+
+  int tile = blockIdx.x;
+  int i0 = 0, i1 = 0, P0 = 0, P1 = 0;
+  if (tile < ntile) {
+    i0 = tiles[tile];
+    i1 = tiles[tile + 1];
+    P0 = off[i0];
+    P1 = off[i1];
+  }
+  for (; tile < ntile; tile += gridDim.x) {
+    const int nt = tile + gridDim.x;  // the next tile's bounds are fetched early
+    const int i0n = nt < ntile ? tiles[nt] : 0, i1n = nt < ntile ? tiles[nt + 1] : 0;
+    __syncthreads();  // the previous tile's readers are done (and the staged C^{IJ} is complete)
+    if (tid <= i1 - i0) sm.off[tid] = off[i0 + tid];
+    if (tid < i1 - i0) sm.type[tid] = type[i0 + tid];
+    for (int cs = P0; cs < P1 || cs == P0; cs += CHT) {  // one pass even for a tile without pairs
+      const int ce = min(cs + CHT, P1);
+      if (cs != P0) __syncthreads();  // the previous chunk's readers are done
+      if (cs + tid < ce) {
+        const int p = cs + tid;
+        const float4 r = rij[p];
+        if (TAN) {
+          const float3 w = tangent_dir(p, r, own, atom_struct, jj, a, Bs);
+          wij[p] = make_float4(w.x, w.y, w.z, 0.f);  // reused by the c-gradient sweep
+          pair_geometry<C>(sm.geo, tid, r, w, dm);
+        } else {
+          const float rr = sqrtf(r.x * r.x + r.y * r.y + r.z * r.z);
+          const float ri = 1.f / rr;
+          float f[KA], B[NLM];
+          radial_basis<KA>(rr, dm.rca_inv, f);
+          harmonics(r.x * ri, r.y * ri, r.z * ri, B);
+#pragma unroll
+          for (int k = 0; k < KA; ++k) sm.geo.f[k][tid] = f[k];
+#pragma unroll
+          for (int q = 0; q < NLM; ++q) sm.geo.B[q][tid] = B[q];
+          sm.geo.J[tid] = (int)r.w;
+        }
+      }
+      __syncthreads();
+      if (tid == 32 * kAngWarps - 1 && cs == P0 && nt < ntile) {
+        // the next tile's pair inputs move into L2 while this one is contracted
+        const int p0n = off[i0n], p1n = off[i1n];
+        prefetch_l2(rij + p0n, (size_t)(p1n - p0n) * sizeof(float4));
+        if (TAN) {
+          prefetch_l2(own + p0n, (size_t)(p1n - p0n) * sizeof(int));
+          prefetch_l2(jj + p0n, (size_t)(p1n - p0n) * sizeof(int));
+          prefetch_l2(Sin + (size_t)i0n * NQA * NLM, (size_t)(i1n - i0n) * NQA * NLM * sizeof(float));
+        }
+      }
+      for (int at = warp; at < i1 - i0; at += kAngWarps) {
+        const int ia0 = sm.off[at], ia1 = sm.off[at + 1];
+        const int q0 = max(ia0, cs) - cs, q1 = min(ia1, ce) - cs;
+        const bool first = ia0 >= cs, last = ia1 <= ce;  // the atom's pairs start / end in this chunk
+        // an atom without pairs is written by the chunk that holds its position in the list
+        const bool mine = ia0 < ia1 ? q0 < q1 : ((ia0 >= cs && ia0 < ce) || (ia0 == P1 && ce == P1));
+        if (!mine) continue;
+        const int I = sm.type[at], i = i0 + at;
+        FragA fc[NS][2];  // C^{IJ}, k-steps of 8 basis functions
+#pragma unroll
+        for (int J = 0; J < NS; ++J)
+#pragma unroll
+          for (int ks = 0; ks < 2; ++ks) {
+            const float* cm = &sm.c[I * NS + J][0][0];
+            const int c0 = 8 * ks + t;
+            frag_a<SPLIT>(fc[J][ks], cm[g * kCS + c0], cm[(g + 8) * kCS + c0], cm[g * kCS + c0 + 4],
+                          cm[(g + 8) * kCS + c0 + 4]);
+          }
+        Acc<SPLIT> sacc[3];
+#pragma unroll
+        for (int nq = 0; nq < 3; ++nq) sacc[nq].zero();
+        for (int p0 = q0; p0 < q1; p0 += 8) {
+          const int sc = p0 + pg;
+          const int Jc = sc < q1 ? sm.geo.J[sc] : -1;
+          Acc<SPLIT> G, Ga;
+          G.zero();
+          Ga.zero();
+#pragma unroll
+          for (int ks = 0; ks < 2; ++ks) {
+            const int k0 = 8 * ks + t, k1 = k0 + 4;
+            const float f0 = (Jc >= 0 && k0 < KA) ? sm.geo.f[k0][sc] : 0.f;
+            const float f1 = (Jc >= 0 && k1 < KA) ? sm.geo.f[k1][sc] : 0.f;
+            float u0 = 0.f, u1 = 0.f;
+            if (TAN) {
+              u0 = (Jc >= 0 && k0 < KA) ? sm.geo.fu[k0][sc] : 0.f;
+              u1 = (Jc >= 0 && k1 < KA) ? sm.geo.fu[k1][sc] : 0.f;
+            }
+#pragma unroll
+            for (int J = 0; J < NS; ++J) {
+              const bool m = Jc == J;
+              FragB bf;
+              frag_b<SPLIT>(bf, m ? f0 : 0.f, m ? f1 : 0.f);
+              mma_acc<SPLIT>(G, fc[J][ks], bf);
+              if (TAN) {
+                FragB bu;
+                frag_b<SPLIT>(bu, m ? u0 : 0.f, m ? u1 : 0.f);
+                mma_acc<SPLIT>(Ga, fc[J][ks], bu);
+              }
+            }
+          }
+          // second products: K rows t and t+4 are the pairs t and t+4
+          const int s0 = p0 + t, s1 = p0 + t + 4;
+          const bool v0 = s0 < q1, v1 = s1 < q1;
+          FragA ag, aga;
+          frag_a<SPLIT>(ag, G.get(0), G.get(2), G.get(1), G.get(3));
+          if (TAN) frag_a<SPLIT>(aga, Ga.get(0), Ga.get(2), Ga.get(1), Ga.get(3));
+#pragma unroll
+          for (int nq = 0; nq < 3; ++nq) {
+            const int q = 8 * nq + g;
+            FragB bb;
+            frag_b<SPLIT>(bb, v0 ? sm.geo.B[q][s0] : 0.f, v1 ? sm.geo.B[q][s1] : 0.f);
+            if (TAN) {
+              FragB bd;
+              frag_b<SPLIT>(bd, v0 ? sm.geo.D[q][s0] : 0.f, v1 ? sm.geo.D[q][s1] : 0.f);
+              mma_acc<SPLIT>(sacc[nq], aga, bb);
+              mma_acc<SPLIT>(sacc[nq], ag, bd);
+            } else {
+              mma_acc<SPLIT>(sacc[nq], ag, bb);
+            }
+          }
+        }
+        float acc[3][4];
+#pragma unroll
+        for (int nq = 0; nq < 3; ++nq)
+#pragma unroll
+          for (int r = 0; r < 4; ++r) acc[nq][r] = sacc[nq].get(r);
+        // S (or Sdot) of row n = g + 8h at q = 8 nq + 2t, +1
+        float* srow[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) srow[h] = Sout + ((size_t)i * NQA + min(g + 8 * h, NQA - 1)) * NLM;
+        if (!first) {  // earlier chunks of this tile left a partial sum
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+            if (g + 8 * h < NQA)
+#pragma unroll
+              for (int nq = 0; nq < 3; ++nq) {
+                const float2 v = *reinterpret_cast<const float2*>(srow[h] + 8 * nq + 2 * t);
+                acc[nq][2 * h] += v.x;
+                acc[nq][2 * h + 1] += v.y;
+              }
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+          if (g + 8 * h < NQA)
+#pragma unroll
+            for (int nq = 0; nq < 3; ++nq)
+              *reinterpret_cast<float2*>(srow[h] + 8 * nq + 2 * t) = make_float2(acc[nq][2 * h], acc[nq][2 * h + 1]);
+        if (!last) continue;  // completed in a later chunk
+        float* gi = Gout + (size_t)i * C::NDES;
+        if (!TAN) {
+          float ql[2][4];
+          lsum_rows(acc, acc, sm.clm, t, ql);  // q_nl = sum_m C_lm S_nlm^2 (Eq. 7)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            float s2[5];
+            gather_l2(acc, h, lane, s2);
+            const int n = g + 8 * h;
+            if (n < NQA) {
+              gi[C::vang(n, t + 1)] = pick4(ql[h], t);
+              if (C::FB && t == 0) gi[C::v4b(n)] = q4_value(s2);
+            }
+          }
+        } else {
+          float sv[3][4];  // S at the lane's positions
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const float* srow_in = Sin + ((size_t)i * NQA + min(g + 8 * h, NQA - 1)) * NLM;
+#pragma unroll
+            for (int nq = 0; nq < 3; ++nq) {
+              const float2 v = g + 8 * h < NQA ? *reinterpret_cast<const float2*>(srow_in + 8 * nq + 2 * t)
+                                               : make_float2(0.f, 0.f);
+              sv[nq][2 * h] = v.x;
+              sv[nq][2 * h + 1] = v.y;
+            }
+          }
+          float ql[2][4];
+          lsum_rows(sv, acc, sm.clm, t, ql);  // qdot_nl = 2 sum_m C_lm S_nlm Sdot_nlm
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            float s2[5], d2[5];
+            gather_l2(sv, h, lane, s2);
+            gather_l2(acc, h, lane, d2);
+            const int n = g + 8 * h;
+            if (n < NQA) {
+              gi[C::vang(n, t + 1)] = 2.f * pick4(ql[h], t);
+              if (C::FB && t == 0) {
+                float g4[5];
+                q4_grad(s2, g4);
+                float q = 0.f;
+#pragma unroll
+                for (int m = 0; m < 5; ++m) q = fmaf(g4[m], d2[m], q);
+                gi[C::v4b(n)] = q;
+              }
+            }
+          }
+        }
+      }
+      if (ce >= P1) break;
+    }
+    i0 = i0n;
+    i1 = i1n;
+    if (nt < ntile) {
+      P0 = off[i0];
+      P1 = off[i1];
+    }
+  }
+}
+
+template <class C, bool TAN, bool SPLIT>
+int ang_grid_cap() {
+  static int cap = 0;  // resident blocks on this GPU (the same value on every call)
+  if (!cap) {
+    int per_sm = 0, dev = 0, sms = 0;
+    GNEP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ang_mma<C, TAN, SPLIT>, 32 * kAngWarps,
+                                                            sizeof(AngSmem<C, TAN>)));
+    GNEP_CUDA(cudaGetDevice(&dev));
+    GNEP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    cap = (per_sm > 0 ? per_sm : 1) * sms;
+  }
+  return cap;
+}
+
+// Descriptor (TAN = false: S, q_nl, q4 into Sout, Gout) or tangent (TAN = true:
+// Sdot, qdot into Sout, Gout; w_ij into wij) sweep over the tiles of atile[0].
+// Products carry FP32 accuracy (3xTF32) except in the BF16 precision mode.
+template <class C, bool TAN>
+int launch_ang(const gnep_model* m, const gnep_nlist* nl, cudaStream_t st, const float4* a, const float* Bs,
+               const float* Sin, float* Sout, float* Gout, float4* wij) {
+  const int ntile = nl->natile[0];
+  if (ntile < 1) return GNEP_OK;
+  const bool split = m->precision != GNEP_PREC_BF16;
+  const int cap = split ? ang_grid_cap<C, TAN, true>() : ang_grid_cap<C, TAN, false>();
+  const int nb = ntile < cap ? ntile : cap;
+  auto kern = split ? k_ang_mma<C, TAN, true> : k_ang_mma<C, TAN, false>;
+  kern<<<nb, 32 * kAngWarps, sizeof(AngSmem<C, TAN>), st>>>(ntile, nl->atile[0], m->dev(), nl->type, nl->atom_struct,
+                                                            nl->L[1].off, nl->L[1].owner, nl->L[1].j, nl->L[1].rij,
+                                                            a, Bs, Sin, Sout, Gout, wij);
+  return GNEP_OK;
+}
+
+template <class C, bool TAN, bool SPLIT>
+int setup_ang() {
+  GNEP_CUDA(cudaFuncSetAttribute(k_ang_mma<C, TAN, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(AngSmem<C, TAN>)));
+  GNEP_CUDA(cudaFuncSetAttribute(k_ang_mma<C, TAN, SPLIT>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+  return ang_grid_cap<C, TAN, SPLIT>() > 0 ? GNEP_OK : GNEP_ERR_CUDA;
+}
+
 // ------------------------------------------------------------- launchers
 
 namespace {
-
-constexpr int kNptDesc = 2;     // channels per thread, descriptor sweep
-constexpr int kChDesc = 256;    // pairs per geometry chunk, descriptor sweep
-constexpr int kNptTangent = 1;  // channels per thread, tangent sweep
 
 // Fork / join of a second stream for two sweeps of one phase that do not
 // depend on each other.  Under stream capture this records two parallel
@@ -1025,8 +1195,7 @@ struct Runner {
     k_desc_radial<C><<<blocks_for((int64_t)N * RL, 128), 128, 0, fk.side>>>(N, dm, nl->type, nl->L[0].off,
                                                                              nl->L[0].rij, w.FR, w.G);
     stage("desc_radial");
-    k_desc_angular<C, kNptDesc, kChDesc><<<nl->natile[0], 128, 0, A.st>>>(N, dm, nl->atile[0], nl->type,
-                                                                           nl->L[1].off, nl->L[1].rij, w.S, w.G);
+    if (int rc = launch_ang<C, false>(m, nl, A.st, nullptr, nullptr, nullptr, w.S, w.G, nullptr)) return rc;
     stage("desc_angular");
     GNEP_CHECK_LAUNCH("descriptor sweep");
     if (int rc = fk.join(nl)) return rc;
@@ -1072,9 +1241,7 @@ struct Runner {
     k_tangent_radial<C><<<blocks_for((int64_t)N * RL, 128), 128, 0, fk.side>>>(
         N, dm, nl->type, nl->atom_struct, nl->L[0].off, nl->L[0].j, nl->L[0].rij, w.a, w.Bs, w.FRd, w.Gd);
     stage("tangent_radial");
-    k_tangent_angular<C, kNptTangent><<<nl->natile[1], 128, 0, A.st>>>(
-        N, dm, nl->atile[1], nl->type, nl->atom_struct, nl->L[1].off, nl->L[1].owner, nl->L[1].j, nl->L[1].rij, w.a,
-        w.Bs, w.S, w.Sd, w.Gd, w.wij);
+    if (int rc = launch_ang<C, true>(m, nl, A.st, w.a, w.Bs, w.S, w.Sd, w.Gd, w.wij)) return rc;
     stage("tangent_angular");
     if (int rc = fk.join(nl)) return rc;
     if (int rc = network_backward(m, nl, A.st)) return rc;
@@ -1114,6 +1281,10 @@ bool shape_supported(const Shape& s) {
 namespace {
 template <class C>
 int setup_shape() {
+  if (int rc = setup_ang<C, false, false>()) return rc;
+  if (int rc = setup_ang<C, false, true>()) return rc;
+  if (int rc = setup_ang<C, true, false>()) return rc;
+  if (int rc = setup_ang<C, true, true>()) return rc;
   GNEP_CUDA(cudaFuncSetAttribute(k_cgrad_ang<C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sizeof(CgSmem<C>)));
   GNEP_CUDA(cudaFuncSetAttribute(k_cgrad_ang<C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1178,14 +1349,14 @@ int cgrad_blocks(const gnep_nlist* nl) {
   return ntiles < cap ? (ntiles > 0 ? ntiles : 1) : cap;
 }
 
-// Tile limits of the angular sweeps: [0] descriptor sweep (kNptDesc channels
-// per thread, kChDesc pairs), [1] force, tangent and c-gradient sweeps (one
-// channel per thread, CH pairs).
+// Tile limits of the angular sweeps: [0] descriptor and tangent sweeps (one
+// warp per atom, chunks of 256 pairs: 32 atoms, 256 pairs), [1] force and
+// c-gradient sweeps (one thread per (atom, channel) in the force sweep, CH pairs).
 void angular_tile_limits(const Shape& s, int which, int* na, int* ch) {
   const int nq = s.nqr > s.nqa ? s.nqr : s.nqa;
   if (which == 0) {
-    *na = 128 / ((s.nqa + kNptDesc - 1) / kNptDesc);
-    *ch = kChDesc;
+    *na = 32;
+    *ch = AGeo<Sh<1, 1, 1, 1, 1, false>, false>::CHT;
   } else {
     *na = 128 / nq;
     *ch = CH;
@@ -1252,9 +1423,7 @@ int descriptors_static(const StepArgs& A, float* G) {
   // array needs no clearing between calls.
   k_desc_radial<C><<<blocks_for(N * RL, 128), 128, 0, A.st>>>((int)N, dm, nl->type, nl->L[0].off, nl->L[0].rij,
                                                               scratch, G);
-  k_desc_angular<C, kNptDesc, kChDesc><<<nl->natile[0], 128, 0, A.st>>>((int)N, dm, nl->atile[0], nl->type,
-                                                                         nl->L[1].off, nl->L[1].rij,
-                                                                         scratch + fr_padded, G);
+  if ((rc = launch_ang<C, false>(m, nl, A.st, nullptr, nullptr, nullptr, scratch + fr_padded, G, nullptr))) return rc;
   GNEP_CHECK_LAUNCH("descriptor sweep (static scratch)");
   return GNEP_OK;
 }
