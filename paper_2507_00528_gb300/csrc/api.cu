@@ -261,12 +261,30 @@ int gnep_compute_descriptor_scale(gnep_model* m, const gnep_nlist* nl_, void* st
 
 // --------------------------------------------------------------- batches
 
+// True when the host can read p directly (pageable or pinned host memory).
+static bool host_readable(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeUnregistered || a.type == cudaMemoryTypeHost;
+}
+
 static int load_batch(gnep_model* m, const gnep_batch* b, gnep_nlist* nl, cudaStream_t st) {
   const int S = b->n_struct, N = b->n_atoms;
-  std::vector<int> off(S + 1), typ(N > 0 ? N : 1);
-  GNEP_CUDA(cudaMemcpyAsync(off.data(), b->struct_off, sizeof(int) * (S + 1), cudaMemcpyDefault, st));
-  if (N > 0) GNEP_CUDA(cudaMemcpyAsync(typ.data(), b->type, sizeof(int) * N, cudaMemcpyDefault, st));
-  GNEP_CUDA(cudaStreamSynchronize(st));
+  std::vector<int> off_copy, typ_copy;
+  const int *off = b->struct_off, *typ = b->type;
+  const bool host = host_readable(b->struct_off) && (N == 0 || host_readable(b->type));
+  if (!host) {  // device arrays: bring them over for the checks
+    off_copy.resize(S + 1);
+    typ_copy.resize(N > 0 ? N : 1);
+    GNEP_CUDA(cudaMemcpyAsync(off_copy.data(), b->struct_off, sizeof(int) * (S + 1), cudaMemcpyDefault, st));
+    if (N > 0) GNEP_CUDA(cudaMemcpyAsync(typ_copy.data(), b->type, sizeof(int) * N, cudaMemcpyDefault, st));
+    GNEP_CUDA(cudaStreamSynchronize(st));
+    off = off_copy.data();
+    typ = typ_copy.data();
+  }
   if (off[0] != 0 || off[S] != N) return set_error(GNEP_ERR_INVALID_ARG, "struct_off must start at 0 and end at n_atoms");
   for (int s = 0; s < S; ++s)
     if (off[s + 1] <= off[s])
@@ -274,48 +292,59 @@ static int load_batch(gnep_model* m, const gnep_batch* b, gnep_nlist* nl, cudaSt
   for (int i = 0; i < N; ++i)
     if (typ[i] < 0 || typ[i] >= m->shape.ns) return set_error(GNEP_ERR_INVALID_ARG, "species index out of range");
   // the species grouping only changes with the species (a rebuild usually keeps them)
-  nl->types_changed = !(nl->host_types.size() == (size_t)N && std::equal(typ.begin(), typ.begin() + N,
-                                                                          nl->host_types.begin()));
-  if (nl->types_changed) nl->host_types.assign(typ.begin(), typ.begin() + N);
-  GNEP_CUDA(cudaMemcpyAsync(nl->struct_off, off.data(), sizeof(int) * (S + 1), cudaMemcpyHostToDevice, st));
+  nl->types_changed = !(nl->host_types.size() == (size_t)N && std::equal(typ, typ + N, nl->host_types.begin()));
+  if (nl->types_changed) nl->host_types.assign(typ, typ + N);
+  GNEP_CUDA(cudaMemcpyAsync(nl->struct_off, b->struct_off, sizeof(int) * (S + 1), cudaMemcpyDefault, st));
   if (N > 0) {
-    GNEP_CUDA(cudaMemcpyAsync(nl->type, typ.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+    GNEP_CUDA(cudaMemcpyAsync(nl->type, b->type, sizeof(int) * N, cudaMemcpyDefault, st));
     GNEP_CUDA(cudaMemcpyAsync(nl->pos, b->pos, sizeof(double) * 3 * (size_t)N, cudaMemcpyDefault, st));
   }
   GNEP_CUDA(cudaMemcpyAsync(nl->cell, b->cell, sizeof(double) * 9 * (size_t)S, cudaMemcpyDefault, st));
   return GNEP_OK;
 }
 
-// Greedy tiles of consecutive atoms with at most na atoms and ch angular pairs.
+// Greedy tiles of consecutive atoms with at most na atoms and ch angular pairs,
+// cut on the host from the angular offsets of the last list build and uploaded
+// from pinned staging (the upload overlaps the rest of the build).
 static int build_angular_tiles(gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
   const int N = nl->n_atoms;
-  std::vector<int> off(N + 1);
-  GNEP_CUDA(cudaMemcpyAsync(off.data(), nl->L[1].off, sizeof(int) * (N + 1), cudaMemcpyDeviceToHost, st));
-  GNEP_CUDA(cudaStreamSynchronize(st));
+  const std::vector<long long>& off = nl->host_aoff;
+  if (off.size() != (size_t)N + 1) return set_error(GNEP_ERR_CUDA, "angular offsets missing (internal error)");
+  if (!nl->tile_host || nl->tile_host_cap < 2 * ((int64_t)N + 1)) {
+    if (nl->tile_host) {
+      GNEP_CUDA(cudaEventSynchronize(nl->tile_ev));
+      cudaFreeHost(nl->tile_host);
+      nl->tile_host = nullptr;
+    }
+    GNEP_CUDA(cudaMallocHost(&nl->tile_host, sizeof(int) * 2 * ((size_t)N + 1)));
+    nl->tile_host_cap = 2 * ((int64_t)N + 1);
+  }
+  if (!nl->tile_ev) GNEP_CUDA(cudaEventCreateWithFlags(&nl->tile_ev, cudaEventDisableTiming));
+  GNEP_CUDA(cudaEventSynchronize(nl->tile_ev));  // the previous upload has left the staging
   for (int which = 0; which < 2; ++which) {
     int na = 0, ch = 0;
     angular_tile_limits(m->shape, which, &na, &ch);
     if (nl->tune.na[which] > 0 && nl->tune.na[which] < na) na = nl->tune.na[which];
     if (nl->tune.ch[which] > 0) ch = nl->tune.ch[which];
-    std::vector<int> t;
-    int i = 0;
+    int* t = nl->tile_host + which * ((size_t)N + 1);
+    int nt = 0, i = 0;
     while (i < N) {
-      t.push_back(i);
+      t[nt++] = i;
       int j = i + 1;
       while (j < N && j - i < na && off[j + 1] - off[i] <= ch) ++j;
       i = j;
     }
-    t.push_back(N);
-    if (!nl->atile[which] || nl->atile_cap[which] < (int64_t)t.size()) {  // at most N + 1 bounds
+    t[nt++] = N;
+    if (!nl->atile[which] || nl->atile_cap[which] < (int64_t)nt) {  // at most N + 1 bounds
       cudaFree(nl->atile[which]);
       nl->atile[which] = nullptr;
       GNEP_CUDA(cudaMalloc(&nl->atile[which], sizeof(int) * (size_t)(N + 1)));
       nl->atile_cap[which] = N + 1;
     }
-    GNEP_CUDA(cudaMemcpyAsync(nl->atile[which], t.data(), sizeof(int) * t.size(), cudaMemcpyHostToDevice, st));
-    nl->natile[which] = (int)t.size() - 1;
+    GNEP_CUDA(cudaMemcpyAsync(nl->atile[which], t, sizeof(int) * nt, cudaMemcpyHostToDevice, st));
+    nl->natile[which] = nt - 1;
   }
-  GNEP_CUDA(cudaStreamSynchronize(st));
+  GNEP_CUDA(cudaEventRecord(nl->tile_ev, st));
   return GNEP_OK;
 }
 
@@ -336,7 +365,13 @@ static int finish_build(gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
     }
   }
   if ((rc = alloc_workspace(m, nl))) return rc;
+  int herr = 0;
+  GNEP_CUDA(cudaMemcpyAsync(&herr, m->err, sizeof(int), cudaMemcpyDeviceToHost, st));
   GNEP_CUDA(cudaStreamSynchronize(st));
+  if (herr & kErrRevMissing) {
+    GNEP_CUDA(cudaMemset(m->err, 0, sizeof(int)));
+    return set_error(GNEP_ERR_INVALID_ARG, "neighbour lists are not symmetric (internal error)");
+  }
   return GNEP_OK;
 }
 
@@ -345,6 +380,11 @@ int gnep_nlist_destroy(gnep_nlist* nl) {
   cudaFree(nl->struct_off); cudaFree(nl->type); cudaFree(nl->pos); cudaFree(nl->cell);
   cudaFree(nl->atom_struct); cudaFree(nl->perm);
   cudaFree(nl->atile[0]); cudaFree(nl->atile[1]);
+  if (nl->tile_ev) {
+    cudaEventSynchronize(nl->tile_ev);
+    cudaEventDestroy(nl->tile_ev);
+  }
+  if (nl->tile_host) cudaFreeHost(nl->tile_host);
   if (nl->side) cudaStreamDestroy(nl->side);
   if (nl->fork_ev) cudaEventDestroy(nl->fork_ev);
   if (nl->join_ev) cudaEventDestroy(nl->join_ev);

@@ -439,6 +439,11 @@ int build_lists(gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
   GNEP_CUDA(cudaMemcpyAsync(hmax, maxc, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
   int herr = 0;
   GNEP_CUDA(cudaMemcpyAsync(&herr, m->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  // the angular offsets come back with the counts: the host cuts the angular
+  // tiles from them while the lists are compacted on the device
+  nl->host_aoff.resize((size_t)N + 1);
+  GNEP_CUDA(cudaMemcpyAsync(nl->host_aoff.data(), off1, sizeof(long long) * ((size_t)N + 1), cudaMemcpyDeviceToHost,
+                            st));
   GNEP_CUDA(cudaStreamSynchronize(st));
   if (herr & kErrUnwrapped) {
     cleanup();
@@ -490,13 +495,7 @@ int build_lists(gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
       k_reverse<<<blocks_for(P.n, 256), 256, 0, st>>>(P.n, P.off, P.j, P.owner, P.shift, P.rev, m->err);
   }
   GNEP_CHECK_LAUNCH("k_reverse");
-  cleanup();
-  GNEP_CUDA(cudaStreamSynchronize(st));
-  GNEP_CUDA(cudaMemcpy(&herr, m->err, sizeof(int), cudaMemcpyDeviceToHost));
-  if (herr & kErrRevMissing) {
-    GNEP_CUDA(cudaMemset(m->err, 0, sizeof(int)));
-    return set_error(GNEP_ERR_INVALID_ARG, "neighbour lists are not symmetric (internal error)");
-  }
+  cleanup();  // the reverse search sets kErrRevMissing, read at the end of the build
   return GNEP_OK;
 }
 
