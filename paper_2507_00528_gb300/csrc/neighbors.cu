@@ -150,7 +150,6 @@ struct ListParams {
 struct Slots {
   int cap[2];
   int* j[2];
-  float4* r[2];
   char4* sh[2];
 };
 
@@ -213,28 +212,28 @@ __global__ void __launch_bounds__(128) k_pairs(
             if (band1) in1 = d2 < lp.rc2[1];
           }
           if (!in0 && !in1) continue;
-          if (kFill || kStage) {
+          if (kStage) {  // r_ij is formed by the compaction, one thread per entry
+            if (in0 && c0 < sl.cap[0]) {
+              const size_t q = (size_t)i * sl.cap[0] + c0;
+              sl.j[0][q] = j;
+              sl.sh[0][q] = make_char4((signed char)na, (signed char)nb, (signed char)nc, 0);
+            }
+            if (in1 && c1 < sl.cap[1]) {
+              const size_t q = (size_t)i * sl.cap[1] + c1;
+              sl.j[1][q] = j;
+              sl.sh[1][q] = make_char4((signed char)na, (signed char)nb, (signed char)nc, 0);
+            }
+            c0 += in0;
+            c1 += in1;
+          } else if (kFill) {
             const float4 pjl = plo[j];
             const float rx = pair_component(pjh.x, pjl.x, pih.x, pil.x, na, nb, nc, Hh[0], Hl[0], Hh[3], Hl[3], Hh[6], Hl[6]);
             const float ry = pair_component(pjh.y, pjl.y, pih.y, pil.y, na, nb, nc, Hh[1], Hl[1], Hh[4], Hl[4], Hh[7], Hl[7]);
             const float rz = pair_component(pjh.z, pjl.z, pih.z, pil.z, na, nb, nc, Hh[2], Hl[2], Hh[5], Hl[5], Hh[8], Hl[8]);
             const float4 rv = make_float4(rx, ry, rz, pjh.w);
             const char4 sv = make_char4((signed char)na, (signed char)nb, (signed char)nc, 0);
-            if (kFill) {
-              if (in0) { j0[w0] = j; own0[w0] = i; r0[w0] = rv; sh0[w0] = sv; ++w0; }
-              if (in1) { j1[w1] = j; own1[w1] = i; r1[w1] = rv; sh1[w1] = sv; ++w1; }
-            } else {
-              if (in0 && c0 < sl.cap[0]) {
-                const size_t q = (size_t)i * sl.cap[0] + c0;
-                sl.j[0][q] = j; sl.r[0][q] = rv; sl.sh[0][q] = sv;
-              }
-              if (in1 && c1 < sl.cap[1]) {
-                const size_t q = (size_t)i * sl.cap[1] + c1;
-                sl.j[1][q] = j; sl.r[1][q] = rv; sl.sh[1][q] = sv;
-              }
-              c0 += in0;
-              c1 += in1;
-            }
+            if (in0) { j0[w0] = j; own0[w0] = i; r0[w0] = rv; sh0[w0] = sv; ++w0; }
+            if (in1) { j1[w1] = j; own1[w1] = i; r1[w1] = rv; sh1[w1] = sv; ++w1; }
           } else {
             c0 += in0;
             c1 += in1;
@@ -247,19 +246,30 @@ __global__ void __launch_bounds__(128) k_pairs(
   }
 }
 
-// Copies the per-atom slots into the CSR lists (thread per atom and slot).
+// Copies the per-atom slots into the CSR lists and forms r_ij (thread per atom
+// and slot, so the float-float arithmetic runs on dense lanes).
 __global__ void k_compact(int N, int cap, const int* __restrict__ cnt, const long long* __restrict__ off,
-                          const int* __restrict__ sj, const float4* __restrict__ sr, const char4* __restrict__ ssh,
-                          int* __restrict__ j, int* __restrict__ own, float4* __restrict__ r, char4* __restrict__ sh) {
+                          const int* __restrict__ sj, const char4* __restrict__ ssh,
+                          const int* __restrict__ atom_struct, const float* __restrict__ hsplit,
+                          const float4* __restrict__ phi, const float4* __restrict__ plo, int* __restrict__ j,
+                          int* __restrict__ own, float4* __restrict__ r, char4* __restrict__ sh) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= (int64_t)N * cap) return;
   const int i = (int)(g / cap), c = (int)(g % cap);
   if (c >= cnt[i]) return;
   const long long d = off[i] + c;
-  j[d] = sj[g];
+  const int jj = sj[g];
+  const char4 sv = ssh[g];
+  const float* Hs = hsplit + 18 * atom_struct[i];
+  const float4 pih = phi[i], pil = plo[i], pjh = phi[jj], pjl = plo[jj];
+  const int na = sv.x, nb = sv.y, nc = sv.z;
+  const float rx = pair_component(pjh.x, pjl.x, pih.x, pil.x, na, nb, nc, Hs[0], Hs[9], Hs[3], Hs[12], Hs[6], Hs[15]);
+  const float ry = pair_component(pjh.y, pjl.y, pih.y, pil.y, na, nb, nc, Hs[1], Hs[10], Hs[4], Hs[13], Hs[7], Hs[16]);
+  const float rz = pair_component(pjh.z, pjl.z, pih.z, pil.z, na, nb, nc, Hs[2], Hs[11], Hs[5], Hs[14], Hs[8], Hs[17]);
+  j[d] = jj;
   own[d] = i;
-  r[d] = sr[g];
-  sh[d] = ssh[g];
+  r[d] = make_float4(rx, ry, rz, pjh.w);
+  sh[d] = sv;
 }
 
 // Exclusive scan of int counts into int64 offsets: one block per 1024 items,
@@ -407,11 +417,9 @@ int build_lists(gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
   {
     const size_t n0 = (size_t)N * sl.cap[0], n1 = (size_t)N * sl.cap[1];
     char* slots = nullptr;
-    GNEP_CUDA(cudaMallocAsync(&slots, (n0 + n1) * (sizeof(int) + sizeof(float4) + sizeof(char4)), st));
+    GNEP_CUDA(cudaMallocAsync(&slots, (n0 + n1) * (sizeof(int) + sizeof(char4)), st));
     tmp.push_back(slots);
-    sl.r[0] = reinterpret_cast<float4*>(slots);
-    sl.r[1] = sl.r[0] + n0;
-    sl.j[0] = reinterpret_cast<int*>(sl.r[1] + n1);
+    sl.j[0] = reinterpret_cast<int*>(slots);
     sl.j[1] = sl.j[0] + n0;
     sl.sh[0] = reinterpret_cast<char4*>(sl.j[1] + n1);
     sl.sh[1] = sl.sh[0] + n0;
@@ -478,8 +486,9 @@ int build_lists(gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
       const int64_t nt = (int64_t)N * sl.cap[L];
       if (nt > 0)
         k_compact<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(N, sl.cap[L], L == 0 ? cnt0 : cnt1,
-                                                                L == 0 ? off0 : off1, sl.j[L], sl.r[L], sl.sh[L],
-                                                                P.j, P.owner, P.rij, P.shift);
+                                                                L == 0 ? off0 : off1, sl.j[L], sl.sh[L],
+                                                                nl->atom_struct, hsplit, phi, plo, P.j, P.owner,
+                                                                P.rij, P.shift);
     }
     GNEP_CHECK_LAUNCH("k_compact");
   } else {
