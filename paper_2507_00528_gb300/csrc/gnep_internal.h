@@ -41,7 +41,7 @@ struct PairList {
   int* off = nullptr;      // [N+1]
   int* j = nullptr;        // [n] neighbour (global atom index)
   int* owner = nullptr;    // [n] central atom i
-  int* rev = nullptr;      // [n] index of (j, i, -shift)
+  int* rev = nullptr;      // [n] index of (j, i, -shift) (angular list only)
   float4* rij = nullptr;   // [n] r_ij (x, y, z), w = species of j (as float)
   char4* shift = nullptr;  // [n] image (na, nb, nc, 0)
 };

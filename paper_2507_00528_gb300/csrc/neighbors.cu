@@ -141,17 +141,23 @@ struct ListParams {
   float reject2;     // max(hi2): candidates above it are outside both
 };
 
-// One thread per central atom walks every (j, image) of its structure in
-// canonical order.  kMode 0 counts; kMode 1 writes the CSR lists at the
-// scanned offsets; kMode 2 counts and writes each atom's first cap entries
-// into fixed per-atom slots (one pass; the slots are then compacted).  All
-// modes take the same decisions (FP32 away from the cut-offs, FP64 within the
-// band).
+// One warp per central atom i.  Lane l tests the neighbours j = a0 + l,
+// a0 + l + 32, ...: in each round of 32 consecutive j every lane walks the
+// images of its j in lexicographic order, and the warp places the accepted
+// entries by an exclusive scan of the per-lane counts, so each list comes out
+// in canonical order (j ascending, then image).  kMode 1 writes the CSR lists
+// at the scanned offsets; kMode 2 counts and writes each atom's first cap
+// entries into its slots (the slots are then compacted).  Both modes take the
+// same decisions (FP32 away from the cut-offs, FP64 within the band).  A lane
+// keeps up to kBuf accepted images of its j in a packed register; a round in
+// which some lane accepts more walks the images again to place them.
 struct Slots {
   int cap[2];
   int* j[2];
   char4* sh[2];
 };
+
+constexpr int kBuf = 4;
 
 template <int kMode>
 __global__ void __launch_bounds__(128) k_pairs(
@@ -163,86 +169,130 @@ __global__ void __launch_bounds__(128) k_pairs(
     int* __restrict__ j0, int* __restrict__ own0, float4* __restrict__ r0, char4* __restrict__ sh0,
     int* __restrict__ j1, int* __restrict__ own1, float4* __restrict__ r1, char4* __restrict__ sh1, Slots sl) {
   constexpr bool kFill = kMode == 1;
-  constexpr bool kStage = kMode == 2;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
+  const int i = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= N) return;  // the whole warp
   const int s = atom_struct[i];
   const int a0 = struct_off[s], a1 = struct_off[s + 1];
   float Hh[9], Hl[9];
 #pragma unroll
   for (int q = 0; q < 9; ++q) {
     Hh[q] = hsplit[18 * s + q];
-    Hl[q] = hsplit[18 * s + 9 + q];
+    Hl[q] = kFill ? hsplit[18 * s + 9 + q] : 0.f;
   }
   const float4 pih = phi[i], pil = plo[i];
   const int ka = krange[3 * s], kb = krange[3 * s + 1], kc = krange[3 * s + 2];
-  int c0 = 0, c1 = 0;
-  long long w0 = kFill ? off0[i] : 0, w1 = kFill ? off1[i] : 0;
+  const bool packable = ka <= 7 && kb <= 7 && kc <= 7;  // image indices fit 4 bits
   // |r_j + n.H - r_i| >= |df_x + n_x| w_x, so only shifts with |df_x + n_x| < rc / w_x
   // (with a margin far above FP32 rounding) can pass the test below.
   const float4 fi = frac[i];
   const float t0 = tw[3 * s] + 1e-3f, t1 = tw[3 * s + 1] + 1e-3f, t2 = tw[3 * s + 2] + 1e-3f;
-  for (int j = a0; j < a1; ++j) {
-    const float4 pjh = phi[j];
+  int base0 = 0, base1 = 0;
+  for (int jb = a0; jb < a1; jb += 32) {
+    const int j = jb + lane;
+    const bool vj = j < a1;
+    const float4 pjh = vj ? phi[j] : pih;
+    const float4 fj = vj ? frac[j] : fi;
     const float dj[3] = {pjh.x - pih.x, pjh.y - pih.y, pjh.z - pih.z};
-    const float4 fj = frac[j];
     const float dfa = fj.x - fi.x, dfb = fj.y - fi.y, dfc = fj.z - fi.z;
-    const int alo = max(-ka, (int)ceilf(-t0 - dfa)), ahi = min(ka, (int)floorf(t0 - dfa));
+    const int alo = max(-ka, (int)ceilf(-t0 - dfa)), ahi = vj ? min(ka, (int)floorf(t0 - dfa)) : alo - 1;
     const int blo = max(-kb, (int)ceilf(-t1 - dfb)), bhi = min(kb, (int)floorf(t1 - dfb));
     const int clo = max(-kc, (int)ceilf(-t2 - dfc)), chi = min(kc, (int)floorf(t2 - dfc));
+    // the list decisions for image n of this lane's j
+    auto decide = [&](int na, int nb, int nc, bool& in0, bool& in1) {
+      in0 = in1 = false;
+      if (j == i && na == 0 && nb == 0 && nc == 0) return;
+      const float fx = dj[0] + ((float)na * Hh[0] + (float)nb * Hh[3] + (float)nc * Hh[6]);
+      const float fy = dj[1] + ((float)na * Hh[1] + (float)nb * Hh[4] + (float)nc * Hh[7]);
+      const float fz = dj[2] + ((float)na * Hh[2] + (float)nb * Hh[5] + (float)nc * Hh[8]);
+      const float d2f = fx * fx + fy * fy + fz * fz;
+      if (d2f > lp.reject2) return;
+      in0 = d2f < lp.lo2[0];
+      in1 = d2f < lp.lo2[1];
+      const bool band0 = !in0 && d2f <= lp.hi2[0], band1 = !in1 && d2f <= lp.hi2[1];
+      if (band0 || band1) {  // near a cut-off: the FP64 decision
+        const double* Hd = cell + 9 * s;
+        const double H[9] = {Hd[0], Hd[1], Hd[2], Hd[3], Hd[4], Hd[5], Hd[6], Hd[7], Hd[8]};
+        const double pi[3] = {pos[3 * (size_t)i], pos[3 * (size_t)i + 1], pos[3 * (size_t)i + 2]};
+        const double pj[3] = {pos[3 * (size_t)j], pos[3 * (size_t)j + 1], pos[3 * (size_t)j + 2]};
+        double d[3];
+        const double d2 = pair_d2_exact(H, pi, pj, na, nb, nc, d);
+        if (band0) in0 = d2 < lp.rc2[0];
+        if (band1) in1 = d2 < lp.rc2[1];
+      }
+    };
+    // places one accepted entry at the next positions of its lists
+    auto put = [&](int na, int nb, int nc, bool in0, bool in1, int& w0, int& w1) {
+      const char4 sv = make_char4((signed char)na, (signed char)nb, (signed char)nc, 0);
+      if (kFill) {
+        const float4 pjl = plo[j];
+        const float rx = pair_component(pjh.x, pjl.x, pih.x, pil.x, na, nb, nc, Hh[0], Hl[0], Hh[3], Hl[3], Hh[6], Hl[6]);
+        const float ry = pair_component(pjh.y, pjl.y, pih.y, pil.y, na, nb, nc, Hh[1], Hl[1], Hh[4], Hl[4], Hh[7], Hl[7]);
+        const float rz = pair_component(pjh.z, pjl.z, pih.z, pil.z, na, nb, nc, Hh[2], Hl[2], Hh[5], Hl[5], Hh[8], Hl[8]);
+        const float4 rv = make_float4(rx, ry, rz, pjh.w);
+        if (in0) { const long long d = off0[i] + w0; j0[d] = j; own0[d] = i; r0[d] = rv; sh0[d] = sv; }
+        if (in1) { const long long d = off1[i] + w1; j1[d] = j; own1[d] = i; r1[d] = rv; sh1[d] = sv; }
+      } else {  // r_ij is formed by the compaction
+        if (in0 && w0 < sl.cap[0]) {
+          const size_t q = (size_t)i * sl.cap[0] + w0;
+          sl.j[0][q] = j;
+          sl.sh[0][q] = sv;
+        }
+        if (in1 && w1 < sl.cap[1]) {
+          const size_t q = (size_t)i * sl.cap[1] + w1;
+          sl.j[1][q] = j;
+          sl.sh[1][q] = sv;
+        }
+      }
+      w0 += in0;
+      w1 += in1;
+    };
+    int n0 = 0, n1 = 0, nacc = 0;
+    unsigned long long buf = 0;
     for (int na = alo; na <= ahi; ++na)
       for (int nb = blo; nb <= bhi; ++nb)
         for (int nc = clo; nc <= chi; ++nc) {
-          if (j == i && na == 0 && nb == 0 && nc == 0) continue;
-          const float fx = dj[0] + ((float)na * Hh[0] + (float)nb * Hh[3] + (float)nc * Hh[6]);
-          const float fy = dj[1] + ((float)na * Hh[1] + (float)nb * Hh[4] + (float)nc * Hh[7]);
-          const float fz = dj[2] + ((float)na * Hh[2] + (float)nb * Hh[5] + (float)nc * Hh[8]);
-          const float d2f = fx * fx + fy * fy + fz * fz;
-          if (d2f > lp.reject2) continue;
-          bool in0 = d2f < lp.lo2[0], in1 = d2f < lp.lo2[1];
-          const bool band0 = !in0 && d2f <= lp.hi2[0], band1 = !in1 && d2f <= lp.hi2[1];
-          if (band0 || band1) {  // near a cut-off: the FP64 decision
-            const double* Hd = cell + 9 * s;
-            const double H[9] = {Hd[0], Hd[1], Hd[2], Hd[3], Hd[4], Hd[5], Hd[6], Hd[7], Hd[8]};
-            const double pi[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
-            const double pj[3] = {pos[3 * j], pos[3 * j + 1], pos[3 * j + 2]};
-            double d[3];
-            const double d2 = pair_d2_exact(H, pi, pj, na, nb, nc, d);
-            if (band0) in0 = d2 < lp.rc2[0];
-            if (band1) in1 = d2 < lp.rc2[1];
-          }
+          bool in0, in1;
+          decide(na, nb, nc, in0, in1);
           if (!in0 && !in1) continue;
-          if (kStage) {  // r_ij is formed by the compaction, one thread per entry
-            if (in0 && c0 < sl.cap[0]) {
-              const size_t q = (size_t)i * sl.cap[0] + c0;
-              sl.j[0][q] = j;
-              sl.sh[0][q] = make_char4((signed char)na, (signed char)nb, (signed char)nc, 0);
-            }
-            if (in1 && c1 < sl.cap[1]) {
-              const size_t q = (size_t)i * sl.cap[1] + c1;
-              sl.j[1][q] = j;
-              sl.sh[1][q] = make_char4((signed char)na, (signed char)nb, (signed char)nc, 0);
-            }
-            c0 += in0;
-            c1 += in1;
-          } else if (kFill) {
-            const float4 pjl = plo[j];
-            const float rx = pair_component(pjh.x, pjl.x, pih.x, pil.x, na, nb, nc, Hh[0], Hl[0], Hh[3], Hl[3], Hh[6], Hl[6]);
-            const float ry = pair_component(pjh.y, pjl.y, pih.y, pil.y, na, nb, nc, Hh[1], Hl[1], Hh[4], Hl[4], Hh[7], Hl[7]);
-            const float rz = pair_component(pjh.z, pjl.z, pih.z, pil.z, na, nb, nc, Hh[2], Hl[2], Hh[5], Hl[5], Hh[8], Hl[8]);
-            const float4 rv = make_float4(rx, ry, rz, pjh.w);
-            const char4 sv = make_char4((signed char)na, (signed char)nb, (signed char)nc, 0);
-            if (in0) { j0[w0] = j; own0[w0] = i; r0[w0] = rv; sh0[w0] = sv; ++w0; }
-            if (in1) { j1[w1] = j; own1[w1] = i; r1[w1] = rv; sh1[w1] = sv; ++w1; }
-          } else {
-            c0 += in0;
-            c1 += in1;
-          }
+          if (packable && nacc < kBuf)
+            buf |= (unsigned long long)((na + 8) | (nb + 8) << 4 | (nc + 8) << 8 | (int)in0 << 12 | (int)in1 << 13)
+                   << (16 * nacc);
+          ++nacc;
+          n0 += in0;
+          n1 += in1;
         }
+    int p0 = n0, p1 = n1;  // inclusive scan over the lanes (j order)
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u0 = __shfl_up_sync(0xffffffffu, p0, o), u1 = __shfl_up_sync(0xffffffffu, p1, o);
+      if (lane >= o) {
+        p0 += u0;
+        p1 += u1;
+      }
+    }
+    const int tot0 = __shfl_sync(0xffffffffu, p0, 31), tot1 = __shfl_sync(0xffffffffu, p1, 31);
+    int w0 = base0 + p0 - n0, w1 = base1 + p1 - n1;
+    if (!__any_sync(0xffffffffu, nacc > kBuf || (nacc > 0 && !packable))) {
+      for (int e = 0; e < nacc; ++e) {
+        const int v = (int)((buf >> (16 * e)) & 0xffffu);
+        put((v & 15) - 8, ((v >> 4) & 15) - 8, ((v >> 8) & 15) - 8, (v >> 12) & 1, (v >> 13) & 1, w0, w1);
+      }
+    } else {  // walk the images again, placing each accepted one
+      for (int na = alo; na <= ahi; ++na)
+        for (int nb = blo; nb <= bhi; ++nb)
+          for (int nc = clo; nc <= chi; ++nc) {
+            bool in0, in1;
+            decide(na, nb, nc, in0, in1);
+            if (in0 || in1) put(na, nb, nc, in0, in1, w0, w1);
+          }
+    }
+    base0 += tot0;
+    base1 += tot1;
   }
-  if (!kFill) {
-    cnt0[i] = c0;
-    cnt1[i] = c1;
+  if (!kFill && lane == 0) {
+    cnt0[i] = base0;
+    cnt1[i] = base1;
   }
 }
 
@@ -424,7 +474,7 @@ int build_lists(gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
     sl.sh[0] = reinterpret_cast<char4*>(sl.j[1] + n1);
     sl.sh[1] = sl.sh[0] + n0;
   }
-  k_pairs<2><<<blocks_for(N, 128), 128, 0, st>>>(
+  k_pairs<2><<<blocks_for((int64_t)N * 32, 128), 128, 0, st>>>(
       N, nl->struct_off, nl->atom_struct, nl->pos, nl->cell, kr, tw, hsplit, frac, phi, plo, lp, cnt0, cnt1,
       nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, sl);
   GNEP_CHECK_LAUNCH("k_pairs<stage>");
@@ -471,7 +521,7 @@ int build_lists(gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
       const int64_t cap = tot[L] > 0 ? tot[L] + tot[L] / 8 + 64 : 64;  // headroom for rebuilds (MD)
       GNEP_CUDA(cudaMalloc(&P.j, sizeof(int) * cap));
       GNEP_CUDA(cudaMalloc(&P.owner, sizeof(int) * cap));
-      GNEP_CUDA(cudaMalloc(&P.rev, sizeof(int) * cap));
+      if (L == 1) GNEP_CUDA(cudaMalloc(&P.rev, sizeof(int) * cap));  // the force sweep pairs angular entries
       GNEP_CUDA(cudaMalloc(&P.rij, sizeof(float4) * cap));
       GNEP_CUDA(cudaMalloc(&P.shift, sizeof(char4) * cap));
       P.cap = cap;
@@ -492,14 +542,14 @@ int build_lists(gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
     }
     GNEP_CHECK_LAUNCH("k_compact");
   } else {
-    k_pairs<1><<<blocks_for(N, 128), 128, 0, st>>>(
+    k_pairs<1><<<blocks_for((int64_t)N * 32, 128), 128, 0, st>>>(
         N, nl->struct_off, nl->atom_struct, nl->pos, nl->cell, kr, tw, hsplit, frac, phi, plo, lp, nullptr, nullptr,
         off0, off1, nl->L[0].j, nl->L[0].owner, nl->L[0].rij, nl->L[0].shift, nl->L[1].j, nl->L[1].owner,
         nl->L[1].rij, nl->L[1].shift, sl);
     GNEP_CHECK_LAUNCH("k_pairs<fill>");
   }
-  for (int L = 0; L < 2; ++L) {
-    PairList& P = nl->L[L];
+  {  // reverse entries of the angular list (the radial force terms need none)
+    PairList& P = nl->L[1];
     if (P.n > 0)
       k_reverse<<<blocks_for(P.n, 256), 256, 0, st>>>(P.n, P.off, P.j, P.owner, P.shift, P.rev, m->err);
   }

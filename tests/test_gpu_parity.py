@@ -297,3 +297,26 @@ def test_skewed_cells_many_images_and_largest_structure():
     _, eso, fo, wo = O.forward(c.cfg, c.P64, c.s64, b.subset([2]))
     assert abs(Es[2] - eso[0]) <= E_TOL * abs(eso[0])
     assert rel_l2(F[26:], fo) < F_TOL and rel_l2(W[2], wo[0]) < F_TOL
+
+
+def test_dense_image_lattice_overflows_the_slots():
+    """A one-atom cubic cell of 2.3 A holds about 118 images within the radial
+    cut-off, more than the 96 per-atom slots of the one-pass search: the lists
+    are then written by the counting pass's fill fallback, and must still equal
+    the oracle's (Eq. 2), with energies and forces to match."""
+    cells = np.stack([np.eye(3) * 2.3, np.diag([3.4, 3.3, 3.6])])
+    pos = np.array([[0.4, 0.7, 1.1], [0.2, 0.3, 0.1], [1.9, 1.6, 1.7]])
+    b = synth.Batch(np.array([0, 1, 3], dtype=np.int32), pos, np.array([1, 0, 1], dtype=np.int32), cells)
+    c = Case("nmax4_basis8_h30", b, labels=False)
+    for which, rc in ((0, 7.0), (1, 4.0)):
+        off, j, sh = c.nl.export(which)
+        ooff, oj, osh = O.neighbors(b, rc)
+        assert which == 1 or off[1] - off[0] > 96
+        np.testing.assert_array_equal(off, ooff)
+        np.testing.assert_array_equal(j, oj)
+        np.testing.assert_array_equal(sh, osh)
+    Ea, Es, F, W = (t.double().cpu().numpy() for t in c.m.forward(c.nl))
+    Eao, Eso, Fo, Wo = O.forward(c.cfg, c.P64, c.s64, b)
+    assert rel_l2(Ea, Eao) < E_TOL
+    assert rel_l2(W, Wo) < F_TOL
+    assert np.abs(F - Fo).max() <= F_TOL * max(np.abs(Fo).max(), 1.0)
