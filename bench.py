@@ -76,6 +76,28 @@ def algo_flops(nqr=9, kr=13, nqa=9, ka=13, ns=2, H=50, fb=True, N=1, PR=1, PA=1)
     return f
 
 
+def algo_bytes(nqr=9, kr=13, nqa=9, ka=13, ns=2, H=50, fb=True, N=1, PR=1, PA=1, HP=64):
+    """Compulsory DRAM bytes per launch of each kernel: every input the
+    kernel needs read once and every output written once (FP32 arrays, int32
+    indices, float4 pair vectors), nothing re-read."""
+    D = nqr + 4 * nqa + (nqa if fb else 0)
+    A = nqa * 24                   # S_nlm per atom
+    FRn = ns * kr
+    ang_cols = 4 * nqa + (nqa if fb else 0)
+    b = {}
+    b["desc_radial"] = 4 * (PR * 4 + 2 * N + N * FRn + N * nqr)
+    b["desc_angular"] = 4 * (PA * 4 + 2 * N + N * A + N * ang_cols)
+    b["mlp_fwd"] = 4 * N * (D + D + 1 + HP + FRn)
+    b["force_angular"] = 4 * (PA * 5 + N * A + N * D + PA * 4)
+    b["force_atoms"] = 4 * (PR * 5 + N * FRn + N + PA * 9 + 9 * N)
+    b["tangent_radial"] = 4 * (PR * 5 + 4 * N + N * FRn + N * nqr)
+    b["tangent_angular"] = 4 * (PA * 6 + 4 * N + N * A + N * A + N * ang_cols + PA * 4)
+    b["mlp_bwd"] = 4 * N * (2 * D + HP + D + 2)
+    b["cgrad"] = 4 * (N * (2 * A + 2 * (ang_cols + nqr)) + PA * 8 + N)
+    b["cgrad_radial"] = 4 * N * (2 * nqr + 2 * FRn + 1)
+    return b
+
+
 # ----------------------------------------------------------------- helpers
 
 def csrc_sha() -> str:
@@ -364,11 +386,18 @@ def run_gnep(args):
         for name, ms in student_profile(student, nl, y, gnep):
             stage_ms[name] = stage_ms.get(name, 0.0) + ms / reps
     fl = algo_flops(N=n_atoms, PR=PR, PA=PA)
+    by = algo_bytes(N=n_atoms, PR=PR, PA=PA)
     kernels = {k: v for k, v in stage_ms.items() if k in fl}
     dom = max(kernels, key=kernels.get)
     peaks = measured_peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)  # GB/s, measured copy (else the fallback figure)
+    # the bound is the resource that limits at speed of light: compulsory bytes
+    # at the measured copy bandwidth, or the formulation's FP32 work at the ALU peak
+    t_hbm = by[dom] / (hbm_peak * 1e9)
+    t_alu = fl[dom] / (fp32_peak * 1e12)
+    achieved_gbs = by[dom] / (stage_ms[dom] / 1e3) / 1e9
     achieved = fl[dom] / (stage_ms[dom] / 1e3) / 1e12
     step_flops = sum(fl.values())
     clocks = clk.summary()
@@ -421,20 +450,34 @@ def run_gnep(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp32": "f32", "tf32": "tf32 network / f32 sweeps", "bf16": "bf16 network / f32 sweeps"}[
-            args.precision],
+        "dtype": {"fp32": "f32 (sweep contractions as split-TF32 tensor-core products, FP32-accurate)",
+                  "tf32": "tf32 network / split-TF32 sweep contractions / f32 geometry",
+                  "bf16": "bf16 network / tf32 sweep contractions / f32 geometry"}[args.precision],
         "data": "synthetic",
         "config": dict(WORKLOAD, atoms_per_step_per_gpu=n_atoms, radial_pairs=PR, angular_pairs=PA,
                        graph=world == 1, precision=args.precision, l2="flushed between steps (256 MB write)",
                        parallelism=f"dp{world}" + (" (FP64 gradient all-reduce per step)" if world > 1 else ""),
                        neighbor_build_ms=round(nbuild_ms, 3)),
-        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32_peak,
-                     "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                     "traffic": committed_traffic(dom),
-                     "peak_source": f"FP32 {props.multi_processor_count} SMs x 128 lanes x 2 x {sm_max:.0f} MHz",
-                     "kernel_ms": stage_ms[dom], "kernel_algo_flops": fl[dom],
-                     "step_algo_gflop": step_flops / 1e9,
-                     "step_achieved_tflops": step_flops / (total_ms / args.steps / 1e3) / 1e12},
+        "roofline": ({"bound": "hbm", "kernel": dom, "achieved": achieved_gbs, "peak": hbm_peak,
+                      "unit": "GB/s", "frac": achieved_gbs / hbm_peak,
+                      "traffic": committed_traffic(dom),
+                      "peak_source": ("MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks
+                                      else "fallback 6.8 TB/s (of fallback)"),
+                      "kernel_ms": stage_ms[dom], "kernel_algo_bytes": by[dom],
+                      "kernel_algo_flops": fl[dom], "alu_frac": achieved / fp32_peak,
+                      "sol_us": {"hbm": t_hbm * 1e6, "fp32_alu": t_alu * 1e6},
+                      "step_algo_gflop": step_flops / 1e9,
+                      "step_achieved_tflops": step_flops / (total_ms / args.steps / 1e3) / 1e12}
+                     if t_hbm >= t_alu else
+                     {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32_peak,
+                      "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                      "traffic": committed_traffic(dom),
+                      "peak_source": f"FP32 {props.multi_processor_count} SMs x 128 lanes x 2 x {sm_max:.0f} MHz",
+                      "kernel_ms": stage_ms[dom], "kernel_algo_bytes": by[dom],
+                      "kernel_algo_flops": fl[dom], "hbm_frac": achieved_gbs / hbm_peak,
+                      "sol_us": {"hbm": t_hbm * 1e6, "fp32_alu": t_alu * 1e6},
+                      "step_algo_gflop": step_flops / 1e9,
+                      "step_achieved_tflops": step_flops / (total_ms / args.steps / 1e3) / 1e12}),
         "kernel_ms": {k: round(v, 5) for k, v in stage_ms.items()},
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -308,8 +308,9 @@ static int load_batch(gnep_model* m, const gnep_batch* b, gnep_nlist* nl, cudaSt
 // from pinned staging (the upload overlaps the rest of the build).
 static int build_angular_tiles(gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
   const int N = nl->n_atoms;
-  const std::vector<long long>& off = nl->host_aoff;
-  if (off.size() != (size_t)N + 1) return set_error(GNEP_ERR_CUDA, "angular offsets missing (internal error)");
+  const long long* off = nl->host_aoff;
+  if (!off || nl->host_aoff_n != (int64_t)N + 1)
+    return set_error(GNEP_ERR_CUDA, "angular offsets missing (internal error)");
   if (!nl->tile_host || nl->tile_host_cap < 2 * ((int64_t)N + 1)) {
     if (nl->tile_host) {
       GNEP_CUDA(cudaEventSynchronize(nl->tile_ev));
@@ -385,6 +386,7 @@ int gnep_nlist_destroy(gnep_nlist* nl) {
     cudaEventDestroy(nl->tile_ev);
   }
   if (nl->tile_host) cudaFreeHost(nl->tile_host);
+  if (nl->host_aoff) cudaFreeHost(nl->host_aoff);
   if (nl->side) cudaStreamDestroy(nl->side);
   if (nl->fork_ev) cudaEventDestroy(nl->fork_ev);
   if (nl->join_ev) cudaEventDestroy(nl->join_ev);

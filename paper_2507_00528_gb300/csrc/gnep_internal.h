@@ -100,7 +100,8 @@ struct gnep_nlist {
   // radial and angular sweeps of one phase), with its fork / join events.
   std::vector<int> host_types;  // species of the last build (host copy)
   bool types_changed = true;
-  std::vector<long long> host_aoff;  // angular list offsets of the last build (host copy, for the tiles)
+  long long* host_aoff = nullptr;    // pinned: angular list offsets of the last build (for the tiles)
+  int64_t host_aoff_cap = 0, host_aoff_n = 0;
   int* tile_host = nullptr;          // pinned staging of the tile bounds (both tile sets)
   int64_t tile_host_cap = 0;
   cudaEvent_t tile_ev = nullptr;     // the last upload from tile_host

@@ -499,9 +499,15 @@ int build_lists(gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
   GNEP_CUDA(cudaMemcpyAsync(&herr, m->err, sizeof(int), cudaMemcpyDeviceToHost, st));
   // the angular offsets come back with the counts: the host cuts the angular
   // tiles from them while the lists are compacted on the device
-  nl->host_aoff.resize((size_t)N + 1);
-  GNEP_CUDA(cudaMemcpyAsync(nl->host_aoff.data(), off1, sizeof(long long) * ((size_t)N + 1), cudaMemcpyDeviceToHost,
-                            st));
+  if (nl->host_aoff_cap < (int64_t)N + 1) {
+    if (nl->host_aoff) cudaFreeHost(nl->host_aoff);
+    nl->host_aoff = nullptr;
+    nl->host_aoff_cap = 0;
+    GNEP_CUDA(cudaMallocHost(&nl->host_aoff, sizeof(long long) * ((size_t)N + 1)));
+    nl->host_aoff_cap = (int64_t)N + 1;
+  }
+  nl->host_aoff_n = (int64_t)N + 1;
+  GNEP_CUDA(cudaMemcpyAsync(nl->host_aoff, off1, sizeof(long long) * ((size_t)N + 1), cudaMemcpyDeviceToHost, st));
   GNEP_CUDA(cudaStreamSynchronize(st));
   if (herr & kErrUnwrapped) {
     cleanup();
