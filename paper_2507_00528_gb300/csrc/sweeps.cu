@@ -98,14 +98,54 @@ __device__ __forceinline__ void lane_reduce(float (&acc)[NS][K]) {
       for (int k = 0; k < K; ++k) acc[s][k] += __shfl_xor_sync(0xffffffffu, acc[s][k], o);
 }
 
-// Harmonics on the unit vector and, for a direction w, the directional
-// derivatives D_lm = grad_d B_lm . w = (I - u u^T) grad p(u) . w / r (B9.2).
+// Harmonics on the unit vector u and, for a direction w, the directional
+// derivatives D_lm = grad_d B_lm . w (B9.2).  Each B_lm is the degree-l
+// homogeneous polynomial h_lm (the r = 1 forms with 1 read as r^2) on u, so
+// grad_d B_lm = (grad h_lm(u) - l h_lm(u) u) / r (Euler's relation u . grad h =
+// l h removes the radial part), and grad h_lm(u) . w is the derivative of h_lm
+// along w, evaluated here with dx = w_x, dy = w_y, dz = w_z, d(r^2) = 2 u . w.
 __device__ __forceinline__ void harmonics_dir(float x, float y, float z, float rinv, float wx, float wy, float wz,
                                               float (&B)[NLM], float (&Dd)[NLM]) {
-  float gx[NLM], gy[NLM], gz[NLM];
-  harmonics_grad(x, y, z, 1.f, B, gx, gy, gz);  // projected gradient, not yet divided by r
+  harmonics(x, y, z, B);
+  const float ru = x * wx + y * wy + z * wz;  // u . w; d(r^2) = 2 ru
+  const float x2 = x * x, y2 = y * y, z2 = z * z;
+  const float dx2 = 2.f * x * wx, dy2 = 2.f * y * wy, dz2 = 2.f * z * wz, dr2 = 2.f * ru;
+  float d[NLM];
+  // l = 1
+  d[0] = wz; d[1] = wx; d[2] = wy;
+  // l = 2
+  d[3] = 3.f * dz2 - dr2;
+  d[4] = wx * z + x * wz;
+  d[5] = wy * z + y * wz;
+  d[6] = dx2 - dy2;
+  d[7] = 2.f * (wx * y + x * wy);
+  // l = 3: p3 = 5 z^2 - r^2
+  const float p3 = 5.f * z2 - 1.f, dp3 = 5.f * dz2 - dr2;
+  d[8] = (5.f * dz2 - 3.f * dr2) * z + (5.f * z2 - 3.f) * wz;
+  d[9] = dp3 * x + p3 * wx;
+  d[10] = dp3 * y + p3 * wy;
+  const float xmy = x2 - y2, dxmy = dx2 - dy2;
+  d[11] = dxmy * z + xmy * wz;
+  d[12] = 2.f * ((wx * y + x * wy) * z + x * y * wz);
+  const float a13 = x2 - 3.f * y2, da13 = dx2 - 3.f * dy2;
+  const float a14 = 3.f * x2 - y2, da14 = 3.f * dx2 - dy2;
+  d[13] = da13 * x + a13 * wx;
+  d[14] = da14 * y + a14 * wy;
+  // l = 4: w4 = (7 z^2 - 3 r^2) z, p4 = 7 z^2 - r^2
+  const float w4 = (7.f * z2 - 3.f) * z, dw4 = (7.f * dz2 - 3.f * dr2) * z + (7.f * z2 - 3.f) * wz;
+  const float p4 = 7.f * z2 - 1.f, dp4 = 7.f * dz2 - dr2;
+  d[15] = 35.f * 2.f * z2 * dz2 - 30.f * (dz2 + z2 * dr2) + 3.f * 2.f * dr2;
+  d[16] = dw4 * x + w4 * wx;
+  d[17] = dw4 * y + w4 * wy;
+  d[18] = dp4 * xmy + p4 * dxmy;
+  const float xy = x * y, dxy = wx * y + x * wy;
+  d[19] = 2.f * (dp4 * xy + p4 * dxy);
+  d[20] = da13 * x * z + a13 * (wx * z + x * wz);
+  d[21] = da14 * y * z + a14 * (wy * z + y * wz);
+  d[22] = 2.f * x2 * dx2 - 6.f * (dx2 * y2 + x2 * dy2) + 2.f * y2 * dy2;
+  d[23] = 4.f * (dxy * xmy + xy * dxmy);
 #pragma unroll
-  for (int q = 0; q < NLM; ++q) Dd[q] = (gx[q] * wx + gy[q] * wy + gz[q] * wz) * rinv;
+  for (int q = 0; q < NLM; ++q) Dd[q] = (d[q] - (float)lm_l(q) * B[q] * ru) * rinv;
 }
 
 }  // namespace
@@ -795,30 +835,29 @@ template <class C, bool TAN>
 struct AngSmem {
   AGeo<C, TAN> geo;
   float c[C::NS * C::NS][16][kCS];  // C^{IJ}[n][k], zero-padded to 16 x 16
-  float clm[NLM];
   int off[kAngMaxAtoms + 1];
   int type[kAngMaxAtoms];
 };
 
 // Lane (g, t) of an accumulator holds S[n][q] for n = g + 8h (h = r / 2) and
-// q = 8 nt + 2t + (r mod 2).  Sum over the lane's q of C_q x_q y_q per degree l,
-// completed over the four lanes of the row.
-__device__ __forceinline__ void lsum_rows(const float (&x)[3][4], const float (&y)[3][4], const float* clm, int t,
-                                          float (&out)[2][4]) {
+// q = 8 nq + 2t + (r mod 2).  Sum over the lane's q of C_q x_q y_q per degree
+// l, completed over the four lanes of the row.  With l = 1 for q < 3, 2 for
+// q < 8, 3 for q < 15 and 4 above, a lane's positions fall as: nq = 0 into
+// l = 1 or 2 (by t), nq = 1 into l = 3 (q = 15 into l = 4), nq = 2 into l = 4.
+// cq[nq][e] = C_q of the lane's positions.
+__device__ __forceinline__ void lsum_rows(const float (&x)[3][4], const float (&y)[3][4], const float (&cq)[3][2],
+                                          int t, float (&out)[2][4]) {
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
+    float v[3][2];
 #pragma unroll
-    for (int l = 0; l < 4; ++l) out[h][l] = 0.f;
+    for (int nq = 0; nq < 3; ++nq)
 #pragma unroll
-    for (int nt = 0; nt < 3; ++nt)
-#pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const int q = 8 * nt + 2 * t + e;
-        const float v = clm[q] * x[nt][2 * h + e] * y[nt][2 * h + e];
-        const int l = lm_l(q) - 1;
-#pragma unroll
-        for (int ll = 0; ll < 4; ++ll) out[h][ll] += (ll == l) ? v : 0.f;
-      }
+      for (int e = 0; e < 2; ++e) v[nq][e] = cq[nq][e] * x[nq][2 * h + e] * y[nq][2 * h + e];
+    out[h][0] = t == 0 ? v[0][0] + v[0][1] : (t == 1 ? v[0][0] : 0.f);
+    out[h][1] = t == 1 ? v[0][1] : (t >= 2 ? v[0][0] + v[0][1] : 0.f);
+    out[h][2] = v[1][0] + (t == 3 ? 0.f : v[1][1]);
+    out[h][3] = (t == 3 ? v[1][1] : 0.f) + v[2][0] + v[2][1];
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
       out[h][l] += __shfl_xor_sync(0xffffffffu, out[h][l], 1);
@@ -861,7 +900,11 @@ __global__ void __launch_bounds__(32 * kAngWarps, 2)
     const int ij = q / (16 * kCS), r = q % (16 * kCS), n = r / kCS, k = r % kCS;
     sm.c[ij][n][k] = (n < NQA && k < KA) ? dm.params[dm.off_cA + (ij * NQA + n) * KA + k] : 0.f;
   }
-  if (tid < NLM) sm.clm[tid] = kClm[tid];
+  float cq[3][2];  // C_lm at this lane's accumulator positions
+#pragma unroll
+  for (int nq = 0; nq < 3; ++nq)
+#pragma unroll
+    for (int e = 0; e < 2; ++e) cq[nq][e] = kClm[8 * nq + 2 * t + e];
 
   int tile = blockIdx.x;
   int i0 = 0, i1 = 0, P0 = 0, P1 = 0;
@@ -1012,7 +1055,7 @@ __global__ void __launch_bounds__(32 * kAngWarps, 2)
         float* gi = Gout + (size_t)i * C::NDES;
         if (!TAN) {
           float ql[2][4];
-          lsum_rows(acc, acc, sm.clm, t, ql);  // q_nl = sum_m C_lm S_nlm^2 (Eq. 7)
+          lsum_rows(acc, acc, cq, t, ql);  // q_nl = sum_m C_lm S_nlm^2 (Eq. 7)
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             float s2[5];
@@ -1037,7 +1080,7 @@ __global__ void __launch_bounds__(32 * kAngWarps, 2)
             }
           }
           float ql[2][4];
-          lsum_rows(sv, acc, sm.clm, t, ql);  // qdot_nl = 2 sum_m C_lm S_nlm Sdot_nlm
+          lsum_rows(sv, acc, cq, t, ql);  // qdot_nl = 2 sum_m C_lm S_nlm Sdot_nlm
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             float s2[5], d2[5];
