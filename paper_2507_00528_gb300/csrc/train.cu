@@ -160,68 +160,47 @@ __global__ void k_residuals(int N, int S, const float* __restrict__ F, const flo
 
 // ---------------------------------------------------------- gradient sums
 
-// grad[q] = sum over block partials + 2 lambda_l2 theta_q / N_par, one warp
-// per parameter.  Lane l sums the partials of blocks l, l + 32, ... in FP32
-// (at most a few tens of terms); the 32 lane sums are added in FP64 in lane
-// order.  Network parameters come from the network backward pass (net_part),
-// the coefficients from the c-gradient sweep (cpart).
-__global__ void __launch_bounds__(256) k_grad_final(DevModel dm, int ns, int nb_net, int nb_cg,
-                                                    const float* __restrict__ net_part,
-                                                    const float* __restrict__ cpart, double l2coef,
-                                                    double* __restrict__ grad) {
-  __shared__ double sh[8][32];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  float s = 0.f;
+// grad[q] = sum over block partials + 2 lambda_l2 theta_q / N_par; network
+// parameters come from the network backward pass (net_part), the coefficients
+// from the c-gradient sweeps (cpart).  A block takes 32
+// consecutive parameters (coalesced rows) and 16 subsets of the partial rows:
+// each thread sums its rows in FP32 (at most a few dozen leaves), the 16
+// subset sums of a parameter are combined in FP64 in a fixed order.
+constexpr int kGfCols = 32, kGfRows = 16;
+
+__global__ void __launch_bounds__(kGfCols* kGfRows) k_grad_final(DevModel dm, int ns, int nb_net, int nb_cg,
+                                                                 const float* __restrict__ net_part,
+                                                                 const float* __restrict__ cpart, double l2coef,
+                                                                 double* __restrict__ grad) {
+  __shared__ double sh[kGfRows][kGfCols];
+  const int tx = threadIdx.x % kGfCols, ty = threadIdx.x / kGfCols;
+  const int64_t q = (int64_t)blockIdx.x * kGfCols + tx;
+  const int64_t nnet = (int64_t)ns * dm.net_size;
+  float leaf = 0.f;
   if (q < dm.n_params) {
-    if (q < (int64_t)ns * dm.net_size) {
-      const int e = (int)(q / dm.net_size), l = (int)(q % dm.net_size);
-      for (int b = lane; b < nb_net; b += 32) s += net_part[((size_t)b * ns + e) * dm.net_size + l];
+    const float* src;
+    int64_t stride;
+    int nb;
+    if (q < nnet) {  // net_part[b][e][l] = row b, column q
+      src = net_part + q;
+      stride = nnet;
+      nb = nb_net;
     } else {
-      const int64_t nc = dm.n_params - (int64_t)ns * dm.net_size;
-      const int64_t c = q - dm.off_cR;
-      for (int b = lane; b < nb_cg; b += 32) s += cpart[(size_t)b * nc + c];
+      stride = dm.n_params - nnet;
+      src = cpart + (q - dm.off_cR);
+      nb = nb_cg;
     }
+#pragma unroll 4
+    for (int b = ty; b < nb; b += kGfRows) leaf += src[(size_t)b * stride];
   }
-  sh[w][lane] = (double)s;
-  __syncwarp();
-  if (lane == 0 && q < dm.n_params) {
+  sh[ty][tx] = (double)leaf;
+  __syncthreads();
+  if (ty == 0 && q < dm.n_params) {
     double t = 0.0;
-    for (int k = 0; k < 32; ++k) t += sh[w][k];
+#pragma unroll
+    for (int k = 0; k < kGfRows; ++k) t += sh[k][tx];
     grad[q] = t + l2coef * (double)dm.params[q];
   }
-}
-
-// The same sum for few partials (at most 64 per parameter, small batches):
-// one thread per parameter, FP32 leaves of at most 32 partials, FP64 above.
-__global__ void __launch_bounds__(256) k_grad_final_small(DevModel dm, int ns, int nb_net, int nb_cg,
-                                                          const float* __restrict__ net_part,
-                                                          const float* __restrict__ cpart, double l2coef,
-                                                          double* __restrict__ grad) {
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= dm.n_params) return;
-  const float* src;
-  size_t stride;
-  int nb;
-  if (q < (int64_t)ns * dm.net_size) {
-    const int e = (int)(q / dm.net_size), l = (int)(q % dm.net_size);
-    src = net_part + (size_t)e * dm.net_size + l;
-    stride = (size_t)ns * dm.net_size;
-    nb = nb_net;
-  } else {
-    const int64_t nc = dm.n_params - (int64_t)ns * dm.net_size;
-    src = cpart + (q - dm.off_cR);
-    stride = (size_t)nc;
-    nb = nb_cg;
-  }
-  double t = 0.0;
-  for (int b0 = 0; b0 < nb; b0 += 32) {
-    float leaf = 0.f;
-    const int b1 = b0 + 32 < nb ? b0 + 32 : nb;
-    for (int b = b0; b < b1; ++b) leaf += src[(size_t)b * stride];
-    t += (double)leaf;
-  }
-  grad[q] = t + l2coef * (double)dm.params[q];
 }
 
 // ---------------------------------------------------------- Adam, Eq. 17
@@ -414,12 +393,8 @@ int run_grad_reduce_impl(const gnep_model* m, gnep_nlist* nl, double lambda_l2, 
   const int nb_net = nl->ws.net_blocks;
   const int nb_cg = nl->n_atoms > 0 ? cgrad_blocks(nl) : 0;
   const double l2coef = 2.0 * lambda_l2 / (double)m->n_params;
-  if (nb_net <= 64 && nb_cg <= 64)
-    k_grad_final_small<<<blocks_for(m->n_params, 256), 256, 0, st>>>(dm, ns, nb_net, nb_cg, nl->ws.net_part,
-                                                                      nl->ws.cpart, l2coef, m->grad);
-  else
-    k_grad_final<<<blocks_for(m->n_params * 32, 256), 256, 0, st>>>(dm, ns, nb_net, nb_cg, nl->ws.net_part,
-                                                                    nl->ws.cpart, l2coef, m->grad);
+  k_grad_final<<<blocks_for(m->n_params, kGfCols), kGfCols * kGfRows, 0, st>>>(dm, ns, nb_net, nb_cg, nl->ws.net_part,
+                                                                              nl->ws.cpart, l2coef, m->grad);
   stage("grad_final");
   GNEP_CHECK_LAUNCH("gradient reduction");
   return GNEP_OK;
