@@ -38,38 +38,71 @@ __device__ __forceinline__ void tile_of(const Tiles& T, int t, int& e, int& a0, 
   na = min(TA, T.soff[e + 1] - a0);
 }
 
+// Bytes of an R x C operand whose K-adjacent core matrices are L bytes apart.
+template <bool TF32>
+constexpr int op_bytes(int R, int C, uint32_t L) {
+  return (R / 8) * (int)tc::sbo<TF32>(C, L);
+}
+// Blocks per SM that TMEM and shared memory admit (caps the registers per thread via launch bounds).
+constexpr int tc_fits(int smem, int cols) {
+  const int by_smem = kSmemPerSm / (smem + 6 * 1024), by_tmem = 512 / cols;
+  const int b = by_smem < by_tmem ? by_smem : by_tmem;
+  return b < 1 ? 1 : (b > 2 ? 2 : b);
+}
+constexpr int kMaxDynSmem = 232448;  // per block (227 KB)
+
+template <bool TF32, int D, int HPn>
+struct Layout {
+  static constexpr int DPn = (D + 1 + 15) / 16 * 16;  // descriptor width + the ones column, padded
+  static constexpr int bO = TA * (D + 1) * 4;
+  static constexpr int fwd(uint32_t L) {
+    const int g = op_bytes<TF32>(TA, DPn, L), h = op_bytes<TF32>(TA, HPn, L);
+    return (g > h ? g : h) + 2 * op_bytes<TF32>(HPn, DPn, L) + bO;
+  }
+  static constexpr int bwd(uint32_t L) {
+    const int g2 = 2 * op_bytes<TF32>(TA, DPn, L), h = op_bytes<TF32>(TA, HPn, L);
+    return (g2 > h ? g2 : h) + op_bytes<TF32>(DPn, TA, L) + op_bytes<TF32>(128, TA, L) + 2 * op_bytes<TF32>(HPn, DPn, L);
+  }
+  static constexpr int fwd_cols = tc::pow2_cols(HPn + DPn);
+  static constexpr int bwd_cols = tc::pow2_cols(2 * HPn + 2 * DPn);
+  // padded core matrices where they cost no block per SM and fit a block
+  static constexpr uint32_t lbo() {
+    return (fwd(144) <= kMaxDynSmem && bwd(144) <= kMaxDynSmem &&
+            tc_fits(fwd(144), fwd_cols) >= tc_fits(fwd(128), fwd_cols) &&
+            tc_fits(bwd(144), bwd_cols) >= tc_fits(bwd(128), bwd_cols))
+               ? 144u
+               : 128u;
+  }
+};
+
 template <bool TF32, int D, int HPn>
 struct Dims {
-  static constexpr int ES = tc::Elem<TF32>::ES;
-  static constexpr int DPn = (D + 1 + 15) / 16 * 16;  // descriptor width + the ones column, padded
-  static constexpr uint32_t sG = tc::sbo<TF32>(DPn);  // rows of length DPn:  [atoms][v], [mu][v]
-  static constexpr uint32_t sH = tc::sbo<TF32>(HPn);  // rows of length HPn:  [atoms][mu], [v][mu]
-  static constexpr uint32_t sA = tc::sbo<TF32>(TA);   // rows of length TA:   [mu][atoms], [v][atoms]
-  static constexpr int bG = TA * DPn * ES;
-  static constexpr int bH = TA * HPn * ES;
-  static constexpr int bW0 = HPn * DPn * ES;
-  static constexpr int bT = 128 * TA * ES;  // [mu][atoms], 128 rows (the MMA's M) whatever H is
-  static constexpr int bGT = DPn * TA * ES;
+  using Lay = Layout<TF32, D, HPn>;
+  static constexpr int DPn = Lay::DPn;
+  static constexpr uint32_t LBO = Lay::lbo();
+  static constexpr uint32_t sG = tc::sbo<TF32>(DPn, LBO);  // rows of length DPn:  [atoms][v], [mu][v]
+  static constexpr uint32_t sH = tc::sbo<TF32>(HPn, LBO);  // rows of length HPn:  [atoms][mu], [v][mu]
+  static constexpr uint32_t sA = tc::sbo<TF32>(TA, LBO);   // rows of length TA:   [mu][atoms], [v][atoms]
+  static constexpr int bG = op_bytes<TF32>(TA, DPn, LBO);
+  static constexpr int bH = op_bytes<TF32>(TA, HPn, LBO);
+  static constexpr int bW0 = op_bytes<TF32>(HPn, DPn, LBO);
+  static constexpr int bT = op_bytes<TF32>(128, TA, LBO);  // [mu][atoms], 128 rows (the MMA's M) whatever H is
+  static constexpr int bGT = op_bytes<TF32>(DPn, TA, LBO);
   static constexpr int OW = D + 1;          // row pitch (floats) of the FP32 output tile, odd: conflict-free rows
-  static constexpr int bO = TA * OW * 4;
+  static constexpr int bO = Lay::bO;
   // forward: RA (s.G, then beta) | W0 [mu][v] | W0t [v][mu] | output tile (E')
   static constexpr int fRA = bG > bH ? bG : bH;
   static constexpr int fwd_smem = fRA + 2 * bW0 + bO;
-  static constexpr int fwd_cols = tc::pow2_cols(HPn + DPn);
+  static constexpr int fwd_cols = Lay::fwd_cols;
   // backward: RA (s.G | s.Gdot, then alpha) | RG ((s.G)^T, then (s.Gdot)^T) |
   //           RT (alpha^T, then the Gbar output tile, then -beta^T) | W0 | W0t
   static constexpr int bRA = 2 * bG > bH ? 2 * bG : bH;
   static constexpr int bwd_smem = bRA + bGT + bT + 2 * bW0;
-  static constexpr int bwd_cols = tc::pow2_cols(2 * HPn + 2 * DPn);
+  static constexpr int bwd_cols = Lay::bwd_cols;
   static_assert(bO <= bT, "the Gbar output tile lives in the [mu][atoms] operand");
-  // blocks per SM that TMEM and shared memory admit (caps the registers per thread via launch bounds)
-  static constexpr int fits(int smem, int cols) {
-    const int by_smem = kSmemPerSm / (smem + 6 * 1024), by_tmem = 512 / cols;
-    const int b = by_smem < by_tmem ? by_smem : by_tmem;
-    return b < 1 ? 1 : (b > 2 ? 2 : b);
-  }
-  static constexpr int fwd_minb = fits(fwd_smem, fwd_cols);
-  static constexpr int bwd_minb = fits(bwd_smem, bwd_cols);
+  static_assert(fwd_smem == Lay::fwd(LBO) && bwd_smem == Lay::bwd(LBO), "layout sizes");
+  static constexpr int fwd_minb = tc_fits(fwd_smem, fwd_cols);
+  static constexpr int bwd_minb = tc_fits(bwd_smem, bwd_cols);
 };
 
 // W0 of species e as [mu][v] and [v][mu] operands (zero-padded), b0 and w1.
@@ -81,8 +114,8 @@ __device__ void stage_weights(const DevModel& dm, int e, uint8_t* W0, uint8_t* W
   for (int q = threadIdx.x; q < HPn * Dm::DPn; q += NTC) {
     const int mu = q / Dm::DPn, v = q % Dm::DPn;
     const float w = (mu < H && v < D) ? P[mu * D + v] : 0.f;
-    tc::st_elem<TF32>(W0, tc::core_off<TF32>(mu, v, Dm::sG), w);
-    tc::st_elem<TF32>(W0t, tc::core_off<TF32>(v, mu, Dm::sH), w);
+    tc::st_elem<TF32>(W0, tc::core_off<TF32>(mu, v, Dm::sG, Dm::LBO), w);
+    tc::st_elem<TF32>(W0t, tc::core_off<TF32>(v, mu, Dm::sH, Dm::LBO), w);
   }
   for (int mu = threadIdx.x; mu < HPn; mu += NTC) {
     b0s[mu] = mu < H ? P[D * H + mu] : 0.f;
@@ -196,11 +229,11 @@ __global__ void __launch_bounds__(NTC, (Dims<TF32, D, HPn>::fwd_minb))
     if (tid < TA) rows[tid] = tid < na ? T.perm[a0 + tid] : -1;
     __syncthreads();
     stage_rows<D, DPn, false>(G, nullptr, rows, [&](int a, int v, float g, float) {
-      tc::st_elem<TF32>(RA, tc::core_off<TF32>(a, v, Dm::sG), sc[v] * g);
+      tc::st_elem<TF32>(RA, tc::core_off<TF32>(a, v, Dm::sG, Dm::LBO), sc[v] * g);
     });
     sync_for_mma();
     if (tid == 0) {
-      tc::mma_chain<TF32>(tm + cZ, RA, Dm::sG, W0, Dm::sG, DPn, HPn, false);
+      tc::mma_chain<TF32>(tm + cZ, RA, Dm::sG, W0, Dm::sG, DPn, HPn, false, Dm::LBO);
       tc::commit(&mbar);
     }
     if (!(ok = wait_mma(&mbar, ph))) break;
@@ -218,12 +251,12 @@ __global__ void __launch_bounds__(NTC, (Dims<TF32, D, HPn>::fwd_minb))
       }
 #pragma unroll
       for (int q = 0; q < 16; q += tc::Elem<TF32>::EPC)
-        tc::st_chunk<TF32>(RA, tc::core_off<TF32>(arow, 16 * c + q, Dm::sH), bt + q);
+        tc::st_chunk<TF32>(RA, tc::core_off<TF32>(arow, 16 * c + q, Dm::sH, Dm::LBO), bt + q);
     }
     Eh[half][arow] = E;
     sync_for_mma();
     if (tid == 0) {
-      tc::mma_chain<TF32>(tm + cE, RA, Dm::sH, W0t, Dm::sH, HPn, DPn, false);
+      tc::mma_chain<TF32>(tm + cE, RA, Dm::sH, W0t, Dm::sH, HPn, DPn, false, Dm::LBO);
       tc::commit(&mbar);
     }
     if (tid < TA) {
@@ -355,15 +388,15 @@ __global__ void __launch_bounds__(NTC, (Dims<TF32, D, HPn>::bwd_minb))
     if (tid == 0)
       for (int a = 0; a < na; ++a) cb1 += ei[a];
     stage_rows<D, DPn, true>(G, Gd, rows, [&](int a, int v, float g, float gd) {
-      const uint32_t o = tc::core_off<TF32>(a, v, Dm::sG);
+      const uint32_t o = tc::core_off<TF32>(a, v, Dm::sG, Dm::LBO);
       tc::st_elem<TF32>(RA, o, sc[v] * g);
       tc::st_elem<TF32>(RA + Dm::bG, o, sc[v] * gd);
-      tc::st_elem<TF32>(RG, tc::core_off<TF32>(v, a, Dm::sA), v == D ? (rows[a] >= 0 ? 1.f : 0.f) : sc[v] * g);
+      tc::st_elem<TF32>(RG, tc::core_off<TF32>(v, a, Dm::sA, Dm::LBO), v == D ? (rows[a] >= 0 ? 1.f : 0.f) : sc[v] * g);
     });
     sync_for_mma();
     if (tid == 0) {
-      tc::mma_chain<TF32>(tm + cZ, RA, Dm::sG, W0, Dm::sG, DPn, HPn, false);
-      tc::mma_chain<TF32>(tm + cZd, RA + Dm::bG, Dm::sG, W0, Dm::sG, DPn, HPn, false);
+      tc::mma_chain<TF32>(tm + cZ, RA, Dm::sG, W0, Dm::sG, DPn, HPn, false, Dm::LBO);
+      tc::mma_chain<TF32>(tm + cZd, RA + Dm::bG, Dm::sG, W0, Dm::sG, DPn, HPn, false, Dm::LBO);
       tc::commit(&mbar);
     }
     if (!(ok = wait_mma(&mbar, ph))) break;
@@ -384,17 +417,17 @@ __global__ void __launch_bounds__(NTC, (Dims<TF32, D, HPn>::bwd_minb))
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) q1 += __shfl_xor_sync(0xffffffffu, q1, o);
         if (ln == 0) wpart[warp & 3][mu] = q1;
-        tc::st_elem<TF32>(RT, tc::core_off<TF32>(mu, arow, Dm::sA), al[q]);
+        tc::st_elem<TF32>(RT, tc::core_off<TF32>(mu, arow, Dm::sA, Dm::LBO), al[q]);
       }
 #pragma unroll
       for (int q = 0; q < 16; q += tc::Elem<TF32>::EPC)
-        tc::st_chunk<TF32>(RA, tc::core_off<TF32>(arow, 16 * c + q, Dm::sH), al + q);
+        tc::st_chunk<TF32>(RA, tc::core_off<TF32>(arow, 16 * c + q, Dm::sH, Dm::LBO), al + q);
     }
     sync_for_mma();
     if (tid < HPn) acc_w1 += ((wpart[0][tid] + wpart[1][tid]) + wpart[2][tid]) + wpart[3][tid];
     if (tid == 0) {
-      tc::mma_chain<TF32>(tm + cGb, RA, Dm::sH, W0t, Dm::sH, HPn, DPn, false);
-      tc::mma_chain<TF32>(tm + cW, RT, Dm::sA, RG, Dm::sA, TA, DPn, !fresh);
+      tc::mma_chain<TF32>(tm + cGb, RA, Dm::sH, W0t, Dm::sH, HPn, DPn, false, Dm::LBO);
+      tc::mma_chain<TF32>(tm + cW, RT, Dm::sA, RG, Dm::sA, TA, DPn, !fresh, Dm::LBO);
       tc::commit(&mbar);
     }
     if (!(ok = wait_mma(&mbar, ph))) break;
@@ -422,16 +455,16 @@ __global__ void __launch_bounds__(NTC, (Dims<TF32, D, HPn>::bwd_minb))
       for (int q = 0; q < 16; ++q) {
         const int mu = 16 * c + q;
         const float x = tanhf(z[q] + b0s[mu]);
-        tc::st_elem<TF32>(RT, tc::core_off<TF32>(mu, arow, Dm::sA), -w1s[mu] * (1.f - x * x));
+        tc::st_elem<TF32>(RT, tc::core_off<TF32>(mu, arow, Dm::sA, Dm::LBO), -w1s[mu] * (1.f - x * x));
       }
     }
     zero_pad_rows();
     stage_rows<D, DPn, false>(Gd, nullptr, rows, [&](int a, int v, float gd, float) {
-      tc::st_elem<TF32>(RG, tc::core_off<TF32>(v, a, Dm::sA), sc[v] * gd);
+      tc::st_elem<TF32>(RG, tc::core_off<TF32>(v, a, Dm::sA, Dm::LBO), sc[v] * gd);
     });
     sync_for_mma();
     if (tid == 0) {
-      tc::mma_chain<TF32>(tm + cW, RT, Dm::sA, RG, Dm::sA, TA, DPn, true);
+      tc::mma_chain<TF32>(tm + cW, RT, Dm::sA, RG, Dm::sA, TA, DPn, true, Dm::LBO);
       tc::commit(&mbar);
     }
     if (!(ok = wait_mma(&mbar, ph))) break;

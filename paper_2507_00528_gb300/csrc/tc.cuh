@@ -5,10 +5,12 @@
 // Operand layout (both A and B "K-major", no swizzle): a matrix of R rows and
 // C columns (C along the contraction K) is stored as 8-row x 16-byte core
 // matrices.  Element (r, c) sits at byte
-//     (r / 8) * SBO + (c / EPC) * 128 + (r % 8) * 16 + (c % EPC) * ES,
+//     (r / 8) * SBO + (c / EPC) * LBO + (r % 8) * 16 + (c % EPC) * ES,
 // with ES the element size, EPC = 16 / ES elements per core row and
-// SBO = (C / EPC) * 128 the stride between 8-row groups; core matrices adjacent
-// along K are 128 bytes apart (the descriptor's leading-dimension offset).
+// SBO = (C / EPC) * LBO the stride between 8-row groups; core matrices adjacent
+// along K are LBO bytes apart (the descriptor's leading-dimension offset): 128
+// packs them, 144 leaves 16 bytes after each, which puts the core matrices
+// that one warp's row-wise or transposed element stores touch 4 banks apart.
 // One MMA of M = 128 consumes 32 bytes of K (16 BF16 or 8 TF32 elements) and
 // accumulates D[m][n] += sum_k A[m][k] B[n][k] in FP32 in tensor memory, row m
 // in TMEM lane m, column n in TMEM column n.
@@ -34,14 +36,14 @@ struct Elem<true> {  // TF32 operands, kind::tf32
 
 // Byte stride between 8-row groups of an operand with C columns.
 template <bool TF32>
-__host__ __device__ constexpr uint32_t sbo(int C) {
-  return (uint32_t)(C / Elem<TF32>::EPC) * 128u;
+__host__ __device__ constexpr uint32_t sbo(int C, uint32_t lbo = 128u) {
+  return (uint32_t)(C / Elem<TF32>::EPC) * lbo;
 }
 
 template <bool TF32>
-__device__ __forceinline__ uint32_t core_off(int r, int c, uint32_t sbo_) {
+__device__ __forceinline__ uint32_t core_off(int r, int c, uint32_t sbo_, uint32_t lbo = 128u) {
   constexpr int ES = Elem<TF32>::ES, EPC = Elem<TF32>::EPC;
-  return (uint32_t)(r >> 3) * sbo_ + (uint32_t)(c / EPC) * 128u + (uint32_t)(r & 7) * 16u + (uint32_t)(c % EPC) * ES;
+  return (uint32_t)(r >> 3) * sbo_ + (uint32_t)(c / EPC) * lbo + (uint32_t)(r & 7) * 16u + (uint32_t)(c % EPC) * ES;
 }
 
 // FP32 -> operand bits (round to nearest).
@@ -105,13 +107,13 @@ __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uin
 // operands K-major in shared memory with the given 8-row-group strides.
 template <bool TF32>
 __device__ __forceinline__ void mma_chain(uint32_t d_tmem, const void* A, uint32_t a_sbo, const void* B, uint32_t b_sbo,
-                                          int K, int N, bool accumulate) {
+                                          int K, int N, bool accumulate, uint32_t lbo = 128u) {
   using E = Elem<TF32>;
   const uint32_t id = idesc(E::FMT, 128, N);
   const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
   for (int k = 0; k < K; k += E::KSTEP) {
-    const uint32_t koff = (uint32_t)(k / E::EPC) * 128u;
-    mma<TF32>(d_tmem, sdesc(a0 + koff, 128u, a_sbo), sdesc(b0 + koff, 128u, b_sbo), id,
+    const uint32_t koff = (uint32_t)(k / E::EPC) * lbo;
+    mma<TF32>(d_tmem, sdesc(a0 + koff, lbo, a_sbo), sdesc(b0 + koff, lbo, b_sbo), id,
               (accumulate || k > 0) ? 1u : 0u);
   }
 }
