@@ -15,7 +15,7 @@
 // the running sum, whose low bits the tensor core's accumulation drops, made
 // the error of a K = 16 dot product 1.7 times that of an FP32 FMA chain, while
 // two chains match it (measured on random operands of mixed sign).  Without
-// SPLIT a product takes hi*hi alone (TF32 accuracy).
+// SPLIT a product takes the operands' TF32 truncations alone (TF32 accuracy).
 #pragma once
 #include <cstdint>
 
@@ -34,10 +34,19 @@ __device__ __forceinline__ uint32_t tf32_rna(float x) {
   return r;
 }
 
+// With SPLIT: hi rounded to nearest, lo the rounded remainder.  Without: the
+// FP32 bits as they are (the tensor core reads a TF32 operand from the upper 19
+// bits, i.e. rounds toward zero), which saves the conversion where single TF32
+// products are accurate enough anyway.
 template <bool SPLIT>
 __device__ __forceinline__ void split_tf32(float x, uint32_t& h, uint32_t& l) {
-  h = tf32_rna(x);
-  l = SPLIT ? tf32_rna(x - __uint_as_float(h)) : 0u;
+  if constexpr (SPLIT) {
+    h = tf32_rna(x);
+    l = tf32_rna(x - __uint_as_float(h));
+  } else {
+    h = __float_as_uint(x);
+    l = 0u;
+  }
 }
 
 template <bool SPLIT>
