@@ -1293,7 +1293,7 @@ struct Runner {
     Fork fc(nl, A.st);  // radial and angular parts write disjoint columns of cpart
     k_cgrad_radial<C><<<nb, 32 * kCgRadialWarps, 0, fc.side>>>(N, nl->type, w.Gb, w.Ep, w.FR, w.FRd, w.cpart);
     stage("cgrad_radial");
-    auto ang = m->precision == GNEP_PREC_FP32 ? k_cgrad_ang<C, true> : k_cgrad_ang<C, false>;
+    auto ang = m->precision != GNEP_PREC_BF16 ? k_cgrad_ang<C, true> : k_cgrad_ang<C, false>;
     ang<<<nb, 32 * kCgWarps, sizeof(CgSmem<C>), A.st>>>(nl->natile[1], nl->atile[1], dm, nl->type, nl->L[1].off,
                                                          nl->L[1].rij, w.wij, w.S, w.Sd, w.Gb, w.Ep, w.cpart);
     stage("cgrad");
