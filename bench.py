@@ -396,7 +396,12 @@ def run_gnep(args):
     # the bound is the resource that limits at speed of light: compulsory bytes
     # at the measured copy bandwidth, or the formulation's FP32 work at the ALU peak
     t_hbm = by[dom] / (hbm_peak * 1e9)
-    t_alu = fl[dom] / (fp32_peak * 1e12)
+    # the network kernels of the tensor-core modes run their FLOPs on the tensor
+    # pipe (TF32 at half the measured BF16 rate, the nominal ratio)
+    on_tensor = dom in ("mlp_fwd", "mlp_bwd") and args.precision != "fp32"
+    flop_peak = (peaks.get("bf16_tflops", 1900.0) * (0.5 if args.precision == "tf32" else 1.0)) if on_tensor \
+        else fp32_peak
+    t_alu = fl[dom] / (flop_peak * 1e12)
     achieved_gbs = by[dom] / (stage_ms[dom] / 1e3) / 1e9
     achieved = fl[dom] / (stage_ms[dom] / 1e3) / 1e12
     step_flops = sum(fl.values())
@@ -469,13 +474,14 @@ def run_gnep(args):
                       "step_algo_gflop": step_flops / 1e9,
                       "step_achieved_tflops": step_flops / (total_ms / args.steps / 1e3) / 1e12}
                      if t_hbm >= t_alu else
-                     {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32_peak,
-                      "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                     {"bound": "tensor" if on_tensor else "alu", "kernel": dom, "achieved": achieved,
+                      "peak": flop_peak, "unit": "TFLOP/s", "frac": achieved / flop_peak,
                       "traffic": committed_traffic(dom),
-                      "peak_source": f"FP32 {props.multi_processor_count} SMs x 128 lanes x 2 x {sm_max:.0f} MHz",
+                      "peak_source": ("MEASURED_PEAKS.json bf16_tflops (of measured)" if on_tensor else
+                                      f"FP32 {props.multi_processor_count} SMs x 128 lanes x 2 x {sm_max:.0f} MHz"),
                       "kernel_ms": stage_ms[dom], "kernel_algo_bytes": by[dom],
                       "kernel_algo_flops": fl[dom], "hbm_frac": achieved_gbs / hbm_peak,
-                      "sol_us": {"hbm": t_hbm * 1e6, "fp32_alu": t_alu * 1e6},
+                      "sol_us": {"hbm": t_hbm * 1e6, ("tensor" if on_tensor else "fp32_alu"): t_alu * 1e6},
                       "step_algo_gflop": step_flops / 1e9,
                       "step_achieved_tflops": step_flops / (total_ms / args.steps / 1e3) / 1e12}),
         "kernel_ms": {k: round(v, 5) for k, v in stage_ms.items()},
