@@ -208,9 +208,9 @@ int gnep_loss_grad(gnep_model *m, const gnep_nlist *nl, const gnep_labels *y,
                    double *loss_terms, float *grad, void *stream);
 
 /* Autotuner.  Launch shapes of the angular sweeps are per batch: atoms and
- * pairs per tile of the descriptor sweep's tiles and of the force / tangent /
- * c-gradient sweeps' tiles, and the number of persistent blocks of the
- * c-gradient sweep.  gnep_autotune times the loss + gradient evaluation of
+ * pairs per tile of the descriptor and tangent sweeps' tiles and of the angular
+ * force and c-gradient sweeps' tiles, and the number of persistent blocks of
+ * the c-gradient sweep.  gnep_autotune times the loss + gradient evaluation of
  * this batch (median of `reps` runs, no parameter update) over candidate
  * values of each in turn and keeps the fastest in the neighbour list.  It
  * synchronizes `stream` and must not run during stream capture; graphs
