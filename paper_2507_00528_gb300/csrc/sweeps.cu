@@ -1057,14 +1057,18 @@ __global__ void __launch_bounds__(32 * kAngWarps, 2)
           float ql[2][4];
           lsum_rows(acc, acc, cq, t, ql);  // q_nl = sum_m C_lm S_nlm^2 (Eq. 7)
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            float s2[5];
-            gather_l2(acc, h, lane, s2);
-            const int n = g + 8 * h;
-            if (n < NQA) {
-              gi[C::vang(n, t + 1)] = pick4(ql[h], t);
-              if (C::FB && t == 0) gi[C::v4b(n)] = q4_value(s2);
-            }
+          for (int h = 0; h < 2; ++h)
+            if (g + 8 * h < NQA) gi[C::vang(g + 8 * h, t + 1)] = pick4(ql[h], t);
+          if (C::FB) {  // q4 of row g + 8h on lane t = h: one evaluation per lane for both halves
+            float s2[2][5];
+            gather_l2(acc, 0, lane, s2[0]);
+            gather_l2(acc, 1, lane, s2[1]);
+            const int h = t & 1, n = g + 8 * h;
+            float sel[5];
+#pragma unroll
+            for (int m = 0; m < 5; ++m) sel[m] = h ? s2[1][m] : s2[0][m];
+            const float q4 = q4_value(sel);
+            if (t < 2 && n < NQA) gi[C::v4b(n)] = q4;
           }
         } else {
           float sv[3][4];  // S at the lane's positions
@@ -1082,22 +1086,27 @@ __global__ void __launch_bounds__(32 * kAngWarps, 2)
           float ql[2][4];
           lsum_rows(sv, acc, cq, t, ql);  // qdot_nl = 2 sum_m C_lm S_nlm Sdot_nlm
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            float s2[5], d2[5];
-            gather_l2(sv, h, lane, s2);
-            gather_l2(acc, h, lane, d2);
-            const int n = g + 8 * h;
-            if (n < NQA) {
-              gi[C::vang(n, t + 1)] = 2.f * pick4(ql[h], t);
-              if (C::FB && t == 0) {
-                float g4[5];
-                q4_grad(s2, g4);
-                float q = 0.f;
+          for (int h = 0; h < 2; ++h)
+            if (g + 8 * h < NQA) gi[C::vang(g + 8 * h, t + 1)] = 2.f * pick4(ql[h], t);
+          if (C::FB) {  // qdot4 of row g + 8h on lane t = h: one evaluation per lane for both halves
+            float s2[2][5], d2[2][5];
 #pragma unroll
-                for (int m = 0; m < 5; ++m) q = fmaf(g4[m], d2[m], q);
-                gi[C::v4b(n)] = q;
-              }
+            for (int h = 0; h < 2; ++h) {
+              gather_l2(sv, h, lane, s2[h]);
+              gather_l2(acc, h, lane, d2[h]);
             }
+            const int h = t & 1, n = g + 8 * h;
+            float ss[5], dd[5], g4[5];
+#pragma unroll
+            for (int m = 0; m < 5; ++m) {
+              ss[m] = h ? s2[1][m] : s2[0][m];
+              dd[m] = h ? d2[1][m] : d2[0][m];
+            }
+            q4_grad(ss, g4);
+            float q = 0.f;
+#pragma unroll
+            for (int m = 0; m < 5; ++m) q = fmaf(g4[m], dd[m], q);
+            if (t < 2 && n < NQA) gi[C::v4b(n)] = q;
           }
         }
       }
