@@ -320,3 +320,32 @@ def test_dense_image_lattice_overflows_the_slots():
     assert rel_l2(Ea, Eao) < E_TOL
     assert rel_l2(W, Wo) < F_TOL
     assert np.abs(F - Fo).max() <= F_TOL * max(np.abs(Fo).max(), 1.0)
+
+
+def test_atoms_without_angular_neighbours():
+    """A sparse cell whose atoms lie 5.5-6.5 A apart: radial neighbours (r_c 7 A)
+    but no angular ones (r_c 4 A).  Their S, q_nl and q4 are zero, and the
+    sweeps that walk angular pairs per atom still write them (Eqs. 5-8), next to
+    an ordinary structure in the same tiles; energies, forces and the gradient
+    match the oracle."""
+    rng = np.random.default_rng(41)
+    H = np.diag([12.0, 12.0, 12.0])
+    sparse = np.array([[1.0, 1.0, 1.0], [7.0, 1.5, 1.2], [1.3, 7.2, 1.1], [6.6, 6.9, 6.8]])
+    dense = synth.make_batch([30], [1], rng)
+    pos = np.concatenate([sparse, dense.pos])
+    types = np.concatenate([[0, 1, 1, 0], dense.types]).astype(np.int32)
+    b = synth.Batch(np.array([0, 4, 34], dtype=np.int32), pos, types, np.stack([H, dense.cell[0]]))
+    c = Case("nmax8_basis12_h50_4b", b)
+    off, _, _ = c.nl.export(1)
+    assert np.all(np.diff(off)[:4] == 0) and off[-1] > 0
+    G = c.m.descriptors(c.nl).double().cpu().numpy()
+    Go = O.descriptors(c.cfg, c.P64, b)
+    assert np.all(G[:4, c.cfg.nq_r:] == 0.0)
+    assert rel_l2(G, Go) < 2e-6
+    Ea, Es, F, W = (t.double().cpu().numpy() for t in c.m.forward(c.nl))
+    Eao, Eso, Fo, Wo = O.forward(c.cfg, c.P64, c.s64, b)
+    assert rel_l2(Ea, Eao) < E_TOL and rel_l2(F, Fo) < F_TOL and rel_l2(W, Wo) < F_TOL
+    y = c.gpu_labels()
+    _, g = c.m.loss_grad(c.nl, y)
+    _, ref = O.loss_grad(c.cfg, c.P64, c.s64, b, c.y)
+    check_grad(g.cpu().numpy(), ref)
