@@ -975,6 +975,20 @@ __global__ void __launch_bounds__(32 * kAngWarps, 2)
         Acc<SPLIT> sacc[3];
 #pragma unroll
         for (int nq = 0; nq < 3; ++nq) sacc[nq].zero();
+        float sv[3][4];  // tangent: S at the lane's accumulator positions, loaded ahead of the products
+        if (TAN) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const float* srow_in = Sin + ((size_t)i * NQA + min(g + 8 * h, NQA - 1)) * NLM;
+#pragma unroll
+            for (int nq = 0; nq < 3; ++nq) {
+              const float2 v = g + 8 * h < NQA ? *reinterpret_cast<const float2*>(srow_in + 8 * nq + 2 * t)
+                                               : make_float2(0.f, 0.f);
+              sv[nq][2 * h] = v.x;
+              sv[nq][2 * h + 1] = v.y;
+            }
+          }
+        }
         for (int p0 = q0; p0 < q1; p0 += 8) {
           const int sc = p0 + pg;
           const int Jc = sc < q1 ? sm.geo.J[sc] : -1;
@@ -1071,18 +1085,6 @@ __global__ void __launch_bounds__(32 * kAngWarps, 2)
             if (t < 2 && n < NQA) gi[C::v4b(n)] = q4;
           }
         } else {
-          float sv[3][4];  // S at the lane's positions
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const float* srow_in = Sin + ((size_t)i * NQA + min(g + 8 * h, NQA - 1)) * NLM;
-#pragma unroll
-            for (int nq = 0; nq < 3; ++nq) {
-              const float2 v = g + 8 * h < NQA ? *reinterpret_cast<const float2*>(srow_in + 8 * nq + 2 * t)
-                                               : make_float2(0.f, 0.f);
-              sv[nq][2 * h] = v.x;
-              sv[nq][2 * h + 1] = v.y;
-            }
-          }
           float ql[2][4];
           lsum_rows(sv, acc, cq, t, ql);  // qdot_nl = 2 sum_m C_lm S_nlm Sdot_nlm
 #pragma unroll
