@@ -881,7 +881,7 @@ __device__ __forceinline__ void gather_l2(const float (&x)[3][4], int h, int lan
 }
 
 template <class C, bool TAN, bool SPLIT>
-__global__ void __launch_bounds__(32 * kAngWarps, 2)
+__global__ void __launch_bounds__(32 * kAngWarps, (TAN || SPLIT) ? 2 : 3)
     k_ang_mma(int ntile, const int* __restrict__ tiles, DevModel dm, const int* __restrict__ type,
               const int* __restrict__ atom_struct, const int* __restrict__ off, const int* __restrict__ own,
               const int* __restrict__ jj, const float4* __restrict__ rij, const float4* __restrict__ a,
