@@ -539,9 +539,24 @@ struct CgSmem {
     float red[kCgWarps][C::NS * C::NS * KT * 128];  // per warp: [I][J][kt][lane][4] accumulator registers
   };
   float A[NA][C::NQA][kAS];
+  // the next tile's atom rows (S, Sdot, Gbar, E'), copied asynchronously while
+  // the current tile is contracted
+  float stS[NA * C::NQA * NLM];
+  float stD[NA * C::NQA * NLM];
+  float stG[NA * C::NDES];
+  float stE[NA * C::NDES];
   int type[NA];
   int off[NA + 1];
 };
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
 
 template <class C, bool SPLIT>
 __global__ void __launch_bounds__(32 * kCgWarps, SPLIT ? 1 : 2)
@@ -565,6 +580,22 @@ __global__ void __launch_bounds__(32 * kCgWarps, SPLIT ? 1 : 2)
 #pragma unroll
       for (int kt = 0; kt < KT; ++kt) acc[s][J][kt].zero();
 
+  // atom rows of tile atoms [a0, a1) into the staging arrays (one commit group)
+  auto stage_rows = [&](int a0, int a1) {
+    const int n4 = (a1 - a0) * NQA * NLM / 4, ng = (a1 - a0) * C::NDES;
+    const float4* s4 = reinterpret_cast<const float4*>(Sang + (size_t)a0 * NQA * NLM);
+    const float4* d4 = reinterpret_cast<const float4*>(Sdd + (size_t)a0 * NQA * NLM);
+    for (int q = tid; q < n4; q += blockDim.x) {
+      cp_async16(&sm.stS[4 * q], s4 + q);
+      cp_async16(&sm.stD[4 * q], d4 + q);
+    }
+    for (int q = tid; q < ng; q += blockDim.x) {
+      cp_async4(&sm.stG[q], Gb + (size_t)a0 * C::NDES + q);
+      cp_async4(&sm.stE[q], Ep + (size_t)a0 * C::NDES + q);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+
   int tile = blockIdx.x;
   int i0 = 0, i1 = 0, P0 = 0, P1 = 0;
   if (tile < ntile) {
@@ -572,19 +603,21 @@ __global__ void __launch_bounds__(32 * kCgWarps, SPLIT ? 1 : 2)
     i1 = tiles[tile + 1];
     P0 = off[i0];
     P1 = off[i1];
+    stage_rows(i0, i1);
   }
   for (; tile < ntile; tile += gridDim.x) {
     const int nt = tile + gridDim.x;  // the next tile's bounds are fetched early
     const int i0n = nt < ntile ? tiles[nt] : 0, i1n = nt < ntile ? tiles[nt + 1] : 0;
-    __syncthreads();  // the previous tile's readers are done
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();  // the previous tile's readers are done and this tile's rows are staged
     if (tid >= 128) {
       // atom rows [Sbar | Sdbar], one thread per (atom, channel)
       const int u = tid - 128, at = u / NQA, n = u % NQA, i = i0 + at;
       if (at < NA && i < i1) {
-        const float4* S4 = reinterpret_cast<const float4*>(Sang + ((size_t)i * NQA + n) * NLM);
-        const float4* D4 = reinterpret_cast<const float4*>(Sdd + ((size_t)i * NQA + n) * NLM);
-        const float* gb = Gb + (size_t)i * C::NDES;
-        const float* ep = Ep + (size_t)i * C::NDES;
+        const float4* S4 = reinterpret_cast<const float4*>(&sm.stS[(at * NQA + n) * NLM]);
+        const float4* D4 = reinterpret_cast<const float4*>(&sm.stD[(at * NQA + n) * NLM]);
+        const float* gb = &sm.stG[at * C::NDES];
+        const float* ep = &sm.stE[at * C::NDES];
         float s[NLM], d[NLM], sb[NLM], sdb[NLM];
 #pragma unroll
         for (int q = 0; q < NLM / 4; ++q) {
@@ -633,17 +666,15 @@ __global__ void __launch_bounds__(32 * kCgWarps, SPLIT ? 1 : 2)
         pair_geometry<C>(sm.geo, tid, r, make_float3(w.x, w.y, w.z), dm);
       }
       __syncthreads();
-      if (tid == 32 * kCgWarps - 1 && cs == P0 && nt < ntile) {
-        // the next tile's inputs move into L2 while this one is contracted (the
-        // last warp has the fewest atoms)
-        const int p0n = off[i0n], p1n = off[i1n];
-        const size_t na = (size_t)(i1n - i0n);
-        prefetch_l2(Sang + (size_t)i0n * NQA * NLM, na * NQA * NLM * sizeof(float));
-        prefetch_l2(Sdd + (size_t)i0n * NQA * NLM, na * NQA * NLM * sizeof(float));
-        prefetch_l2(Gb + (size_t)i0n * C::NDES, na * C::NDES * sizeof(float));
-        prefetch_l2(Ep + (size_t)i0n * C::NDES, na * C::NDES * sizeof(float));
-        prefetch_l2(rij + p0n, (size_t)(p1n - p0n) * sizeof(float4));
-        prefetch_l2(wij + p0n, (size_t)(p1n - p0n) * sizeof(float4));
+      if (cs == P0 && nt < ntile) {
+        // while this tile is contracted: the next tile's atom rows to shared
+        // memory, its pair rows into L2 (the last warp has the fewest atoms)
+        stage_rows(i0n, i1n);
+        if (tid == 32 * kCgWarps - 1) {
+          const int p0n = off[i0n], p1n = off[i1n];
+          prefetch_l2(rij + p0n, (size_t)(p1n - p0n) * sizeof(float4));
+          prefetch_l2(wij + p0n, (size_t)(p1n - p0n) * sizeof(float4));
+        }
       }
       for (int at = warp; at < i1 - i0; at += kCgWarps) {
         const int q0 = max(sm.off[at], cs) - cs, q1 = min(sm.off[at + 1], ce) - cs;
