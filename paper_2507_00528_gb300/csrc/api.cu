@@ -172,7 +172,7 @@ int gnep_create(gnep_model** out, int n_species, const int* species_z, double rc
   if ((e = cudaMalloc(&m->adam_v, 4 * n)) != cudaSuccess) return fail(e, "cudaMalloc adam");
   if ((e = cudaMalloc(&m->grad, 8 * n)) != cudaSuccess) return fail(e, "cudaMalloc grad");
   if ((e = cudaMalloc(&m->step, sizeof(long long))) != cudaSuccess) return fail(e, "cudaMalloc step");
-  if ((e = cudaMalloc(&m->err, 2 * sizeof(int))) != cudaSuccess) return fail(e, "cudaMalloc err");
+  if ((e = cudaMalloc(&m->err, 3 * sizeof(int))) != cudaSuccess) return fail(e, "cudaMalloc err");
   std::vector<float> h(n);
   uint64_t st = seed;
   for (size_t q = 0; q < n; ++q) h[q] = (float)((double)(splitmix64(st) >> 11) * 0x1.0p-53 - 0.5);
@@ -183,7 +183,7 @@ int gnep_create(gnep_model** out, int n_species, const int* species_z, double rc
   cudaMemset(m->adam_v, 0, 4 * n);
   cudaMemset(m->grad, 0, 8 * n);
   cudaMemset(m->step, 0, sizeof(long long));
-  if ((e = cudaMemset(m->err, 0, 2 * sizeof(int))) != cudaSuccess) return fail(e, "init");
+  if ((e = cudaMemset(m->err, 0, 3 * sizeof(int))) != cudaSuccess) return fail(e, "init");
   *out = m;
   return GNEP_OK;
 }

@@ -125,7 +125,7 @@ struct gnep_model {
   float* adam_v = nullptr;
   double* grad = nullptr;   // device [n_params]
   long long* step = nullptr;  // device update count
-  int* err = nullptr;       // device error flag, then a block counter of the Adam kernel (err[1])
+  int* err = nullptr;       // device error flag, then block counters of the Adam (err[1]) and loss (err[2]) kernels
   gnep::DevModel dev() const {
     gnep::DevModel d;
     d.ns = shape.ns; d.nqr = shape.nqr; d.kr = shape.kr; d.nqa = shape.nqa; d.ka = shape.ka;

@@ -32,55 +32,6 @@ __device__ __forceinline__ double block_sums(double (&v)[K], double* sh) {
   return r;
 }
 
-// Per structure s (one block of 128 threads): the sums E_s and W_s (Eqs. 1, 4)
-// and the structure's squared residuals of Eqs. 10-12 (energy, virial, and the
-// force term over its atoms).  Each thread sums its few atoms in FP32; the 128
-// thread sums are combined in FP64 by a fixed tree.
-__global__ void __launch_bounds__(128) k_struct_loss(const int* __restrict__ soff, const float* __restrict__ Eatom,
-                                                     const float* __restrict__ Wat, const float* __restrict__ F,
-                                                     const double* __restrict__ le, const float* __restrict__ lf,
-                                                     const double* __restrict__ lv, double* __restrict__ Es,
-                                                     double* __restrict__ Ws, double* __restrict__ red) {
-  const int s = blockIdx.x;
-  const int a0 = soff[s], a1 = soff[s + 1];
-  float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
-    acc[0] += Eatom[i];
-#pragma unroll
-    for (int q = 0; q < 6; ++q) acc[1 + q] += Wat[6 * (size_t)i + q];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const float d = F[3 * (size_t)i + c] - lf[3 * (size_t)i + c];
-      acc[7] = fmaf(d, d, acc[7]);
-    }
-  }
-  __shared__ double sh[8][128];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) sh[q][threadIdx.x] = (double)acc[q];
-  __syncthreads();
-  for (int o = 64; o > 0; o >>= 1) {
-    if (threadIdx.x < o)
-#pragma unroll
-      for (int q = 0; q < 8; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x != 0) return;
-  const double inv = 1.0 / (double)(a1 - a0);
-  const double E = sh[0][0];
-  Es[s] = E;
-  const double de = E * inv - le[s];
-  double sv = 0.0;
-  for (int c = 0; c < 6; ++c) {
-    const double w = sh[1 + c][0];
-    Ws[6 * s + c] = w;
-    const double dv = w * inv - lv[6 * s + c];
-    sv += dv * dv;
-  }
-  red[3 * s] = de * de;
-  red[3 * s + 1] = sh[7][0];
-  red[3 * s + 2] = sv;
-}
-
 struct LossArgs {
   int N, S;
   double le, lf, lv, l2;
@@ -89,13 +40,12 @@ struct LossArgs {
   double inv_S, inv_3N, inv_6S, inv_np;  // reciprocal normalisers (0 for empty sets), formed on the host
 };
 
-// Loss terms and the scalar weights of the residuals:
+// Loss terms and the scalar weights of the residuals, by one block:
 // coef[0..3] = {L, L_e, L_f, L_v}; coef[4] = cf, coef[5] = ce, coef[6] = cv with
 //   a_i = cf (F_i - F_i^tar),  e_s = ce (E_s/N_s - E_s^tar)/N_s,
 //   B_s = cv (W_s/N_s - V_s^tar)/N_s  (off-diagonals halved).
-__global__ void __launch_bounds__(256) k_loss_final(LossArgs a, int nred, const double* __restrict__ red,
-                                                    const float* __restrict__ params, double* __restrict__ coef,
-                                                    int* __restrict__ err) {
+__device__ void loss_final_block(const LossArgs& a, int nred, const double* __restrict__ red,
+                                 const float* __restrict__ params, double* __restrict__ coef, int* __restrict__ err) {
   __shared__ double sh[32 * 4];
   __shared__ double tot[4];
   double v[4] = {0.0, 0.0, 0.0, 0.0};
@@ -133,6 +83,75 @@ __global__ void __launch_bounds__(256) k_loss_final(LossArgs a, int nred, const 
   coef[6] = 2.0 * a.lv * kv * a.inv_6S;  // Eq. 16
   if (!isfinite(L)) atomicOr(err, kErrNonFinite);
 }
+
+__global__ void __launch_bounds__(256) k_loss_final(LossArgs a, int nred, const double* __restrict__ red,
+                                                    const float* __restrict__ params, double* __restrict__ coef,
+                                                    int* __restrict__ err) {
+  loss_final_block(a, nred, red, params, coef, err);
+}
+
+// Per structure s (one block of 128 threads): the sums E_s and W_s (Eqs. 1, 4)
+// and the structure's squared residuals of Eqs. 10-12 (energy, virial, and the
+// force term over its atoms).  Each thread sums its few atoms in FP32; the 128
+// thread sums are combined in FP64 by a fixed tree.  The last block to finish
+// (counted in *done, which it resets) forms the loss terms from all blocks'
+// residuals in structure order.
+__global__ void __launch_bounds__(128) k_struct_loss(const int* __restrict__ soff, const float* __restrict__ Eatom,
+                                                     const float* __restrict__ Wat, const float* __restrict__ F,
+                                                     const double* __restrict__ le, const float* __restrict__ lf,
+                                                     const double* __restrict__ lv, double* __restrict__ Es,
+                                                     double* __restrict__ Ws, double* __restrict__ red, LossArgs la,
+                                                     const float* __restrict__ params, double* __restrict__ coef,
+                                                     int* __restrict__ err, int* __restrict__ done) {
+  const int s = blockIdx.x;
+  const int a0 = soff[s], a1 = soff[s + 1];
+  float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
+    acc[0] += Eatom[i];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) acc[1 + q] += Wat[6 * (size_t)i + q];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float d = F[3 * (size_t)i + c] - lf[3 * (size_t)i + c];
+      acc[7] = fmaf(d, d, acc[7]);
+    }
+  }
+  __shared__ double sh[8][128];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) sh[q][threadIdx.x] = (double)acc[q];
+  __syncthreads();
+  for (int o = 64; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + o];
+    __syncthreads();
+  }
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    const double inv = 1.0 / (double)(a1 - a0);
+    const double E = sh[0][0];
+    Es[s] = E;
+    const double de = E * inv - le[s];
+    double sv = 0.0;
+    for (int c = 0; c < 6; ++c) {
+      const double w = sh[1 + c][0];
+      Ws[6 * s + c] = w;
+      const double dv = w * inv - lv[6 * s + c];
+      sv += dv * dv;
+    }
+    red[3 * s] = de * de;
+    red[3 * s + 1] = sh[7][0];
+    red[3 * s + 2] = sv;
+    __threadfence();
+    last = atomicAdd(done, 1) == (int)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  loss_final_block(la, (int)gridDim.x, red, params, coef, err);
+  if (threadIdx.x == 0) *done = 0;
+}
+
 
 // Residual weights of the loss gradient: a_i for atoms i < N, then e_s and
 // B_s (off-diagonals halved) for structures s = i - N (Eqs. 14-16).
@@ -367,9 +386,6 @@ int run_loss_impl(const gnep_model* m, gnep_nlist* nl, const double* le, const f
                   const gnep_labels* y, cudaStream_t st) {
   Workspace& w = nl->ws;
   const int N = nl->n_atoms, S = nl->n_struct;
-  if (S > 0)
-    k_struct_loss<<<S, 128, 0, st>>>(nl->struct_off, w.Eatom, w.Wat, w.F, le, lf, lv, w.Es, w.Ws, w.red);
-  stage("struct_loss");
   LossArgs a;
   a.N = N; a.S = S; a.le = y->lambda_e; a.lf = y->lambda_f; a.lv = y->lambda_v; a.l2 = y->lambda_l2;
   a.form = y->loss_form; a.n_params = m->n_params;
@@ -377,8 +393,13 @@ int run_loss_impl(const gnep_model* m, gnep_nlist* nl, const double* le, const f
   a.inv_3N = N > 0 ? 1.0 / (3.0 * N) : 0.0;
   a.inv_6S = S > 0 ? 1.0 / (6.0 * S) : 0.0;
   a.inv_np = 1.0 / (double)m->n_params;
-  k_loss_final<<<1, 256, 0, st>>>(a, S, w.red, m->params, w.coef, m->err);
-  stage("loss_final");
+  if (S > 0) {  // per-structure residuals; the last block forms the loss terms
+    k_struct_loss<<<S, 128, 0, st>>>(nl->struct_off, w.Eatom, w.Wat, w.F, le, lf, lv, w.Es, w.Ws, w.red, a,
+                                     m->params, w.coef, m->err, m->err + 2);
+  } else {
+    k_loss_final<<<1, 256, 0, st>>>(a, 0, w.red, m->params, w.coef, m->err);
+  }
+  stage("struct_loss");
   if (N + S > 0)
     k_residuals<<<blocks_for(N + S, 256), 256, 0, st>>>(N, S, w.F, lf, nl->struct_off, w.Es, w.Ws, le, lv, w.coef,
                                                          w.a, w.es, w.Bs);
