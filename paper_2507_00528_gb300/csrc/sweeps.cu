@@ -307,14 +307,21 @@ __global__ void __launch_bounds__(128) k_force_atoms(int N, DevModel dm, const i
 #pragma unroll
       for (int k = 0; k < C::KR; ++k) ci[s][k] = chat[((size_t)i * C::NS + s) * C::KR + k];
     const int p1 = offR[i + 1];
-    for (int p = offR[i] + lane; p < p1; p += RL) {
-      const float4 r = rijR[p];
-      const int j = jR[p];
+    int p = offR[i] + lane;
+    float4 rn = p < p1 ? rijR[p] : make_float4(1.f, 0.f, 0.f, 0.f);  // the pair after the current one
+    int jn = p < p1 ? jR[p] : 0;
+    for (; p < p1; p += RL) {
+      const float4 r = rn;
+      const int j = jn;
+      if (p + RL < p1) {
+        rn = rijR[p + RL];
+        jn = jR[p + RL];
+      }
+      const float* cj = chat + ((size_t)j * C::NS + I) * C::KR;
       const float rr = sqrtf(r.x * r.x + r.y * r.y + r.z * r.z);
       float f[C::KR], fp[C::KR];
       radial_basis_d<C::KR>(rr, dm.rcr_inv, f, fp);
       const float dij = dot_row<C::NS, C::KR>(ci, (int)r.w, fp);
-      const float* cj = chat + ((size_t)j * C::NS + I) * C::KR;
       float dji = 0.f;
 #pragma unroll
       for (int k = 0; k < C::KR; ++k) dji = fmaf(cj[k], fp[k], dji);
