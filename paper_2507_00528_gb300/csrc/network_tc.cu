@@ -15,8 +15,12 @@
 // written once, as one partial per block and species; db0 = sum of alpha comes
 // out of the same accumulator through a column of ones appended to (s.G)^T.
 // All operands are K-major; the operands of the atom contraction are written
-// transposed by the epilogue.  The network in FP32 (network.cu) is the plain
-// form these modes are measured against.
+// transposed by the epilogue.  Per-atom rows are staged one 8 x 16-byte core
+// matrix per warp step with 4-byte stores that fill the 32 banks, and the
+// atom-contraction operands take padded core matrices where that costs no
+// block per SM, so that the epilogue's transposed stores do not collide.  The
+// network in FP32 (network.cu) is the plain form these modes are measured
+// against.
 #include "gnep_internal.h"
 #include "network.cuh"
 #include "tc.cuh"
@@ -27,7 +31,6 @@ namespace {
 
 constexpr int TA = 128;                      // atoms per tile = MMA rows = TMEM lanes
 constexpr int NTC = 256;                     // threads per block: warps w and w + 4 share TMEM lanes 32 (w % 4) ..
-constexpr int kLB = 16;                      // global loads a thread keeps in flight while staging a tile
 constexpr uint64_t kWaitNs = 1000000000ull;  // give up on an MMA completion after 1 s
 constexpr int kSmemPerSm = 233472;           // shared memory per SM (228 KB)
 
@@ -47,7 +50,7 @@ constexpr int op_bytes(int R, int C, uint32_t L) {
 constexpr int tc_fits(int smem, int cols) {
   const int by_smem = kSmemPerSm / (smem + 6 * 1024), by_tmem = 512 / cols;
   const int b = by_smem < by_tmem ? by_smem : by_tmem;
-  return b < 1 ? 1 : (b > 2 ? 2 : b);
+  return b < 1 ? 1 : (b > 3 ? 3 : b);
 }
 constexpr int kMaxDynSmem = 232448;  // per block (227 KB)
 
@@ -59,17 +62,25 @@ struct Layout {
     const int g = op_bytes<TF32>(TA, DPn, L), h = op_bytes<TF32>(TA, HPn, L);
     return (g > h ? g : h) + 2 * op_bytes<TF32>(HPn, DPn, L) + bO;
   }
-  static constexpr int bwd(uint32_t L) {
+  // L: operands contracted over v or mu; LT: the backward's operands contracted over the tile's atoms
+  static constexpr int bwd(uint32_t L, uint32_t LT) {
     const int g2 = 2 * op_bytes<TF32>(TA, DPn, L), h = op_bytes<TF32>(TA, HPn, L);
-    return (g2 > h ? g2 : h) + op_bytes<TF32>(DPn, TA, L) + op_bytes<TF32>(128, TA, L) + 2 * op_bytes<TF32>(HPn, DPn, L);
+    return (g2 > h ? g2 : h) + op_bytes<TF32>(DPn, TA, LT) + op_bytes<TF32>(128, TA, LT) +
+           2 * op_bytes<TF32>(HPn, DPn, L);
   }
   static constexpr int fwd_cols = tc::pow2_cols(HPn + DPn);
   static constexpr int bwd_cols = tc::pow2_cols(2 * HPn + 2 * DPn);
   // padded core matrices where they cost no block per SM and fit a block
   static constexpr uint32_t lbo() {
-    return (fwd(144) <= kMaxDynSmem && bwd(144) <= kMaxDynSmem &&
+    return (fwd(144) <= kMaxDynSmem && bwd(144, 144) <= kMaxDynSmem &&
             tc_fits(fwd(144), fwd_cols) >= tc_fits(fwd(128), fwd_cols) &&
-            tc_fits(bwd(144), bwd_cols) >= tc_fits(bwd(128), bwd_cols))
+            tc_fits(bwd(144, 144), bwd_cols) >= tc_fits(bwd(128, 128), bwd_cols))
+               ? 144u
+               : 128u;
+  }
+  // the atom-contraction operands alone, where padding all operands costs a block
+  static constexpr uint32_t lbo_t() {
+    return (bwd(lbo(), 144) <= kMaxDynSmem && tc_fits(bwd(lbo(), 144), bwd_cols) >= tc_fits(bwd(lbo(), 128), bwd_cols))
                ? 144u
                : 128u;
   }
@@ -79,15 +90,15 @@ template <bool TF32, int D, int HPn>
 struct Dims {
   using Lay = Layout<TF32, D, HPn>;
   static constexpr int DPn = Lay::DPn;
-  static constexpr uint32_t LBO = Lay::lbo();
+  static constexpr uint32_t LBO = Lay::lbo(), LBOT = Lay::lbo_t();
   static constexpr uint32_t sG = tc::sbo<TF32>(DPn, LBO);  // rows of length DPn:  [atoms][v], [mu][v]
   static constexpr uint32_t sH = tc::sbo<TF32>(HPn, LBO);  // rows of length HPn:  [atoms][mu], [v][mu]
-  static constexpr uint32_t sA = tc::sbo<TF32>(TA, LBO);   // rows of length TA:   [mu][atoms], [v][atoms]
+  static constexpr uint32_t sA = tc::sbo<TF32>(TA, LBOT);  // rows of length TA:   [mu][atoms], [v][atoms]
   static constexpr int bG = op_bytes<TF32>(TA, DPn, LBO);
   static constexpr int bH = op_bytes<TF32>(TA, HPn, LBO);
   static constexpr int bW0 = op_bytes<TF32>(HPn, DPn, LBO);
-  static constexpr int bT = op_bytes<TF32>(128, TA, LBO);  // [mu][atoms], 128 rows (the MMA's M) whatever H is
-  static constexpr int bGT = op_bytes<TF32>(DPn, TA, LBO);
+  static constexpr int bT = op_bytes<TF32>(128, TA, LBOT);  // [mu][atoms], 128 rows (the MMA's M) whatever H is
+  static constexpr int bGT = op_bytes<TF32>(DPn, TA, LBOT);
   static constexpr int OW = D + 1;          // row pitch (floats) of the FP32 output tile, odd: conflict-free rows
   static constexpr int bO = Lay::bO;
   // forward: RA (s.G, then beta) | W0 [mu][v] | W0t [v][mu] | output tile (E')
@@ -100,7 +111,7 @@ struct Dims {
   static constexpr int bwd_smem = bRA + bGT + bT + 2 * bW0;
   static constexpr int bwd_cols = Lay::bwd_cols;
   static_assert(bO <= bT, "the Gbar output tile lives in the [mu][atoms] operand");
-  static_assert(fwd_smem == Lay::fwd(LBO) && bwd_smem == Lay::bwd(LBO), "layout sizes");
+  static_assert(fwd_smem == Lay::fwd(LBO) && bwd_smem == Lay::bwd(LBO, LBOT), "layout sizes");
   static constexpr int fwd_minb = tc_fits(fwd_smem, fwd_cols);
   static constexpr int bwd_minb = tc_fits(bwd_smem, bwd_cols);
 };
@@ -124,36 +135,90 @@ __device__ void stage_weights(const DevModel& dm, int e, uint8_t* W0, uint8_t* W
 }
 
 // Rows `rows[a]` (a < TA, -1 = padding) of one or two per-atom arrays of
-// width D, zero-padded to DPn columns, handed to store(a, v, x0, x1).  Each
-// thread keeps LB loads in flight (LB / 2 of each of two arrays) before it
-// stores them.
-template <int D, int DPn, bool TWO, class F>
-__device__ __forceinline__ void stage_rows(const float* __restrict__ s0, const float* __restrict__ s1,
-                                           const int* rows, F store) {
-  constexpr int PER = TA * DPn / NTC;
-  constexpr int LB = TWO ? kLB / 2 : kLB;
+// width D, zero-padded to DPn columns, staged one core matrix per warp step:
+// the atoms 8 ab .. 8 ab + 7 and the EPC columns of column chunk vc.  Lane l
+// takes atom 8 ab + l / 4 and the EW = 4 / ES columns of word l % 4 of that
+// core row and hands them to store(a, v, x[array][e]), so that the warp's 32
+// word stores into an [atoms][v] operand fill the 32 banks.  A warp takes
+// consecutive blocks (all column chunks of two atom groups) and keeps NB
+// blocks of loads in flight.
+template <bool TF32, int D, int DPn, int NARR, class F>
+__device__ __forceinline__ void stage_blocks(const float* __restrict__ s0, const float* __restrict__ s1,
+                                             const int* rows, F store) {
+  constexpr int EPC = tc::Elem<TF32>::EPC, EW = 4 / tc::Elem<TF32>::ES, NVC = DPn / EPC;
+  constexpr int PERW = (TA / 8) * NVC / (NTC / 32), NB = 4;
+  static_assert((TA / 8) * NVC % (NTC / 32) == 0 && PERW % NB == 0, "blocks per warp");
+  const int lane = threadIdx.x & 31, b0 = (threadIdx.x >> 5) * PERW, ai = lane >> 2, w = lane & 3;
+#pragma unroll 1
+  for (int bb = 0; bb < PERW; bb += NB) {
+    float x[NB][NARR][EW];
 #pragma unroll
-  for (int b0 = 0; b0 < PER; b0 += LB) {
-    float x0[LB], x1[LB];
+    for (int u = 0; u < NB; ++u) {
+      const int blk = b0 + bb + u, a = 8 * (blk / NVC) + ai, v = EPC * (blk % NVC) + EW * w, r = rows[a];
 #pragma unroll
-    for (int u = 0; u < LB; ++u) {
-      const int k = b0 + u;
-      if (k < PER) {
-        const int q = threadIdx.x + k * NTC, a = q / DPn, v = q % DPn, r = rows[a];
-        const bool in = r >= 0 && v < D;
-        x0[u] = in ? s0[(size_t)r * D + v] : 0.f;
-        if (TWO) x1[u] = in ? s1[(size_t)r * D + v] : 0.f;
+      for (int e = 0; e < EW; ++e) {
+        const bool in = r >= 0 && v + e < D;
+        x[u][0][e] = in ? s0[(size_t)r * D + v + e] : 0.f;
+        if constexpr (NARR > 1) x[u][NARR - 1][e] = in ? s1[(size_t)r * D + v + e] : 0.f;
       }
     }
 #pragma unroll
-    for (int u = 0; u < LB; ++u) {
-      const int k = b0 + u;
-      if (k < PER) {
-        const int q = threadIdx.x + k * NTC;
-        store(q / DPn, q % DPn, x0[u], TWO ? x1[u] : 0.f);
-      }
+    for (int u = 0; u < NB; ++u) {
+      const int blk = b0 + bb + u;
+      store(8 * (blk / NVC) + ai, EPC * (blk % NVC) + EW * w, x[u]);
     }
   }
+}
+
+// This lane's values of stage_blocks (atom a, columns v .. v + EW - 1) into a
+// [v][atoms] operand as one word store.  BF16: lanes l and l ^ 4 (atoms a and
+// a ^ 1) swap one value, so that the lane of the even atom stores column v of
+// both atoms and its partner column v + 1; the warp's 32 words fill the 32
+// banks.  TF32: one element per word.  Called by all 32 lanes together.
+template <bool TF32>
+__device__ __forceinline__ void st_trans(uint8_t* base, int a, int v, const float (&t)[4 / tc::Elem<TF32>::ES],
+                                         uint32_t sbo_, uint32_t lbo) {
+  if constexpr (TF32) {
+    tc::st_elem<true>(base, tc::core_off<true>(v, a, sbo_, lbo), t[0]);
+  } else {
+    const bool odd = a & 1;
+    const float recv = __shfl_xor_sync(0xffffffffu, odd ? t[0] : t[1], 4);
+    const float pair[2] = {odd ? recv : t[0], odd ? t[1] : recv};
+    tc::st_word<false>(base, tc::core_off<false>(odd ? v + 1 : v, a & ~1, sbo_, lbo), pair);
+  }
+}
+
+// tanh of the hidden layer: the hardware approximation (relative error about
+// 2^-11, below the BF16 rounding of the operands it feeds) with BF16 operands,
+// the full-precision function with TF32 operands.
+template <bool TF32>
+__device__ __forceinline__ float act_tanh(float x) {
+  if constexpr (TF32) {
+    return tanhf(x);
+  } else {
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+  }
+}
+
+// Sums of v[0..15] over the 32 lanes of the warp by halving exchanges (16
+// shuffles instead of 80): after the exchange over lane distance 16 >> s a
+// lane keeps the half of its values whose index bit 3 - s matches its lane
+// bit 4 - s.  The sum of v[i] ends in lanes 2i and 2i + 1.
+__device__ __forceinline__ float warp_colsum16(float (&v)[16]) {
+  const int ln = threadIdx.x & 31;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const int h = 8 >> s, o = 16 >> s;
+    const bool up = (ln & o) != 0;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const float send = up ? v[i] : v[i + h], keep = up ? v[i + h] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
 // Make this thread's generic-proxy shared-memory writes and TMEM reads
@@ -193,6 +258,7 @@ __global__ void __launch_bounds__(NTC, (Dims<TF32, D, HPn>::fwd_minb))
                  float* __restrict__ Eatom, float* __restrict__ chat, int* __restrict__ err) {
   using Dm = Dims<TF32, D, HPn>;
   constexpr int DPn = Dm::DPn, OW = Dm::OW, NCZ = HPn / 16, NCE = DPn / 16, NJK = NS * KR;
+  constexpr int EW = 4 / tc::Elem<TF32>::ES;  // operand elements per 4-byte word
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* RA = smem;
   uint8_t* W0 = RA + Dm::fRA;
@@ -228,8 +294,11 @@ __global__ void __launch_bounds__(NTC, (Dims<TF32, D, HPn>::fwd_minb))
     }
     if (tid < TA) rows[tid] = tid < na ? T.perm[a0 + tid] : -1;
     __syncthreads();
-    stage_rows<D, DPn, false>(G, nullptr, rows, [&](int a, int v, float g, float) {
-      tc::st_elem<TF32>(RA, tc::core_off<TF32>(a, v, Dm::sG, Dm::LBO), sc[v] * g);
+    stage_blocks<TF32, D, DPn, 1>(G, nullptr, rows, [&](int a, int v, const auto& x) {
+      float g[EW];
+#pragma unroll
+      for (int e = 0; e < EW; ++e) g[e] = sc[v + e] * x[0][e];
+      tc::st_word<TF32>(RA, tc::core_off<TF32>(a, v, Dm::sG, Dm::LBO), g);
     });
     sync_for_mma();
     if (tid == 0) {
@@ -245,7 +314,7 @@ __global__ void __launch_bounds__(NTC, (Dims<TF32, D, HPn>::fwd_minb))
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
         const int mu = 16 * c + q;
-        const float x = tanhf(z[q] + b0s[mu]);
+        const float x = act_tanh<TF32>(z[q] + b0s[mu]);
         E = fmaf(w1s[mu], x, E);
         bt[q] = w1s[mu] * (1.f - x * x);
       }
@@ -312,6 +381,7 @@ __global__ void __launch_bounds__(NTC, (Dims<TF32, D, HPn>::bwd_minb))
                  float* __restrict__ part, int part_stride, int* __restrict__ err) {
   using Dm = Dims<TF32, D, HPn>;
   constexpr int DPn = Dm::DPn, OW = Dm::OW, NCZ = HPn / 16, NCD = DPn / 16;
+  constexpr int EW = 4 / tc::Elem<TF32>::ES;  // operand elements per 4-byte word
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* RA = smem;          // s.G | s.Gdot as [atoms][v]; then alpha as [atoms][mu]
   uint8_t* RG = RA + Dm::bRA;  // (s.G)^T with a row of ones at v = D, then (s.Gdot)^T, as [v][atoms]
@@ -387,11 +457,18 @@ __global__ void __launch_bounds__(NTC, (Dims<TF32, D, HPn>::bwd_minb))
     __syncthreads();
     if (tid == 0)
       for (int a = 0; a < na; ++a) cb1 += ei[a];
-    stage_rows<D, DPn, true>(G, Gd, rows, [&](int a, int v, float g, float gd) {
+    stage_blocks<TF32, D, DPn, 2>(G, Gd, rows, [&](int a, int v, const auto& x) {
+      float g[EW], gd[EW], gt[EW];
+#pragma unroll
+      for (int e = 0; e < EW; ++e) {
+        g[e] = sc[v + e] * x[0][e];
+        gd[e] = sc[v + e] * x[1][e];
+        gt[e] = v + e == D ? (rows[a] >= 0 ? 1.f : 0.f) : g[e];
+      }
       const uint32_t o = tc::core_off<TF32>(a, v, Dm::sG, Dm::LBO);
-      tc::st_elem<TF32>(RA, o, sc[v] * g);
-      tc::st_elem<TF32>(RA + Dm::bG, o, sc[v] * gd);
-      tc::st_elem<TF32>(RG, tc::core_off<TF32>(v, a, Dm::sA, Dm::LBO), v == D ? (rows[a] >= 0 ? 1.f : 0.f) : sc[v] * g);
+      tc::st_word<TF32>(RA, o, g);
+      tc::st_word<TF32>(RA + Dm::bG, o, gd);
+      st_trans<TF32>(RG, a, v, gt, Dm::sA, Dm::LBOT);
     });
     sync_for_mma();
     if (tid == 0) {
@@ -403,22 +480,21 @@ __global__ void __launch_bounds__(NTC, (Dims<TF32, D, HPn>::bwd_minb))
     // alpha -> RA ([atoms][mu]) and RT ([mu][atoms]); column sums of e x - (1 - x^2) zdot
     const float ea = ei[arow];
     for (int c = half; c < NCZ; c += 2) {
-      float z[16], zd[16], al[16];
+      float z[16], zd[16], al[16], q1[16];
       tc::ld16(lane + cZ + 16 * c, z);
       tc::ld16(lane + cZd + 16 * c, zd);
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
         const int mu = 16 * c + q;
-        const float x = tanhf(z[q] + b0s[mu]);
+        const float x = act_tanh<TF32>(z[q] + b0s[mu]);
         const float t1 = 1.f - x * x;
         const float beta = w1s[mu] * t1;
         al[q] = ea * beta + 2.f * x * beta * zd[q];
-        float q1 = ea * x - t1 * zd[q];  // zero for padded atoms (e = 0, zdot = 0)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) q1 += __shfl_xor_sync(0xffffffffu, q1, o);
-        if (ln == 0) wpart[warp & 3][mu] = q1;
-        tc::st_elem<TF32>(RT, tc::core_off<TF32>(mu, arow, Dm::sA, Dm::LBO), al[q]);
+        q1[q] = ea * x - t1 * zd[q];  // zero for padded atoms (e = 0, zdot = 0)
+        tc::st_elem<TF32>(RT, tc::core_off<TF32>(mu, arow, Dm::sA, Dm::LBOT), al[q]);
       }
+      const float q1s = warp_colsum16(q1);
+      if ((ln & 1) == 0) wpart[warp & 3][16 * c + (ln >> 1)] = q1s;
 #pragma unroll
       for (int q = 0; q < 16; q += tc::Elem<TF32>::EPC)
         tc::st_chunk<TF32>(RA, tc::core_off<TF32>(arow, 16 * c + q, Dm::sH, Dm::LBO), al + q);
@@ -427,7 +503,7 @@ __global__ void __launch_bounds__(NTC, (Dims<TF32, D, HPn>::bwd_minb))
     if (tid < HPn) acc_w1 += ((wpart[0][tid] + wpart[1][tid]) + wpart[2][tid]) + wpart[3][tid];
     if (tid == 0) {
       tc::mma_chain<TF32>(tm + cGb, RA, Dm::sH, W0t, Dm::sH, HPn, DPn, false, Dm::LBO);
-      tc::mma_chain<TF32>(tm + cW, RT, Dm::sA, RG, Dm::sA, TA, DPn, !fresh, Dm::LBO);
+      tc::mma_chain<TF32>(tm + cW, RT, Dm::sA, RG, Dm::sA, TA, DPn, !fresh, Dm::LBOT);
       tc::commit(&mbar);
     }
     if (!(ok = wait_mma(&mbar, ph))) break;
@@ -454,17 +530,20 @@ __global__ void __launch_bounds__(NTC, (Dims<TF32, D, HPn>::bwd_minb))
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
         const int mu = 16 * c + q;
-        const float x = tanhf(z[q] + b0s[mu]);
-        tc::st_elem<TF32>(RT, tc::core_off<TF32>(mu, arow, Dm::sA, Dm::LBO), -w1s[mu] * (1.f - x * x));
+        const float x = act_tanh<TF32>(z[q] + b0s[mu]);
+        tc::st_elem<TF32>(RT, tc::core_off<TF32>(mu, arow, Dm::sA, Dm::LBOT), -w1s[mu] * (1.f - x * x));
       }
     }
     zero_pad_rows();
-    stage_rows<D, DPn, false>(Gd, nullptr, rows, [&](int a, int v, float gd, float) {
-      tc::st_elem<TF32>(RG, tc::core_off<TF32>(v, a, Dm::sA, Dm::LBO), sc[v] * gd);
+    stage_blocks<TF32, D, DPn, 1>(Gd, nullptr, rows, [&](int a, int v, const auto& x) {
+      float gt[EW];
+#pragma unroll
+      for (int e = 0; e < EW; ++e) gt[e] = sc[v + e] * x[0][e];
+      st_trans<TF32>(RG, a, v, gt, Dm::sA, Dm::LBOT);
     });
     sync_for_mma();
     if (tid == 0) {
-      tc::mma_chain<TF32>(tm + cW, RT, Dm::sA, RG, Dm::sA, TA, DPn, true, Dm::LBO);
+      tc::mma_chain<TF32>(tm + cW, RT, Dm::sA, RG, Dm::sA, TA, DPn, true, Dm::LBOT);
       tc::commit(&mbar);
     }
     if (!(ok = wait_mma(&mbar, ph))) break;

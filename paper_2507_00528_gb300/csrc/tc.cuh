@@ -11,6 +11,9 @@
 // along K are LBO bytes apart (the descriptor's leading-dimension offset): 128
 // packs them, 144 leaves 16 bytes after each, which puts the core matrices
 // that one warp's row-wise or transposed element stores touch 4 banks apart.
+// The two operands of one MMA may take different LBOs (each has its own
+// descriptor); mma_chain takes one for both, so operands contracted with each
+// other share it.
 // One MMA of M = 128 consumes 32 bytes of K (16 BF16 or 8 TF32 elements) and
 // accumulates D[m][n] += sum_k A[m][k] B[n][k] in FP32 in tensor memory, row m
 // in TMEM lane m, column n in TMEM column n.
@@ -61,6 +64,16 @@ __device__ __forceinline__ void st_elem(uint8_t* base, uint32_t off, float x) {
     *reinterpret_cast<uint32_t*>(base + off) = to_tf32(x);
   else
     *reinterpret_cast<uint16_t*>(base + off) = to_bf16(x);
+}
+
+// Store one 4-byte word: 4 / ES consecutive columns of one row (the first at a
+// column divisible by 4 / ES).
+template <bool TF32>
+__device__ __forceinline__ void st_word(uint8_t* base, uint32_t off, const float (&x)[4 / Elem<TF32>::ES]) {
+  if constexpr (TF32)
+    *reinterpret_cast<uint32_t*>(base + off) = to_tf32(x[0]);
+  else
+    *reinterpret_cast<uint32_t*>(base + off) = (uint32_t)to_bf16(x[0]) | ((uint32_t)to_bf16(x[1]) << 16);
 }
 
 // Store one 16-byte core row: EPC consecutive columns c0.. of row r (c0 % EPC == 0).
