@@ -188,6 +188,32 @@ __device__ __forceinline__ void st_trans(uint8_t* base, int a, int v, const floa
   }
 }
 
+// The [v][atoms] operand from an [atoms][v] operand already in shared memory
+// (same values, already rounded), in the blocks and lane roles of
+// stage_blocks: each lane reads its word and, for BF16, swaps one half with
+// lane l ^ 4 as st_trans does.  Called by all threads of the block.
+template <bool TF32, int DPn>
+__device__ __forceinline__ void transpose_blocks(const uint8_t* src, uint32_t sbo_src, uint32_t lbo_src, uint8_t* dst,
+                                                 uint32_t sbo_dst, uint32_t lbo_dst) {
+  constexpr int EPC = tc::Elem<TF32>::EPC, EW = 4 / tc::Elem<TF32>::ES, NVC = DPn / EPC;
+  constexpr int PERW = (TA / 8) * NVC / (NTC / 32);
+  const int lane = threadIdx.x & 31, b0 = (threadIdx.x >> 5) * PERW, ai = lane >> 2, w = lane & 3;
+#pragma unroll 4
+  for (int k = 0; k < PERW; ++k) {
+    const int blk = b0 + k, a = 8 * (blk / NVC) + ai, v = EPC * (blk % NVC) + EW * w;
+    const uint32_t word = *reinterpret_cast<const uint32_t*>(src + tc::core_off<TF32>(a, v, sbo_src, lbo_src));
+    if constexpr (TF32) {
+      *reinterpret_cast<uint32_t*>(dst + tc::core_off<true>(v, a, sbo_dst, lbo_dst)) = word;
+    } else {
+      // low half: column v, high half: column v + 1 (of atom a)
+      const bool odd = a & 1;
+      const uint32_t recv = __shfl_xor_sync(0xffffffffu, odd ? (word & 0xFFFFu) : (word >> 16), 4);
+      const uint32_t out = odd ? (recv | (word & 0xFFFF0000u)) : ((word & 0xFFFFu) | (recv << 16));
+      *reinterpret_cast<uint32_t*>(dst + tc::core_off<false>(odd ? v + 1 : v, a & ~1, sbo_dst, lbo_dst)) = out;
+    }
+  }
+}
+
 // tanh of the hidden layer: the hardware approximation (relative error about
 // 2^-11, below the BF16 rounding of the operands it feeds) with BF16 operands,
 // the full-precision function with TF32 operands.
@@ -391,7 +417,7 @@ __global__ void __launch_bounds__(NTC, (Dims<TF32, D, HPn>::bwd_minb))
   float* O = reinterpret_cast<float*>(RT);
   __shared__ float b0s[HPn], w1s[HPn], sc[DPn], wpart[4][HPn];
   __shared__ int rows[TA];
-  __shared__ float ei[TA];
+  __shared__ float cbp[4];
   __shared__ uint64_t mbar;
   __shared__ uint32_t tbase;
   const int tid = threadIdx.x, warp = tid >> 5, ln = tid & 31, half = warp >> 2;
@@ -449,14 +475,11 @@ __global__ void __launch_bounds__(NTC, (Dims<TF32, D, HPn>::bwd_minb))
       fresh = true;
       cur_e = e;
     }
-    if (tid < TA) {
-      const int r = tid < na ? T.perm[a0 + tid] : -1;
-      rows[tid] = r;
-      ei[tid] = r >= 0 ? es[atom_struct[r]] : 0.f;
-    }
+    if (tid < TA) rows[tid] = tid < na ? T.perm[a0 + tid] : -1;
     __syncthreads();
-    if (tid == 0)
-      for (int a = 0; a < na; ++a) cb1 += ei[a];
+    // e_i of this thread's atom: the structure index is fetched beside the
+    // staging loads and the weight during the first products
+    const int s_a = rows[arow] >= 0 ? atom_struct[rows[arow]] : -1;
     stage_blocks<TF32, D, DPn, 2>(G, Gd, rows, [&](int a, int v, const auto& x) {
       float g[EW], gd[EW], gt[EW];
 #pragma unroll
@@ -470,6 +493,7 @@ __global__ void __launch_bounds__(NTC, (Dims<TF32, D, HPn>::bwd_minb))
       tc::st_word<TF32>(RA + Dm::bG, o, gd);
       st_trans<TF32>(RG, a, v, gt, Dm::sA, Dm::LBOT);
     });
+    const float ea = s_a >= 0 ? es[s_a] : 0.f;
     sync_for_mma();
     if (tid == 0) {
       tc::mma_chain<TF32>(tm + cZ, RA, Dm::sG, W0, Dm::sG, DPn, HPn, false, Dm::LBO);
@@ -478,7 +502,12 @@ __global__ void __launch_bounds__(NTC, (Dims<TF32, D, HPn>::bwd_minb))
     }
     if (!(ok = wait_mma(&mbar, ph))) break;
     // alpha -> RA ([atoms][mu]) and RT ([mu][atoms]); column sums of e x - (1 - x^2) zdot
-    const float ea = ei[arow];
+    if (half == 0) {  // the tile's sum of e_i, for db1
+      float se = ea;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) se += __shfl_xor_sync(0xffffffffu, se, o);
+      if (ln == 0) cbp[warp] = se;
+    }
     for (int c = half; c < NCZ; c += 2) {
       float z[16], zd[16], al[16], q1[16];
       tc::ld16(lane + cZ + 16 * c, z);
@@ -501,6 +530,7 @@ __global__ void __launch_bounds__(NTC, (Dims<TF32, D, HPn>::bwd_minb))
     }
     sync_for_mma();
     if (tid < HPn) acc_w1 += ((wpart[0][tid] + wpart[1][tid]) + wpart[2][tid]) + wpart[3][tid];
+    if (tid == 0) cb1 += ((cbp[0] + cbp[1]) + cbp[2]) + cbp[3];
     if (tid == 0) {
       tc::mma_chain<TF32>(tm + cGb, RA, Dm::sH, W0t, Dm::sH, HPn, DPn, false, Dm::LBO);
       tc::mma_chain<TF32>(tm + cW, RT, Dm::sA, RG, Dm::sA, TA, DPn, !fresh, Dm::LBOT);
@@ -535,12 +565,17 @@ __global__ void __launch_bounds__(NTC, (Dims<TF32, D, HPn>::bwd_minb))
       }
     }
     zero_pad_rows();
-    stage_blocks<TF32, D, DPn, 1>(Gd, nullptr, rows, [&](int a, int v, const auto& x) {
-      float gt[EW];
+    if constexpr (Dm::bH <= Dm::bG) {
+      // s.Gdot is still in RA behind the alpha operand
+      transpose_blocks<TF32, DPn>(RA + Dm::bG, Dm::sG, Dm::LBO, RG, Dm::sA, Dm::LBOT);
+    } else {
+      stage_blocks<TF32, D, DPn, 1>(Gd, nullptr, rows, [&](int a, int v, const auto& x) {
+        float gt[EW];
 #pragma unroll
-      for (int e = 0; e < EW; ++e) gt[e] = sc[v + e] * x[0][e];
-      st_trans<TF32>(RG, a, v, gt, Dm::sA, Dm::LBOT);
-    });
+        for (int e = 0; e < EW; ++e) gt[e] = sc[v + e] * x[0][e];
+        st_trans<TF32>(RG, a, v, gt, Dm::sA, Dm::LBOT);
+      });
+    }
     sync_for_mma();
     if (tid == 0) {
       tc::mma_chain<TF32>(tm + cW, RT, Dm::sA, RG, Dm::sA, TA, DPn, true, Dm::LBOT);
