@@ -1,7 +1,8 @@
 // Loss (Eqs. 9-12), residual weights, parameter-gradient reductions
 // (Eqs. 13-16, D1.18-D1.21), Adam with the Eq. 17 schedule, descriptor scale
-// and the species-grouped atom order.  Every cross-atom sum is FP64 in a fixed
-// order, so a step is bit-reproducible.
+// and the species-grouped atom order.  Every cross-atom sum runs in a fixed
+// order, so a step is bit-reproducible: FP32 leaves, FP64 above them (the
+// per-structure sums combine a warp's lanes as exact FP32 pairs first).
 #include <cmath>
 
 #include "gnep_internal.h"
@@ -30,6 +31,30 @@ __device__ __forceinline__ double block_sums(double (&v)[K], double* sh) {
   if (threadIdx.x < K)
     for (int w = 0; w < nw; ++w) r += sh[w * K + threadIdx.x];
   return r;
+}
+
+// Sums carried as FP32 pairs hi + lo without rounding error in the additions
+// (Knuth's TwoSum for the sum of the high parts and again to renormalise), so
+// that a warp's cross-atom sums keep about 44 significant bits on the FP32
+// pipes; FP64 is used only above the warps.
+struct F2 {
+  float hi, lo;
+};
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
+  const float s = a.hi + b.hi, bs = s - a.hi;
+  const float e = (a.hi - (s - bs)) + (b.hi - bs);  // s + e = a.hi + b.hi exactly
+  const float t = e + (a.lo + b.lo);
+  const float h = s + t, bh = h - s;
+  return {h, (s - (h - bh)) + (t - bh)};  // h + lo = s + t exactly
+}
+// The sum over the warp's 32 lanes (xor butterflies; every lane gets a sum).
+__device__ __forceinline__ F2 f2_warp_sum(F2 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const F2 w = {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+    v = f2_add(v, w);
+  }
+  return v;
 }
 
 struct LossArgs {
@@ -92,15 +117,19 @@ __global__ void __launch_bounds__(256) k_loss_final(LossArgs a, int nred, const 
 
 // Per structure s (one block of 128 threads): the sums E_s and W_s (Eqs. 1, 4)
 // and the structure's squared residuals of Eqs. 10-12 (energy, virial, and the
-// force term over its atoms).  Each thread sums its few atoms in FP32; the 128
-// thread sums are combined in FP64 by a fixed tree.  The last block to finish
-// (counted in *done, which it resets) forms the loss terms from all blocks'
-// residuals in structure order.
+// force term over its atoms), and the residuals divided by N_s for the weights
+// of the loss gradient: rn[7 s] = (E_s/N_s - E_s^tar)/N_s, rn[7 s + 1 + c] =
+// (W_sc/N_s - V_sc^tar)/N_s.  Each thread sums its few atoms in FP32, the
+// warps combine their lanes as FP32 pairs (F2) and the four warp sums are
+// added in FP64 in order.  The last block to finish (counted in *done, which
+// it resets) forms the loss terms from all blocks' residuals in structure
+// order.
 __global__ void __launch_bounds__(128) k_struct_loss(const int* __restrict__ soff, const float* __restrict__ Eatom,
                                                      const float* __restrict__ Wat, const float* __restrict__ F,
                                                      const double* __restrict__ le, const float* __restrict__ lf,
                                                      const double* __restrict__ lv, double* __restrict__ Es,
-                                                     double* __restrict__ Ws, double* __restrict__ red, LossArgs la,
+                                                     double* __restrict__ Ws, double* __restrict__ red,
+                                                     double* __restrict__ rn, LossArgs la,
                                                      const float* __restrict__ params, double* __restrict__ coef,
                                                      int* __restrict__ err, int* __restrict__ done) {
   const int s = blockIdx.x;
@@ -116,31 +145,39 @@ __global__ void __launch_bounds__(128) k_struct_loss(const int* __restrict__ sof
       acc[7] = fmaf(d, d, acc[7]);
     }
   }
-  __shared__ double sh[8][128];
+  __shared__ float2 wsum[4][8];
+  __shared__ double tot[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int q = 0; q < 8; ++q) sh[q][threadIdx.x] = (double)acc[q];
-  __syncthreads();
-  for (int o = 64; o > 0; o >>= 1) {
-    if (threadIdx.x < o)
-#pragma unroll
-      for (int q = 0; q < 8; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + o];
-    __syncthreads();
+  for (int q = 0; q < 8; ++q) {
+    const F2 v = f2_warp_sum(F2{acc[q], 0.f});
+    if (lane == 0) wsum[warp][q] = make_float2(v.hi, v.lo);
   }
+  __syncthreads();
+  if (threadIdx.x < 8) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) t += (double)wsum[w][threadIdx.x].x + (double)wsum[w][threadIdx.x].y;
+    tot[threadIdx.x] = t;
+  }
+  __syncthreads();
   __shared__ bool last;
   if (threadIdx.x == 0) {
     const double inv = 1.0 / (double)(a1 - a0);
-    const double E = sh[0][0];
+    const double E = tot[0];
     Es[s] = E;
     const double de = E * inv - le[s];
+    rn[7 * s] = de * inv;
     double sv = 0.0;
     for (int c = 0; c < 6; ++c) {
-      const double w = sh[1 + c][0];
+      const double w = tot[1 + c];
       Ws[6 * s + c] = w;
       const double dv = w * inv - lv[6 * s + c];
+      rn[7 * s + 1 + c] = dv * inv;
       sv += dv * dv;
     }
     red[3 * s] = de * de;
-    red[3 * s + 1] = sh[7][0];
+    red[3 * s + 1] = tot[7];
     red[3 * s + 2] = sv;
     __threadfence();
     last = atomicAdd(done, 1) == (int)gridDim.x - 1;
@@ -152,14 +189,12 @@ __global__ void __launch_bounds__(128) k_struct_loss(const int* __restrict__ sof
   if (threadIdx.x == 0) *done = 0;
 }
 
-
 // Residual weights of the loss gradient: a_i for atoms i < N, then e_s and
-// B_s (off-diagonals halved) for structures s = i - N (Eqs. 14-16).
+// B_s (off-diagonals halved) for structures s = i - N (Eqs. 14-16), from the
+// structures' residuals divided by N_s (rn) that the loss kernel left.
 __global__ void k_residuals(int N, int S, const float* __restrict__ F, const float* __restrict__ lf,
-                            const int* __restrict__ soff, const double* __restrict__ Es,
-                            const double* __restrict__ Ws, const double* __restrict__ le,
-                            const double* __restrict__ lv, const double* __restrict__ coef,
-                            float4* __restrict__ a, float* __restrict__ es, float* __restrict__ Bs) {
+                            const double* __restrict__ rn, const double* __restrict__ coef, float4* __restrict__ a,
+                            float* __restrict__ es, float* __restrict__ Bs) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < N) {
     const float cf = (float)coef[4];
@@ -169,10 +204,9 @@ __global__ void k_residuals(int N, int S, const float* __restrict__ F, const flo
   }
   const int s = i - N;
   if (s >= S) return;
-  const double inv = 1.0 / (double)(soff[s + 1] - soff[s]);
-  es[s] = (float)(coef[5] * (Es[s] * inv - le[s]) * inv);
+  es[s] = (float)(coef[5] * rn[7 * s]);
   for (int c = 0; c < 6; ++c) {
-    const double g = coef[6] * (Ws[6 * s + c] * inv - lv[6 * s + c]) * inv;
+    const double g = coef[6] * rn[7 * s + 1 + c];
     Bs[6 * s + c] = (float)(c < 3 ? g : 0.5 * g);
   }
 }
@@ -182,10 +216,11 @@ __global__ void k_residuals(int N, int S, const float* __restrict__ F, const flo
 // grad[q] = sum over block partials + 2 lambda_l2 theta_q / N_par; network
 // parameters come from the network backward pass (net_part), the coefficients
 // from the c-gradient sweeps (cpart).  A block takes 32
-// consecutive parameters (coalesced rows) and 16 subsets of the partial rows:
-// each thread sums its rows in FP32 (at most a few dozen leaves), the 16
-// subset sums of a parameter are combined in FP64 in a fixed order.
-constexpr int kGfCols = 32, kGfRows = 16;
+// consecutive parameters (coalesced rows) and 32 subsets of the partial rows:
+// each thread sums its rows in FP32 (at most a few dozen leaves, eight loads
+// in flight), the 32 subset sums of a parameter are combined in FP64 in a
+// fixed order.
+constexpr int kGfCols = 32, kGfRows = 32;
 
 __global__ void __launch_bounds__(kGfCols* kGfRows) k_grad_final(DevModel dm, int ns, int nb_net, int nb_cg,
                                                                  const float* __restrict__ net_part,
@@ -209,7 +244,7 @@ __global__ void __launch_bounds__(kGfCols* kGfRows) k_grad_final(DevModel dm, in
       src = cpart + (q - dm.off_cR);
       nb = nb_cg;
     }
-#pragma unroll 4
+#pragma unroll 8
     for (int b = ty; b < nb; b += kGfRows) leaf += src[(size_t)b * stride];
   }
   sh[ty][tx] = (double)leaf;
@@ -359,7 +394,8 @@ __global__ void __launch_bounds__(kPermBlock) k_species_scatter(int N, int ns, c
 
 }  // namespace
 
-int64_t loss_partial_doubles(int n_struct) { return 3LL * (n_struct > 0 ? n_struct : 1); }
+// Loss partials per structure: three squared residuals and seven residuals divided by N_s.
+int64_t loss_partial_doubles(int n_struct) { return 10LL * (n_struct > 0 ? n_struct : 1); }
 
 int run_species_perm(gnep_nlist* nl, cudaStream_t st) {
   int* soff_dev = nullptr;
@@ -394,15 +430,15 @@ int run_loss_impl(const gnep_model* m, gnep_nlist* nl, const double* le, const f
   a.inv_6S = S > 0 ? 1.0 / (6.0 * S) : 0.0;
   a.inv_np = 1.0 / (double)m->n_params;
   if (S > 0) {  // per-structure residuals; the last block forms the loss terms
-    k_struct_loss<<<S, 128, 0, st>>>(nl->struct_off, w.Eatom, w.Wat, w.F, le, lf, lv, w.Es, w.Ws, w.red, a,
-                                     m->params, w.coef, m->err, m->err + 2);
+    k_struct_loss<<<S, 128, 0, st>>>(nl->struct_off, w.Eatom, w.Wat, w.F, le, lf, lv, w.Es, w.Ws, w.red,
+                                     w.red + 3 * (size_t)S, a, m->params, w.coef, m->err, m->err + 2);
   } else {
     k_loss_final<<<1, 256, 0, st>>>(a, 0, w.red, m->params, w.coef, m->err);
   }
   stage("struct_loss");
   if (N + S > 0)
-    k_residuals<<<blocks_for(N + S, 256), 256, 0, st>>>(N, S, w.F, lf, nl->struct_off, w.Es, w.Ws, le, lv, w.coef,
-                                                         w.a, w.es, w.Bs);
+    k_residuals<<<blocks_for(N + S, 256), 256, 0, st>>>(N, S, w.F, lf, w.red + 3 * (size_t)S, w.coef, w.a, w.es,
+                                                         w.Bs);
   stage("residuals");
   GNEP_CHECK_LAUNCH("loss");
   return GNEP_OK;
