@@ -139,7 +139,16 @@ int gnep_compute_descriptor_scale(gnep_model *m, const gnep_nlist *nl, void *str
 int gnep_build_neighbors(gnep_model *m, const gnep_batch *b, gnep_nlist **out,
                          void *stream);
 /* Rebuild `nl` in place for a batch of the same n_struct and n_atoms (new
- * positions, cells or species); grows the lists only if the pair count grows. */
+ * positions, cells or species); grows the lists only if the pair count grows.
+ * Synchronises with the host once, when the pair counts are known (input
+ * errors such as unwrapped positions are returned then), and returns with the
+ * rest of the build (compaction, reverse entries, tile upload) queued on
+ * `stream`: every call that reads `nl` afterwards, on any stream, is ordered
+ * after that work by an event the list keeps.  The batch's host arrays may be
+ * reused once this returns.  The lists' internal consistency check of that
+ * queued work is reported by gnep_sync_status() (or by the next
+ * gnep_build_neighbors / gnep_md_verlet).  The caller keeps the usual duty of
+ * not rebuilding a list that queued work on another stream still reads. */
 int gnep_rebuild_neighbors(gnep_model *m, const gnep_batch *b, gnep_nlist *nl,
                            void *stream);
 int gnep_nlist_destroy(gnep_nlist *nl);

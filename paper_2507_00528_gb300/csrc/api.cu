@@ -247,8 +247,21 @@ static int check_nlist(const gnep_model* m, const gnep_nlist* nl) {
   return GNEP_OK;
 }
 
+// Orders the work that follows on `st` after the device work of the last
+// build of `nl` (a rebuild returns before that work has finished).
+static int after_build(const gnep_nlist* nl, cudaStream_t st) {
+  if (nl && nl->ready_ev) GNEP_CUDA(cudaStreamWaitEvent(st, nl->ready_ev, 0));
+  return GNEP_OK;
+}
+
+// check_nlist, then after_build on `st`.
+static int use_nlist(const gnep_model* m, const gnep_nlist* nl, cudaStream_t st) {
+  const int rc = check_nlist(m, nl);
+  return rc ? rc : after_build(nl, st);
+}
+
 int gnep_compute_descriptor_scale(gnep_model* m, const gnep_nlist* nl_, void* stream) {
-  int rc = check_nlist(m, nl_);
+  int rc = use_nlist(m, nl_, (cudaStream_t)stream);
   if (rc) return rc;
   gnep_nlist* nl = const_cast<gnep_nlist*>(nl_);
   cudaStream_t st = (cudaStream_t)stream;
@@ -349,7 +362,14 @@ static int build_angular_tiles(gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
   return GNEP_OK;
 }
 
-static int finish_build(gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
+// The lists, species grouping, angular tiles and workspace of `nl` for the
+// batch already on the device.  The build synchronises with the host once the
+// pair counts are known; with `wait` it also waits for the end of its device
+// work and reports the lists' consistency flag, otherwise it returns after
+// queueing that work (its end is nl->ready_ev, which every consumer of the
+// list waits on, and the flag is reported by the next synchronising build or
+// by gnep_sync_status).
+static int finish_build(gnep_model* m, gnep_nlist* nl, cudaStream_t st, bool wait) {
   int rc;
   ++nl->gen;
   if (nl->n_atoms > 0) {
@@ -366,6 +386,9 @@ static int finish_build(gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
     }
   }
   if ((rc = alloc_workspace(m, nl))) return rc;
+  if (!nl->ready_ev) GNEP_CUDA(cudaEventCreateWithFlags(&nl->ready_ev, cudaEventDisableTiming));
+  GNEP_CUDA(cudaEventRecord(nl->ready_ev, st));
+  if (!wait) return GNEP_OK;
   int herr = 0;
   GNEP_CUDA(cudaMemcpyAsync(&herr, m->err, sizeof(int), cudaMemcpyDeviceToHost, st));
   GNEP_CUDA(cudaStreamSynchronize(st));
@@ -381,6 +404,10 @@ int gnep_nlist_destroy(gnep_nlist* nl) {
   cudaFree(nl->struct_off); cudaFree(nl->type); cudaFree(nl->pos); cudaFree(nl->cell);
   cudaFree(nl->atom_struct); cudaFree(nl->perm);
   cudaFree(nl->atile[0]); cudaFree(nl->atile[1]);
+  if (nl->ready_ev) {
+    cudaEventSynchronize(nl->ready_ev);
+    cudaEventDestroy(nl->ready_ev);
+  }
   if (nl->tile_ev) {
     cudaEventSynchronize(nl->tile_ev);
     cudaEventDestroy(nl->tile_ev);
@@ -425,7 +452,7 @@ int gnep_build_neighbors(gnep_model* m, const gnep_batch* b, gnep_nlist** out, v
     return cuda_error(e, "cudaMalloc batch");
   }
   int rc = load_batch(m, b, nl, st);
-  if (!rc) rc = finish_build(m, nl, st);
+  if (!rc) rc = finish_build(m, nl, st, true);
   if (rc) {
     gnep_nlist_destroy(nl);
     return rc;
@@ -435,13 +462,13 @@ int gnep_build_neighbors(gnep_model* m, const gnep_batch* b, gnep_nlist** out, v
 }
 
 int gnep_rebuild_neighbors(gnep_model* m, const gnep_batch* b, gnep_nlist* nl, void* stream) {
-  int rc = check_nlist(m, nl);
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = use_nlist(m, nl, st);
   if (rc) return rc;
   if (!b || b->n_struct != nl->n_struct || b->n_atoms != nl->n_atoms)
     return set_error(GNEP_ERR_INVALID_ARG, "rebuild needs the same structure and atom counts");
-  cudaStream_t st = (cudaStream_t)stream;
   if ((rc = load_batch(m, b, nl, st))) return rc;
-  return finish_build(m, nl, st);
+  return finish_build(m, nl, st, false);
 }
 
 int gnep_nlist_info(const gnep_nlist* nl, int64_t* nr, int64_t* na) {
@@ -464,7 +491,8 @@ int gnep_nlist_export(const gnep_nlist* nl, int which, int32_t* off, int32_t* j,
   if (!nl || which < 0 || which > 1) return set_error(GNEP_ERR_INVALID_ARG, "bad list");
   cudaStream_t st = (cudaStream_t)stream;
   const PairList& P = nl->L[which];
-  int rc;
+  int rc = after_build(nl, st);
+  if (rc) return rc;
   if ((rc = copy_out(off, P.off, sizeof(int) * ((size_t)nl->n_atoms + 1), st))) return rc;
   if (P.n == 0) return GNEP_OK;
   if ((rc = copy_out(j, P.j, sizeof(int) * (size_t)P.n, st))) return rc;
@@ -482,7 +510,7 @@ int gnep_nlist_export(const gnep_nlist* nl, int which, int32_t* off, int32_t* j,
 // ------------------------------------------------------------ evaluation
 
 int gnep_descriptors(gnep_model* m, const gnep_nlist* nl_, float* G, void* stream) {
-  int rc = check_nlist(m, nl_);
+  int rc = use_nlist(m, nl_, (cudaStream_t)stream);
   if (rc) return rc;
   gnep_nlist* nl = const_cast<gnep_nlist*>(nl_);
   cudaStream_t st = (cudaStream_t)stream;
@@ -492,7 +520,7 @@ int gnep_descriptors(gnep_model* m, const gnep_nlist* nl_, float* G, void* strea
 }
 
 int gnep_descriptors_noalloc(gnep_model* m, const gnep_nlist* nl_, float* G, void* stream) {
-  int rc = check_nlist(m, nl_);
+  int rc = use_nlist(m, nl_, (cudaStream_t)stream);
   if (rc) return rc;
   if (!G || !is_device_ptr(G))
     return set_error(GNEP_ERR_INVALID_ARG, "gnep_descriptors_noalloc writes G in place: G must be device memory");
@@ -502,7 +530,7 @@ int gnep_descriptors_noalloc(gnep_model* m, const gnep_nlist* nl_, float* G, voi
 
 int gnep_forward(gnep_model* m, const gnep_nlist* nl_, float* E_atom, double* E_struct, float* F,
                  double* W_struct, void* stream) {
-  int rc = check_nlist(m, nl_);
+  int rc = use_nlist(m, nl_, (cudaStream_t)stream);
   if (rc) return rc;
   gnep_nlist* nl = const_cast<gnep_nlist*>(nl_);
   cudaStream_t st = (cudaStream_t)stream;
@@ -518,7 +546,7 @@ int gnep_forward(gnep_model* m, const gnep_nlist* nl_, float* E_atom, double* E_
 
 int gnep_md_verlet(gnep_model* m, gnep_nlist* nl, double* pos, double* vel, const double* inv_mass, float* F,
                    double dt, double* E_struct, void* stream) {
-  int rc = check_nlist(m, nl);
+  int rc = use_nlist(m, nl, (cudaStream_t)stream);
   if (rc) return rc;
   if (nl->n_atoms > 0 && (!is_device_ptr(pos) || !is_device_ptr(vel) || !is_device_ptr(inv_mass) || !is_device_ptr(F)))
     return set_error(GNEP_ERR_INVALID_ARG, "md: pos, vel, inv_mass and F must be device arrays");
@@ -527,7 +555,7 @@ int gnep_md_verlet(gnep_model* m, gnep_nlist* nl, double* pos, double* vel, cons
   const size_t N = nl->n_atoms;
   if ((rc = md_kick_drift(nl, pos, vel, inv_mass, F, dt, st))) return rc;
   if (N > 0) GNEP_CUDA(cudaMemcpyAsync(nl->pos, pos, 24 * N, cudaMemcpyDeviceToDevice, st));
-  if ((rc = finish_build(m, nl, st))) return rc;  // lists for the new positions
+  if ((rc = finish_build(m, nl, st, true))) return rc;  // lists for the new positions
   StepArgs A{m, nl, st};
   if ((rc = run_descriptors(A, true))) return rc;
   if ((rc = run_forward(A))) return rc;
@@ -568,7 +596,7 @@ static int loss_grad_core(gnep_model* m, gnep_nlist* nl, const gnep_labels* y, c
 }
 
 int gnep_loss(gnep_model* m, const gnep_nlist* nl_, const gnep_labels* y, double* loss_terms, void* stream) {
-  int rc = check_nlist(m, nl_);
+  int rc = use_nlist(m, nl_, (cudaStream_t)stream);
   if (rc) return rc;
   gnep_nlist* nl = const_cast<gnep_nlist*>(nl_);
   cudaStream_t st = (cudaStream_t)stream;
@@ -590,7 +618,7 @@ int gnep_set_grad(gnep_model* m, const double* src, int64_t n, void* stream) {
 
 int gnep_loss_grad(gnep_model* m, const gnep_nlist* nl_, const gnep_labels* y, double* loss_terms, float* grad,
                    void* stream) {
-  int rc = check_nlist(m, nl_);
+  int rc = use_nlist(m, nl_, (cudaStream_t)stream);
   if (rc) return rc;
   gnep_nlist* nl = const_cast<gnep_nlist*>(nl_);
   cudaStream_t st = (cudaStream_t)stream;
@@ -656,6 +684,7 @@ int gnep_graph_create(gnep_model* m, const gnep_nlist* nl_, const gnep_labels* y
     return set_error(GNEP_ERR_INVALID_ARG, "graph capture needs device labels and a device loss buffer");
   gnep_nlist* nl = const_cast<gnep_nlist*>(nl_);
   cudaStream_t st = (cudaStream_t)stream;
+  if (nl->ready_ev) GNEP_CUDA(cudaEventSynchronize(nl->ready_ev));  // a capture cannot wait on it
   GNEP_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
   rc = loss_grad_core(m, nl, y, st);
   if (!rc && loss_out) {
@@ -688,6 +717,7 @@ int gnep_graph_launch(gnep_graph* g, void* stream) {
   if (!g) return set_error(GNEP_ERR_INVALID_ARG, "NULL graph");
   if (g->nl && g->nl->gen != g->gen)
     return set_error(GNEP_ERR_INVALID_ARG, "the neighbour list was rebuilt or retuned after this graph was captured");
+  if (int rc = after_build(g->nl, (cudaStream_t)stream)) return rc;
   GNEP_CUDA(cudaGraphLaunch(g->ge, (cudaStream_t)stream));
   return GNEP_OK;
 }
@@ -754,7 +784,7 @@ int gnep_tuning_get(const gnep_model* m, const gnep_nlist* nl, int32_t* values) 
 }
 
 int gnep_tuning_set(gnep_model* m, gnep_nlist* nl, const int32_t* values, void* stream) {
-  int rc = check_nlist(m, nl);
+  int rc = use_nlist(m, nl, (cudaStream_t)stream);
   if (rc) return rc;
   if (!values) return set_error(GNEP_ERR_INVALID_ARG, "NULL values");
   for (int k = 0; k < kTuneKnobs; ++k)
@@ -767,7 +797,7 @@ int gnep_tuning_set(gnep_model* m, gnep_nlist* nl, const int32_t* values, void* 
 }
 
 int gnep_autotune(gnep_model* m, gnep_nlist* nl, const gnep_labels* y, int reps, void* stream) {
-  int rc = check_nlist(m, nl);
+  int rc = use_nlist(m, nl, (cudaStream_t)stream);
   if (rc) return rc;
   if (!y) return set_error(GNEP_ERR_INVALID_ARG, "NULL labels");
   if (nl->n_atoms == 0) return GNEP_OK;
@@ -926,7 +956,7 @@ static int g_stage_count = 0;
 
 int gnep_profile_step(gnep_model* m, const gnep_nlist* nl_, const gnep_labels* y, float* stage_ms,
                       int32_t cap, int32_t* n_stages, void* stream) {
-  int rc = check_nlist(m, nl_);
+  int rc = use_nlist(m, nl_, (cudaStream_t)stream);
   if (rc) return rc;
   if (!stage_ms || !n_stages || cap < 1) return set_error(GNEP_ERR_INVALID_ARG, "bad output arrays");
   gnep_nlist* nl = const_cast<gnep_nlist*>(nl_);
@@ -972,6 +1002,7 @@ int gnep_sync_status(gnep_model* m, void* stream) {
   if (flag) GNEP_CUDA(cudaMemset(m->err, 0, sizeof(int)));
   if (flag & kErrNonFinite) return set_error(GNEP_ERR_NONFINITE, "loss was not finite; the update was skipped");
   if (flag & kErrTimeout) return set_error(GNEP_ERR_TIMEOUT, "a device-side wait gave up");
+  if (flag & kErrRevMissing) return set_error(GNEP_ERR_INVALID_ARG, "neighbour lists are not symmetric (internal error)");
   if (flag) return set_error(GNEP_ERR_INVALID_ARG, "device reported an invalid input");
   return GNEP_OK;
 }

@@ -105,6 +105,7 @@ struct gnep_nlist {
   int* tile_host = nullptr;          // pinned staging of the tile bounds (both tile sets)
   int64_t tile_host_cap = 0;
   cudaEvent_t tile_ev = nullptr;     // the last upload from tile_host
+  cudaEvent_t ready_ev = nullptr;    // the end of the last build's device work (consumers wait on it)
   cudaStream_t side = nullptr;
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   gnep::Workspace ws;

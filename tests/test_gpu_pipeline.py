@@ -60,3 +60,34 @@ def test_rebuild_beside_training_step(precision):
     for w in (0, 1):
         for x, y in zip(nl_b.export(w), nl_a.export(w)):
             np.testing.assert_array_equal(x, y)
+
+
+def test_calls_on_other_streams_wait_for_a_rebuild():
+    """A rebuild returns with its compaction, reverse entries and tile upload
+    still queued on its stream; calls that read the list on other streams (a
+    loss + gradient, a list export on the default stream) must see the new
+    lists without any wait by the caller."""
+    a = synth.make_config(2, n_struct=24)
+    bb = _moved(a, 6)
+    m = gnep.GNEP(**SHAPE, seed=12, precision="fp32")
+    nl = m.neighbors(gnep.DeviceBatch.from_host(a))
+    m.compute_scale(nl)
+    ref = m.neighbors(gnep.DeviceBatch.from_host(bb))
+    y = m.teacher_labels(ref, bb.sizes())
+    t_ref, g_ref = m.loss_grad(ref, y)
+    torch.cuda.synchronize()
+    t_ref, g_ref = t_ref.cpu().clone(), g_ref.cpu().clone()
+    lists_ref = [ref.export(w) for w in (0, 1)]
+    s_load, s_use = torch.cuda.Stream(), torch.cuda.Stream()
+    torch.cuda.synchronize()
+    for _ in range(3):
+        nl.rebuild(bb, stream=s_load)
+        t, g = m.loss_grad(nl, y, stream=s_use)
+        for w in (0, 1):
+            for x, z in zip(nl.export(w), lists_ref[w]):
+                np.testing.assert_array_equal(x, z)
+        s_use.synchronize()
+        assert torch.equal(t.cpu(), t_ref) and torch.equal(g.cpu(), g_ref)
+        nl.rebuild(a, stream=s_load)  # and back, for the next round
+        s_load.synchronize()
+    m.sync_status()
