@@ -122,6 +122,41 @@ def test_blm_printed_forms(oracle):
     assert B[23] == pytest.approx(4 * x ** 3 * y - 4 * x * y ** 3)
 
 
+def _printed_blm():
+    """The 24 printed forms of the fixture as (index, equation, function of x, y, z, r)."""
+    import ast
+    import pathlib
+    out = []
+    for line in (pathlib.Path(__file__).parent / "golden" / "blm_cartesian_l1_4.txt").read_text().splitlines():
+        if not line.strip() or line.startswith("#"):
+            continue
+        l, m, eq, expr = line.split(maxsplit=3)
+        tree = ast.parse(expr, mode="eval")
+        names = {n.id for n in ast.walk(tree) if isinstance(n, ast.Name)}
+        assert names <= {"x", "y", "z", "r"}, (eq, names)
+        code = compile(tree, eq, "eval")
+        out.append(((int(l) ** 2 - 1) + int(m), eq, lambda x, y, z, r, c=code: eval(c, {"__builtins__": {}},
+                                                                                    dict(x=x, y=y, z=z, r=r))))
+    return out
+
+
+def test_blm_all_printed_forms_of_appendix_b(oracle):
+    """All 24 printed b_lm of App. B (B1.1-B4.9, fixture tests/golden/blm_cartesian_l1_4.txt):
+    the oracle's components, in its (l, m) order, equal the printed forms at unit
+    vectors, and, by homogeneity of degree l, |d|^l times them at any vector d."""
+    forms = _printed_blm()
+    assert sorted(q for q, _, _ in forms) == list(range(24))
+    rng = np.random.default_rng(8)
+    for d in rng.standard_normal((12, 3)) * rng.uniform(0.5, 3.0, (12, 1)):
+        B, _ = oracle.blm(d)
+        r = float(np.linalg.norm(d))
+        u = d / r
+        for q, eq, f in forms:
+            l = int(np.floor(np.sqrt(q + 1)))
+            assert B[q] == pytest.approx(f(*u, 1.0), rel=1e-12, abs=1e-12), eq
+            assert r ** l * B[q] == pytest.approx(f(*d, r), rel=1e-11, abs=1e-11), eq
+
+
 # ---------------------------------------------------------------- Eq. 2
 
 def _numpy_neighbors(batch, rc, extra=1):
