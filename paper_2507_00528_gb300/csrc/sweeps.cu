@@ -882,30 +882,28 @@ struct AngSmem {
 // l, completed over the four lanes of the row.  With l = 1 for q < 3, 2 for
 // q < 8, 3 for q < 15 and 4 above, a lane's positions fall as: nq = 0 into
 // l = 1 or 2 (by t), nq = 1 into l = 3 (q = 15 into l = 4), nq = 2 into l = 4.
-// cq[nq][e] = C_q of the lane's positions.
+// cq[nq][e] = C_q of the lane's positions.  The four sums are completed by
+// halving exchanges (lane distance 2, then 1: each lane sends the half of its
+// partial sums that it does not keep), so that lane t ends with the sum of
+// degree l = t + 1 of each row half: out[h].
 __device__ __forceinline__ void lsum_rows(const float (&x)[3][4], const float (&y)[3][4], const float (&cq)[3][2],
-                                          int t, float (&out)[2][4]) {
+                                          int t, float (&out)[2]) {
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
-    float v[3][2];
+    float v[3][2], p[4];
 #pragma unroll
     for (int nq = 0; nq < 3; ++nq)
 #pragma unroll
       for (int e = 0; e < 2; ++e) v[nq][e] = cq[nq][e] * x[nq][2 * h + e] * y[nq][2 * h + e];
-    out[h][0] = t == 0 ? v[0][0] + v[0][1] : (t == 1 ? v[0][0] : 0.f);
-    out[h][1] = t == 1 ? v[0][1] : (t >= 2 ? v[0][0] + v[0][1] : 0.f);
-    out[h][2] = v[1][0] + (t == 3 ? 0.f : v[1][1]);
-    out[h][3] = (t == 3 ? v[1][1] : 0.f) + v[2][0] + v[2][1];
-#pragma unroll
-    for (int l = 0; l < 4; ++l) {
-      out[h][l] += __shfl_xor_sync(0xffffffffu, out[h][l], 1);
-      out[h][l] += __shfl_xor_sync(0xffffffffu, out[h][l], 2);
-    }
+    p[0] = t == 0 ? v[0][0] + v[0][1] : (t == 1 ? v[0][0] : 0.f);
+    p[1] = t == 1 ? v[0][1] : (t >= 2 ? v[0][0] + v[0][1] : 0.f);
+    p[2] = v[1][0] + (t == 3 ? 0.f : v[1][1]);
+    p[3] = (t == 3 ? v[1][1] : 0.f) + v[2][0] + v[2][1];
+    const bool hi = t & 2, odd = t & 1;
+    const float k0 = (hi ? p[2] : p[0]) + __shfl_xor_sync(0xffffffffu, hi ? p[0] : p[2], 2);
+    const float k1 = (hi ? p[3] : p[1]) + __shfl_xor_sync(0xffffffffu, hi ? p[1] : p[3], 2);
+    out[h] = (odd ? k1 : k0) + __shfl_xor_sync(0xffffffffu, odd ? k0 : k1, 1);
   }
-}
-
-__device__ __forceinline__ float pick4(const float (&v)[4], int t) {
-  return t == 0 ? v[0] : t == 1 ? v[1] : t == 2 ? v[2] : v[3];
 }
 
 // The five l = 2 moments (q = 3..7) of row half h, gathered from the lanes t = 1..3 of the row.
@@ -1106,11 +1104,11 @@ __global__ void __launch_bounds__(32 * kAngWarps, (TAN || SPLIT) ? 2 : 3)
         if (!last) continue;  // completed in a later chunk
         float* gi = Gout + (size_t)i * C::NDES;
         if (!TAN) {
-          float ql[2][4];
+          float ql[2];
           lsum_rows(acc, acc, cq, t, ql);  // q_nl = sum_m C_lm S_nlm^2 (Eq. 7)
 #pragma unroll
           for (int h = 0; h < 2; ++h)
-            if (g + 8 * h < NQA) gi[C::vang(g + 8 * h, t + 1)] = pick4(ql[h], t);
+            if (g + 8 * h < NQA) gi[C::vang(g + 8 * h, t + 1)] = ql[h];
           if (C::FB) {  // q4 of row g + 8h on lane t = h: one evaluation per lane for both halves
             float s2[2][5];
             gather_l2(acc, 0, lane, s2[0]);
@@ -1123,11 +1121,11 @@ __global__ void __launch_bounds__(32 * kAngWarps, (TAN || SPLIT) ? 2 : 3)
             if (t < 2 && n < NQA) gi[C::v4b(n)] = q4;
           }
         } else {
-          float ql[2][4];
+          float ql[2];
           lsum_rows(sv, acc, cq, t, ql);  // qdot_nl = 2 sum_m C_lm S_nlm Sdot_nlm
 #pragma unroll
           for (int h = 0; h < 2; ++h)
-            if (g + 8 * h < NQA) gi[C::vang(g + 8 * h, t + 1)] = 2.f * pick4(ql[h], t);
+            if (g + 8 * h < NQA) gi[C::vang(g + 8 * h, t + 1)] = 2.f * ql[h];
           if (C::FB) {  // qdot4 of row g + 8h on lane t = h: one evaluation per lane for both halves
             float s2[2][5], d2[2][5];
 #pragma unroll
