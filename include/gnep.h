@@ -306,7 +306,10 @@ const char *gnep_profile_stage_name(int32_t i);
 int gnep_save(gnep_model *m, const char *path);
 int gnep_load(gnep_model *m, const char *path);
 
-/* Synchronise `stream`, read and clear the model's device error flag. */
+/* Synchronise `stream`, read and clear the model's device error flag:
+ * NONFINITE (a loss was not finite; that Adam update was skipped), TIMEOUT (a
+ * device-side wait gave up), INVALID_ARG (a rebuild's lists failed their
+ * consistency check, or another input check on the device failed). */
 int gnep_sync_status(gnep_model *m, void *stream);
 const char *gnep_last_error(void);
 int gnep_abi_version(void);
