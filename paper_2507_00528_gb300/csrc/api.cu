@@ -414,9 +414,6 @@ int gnep_nlist_destroy(gnep_nlist* nl) {
   }
   if (nl->tile_host) cudaFreeHost(nl->tile_host);
   if (nl->host_aoff) cudaFreeHost(nl->host_aoff);
-  if (nl->side) cudaStreamDestroy(nl->side);
-  if (nl->fork_ev) cudaEventDestroy(nl->fork_ev);
-  if (nl->join_ev) cudaEventDestroy(nl->join_ev);
   for (int L = 0; L < 2; ++L) {
     PairList& P = nl->L[L];
     cudaFree(P.off); cudaFree(P.j); cudaFree(P.owner); cudaFree(P.rev); cudaFree(P.rij); cudaFree(P.shift);

@@ -96,8 +96,6 @@ struct gnep_nlist {
     int na[2] = {0, 0}, ch[2] = {0, 0}, cg_blocks = 0;
   } tune;
   uint64_t gen = 0;  // bumped whenever lists or tiles change (captured graphs check it)
-  // Second stream for sweeps that can run beside the caller's stream (the
-  // radial and angular sweeps of one phase), with its fork / join events.
   std::vector<int> host_types;  // species of the last build (host copy)
   bool types_changed = true;
   long long* host_aoff = nullptr;    // pinned: angular list offsets of the last build (for the tiles)
@@ -106,8 +104,6 @@ struct gnep_nlist {
   int64_t tile_host_cap = 0;
   cudaEvent_t tile_ev = nullptr;     // the last upload from tile_host
   cudaEvent_t ready_ev = nullptr;    // the end of the last build's device work (consumers wait on it)
-  cudaStream_t side = nullptr;
-  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   gnep::Workspace ws;
   void* ws_mem = nullptr;      // one allocation carved into the workspace
   int64_t ws_pairs[2] = {-1, -1};  // pair counts the workspace was sized for
