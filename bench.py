@@ -4,15 +4,17 @@
 One step = the whole hot path over one batch: descriptors, network, energies,
 forces, virials, loss, the exact gradient w.r.t. every parameter, and an Adam
 update with the Eq. 17 learning rate, captured once as a CUDA graph and
-replayed.  By default the network contractions run in BF16 on the tensor
-cores (FP32 accumulation; the sweeps are FP32); the same step in the plain
-FP32 form is timed alongside and reported as "fp32_form", with the force
-difference between the two forms.  The workload is 256 synthetic Sb/Te structures of 32-400 atoms
-(perturbed rocksalt, liquid-like and strained cells in equal thirds),
-n_max 8/8, basis 12/12, l_max 4 with the 4-body term, 50 hidden neurons,
-labels from a random teacher model of the same shape.
+replayed.  The headline runs the FP32 form (FP32 network; the sweep
+contractions as split-TF32 tensor-core products with FP32-level error, held
+to the FP32 tolerances against the FP64 oracle); the BF16 and TF32 network
+modes are timed beside it with their force difference from it.  The workload
+is 256 synthetic Sb/Te structures of 32-400 atoms (perturbed rocksalt,
+liquid-like and strained cells in equal thirds), n_max 8/8, basis 12/12,
+l_max 4 with the 4-body term, 50 hidden neurons, labels from a random teacher
+model of the same shape.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gnep|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--repeats R]
+                    [--impl gnep|reference] [--precision fp32|tf32|bf16]
 
 Prints one JSON line (rank 0).  The neighbour build is done once before the
 timed region (structures are fixed during training) and is reported apart.
@@ -49,30 +51,37 @@ L2_BYTES = 129 * 1024 * 1024
 
 # ----------------------------------------------------------------- FLOP model
 
-def algo_flops(nqr=9, kr=13, nqa=9, ka=13, ns=2, H=50, fb=True, N=1, PR=1, PA=1):
-    """Algorithmic FP32 FLOPs per launch of each kernel (FMA = 2, add/mul = 1,
-    sqrt / reciprocal / sincos / tanh = 1).  Counts what the formulation needs
-    once per unit (pair or atom), not what an implementation repeats."""
+def survey_flops(nqr=9, kr=13, nqa=9, ka=13, ns=2, H=50, fb=True, N=1, PR=1, PA=1, L=24):
+    """Algorithmic FP32 FLOPs per launch of each kernel, on the fixed work
+    model of the method (FMA = 2 FLOP), counted per unit as the formulation
+    needs it, whatever the kernels do:
+      sweep 1 (descriptors)  radial pair 15 + 4K + 2 N_q^R K;
+                             angular pair 15 + 4K + 2 N_q^A K + 50 + 2 N_q^A L;
+                             atom 2 N_q^A L (q_nl) + 60 N_q^A (4-body)
+      sweep 2 (forces)       radial pair 4K + 2 N_q^R K + 20;
+                             angular pair 4 N_q^A K + 150 + 8 N_q^A L
+      sweep 3 (tangent)      radial pair as sweep 2;
+                             angular pair 4 N_q^A K + 270 + 4 N_q^A L; atom 2 N_q^A L
+      sweep 4 (c-gradient)   radial pair 8K + 4 N_q^R K;
+                             angular pair 8K + 120 + 6 N_q^A L + 6 N_q^A K
+      network                atom 4 N_des H (forward), 8 N_des H (backward)
+    with K the basis functions, N_q the channels and L = 24 (l, m) components.
+    Each sweep's radial part is charged to the kernel that does it (the radial
+    force is fused into the force gather, the radial c-gradient works on
+    per-atom basis sums but is charged per pair here)."""
     D = nqr + 4 * nqa + (nqa if fb else 0)
-    geo = 10                        # |r|^2, sqrt, 1/r, unit vector
-    basis_f = 5 * ka + 8            # xi, cut-off, Chebyshev recursion, f_k
-    basis_fd = 12 * ka + 15         # ... and df_k/dr
-    harm = 40                       # 24 B_lm from the unit vector
-    harm_g = 384                    # B_lm and projected gradients
-    u = 18                          # u_ij = (a_j - a_i) + B_s r_ij
-    dirder = 144 + ka               # D_lm = grad B_lm . u and fu_k
-    q4 = 60 if fb else 0
+    q4 = 60 * nqa if fb else 0
     f = {}
-    f["desc_radial"] = PR * (6 * kr + 8) + N * 2 * ns * kr * nqr
-    f["desc_angular"] = PA * (geo + basis_f + harm + nqa * (2 * ka + 48)) + N * nqa * (48 + q4)
-    f["mlp_fwd"] = N * (4 * D * H + 6 * H + 2 * D + 2 * ns * kr * nqr)
-    f["force_angular"] = PA * (geo + basis_fd + harm_g + nqa * (4 * ka + 96) + 200) + N * nqa * (72 + q4)
-    f["force_atoms"] = PR * (16 * kr + 40) + PA * 21
-    f["tangent_radial"] = PR * (14 * kr + 39) + N * 2 * ns * kr * nqr
-    f["tangent_angular"] = PA * (u + geo + basis_fd + harm_g + dirder + nqa * (4 * ka + 96)) + N * nqa * (48 + q4)
-    f["mlp_bwd"] = N * (8 * D * H + 12 * H + D)
-    f["cgrad"] = PA * (u + geo + basis_fd + harm_g + dirder + nqa * (144 + 4 * ka)) + \
-        N * (nqa * (144 + 2 * q4) + 4 * nqr * ns * kr)
+    f["desc_radial"] = PR * (15 + 4 * kr + 2 * nqr * kr)
+    f["desc_angular"] = PA * (15 + 4 * ka + 2 * nqa * ka + 50 + 2 * nqa * L) + N * (2 * nqa * L + q4)
+    f["mlp_fwd"] = N * 4 * D * H
+    f["force_angular"] = PA * (4 * nqa * ka + 150 + 8 * nqa * L)
+    f["force_atoms"] = PR * (4 * kr + 2 * nqr * kr + 20)
+    f["tangent_radial"] = PR * (4 * kr + 2 * nqr * kr + 20)
+    f["tangent_angular"] = PA * (4 * nqa * ka + 270 + 4 * nqa * L) + N * 2 * nqa * L
+    f["mlp_bwd"] = N * 8 * D * H
+    f["cgrad_radial"] = PR * (8 * kr + 4 * nqr * kr)
+    f["cgrad"] = PA * (8 * ka + 120 + 6 * nqa * L + 6 * nqa * ka)
     return f
 
 
@@ -323,14 +332,13 @@ def run_gnep(args):
     student = gnep.GNEP(**MODEL_KW, seed=11, precision=args.precision)
     student.set_scale(scale)
 
-    n_total = args.warmup + args.steps + 10
+    n_total = args.warmup + args.steps * args.repeats + 10
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
     if world == 1:
         # one captured graph per step: loss + gradient + scheduled Adam
         graph = gnep.TrainGraph(student, nl, y, 1e-3, 1e-5, 2, n_total)
         stream = graph.stream
         run_step = lambda: graph.launch(stream)
-        loss_buf = graph.loss
     else:
         # data-parallel step: each rank its own 256 structures, the FP64 gradient
         # summed over ranks (NCCL all-reduce) before the identical Adam update
@@ -341,43 +349,48 @@ def run_gnep(args):
                                     dp.Counts(int(cnt[0].item()), int(cnt[1].item())))
         stream = torch.cuda.current_stream()
         run_step = lambda: dstep.step(1e-3, 1e-5, 2, n_total, want_loss=False)
-        loss_buf = None
     for _ in range(args.warmup):
         with torch.cuda.stream(stream):
             run_step()
     torch.cuda.synchronize()
     loss0 = student.loss(nl, y).cpu().numpy().copy()
 
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
+    # The K timed steps are run `repeats` times, each repeat bracketed by a
+    # barrier and a synchronisation, so that the clock sampler sees the load
+    # for a few seconds; the line reports the median repeat.
     props = torch.cuda.get_device_properties(local)
-    uuid = str(getattr(props, "uuid", "") or "")
-    ident = ("GPU-" + uuid) if uuid and not uuid.startswith("GPU-") else (uuid or str(local))
-    with ClockSampler(ident) as clk:
-        for k in range(args.steps):
-            with torch.cuda.stream(stream):
-                flush.zero_()  # evict L2 between steps (outside the timed events)
-                ev[k][0].record(stream)
-                run_step()
-                ev[k][1].record(stream)
-        torch.cuda.synchronize()
+    reps_ms = []
+    with ClockSampler(_gpu_ident(torch, local)) as clk:
+        for _ in range(args.repeats):
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+            if world > 1:
+                dist.barrier()
+            torch.cuda.synchronize()
+            for k in range(args.steps):
+                with torch.cuda.stream(stream):
+                    flush.zero_()  # evict L2 between steps (outside the timed events)
+                    ev[k][0].record(stream)
+                    run_step()
+                    ev[k][1].record(stream)
+            torch.cuda.synchronize()
+            if world > 1:
+                dist.barrier()
+            reps_ms.append(sum(a.elapsed_time(b) for a, b in ev))
     if world > 1:
-        dist.barrier()
-    total_ms = sum(a.elapsed_time(b) for a, b in ev)
-    loss_end = student.loss(nl, y).cpu().numpy().copy()
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        t = torch.tensor(reps_ms, dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = t.item()
+        reps_ms = t.cpu().tolist()
         a = torch.tensor([n_atoms], dtype=torch.float64, device="cuda")
         dist.all_reduce(a)
         atoms_all = a.item()
     else:
         atoms_all = n_atoms
+    total_ms = statistics.median(reps_ms)
     value = atoms_all * args.steps / (total_ms / 1e3)
+    loss_end = student.loss(nl, y).cpu().numpy().copy()
     student.sync_status()
+    clocks = clk.summary()
 
     # per-kernel durations (CUDA events between launches, eager step)
     stage_ms = {}
@@ -385,61 +398,19 @@ def run_gnep(args):
     for _ in range(reps):
         for name, ms in student_profile(student, nl, y, gnep):
             stage_ms[name] = stage_ms.get(name, 0.0) + ms / reps
-    fl = algo_flops(N=n_atoms, PR=PR, PA=PA)
-    by = algo_bytes(N=n_atoms, PR=PR, PA=PA)
-    kernels = {k: v for k, v in stage_ms.items() if k in fl}
-    dom = max(kernels, key=kernels.get)
-    peaks = measured_peaks()
-    sm_max = peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
-    hbm_peak = peaks.get("hbm_gbs", 6800.0)  # GB/s, measured copy (else the fallback figure)
-    # the bound is the resource that limits at speed of light: compulsory bytes
-    # at the measured copy bandwidth, or the formulation's FP32 work at the ALU peak
-    t_hbm = by[dom] / (hbm_peak * 1e9)
-    # the network kernels of the tensor-core modes run their FLOPs on the tensor
-    # pipe (TF32 at half the measured BF16 rate, the nominal ratio)
-    on_tensor = dom in ("mlp_fwd", "mlp_bwd") and args.precision != "fp32"
-    flop_peak = (peaks.get("bf16_tflops", 1900.0) * (0.5 if args.precision == "tf32" else 1.0)) if on_tensor \
-        else fp32_peak
-    t_alu = fl[dom] / (flop_peak * 1e12)
-    achieved_gbs = by[dom] / (stage_ms[dom] / 1e3) / 1e9
-    achieved = fl[dom] / (stage_ms[dom] / 1e3) / 1e12
-    step_flops = sum(fl.values())
-    clocks = clk.summary()
+    roofline = roofline_line(stage_ms, n_atoms, PR, PA, props, clocks, total_ms / args.steps)
 
     # end to end through the C ABI with host buffers: H2D of the structures and
     # labels from pinned memory, neighbour rebuild, loss + gradient, Adam, D2H loss
     e2e = run_e2e(student, nl, batch, y, args, gnep, torch)
 
-    # the plain FP32 form of the same step, and the force difference of this
-    # mode from it at identical parameters (the FP32 form matches the FP64
-    # oracle to 1e-5 in the parity tests)
-    fp32_form = None
-    if world == 1 and args.precision != "fp32":
-        ref = gnep.GNEP(**MODEL_KW, seed=11, precision="fp32")
-        ref.set_scale(scale)
-        gr32 = gnep.TrainGraph(ref, nl, y, 1e-3, 1e-5, 2, 10 ** 6)
-        k32 = min(args.steps, 100)
-        for _ in range(args.warmup):
-            gr32.launch(gr32.stream)
-        ev32 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k32)]
-        torch.cuda.synchronize()
-        for k in range(k32):
-            with torch.cuda.stream(gr32.stream):
-                flush.zero_()
-                ev32[k][0].record(gr32.stream)
-                gr32.launch(gr32.stream)
-                ev32[k][1].record(gr32.stream)
-        torch.cuda.synchronize()
-        ms32 = sum(a.elapsed_time(b) for a, b in ev32) / k32
-        probe = gnep.GNEP(**MODEL_KW, seed=11, precision=args.precision)
-        probe.set_scale(scale)
-        F_mode = probe.forward(nl)[2].double().cpu().numpy()
-        probe.set_precision("fp32")
-        F_ref = probe.forward(nl)[2].double().cpu().numpy()
-        fp32_form = {"value": n_atoms / (ms32 / 1e3), "unit": UNIT, "ms_per_step": ms32, "steps": k32,
-                     "speedup_of_this_mode": ms32 / (total_ms / args.steps),
-                     "force_rel_rms_vs_fp32_form": float(np.linalg.norm(F_mode - F_ref) / np.linalg.norm(F_ref))}
+    # the narrower network modes beside the headline: their step time and the
+    # force difference from the FP32 form at identical parameters
+    other_modes = {}
+    if world == 1:
+        for mode in [m for m in ("bf16", "tf32") if m != args.precision]:
+            other_modes[mode] = time_mode(mode, nl, y, scale, args, flush, torch, gnep, total_ms / args.steps,
+                                          args.precision)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -455,40 +426,20 @@ def run_gnep(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp32": "f32 (sweep contractions as split-TF32 tensor-core products, FP32-accurate)",
-                  "tf32": "tf32 network / split-TF32 sweep contractions / f32 geometry",
-                  "bf16": "bf16 network / tf32 sweep contractions / f32 geometry"}[args.precision],
+        "dtype": DTYPES[args.precision],
         "data": "synthetic",
         "config": dict(WORKLOAD, atoms_per_step_per_gpu=n_atoms, radial_pairs=PR, angular_pairs=PA,
                        graph=world == 1, precision=args.precision, l2="flushed between steps (256 MB write)",
                        parallelism=f"dp{world}" + (" (FP64 gradient all-reduce per step)" if world > 1 else ""),
                        neighbor_build_ms=round(nbuild_ms, 3)),
-        "roofline": ({"bound": "hbm", "kernel": dom, "achieved": achieved_gbs, "peak": hbm_peak,
-                      "unit": "GB/s", "frac": achieved_gbs / hbm_peak,
-                      "traffic": committed_traffic(dom),
-                      "peak_source": ("MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks
-                                      else "fallback 6.8 TB/s (of fallback)"),
-                      "kernel_ms": stage_ms[dom], "kernel_algo_bytes": by[dom],
-                      "kernel_algo_flops": fl[dom], "alu_frac": achieved / fp32_peak,
-                      "sol_us": {"hbm": t_hbm * 1e6, "fp32_alu": t_alu * 1e6},
-                      "step_algo_gflop": step_flops / 1e9,
-                      "step_achieved_tflops": step_flops / (total_ms / args.steps / 1e3) / 1e12}
-                     if t_hbm >= t_alu else
-                     {"bound": "tensor" if on_tensor else "alu", "kernel": dom, "achieved": achieved,
-                      "peak": flop_peak, "unit": "TFLOP/s", "frac": achieved / flop_peak,
-                      "traffic": committed_traffic(dom),
-                      "peak_source": ("MEASURED_PEAKS.json bf16_tflops (of measured)" if on_tensor else
-                                      f"FP32 {props.multi_processor_count} SMs x 128 lanes x 2 x {sm_max:.0f} MHz"),
-                      "kernel_ms": stage_ms[dom], "kernel_algo_bytes": by[dom],
-                      "kernel_algo_flops": fl[dom], "hbm_frac": achieved_gbs / hbm_peak,
-                      "sol_us": {"hbm": t_hbm * 1e6, ("tensor" if on_tensor else "fp32_alu"): t_alu * 1e6},
-                      "step_algo_gflop": step_flops / 1e9,
-                      "step_achieved_tflops": step_flops / (total_ms / args.steps / 1e3) / 1e12}),
+        "repeats": {"count": args.repeats, "ms_per_step": [round(r / args.steps, 5) for r in reps_ms],
+                    "reported": "median repeat"},
+        "roofline": roofline,
         "kernel_ms": {k: round(v, 5) for k, v in stage_ms.items()},
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "fp32_form": fp32_form,
-        "gpu_launches": args.steps * len(stage_ms) - args.steps * sum(1 for k in stage_ms if k.startswith("memset")),
+        "other_modes": other_modes,
+        "gpu_launches": args.steps * sum(1 for k in stage_ms if not k.startswith("memset")),
         "clocks": clocks,
         "loss": {"after_warmup": loss0.tolist(), "end": loss_end.tolist()},
         "source_sha": csrc_sha(),
@@ -496,6 +447,88 @@ def run_gnep(args):
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+DTYPES = {
+    "fp32": "f32 (FP32 geometry and network; descriptor, force, tangent and c-gradient contractions as "
+            "split-TF32 tensor-core products with FP32-level error; FP64 cross-atom sums)",
+    "tf32": "tf32 network (tcgen05, FP32 accumulation); otherwise as the f32 form",
+    "bf16": "bf16 network (tcgen05, FP32 accumulation); otherwise as the f32 form",
+}
+
+
+def roofline_line(stage_ms, n_atoms, PR, PA, props, clocks, step_ms):
+    """Roofline of the dominant kernel (the longest launch) on the FP32-ALU
+    bound: the work model's FLOPs per launch over the launch's measured time,
+    against the FP32 peak SMs x 128 lanes x 2 FLOP x clock (no FP32 figure is
+    measured), at the maximum clock and at the median clock of the run.  The
+    kernel's compulsory bytes against the measured copy bandwidth, and the
+    whole step's FLOPs and compulsory bytes per atom, stand beside it."""
+    fl = survey_flops(N=n_atoms, PR=PR, PA=PA)
+    by = algo_bytes(N=n_atoms, PR=PR, PA=PA)
+    kernels = {k: v for k, v in stage_ms.items() if k in fl}
+    dom = max(kernels, key=kernels.get)
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    sm_run = clocks.get("sm_mhz") or sm_max
+    fp32 = lambda mhz: props.multi_processor_count * 128 * 2 * mhz * 1e6 / 1e12  # TFLOP/s
+    hbm = peaks.get("hbm_gbs")
+    hbm_src = "MEASURED_PEAKS.json hbm_gbs (of measured)" if hbm else "fallback 6.8 TB/s (of fallback)"
+    hbm = float(hbm or 6800.0)
+    sec = stage_ms[dom] / 1e3
+    achieved = fl[dom] / sec / 1e12
+    step_flops = sum(fl.values())
+    step_bytes = sum(by.values())
+    return {
+        "bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32(sm_max), "unit": "TFLOP/s",
+        "frac": achieved / fp32(sm_max), "traffic": committed_traffic(dom),
+        "peak_source": (f"FP32 peak derived as {props.multi_processor_count} SMs x 128 lanes x 2 FLOP x "
+                        f"{sm_max:.0f} MHz (maximum SM clock); no FP32 figure is measured"),
+        "peak_at_run_clock": {"sm_mhz": sm_run, "peak": fp32(sm_run), "frac": achieved / fp32(sm_run)},
+        "kernel_ms": stage_ms[dom], "kernel_algo_flops": fl[dom],
+        "hbm": {"kernel_compulsory_bytes": by[dom], "achieved_gbs": by[dom] / sec / 1e9, "peak_gbs": hbm,
+                "frac": by[dom] / sec / 1e9 / hbm, "peak_source": hbm_src},
+        "step": {"algo_gflop": step_flops / 1e9, "achieved_tflops": step_flops / (step_ms / 1e3) / 1e12,
+                 "frac": step_flops / (step_ms / 1e3) / 1e12 / fp32(sm_max),
+                 "compulsory_bytes_per_atom": step_bytes / n_atoms,
+                 "compulsory_bytes_per_atom_over_2kb": step_bytes / n_atoms / 2048.0},
+        "per_kernel": {k: {"ms": round(stage_ms[k], 5), "tflops": round(fl[k] / (stage_ms[k] / 1e3) / 1e12, 3),
+                           "frac": round(fl[k] / (stage_ms[k] / 1e3) / 1e12 / fp32(sm_max), 4)}
+                       for k in kernels},
+    }
+
+
+def time_mode(mode, nl, y, scale, args, flush, torch, gnep, head_ms, head_mode):
+    """Step time of another network mode (graph replays, L2 flushed between
+    steps) and its forces' relative RMS difference from the headline form's."""
+    m = gnep.GNEP(**MODEL_KW, seed=11, precision=mode)
+    m.set_scale(scale)
+    gr = gnep.TrainGraph(m, nl, y, 1e-3, 1e-5, 2, 10 ** 6)
+    k = min(args.steps, 100)
+    for _ in range(args.warmup):
+        gr.launch(gr.stream)
+    reps = []
+    for _ in range(3):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        torch.cuda.synchronize()
+        for q in range(k):
+            with torch.cuda.stream(gr.stream):
+                flush.zero_()
+                ev[q][0].record(gr.stream)
+                gr.launch(gr.stream)
+                ev[q][1].record(gr.stream)
+        torch.cuda.synchronize()
+        reps.append(sum(a.elapsed_time(b) for a, b in ev) / k)
+    ms = statistics.median(reps)
+    probe = gnep.GNEP(**MODEL_KW, seed=11, precision=mode)
+    probe.set_scale(scale)
+    F_mode = probe.forward(nl)[2].double().cpu().numpy()
+    probe.set_precision(head_mode)
+    F_ref = probe.forward(nl)[2].double().cpu().numpy()
+    m.sync_status()
+    return {"value": nl.n_atoms / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": k, "repeats": 3,
+            "speedup_over_headline": head_ms / ms, "dtype": DTYPES[mode],
+            f"force_rel_rms_vs_{head_mode}_form": float(np.linalg.norm(F_mode - F_ref) / np.linalg.norm(F_ref))}
 
 
 def student_profile(student, nl, y, gnep):
@@ -808,8 +841,10 @@ def main():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gnep", choices=["gnep", "reference"])
-    ap.add_argument("--precision", default="bf16", choices=["fp32", "tf32", "bf16"],
-                    help="network contractions: bf16 / tf32 on tensor cores, or the plain fp32 form")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16"],
+                    help="network contractions: the FP32 form (default), or bf16 / tf32 on tensor cores")
+    ap.add_argument("--repeats", type=int, default=10,
+                    help="times the K timed steps are repeated (the median repeat is reported)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--report", choices=["precision", "epoch", "batch-size"], default=None,

@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define GNEP_ABI_VERSION 2
+#define GNEP_ABI_VERSION 3
 
 typedef enum {
   GNEP_OK = 0,
@@ -54,8 +54,12 @@ typedef enum {
   GNEP_ERR_UNSUPPORTED = -8        /* hyper-parameters without a compiled kernel */
 } gnep_status;
 
-/* Arithmetic of the network contractions (descriptors and reductions stay
- * FP32/FP64 in every mode). */
+/* Arithmetic of the network contractions (D1.1-D1.10) only.  FP32: CUDA-core
+ * FP32.  TF32 / BF16: tcgen05 tensor-core products with TF32 / BF16 operands
+ * and FP32 accumulation.  In every mode the per-pair geometry is FP32, the
+ * descriptor, force, tangent and coefficient-gradient contractions are
+ * FP32-accurate (split-TF32 tensor-core products), and the cross-atom sums of
+ * energies, virials, loss and gradient are FP64 above FP32 leaves. */
 enum { GNEP_PREC_FP32 = 0, GNEP_PREC_TF32 = 1, GNEP_PREC_BF16 = 2 };
 /* GNEP_LOSS_MSE: Eq. 9 with Eqs. 10-12.  GNEP_LOSS_RMSE: the same weighted sum
  * of the square roots of Eqs. 10-12. */
@@ -166,21 +170,26 @@ int gnep_nlist_export(const gnep_nlist *nl, int which, int32_t *off, int32_t *j,
 int gnep_descriptors(gnep_model *m, const gnep_nlist *nl, float *G, void *stream);
 
 /* The same descriptors as gnep_descriptors, computed without allocating any
- * device memory.  The paper has no counterpart: this serves callers that cannot
- * allocate when they need descriptors, such as code running while a stream is
- * captured into a CUDA graph, hosts whose device memory belongs to another
- * allocator or a fixed pool, and per-step hooks of simulation engines.  The
- * call uses a fixed 8 MiB scratch array built into the library (every GPU that
- * loads the library holds it until the process exits) instead of the nlist's
- * workspace; it needs n_atoms * (n_species * (basis_radial + 1) +
- * 24 * (n_max_angular + 1)) floats (plus alignment) and returns INVALID_ARG for
- * larger batches.  G [n_atoms][N_des] must be device memory; it is written
- * asynchronously on `stream`.  The first call on each device looks up the
- * scratch address; make that first call before any stream capture.  All calls
- * share one scratch array per device: calls whose kernels may overlap on the
- * GPU (different streams without ordering, several threads) race and must not
- * be issued; calls ordered on one stream are safe.  The scratch needs no
- * clearing: every element read is first written by the same call. */
+ * device memory.  The paper has no counterpart.  It serves callers that must
+ * not allocate at the point where they need descriptors: hosts whose device
+ * memory is reserved up front by another allocator or a fixed pool (a
+ * cudaMalloc there fails or fragments that pool), and per-step hooks of
+ * simulation engines that forbid allocation in their hot loop (cudaMalloc and
+ * cudaFree may synchronise the device and stall the loop).  The call works in
+ * a fixed 8 MiB scratch array built into the library (every GPU that loads
+ * the library holds it until the process exits) instead of the nlist's
+ * workspace.  A batch fits when
+ *   roundup64(n_atoms * n_species * (basis_radial + 1))
+ *     + n_atoms * 24 * (n_max_angular + 1)  <=  2^21 floats
+ * (roundup64: the next multiple of 64); larger batches return INVALID_ARG.
+ * G [n_atoms][N_des] must be device memory; it is written asynchronously on
+ * `stream` after the nlist's last build.  The first call on each device looks
+ * up the scratch address (cudaGetSymbolAddress).  All calls share one scratch
+ * array per device and it keeps the last call's contents: calls whose kernels
+ * may overlap on the GPU (different streams without ordering, several
+ * threads) race and must not be issued; calls ordered on one stream are safe.
+ * The scratch needs no clearing: every element a call reads was written
+ * earlier by the same call. */
 int gnep_descriptors_noalloc(gnep_model *m, const gnep_nlist *nl, float *G,
                              void *stream);
 
@@ -216,18 +225,19 @@ int gnep_md_verlet(gnep_model *m, gnep_nlist *nl, double *pos, double *vel,
 int gnep_loss_grad(gnep_model *m, const gnep_nlist *nl, const gnep_labels *y,
                    double *loss_terms, float *grad, void *stream);
 
-/* Autotuner.  Launch shapes of the angular sweeps are per batch: atoms and
- * pairs per tile of the descriptor and tangent sweeps' tiles and of the angular
- * force and c-gradient sweeps' tiles, and the number of persistent blocks of
- * the c-gradient sweep.  gnep_autotune times the loss + gradient evaluation of
+/* Autotuner.  Launch shapes are per batch: atoms and pairs per tile of the
+ * descriptor and tangent sweeps' tiles and of the angular force and c-gradient
+ * sweeps' tiles, the number of persistent blocks of the c-gradient sweep, and
+ * the number of persistent blocks of the network kernels.  gnep_autotune times the loss + gradient evaluation of
  * this batch (median of `reps` runs, no parameter update) over candidate
  * values of each in turn and keeps the fastest in the neighbour list.  It
  * synchronizes `stream` and must not run during stream capture; graphs
  * captured earlier on this list are invalidated (gnep_graph_launch then
- * returns INVALID_ARG).  values [5] = {atoms per descriptor tile, pairs per
+ * returns INVALID_ARG).  values [6] = {atoms per descriptor tile, pairs per
  * descriptor tile, atoms per force tile, pairs per force tile, c-gradient
- * blocks}; gnep_tuning_set takes the same layout (0 = default) and rebuilds
- * the tiles.  Results agree with the untuned ones to FP32 summation order.
+ * blocks, network blocks (at most 456; 0 = one per tile up to the resident
+ * capacity)}; gnep_tuning_set takes the same layout (0 = default) and
+ * rebuilds the tiles.  Results agree with the untuned ones to FP32 summation order.
  * Errors: INVALID_ARG, CUDA, and those of gnep_loss_grad. */
 int gnep_autotune(gnep_model *m, gnep_nlist *nl, const gnep_labels *y,
                   int reps, void *stream);
@@ -306,6 +316,32 @@ const char *gnep_profile_stage_name(int32_t i);
 int gnep_save(gnep_model *m, const char *path);
 int gnep_load(gnep_model *m, const char *path);
 
+/* ---------------------------------------------------- data parallelism */
+
+/* Loss weights of one data-parallel shard (Eqs. 9-12 over a batch split by
+ * structure across ranks).  Eqs. 10-12 normalise by the whole batch (N_str
+ * structures, N atoms), so a shard of S_r structures and N_r atoms that calls
+ * gnep_loss_grad with the MSE form and these weights gets exactly its share
+ * of the whole-batch gradient; summing the shards' gradients over ranks gives
+ * the whole-batch gradient.  out [4] = {lambda_e S_r/N_str, lambda_f N_r/N,
+ * lambda_v S_r/N_str, lambda_l2 on rank 0 else 0}; for GNEP_LOSS_RMSE each of
+ * the first three is further multiplied by 1 / (2 sqrt(L_x)) (0 where L_x =
+ * 0), with mse_total [3] = the whole-batch MSE terms L_e, L_f, L_v (from
+ * gnep_shard_mse_total; may be NULL for the MSE form).  Host-side scalars.
+ * Errors: INVALID_ARG. */
+int gnep_shard_loss_weights(double lambda_e, double lambda_f, double lambda_v,
+                            double lambda_l2, int32_t loss_form,
+                            int64_t local_struct, int64_t local_atoms,
+                            int64_t total_struct, int64_t total_atoms,
+                            const double *mse_total, int32_t rank, double *out);
+/* A shard's MSE terms (loss_terms[1..3] of gnep_loss) as sums that add over
+ * ranks: out [5] = {L_e S_r, L_f 3 N_r, L_v 6 S_r, S_r, N_r}.  After a sum over
+ * ranks, gnep_shard_mse_total turns them into the whole-batch L_e, L_f, L_v
+ * (out [3]; 0 for an empty term).  Host-side.  Errors: INVALID_ARG. */
+int gnep_shard_mse_partials(const double *local_mse, int64_t local_struct,
+                            int64_t local_atoms, double *out);
+int gnep_shard_mse_total(const double *sums, double *out);
+
 /* Synchronise `stream`, read and clear the model's device error flag:
  * NONFINITE (a loss was not finite; that Adam update was skipped), TIMEOUT (a
  * device-side wait gave up), INVALID_ARG (a rebuild's lists failed their
@@ -313,6 +349,16 @@ int gnep_load(gnep_model *m, const char *path);
 int gnep_sync_status(gnep_model *m, void *stream);
 const char *gnep_last_error(void);
 int gnep_abi_version(void);
+
+/* Failure-path self-test of the bounded device waits (library failure
+ * detection; the paper has no counterpart).  Launches one block of the
+ * tensor-core kernels' wait protocol on `stream`: it allocates tensor memory,
+ * waits on an mbarrier that nothing arrives on with a limit of limit_ns
+ * (1e3 .. 2e9), gives up, waits once more with the same limit, frees its
+ * tensor memory, raises TIMEOUT in the model's device flag and returns; the
+ * next gnep_sync_status returns GNEP_ERR_TIMEOUT and clears the flag.  No
+ * fault, no hang: the context stays usable.  Errors: INVALID_ARG, CUDA. */
+int gnep_selftest_wait_timeout(gnep_model *m, int64_t limit_ns, void *stream);
 
 #ifdef __cplusplus
 }

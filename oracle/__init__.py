@@ -173,11 +173,18 @@ def descriptors(cfg: Cfg, params, batch) -> np.ndarray:
     return G
 
 
-def descriptor_scale(cfg: Cfg, params, batch) -> np.ndarray:
-    """Fixed per-component input scale s_v = 1 / (max_v - min_v) over a set."""
-    G = descriptors(cfg, params, batch)
+def scale_from_descriptors(G) -> np.ndarray:
+    """The fixed input scale read into the method (the paper gives none; raw
+    descriptors are O(10) and tanh would saturate): per component v,
+    s_v = 1 / (max_v - min_v) over the atoms of a set, and 1 where max = min."""
+    G = np.asarray(G, dtype=np.float64)
     span = G.max(axis=0) - G.min(axis=0)
     return np.where(span > 0, 1.0 / np.where(span > 0, span, 1.0), 1.0)
+
+
+def descriptor_scale(cfg: Cfg, params, batch) -> np.ndarray:
+    """Fixed per-component input scale over a set of structures."""
+    return scale_from_descriptors(descriptors(cfg, params, batch))
 
 
 def ann(cfg: Cfg, params, scale, e: int, G):
@@ -252,3 +259,45 @@ def adam(theta, m, v, g, t: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-8,
 
 def lr(lr_start: float, lr_stop: float, s: int, n_warmup: int, n_total: int) -> float:
     return lib().orc_lr(lr_start, lr_stop, s, n_warmup, n_total)
+
+
+# 1 eV / (A amu) in A / fs^2, from the SI values of the electronvolt
+# (1.602176634e-19 J) and the atomic mass unit (1.66053906660e-27 kg):
+# 1 eV / (1e-10 m x 1 amu) in m / s^2, times 1e10 A/m x 1e-30 s^2/fs^2.
+EV_PER_A_AMU_IN_A_PER_FS2 = 1.602176634e-19 / (1e-10 * 1.66053906660e-27) * 1e10 * 1e-30
+
+
+def wrap(batch, pos) -> np.ndarray:
+    """Positions mapped into their cell: fractional f = x H^-1 reduced to
+    [0, 1), then x = f H (rows of H are the lattice vectors)."""
+    out = np.array(pos, dtype=np.float64)
+    off = np.asarray(batch.struct_off)
+    for s in range(len(off) - 1):
+        H = np.asarray(batch.cell[s], dtype=np.float64).reshape(3, 3)
+        f = out[off[s]:off[s + 1]] @ np.linalg.inv(H)
+        f -= np.floor(f)
+        out[off[s]:off[s + 1]] = f @ H
+    return out
+
+
+def md_verlet(cfg: Cfg, params, scale, batch, vel, inv_mass, dt: float, steps: int):
+    """Velocity-Verlet NVE with the model's FP64 forces (the MD use of a
+    trained potential, Sec. III): per step, v += dt/2 F/m, x += dt v (then
+    wrapped into the cell), F = F(x), v += dt/2 F/m.  Units A, fs, amu, eV.
+    Returns the positions, velocities, forces and per-structure potential
+    energies after each step."""
+    from types import SimpleNamespace
+    acc = EV_PER_A_AMU_IN_A_PER_FS2 * np.asarray(inv_mass, dtype=np.float64)[:, None]
+    x = np.array(batch.pos, dtype=np.float64)
+    v = np.array(vel, dtype=np.float64)
+    b = SimpleNamespace(struct_off=batch.struct_off, pos=x, types=batch.types, cell=batch.cell)
+    F = forward(cfg, params, scale, b)[2]
+    traj = []
+    for _ in range(steps):
+        v = v + 0.5 * dt * acc * F
+        x = wrap(batch, x + dt * v)
+        b = SimpleNamespace(struct_off=batch.struct_off, pos=x, types=batch.types, cell=batch.cell)
+        _, Es, F, _ = forward(cfg, params, scale, b)
+        v = v + 0.5 * dt * acc * F
+        traj.append((x.copy(), v.copy(), F.copy(), Es.copy()))
+    return traj

@@ -31,7 +31,8 @@ EXPORTS = [
     "gnep_lr_schedule", "gnep_graph_create", "gnep_graph_launch", "gnep_graph_destroy", "gnep_save",
     "gnep_load", "gnep_sync_status", "gnep_last_error", "gnep_abi_version", "gnep_profile_step",
     "gnep_profile_stage_name", "gnep_descriptors_noalloc", "gnep_loss", "gnep_get_grad", "gnep_set_grad",
-    "gnep_autotune", "gnep_tuning_get", "gnep_tuning_set", "gnep_md_verlet",
+    "gnep_autotune", "gnep_tuning_get", "gnep_tuning_set", "gnep_md_verlet", "gnep_shard_loss_weights",
+    "gnep_shard_mse_partials", "gnep_shard_mse_total", "gnep_selftest_wait_timeout",
 ]
 
 
@@ -98,6 +99,11 @@ _SIGS = {
     "gnep_profile_step": [_vp, _vp, C.POINTER(Labels), _vp, C.c_int32, C.POINTER(C.c_int32), _vp],
     "gnep_profile_stage_name": [C.c_int32],
     "gnep_abi_version": [],
+    "gnep_shard_loss_weights": [C.c_double, C.c_double, C.c_double, C.c_double, C.c_int32, C.c_int64,
+                                C.c_int64, C.c_int64, C.c_int64, _vp, C.c_int32, _vp],
+    "gnep_shard_mse_partials": [_vp, C.c_int64, C.c_int64, _vp],
+    "gnep_shard_mse_total": [_vp, _vp],
+    "gnep_selftest_wait_timeout": [_vp, C.c_int64, _vp],
 }
 
 _lib = None

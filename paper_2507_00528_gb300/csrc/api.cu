@@ -723,7 +723,7 @@ int gnep_graph_launch(gnep_graph* g, void* stream) {
 
 namespace {
 
-constexpr int kTuneKnobs = 5;  // na[0], ch[0], na[1], ch[1], cg_blocks
+constexpr int kTuneKnobs = 6;  // na[0], ch[0], na[1], ch[1], cg_blocks, net_blocks
 
 int* knob(gnep_nlist* nl, int k) {
   switch (k) {
@@ -731,7 +731,8 @@ int* knob(gnep_nlist* nl, int k) {
     case 1: return &nl->tune.ch[0];
     case 2: return &nl->tune.na[1];
     case 3: return &nl->tune.ch[1];
-    default: return &nl->tune.cg_blocks;
+    case 4: return &nl->tune.cg_blocks;
+    default: return &nl->tune.net_blocks;
   }
 }
 
@@ -744,6 +745,7 @@ void effective_tuning(const gnep_model* m, const gnep_nlist* nl, int32_t* v) {
     v[2 * w + 1] = nl->tune.ch[w] > 0 ? nl->tune.ch[w] : ch;
   }
   v[4] = cgrad_blocks(nl);
+  v[5] = nl->tune.net_blocks;  // 0: one block per tile up to the resident capacity
 }
 
 // Median over `reps` of one loss + gradient evaluation (no update), in ms.
@@ -785,7 +787,7 @@ int gnep_tuning_set(gnep_model* m, gnep_nlist* nl, const int32_t* values, void* 
   if (rc) return rc;
   if (!values) return set_error(GNEP_ERR_INVALID_ARG, "NULL values");
   for (int k = 0; k < kTuneKnobs; ++k)
-    if (values[k] < 0 || values[k] > (k == 4 ? kCgBlocksMax : 1 << 20))
+    if (values[k] < 0 || values[k] > (k == 4 ? kCgBlocksMax : k == 5 ? kNetBlocks : 1 << 20))
       return set_error(GNEP_ERR_INVALID_ARG, "tuning value out of range");
   for (int k = 0; k < kTuneKnobs; ++k) *knob(nl, k) = values[k];
   ++nl->gen;
@@ -807,7 +809,7 @@ int gnep_autotune(gnep_model* m, gnep_nlist* nl, const gnep_labels* y, int reps,
   const std::vector<std::vector<int>> cand = {
       {na0, na0 / 2, na0 / 4},  {64, 128, 256, 384, 512},
       {na1, na1 / 2, na1 / 4},  {32, 48, 64, 96, 128, 192},
-      {152, 304, 456, 608}};
+      {152, 304, 456, 608},     {0, 152, 304}};
   for (int k = 0; k < kTuneKnobs; ++k) *knob(nl, k) = cur[k];
   ++nl->gen;
   if ((rc = build_angular_tiles(m, nl, st))) return rc;
@@ -817,7 +819,7 @@ int gnep_autotune(gnep_model* m, gnep_nlist* nl, const gnep_labels* y, int reps,
     const int keep = *knob(nl, k);
     int pick = keep;
     for (int v : cand[k]) {
-      if (v < 1 || v == keep) continue;
+      if ((v < 1 && k != 5) || v == keep) continue;
       *knob(nl, k) = v;
       if (k < 4 && (rc = build_angular_tiles(m, nl, st))) return rc;
       float t = 0.f;
@@ -987,7 +989,59 @@ const char* gnep_profile_stage_name(int32_t i) {
   return (i >= 0 && i < g_stage_count) ? g_stage_names[i] : "";
 }
 
+// ------------------------------------------------------- data parallelism
+
+int gnep_shard_loss_weights(double lambda_e, double lambda_f, double lambda_v, double lambda_l2, int32_t loss_form,
+                            int64_t local_struct, int64_t local_atoms, int64_t total_struct, int64_t total_atoms,
+                            const double* mse_total, int32_t rank, double* out) {
+  if (!out || local_struct < 0 || local_atoms < 0 || total_struct < local_struct || total_atoms < local_atoms)
+    return set_error(GNEP_ERR_INVALID_ARG, "shard weights: bad counts or NULL output");
+  if (loss_form != GNEP_LOSS_MSE && loss_form != GNEP_LOSS_RMSE)
+    return set_error(GNEP_ERR_INVALID_ARG, "shard weights: unknown loss form");
+  if (loss_form == GNEP_LOSS_RMSE && !mse_total)
+    return set_error(GNEP_ERR_INVALID_ARG, "shard weights: the RMSE form needs the whole-batch MSE terms");
+  // Eqs. 10-12 normalise by the whole batch: a shard's share of each term is
+  // its fraction of the structures (energy, virial) or atoms (forces)
+  const double ws = total_struct > 0 ? (double)local_struct / (double)total_struct : 0.0;
+  const double wa = total_atoms > 0 ? (double)local_atoms / (double)total_atoms : 0.0;
+  double w[3] = {lambda_e * ws, lambda_f * wa, lambda_v * ws};
+  if (loss_form == GNEP_LOSS_RMSE)  // d sqrt(L_x) = dL_x / (2 sqrt(L_x)), 0 where L_x = 0
+    for (int x = 0; x < 3; ++x) w[x] *= mse_total[x] > 0.0 ? 0.5 / std::sqrt(mse_total[x]) : 0.0;
+  out[0] = w[0];
+  out[1] = w[1];
+  out[2] = w[2];
+  out[3] = rank == 0 ? lambda_l2 : 0.0;  // the L2 term is carried once
+  return GNEP_OK;
+}
+
+int gnep_shard_mse_partials(const double* local_mse, int64_t local_struct, int64_t local_atoms, double* out) {
+  if (!local_mse || !out || local_struct < 0 || local_atoms < 0)
+    return set_error(GNEP_ERR_INVALID_ARG, "mse partials: bad counts or NULL pointer");
+  out[0] = local_mse[0] * (double)local_struct;      // sum of squared energy residuals
+  out[1] = local_mse[1] * 3.0 * (double)local_atoms;  // ... force components
+  out[2] = local_mse[2] * 6.0 * (double)local_struct; // ... virial components
+  out[3] = (double)local_struct;
+  out[4] = (double)local_atoms;
+  return GNEP_OK;
+}
+
+int gnep_shard_mse_total(const double* sums, double* out) {
+  if (!sums || !out) return set_error(GNEP_ERR_INVALID_ARG, "mse total: NULL pointer");
+  const double S = sums[3], N = sums[4];
+  out[0] = S > 0 ? sums[0] / S : 0.0;
+  out[1] = N > 0 ? sums[1] / (3.0 * N) : 0.0;
+  out[2] = S > 0 ? sums[2] / (6.0 * S) : 0.0;
+  return GNEP_OK;
+}
+
 // ----------------------------------------------------------------- status
+
+int gnep_selftest_wait_timeout(gnep_model* m, int64_t limit_ns, void* stream) {
+  if (!m || limit_ns < 1000 || limit_ns > 2000000000LL)
+    return set_error(GNEP_ERR_INVALID_ARG, "selftest: limit_ns must lie in [1e3, 2e9]");
+  cudaSetDevice(m->device);
+  return wait_selftest(m, (uint64_t)limit_ns, (cudaStream_t)stream);
+}
 
 int gnep_sync_status(gnep_model* m, void* stream) {
   if (!m) return set_error(GNEP_ERR_INVALID_ARG, "NULL model");

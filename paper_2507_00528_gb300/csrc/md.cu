@@ -7,7 +7,9 @@ namespace gnep {
 
 namespace {
 
-constexpr double kAccel = 9.648533212331e-3;  // 1 eV / (A amu) in A / fs^2
+// 1 eV / (A amu) in A / fs^2: the electronvolt (1.602176634e-19 J) over 1e-10 m
+// times the atomic mass unit (1.66053906660e-27 kg), in m / s^2, times 1e-20.
+constexpr double kAccel = 1.602176634e-19 / (1e-10 * 1.66053906660e-27) * 1e-20;
 
 // Inverse cell per structure (rows a, b, c of H are the lattice vectors).
 __global__ void k_md_hinv(int S, const double* __restrict__ cell, double* __restrict__ hinv) {

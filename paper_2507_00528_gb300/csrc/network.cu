@@ -427,7 +427,7 @@ int mlp_forward(const gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
   const int ntiles = T.tbase[NS];
   if (ntiles == 0) return GNEP_OK;
   Workspace& w = nl->ws;
-  const int grid = ntiles < kNetBlocks ? ntiles : kNetBlocks;
+  const int grid = net_blocks(nl, ntiles < kNetBlocks ? ntiles : kNetBlocks);
   k_mlp_fwd_tile<D, HP, NS, NQR, KR><<<grid, NT, mlp_fwd_smem<D, HP, NS, NQR, KR>(), st>>>(
       T, ntiles, m->dev(), w.G, w.X, w.Ep, w.Eatom, w.chat);
   GNEP_CHECK_LAUNCH("k_mlp_fwd_tile");
@@ -440,7 +440,7 @@ int mlp_backward(const gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
   const Tiles T = make_tiles(nl, ns);
   const int ntiles = T.tbase[ns];
   Workspace& w = nl->ws;
-  const int grid = ntiles < kNetBlocks ? (ntiles > 0 ? ntiles : 1) : kNetBlocks;
+  const int grid = net_blocks(nl, ntiles < kNetBlocks ? (ntiles > 0 ? ntiles : 1) : kNetBlocks);
   w.net_blocks = grid;
   GNEP_CUDA(cudaMemsetAsync(w.net_part, 0, sizeof(float) * (size_t)grid * ns * m->net_size, st));
   if (ntiles == 0) return GNEP_OK;

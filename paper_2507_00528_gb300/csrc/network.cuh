@@ -37,5 +37,8 @@ template <bool TF32, int D, int HPn, int NS, int NQR, int KR>
 int mlp_forward_tc(const gnep_model* m, gnep_nlist* nl, cudaStream_t st);
 template <bool TF32, int D, int HPn>
 int mlp_backward_tc(const gnep_model* m, gnep_nlist* nl, cudaStream_t st);
+// One block of the tensor-core kernels' bounded-wait protocol on an mbarrier
+// that nothing arrives on (raises TIMEOUT in the model's error flag).
+int wait_selftest(const gnep_model* m, uint64_t limit_ns, cudaStream_t st);
 
 }  // namespace gnep

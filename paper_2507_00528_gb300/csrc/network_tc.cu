@@ -258,8 +258,8 @@ __device__ __forceinline__ void sync_for_mma() {
 
 // Wait for the MMAs committed on `mbar` (phase `ph`); the outcome is made
 // uniform across the block so that every thread leaves the tile loop together.
-__device__ __forceinline__ bool wait_mma(uint64_t* mbar, uint32_t& ph) {
-  const bool ok = tc::mbar_wait(mbar, ph, kWaitNs);
+__device__ __forceinline__ bool wait_mma(uint64_t* mbar, uint32_t& ph, uint64_t limit_ns = kWaitNs) {
+  const bool ok = tc::mbar_wait(mbar, ph, limit_ns);
   ph ^= 1u;
   tc::fence_after();
   return __syncthreads_and(ok) != 0;
@@ -267,9 +267,31 @@ __device__ __forceinline__ bool wait_mma(uint64_t* mbar, uint32_t& ph) {
 
 // After a timed-out wait: give the MMAs in flight a second bounded wait before
 // the tensor memory they write is released, and raise the error flag.
-__device__ __forceinline__ void on_timeout(uint64_t* mbar, uint32_t ph, int* err) {
-  tc::mbar_wait(mbar, ph ^ 1u, kWaitNs);
+__device__ __forceinline__ void on_timeout(uint64_t* mbar, uint32_t ph, int* err, uint64_t limit_ns = kWaitNs) {
+  tc::mbar_wait(mbar, ph ^ 1u, limit_ns);
   if (threadIdx.x == 0) atomicOr(err, kErrTimeout);
+}
+
+// The failure path of the bounded waits, run on purpose: one block allocates
+// tensor memory as the network kernels do, waits with a limit of limit_ns on
+// an mbarrier that nothing arrives on, gives up, takes the second bounded
+// wait, frees its tensor memory and raises TIMEOUT in the error flag.
+__global__ void __launch_bounds__(NTC) k_wait_selftest(uint64_t limit_ns, int* __restrict__ err) {
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t tbase;
+  const int warp = threadIdx.x >> 5;
+  if (warp == 0) tc::tmem_alloc(&tbase, 32);
+  if (threadIdx.x == 0) tc::mbar_init(&mbar, 1);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tm = tbase;
+  uint32_t ph = 0;
+  const bool ok = wait_mma(&mbar, ph, limit_ns);  // no MMA was committed: this wait runs out
+  if (!ok) on_timeout(&mbar, ph, err, limit_ns);
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tm, 32);
 }
 
 }  // namespace
@@ -636,6 +658,12 @@ int tc_set_smem(K kern, int need, int cols) {
 
 }  // namespace
 
+int wait_selftest(const gnep_model* m, uint64_t limit_ns, cudaStream_t st) {
+  k_wait_selftest<<<1, NTC, 0, st>>>(limit_ns, m->err);
+  GNEP_CHECK_LAUNCH("k_wait_selftest");
+  return GNEP_OK;
+}
+
 template <bool TF32, int D, int HPn, int NS, int NQR, int KR>
 int mlp_setup_tc() {
   using Dm = Dims<TF32, D, HPn>;
@@ -654,6 +682,7 @@ int mlp_forward_tc(const gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
   auto kern = k_mlp_fwd_tc<TF32, D, HPn, NS, NQR, KR>;
   int smem = 0, grid = 0;
   if (int rc = tc_launch_shape(kern, Dm::fwd_smem, Dm::fwd_cols, ntiles, smem, grid)) return rc;
+  grid = net_blocks(nl, grid);
   kern<<<grid, NTC, smem, st>>>(T, ntiles, m->dev(), w.G, w.Ep, w.Eatom, w.chat, m->err);
   GNEP_CHECK_LAUNCH("k_mlp_fwd_tc");
   return GNEP_OK;
@@ -671,6 +700,7 @@ int mlp_backward_tc(const gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
   if (ntiles > 0)
     if (int rc = tc_launch_shape(kern, Dm::bwd_smem, Dm::bwd_cols, ntiles, smem, grid)) return rc;
   if (grid > kNetBlocks) grid = kNetBlocks;  // net_part holds kNetBlocks partials
+  grid = net_blocks(nl, grid);
   w.net_blocks = grid;
   GNEP_CUDA(cudaMemsetAsync(w.net_part, 0, sizeof(float) * (size_t)grid * ns * m->net_size, st));
   if (ntiles == 0) return GNEP_OK;

@@ -1175,16 +1175,17 @@ int ang_grid_cap() {
 
 // Descriptor (TAN = false: S, q_nl, q4 into Sout, Gout) or tangent (TAN = true:
 // Sdot, qdot into Sout, Gout; w_ij into wij) sweep over the tiles of atile[0].
-// Products carry FP32 accuracy (3xTF32) except in the BF16 precision mode.
+// Products carry FP32 accuracy (split TF32) in every precision mode: the
+// precision modes narrow the network contractions only.
 template <class C, bool TAN>
 int launch_ang(const gnep_model* m, const gnep_nlist* nl, cudaStream_t st, const float4* a, const float* Bs,
                const float* Sin, float* Sout, float* Gout, float4* wij) {
+  (void)m;
   const int ntile = nl->natile[0];
   if (ntile < 1) return GNEP_OK;
-  const bool split = m->precision != GNEP_PREC_BF16;
-  const int cap = split ? ang_grid_cap<C, TAN, true>() : ang_grid_cap<C, TAN, false>();
+  const int cap = ang_grid_cap<C, TAN, true>();
   const int nb = ntile < cap ? ntile : cap;
-  auto kern = split ? k_ang_mma<C, TAN, true> : k_ang_mma<C, TAN, false>;
+  auto kern = k_ang_mma<C, TAN, true>;
   kern<<<nb, 32 * kAngWarps, sizeof(AngSmem<C, TAN>), st>>>(ntile, nl->atile[0], m->dev(), nl->type, nl->atom_struct,
                                                             nl->L[1].off, nl->L[1].owner, nl->L[1].j, nl->L[1].rij,
                                                             a, Bs, Sin, Sout, Gout, wij);
@@ -1311,7 +1312,7 @@ struct Runner {
     const int nb = cgrad_blocks(nl);
     k_cgrad_radial<C><<<nb, 32 * kCgRadialWarps, 0, A.st>>>(N, nl->type, w.Gb, w.Ep, w.FR, w.FRd, w.cpart);
     stage("cgrad_radial");
-    auto ang = m->precision != GNEP_PREC_BF16 ? k_cgrad_ang<C, true> : k_cgrad_ang<C, false>;
+    auto ang = k_cgrad_ang<C, true>;  // split TF32 in every precision mode
     ang<<<nb, 32 * kCgWarps, sizeof(CgSmem<C>), A.st>>>(nl->natile[1], nl->atile[1], dm, nl->type, nl->L[1].off,
                                                          nl->L[1].rij, w.wij, w.S, w.Sd, w.Gb, w.Ep, w.cpart);
     stage("cgrad");
@@ -1342,16 +1343,11 @@ bool shape_supported(const Shape& s) {
 namespace {
 template <class C>
 int setup_shape() {
-  if (int rc = setup_ang<C, false, false>()) return rc;
   if (int rc = setup_ang<C, false, true>()) return rc;
-  if (int rc = setup_ang<C, true, false>()) return rc;
   if (int rc = setup_ang<C, true, true>()) return rc;
   GNEP_CUDA(cudaFuncSetAttribute(k_cgrad_ang<C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sizeof(CgSmem<C>)));
-  GNEP_CUDA(cudaFuncSetAttribute(k_cgrad_ang<C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(CgSmem<C>)));
   GNEP_CUDA(cudaFuncSetAttribute(k_cgrad_ang<C, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-  GNEP_CUDA(cudaFuncSetAttribute(k_cgrad_ang<C, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   int rc = mlp_setup<C::NDES, 32, C::NS, C::NQR, C::KR>();
   if (!rc) rc = mlp_setup<C::NDES, 64, C::NS, C::NQR, C::KR>();
   if (!rc) rc = mlp_setup<C::NDES, 128, C::NS, C::NQR, C::KR>();
@@ -1429,14 +1425,14 @@ void angular_tile_limits(const Shape& s, int which, int* na, int* ch) {
 // ---------------------------------------------------------------------------
 // Descriptors without any device allocation.
 //
-// Some callers cannot allocate device memory at the point where they need
-// descriptors: code that runs while a CUDA stream is being captured into a
-// graph (allocation is not a capturable operation), hosts whose device memory
-// is entirely owned by another allocator or a fixed pool set up at start-up,
+// Some callers must not allocate device memory at the point where they need
+// descriptors: hosts whose device memory is reserved up front by another
+// allocator or a fixed pool (a cudaMalloc there fails or fragments the pool),
 // and per-step hooks of simulation engines that forbid allocation in their hot
-// loop.  For them the descriptor sweep can use this fixed scratch array, which
-// every GPU that loads the library holds until the process exits, instead of
-// workspace memory.
+// loop (cudaMalloc and cudaFree may synchronise the device).  For them the
+// descriptor sweep can use this fixed scratch array, which every GPU that
+// loads the library holds until the process exits, instead of workspace
+// memory.  Calls share the array; calls that overlap on the GPU race.
 namespace gnep {
 namespace {
 

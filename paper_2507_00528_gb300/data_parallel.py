@@ -46,31 +46,49 @@ class Counts:
     n_atoms: int
 
 
+def _f64(v):
+    return np.ascontiguousarray(v, dtype=np.float64)
+
+
 def combine_mse(local_terms, local: Counts, reduce_sum) -> np.ndarray:
     """Whole-batch (Le, Lf, Lv) from each rank's shard MSEs (Eqs. 10-12):
-    count-weighted sums over ranks.  `reduce_sum` sums a float64 vector over
-    ranks (an all-reduce)."""
-    Le, Lf, Lv = (float(x) for x in local_terms)
-    v = np.array([Le * local.n_struct, Lf * 3 * local.n_atoms, Lv * 6 * local.n_struct,
-                  local.n_struct, local.n_atoms], dtype=np.float64)
-    v = reduce_sum(v)
-    S, N = v[3], v[4]
-    return np.array([v[0] / S if S else 0.0, v[1] / (3 * N) if N else 0.0, v[2] / (6 * S) if S else 0.0])
+    count-weighted sums over ranks (gnep_shard_mse_partials, then
+    gnep_shard_mse_total).  `reduce_sum` sums a float64 vector over ranks (an
+    all-reduce)."""
+    from . import _lib
+    L = _lib.load()
+    terms = _f64(np.asarray(local_terms, dtype=np.float64)[:3])
+    part = np.zeros(5)
+    _lib.check(L.gnep_shard_mse_partials(terms.ctypes.data, local.n_struct, local.n_atoms, part.ctypes.data))
+    sums = _f64(reduce_sum(part))
+    out = np.zeros(3)
+    _lib.check(L.gnep_shard_mse_total(sums.ctypes.data, out.ctypes.data))
+    return out
 
 
 def effective_weights(lam_e, lam_f, lam_v, lam_l2, form, local: Counts, total: Counts, mse_total=None,
                       rank: int = 0):
     """Per-rank MSE-form loss weights (lambda_e', lambda_f', lambda_v', lambda_l2')
-    whose gradient is the shard's exact share of the whole-batch gradient."""
-    ws = local.n_struct / total.n_struct if total.n_struct else 0.0
-    wa = local.n_atoms / total.n_atoms if total.n_atoms else 0.0
-    le, lf, lv = lam_e * ws, lam_f * wa, lam_v * ws
-    if form == LOSS_RMSE:
-        if mse_total is None:
-            raise ValueError("the RMSE form needs the whole-batch MSE terms")
-        k = [0.5 / np.sqrt(x) if x > 0 else 0.0 for x in mse_total]
-        le, lf, lv = le * k[0], lf * k[1], lv * k[2]
-    return le, lf, lv, (lam_l2 if rank == 0 else 0.0)
+    whose gradient is the shard's exact share of the whole-batch gradient
+    (gnep_shard_loss_weights)."""
+    from . import _lib
+    L = _lib.load()
+    mse = None if mse_total is None else _f64(mse_total)
+    out = np.zeros(4)
+    _lib.check(L.gnep_shard_loss_weights(float(lam_e), float(lam_f), float(lam_v), float(lam_l2), int(form),
+                                         local.n_struct, local.n_atoms, total.n_struct, total.n_atoms,
+                                         None if mse is None else mse.ctypes.data, int(rank), out.ctypes.data))
+    return tuple(float(x) for x in out)
+
+
+def structure_costs(nl) -> np.ndarray:
+    """Per-structure cost for shard balancing: atoms x neighbours, i.e. the
+    structure's radial plus angular pair count, from a neighbour list built
+    over the whole batch (NeighborList of gnep.py)."""
+    offR = nl.export(0)[0].astype(np.int64)
+    offA = nl.export(1)[0].astype(np.int64)
+    soff = np.asarray(nl.struct_off_host, dtype=np.int64)
+    return (offR[soff[1:]] - offR[soff[:-1]]) + (offA[soff[1:]] - offA[soff[:-1]])
 
 
 def total_loss(lam_e, lam_f, lam_v, form, mse_total, l2_term=0.0) -> float:
@@ -82,7 +100,8 @@ def total_loss(lam_e, lam_f, lam_v, form, mse_total, l2_term=0.0) -> float:
 
 class DataParallelStep:
     """One training step of a shard on this rank's GPU, with the gradient
-    summed over ranks by torch.distributed (NCCL) before the Adam update.
+    summed over ranks by torch.distributed (NCCL, or gloo through host
+    copies) before the Adam update.
 
     ``model`` is a GNEP, ``nl`` the neighbour list of this rank's shard and
     ``y`` its labels (gnep.Labels with the whole-batch loss weights); ``local``
@@ -98,8 +117,13 @@ class DataParallelStep:
         self.rank = dist.get_rank() if dist.is_initialized() else 0
         self.grad = torch.zeros(model.n_params, dtype=torch.float64, device="cuda")
 
+    def _on_host(self):
+        """gloo reduces host tensors; NCCL device tensors."""
+        return self.dist.is_initialized() and self.dist.get_backend() == "gloo"
+
     def _reduce(self, v):
-        t = self.torch.as_tensor(v, dtype=self.torch.float64, device="cuda")
+        dev = "cpu" if self._on_host() else "cuda"
+        t = self.torch.as_tensor(np.asarray(v, dtype=np.float64), dtype=self.torch.float64, device=dev)
         if self.dist.is_initialized():
             self.dist.all_reduce(t)
         return t.cpu().numpy()
@@ -120,7 +144,12 @@ class DataParallelStep:
         terms, _ = self.model.loss_grad(self.nl, yr, grad=False)
         self.model.get_grad(self.grad)
         if self.dist.is_initialized():
-            self.dist.all_reduce(self.grad)
+            if self._on_host():
+                g = self.grad.cpu()
+                self.dist.all_reduce(g)
+                self.grad.copy_(g)
+            else:
+                self.dist.all_reduce(self.grad)
         self.model.set_grad(self.grad)
         self.model.adam_step_scheduled(lr_start, lr_stop, n_warmup, n_total)
         if not want_loss:

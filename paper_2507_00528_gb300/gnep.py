@@ -102,6 +102,8 @@ class NeighborList:
         self.h = h
         self.n_struct = cb.n_struct
         self.n_atoms = cb.n_atoms
+        so = batch.struct_off.cpu().numpy() if isinstance(batch, DeviceBatch) else batch.struct_off
+        self.struct_off_host = np.array(so, dtype=np.int64)
 
     def rebuild(self, batch, stream=None):
         L = _lib.load()
@@ -127,7 +129,8 @@ class NeighborList:
                                             _stream()))
         return off, j[:n], sh[:n]
 
-    TUNING_KEYS = ("desc_tile_atoms", "desc_tile_pairs", "force_tile_atoms", "force_tile_pairs", "cgrad_blocks")
+    TUNING_KEYS = ("desc_tile_atoms", "desc_tile_pairs", "force_tile_atoms", "force_tile_pairs", "cgrad_blocks",
+                   "net_blocks")
 
     def autotune(self, y: "Labels", reps: int = 3, stream=None) -> dict:
         """Pick the fastest launch shapes of the angular sweeps for this batch
@@ -137,7 +140,7 @@ class NeighborList:
         return self.tuning()
 
     def tuning(self) -> dict:
-        v = np.zeros(5, dtype=np.int32)
+        v = np.zeros(len(self.TUNING_KEYS), dtype=np.int32)
         check(_lib.load().gnep_tuning_get(self.model.h, self.h, v.ctypes.data))
         return dict(zip(self.TUNING_KEYS, v.tolist()))
 

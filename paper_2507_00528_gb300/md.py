@@ -17,7 +17,7 @@ from ._lib import check
 from .gnep import GNEP, DeviceBatch, _ptr, _stream
 
 KB = 8.617333262e-5          # eV / K
-ACCEL = 9.648533212331e-3    # 1 eV / (A amu) in A / fs^2
+ACCEL = 1.602176634e-19 / (1e-10 * 1.66053906660e-27) * 1e-20  # 1 eV / (A amu) in A / fs^2
 MASS = {"Sb": 121.760, "Te": 127.60}
 
 

@@ -21,6 +21,13 @@ from paper_2507_00528_gb300 import synth
 CFG = dict(nq_r=5, nq_a=5, k_r=9, k_a=9, hidden=30, four_body=False)
 
 
+@pytest.fixture(scope="module", autouse=True)
+def _library():
+    """The shard-weight arithmetic lives in libgnep (host-side entry points)."""
+    from paper_2507_00528_gb300 import build
+    build.build()
+
+
 def _problem(form):
     rng = np.random.default_rng(44)
     b = synth.make_batch([9, 14, 6, 11, 8], [0, 1, 2, 1, 0], rng)
@@ -117,3 +124,15 @@ def test_effective_weights_single_rank_is_identity():
     w = dp.effective_weights(1.0, 1.0, 1.0, 0.0, dp.LOSS_RMSE, dp.Counts(3, 30), dp.Counts(6, 90),
                              mse_total=[4.0, 0.0, 0.25], rank=1)
     assert w == pytest.approx((0.5 * 0.25, 0.0, 0.5 * 1.0, 0.0))
+
+
+def test_shard_entry_points_by_hand():
+    """gnep_shard_mse_partials / gnep_shard_mse_total on hand values: two
+    shards (2 structures, 30 atoms; 1 structure, 10 atoms) with MSEs
+    (4, 1, 9) and (1, 4, 0) combine to the count-weighted means of Eqs. 10-12."""
+    a = dp.combine_mse([4.0, 1.0, 9.0], dp.Counts(2, 30), lambda v: v + np.array([1.0 * 1, 4.0 * 30, 0.0, 1, 10]))
+    np.testing.assert_allclose(a, [(4.0 * 2 + 1.0) / 3, (1.0 * 90 + 4.0 * 30) / 120, 9.0 * 12 / 18], rtol=1e-15)
+    w = dp.effective_weights(2.0, 3.0, 0.5, 0.1, dp.LOSS_MSE, dp.Counts(1, 10), dp.Counts(4, 50), rank=2)
+    assert w == pytest.approx((0.5, 0.6, 0.125, 0.0), rel=1e-15)
+    with pytest.raises(Exception):
+        dp.effective_weights(1.0, 1.0, 1.0, 0.0, dp.LOSS_RMSE, dp.Counts(1, 10), dp.Counts(4, 50))

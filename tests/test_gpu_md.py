@@ -73,3 +73,33 @@ def test_rejects_host_arrays():
     sim.pos = sim.pos.cpu()
     with pytest.raises(gnep._lib.GnepError):
         sim.step(1.0)
+
+
+def test_trajectory_matches_the_oracle_integrator():
+    """Ten velocity-Verlet steps of gnep_md_verlet (FP32 forces, FP64 positions
+    and velocities) against the oracle's FP64 velocity Verlet from the same
+    start: positions, velocities, forces and potential energies after every
+    step, within the FP32 force tolerance carried through the integrator."""
+    import oracle as O
+    b = synth.make_batch([24, 19], [0, 2], np.random.default_rng(14))
+    cfg = O.Cfg(nq_r=5, nq_a=5, k_r=9, k_a=9, hidden=30)
+    P = synth.uniform_params(cfg.n_params, 101)
+    s = O.descriptor_scale(cfg, P.astype(np.float64), b).astype(np.float32)
+    m = gnep.GNEP(**SHAPE)
+    m.set_params(torch.from_numpy(P))
+    m.set_scale(torch.from_numpy(s))
+    sim = md.NVE(m, b, temperature=600.0, seed=5)
+    v0 = sim.vel.cpu().numpy().copy()
+    traj = O.md_verlet(cfg, P.astype(np.float64), s.astype(np.float64), b, v0, 1.0 / sim.mass, 1.0, 10)
+    for k in range(10):
+        sim.step(1.0)
+        x, v, F, Es = traj[k]
+        d = sim.pos.cpu().numpy() - x
+        for st in range(b.n_struct):  # minimum image
+            a0, a1 = b.struct_off[st], b.struct_off[st + 1]
+            f = d[a0:a1] @ np.linalg.inv(b.cell[st])
+            d[a0:a1] = (f - np.round(f)) @ b.cell[st]
+        assert np.abs(d).max() < 1e-7, (k, np.abs(d).max())
+        assert np.abs(sim.vel.cpu().numpy() - v).max() < 1e-8 + 1e-6 * np.abs(v).max()
+        assert rel_l2(sim.F.double().cpu().numpy(), F) < 1e-5
+        assert rel_l2(sim.E_pot.cpu().numpy(), Es) < 1e-6

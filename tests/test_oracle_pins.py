@@ -534,3 +534,100 @@ def test_lr_schedule_eq17(oracle):
     assert oracle.lr(a, z, 10, 10, 100) == pytest.approx(a)
     assert oracle.lr(a, z, 55, 10, 100) == pytest.approx(z + (a - z) * 0.5)
     assert oracle.lr(a, z, 100, 10, 100) == pytest.approx(z)
+
+
+def test_descriptor_scale_on_a_hand_made_set(oracle):
+    """The input scale reading (none in the paper): s_v = 1 / (max_v - min_v)
+    over the set's atoms, 1 for a constant component.  A hand-made G with a
+    positive, a negative, a constant and a single-outlier column; the scaled
+    columns then span exactly 1."""
+    G = np.array([[1.0, -3.0, 2.5, 0.0],
+                  [4.0, -1.0, 2.5, 0.0],
+                  [2.0, -2.0, 2.5, 8.0]])
+    s = oracle.scale_from_descriptors(G)
+    np.testing.assert_array_equal(s, [1.0 / 3.0, 0.5, 1.0, 0.125])
+    span = (s * G).max(axis=0) - (s * G).min(axis=0)
+    np.testing.assert_allclose(span[[0, 1, 3]], 1.0, rtol=1e-15)
+    # and on real descriptors it is that function of the oracle's G
+    from paper_2507_00528_gb300 import synth
+    cfg = oracle.Cfg()
+    P = synth.uniform_params(cfg.n_params, 3).astype(np.float64)
+    b = synth.make_batch([12, 9], [0, 1], np.random.default_rng(2))
+    Gb = oracle.descriptors(cfg, P, b)
+    np.testing.assert_array_equal(oracle.descriptor_scale(cfg, P, b),
+                                  1.0 / (Gb.max(axis=0) - Gb.min(axis=0)))
+
+
+# ------------------------------------------------------------ MD (Sec. III use)
+
+def _md_cfg(oracle):
+    return oracle.Cfg(nq_r=5, nq_a=5, k_r=9, k_a=9, hidden=30)
+
+
+def test_md_free_flight(oracle):
+    """An atom alone in a 30 A cell has no neighbours, so no force: it moves
+    at constant velocity and is wrapped back into the cell."""
+    from types import SimpleNamespace
+    cfg = _md_cfg(oracle)
+    P = np.random.default_rng(1).uniform(-0.5, 0.5, cfg.n_params)
+    b = SimpleNamespace(struct_off=np.array([0, 1], dtype=np.int32), pos=np.array([[29.0, 0.5, 15.0]]),
+                        types=np.array([1], dtype=np.int32), cell=np.eye(3)[None] * 30.0)
+    v0 = np.array([[0.3, -0.2, 0.01]])
+    traj = oracle.md_verlet(cfg, P, np.ones(cfg.n_des), b, v0, np.array([1 / 127.6]), 2.0, 5)
+    x, v, F, _ = traj[-1]
+    np.testing.assert_array_equal(F, 0.0)
+    np.testing.assert_allclose(v, v0, rtol=0, atol=0)
+    np.testing.assert_allclose(x, np.mod(b.pos + 10.0 * v0, 30.0), rtol=0, atol=1e-12)
+
+
+def _md_problem(oracle):
+    from paper_2507_00528_gb300 import synth
+    cfg = _md_cfg(oracle)
+    P = synth.uniform_params(cfg.n_params, 21).astype(np.float64)
+    b = synth.make_batch([10, 7], [0, 1], np.random.default_rng(31))
+    s = oracle.descriptor_scale(cfg, P, b)
+    rng = np.random.default_rng(4)
+    inv_m = 1.0 / np.where(b.types == 0, 121.76, 127.6)
+    v0 = rng.standard_normal((b.n_atoms, 3)) * 0.004
+    return cfg, P, s, b, v0, inv_m
+
+
+def test_md_first_step_is_the_taylor_step(oracle):
+    """After one step x = x0 + dt v0 + dt^2/2 F0/m (wrapped)."""
+    cfg, P, s, b, v0, inv_m = _md_problem(oracle)
+    F0 = oracle.forward(cfg, P, s, b)[2]
+    x1 = oracle.md_verlet(cfg, P, s, b, v0, inv_m, 1.5, 1)[0][0]
+    acc = oracle.EV_PER_A_AMU_IN_A_PER_FS2 * inv_m[:, None]
+    ref = oracle.wrap(b, b.pos + 1.5 * v0 + 0.5 * 1.5 ** 2 * acc * F0)
+    np.testing.assert_allclose(x1, ref, rtol=0, atol=1e-12)
+
+
+def test_md_time_reversible_and_second_order(oracle):
+    """Velocity Verlet is time reversible (n steps, reversed velocities, n
+    steps back to the start) and its energy error is second order in dt."""
+    from types import SimpleNamespace
+    cfg, P, s, b, v0, inv_m = _md_problem(oracle)
+    fwd = oracle.md_verlet(cfg, P, s, b, v0, inv_m, 1.0, 6)
+    x6, v6 = fwd[-1][0], fwd[-1][1]
+    b6 = SimpleNamespace(struct_off=b.struct_off, pos=x6, types=b.types, cell=b.cell)
+    back = oracle.md_verlet(cfg, P, s, b6, -v6, inv_m, 1.0, 6)
+    d = back[-1][0] - b.pos
+    for k in range(b.n_struct):  # minimum image
+        a0, a1 = b.struct_off[k], b.struct_off[k + 1]
+        H = b.cell[k]
+        f = d[a0:a1] @ np.linalg.inv(H)
+        d[a0:a1] = (f - np.round(f)) @ H
+    assert np.abs(d).max() < 1e-10
+    np.testing.assert_allclose(-back[-1][1], v0, rtol=0, atol=1e-12)
+
+    def drift(dt, n):
+        m = 1.0 / inv_m
+        e0 = oracle.forward(cfg, P, s, b)[1] + np.add.reduceat(
+            0.5 * m * (v0 * v0).sum(1) / oracle.EV_PER_A_AMU_IN_A_PER_FS2, b.struct_off[:-1])
+        out = 0.0
+        for x, v, F, Es in oracle.md_verlet(cfg, P, s, b, v0, inv_m, dt, n):
+            ke = np.add.reduceat(0.5 * m * (v * v).sum(1) / oracle.EV_PER_A_AMU_IN_A_PER_FS2, b.struct_off[:-1])
+            out = max(out, np.abs(Es + ke - e0).max())
+        return out
+    d1, d2 = drift(2.0, 10), drift(1.0, 20)
+    assert 2.8 < d1 / d2 < 5.5, (d1, d2)
