@@ -57,6 +57,9 @@ def lib():
         L.orc_cutoff.argtypes = [C.c_double, C.c_double, _dp, _dp]
         L.orc_radial_basis.argtypes = [C.c_int, C.c_double, C.c_double, _dp, _dp]
         L.orc_blm.argtypes = [_dp, _dp, _dp]
+        L.orc_blm_lmax.argtypes = [_dp, C.c_int, _dp, _dp]
+        L.orc_clm_quadrature.argtypes = [C.c_int]
+        L.orc_clm_quadrature.restype = C.c_double
         L.orc_neighbors.argtypes = [C.POINTER(_Batch), C.c_double, C.c_long, _lp, _ip, _ip]
         L.orc_neighbors.restype = C.c_long
         L.orc_descriptors.argtypes = [C.POINTER(_Cfg), _dp, C.POINTER(_Batch), _dp]
@@ -121,9 +124,19 @@ class _BatchView:
         self.n_atoms = int(self.off[-1])
 
 
-def clm() -> np.ndarray:
+def nlm(l_max: int = 4) -> int:
+    """(l, m) components for l = 1..l_max."""
+    return (l_max + 1) ** 2 - 1
+
+
+def clm(l_max: int = 4) -> np.ndarray:
     p = lib().orc_clm()
-    return np.array([p[i] for i in range(24)])
+    return np.array([p[i] for i in range(nlm(l_max))])
+
+
+def clm_quadrature(lm: int) -> float:
+    """4 pi / ((2l + 1) int B_lm^2 dOmega) by the oracle's quadrature."""
+    return lib().orc_clm_quadrature(lm)
 
 
 def chebyshev(K: int, xi: float):
@@ -144,11 +157,13 @@ def radial_basis(K: int, rc: float, r: float):
     return f, fp
 
 
-def blm(d):
+def blm(d, l_max: int = 4):
+    """B_lm (B9.1) and their gradients (B9.2) for l = 1..l_max (at most 8)."""
     d = _d(d)
-    B = np.zeros(24); dB = np.zeros(72)
-    lib().orc_blm(_p(d), _p(B), _p(dB))
-    return B, dB.reshape(24, 3)
+    n = nlm(l_max)
+    B = np.zeros(n); dB = np.zeros(3 * n)
+    lib().orc_blm_lmax(_p(d), l_max, _p(B), _p(dB))
+    return B, dB.reshape(n, 3)
 
 
 def neighbors(batch, rc: float):

@@ -59,19 +59,30 @@
 #define M_PI 3.14159265358979323846
 #endif
 
-#define NLM 24
+#define NLM 80 /* (l, m) components for l = 1..8, the stride of every per-(l, m) array */
+#define LMAX 8
 
-/* C_lm of Eq. 7 for l = 1..4, m = 0..2l in the order of App. B. */
-static const double C_LM[NLM] = {
+static int lm_first(int l) { return l * l - 1; } /* l=1 -> 0, 2 -> 3, 3 -> 8, 4 -> 15, ... */
+static int nlm_of(int l_max) { return (l_max + 1) * (l_max + 1) - 1; }
+
+/* C_lm of Eq. 7 (the paper only calls them constants): the addition-theorem
+ * normalisation sum_m C_lm B_lm(u) B_lm(v) = P_l(u.v).  For l = 1..4 the
+ * values derived from the standard real-harmonic norms, in the order of
+ * App. B; for l = 5..8 (B5-B8) each value is 4 pi / ((2l + 1) int B_lm^2 dOmega)
+ * by the quadrature of clm_quadrature() below, filled in on first use. */
+static double C_LM[NLM] = {
     1.0, 1.0, 1.0,
     0.25, 3.0, 3.0, 0.75, 0.75,
     0.25, 0.375, 0.375, 3.75, 3.75, 0.625, 0.625,
     1.0 / 64.0, 0.625, 0.625, 0.3125, 0.3125, 4.375, 4.375, 35.0 / 64.0,
     35.0 / 64.0};
+static int C_LM_ready = 0;
+static void clm_init(void);
 
-const double *orc_clm(void) { return C_LM; }
-
-static int lm_first(int l) { return l * l - 1; } /* l=1 -> 0, 2 -> 3, 3 -> 8, 4 -> 15 */
+const double *orc_clm(void) {
+  clm_init();
+  return C_LM;
+}
 
 /* ------------------------------------------------------------------ layout */
 
@@ -156,7 +167,7 @@ void orc_blm(const double *d, double *B, double *dB) {
   const double x = d[0], y = d[1], z = d[2];
   const double r2 = x * x + y * y + z * z;
   const double r = sqrt(r2);
-  double b[NLM], g[NLM][3];
+  double b[24], g[24][3];
   /* l = 1 */
   b[0] = z;                      g[0][0] = 0;     g[0][1] = 0;     g[0][2] = 1;
   b[1] = x;                      g[1][0] = 1;     g[1][1] = 0;     g[1][2] = 0;
@@ -217,13 +228,173 @@ void orc_blm(const double *d, double *B, double *dB) {
     g[23][0] = 12 * x * x * y - 4 * y * y * y; g[23][1] = 4 * x * x * x - 12 * x * y * y;
     g[23][2] = 0;
   }
-  for (int lm = 0; lm < NLM; ++lm) {
+  for (int lm = 0; lm < 24; ++lm) {
     int l = lm < 3 ? 1 : lm < 8 ? 2 : lm < 15 ? 3 : 4;
     double rl = pow(r, l);
     B[lm] = b[lm] / rl;
     for (int c = 0; c < 3; ++c)
       dB[lm * 3 + c] = g[lm][c] / rl - l * b[lm] * d[c] / (rl * r2);
   }
+}
+
+/* B5.1-B8.17 as printed.  Every printed form is a product of a polynomial in
+ * z and r^2, sum_k zc[k] z^(zdeg - 2k) r^(2k), and a polynomial in x and y,
+ * sum_j xyc[j] x^xp[j] y^yp[j]; the table holds the two factors as printed. */
+typedef struct {
+  int zdeg;
+  double zc[5];
+  int nxy;
+  double xyc[5];
+  int xp[5], yp[5];
+} printed_form;
+
+#define XY1 1, {1}, {0}, {0}
+#define XY_X 1, {1}, {1}, {0}
+#define XY_Y 1, {1}, {0}, {1}
+#define XY_C2 2, {1, -1}, {2, 0}, {0, 2}               /* x^2 - y^2 */
+#define XY_S2 1, {2}, {1}, {1}                          /* 2xy */
+#define XY_C3 2, {1, -3}, {3, 1}, {0, 2}               /* x^3 - 3xy^2 */
+#define XY_S3 2, {3, -1}, {2, 0}, {1, 3}               /* 3x^2y - y^3 */
+#define XY_C4 3, {1, -6, 1}, {4, 2, 0}, {0, 2, 4}      /* x^4 - 6x^2y^2 + y^4 */
+#define XY_S4 2, {4, -4}, {3, 1}, {1, 3}               /* 4x^3y - 4xy^3 */
+#define XY_C5 3, {1, -10, 5}, {5, 3, 1}, {0, 2, 4}     /* x^5 - 10x^3y^2 + 5xy^4 */
+#define XY_S5 3, {5, -10, 1}, {4, 2, 0}, {1, 3, 5}     /* 5x^4y - 10x^2y^3 + y^5 */
+#define XY_C6 4, {1, -15, 15, -1}, {6, 4, 2, 0}, {0, 2, 4, 6}
+#define XY_S6 3, {6, -20, 6}, {5, 3, 1}, {1, 3, 5}
+#define XY_C7 4, {1, -21, 35, -7}, {7, 5, 3, 1}, {0, 2, 4, 6}
+#define XY_S7 4, {7, -35, 21, -1}, {6, 4, 2, 0}, {1, 3, 5, 7}
+#define XY_C8 5, {1, -28, 70, -28, 1}, {8, 6, 4, 2, 0}, {0, 2, 4, 6, 8}
+#define XY_S8 4, {8, -56, 56, -8}, {7, 5, 3, 1}, {1, 3, 5, 7}
+
+static const printed_form FORMS_5_8[56] = {
+    /* l = 5: B5.1-B5.11 */
+    {5, {63, -70, 15}, XY1},    {4, {21, -14, 1}, XY_X},  {4, {21, -14, 1}, XY_Y},
+    {3, {3, -1}, XY_C2},        {3, {3, -1}, XY_S2},      {2, {9, -1}, XY_C3},
+    {2, {9, -1}, XY_S3},        {1, {1}, XY_C4},          {1, {1}, XY_S4},
+    {0, {1}, XY_C5},            {0, {1}, XY_S5},
+    /* l = 6: B6.1-B6.13 */
+    {6, {231, -315, 105, -5}, XY1}, {5, {33, -30, 5}, XY_X}, {5, {33, -30, 5}, XY_Y},
+    {4, {33, -18, 1}, XY_C2},   {4, {33, -18, 1}, XY_S2}, {3, {11, -3}, XY_C3},
+    {3, {11, -3}, XY_S3},       {2, {11, -1}, XY_C4},     {2, {11, -1}, XY_S4},
+    {1, {1}, XY_C5},            {1, {1}, XY_S5},          {0, {1}, XY_C6},
+    {0, {1}, XY_S6},
+    /* l = 7: B7.1-B7.15 */
+    {7, {429, -693, 315, -35}, XY1}, {6, {429, -495, 135, -5}, XY_X},
+    {6, {429, -495, 135, -5}, XY_Y}, {5, {143, -110, 15}, XY_C2}, {5, {143, -110, 15}, XY_S2},
+    {4, {143, -66, 3}, XY_C3},  {4, {143, -66, 3}, XY_S3}, {3, {13, -3}, XY_C4},
+    {3, {13, -3}, XY_S4},       {2, {13, -1}, XY_C5},     {2, {13, -1}, XY_S5},
+    {1, {1}, XY_C6},            {1, {1}, XY_S6},          {0, {1}, XY_C7},
+    {0, {1}, XY_S7},
+    /* l = 8: B8.1-B8.17 */
+    {8, {6435, -12012, 6930, -1260, 35}, XY1}, {7, {715, -1001, 385, -35}, XY_X},
+    {7, {715, -1001, 385, -35}, XY_Y}, {6, {143, -143, 33, -1}, XY_C2},
+    {6, {143, -143, 33, -1}, XY_S2}, {5, {39, -26, 3}, XY_C3}, {5, {39, -26, 3}, XY_S3},
+    {4, {65, -26, 1}, XY_C4},   {4, {65, -26, 1}, XY_S4}, {3, {5, -1}, XY_C5},
+    {3, {5, -1}, XY_S5},        {2, {15, -1}, XY_C6},     {2, {15, -1}, XY_S6},
+    {1, {1}, XY_C7},            {1, {1}, XY_S7},          {0, {1}, XY_C8},
+    {0, {1}, XY_S8}};
+
+static double ipow(double a, int k) {
+  double r = 1.0;
+  for (int i = 0; i < k; ++i) r *= a;
+  return r;
+}
+
+/* b = Z(z, r^2) XY(x, y) of one printed form and its Cartesian gradient,
+ * each monomial differentiated by hand (d r^2 / d x_c = 2 x_c). */
+static void printed_eval(const printed_form *f, const double *d, double *b, double *g) {
+  const double x = d[0], y = d[1], z = d[2], R = x * x + y * y + z * z;
+  double Z = 0, Zr = 0, Zz = 0; /* Z, dZ/d(r^2), partial dZ/dz at fixed r^2 */
+  for (int k = 0; 2 * k <= f->zdeg; ++k) {
+    const int a = f->zdeg - 2 * k;
+    Z += f->zc[k] * ipow(z, a) * ipow(R, k);
+    if (k > 0) Zr += f->zc[k] * ipow(z, a) * k * ipow(R, k - 1);
+    if (a > 0) Zz += f->zc[k] * a * ipow(z, a - 1) * ipow(R, k);
+  }
+  double P = 0, Px = 0, Py = 0;
+  for (int j = 0; j < f->nxy; ++j) {
+    const int p = f->xp[j], q = f->yp[j];
+    P += f->xyc[j] * ipow(x, p) * ipow(y, q);
+    if (p > 0) Px += f->xyc[j] * p * ipow(x, p - 1) * ipow(y, q);
+    if (q > 0) Py += f->xyc[j] * q * ipow(x, p) * ipow(y, q - 1);
+  }
+  *b = Z * P;
+  g[0] = 2 * x * Zr * P + Z * Px;
+  g[1] = 2 * y * Zr * P + Z * Py;
+  g[2] = (Zz + 2 * z * Zr) * P;
+}
+
+/* B_lm and grad B_lm (B9.1, B9.2) for l = 1..l_max (at most 8): B1-B4 by
+ * orc_blm, B5-B8 from the printed forms.  B is [nlm], dB [nlm][3] with
+ * nlm = (l_max + 1)^2 - 1. */
+void orc_blm_lmax(const double *d, int l_max, double *B, double *dB) {
+  orc_blm(d, B, dB);
+  if (l_max <= 4) return;
+  const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+  const double r = sqrt(r2);
+  for (int lm = 24; lm < nlm_of(l_max); ++lm) {
+    int l = 5;
+    while (lm >= lm_first(l + 1)) ++l;
+    double b, g[3];
+    printed_eval(&FORMS_5_8[lm - 24], d, &b, g);
+    const double rl = pow(r, l);
+    B[lm] = b / rl;
+    for (int c = 0; c < 3; ++c) dB[lm * 3 + c] = g[c] / rl - l * b * d[c] / (rl * r2);
+  }
+}
+
+/* Gauss-Legendre nodes and weights on [-1, 1] (n points, exact for
+ * polynomials of degree 2n - 1): Newton's method on P_n from the three-term
+ * recurrence, started at the Chebyshev-like guess cos(pi (i + 3/4) / (n + 1/2)). */
+static void gauss_legendre(int n, double *xs, double *ws) {
+  for (int i = 0; i < n; ++i) {
+    double t = cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = t;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (t * p1 - p0) / (t * t - 1.0);
+      const double dt = p1 / dp;
+      t -= dt;
+      if (fabs(dt) < 1e-16) break;
+    }
+    xs[i] = t;
+    ws[i] = 2.0 / ((1.0 - t * t) * dp * dp);
+  }
+}
+
+/* 4 pi / ((2l + 1) int B_lm^2 dOmega) over the unit sphere: 12 Gauss-Legendre
+ * nodes in z = cos(theta) (exact to degree 23) times 36 equal steps in phi
+ * (exact for trigonometric polynomials below degree 36); B_lm^2 has degree
+ * 2l <= 16 in both. */
+static double clm_quadrature(int lm, int l) {
+  double xs[12], ws[12], acc = 0.0;
+  gauss_legendre(12, xs, ws);
+  for (int i = 0; i < 12; ++i)
+    for (int j = 0; j < 36; ++j) {
+      const double ph = 2.0 * M_PI * j / 36.0, st = sqrt(1.0 - xs[i] * xs[i]);
+      const double u[3] = {st * cos(ph), st * sin(ph), xs[i]};
+      double B[NLM], dB[NLM * 3];
+      orc_blm_lmax(u, l, B, dB);
+      acc += ws[i] * (2.0 * M_PI / 36.0) * B[lm] * B[lm];
+    }
+  return 4.0 * M_PI / ((2.0 * l + 1.0) * acc);
+}
+
+double orc_clm_quadrature(int lm) {
+  int l = 1;
+  while (lm >= lm_first(l + 1)) ++l;
+  return clm_quadrature(lm, l);
+}
+
+static void clm_init(void) {
+  if (C_LM_ready) return;
+  for (int l = 5; l <= LMAX; ++l)
+    for (int m = 0; m <= 2 * l; ++m) C_LM[lm_first(l) + m] = clm_quadrature(lm_first(l) + m, l);
+  C_LM_ready = 1;
 }
 
 /* A(u) = (3 u u^T - I)/2 and dA_ab/dd_c for the 4-body reading. */
@@ -431,6 +602,7 @@ static void free_atoms(oatoms *A) {
 /* Eqs. 5-8 (and the 4-body reading) for atom i of a structure. */
 static void atom_descriptors(const orc_cfg *c, const double *P, const int *type,
                              int i, const olist *LR, const olist *LA, oatom *t) {
+  clm_init();
   int I = type[i];
   double f[64], fp[64];
   t->type = I;
@@ -450,16 +622,16 @@ static void atom_descriptors(const orc_cfg *c, const double *P, const int *type,
     int J = type[p->j];
     double B[NLM], dB[NLM * 3], A[9], dA[27];
     orc_radial_basis(c->k_a, c->rc_a, p->r, f, fp);
-    orc_blm(p->d, B, dB);
+    orc_blm_lmax(p->d, c->l_max, B, dB);
     quad_tensor(p->d, p->r, A, dA);
     for (int n = 0; n < c->nq_a; ++n) {
       double g = 0; /* Eq. 6 with c^A */
       for (int k = 0; k < c->k_a; ++k) g += P[off_cA(c, I, J, n, k)] * f[k];
-      for (int lm = 0; lm < NLM; ++lm) t->S[n * NLM + lm] += g * B[lm]; /* Eq. 8 */
+      for (int lm = 0; lm < nlm_of(c->l_max); ++lm) t->S[n * NLM + lm] += g * B[lm]; /* Eq. 8 */
       for (int ab = 0; ab < 9; ++ab) t->Q[n * 9 + ab] += g * A[ab];
     }
     for (int k = 0; k < c->k_a; ++k) {
-      for (int lm = 0; lm < NLM; ++lm)
+      for (int lm = 0; lm < nlm_of(c->l_max); ++lm)
         t->SA[(J * c->k_a + k) * NLM + lm] += f[k] * B[lm];
       for (int ab = 0; ab < 9; ++ab) t->QA[(J * c->k_a + k) * 9 + ab] += f[k] * A[ab];
     }
@@ -536,6 +708,7 @@ typedef struct {
 
 static void pair_dG(const orc_cfg *c, const double *P, const oatom *t, int L,
                     const opair *p, int J, double *dG, pairwork *w) {
+  clm_init();
   int d = orc_num_des(c), I = t->type;
   for (int q = 0; q < 3 * d; ++q) dG[q] = 0;
   for (int x = 0; x < 3; ++x) w->u[x] = p->d[x] / p->r;
@@ -549,7 +722,7 @@ static void pair_dG(const orc_cfg *c, const double *P, const oatom *t, int L,
     return;
   }
   orc_radial_basis(c->k_a, c->rc_a, p->r, w->f, w->fp);
-  orc_blm(p->d, w->B, w->dB);
+  orc_blm_lmax(p->d, c->l_max, w->B, w->dB);
   quad_tensor(p->d, p->r, w->A, w->dA);
   for (int n = 0; n < c->nq_a; ++n) {
     double g = 0, gp = 0;
@@ -557,7 +730,7 @@ static void pair_dG(const orc_cfg *c, const double *P, const oatom *t, int L,
       g += P[off_cA(c, I, J, n, k)] * w->f[k];
       gp += P[off_cA(c, I, J, n, k)] * w->fp[k];
     }
-    for (int lm = 0; lm < NLM; ++lm)
+    for (int lm = 0; lm < nlm_of(c->l_max); ++lm)
       for (int x = 0; x < 3; ++x) /* C2.3 */
         w->dS[(n * NLM + lm) * 3 + x] = g * w->dB[lm * 3 + x] + gp * w->u[x] * w->B[lm];
     for (int l = 1; l <= c->l_max; ++l)
@@ -759,6 +932,7 @@ int orc_loss(const orc_cfg *c, const double *params, const double *scale,
 /* dE_i/dtheta: D1.7-D1.10 for the network, C3.5 (with C1.3, C2.5, C2.8) for c. */
 static void energy_jacobian(const orc_cfg *c, const double *P, const oatom *t,
                             double *gE /* [N_par], accumulated */) {
+  clm_init();
   int d = orc_num_des(c), H = c->hidden, e = t->type, I = t->type;
   const double *w1 = P + off_w1(c, e);
   for (int mu = 0; mu < H; ++mu) {
@@ -804,6 +978,7 @@ static void energy_jacobian(const orc_cfg *c, const double *P, const oatom *t,
 static void pair_jacobian(const orc_cfg *c, const double *P, const double *scale,
                           const oatom *t, int L, const opair *p, int typej,
                           double *J, double *dG, double *h, pairwork *w) {
+  clm_init();
   int d = orc_num_des(c), H = c->hidden, e = t->type, I = t->type;
   pair_dG(c, P, t, L, p, typej, dG, w);
   const double *W0 = P + off_W0(c, e), *w1 = P + off_w1(c, e);
@@ -859,7 +1034,7 @@ static void pair_jacobian(const orc_cfg *c, const double *P, const double *scale
       for (int k = 0; k < c->k_a; ++k) {
         const double *SA = t->SA + (Jp * c->k_a + k) * NLM;
         const double *QA = t->QA + (Jp * c->k_a + k) * 9;
-        double dGdc[8]; /* dq_nl/dc for l = 1..4, C2.5 with C2.8 */
+        double dGdc[LMAX + 1]; /* dq_nl/dc for l = 1..l_max, C2.5 with C2.8 */
         for (int l = 1; l <= c->l_max; ++l) {
           double s = 0;
           for (int m = 0; m <= 2 * l; ++m) {

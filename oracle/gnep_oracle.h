@@ -50,6 +50,11 @@ void orc_chebyshev(int K, double xi, double *T, double *dT);
 void orc_cutoff(double rc, double r, double *fc, double *fcp);
 void orc_radial_basis(int K, double rc, double r, double *f, double *fp);
 void orc_blm(const double *d, double *B, double *dB);
+/* B_lm and grad B_lm for l = 1..l_max (l_max <= 8; B5-B8 from the printed
+ * forms); B [nlm], dB [nlm][3], nlm = (l_max + 1)^2 - 1. */
+void orc_blm_lmax(const double *d, int l_max, double *B, double *dB);
+/* 4 pi / ((2l + 1) int B_lm^2 dOmega) by quadrature, for component lm. */
+double orc_clm_quadrature(int lm);
 
 long orc_neighbors(const orc_batch *b, double rc, long cap, long *off,
                    int *nbr_j, int *nbr_shift);

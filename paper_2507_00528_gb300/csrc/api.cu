@@ -76,14 +76,13 @@ int alloc_workspace(gnep_model* m, gnep_nlist* nl) {
   const size_t N = nl->n_atoms > 0 ? nl->n_atoms : 1, S = nl->n_struct;
   // pair-sized buffers get headroom so that rebuilds with a few more pairs (MD) do not reallocate
   const size_t PR = nl->L[0].n + nl->L[0].n / 8 + 64, PA = nl->L[1].n + nl->L[1].n / 8 + 64;
-  const size_t D = s.ndes, A24 = (size_t)s.nqa * 24, FRn = (size_t)s.ns * s.kr;
-  const size_t HPad = (size_t)hidden_pad(s.H);  // row pitch of the hidden activations
+  const size_t D = s.ndes, A24 = (size_t)s.nqa * ((s.lmax + 1) * (s.lmax + 1) - 1), FRn = (size_t)s.ns * s.kr;
   struct Item { void** p; size_t bytes; };
   Workspace& w = nl->ws;
   w.red_len = loss_partial_doubles(nl->n_struct);
   const size_t NC = (size_t)(m->n_params - (int64_t)s.ns * m->net_size);
   std::vector<Item> items = {
-      {(void**)&w.G, 4 * N * D},        {(void**)&w.Ep, 4 * N * D},       {(void**)&w.X, 4 * N * HPad},
+      {(void**)&w.G, 4 * N * D},        {(void**)&w.Ep, 4 * N * D},
       {(void**)&w.Eatom, 4 * N},        {(void**)&w.S, 4 * N * A24},      {(void**)&w.FR, 4 * N * FRn},
       {(void**)&w.chat, 4 * N * FRn},   {(void**)&w.dA, 16 * PA},         {(void**)&w.F, 12 * N},
       {(void**)&w.Wat, 24 * N},         {(void**)&w.Es, 8 * S},           {(void**)&w.Ws, 48 * S},
@@ -129,7 +128,7 @@ int gnep_create(gnep_model** out, int n_species, const int* species_z, double rc
   *out = nullptr;
   if (n_species < 1 || n_species > 8 || !(rc_radial > 0) || !(rc_angular > 0) || rc_angular > rc_radial ||
       n_max_radial < 0 || n_max_angular < 0 || basis_radial < 0 || basis_angular < 0 || l_max < 1 ||
-      l_max > 4 || hidden < 1 || hidden > kMaxHidden || precision < 0 || precision > 2)
+      l_max > 8 || hidden < 1 || hidden > kMaxHidden || precision < 0 || precision > 2)
     return set_error(GNEP_ERR_INVALID_ARG, "hyper-parameter out of range");
   Shape s;
   s.ns = n_species; s.nqr = n_max_radial + 1; s.kr = basis_radial + 1; s.nqa = n_max_angular + 1;
@@ -137,10 +136,13 @@ int gnep_create(gnep_model** out, int n_species, const int* species_z, double rc
   s.ndes = s.nqr + s.nqa * s.lmax + (s.fb ? s.nqa : 0);
   if (!shape_supported(s))
     return set_error(GNEP_ERR_UNSUPPORTED,
-                     "no compiled kernel for this shape (built: 2 species, l_max 4, n_max/basis 4/8 without "
-                     "4-body or 8/12 with or without 4-body)");
+                     "no compiled kernel for this shape (built: 2 species; l_max 4 with n_max/basis 4/8 without "
+                     "4-body or 8/12 with or without 4-body; n_max/basis 4/8 with l_max 6 without 4-body or "
+                     "l_max 8 with 4-body)");
   if (precision != GNEP_PREC_FP32 && hidden > kMaxHiddenTc)
     return set_error(GNEP_ERR_UNSUPPORTED, "TF32/BF16 network tiles hold at most 112 hidden neurons");
+  if (precision != GNEP_PREC_FP32 && l_max > 4)
+    return set_error(GNEP_ERR_UNSUPPORTED, "l_max > 4 runs the FP32 network only");
   gnep_model* m = new gnep_model();
   m->shape = s;
   m->rcr = rc_radial;
@@ -200,6 +202,8 @@ int gnep_set_precision(gnep_model* m, int precision) {
   if (!m || precision < 0 || precision > 2) return set_error(GNEP_ERR_INVALID_ARG, "bad precision");
   if (precision != GNEP_PREC_FP32 && m->shape.H > kMaxHiddenTc)
     return set_error(GNEP_ERR_UNSUPPORTED, "TF32/BF16 network tiles hold at most 112 hidden neurons");
+  if (precision != GNEP_PREC_FP32 && m->shape.lmax > 4)
+    return set_error(GNEP_ERR_UNSUPPORTED, "l_max > 4 runs the FP32 network only");
   m->precision = precision;
   return GNEP_OK;
 }

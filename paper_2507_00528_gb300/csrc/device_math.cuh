@@ -129,6 +129,57 @@ __device__ __forceinline__ void harmonics_grad(float x, float y, float z, float 
   }
 }
 
+// Harmonics on the unit vector u and, for a direction w, the directional
+// derivatives D_lm = grad_d B_lm . w (B9.2).  Each B_lm is the degree-l
+// homogeneous polynomial h_lm (the r = 1 forms with 1 read as r^2) on u, so
+// grad_d B_lm = (grad h_lm(u) - l h_lm(u) u) / r (Euler's relation u . grad h =
+// l h removes the radial part), and grad h_lm(u) . w is the derivative of h_lm
+// along w, evaluated here with dx = w_x, dy = w_y, dz = w_z, d(r^2) = 2 u . w.
+__device__ __forceinline__ void harmonics_dir(float x, float y, float z, float rinv, float wx, float wy, float wz,
+                                              float (&B)[NLM], float (&Dd)[NLM]) {
+  harmonics(x, y, z, B);
+  const float ru = x * wx + y * wy + z * wz;  // u . w; d(r^2) = 2 ru
+  const float x2 = x * x, y2 = y * y, z2 = z * z;
+  const float dx2 = 2.f * x * wx, dy2 = 2.f * y * wy, dz2 = 2.f * z * wz, dr2 = 2.f * ru;
+  float d[NLM];
+  // l = 1
+  d[0] = wz; d[1] = wx; d[2] = wy;
+  // l = 2
+  d[3] = 3.f * dz2 - dr2;
+  d[4] = wx * z + x * wz;
+  d[5] = wy * z + y * wz;
+  d[6] = dx2 - dy2;
+  d[7] = 2.f * (wx * y + x * wy);
+  // l = 3: p3 = 5 z^2 - r^2
+  const float p3 = 5.f * z2 - 1.f, dp3 = 5.f * dz2 - dr2;
+  d[8] = (5.f * dz2 - 3.f * dr2) * z + (5.f * z2 - 3.f) * wz;
+  d[9] = dp3 * x + p3 * wx;
+  d[10] = dp3 * y + p3 * wy;
+  const float xmy = x2 - y2, dxmy = dx2 - dy2;
+  d[11] = dxmy * z + xmy * wz;
+  d[12] = 2.f * ((wx * y + x * wy) * z + x * y * wz);
+  const float a13 = x2 - 3.f * y2, da13 = dx2 - 3.f * dy2;
+  const float a14 = 3.f * x2 - y2, da14 = 3.f * dx2 - dy2;
+  d[13] = da13 * x + a13 * wx;
+  d[14] = da14 * y + a14 * wy;
+  // l = 4: w4 = (7 z^2 - 3 r^2) z, p4 = 7 z^2 - r^2
+  const float w4 = (7.f * z2 - 3.f) * z, dw4 = (7.f * dz2 - 3.f * dr2) * z + (7.f * z2 - 3.f) * wz;
+  const float p4 = 7.f * z2 - 1.f, dp4 = 7.f * dz2 - dr2;
+  d[15] = 35.f * 2.f * z2 * dz2 - 30.f * (dz2 + z2 * dr2) + 3.f * 2.f * dr2;
+  d[16] = dw4 * x + w4 * wx;
+  d[17] = dw4 * y + w4 * wy;
+  d[18] = dp4 * xmy + p4 * dxmy;
+  const float xy = x * y, dxy = wx * y + x * wy;
+  d[19] = 2.f * (dp4 * xy + p4 * dxy);
+  d[20] = da13 * x * z + a13 * (wx * z + x * wz);
+  d[21] = da14 * y * z + a14 * (wy * z + y * wz);
+  d[22] = 2.f * x2 * dx2 - 6.f * (dx2 * y2 + x2 * dy2) + 2.f * y2 * dy2;
+  d[23] = 4.f * (dxy * xmy + xy * dxmy);
+#pragma unroll
+  for (int q = 0; q < NLM; ++q) Dd[q] = (d[q] - (float)lm_l(q) * B[q] * ru) * rinv;
+}
+
+
 // 4-body invariant q4 = tr(Q^3) with Q = sum_j g (3 u u^T - I)/2, written in the
 // l = 2 moments S_2m (m = 0..4, i.e. lm = 3..7):
 //   Q_zz = S0/2, Q_xz = 3 S1/2, Q_yz = 3 S2/2, Q_xy = 3 S4/4,

@@ -48,7 +48,7 @@ struct PairList {
 
 // Per-step device workspace of one batch (sized at build, reused every step).
 struct Workspace {
-  float *G = nullptr, *Ep = nullptr, *X = nullptr, *Eatom = nullptr;
+  float *G = nullptr, *Ep = nullptr, *Eatom = nullptr;
   float *S = nullptr, *FR = nullptr, *chat = nullptr;
   float4* dA = nullptr;
   float *F = nullptr, *Wat = nullptr;

@@ -1,15 +1,28 @@
-// Per-element one-hidden-layer network (D1.1-D1.10) on species-homogeneous
-// tiles of 32 atoms.  The contractions are register-blocked FP32 tile GEMMs
-// from shared memory; persistent blocks keep one species' weights resident and
-// walk the tiles of the species-grouped atom order.  The network-parameter
-// gradient (D1.18-D1.21 through the tangent/reverse pass) is accumulated in
-// registers and written once per block and species.  Every sum runs in a fixed
-// order (no atomics), so results are bit-reproducible.
+// Per-element one-hidden-layer network (D1.1-D1.10) in FP32 on the CUDA
+// cores, and its tangent/reverse pass (D1.18-D1.21 through the tangent/adjoint
+// route), over species-homogeneous tiles of 128 atoms of the species-grouped
+// atom order.  Persistent blocks keep one species' weights in shared memory
+// and walk the tiles.  Every sum runs in a fixed order (no atomics), so results
+// are bit-reproducible.
 //
-// Tile GEMM layout: C[m][n] = sum_k A[k][m] B[k][n] with A, B k-major in shared
-// memory; thread t owns the 4x4 block (m0, n0) with m0 = 4 (t mod 8) and
-// n0 = 4 (t div 8), so the 8 threads sharing n0 read 128 contiguous bytes of A
-// and write transposed results as conflict-free 16-byte stores.
+// Thread map: 256 threads, two per atom.  Lanes l and l ^ 16 of warp w take
+// atom 16 w + (l mod 16) and the two halves of the hidden units, so that each
+// thread's descriptor row (and, backward, its tangent row and the adjoint it
+// accumulates) lives in registers while the weight row of hidden unit mu is
+// read by 16-byte loads that the lanes of a half-warp share (one shared-memory
+// wavefront per load for the whole half).  For each mu a thread forms
+// z = W0_mu . (s.G) (interleaved partial sums), the element-wise terms and then
+// the rank-one update of E' (forward) or Gbar (backward) with the same row.
+// The hidden activations are recomputed in the backward pass instead of being
+// stored.  The halves are combined by one exchange between lanes l and l ^ 16
+// (commutative, so both lanes hold the same sum).
+//
+// The weight gradient dW0 += alpha^T (s.G) - beta^T (s.Gdot) contracts over the
+// tile's atoms: after the per-atom phase alpha and -beta are in shared memory
+// and each thread accumulates 4 x 4 blocks of dW0 in registers across all
+// tiles of one species, from four 16-byte loads per atom (alpha, -beta, s.G,
+// s.Gdot).  db0 and dw1 are sums over atoms formed by shuffles within each
+// half-warp and kept per warp in shared memory.
 #include <cstdio>
 
 #include "gnep_internal.h"
@@ -19,381 +32,388 @@ namespace gnep {
 
 namespace {
 
-constexpr int TM = kTileAtoms;  // atoms per tile (32)
-constexpr int NT = 128;         // threads per block
-constexpr int MB = TM / 4;      // m-blocks per tile (8)
+constexpr int TA = 128;  // atoms per tile
+constexpr int NT = 256;  // threads per block (two per atom)
+constexpr int NW = NT / 32;
 
 __device__ __forceinline__ void tile_of(const Tiles& T, int t, int& e, int& a0, int& na) {
   e = 0;
   while (e + 1 < T.ns && t >= T.tbase[e + 1]) ++e;
-  a0 = T.soff[e] + (t - T.tbase[e]) * TM;
-  na = min(TM, T.soff[e + 1] - a0);
+  a0 = T.soff[e] + (t - T.tbase[e]) * TA;
+  na = min(TA, T.soff[e + 1] - a0);
 }
 
-// Blocks of a TM x NP product: thread t handles blocks t, t + NT, ...
-template <int NP, int K, int LDA, int LDB, class F>
-__device__ __forceinline__ void tile_gemm(const float* A, const float* B, F f) {
-  constexpr int NB = MB * (NP / 4);
-  for (int blk = threadIdx.x; blk < NB; blk += NT) {
-    const int m0 = (blk % MB) * 4, n0 = (blk / MB) * 4;
-    float acc[4][4] = {};
-#pragma unroll 4
-    for (int k = 0; k < K; ++k) {
-      const float4 a = *reinterpret_cast<const float4*>(A + k * LDA + m0);
-      const float4 b = *reinterpret_cast<const float4*>(B + k * LDB + n0);
-      const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int w = 0; w < 4; ++w) acc[u][w] = fmaf(av[u], bv[w], acc[u][w]);
-    }
-    f(m0, n0, acc);
-  }
-}
+// Row widths: descriptor rows padded to 16 bytes; hidden units padded to an
+// even count (the two halves take the same number of units; the padding unit
+// has zero weights) and the alpha / beta rows to a multiple of 4.
+template <int D>
+struct RowW {
+  static constexpr int DW = (D + 3) / 4 * 4;
+};
+__host__ __device__ inline int h_even(int H) { return (H + 1) / 2 * 2; }
+__host__ __device__ inline int h_row(int H) { return (h_even(H) + 3) / 4 * 4; }
 
-// Weights of species e, zero-padded: W0t [DP][HP] (for z = G W0^T) and
-// W0n [HP][DP] (for E' = beta W0), b0 and w1 [HP].
-template <int D, int DP, int HP>
-__device__ void load_weights(const DevModel& dm, int e, float* W0t, float* W0n, float* b0, float* w1) {
+// Weights of species e: W [H2][DW] (row mu = W0_mu, zero beyond D and H),
+// b0, w1 [H2] (zero beyond H).
+template <int D>
+__device__ void load_weights(const DevModel& dm, int e, float* W, float* b0, float* w1) {
+  constexpr int DW = RowW<D>::DW;
   const float* P = dm.params + (size_t)e * dm.net_size;
-  const int H = dm.H;
-  for (int q = threadIdx.x; q < DP * HP; q += NT) {  // W0n row-major, coalesced reads
-    const int mu = q / DP, v = q % DP;
-    W0n[q] = (v < D && mu < H) ? P[mu * D + v] : 0.f;
+  const int H = dm.H, H2 = h_even(H);
+  for (int q = threadIdx.x; q < H2 * DW; q += NT) {
+    const int mu = q / DW, v = q % DW;
+    W[q] = (v < D && mu < H) ? P[mu * D + v] : 0.f;
   }
-  __syncthreads();
-  for (int q = threadIdx.x; q < DP * HP; q += NT) {  // W0t from W0n
-    const int v = q / HP, mu = q % HP;
-    W0t[q] = W0n[mu * DP + v];
-  }
-  for (int mu = threadIdx.x; mu < HP; mu += NT) {
+  for (int mu = threadIdx.x; mu < H2; mu += NT) {
     b0[mu] = mu < H ? P[D * H + mu] : 0.f;
     w1[mu] = mu < H ? P[D * H + H + mu] : 0.f;
   }
 }
 
-// Stage rows of a per-atom array (row stride D) into A[k][a] (k-major), zero-padded.
-template <int D, int DP>
-__device__ __forceinline__ void stage_kmajor(const float* __restrict__ src, const int* rows, const float* scale,
-                                             float* dst) {
-  for (int q = threadIdx.x; q < DP * TM; q += NT) {
-    const int v = q / TM, a = q % TM, r = rows[a];
-    dst[q] = (r >= 0 && v < D) ? scale[v] * src[(size_t)r * D + v] : 0.f;
+// Scaled rows s.src of the tile's atoms into R [TA][DW] (zero padding), for
+// NA arrays at once: every thread issues all of its gathered loads before the
+// first store, so that a tile waits for one global-memory latency, not one per
+// element.
+template <int D, int NA>
+__device__ __forceinline__ void stage_rows(const float* __restrict__ s0, const float* __restrict__ s1,
+                                           const int* rows, const float* sc, float* R0, float* R1) {
+  constexpr int DW = RowW<D>::DW, N = TA * DW, IT = (N + NT - 1) / NT;
+  float x[NA][IT];
+#pragma unroll
+  for (int k = 0; k < IT; ++k) {
+    const int q = threadIdx.x + k * NT, a = q / DW, v = q % DW;
+    const int r = q < N ? rows[a] : -1;
+    const bool in = r >= 0 && v < D;
+    x[0][k] = in ? __ldg(s0 + (size_t)r * D + v) : 0.f;
+    if constexpr (NA > 1) x[NA - 1][k] = in ? __ldg(s1 + (size_t)r * D + v) : 0.f;
+  }
+#pragma unroll
+  for (int k = 0; k < IT; ++k) {
+    const int q = threadIdx.x + k * NT;
+    if (q < N) {
+      const float c = sc[q % DW];
+      R0[q] = c * x[0][k];
+      if constexpr (NA > 1) R1[q] = c * x[NA - 1][k];
+    }
   }
 }
 
-// Stage rows into R[a][DP] (atom-major), zero-padded.
-template <int D, int DP>
-__device__ __forceinline__ void stage_rows(const float* __restrict__ src, const int* rows, const float* scale,
-                                           float* dst) {
-  for (int q = threadIdx.x; q < DP * TM; q += NT) {
-    const int a = q / DP, v = q % DP, r = rows[a];
-    dst[q] = (r >= 0 && v < D) ? scale[v] * src[(size_t)r * D + v] : 0.f;
+template <int DW>
+__device__ __forceinline__ void load_row(const float* R, float (&x)[DW]) {
+#pragma unroll
+  for (int v4 = 0; v4 < DW / 4; ++v4) {
+    const float4 t = reinterpret_cast<const float4*>(R)[v4];
+    x[4 * v4] = t.x; x[4 * v4 + 1] = t.y; x[4 * v4 + 2] = t.z; x[4 * v4 + 3] = t.w;
+  }
+}
+
+// Dot product of a register row with a shared-memory weight row, four chains.
+template <int DW>
+__device__ __forceinline__ float dot_row(const float (&x)[DW], const float4* w, float init) {
+  float s0 = init, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll
+  for (int v4 = 0; v4 < DW / 4; ++v4) {
+    const float4 t = w[v4];
+    s0 = fmaf(x[4 * v4], t.x, s0);
+    s1 = fmaf(x[4 * v4 + 1], t.y, s1);
+    s2 = fmaf(x[4 * v4 + 2], t.z, s2);
+    s3 = fmaf(x[4 * v4 + 3], t.w, s3);
+  }
+  return (s0 + s1) + (s2 + s3);
+}
+
+// Two dot products with the same weight row, two chains each.
+template <int DW>
+__device__ __forceinline__ void dot_row2(const float (&x)[DW], const float (&y)[DW], const float4* w, float init,
+                                         float& zx, float& zy) {
+  float a0 = init, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+#pragma unroll
+  for (int v4 = 0; v4 < DW / 4; ++v4) {
+    const float4 t = w[v4];
+    a0 = fmaf(x[4 * v4], t.x, a0);
+    a1 = fmaf(x[4 * v4 + 1], t.y, a1);
+    a0 = fmaf(x[4 * v4 + 2], t.z, a0);
+    a1 = fmaf(x[4 * v4 + 3], t.w, a1);
+    b0 = fmaf(y[4 * v4], t.x, b0);
+    b1 = fmaf(y[4 * v4 + 1], t.y, b1);
+    b0 = fmaf(y[4 * v4 + 2], t.z, b0);
+    b1 = fmaf(y[4 * v4 + 3], t.w, b1);
+  }
+  zx = a0 + a1;
+  zy = b0 + b1;
+}
+
+// acc += c * (weight row)
+template <int DW>
+__device__ __forceinline__ void axpy_row(float (&acc)[DW], float c, const float4* w) {
+#pragma unroll
+  for (int v4 = 0; v4 < DW / 4; ++v4) {
+    const float4 t = w[v4];
+    acc[4 * v4] = fmaf(c, t.x, acc[4 * v4]);
+    acc[4 * v4 + 1] = fmaf(c, t.y, acc[4 * v4 + 1]);
+    acc[4 * v4 + 2] = fmaf(c, t.z, acc[4 * v4 + 2]);
+    acc[4 * v4 + 3] = fmaf(c, t.w, acc[4 * v4 + 3]);
   }
 }
 
 }  // namespace
 
-template <int D, int HP, int NS, int NQR, int KR>
-size_t mlp_fwd_smem() {
-  constexpr int DP = (D + 3) / 4 * 4;
-  return sizeof(float) * (2 * DP * HP + 2 * HP + DP * TM + HP * TM + (HP / 4) * TM + NS * NQR * KR);
+template <int D, int NS, int NQR, int KR>
+size_t mlp_fwd_smem(int H) {
+  constexpr int DW = RowW<D>::DW;
+  const int H2 = h_even(H);
+  return sizeof(float) * ((size_t)H2 * DW + (size_t)TA * DW + 2 * H2 + DW + NS * NQR * KR);
 }
 
 // Forward, persistent over tiles: z = W0 (s.G) + b0, x = tanh z, E = w1.x + b1,
 // E' = s . (W0^T (w1 (1 - x^2)))  (D1.1-D1.5), and the per-atom radial
 // contraction chat_i[J][k] = sum_n E'_n c^R_nk^{IJ} used by the force sweep.
-// X is stored with row pitch HP.
-template <int D, int HP, int NS, int NQR, int KR>
-__global__ void __launch_bounds__(NT) k_mlp_fwd_tile(Tiles T, int ntiles, DevModel dm, const float* __restrict__ G,
-                                                     float* __restrict__ X, float* __restrict__ Ep,
-                                                     float* __restrict__ Eatom, float* __restrict__ chat) {
-  constexpr int DP = (D + 3) / 4 * 4;
+template <int D, int NS, int NQR, int KR>
+__global__ void __launch_bounds__(NT, 1) k_mlp_fwd_row(Tiles T, int ntiles, DevModel dm, const float* __restrict__ G,
+                                                       float* __restrict__ Ep, float* __restrict__ Eatom,
+                                                       float* __restrict__ chat) {
+  constexpr int DW = RowW<D>::DW, NJK = NS * KR;
   extern __shared__ float4 sm4[];
-  float* sm = reinterpret_cast<float*>(sm4);
-  float* W0t = sm;                // [DP][HP]
-  float* W0n = W0t + DP * HP;     // [HP][DP]
-  float* b0 = W0n + HP * DP;      // [HP]
-  float* w1 = b0 + HP;            // [HP]
-  float* Gt = w1 + HP;            // [DP][TM] scaled inputs, then E'
-  float* Bt = Gt + DP * TM;       // [HP][TM] beta
-  float* Ep4 = Bt + HP * TM;      // [HP/4][TM] partial energies per hidden block
-  float* cR = Ep4 + (HP / 4) * TM;  // [NS][NQR][KR] of this species
-  __shared__ int rows[TM];
-  const int H = dm.H;
+  const int H = dm.H, H2 = h_even(H), Hh = H2 / 2;
+  float* W = reinterpret_cast<float*>(sm4);  // [H2][DW]
+  float* R = W + H2 * DW;                    // [TA][DW] s.G, then the scaled E'
+  float* b0 = R + TA * DW;                   // [H2]
+  float* w1 = b0 + H2;                       // [H2]
+  float* sc = w1 + H2;                       // [DW]
+  float* cR = sc + DW;                       // [NS][NQR][KR] of the tile's species
+  __shared__ int rows[TA];
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int a = 16 * (tid >> 5) + (lane & 15), half = lane >> 4;
+  for (int v = tid; v < DW; v += NT) sc[v] = v < D ? dm.scale[v] : 0.f;
   int cur_e = -1;
   float b1 = 0.f;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     int e, a0, na;
     tile_of(T, t, e, a0, na);
-    __syncthreads();
+    __syncthreads();  // the previous tile's readers of R, rows and the weights are done
     if (e != cur_e) {
-      load_weights<D, DP, HP>(dm, e, W0t, W0n, b0, w1);
-      for (int q = threadIdx.x; q < NS * NQR * KR; q += NT) cR[q] = dm.params[dm.off_cR + e * NS * NQR * KR + q];
+      load_weights<D>(dm, e, W, b0, w1);
+      for (int q = tid; q < NS * NQR * KR; q += NT) cR[q] = dm.params[dm.off_cR + e * NS * NQR * KR + q];
       b1 = dm.params[(size_t)e * dm.net_size + D * H + 2 * H];
       cur_e = e;
     }
-    if (threadIdx.x < TM) rows[threadIdx.x] = threadIdx.x < na ? T.perm[a0 + threadIdx.x] : -1;
+    if (tid < TA) rows[tid] = tid < na ? T.perm[a0 + tid] : -1;
     __syncthreads();
-    stage_kmajor<D, DP>(G, rows, dm.scale, Gt);
+    stage_rows<D, 1>(G, nullptr, rows, sc, R, nullptr);
     __syncthreads();
-    tile_gemm<HP, DP, TM, HP>(Gt, W0t, [&](int m0, int n0, float (&acc)[4][4]) {
-      float4 bt[4];
-      float ep[4] = {0.f, 0.f, 0.f, 0.f};
-      float xv[4][4];
+    float g[DW], ep[DW];
+    load_row<DW>(R + a * DW, g);
 #pragma unroll
-      for (int w = 0; w < 4; ++w) {
-        const int mu = n0 + w;
-        float bb[4];
+    for (int v = 0; v < DW; ++v) ep[v] = 0.f;
+    float E = 0.f;
+    for (int mu = half * Hh; mu < (half + 1) * Hh; ++mu) {
+      const float4* wr = reinterpret_cast<const float4*>(W + mu * DW);
+      const float x = tanhf(dot_row<DW>(g, wr, b0[mu]));
+      E = fmaf(w1[mu], x, E);
+      axpy_row<DW>(ep, w1[mu] * (1.f - x * x), wr);
+    }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const float x = mu < H ? tanhf(acc[u][w] + b0[mu]) : 0.f;
-          xv[u][w] = x;
-          bb[u] = w1[mu] * (1.f - x * x);
-          ep[u] = fmaf(w1[mu], x, ep[u]);
-        }
-        bt[w] = make_float4(bb[0], bb[1], bb[2], bb[3]);
-      }
-#pragma unroll
-      for (int w = 0; w < 4; ++w) *reinterpret_cast<float4*>(Bt + (n0 + w) * TM + m0) = bt[w];
-      *reinterpret_cast<float4*>(Ep4 + (n0 / 4) * TM + m0) = make_float4(ep[0], ep[1], ep[2], ep[3]);
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int r = rows[m0 + u];
-        if (r >= 0) *reinterpret_cast<float4*>(X + (size_t)r * HP + n0) = make_float4(xv[u][0], xv[u][1], xv[u][2], xv[u][3]);
-      }
-    });
-    __syncthreads();
-    if (threadIdx.x < na) {  // energies, hidden blocks summed in order
-      const int a = threadIdx.x;
-      float E = 0.f;
-      for (int b = 0; b < HP / 4; ++b) E += Ep4[b * TM + a];
+    for (int v = 0; v < DW; ++v) ep[v] += __shfl_xor_sync(0xffffffffu, ep[v], 16);
+    E += __shfl_xor_sync(0xffffffffu, E, 16);
+    __syncthreads();  // every row of R has been read
+    if (half == 0 && a < na) {
       Eatom[rows[a]] = E + b1;
-    }
-    tile_gemm<DP, HP, TM, DP>(Bt, W0n, [&](int m0, int n0, float (&acc)[4][4]) {
+      float4* o = reinterpret_cast<float4*>(R + a * DW);
 #pragma unroll
-      for (int w = 0; w < 4; ++w) {
-        const int v = n0 + w;
-        const float s = v < D ? dm.scale[v] : 0.f;
-        *reinterpret_cast<float4*>(Gt + v * TM + m0) =
-            make_float4(acc[0][w] * s, acc[1][w] * s, acc[2][w] * s, acc[3][w] * s);
-      }
-    });
-    __syncthreads();
-    for (int q = threadIdx.x; q < na * D; q += NT) {
-      const int a = q / D, v = q % D;
-      Ep[(size_t)rows[a] * D + v] = Gt[v * TM + a];
+      for (int v4 = 0; v4 < DW / 4; ++v4)
+        o[v4] = make_float4(ep[4 * v4] * sc[4 * v4], ep[4 * v4 + 1] * sc[4 * v4 + 1], ep[4 * v4 + 2] * sc[4 * v4 + 2],
+                            ep[4 * v4 + 3] * sc[4 * v4 + 3]);
     }
-    for (int q = threadIdx.x; q < TM * NS * KR; q += NT) {
-      const int a = q % TM, jk = q / TM, J = jk / KR, k = jk % KR;
-      if (a >= na) continue;
+    __syncthreads();
+    // coalesced row writes: E' and chat
+    for (int q = tid; q < na * D; q += NT) {
+      const int r = q / D, v = q % D;
+      Ep[(size_t)rows[r] * D + v] = R[r * DW + v];
+    }
+    for (int q = tid; q < na * NJK; q += NT) {
+      const int r = q / NJK, jk = q % NJK, J = jk / KR, k = jk % KR;
       float s = 0.f;
 #pragma unroll
-      for (int n = 0; n < NQR; ++n) s = fmaf(Gt[n * TM + a], cR[(J * NQR + n) * KR + k], s);
-      chat[(size_t)rows[a] * NS * KR + jk] = s;
+      for (int n = 0; n < NQR; ++n) s = fmaf(R[r * DW + n], cR[(J * NQR + n) * KR + k], s);
+      chat[(size_t)rows[r] * NJK + jk] = s;
     }
   }
 }
 
 template <int D, int HP>
-size_t mlp_bwd_smem() {
-  constexpr int DP = (D + 3) / 4 * 4;
-  return sizeof(float) * (2 * DP * HP + 2 * HP + 3 * TM * DP + 2 * HP * TM + TM * HP);
+size_t mlp_bwd_smem(int H) {
+  constexpr int DW = RowW<D>::DW;
+  const int H2 = h_even(H), HR = h_row(H);
+  return sizeof(float) * ((size_t)H2 * DW + 2 * (size_t)TA * DW + 2 * (size_t)TA * HR + 2 * H2 + DW +
+                          2 * (size_t)NW * HP + TA);
 }
 
-// Tangent and reverse pass, persistent over tiles, with the energy residual
-// weight e_i:
-//   zdot = W0 (s.Gdot), beta = w1 (1 - x^2), alpha = e_i beta + 2 x beta zdot,
-//   Gbar = s . (W0^T alpha),
+// Tangent and reverse pass, persistent over tiles, with e_i the energy residual
+// weight of the atom's structure:
+//   z = W0 (s.G) + b0, zdot = W0 (s.Gdot), x = tanh z, beta = w1 (1 - x^2),
+//   alpha = e_i beta + 2 x beta zdot, Gbar = s . (W0^T alpha),
 //   dW0 += alpha (s.G)^T - beta (s.Gdot)^T, db0 += alpha,
 //   dw1 += e_i x - (1 - x^2) zdot, db1 += e_i.
 // Each block writes one partial per species it visited into
-// part[block][species] (zeroed beforehand).
+// part[block][species] (zeroed beforehand).  HP: hidden width padded to 32, 64
+// or 128 (sets the dW0 blocks a thread owns).
 template <int D, int HP>
-__global__ void __launch_bounds__(NT) k_mlp_bwd_tile(Tiles T, int ntiles, DevModel dm,
-                                                     const int* __restrict__ atom_struct,
-                                                     const float* __restrict__ es, const float* __restrict__ G,
-                                                     const float* __restrict__ Gd, const float* __restrict__ X,
-                                                     float* __restrict__ Gb, float* __restrict__ part,
-                                                     int part_stride) {
-  constexpr int DP = (D + 3) / 4 * 4;
-  constexpr int NBW = ((HP / 4) * (DP / 4) + NT - 1) / NT;  // dW0 4x4 blocks per thread
+__global__ void __launch_bounds__(NT, 1) k_mlp_bwd_row(Tiles T, int ntiles, DevModel dm,
+                                                       const int* __restrict__ atom_struct,
+                                                       const float* __restrict__ es, const float* __restrict__ G,
+                                                       const float* __restrict__ Gd, float* __restrict__ Gb,
+                                                       float* __restrict__ part, int part_stride) {
+  constexpr int DW = RowW<D>::DW, NVB = DW / 4;
+  constexpr int NBK = ((HP / 4) * NVB + NT - 1) / NT;  // dW0 4 x 4 blocks per thread
   extern __shared__ float4 sm4[];
-  float* sm = reinterpret_cast<float*>(sm4);
-  float* W0t = sm;               // [DP][HP]
-  float* W0n = W0t + DP * HP;    // [HP][DP]
-  float* b0 = W0n + HP * DP;
-  float* w1 = b0 + HP;
-  float* Gr = w1 + HP;           // [TM][DP] s.G, atom-major
-  float* Gdr = Gr + TM * DP;     // [TM][DP] s.Gdot, atom-major
-  float* Gdk = Gdr + TM * DP;    // [DP][TM] s.Gdot, k-major
-  float* Al = Gdk + DP * TM;     // [HP][TM] alpha, k-major
-  float* Be = Al + HP * TM;      // [HP][TM] -beta, k-major
-  float* Xs = Be + HP * TM;      // [TM][HP] x
-  __shared__ int rows[TM];
-  __shared__ float ei[TM];
-  const int H = dm.H;
-  constexpr int NCB = (MB * (HP / 4) + NT - 1) / NT;  // GEMM blocks per thread (column groups)
-  float accW[NBW][4][4];
-  float cb0[NCB][4], cw1[NCB][4], cb1 = 0.f;  // column sums of the thread's column groups
+  const int H = dm.H, H2 = h_even(H), Hh = H2 / 2, HR = h_row(H);
+  float* W = reinterpret_cast<float*>(sm4);  // [H2][DW]
+  float* SG = W + H2 * DW;                   // [TA][DW] s.G, then the Gbar output rows
+  float* SD = SG + TA * DW;                  // [TA][DW] s.Gdot
+  float* Al = SD + TA * DW;                  // [TA][HR] alpha
+  float* Be = Al + TA * HR;                  // [TA][HR] -beta
+  float* b0 = Be + TA * HR;                  // [H2]
+  float* w1 = b0 + H2;                       // [H2]
+  float* sc = w1 + H2;                       // [DW]
+  float* wdw1 = sc + DW;                     // [NW][HP] per-warp sums over atoms
+  float* wdb0 = wdw1 + NW * HP;              // [NW][HP]
+  float* ev = wdb0 + NW * HP;                // [TA] e_i of the tile's atoms
+  __shared__ int rows[TA];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int a = 16 * warp + (lane & 15), half = lane >> 4;
+  for (int v = tid; v < DW; v += NT) sc[v] = v < D ? dm.scale[v] : 0.f;
+  for (int q = tid; q < 2 * TA * HR; q += NT) Al[q] = 0.f;  // Be follows Al
+  float acc[NBK][4][4];
+  float cb1 = 0.f;
   int cur_e = -1;
 
   auto reset = [&]() {
 #pragma unroll
-    for (int q = 0; q < NBW; ++q)
+    for (int k = 0; k < NBK; ++k)
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int w = 0; w < 4; ++w) accW[q][u][w] = 0.f;
-#pragma unroll
-    for (int c = 0; c < NCB; ++c)
-#pragma unroll
-      for (int w = 0; w < 4; ++w) cb0[c][w] = cw1[c][w] = 0.f;
+        for (int c = 0; c < 4; ++c) acc[k][u][c] = 0.f;
+    for (int q = tid; q < 2 * NW * HP; q += NT) wdw1[q] = 0.f;  // wdb0 follows wdw1
     cb1 = 0.f;
   };
-  auto flush = [&](int e) {
+  auto flush = [&](int e) {  // after a barrier that follows the last tile of species e
     float* out = part + ((size_t)blockIdx.x * T.ns + e) * part_stride;
 #pragma unroll
-    for (int q = 0; q < NBW; ++q) {
-      const int blk = threadIdx.x + q * NT;
-      if (blk >= (HP / 4) * (DP / 4)) continue;
-      const int m0 = (blk / (DP / 4)) * 4, n0 = (blk % (DP / 4)) * 4;
+    for (int k = 0; k < NBK; ++k) {
+      const int q = tid + k * NT, mb = q / NVB, vb = q % NVB;
+      if (q >= (HP / 4) * NVB) continue;
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int w = 0; w < 4; ++w) {
-          const int mu = m0 + u, v = n0 + w;
-          if (mu < H && v < D) out[mu * D + v] = accW[q][u][w];
+        for (int c = 0; c < 4; ++c) {
+          const int mu = 4 * mb + u, v = 4 * vb + c;
+          if (mu < H && v < D) out[mu * D + v] = acc[k][u][c];
         }
     }
-    // column sums live in the lanes with m-block 0 (threadIdx % MB == 0)
-#pragma unroll
-    for (int c = 0; c < NCB; ++c) {
-      const int blk = threadIdx.x + c * NT;
-      if (threadIdx.x % MB != 0 || blk >= MB * (HP / 4)) continue;
-      const int n0 = (blk / MB) * 4;
-#pragma unroll
-      for (int w = 0; w < 4; ++w)
-        if (n0 + w < H) {
-          out[D * H + n0 + w] = cb0[c][w];
-          out[D * H + H + n0 + w] = cw1[c][w];
-        }
+    for (int mu = tid; mu < H; mu += NT) {
+      float s0 = 0.f, s1 = 0.f;
+      for (int w = 0; w < NW; ++w) {  // warps in order
+        s0 += wdb0[w * HP + mu];
+        s1 += wdw1[w * HP + mu];
+      }
+      out[D * H + mu] = s0;
+      out[D * H + H + mu] = s1;
     }
-    if (threadIdx.x == 0) out[D * H + 2 * H] = cb1;
+    if (tid == 0) out[D * H + 2 * H] = cb1;
   };
   reset();
 
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     int e, a0, na;
     tile_of(T, t, e, a0, na);
-    __syncthreads();
+    __syncthreads();  // the previous tile is done with every shared array
     if (e != cur_e) {
       if (cur_e >= 0) flush(cur_e);
+      __syncthreads();
       reset();
-      load_weights<D, DP, HP>(dm, e, W0t, W0n, b0, w1);
+      load_weights<D>(dm, e, W, b0, w1);
       cur_e = e;
     }
-    if (threadIdx.x < TM) {
-      const int r = threadIdx.x < na ? T.perm[a0 + threadIdx.x] : -1;
-      rows[threadIdx.x] = r;
-      ei[threadIdx.x] = r >= 0 ? es[atom_struct[r]] : 0.f;
+    if (tid < TA) {
+      const int r = tid < na ? T.perm[a0 + tid] : -1;
+      rows[tid] = r;
+      ev[tid] = r >= 0 ? es[atom_struct[r]] : 0.f;
     }
     __syncthreads();
-    stage_rows<D, DP>(G, rows, dm.scale, Gr);
-    stage_rows<D, DP>(Gd, rows, dm.scale, Gdr);
-    stage_kmajor<D, DP>(Gd, rows, dm.scale, Gdk);
-    for (int q = threadIdx.x; q < TM * (HP / 4); q += NT) {
-      const int a = q / (HP / 4), c4 = (q % (HP / 4)) * 4, r = rows[a];
-      const float4 x = r >= 0 ? *reinterpret_cast<const float4*>(X + (size_t)r * HP + c4) : make_float4(0.f, 0.f, 0.f, 0.f);
-      *reinterpret_cast<float4*>(Xs + a * HP + c4) = x;
+    stage_rows<D, 2>(G, Gd, rows, sc, SG, SD);
+    if (tid == 0)
+      for (int r = 0; r < na; ++r) cb1 += ev[r];
+    __syncthreads();
+    // per atom: z, zdot, alpha, -beta, Gbar; column sums of alpha and q1 per half-warp
+    float gb[DW];
+    {
+      float g[DW], gd[DW];
+      load_row<DW>(SG + a * DW, g);
+      load_row<DW>(SD + a * DW, gd);
+#pragma unroll
+      for (int v = 0; v < DW; ++v) gb[v] = 0.f;
+      const float ea = ev[a];
+      for (int mu = half * Hh; mu < (half + 1) * Hh; ++mu) {
+        const float4* wr = reinterpret_cast<const float4*>(W + mu * DW);
+        float z, zd;
+        dot_row2<DW>(g, gd, wr, b0[mu], z, zd);
+        const float x = tanhf(z);
+        const float t1 = 1.f - x * x;
+        const float beta = w1[mu] * t1;
+        const float alpha = ea * beta + 2.f * x * beta * zd;
+        float q1 = ea * x - t1 * zd;  // zero for padding atoms (e = 0, zdot = 0) and the padding unit
+        Al[a * HR + mu] = alpha;
+        Be[a * HR + mu] = -beta;
+        axpy_row<DW>(gb, alpha, wr);
+        float as = alpha;
+#pragma unroll
+        for (int o = 1; o < 16; o <<= 1) {
+          as += __shfl_xor_sync(0xffffffffu, as, o);
+          q1 += __shfl_xor_sync(0xffffffffu, q1, o);
+        }
+        if ((lane & 15) == 0) {
+          wdb0[warp * HP + mu] += as;
+          wdw1[warp * HP + mu] += q1;
+        }
+      }
     }
-    if (threadIdx.x == 0)
-      for (int a = 0; a < na; ++a) cb1 += ei[a];
-    __syncthreads();
-    // zdot = (s.Gdot) W0^T; alpha, beta; column sums of alpha and q1 = e x - (1-x^2) zdot
-    tile_gemm<HP, DP, TM, HP>(Gdk, W0t, [&](int m0, int n0, float (&acc)[4][4]) {
-      float s0[4] = {0.f, 0.f, 0.f, 0.f}, s1[4] = {0.f, 0.f, 0.f, 0.f};
-      float4 al[4], be[4];
 #pragma unroll
-      for (int w = 0; w < 4; ++w) {
-        const int mu = n0 + w;
-        float av[4], bv[4];
+    for (int v = 0; v < DW; ++v) gb[v] += __shfl_xor_sync(0xffffffffu, gb[v], 16);
+    __syncthreads();  // alpha and -beta of the tile are complete
+    // dW0 += alpha^T (s.G) - beta^T (s.Gdot) over the tile's atoms
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int a = m0 + u;
-          const float x = Xs[a * HP + mu];
-          const float t1 = 1.f - x * x;
-          const float beta = w1[mu] * t1;
-          const float zd = acc[u][w];
-          const float ea = ei[a];
-          const float alpha = ea * beta + 2.f * x * beta * zd;
-          av[u] = alpha;
-          bv[u] = -beta;
-          s0[w] += alpha;
-          s1[w] += ea * x - t1 * zd;  // zero for padded atoms (x = 0, zd = 0)
-        }
-        al[w] = make_float4(av[0], av[1], av[2], av[3]);
-        be[w] = make_float4(bv[0], bv[1], bv[2], bv[3]);
-      }
-#pragma unroll
-      for (int w = 0; w < 4; ++w) {
-        *reinterpret_cast<float4*>(Al + (n0 + w) * TM + m0) = al[w];
-        *reinterpret_cast<float4*>(Be + (n0 + w) * TM + m0) = be[w];
-      }
-      // the 8 lanes sharing n0 hold the 32 atoms: sum them in a fixed order
-      const int c = (MB * (n0 / 4) + m0 / 4 - (int)threadIdx.x) / NT;  // this thread's block index
-#pragma unroll
-      for (int w = 0; w < 4; ++w) {
-#pragma unroll
-        for (int o = 1; o < MB; o <<= 1) {
-          s0[w] += __shfl_xor_sync(0xffffffffu, s0[w], o);
-          s1[w] += __shfl_xor_sync(0xffffffffu, s1[w], o);
-        }
-#pragma unroll
-        for (int cc = 0; cc < NCB; ++cc)
-          if (cc == c) {
-            cb0[cc][w] += s0[w];
-            cw1[cc][w] += s1[w];
-          }
-      }
-    });
-    __syncthreads();
-    // Gbar = s . (alpha W0)
-    tile_gemm<DP, HP, TM, DP>(Al, W0n, [&](int m0, int n0, float (&acc)[4][4]) {
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int r = rows[m0 + u];
-        if (r < 0) continue;
-#pragma unroll
-        for (int w = 0; w < 4; ++w) {
-          const int v = n0 + w;
-          if (v < D) Gb[(size_t)r * D + v] = acc[u][w] * dm.scale[v];
-        }
-      }
-    });
-    // dW0 += alpha^T (s.G) - beta^T (s.Gdot) over the tile's atoms (K = atoms)
-#pragma unroll
-    for (int q = 0; q < NBW; ++q) {
-      const int blk = threadIdx.x + q * NT;
-      if (blk >= (HP / 4) * (DP / 4)) continue;
-      const int m0 = (blk / (DP / 4)) * 4, n0 = (blk % (DP / 4)) * 4;
-      for (int a = 0; a < na; ++a) {
-        float av[4], bv[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          av[u] = Al[(m0 + u) * TM + a];
-          bv[u] = Be[(m0 + u) * TM + a];
-        }
-        const float4 g = *reinterpret_cast<const float4*>(Gr + a * DP + n0);
-        const float4 gd = *reinterpret_cast<const float4*>(Gdr + a * DP + n0);
-        const float gv[4] = {g.x, g.y, g.z, g.w}, dv[4] = {gd.x, gd.y, gd.z, gd.w};
+    for (int k = 0; k < NBK; ++k) {
+      const int q = tid + k * NT, mb = q / NVB, vb = q % NVB;
+      if (q >= (HP / 4) * NVB || 4 * mb >= H2) continue;
+      for (int r = 0; r < na; ++r) {
+        const float4 al = *reinterpret_cast<const float4*>(Al + r * HR + 4 * mb);
+        const float4 be = *reinterpret_cast<const float4*>(Be + r * HR + 4 * mb);
+        const float4 g4 = *reinterpret_cast<const float4*>(SG + r * DW + 4 * vb);
+        const float4 d4 = *reinterpret_cast<const float4*>(SD + r * DW + 4 * vb);
+        const float av[4] = {al.x, al.y, al.z, al.w}, bv[4] = {be.x, be.y, be.z, be.w};
+        const float gv[4] = {g4.x, g4.y, g4.z, g4.w}, dv[4] = {d4.x, d4.y, d4.z, d4.w};
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
-          for (int w = 0; w < 4; ++w) accW[q][u][w] = fmaf(av[u], gv[w], fmaf(bv[u], dv[w], accW[q][u][w]));
+          for (int c = 0; c < 4; ++c) acc[k][u][c] = fmaf(av[u], gv[c], fmaf(bv[u], dv[c], acc[k][u][c]));
       }
     }
+    __syncthreads();  // s.G rows are no longer read: they take the Gbar rows
+    if (half == 0) {
+      float4* o = reinterpret_cast<float4*>(SG + a * DW);
+#pragma unroll
+      for (int v4 = 0; v4 < DW / 4; ++v4)
+        o[v4] = make_float4(gb[4 * v4] * sc[4 * v4], gb[4 * v4 + 1] * sc[4 * v4 + 1], gb[4 * v4 + 2] * sc[4 * v4 + 2],
+                            gb[4 * v4 + 3] * sc[4 * v4 + 3]);
+    }
+    __syncthreads();
+    for (int q = tid; q < na * D; q += NT) {
+      const int r = q / D, v = q % D;
+      Gb[(size_t)rows[r] * D + v] = SG[r * DW + v];
+    }
   }
+  __syncthreads();
   if (cur_e >= 0) flush(cur_e);
 }
 
@@ -412,41 +432,65 @@ Tiles make_tiles(const gnep_nlist* nl, int ns, int tile_atoms) {
   return T;
 }
 
+namespace {
+// Resident blocks of a kernel on this GPU.
+template <class K>
+int resident_blocks(K kern, size_t smem, int& out) {
+  int per_sm = 0, dev = 0, sms = 0;
+  GNEP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
+  GNEP_CUDA(cudaGetDevice(&dev));
+  GNEP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (per_sm < 1) return set_error(GNEP_ERR_CUDA, "FP32 network kernel does not fit on an SM");
+  out = per_sm * sms;
+  return GNEP_OK;
+}
+}  // namespace
+
 template <int D, int HP, int NS, int NQR, int KR>
 int mlp_setup() {
-  GNEP_CUDA(cudaFuncSetAttribute(k_mlp_fwd_tile<D, HP, NS, NQR, KR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)mlp_fwd_smem<D, HP, NS, NQR, KR>()));
-  GNEP_CUDA(cudaFuncSetAttribute(k_mlp_bwd_tile<D, HP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)mlp_bwd_smem<D, HP>()));
+  // shared memory for the largest hidden width of this padding
+  GNEP_CUDA(cudaFuncSetAttribute(k_mlp_fwd_row<D, NS, NQR, KR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)mlp_fwd_smem<D, NS, NQR, KR>(kMaxHidden)));
+  GNEP_CUDA(cudaFuncSetAttribute(k_mlp_bwd_row<D, HP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)mlp_bwd_smem<D, HP>(HP)));
+  GNEP_CUDA(cudaFuncSetAttribute(k_mlp_bwd_row<D, HP>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   return GNEP_OK;
 }
 
 template <int D, int HP, int NS, int NQR, int KR>
 int mlp_forward(const gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
-  const Tiles T = make_tiles(nl, NS);
+  const Tiles T = make_tiles(nl, NS, TA);
   const int ntiles = T.tbase[NS];
   if (ntiles == 0) return GNEP_OK;
   Workspace& w = nl->ws;
-  const int grid = net_blocks(nl, ntiles < kNetBlocks ? ntiles : kNetBlocks);
-  k_mlp_fwd_tile<D, HP, NS, NQR, KR><<<grid, NT, mlp_fwd_smem<D, HP, NS, NQR, KR>(), st>>>(
-      T, ntiles, m->dev(), w.G, w.X, w.Ep, w.Eatom, w.chat);
-  GNEP_CHECK_LAUNCH("k_mlp_fwd_tile");
+  auto kern = k_mlp_fwd_row<D, NS, NQR, KR>;
+  const size_t smem = mlp_fwd_smem<D, NS, NQR, KR>(m->shape.H);
+  int cap = 0;
+  if (int rc = resident_blocks(kern, smem, cap)) return rc;
+  const int grid = net_blocks(nl, ntiles < cap ? ntiles : cap);
+  kern<<<grid, NT, smem, st>>>(T, ntiles, m->dev(), w.G, w.Ep, w.Eatom, w.chat);
+  GNEP_CHECK_LAUNCH("k_mlp_fwd_row");
   return GNEP_OK;
 }
 
 template <int D, int HP>
 int mlp_backward(const gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
   const int ns = m->shape.ns;
-  const Tiles T = make_tiles(nl, ns);
+  const Tiles T = make_tiles(nl, ns, TA);
   const int ntiles = T.tbase[ns];
   Workspace& w = nl->ws;
-  const int grid = net_blocks(nl, ntiles < kNetBlocks ? (ntiles > 0 ? ntiles : 1) : kNetBlocks);
+  auto kern = k_mlp_bwd_row<D, HP>;
+  const size_t smem = mlp_bwd_smem<D, HP>(m->shape.H);
+  int cap = 0;
+  if (int rc = resident_blocks(kern, smem, cap)) return rc;
+  if (cap > kNetBlocks) cap = kNetBlocks;  // net_part holds kNetBlocks partials
+  const int grid = net_blocks(nl, ntiles < cap ? (ntiles > 0 ? ntiles : 1) : cap);
   w.net_blocks = grid;
   GNEP_CUDA(cudaMemsetAsync(w.net_part, 0, sizeof(float) * (size_t)grid * ns * m->net_size, st));
   if (ntiles == 0) return GNEP_OK;
-  k_mlp_bwd_tile<D, HP><<<grid, NT, mlp_bwd_smem<D, HP>(), st>>>(T, ntiles, m->dev(), nl->atom_struct, w.es, w.G,
-                                                                 w.Gd, w.X, w.Gb, w.net_part, m->net_size);
-  GNEP_CHECK_LAUNCH("k_mlp_bwd_tile");
+  kern<<<grid, NT, smem, st>>>(T, ntiles, m->dev(), nl->atom_struct, w.es, w.G, w.Gd, w.Gb, w.net_part,
+                               m->net_size);
+  GNEP_CHECK_LAUNCH("k_mlp_bwd_row");
   return GNEP_OK;
 }
 
@@ -465,6 +509,8 @@ int mlp_backward(const gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
 GNEP_NET(25, 5, 9)
 GNEP_NET(54, 9, 13)
 GNEP_NET(45, 9, 13)
+GNEP_NET(35, 5, 9)
+GNEP_NET(50, 5, 9)
 #undef GNEP_NET
 
 }  // namespace gnep

@@ -4,7 +4,6 @@
 
 namespace gnep {
 
-constexpr int kTileAtoms = 32;   // atoms per network tile
 constexpr int kNetBlocks = 456;  // persistent blocks of the backward pass (3 per SM)
 
 // Species-homogeneous tiles over the species-grouped atom order.
@@ -15,7 +14,7 @@ struct Tiles {
   int ns;
 };
 
-Tiles make_tiles(const gnep_nlist* nl, int ns, int tile_atoms = kTileAtoms);
+Tiles make_tiles(const gnep_nlist* nl, int ns, int tile_atoms);
 
 template <int D, int HP, int NS, int NQR, int KR>
 int mlp_setup();

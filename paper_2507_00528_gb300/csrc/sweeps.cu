@@ -31,21 +31,11 @@
 #include "device_math.cuh"
 #include "gnep_internal.h"
 #include "network.cuh"
+#include "shape.cuh"
+#include "sweeps_lmax.cuh"
 #include "warp_mma.cuh"
 
 namespace gnep {
-
-template <int NS_, int NQR_, int KR_, int NQA_, int KA_, bool FB_>
-struct Sh {
-  static constexpr int NS = NS_, NQR = NQR_, KR = KR_, NQA = NQA_, KA = KA_;
-  static constexpr bool FB = FB_;
-  static constexpr int NDES = NQR + NQA * 4 + (FB ? NQA : 0);
-  __host__ __device__ static constexpr int vang(int n, int l) { return NQR + n * 4 + (l - 1); }
-  __host__ __device__ static constexpr int v4b(int n) { return NQR + NQA * 4 + n; }
-  static constexpr int NCR = NS * NS * NQR * KR;
-  static constexpr int NCA = NS * NS * NQA * KA;
-  static constexpr int NQ = NQR > NQA ? NQR : NQA;
-};
 
 constexpr int RL = 4;           // lanes per atom in radial sweeps
 constexpr int CH = 128;         // pairs per geometry chunk
@@ -96,56 +86,6 @@ __device__ __forceinline__ void lane_reduce(float (&acc)[NS][K]) {
     for (int s = 0; s < NS; ++s)
 #pragma unroll
       for (int k = 0; k < K; ++k) acc[s][k] += __shfl_xor_sync(0xffffffffu, acc[s][k], o);
-}
-
-// Harmonics on the unit vector u and, for a direction w, the directional
-// derivatives D_lm = grad_d B_lm . w (B9.2).  Each B_lm is the degree-l
-// homogeneous polynomial h_lm (the r = 1 forms with 1 read as r^2) on u, so
-// grad_d B_lm = (grad h_lm(u) - l h_lm(u) u) / r (Euler's relation u . grad h =
-// l h removes the radial part), and grad h_lm(u) . w is the derivative of h_lm
-// along w, evaluated here with dx = w_x, dy = w_y, dz = w_z, d(r^2) = 2 u . w.
-__device__ __forceinline__ void harmonics_dir(float x, float y, float z, float rinv, float wx, float wy, float wz,
-                                              float (&B)[NLM], float (&Dd)[NLM]) {
-  harmonics(x, y, z, B);
-  const float ru = x * wx + y * wy + z * wz;  // u . w; d(r^2) = 2 ru
-  const float x2 = x * x, y2 = y * y, z2 = z * z;
-  const float dx2 = 2.f * x * wx, dy2 = 2.f * y * wy, dz2 = 2.f * z * wz, dr2 = 2.f * ru;
-  float d[NLM];
-  // l = 1
-  d[0] = wz; d[1] = wx; d[2] = wy;
-  // l = 2
-  d[3] = 3.f * dz2 - dr2;
-  d[4] = wx * z + x * wz;
-  d[5] = wy * z + y * wz;
-  d[6] = dx2 - dy2;
-  d[7] = 2.f * (wx * y + x * wy);
-  // l = 3: p3 = 5 z^2 - r^2
-  const float p3 = 5.f * z2 - 1.f, dp3 = 5.f * dz2 - dr2;
-  d[8] = (5.f * dz2 - 3.f * dr2) * z + (5.f * z2 - 3.f) * wz;
-  d[9] = dp3 * x + p3 * wx;
-  d[10] = dp3 * y + p3 * wy;
-  const float xmy = x2 - y2, dxmy = dx2 - dy2;
-  d[11] = dxmy * z + xmy * wz;
-  d[12] = 2.f * ((wx * y + x * wy) * z + x * y * wz);
-  const float a13 = x2 - 3.f * y2, da13 = dx2 - 3.f * dy2;
-  const float a14 = 3.f * x2 - y2, da14 = 3.f * dx2 - dy2;
-  d[13] = da13 * x + a13 * wx;
-  d[14] = da14 * y + a14 * wy;
-  // l = 4: w4 = (7 z^2 - 3 r^2) z, p4 = 7 z^2 - r^2
-  const float w4 = (7.f * z2 - 3.f) * z, dw4 = (7.f * dz2 - 3.f * dr2) * z + (7.f * z2 - 3.f) * wz;
-  const float p4 = 7.f * z2 - 1.f, dp4 = 7.f * dz2 - dr2;
-  d[15] = 35.f * 2.f * z2 * dz2 - 30.f * (dz2 + z2 * dr2) + 3.f * 2.f * dr2;
-  d[16] = dw4 * x + w4 * wx;
-  d[17] = dw4 * y + w4 * wy;
-  d[18] = dp4 * xmy + p4 * dxmy;
-  const float xy = x * y, dxy = wx * y + x * wy;
-  d[19] = 2.f * (dp4 * xy + p4 * dxy);
-  d[20] = da13 * x * z + a13 * (wx * z + x * wz);
-  d[21] = da14 * y * z + a14 * (wy * z + y * wz);
-  d[22] = 2.f * x2 * dx2 - 6.f * (dx2 * y2 + x2 * dy2) + 2.f * y2 * dy2;
-  d[23] = 4.f * (dxy * xmy + xy * dxmy);
-#pragma unroll
-  for (int q = 0; q < NLM; ++q) Dd[q] = (d[q] - (float)lm_l(q) * B[q] * ru) * rinv;
 }
 
 }  // namespace
@@ -1209,41 +1149,52 @@ struct Runner {
   // Network forward/backward in the model's precision: plain FP32 tiles, or
   // tensor-core tiles with TF32 or BF16 operands.
   static int network_forward(const gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
-    if (m->precision == GNEP_PREC_FP32) {
+    if (C::LMAX > 4 || m->precision == GNEP_PREC_FP32) {
       switch (hidden_pad(m->shape.H)) {
         case 32: return mlp_forward<C::NDES, 32, C::NS, C::NQR, C::KR>(m, nl, st);
         case 64: return mlp_forward<C::NDES, 64, C::NS, C::NQR, C::KR>(m, nl, st);
         default: return mlp_forward<C::NDES, 128, C::NS, C::NQR, C::KR>(m, nl, st);
       }
     }
-    const bool tf = m->precision == GNEP_PREC_TF32;
-    switch (hidden_pad_tc(m->shape.H)) {
-      case 32:
-        return tf ? mlp_forward_tc<true, C::NDES, 32, C::NS, C::NQR, C::KR>(m, nl, st)
-                  : mlp_forward_tc<false, C::NDES, 32, C::NS, C::NQR, C::KR>(m, nl, st);
-      case 64:
-        return tf ? mlp_forward_tc<true, C::NDES, 64, C::NS, C::NQR, C::KR>(m, nl, st)
-                  : mlp_forward_tc<false, C::NDES, 64, C::NS, C::NQR, C::KR>(m, nl, st);
-      default:
-        return tf ? mlp_forward_tc<true, C::NDES, 112, C::NS, C::NQR, C::KR>(m, nl, st)
-                  : mlp_forward_tc<false, C::NDES, 112, C::NS, C::NQR, C::KR>(m, nl, st);
+    if constexpr (C::LMAX > 4) {
+      return set_error(GNEP_ERR_UNSUPPORTED, "l_max > 4 runs the FP32 network only");
+    } else {
+      const bool tf = m->precision == GNEP_PREC_TF32;
+      switch (hidden_pad_tc(m->shape.H)) {
+        case 32:
+          return tf ? mlp_forward_tc<true, C::NDES, 32, C::NS, C::NQR, C::KR>(m, nl, st)
+                    : mlp_forward_tc<false, C::NDES, 32, C::NS, C::NQR, C::KR>(m, nl, st);
+        case 64:
+          return tf ? mlp_forward_tc<true, C::NDES, 64, C::NS, C::NQR, C::KR>(m, nl, st)
+                    : mlp_forward_tc<false, C::NDES, 64, C::NS, C::NQR, C::KR>(m, nl, st);
+        default:
+          return tf ? mlp_forward_tc<true, C::NDES, 112, C::NS, C::NQR, C::KR>(m, nl, st)
+                    : mlp_forward_tc<false, C::NDES, 112, C::NS, C::NQR, C::KR>(m, nl, st);
+      }
     }
   }
 
   static int network_backward(const gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
-    if (m->precision == GNEP_PREC_FP32) {
+    if (C::LMAX > 4 || m->precision == GNEP_PREC_FP32) {
       switch (hidden_pad(m->shape.H)) {
         case 32: return mlp_backward<C::NDES, 32>(m, nl, st);
         case 64: return mlp_backward<C::NDES, 64>(m, nl, st);
         default: return mlp_backward<C::NDES, 128>(m, nl, st);
       }
     }
-    const bool tf = m->precision == GNEP_PREC_TF32;
-    switch (hidden_pad_tc(m->shape.H)) {
-      case 32: return tf ? mlp_backward_tc<true, C::NDES, 32>(m, nl, st) : mlp_backward_tc<false, C::NDES, 32>(m, nl, st);
-      case 64: return tf ? mlp_backward_tc<true, C::NDES, 64>(m, nl, st) : mlp_backward_tc<false, C::NDES, 64>(m, nl, st);
-      default:
-        return tf ? mlp_backward_tc<true, C::NDES, 112>(m, nl, st) : mlp_backward_tc<false, C::NDES, 112>(m, nl, st);
+    if constexpr (C::LMAX > 4) {
+      return set_error(GNEP_ERR_UNSUPPORTED, "l_max > 4 runs the FP32 network only");
+    } else {
+      const bool tf = m->precision == GNEP_PREC_TF32;
+      switch (hidden_pad_tc(m->shape.H)) {
+        case 32:
+          return tf ? mlp_backward_tc<true, C::NDES, 32>(m, nl, st) : mlp_backward_tc<false, C::NDES, 32>(m, nl, st);
+        case 64:
+          return tf ? mlp_backward_tc<true, C::NDES, 64>(m, nl, st) : mlp_backward_tc<false, C::NDES, 64>(m, nl, st);
+        default:
+          return tf ? mlp_backward_tc<true, C::NDES, 112>(m, nl, st)
+                    : mlp_backward_tc<false, C::NDES, 112>(m, nl, st);
+      }
     }
   }
 
@@ -1261,7 +1212,11 @@ struct Runner {
     k_desc_radial<C><<<blocks_for((int64_t)N * RL, 128), 128, 0, A.st>>>(N, dm, nl->type, nl->L[0].off,
                                                                           nl->L[0].rij, w.FR, w.G);
     stage("desc_radial");
-    if (int rc = launch_ang<C, false>(m, nl, A.st, nullptr, nullptr, nullptr, w.S, w.G, nullptr)) return rc;
+    if constexpr (C::LMAX > 4) {
+      if (int rc = hi_desc_angular<C>(m, nl, A.st, w.S, w.G)) return rc;
+    } else {
+      if (int rc = launch_ang<C, false>(m, nl, A.st, nullptr, nullptr, nullptr, w.S, w.G, nullptr)) return rc;
+    }
     stage("desc_angular");
     GNEP_CHECK_LAUNCH("descriptor sweep");
     if (with_mlp) {
@@ -1279,8 +1234,12 @@ struct Runner {
     const int N = nl->n_atoms;
     if (N == 0) return GNEP_OK;
     if (nl->L[1].n > 0) {
-      k_force_angular<C><<<nl->natile[1], 128, 0, A.st>>>(N, dm, nl->atile[1], nl->type, nl->L[1].off,
-                                                           nl->L[1].owner, nl->L[1].rij, w.S, w.Ep, w.dA);
+      if constexpr (C::LMAX > 4) {
+        if (int rc = hi_force_angular<C>(m, nl, A.st, w.S, w.Ep, w.dA)) return rc;
+      } else {
+        k_force_angular<C><<<nl->natile[1], 128, 0, A.st>>>(N, dm, nl->atile[1], nl->type, nl->L[1].off,
+                                                             nl->L[1].owner, nl->L[1].rij, w.S, w.Ep, w.dA);
+      }
       stage("force_angular");
     }
     k_force_atoms<C><<<blocks_for((int64_t)N * RL, 128), 128, 0, A.st>>>(
@@ -1305,16 +1264,24 @@ struct Runner {
     k_tangent_radial<C><<<blocks_for((int64_t)N * RL, 128), 128, 0, A.st>>>(
         N, dm, nl->type, nl->atom_struct, nl->L[0].off, nl->L[0].j, nl->L[0].rij, w.a, w.Bs, w.FRd, w.Gd);
     stage("tangent_radial");
-    if (int rc = launch_ang<C, true>(m, nl, A.st, w.a, w.Bs, w.S, w.Sd, w.Gd, w.wij)) return rc;
+    if constexpr (C::LMAX > 4) {
+      if (int rc = hi_tangent_angular<C>(m, nl, A.st, w.a, w.Bs, w.S, w.Sd, w.Gd, w.wij)) return rc;
+    } else {
+      if (int rc = launch_ang<C, true>(m, nl, A.st, w.a, w.Bs, w.S, w.Sd, w.Gd, w.wij)) return rc;
+    }
     stage("tangent_angular");
     if (int rc = network_backward(m, nl, A.st)) return rc;
     stage("mlp_bwd");
     const int nb = cgrad_blocks(nl);
     k_cgrad_radial<C><<<nb, 32 * kCgRadialWarps, 0, A.st>>>(N, nl->type, w.Gb, w.Ep, w.FR, w.FRd, w.cpart);
     stage("cgrad_radial");
-    auto ang = k_cgrad_ang<C, true>;  // split TF32 in every precision mode
-    ang<<<nb, 32 * kCgWarps, sizeof(CgSmem<C>), A.st>>>(nl->natile[1], nl->atile[1], dm, nl->type, nl->L[1].off,
-                                                         nl->L[1].rij, w.wij, w.S, w.Sd, w.Gb, w.Ep, w.cpart);
+    if constexpr (C::LMAX > 4) {
+      if (int rc = hi_cgrad_angular<C>(m, nl, A.st, nb, w.wij, w.S, w.Sd, w.Gb, w.Ep, w.cpart)) return rc;
+    } else {
+      auto ang = k_cgrad_ang<C, true>;  // split TF32 in every precision mode
+      ang<<<nb, 32 * kCgWarps, sizeof(CgSmem<C>), A.st>>>(nl->natile[1], nl->atile[1], dm, nl->type, nl->L[1].off,
+                                                           nl->L[1].rij, w.wij, w.S, w.Sd, w.Gb, w.Ep, w.cpart);
+    }
     stage("cgrad");
     GNEP_CHECK_LAUNCH("backward sweeps");
     return GNEP_OK;
@@ -1323,18 +1290,21 @@ struct Runner {
 
 }  // namespace
 
-// Shapes with compiled kernels: (species, n_max+1, basis+1 radial; same angular; 4-body).
+// Shapes with compiled kernels: (species, n_max+1, basis+1 radial; same angular; 4-body; l_max).
 #define GNEP_SHAPES(X)            \
-  X(2, 5, 9, 5, 9, false)         \
-  X(2, 9, 13, 9, 13, true)        \
-  X(2, 9, 13, 9, 13, false)
+  X(2, 5, 9, 5, 9, false, 4)      \
+  X(2, 9, 13, 9, 13, true, 4)     \
+  X(2, 9, 13, 9, 13, false, 4)    \
+  X(2, 5, 9, 5, 9, false, 6)      \
+  X(2, 5, 9, 5, 9, true, 8)
 
-#define GNEP_MATCH(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB) \
-  (s.ns == P_NS && s.nqr == P_NQR && s.kr == P_KR && s.nqa == P_NQA && s.ka == P_KA && (s.fb != 0) == P_FB)
+#define GNEP_MATCH(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB, P_LM)                                                \
+  (s.ns == P_NS && s.nqr == P_NQR && s.kr == P_KR && s.nqa == P_NQA && s.ka == P_KA && (s.fb != 0) == P_FB && \
+   s.lmax == P_LM)
 
 bool shape_supported(const Shape& s) {
-#define X(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB) \
-  if (GNEP_MATCH(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB) && s.lmax == 4) return true;
+#define X(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB, P_LM) \
+  if (GNEP_MATCH(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB, P_LM)) return true;
   GNEP_SHAPES(X)
 #undef X
   return false;
@@ -1343,27 +1313,36 @@ bool shape_supported(const Shape& s) {
 namespace {
 template <class C>
 int setup_shape() {
-  if (int rc = setup_ang<C, false, true>()) return rc;
-  if (int rc = setup_ang<C, true, true>()) return rc;
-  GNEP_CUDA(cudaFuncSetAttribute(k_cgrad_ang<C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(CgSmem<C>)));
-  GNEP_CUDA(cudaFuncSetAttribute(k_cgrad_ang<C, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-  int rc = mlp_setup<C::NDES, 32, C::NS, C::NQR, C::KR>();
-  if (!rc) rc = mlp_setup<C::NDES, 64, C::NS, C::NQR, C::KR>();
-  if (!rc) rc = mlp_setup<C::NDES, 128, C::NS, C::NQR, C::KR>();
-  if (!rc) rc = mlp_setup_tc<false, C::NDES, 32, C::NS, C::NQR, C::KR>();
-  if (!rc) rc = mlp_setup_tc<false, C::NDES, 64, C::NS, C::NQR, C::KR>();
-  if (!rc) rc = mlp_setup_tc<false, C::NDES, 112, C::NS, C::NQR, C::KR>();
-  if (!rc) rc = mlp_setup_tc<true, C::NDES, 32, C::NS, C::NQR, C::KR>();
-  if (!rc) rc = mlp_setup_tc<true, C::NDES, 64, C::NS, C::NQR, C::KR>();
-  if (!rc) rc = mlp_setup_tc<true, C::NDES, 112, C::NS, C::NQR, C::KR>();
-  return rc;
+  if constexpr (C::LMAX > 4) {
+    int rc = hi_setup<C>();
+    if (!rc) rc = mlp_setup<C::NDES, 32, C::NS, C::NQR, C::KR>();
+    if (!rc) rc = mlp_setup<C::NDES, 64, C::NS, C::NQR, C::KR>();
+    if (!rc) rc = mlp_setup<C::NDES, 128, C::NS, C::NQR, C::KR>();
+    return rc;
+  } else {
+    if (int rc = setup_ang<C, false, true>()) return rc;
+    if (int rc = setup_ang<C, true, true>()) return rc;
+    GNEP_CUDA(cudaFuncSetAttribute(k_cgrad_ang<C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)sizeof(CgSmem<C>)));
+    GNEP_CUDA(cudaFuncSetAttribute(k_cgrad_ang<C, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    int rc = mlp_setup<C::NDES, 32, C::NS, C::NQR, C::KR>();
+    if (!rc) rc = mlp_setup<C::NDES, 64, C::NS, C::NQR, C::KR>();
+    if (!rc) rc = mlp_setup<C::NDES, 128, C::NS, C::NQR, C::KR>();
+    if (!rc) rc = mlp_setup_tc<false, C::NDES, 32, C::NS, C::NQR, C::KR>();
+    if (!rc) rc = mlp_setup_tc<false, C::NDES, 64, C::NS, C::NQR, C::KR>();
+    if (!rc) rc = mlp_setup_tc<false, C::NDES, 112, C::NS, C::NQR, C::KR>();
+    if (!rc) rc = mlp_setup_tc<true, C::NDES, 32, C::NS, C::NQR, C::KR>();
+    if (!rc) rc = mlp_setup_tc<true, C::NDES, 64, C::NS, C::NQR, C::KR>();
+    if (!rc) rc = mlp_setup_tc<true, C::NDES, 112, C::NS, C::NQR, C::KR>();
+    return rc;
+  }
 }
 }  // namespace
 
 int shape_setup(const Shape& s) {
-#define X(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB) \
-  if (GNEP_MATCH(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB)) return setup_shape<Sh<P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB>>();
+#define X(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB, P_LM) \
+  if (GNEP_MATCH(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB, P_LM)) \
+    return setup_shape<Sh<P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB, P_LM>>();
   GNEP_SHAPES(X)
 #undef X
   return set_error(GNEP_ERR_UNSUPPORTED, "no kernel for this shape");
@@ -1371,9 +1350,9 @@ int shape_setup(const Shape& s) {
 
 int run_descriptors(const StepArgs& A, bool with_mlp) {
   const Shape& s = A.m->shape;
-#define X(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB) \
-  if (GNEP_MATCH(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB)) \
-    return Runner<Sh<P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB>>::descriptors(A, with_mlp);
+#define X(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB, P_LM) \
+  if (GNEP_MATCH(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB, P_LM)) \
+    return Runner<Sh<P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB, P_LM>>::descriptors(A, with_mlp);
   GNEP_SHAPES(X)
 #undef X
   return set_error(GNEP_ERR_UNSUPPORTED, "no kernel for this shape");
@@ -1381,8 +1360,9 @@ int run_descriptors(const StepArgs& A, bool with_mlp) {
 
 int run_forward(const StepArgs& A) {
   const Shape& s = A.m->shape;
-#define X(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB) \
-  if (GNEP_MATCH(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB)) return Runner<Sh<P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB>>::forward(A);
+#define X(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB, P_LM) \
+  if (GNEP_MATCH(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB, P_LM)) \
+    return Runner<Sh<P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB, P_LM>>::forward(A);
   GNEP_SHAPES(X)
 #undef X
   return set_error(GNEP_ERR_UNSUPPORTED, "no kernel for this shape");
@@ -1390,8 +1370,9 @@ int run_forward(const StepArgs& A) {
 
 int run_backward(const StepArgs& A) {
   const Shape& s = A.m->shape;
-#define X(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB) \
-  if (GNEP_MATCH(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB)) return Runner<Sh<P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB>>::backward(A);
+#define X(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB, P_LM) \
+  if (GNEP_MATCH(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB, P_LM)) \
+    return Runner<Sh<P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB, P_LM>>::backward(A);
   GNEP_SHAPES(X)
 #undef X
   return set_error(GNEP_ERR_UNSUPPORTED, "no kernel for this shape");
@@ -1465,7 +1446,7 @@ int descriptors_static(const StepArgs& A, float* G) {
   const gnep_nlist* nl = A.nl;
   const int64_t N = nl->n_atoms;
   const int64_t fr = N * C::NS * C::KR;
-  const int64_t sa = N * C::NQA * NLM;
+  const int64_t sa = N * C::NQA * C::NLX;
   const int64_t fr_padded = (fr + 63) / 64 * 64;
   if (fr_padded + sa > (int64_t)kStaticScratchFloats)
     return set_error(GNEP_ERR_INVALID_ARG,
@@ -1480,7 +1461,11 @@ int descriptors_static(const StepArgs& A, float* G) {
   // array needs no clearing between calls.
   k_desc_radial<C><<<blocks_for(N * RL, 128), 128, 0, A.st>>>((int)N, dm, nl->type, nl->L[0].off, nl->L[0].rij,
                                                               scratch, G);
-  if ((rc = launch_ang<C, false>(m, nl, A.st, nullptr, nullptr, nullptr, scratch + fr_padded, G, nullptr))) return rc;
+  if constexpr (C::LMAX > 4) {
+    if ((rc = hi_desc_angular<C>(m, nl, A.st, scratch + fr_padded, G))) return rc;
+  } else {
+    if ((rc = launch_ang<C, false>(m, nl, A.st, nullptr, nullptr, nullptr, scratch + fr_padded, G, nullptr))) return rc;
+  }
   GNEP_CHECK_LAUNCH("descriptor sweep (static scratch)");
   return GNEP_OK;
 }
@@ -1489,8 +1474,9 @@ int descriptors_static(const StepArgs& A, float* G) {
 
 int run_descriptors_static(const StepArgs& A, float* G) {
   const Shape& s = A.m->shape;
-#define X(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB) \
-  if (GNEP_MATCH(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB)) return descriptors_static<Sh<P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB>>(A, G);
+#define X(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB, P_LM) \
+  if (GNEP_MATCH(P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB, P_LM)) \
+    return descriptors_static<Sh<P_NS, P_NQR, P_KR, P_NQA, P_KA, P_FB, P_LM>>(A, G);
   GNEP_SHAPES(X)
 #undef X
   return set_error(GNEP_ERR_UNSUPPORTED, "no kernel for this shape");

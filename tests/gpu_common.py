@@ -13,6 +13,10 @@ SHAPES = {
                              dict(n_max=(8, 8), basis=(12, 12), hidden=50, four_body=True)),
     "nmax8_basis12_h100": (O.Cfg(nq_r=9, nq_a=9, k_r=13, k_a=13, hidden=100, four_body=False),
                            dict(n_max=(8, 8), basis=(12, 12), hidden=100, four_body=False)),
+    "nmax4_basis8_lmax6_h30": (O.Cfg(nq_r=5, nq_a=5, k_r=9, k_a=9, hidden=30, four_body=False, l_max=6),
+                               dict(n_max=(4, 4), basis=(8, 8), hidden=30, four_body=False, l_max=6)),
+    "nmax4_basis8_lmax8_4b_h30": (O.Cfg(nq_r=5, nq_a=5, k_r=9, k_a=9, hidden=30, four_body=True, l_max=8),
+                                  dict(n_max=(4, 4), basis=(8, 8), hidden=30, four_body=True, l_max=8)),
 }
 
 

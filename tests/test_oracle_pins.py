@@ -77,16 +77,17 @@ def _unit(rng):
 
 
 def test_blm_addition_theorem(oracle):
-    """sum_m C_lm B_lm(u) B_lm(v) = P_l(u.v) and sum_m C_lm B_lm(u)^2 = 1."""
-    C = oracle.clm()
+    """sum_m C_lm B_lm(u) B_lm(v) = P_l(u.v) and sum_m C_lm B_lm(u)^2 = 1, for
+    every l = 1..8 (B1-B8 with the C_lm reading)."""
+    C = oracle.clm(8)
     rng = np.random.default_rng(0)
-    first = [0, 3, 8, 15, 24]
+    first = [l * l - 1 for l in range(1, 10)]
     for _ in range(20):
         u, v = _unit(rng), _unit(rng)
         r1, r2 = rng.uniform(0.5, 5), rng.uniform(0.5, 5)
-        Bu, _ = oracle.blm(u * r1)
-        Bv, _ = oracle.blm(v * r2)
-        for l in range(1, 5):
+        Bu, _ = oracle.blm(u * r1, 8)
+        Bv, _ = oracle.blm(v * r2, 8)
+        for l in range(1, 9):
             s = slice(first[l - 1], first[l])
             P = legendre.legval(u @ v, [0] * l + [1])
             assert np.sum(C[s] * Bu[s] * Bv[s]) == pytest.approx(P, abs=1e-12)
@@ -99,13 +100,13 @@ def test_blm_gradient_fd_and_homogeneity(oracle):
     h = 1e-6
     for _ in range(10):
         d = rng.normal(size=3) * 2
-        B, dB = oracle.blm(d)
+        B, dB = oracle.blm(d, 8)
         for c in range(3):
             e = np.zeros(3); e[c] = h
-            fd = (oracle.blm(d + e)[0] - oracle.blm(d - e)[0]) / (2 * h)
-            np.testing.assert_allclose(dB[:, c], fd, rtol=1e-6, atol=1e-8)
-        B2, _ = oracle.blm(3.7 * d)
-        np.testing.assert_allclose(B, B2, atol=1e-12)
+            fd = (oracle.blm(d + e, 8)[0] - oracle.blm(d - e, 8)[0]) / (2 * h)
+            np.testing.assert_allclose(dB[:, c], fd, rtol=1e-6, atol=1e-7)
+        B2, _ = oracle.blm(3.7 * d, 8)
+        np.testing.assert_allclose(B, B2, atol=1e-11)
 
 
 def test_blm_printed_forms(oracle):
@@ -123,11 +124,15 @@ def test_blm_printed_forms(oracle):
 
 
 def _printed_blm():
-    """The 24 printed forms of the fixture as (index, equation, function of x, y, z, r)."""
+    """The 80 printed forms of the fixtures (B1.1-B4.9 and B5.1-B8.17) as
+    (index, equation, function of x, y, z, r)."""
     import ast
     import pathlib
     out = []
-    for line in (pathlib.Path(__file__).parent / "golden" / "blm_cartesian_l1_4.txt").read_text().splitlines():
+    gold = pathlib.Path(__file__).parent / "golden"
+    lines = (gold / "blm_cartesian_l1_4.txt").read_text().splitlines() + \
+        (gold / "blm_cartesian_l5_8.txt").read_text().splitlines()
+    for line in lines:
         if not line.strip() or line.startswith("#"):
             continue
         l, m, eq, expr = line.split(maxsplit=3)
@@ -141,20 +146,39 @@ def _printed_blm():
 
 
 def test_blm_all_printed_forms_of_appendix_b(oracle):
-    """All 24 printed b_lm of App. B (B1.1-B4.9, fixture tests/golden/blm_cartesian_l1_4.txt):
-    the oracle's components, in its (l, m) order, equal the printed forms at unit
+    """All 80 printed b_lm of App. B (B1.1-B8.17, fixtures
+    tests/golden/blm_cartesian_l1_4.txt and blm_cartesian_l5_8.txt): the
+    oracle's components, in its (l, m) order, equal the printed forms at unit
     vectors, and, by homogeneity of degree l, |d|^l times them at any vector d."""
     forms = _printed_blm()
-    assert sorted(q for q, _, _ in forms) == list(range(24))
+    assert sorted(q for q, _, _ in forms) == list(range(80))
     rng = np.random.default_rng(8)
     for d in rng.standard_normal((12, 3)) * rng.uniform(0.5, 3.0, (12, 1)):
-        B, _ = oracle.blm(d)
+        B, _ = oracle.blm(d, 8)
         r = float(np.linalg.norm(d))
         u = d / r
         for q, eq, f in forms:
             l = int(np.floor(np.sqrt(q + 1)))
             assert B[q] == pytest.approx(f(*u, 1.0), rel=1e-12, abs=1e-12), eq
-            assert r ** l * B[q] == pytest.approx(f(*d, r), rel=1e-11, abs=1e-11), eq
+            assert r ** l * B[q] == pytest.approx(f(*d, r), rel=1e-11, abs=1e-11 * r ** l), eq
+
+
+def test_clm_normalisation_closed_forms(oracle):
+    """The quadrature behind C_lm reproduces the l <= 4 values, and for m = 0,
+    where b_l0(u) = k_l P_l(u_z) with k_l the ratio of the printed leading
+    coefficient of z^l to the Legendre one (2l)! / (2^l l!^2),
+    C_l0 = 1 / k_l^2 (the addition theorem at u = v = z-axis)."""
+    from math import factorial
+    C = oracle.clm(8)
+    for q in range(24):
+        assert oracle.clm_quadrature(q) == pytest.approx(C[q], rel=1e-13)
+    lead = {1: 1, 2: 3, 3: 5, 4: 35, 5: 63, 6: 231, 7: 429, 8: 6435}  # printed coefficient of z^l (B1.1-B8.1)
+    for l in range(1, 9):
+        # the printed b_l0 at u = z-axis: the sum of its z, r^2 coefficients
+        B, _ = oracle.blm(np.array([0.0, 0.0, 1.0]), 8)
+        k = B[l * l - 1]  # = k_l P_l(1) = k_l
+        assert k == pytest.approx(lead[l] / (factorial(2 * l) / (2 ** l * factorial(l) ** 2)), rel=1e-14)
+        assert C[l * l - 1] == pytest.approx(1.0 / k ** 2, rel=1e-13)
 
 
 # ---------------------------------------------------------------- Eq. 2
@@ -207,10 +231,12 @@ def test_neighbor_counts_density(oracle):
 
 # ---------------------------------------------------------------- Eqs. 5-8
 
-def test_q_nl_legendre_double_sum(oracle):
-    """Eqs. 7-8 with the addition theorem: q_nl = sum_jk g_n g_n P_l(cos t_jik)."""
+@pytest.mark.parametrize("l_max", [4, 6, 8])
+def test_q_nl_legendre_double_sum(oracle, l_max):
+    """Eqs. 7-8 with the addition theorem: q_nl = sum_jk g_n g_n P_l(cos t_jik),
+    for l up to l_max."""
     O = oracle
-    cfg = small_cfg(O)
+    cfg = small_cfg(O, l_max=l_max)
     b = small_batch()
     P = synth.uniform_params(cfg.n_params, 3).astype(np.float64)
     G = O.descriptors(cfg, P, b)
@@ -230,9 +256,9 @@ def test_q_nl_legendre_double_sum(oracle):
         vecs, gs = np.array(vecs), np.array(gs)
         cos = vecs @ vecs.T
         for n in range(cfg.nq_a):
-            for l in range(1, 5):
+            for l in range(1, l_max + 1):
                 ref = np.sum(np.outer(gs[:, n], gs[:, n]) * legendre.legval(cos, [0] * l + [1]))
-                assert G[i, cfg.nq_r + n * 4 + l - 1] == pytest.approx(ref, rel=1e-10, abs=1e-13)
+                assert G[i, cfg.nq_r + n * l_max + l - 1] == pytest.approx(ref, rel=1e-10, abs=1e-12)
 
 
 def test_four_body_triple_sum_and_rotation(oracle):
@@ -344,11 +370,11 @@ def test_ann_derivatives_fd(oracle):
 
 # ---------------------------------------------------------------- Eqs. 1, 3, 4
 
-@pytest.mark.parametrize("four_body", [False, True])
-def test_forces_are_minus_energy_gradient(oracle, four_body):
+@pytest.mark.parametrize("four_body,l_max", [(False, 4), (True, 4), (False, 8)])
+def test_forces_are_minus_energy_gradient(oracle, four_body, l_max):
     """Eq. 3: F = -dE/dr (central differences, h = 1e-5 A) and sum F = 0."""
     O = oracle
-    cfg = small_cfg(O, four_body=four_body)
+    cfg = small_cfg(O, four_body=four_body, l_max=l_max)
     b = small_batch()
     P = synth.uniform_params(cfg.n_params, 3).astype(np.float64)
     s = O.descriptor_scale(cfg, P, b)
@@ -414,11 +440,12 @@ def _labels(O, cfg, b, s, **kw):
     return O.teacher_labels(cfg, teacher, s, b, **kw)
 
 
-@pytest.mark.parametrize("four_body,form", [(False, 0), (True, 0), (True, 1)])
-def test_gradient_matches_finite_differences(oracle, four_body, form):
+@pytest.mark.parametrize("four_body,form,l_max", [(False, 0, 4), (True, 0, 4), (True, 1, 4), (True, 0, 6),
+                                                  (False, 0, 8)])
+def test_gradient_matches_finite_differences(oracle, four_body, form, l_max):
     """dL/dtheta by the explicit App. C/D route vs central FD of the loss (h = 1e-5)."""
     O = oracle
-    cfg = small_cfg(O, four_body=four_body)
+    cfg = small_cfg(O, four_body=four_body, l_max=l_max)
     b = small_batch()
     P = synth.uniform_params(cfg.n_params, 3).astype(np.float64)
     s = O.descriptor_scale(cfg, P, b)
