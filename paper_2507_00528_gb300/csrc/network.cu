@@ -21,8 +21,10 @@
 // tile's atoms: after the per-atom phase alpha and -beta are in shared memory
 // and each thread accumulates 4 x 4 blocks of dW0 in registers across all
 // tiles of one species, from four 16-byte loads per atom (alpha, -beta, s.G,
-// s.Gdot).  db0 and dw1 are sums over atoms formed by shuffles within each
-// half-warp and kept per warp in shared memory.
+// s.Gdot).  db0 and dw1 are column sums of alpha and of e x - (1 - x^2) zdot
+// over the tile's atoms, taken from shared memory in the same phase (hidden
+// widths up to 64; above that the rows would not fit and the sums are formed
+// by shuffles within each half-warp in the per-atom phase).
 #include <cstdio>
 
 #include "gnep_internal.h"
@@ -122,25 +124,25 @@ __device__ __forceinline__ float dot_row(const float (&x)[DW], const float4* w, 
   return (s0 + s1) + (s2 + s3);
 }
 
-// Two dot products with the same weight row, two chains each.
+// Two dot products with the same weight row, four chains each.
 template <int DW>
 __device__ __forceinline__ void dot_row2(const float (&x)[DW], const float (&y)[DW], const float4* w, float init,
                                          float& zx, float& zy) {
-  float a0 = init, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+  float a0 = init, a1 = 0.f, a2 = 0.f, a3 = 0.f, b0 = 0.f, b1 = 0.f, b2 = 0.f, b3 = 0.f;
 #pragma unroll
   for (int v4 = 0; v4 < DW / 4; ++v4) {
     const float4 t = w[v4];
     a0 = fmaf(x[4 * v4], t.x, a0);
     a1 = fmaf(x[4 * v4 + 1], t.y, a1);
-    a0 = fmaf(x[4 * v4 + 2], t.z, a0);
-    a1 = fmaf(x[4 * v4 + 3], t.w, a1);
+    a2 = fmaf(x[4 * v4 + 2], t.z, a2);
+    a3 = fmaf(x[4 * v4 + 3], t.w, a3);
     b0 = fmaf(y[4 * v4], t.x, b0);
     b1 = fmaf(y[4 * v4 + 1], t.y, b1);
-    b0 = fmaf(y[4 * v4 + 2], t.z, b0);
-    b1 = fmaf(y[4 * v4 + 3], t.w, b1);
+    b2 = fmaf(y[4 * v4 + 2], t.z, b2);
+    b3 = fmaf(y[4 * v4 + 3], t.w, b3);
   }
-  zx = a0 + a1;
-  zy = b0 + b1;
+  zx = (a0 + a1) + (a2 + a3);
+  zy = (b0 + b1) + (b2 + b3);
 }
 
 // acc += c * (weight row)
@@ -244,8 +246,8 @@ template <int D, int HP>
 size_t mlp_bwd_smem(int H) {
   constexpr int DW = RowW<D>::DW;
   const int H2 = h_even(H), HR = h_row(H);
-  return sizeof(float) * ((size_t)H2 * DW + 2 * (size_t)TA * DW + 2 * (size_t)TA * HR + 2 * H2 + DW +
-                          2 * (size_t)NW * HP + TA);
+  const size_t rows = HP <= 64 ? 3 * (size_t)TA * HR : 2 * (size_t)TA * HR + 2 * (size_t)NW * HP;
+  return sizeof(float) * ((size_t)H2 * DW + 2 * (size_t)TA * DW + rows + 2 * H2 + DW + TA);
 }
 
 // Tangent and reverse pass, persistent over tiles, with e_i the energy residual
@@ -272,18 +274,21 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_bwd_row(Tiles T, int ntiles, DevM
   float* SD = SG + TA * DW;                  // [TA][DW] s.Gdot
   float* Al = SD + TA * DW;                  // [TA][HR] alpha
   float* Be = Al + TA * HR;                  // [TA][HR] -beta
-  float* b0 = Be + TA * HR;                  // [H2]
+  constexpr bool kRows = HP <= 64;          // column sums from shared rows (else per-warp shuffles)
+  float* Q1 = Be + TA * HR;                  // [TA][HR] e_i x - (1 - x^2) zdot (kRows)
+  float* wdw1 = Q1;                          // [NW][HP] per-warp sums over atoms (!kRows)
+  float* wdb0 = wdw1 + NW * HP;              // [NW][HP] (!kRows)
+  float* b0 = Q1 + (kRows ? TA * HR : 2 * NW * HP);  // [H2]
   float* w1 = b0 + H2;                       // [H2]
   float* sc = w1 + H2;                       // [DW]
-  float* wdw1 = sc + DW;                     // [NW][HP] per-warp sums over atoms
-  float* wdb0 = wdw1 + NW * HP;              // [NW][HP]
-  float* ev = wdb0 + NW * HP;                // [TA] e_i of the tile's atoms
+  float* ev = sc + DW;                       // [TA] e_i of the tile's atoms
   __shared__ int rows[TA];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int a = 16 * warp + (lane & 15), half = lane >> 4;
   for (int v = tid; v < DW; v += NT) sc[v] = v < D ? dm.scale[v] : 0.f;
-  for (int q = tid; q < 2 * TA * HR; q += NT) Al[q] = 0.f;  // Be follows Al
+  for (int q = tid; q < 2 * TA * HR + (kRows ? TA * HR : 0); q += NT) Al[q] = 0.f;  // Be, Q1 follow Al
   float acc[NBK][4][4];
+  float cdb0 = 0.f, cdw1 = 0.f;  // column sums of hidden unit tid (tid < H2)
   float cb1 = 0.f;
   int cur_e = -1;
 
@@ -294,7 +299,9 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_bwd_row(Tiles T, int ntiles, DevM
       for (int u = 0; u < 4; ++u)
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[k][u][c] = 0.f;
-    for (int q = tid; q < 2 * NW * HP; q += NT) wdw1[q] = 0.f;  // wdb0 follows wdw1
+    cdb0 = cdw1 = 0.f;
+    if constexpr (!kRows)
+      for (int q = tid; q < 2 * NW * HP; q += NT) wdw1[q] = 0.f;  // wdb0 follows wdw1
     cb1 = 0.f;
   };
   auto flush = [&](int e) {  // after a barrier that follows the last tile of species e
@@ -311,14 +318,21 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_bwd_row(Tiles T, int ntiles, DevM
           if (mu < H && v < D) out[mu * D + v] = acc[k][u][c];
         }
     }
-    for (int mu = tid; mu < H; mu += NT) {
-      float s0 = 0.f, s1 = 0.f;
-      for (int w = 0; w < NW; ++w) {  // warps in order
-        s0 += wdb0[w * HP + mu];
-        s1 += wdw1[w * HP + mu];
+    if constexpr (kRows) {
+      if (tid < H) {
+        out[D * H + tid] = cdb0;
+        out[D * H + H + tid] = cdw1;
       }
-      out[D * H + mu] = s0;
-      out[D * H + H + mu] = s1;
+    } else {
+      for (int mu = tid; mu < H; mu += NT) {
+        float s0 = 0.f, s1 = 0.f;
+        for (int w = 0; w < NW; ++w) {  // warps in order
+          s0 += wdb0[w * HP + mu];
+          s1 += wdw1[w * HP + mu];
+        }
+        out[D * H + mu] = s0;
+        out[D * H + H + mu] = s1;
+      }
     }
     if (tid == 0) out[D * H + 2 * H] = cb1;
   };
@@ -345,7 +359,7 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_bwd_row(Tiles T, int ntiles, DevM
     if (tid == 0)
       for (int r = 0; r < na; ++r) cb1 += ev[r];
     __syncthreads();
-    // per atom: z, zdot, alpha, -beta, Gbar; column sums of alpha and q1 per half-warp
+    // per atom: z, zdot, alpha, -beta, q1 and Gbar
     float gb[DW];
     {
       float g[DW], gd[DW];
@@ -362,19 +376,23 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_bwd_row(Tiles T, int ntiles, DevM
         const float t1 = 1.f - x * x;
         const float beta = w1[mu] * t1;
         const float alpha = ea * beta + 2.f * x * beta * zd;
-        float q1 = ea * x - t1 * zd;  // zero for padding atoms (e = 0, zdot = 0) and the padding unit
         Al[a * HR + mu] = alpha;
         Be[a * HR + mu] = -beta;
+        float q1 = ea * x - t1 * zd;  // zero for padding atoms (e = 0, zdot = 0) and the padding unit
         axpy_row<DW>(gb, alpha, wr);
-        float as = alpha;
+        if constexpr (kRows) {
+          Q1[a * HR + mu] = q1;
+        } else {
+          float as = alpha;
 #pragma unroll
-        for (int o = 1; o < 16; o <<= 1) {
-          as += __shfl_xor_sync(0xffffffffu, as, o);
-          q1 += __shfl_xor_sync(0xffffffffu, q1, o);
-        }
-        if ((lane & 15) == 0) {
-          wdb0[warp * HP + mu] += as;
-          wdw1[warp * HP + mu] += q1;
+          for (int o = 1; o < 16; o <<= 1) {
+            as += __shfl_xor_sync(0xffffffffu, as, o);
+            q1 += __shfl_xor_sync(0xffffffffu, q1, o);
+          }
+          if ((lane & 15) == 0) {
+            wdb0[warp * HP + mu] += as;
+            wdw1[warp * HP + mu] += q1;
+          }
         }
       }
     }
@@ -386,6 +404,7 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_bwd_row(Tiles T, int ntiles, DevM
     for (int k = 0; k < NBK; ++k) {
       const int q = tid + k * NT, mb = q / NVB, vb = q % NVB;
       if (q >= (HP / 4) * NVB || 4 * mb >= H2) continue;
+#pragma unroll 4
       for (int r = 0; r < na; ++r) {
         const float4 al = *reinterpret_cast<const float4*>(Al + r * HR + 4 * mb);
         const float4 be = *reinterpret_cast<const float4*>(Be + r * HR + 4 * mb);
@@ -398,6 +417,15 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_bwd_row(Tiles T, int ntiles, DevM
 #pragma unroll
           for (int c = 0; c < 4; ++c) acc[k][u][c] = fmaf(av[u], gv[c], fmaf(bv[u], dv[c], acc[k][u][c]));
       }
+    }
+    if (kRows && tid < H2) {  // db0, dw1: sums over the tile's atoms in order
+      float s0 = 0.f, s1 = 0.f;
+      for (int r = 0; r < na; ++r) {
+        s0 += Al[r * HR + tid];
+        s1 += Q1[r * HR + tid];
+      }
+      cdb0 += s0;
+      cdw1 += s1;
     }
     __syncthreads();  // s.G rows are no longer read: they take the Gbar rows
     if (half == 0) {
