@@ -835,6 +835,29 @@ def report_batch_size(args):
     print(json.dumps(line), flush=True)
 
 
+def report_step(args):
+    """A driver for profiler captures: the benchmark model and batch, then
+    `--steps` loss + gradient evaluations in `--precision` (no timing, no
+    graph), so that a capture sees the step's kernels in order."""
+    import torch
+    from paper_2507_00528_gb300 import build as gbuild
+    gbuild.build()
+    from paper_2507_00528_gb300 import gnep, synth
+    batch = synth.make_config(2)
+    teacher = gnep.GNEP(**MODEL_KW, seed=12)
+    nl = teacher.neighbors(gnep.DeviceBatch.from_host(batch))
+    teacher.compute_scale(nl)
+    y = teacher.teacher_labels(nl, batch.sizes(), **LAMBDAS)
+    m = gnep.GNEP(**MODEL_KW, seed=11, precision=args.precision)
+    m.set_scale(teacher.get_scale())
+    for _ in range(args.steps):
+        m.loss_grad(nl, y)
+    torch.cuda.synchronize()
+    m.sync_status()
+    print(json.dumps({"report": "step", "precision": args.precision, "evaluations": args.steps,
+                      "n_atoms": batch.n_atoms, "source_sha": csrc_sha()}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -847,7 +870,7 @@ def main():
                     help="times the K timed steps are repeated (the median repeat is reported)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--report", choices=["precision", "epoch", "batch-size"], default=None,
+    ap.add_argument("--report", choices=["precision", "epoch", "batch-size", "step"], default=None,
                     help="a workload report instead of the headline line")
     ap.add_argument("--epochs", type=int, default=20)
     args = ap.parse_args()
@@ -859,6 +882,8 @@ def main():
         report_epoch(args)
     elif args.report == "batch-size":
         report_batch_size(args)
+    elif args.report == "step":
+        report_step(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

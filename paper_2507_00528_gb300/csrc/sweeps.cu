@@ -39,7 +39,7 @@ namespace gnep {
 
 constexpr int RL = 4;           // lanes per atom in radial sweeps
 constexpr int CH = 128;         // pairs per geometry chunk
-constexpr int kCgBlocks = 2 * 152;  // persistent blocks of the c-gradient sweep (2 per SM of 152)
+constexpr int kCgBlocksPerSm = 2;  // default persistent blocks of the c-gradient sweep per SM
 
 // Angular thread map: TPA threads per atom, NPT channels per thread.
 template <int NQ, int NPT>
@@ -454,7 +454,9 @@ __device__ __forceinline__ void pair_geometry(Geo& g, int slot, float4 r, float3
 //   dL/dc^A_nk^{IJ} += P_n f_k + R_n fu_k,
 // and each atom contributes dL/dc^R_nk^{IJ} += Gbar_n FR[J][k] - E'_n FRd[J][k].
 //
-// Angular part: one warp per atom.  For 8 of the atom's pairs at a time,
+// Angular part: one warp per atom, blocks of 4 warps (two per SM: the split
+// products take over 200 registers, and two blocks let one block's tile
+// barriers overlap the other's products).  For 8 of the atom's pairs at a time,
 //   [P | R] = [Sbar | Sdbar] [B D; D 0 ... ]  as three products of K = 24:
 //        P = Sbar B + Sdbar D,  R = Sdbar B            (16 x 24) (24 x 8)
 //   acc^{IJ} += P_J F^T + R_J Fu^T                       (16 x 8) (8 x 16)
@@ -475,7 +477,7 @@ __device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
 }
 
 constexpr int kAS = 2 * NLM + 4;  // row stride of [Sbar | Sdbar] (20 mod 32 words: conflict-free A fragments)
-constexpr int kCgWarps = 8;       // warps 0-3 build the pair geometry while warps 4-7 build the atom rows
+constexpr int kCgWarps = 4;       // per block; two blocks per SM, so one block's barriers overlap the other's work
 
 template <class C>
 struct CgSmem {
@@ -506,7 +508,7 @@ __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
 }
 
 template <class C, bool SPLIT>
-__global__ void __launch_bounds__(32 * kCgWarps, SPLIT ? 1 : 2)
+__global__ void __launch_bounds__(32 * kCgWarps, 2)
     k_cgrad_ang(int ntile, const int* __restrict__ tiles, DevModel dm, const int* __restrict__ type,
                 const int* __restrict__ off, const float4* __restrict__ rij, const float4* __restrict__ wij,
                 const float* __restrict__ Sang, const float* __restrict__ Sdd, const float* __restrict__ Gb,
@@ -557,9 +559,10 @@ __global__ void __launch_bounds__(32 * kCgWarps, SPLIT ? 1 : 2)
     const int i0n = nt < ntile ? tiles[nt] : 0, i1n = nt < ntile ? tiles[nt + 1] : 0;
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();  // the previous tile's readers are done and this tile's rows are staged
-    if (tid >= 128) {
-      // atom rows [Sbar | Sdbar], one thread per (atom, channel)
-      const int u = tid - 128, at = u / NQA, n = u % NQA, i = i0 + at;
+    {
+      // atom rows [Sbar | Sdbar], one thread per (atom, channel), before the
+      // chunk's geometry (separate shared arrays; one barrier covers both)
+      const int u = tid, at = u / NQA, n = u % NQA, i = i0 + at;
       if (at < NA && i < i1) {
         const float4* S4 = reinterpret_cast<const float4*>(&sm.stS[(at * NQA + n) * NLM]);
         const float4* D4 = reinterpret_cast<const float4*>(&sm.stD[(at * NQA + n) * NLM]);
@@ -1382,7 +1385,14 @@ int run_backward(const StepArgs& A) {
 // (or tuned) count, at most kCgBlocksMax (the size of the partial buffer).
 int cgrad_blocks(const gnep_nlist* nl) {
   const int ntiles = nl->natile[1];
-  int cap = nl->tune.cg_blocks > 0 ? nl->tune.cg_blocks : kCgBlocks;
+  static int sms = 0;  // SMs of this GPU (looked up once)
+  if (!sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms < 1)
+      sms = 1;
+  }
+  int cap = nl->tune.cg_blocks > 0 ? nl->tune.cg_blocks : kCgBlocksPerSm * sms;
   if (cap > kCgBlocksMax) cap = kCgBlocksMax;
   return ntiles < cap ? (ntiles > 0 ? ntiles : 1) : cap;
 }
