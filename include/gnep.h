@@ -98,7 +98,10 @@ typedef struct {
  * rc_radial/angular cut-offs r_c^R, r_c^A (A), 0 < rc_angular <= rc_radial
  * n_max_*          descriptors per family are n_max + 1 (n = 0..n_max)
  * basis_*          basis functions per family are basis + 1 (k = 0..N_bas, Eq. 6)
- * l_max            angular degree, 4 in this build (B1-B4)
+ * l_max            angular degree, up to 8 (App. B: B1-B8).  Compiled shapes
+ *                  (n_max/basis both families, 4-body, l_max): 4/8 without
+ *                  4-body, l_max 4; 8/12 with and without 4-body, l_max 4; 4/8 no 4-body, l_max 6;
+ *                  4/8 with 4-body, l_max 8.  l_max > 4 runs the FP32 network only
  * four_body        0/1: add one tr(Q_n^3) descriptor per angular channel n
  * hidden           hidden neurons N_neu (<= 128)
  * seed             parameters are drawn U(-0.5, 0.5) from this seed

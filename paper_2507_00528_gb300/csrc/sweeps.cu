@@ -111,8 +111,11 @@ __global__ void __launch_bounds__(128) k_desc_radial(int N, DevModel dm, const i
     for (int k = 0; k < C::KR; ++k) acc[s][k] = 0.f;
   if (ok) {
     const int p1 = off[i + 1];
-    for (int p = off[i] + lane; p < p1; p += RL) {
-      const float4 r = rij[p];
+    int p = off[i] + lane;
+    float4 rn = p < p1 ? rij[p] : make_float4(1.f, 0.f, 0.f, 0.f);  // the pair after the current one
+    for (; p < p1; p += RL) {
+      const float4 r = rn;
+      if (p + RL < p1) rn = rij[p + RL];
       const float rr = sqrtf(r.x * r.x + r.y * r.y + r.z * r.z);
       float f[C::KR];
       radial_basis<C::KR>(rr, dm.rcr_inv, f);
@@ -362,9 +365,16 @@ __global__ void __launch_bounds__(128) k_tangent_radial(int N, DevModel dm, cons
 #pragma unroll
     for (int q = 0; q < 6; ++q) b[q] = Bs[6 * atom_struct[i] + q];
     const int p1 = off[i + 1];
-    for (int p = off[i] + lane; p < p1; p += RL) {
-      const float4 r = rij[p];
-      const float4 aj = a[jj[p]];
+    int p = off[i] + lane;
+    // the pair after the current one, and its neighbour's tangent
+    float4 rn = p < p1 ? rij[p] : make_float4(1.f, 0.f, 0.f, 0.f);
+    float4 an = p < p1 ? a[jj[p]] : ai;
+    for (; p < p1; p += RL) {
+      const float4 r = rn, aj = an;
+      if (p + RL < p1) {
+        rn = rij[p + RL];
+        an = a[jj[p + RL]];
+      }
       const float3 br = sym_apply(b, make_float3(r.x, r.y, r.z));
       const float ux = aj.x - ai.x + br.x, uy = aj.y - ai.y + br.y, uz = aj.z - ai.z + br.z;
       const float rr = sqrtf(r.x * r.x + r.y * r.y + r.z * r.z);
