@@ -835,6 +835,68 @@ def report_batch_size(args):
     print(json.dumps(line), flush=True)
 
 
+def report_small_batch(args):
+    """Latency of one training step at small batches (the paper trains one
+    structure per step by default): for B structures (`--batches`, default 1,
+    4, 16 and 64) of the 256-structure workload, the graph-replayed step time (`--steps` replays
+    after `--warmup`) and each kernel's time from the library's per-stage
+    events, with their sum beside the step; then the step time with each
+    radial lane count and each network tile size forced (the others at their
+    defaults), to check the default launch-shape rule."""
+    import torch
+    from paper_2507_00528_gb300 import build as gbuild
+    gbuild.build()
+    from paper_2507_00528_gb300 import gnep, synth
+    train = synth.make_config(2)
+    teacher = gnep.GNEP(**MODEL_KW, seed=12)
+    nl_all = teacher.neighbors(gnep.DeviceBatch.from_host(train))
+    teacher.compute_scale(nl_all)
+    scale = teacher.get_scale()
+    order = np.random.default_rng(5).permutation(train.n_struct)
+    out = {}
+    for B in [int(b) for b in args.batches.split(",")]:
+        sub = train.subset(sorted(order[:B]))
+        nl = teacher.neighbors(gnep.DeviceBatch.from_host(sub))
+        y = teacher.teacher_labels(nl, sub.sizes(), **LAMBDAS)
+        student = gnep.GNEP(**MODEL_KW, seed=11, precision=args.precision)
+        student.set_scale(scale)
+
+        def graph_ms():
+            gr = gnep.TrainGraph(student, nl, y, 1e-3, 1e-5, 10, args.steps + args.warmup)
+            for _ in range(args.warmup):
+                gr.launch()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.steps):
+                gr.launch()
+            e1.record()
+            torch.cuda.synchronize()
+            gr.close()
+            return e0.elapsed_time(e1) / args.steps
+
+        default = nl.tuning()
+        variants = {}
+        for key, vals in (("radial_lanes", (4, 8, 16)), ("net_tile_atoms", (32, 128))):
+            for v in vals:
+                nl.set_tuning({key: v})
+                variants[f"{key}={v}"] = round(graph_ms(), 4)
+        nl.set_tuning(None)
+        step_ms = graph_ms()
+        prof = {}
+        for _ in range(5):
+            for k, v in student_profile(student, nl, y, gnep):
+                prof[k] = prof.get(k, 0.0) + v / 5
+        student.sync_status()
+        out[str(B)] = {"atoms": int(sub.n_atoms), "ms_per_step": round(step_ms, 4),
+                       "default_shapes": {k: default[k] for k in ("radial_lanes", "net_tile_atoms")},
+                       "forced_shapes_ms_per_step": variants,
+                       "stage_ms": {k: round(v, 4) for k, v in prof.items()},
+                       "stage_sum_ms": round(sum(prof.values()), 4)}
+    print(json.dumps({"report": "small-batch", "workload": WORKLOAD["workload"], "precision": args.precision,
+                      "steps": args.steps, "by_batch_structures": out, "source_sha": csrc_sha()}), flush=True)
+
+
 def report_step(args):
     """A driver for profiler captures: the benchmark model and batch, then
     `--steps` loss + gradient evaluations in `--precision` (no timing, no
@@ -870,9 +932,11 @@ def main():
                     help="times the K timed steps are repeated (the median repeat is reported)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--report", choices=["precision", "epoch", "batch-size", "step"], default=None,
+    ap.add_argument("--report", choices=["precision", "epoch", "batch-size", "small-batch", "step"], default=None,
                     help="a workload report instead of the headline line")
     ap.add_argument("--epochs", type=int, default=20)
+    ap.add_argument("--batches", default="1,4,16,64",
+                    help="small-batch report: batch sizes in structures, comma separated")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -882,6 +946,8 @@ def main():
         report_epoch(args)
     elif args.report == "batch-size":
         report_batch_size(args)
+    elif args.report == "small-batch":
+        report_small_batch(args)
     elif args.report == "step":
         report_step(args)
     elif args.impl == "reference":

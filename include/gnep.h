@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define GNEP_ABI_VERSION 3
+#define GNEP_ABI_VERSION 4
 
 typedef enum {
   GNEP_OK = 0,
@@ -229,19 +229,28 @@ int gnep_loss_grad(gnep_model *m, const gnep_nlist *nl, const gnep_labels *y,
                    double *loss_terms, float *grad, void *stream);
 
 /* Autotuner.  Launch shapes are per batch: atoms and pairs per tile of the
- * descriptor and tangent sweeps' tiles and of the angular force and c-gradient
- * sweeps' tiles, the number of persistent blocks of the c-gradient sweep, and
- * the number of persistent blocks of the network kernels.  gnep_autotune times the loss + gradient evaluation of
- * this batch (median of `reps` runs, no parameter update) over candidate
- * values of each in turn and keeps the fastest in the neighbour list.  It
- * synchronizes `stream` and must not run during stream capture; graphs
- * captured earlier on this list are invalidated (gnep_graph_launch then
- * returns INVALID_ARG).  values [6] = {atoms per descriptor tile, pairs per
- * descriptor tile, atoms per force tile, pairs per force tile, c-gradient
- * blocks, network blocks (at most 456; 0 = one per tile up to the resident
- * capacity)}; gnep_tuning_set takes the same layout (0 = default) and
- * rebuilds the tiles.  Results agree with the untuned ones to FP32 summation order.
- * Errors: INVALID_ARG, CUDA, and those of gnep_loss_grad. */
+ * descriptor and tangent sweeps' tiles and of the angular force and
+ * c-gradient sweeps' tiles, the number of persistent blocks of the c-gradient
+ * sweep and of the network kernels, the lanes per atom of the radial sweeps,
+ * and the atoms per tile of the FP32 network.  gnep_autotune times the
+ * loss + gradient evaluation of this batch (median of `reps` runs, no
+ * parameter update) over candidate values of each in turn and keeps the
+ * fastest in the neighbour list.  It synchronizes `stream` and must not run
+ * during stream capture; graphs captured earlier on this list are invalidated
+ * (gnep_graph_launch then returns INVALID_ARG).  values [8] =
+ *   [0] atoms per descriptor tile   [1] pairs per descriptor tile
+ *   [2] atoms per force tile        [3] pairs per force tile
+ *   [4] c-gradient blocks (at most 608)
+ *   [5] network blocks (at most 456; 0 = one per tile up to the resident capacity)
+ *   [6] radial lanes per atom: 4, 8 or 16 (default: 4 while four 128-thread
+ *       blocks per SM are filled, more for smaller batches)
+ *   [7] atoms per FP32 network tile: 32 or 128 (default: 128 while the batch
+ *       has a tile per two SMs, else 32; the tensor-core modes always take 128).
+ * gnep_tuning_get gives the effective values; gnep_tuning_set takes the same
+ * layout (0 = default) and rebuilds the tiles.  Results agree with the
+ * untuned ones to FP32 summation order.
+ * Errors: INVALID_ARG (a value out of range), CUDA, and those of
+ * gnep_loss_grad. */
 int gnep_autotune(gnep_model *m, gnep_nlist *nl, const gnep_labels *y,
                   int reps, void *stream);
 int gnep_tuning_get(const gnep_model *m, const gnep_nlist *nl,

@@ -727,7 +727,7 @@ int gnep_graph_launch(gnep_graph* g, void* stream) {
 
 namespace {
 
-constexpr int kTuneKnobs = 6;  // na[0], ch[0], na[1], ch[1], cg_blocks, net_blocks
+constexpr int kTuneKnobs = 8;  // na[0], ch[0], na[1], ch[1], cg_blocks, net_blocks, radial_lanes, net_tile
 
 int* knob(gnep_nlist* nl, int k) {
   switch (k) {
@@ -736,7 +736,9 @@ int* knob(gnep_nlist* nl, int k) {
     case 2: return &nl->tune.na[1];
     case 3: return &nl->tune.ch[1];
     case 4: return &nl->tune.cg_blocks;
-    default: return &nl->tune.net_blocks;
+    case 5: return &nl->tune.net_blocks;
+    case 6: return &nl->tune.radial_lanes;
+    default: return &nl->tune.net_tile;
   }
 }
 
@@ -750,6 +752,9 @@ void effective_tuning(const gnep_model* m, const gnep_nlist* nl, int32_t* v) {
   }
   v[4] = cgrad_blocks(nl);
   v[5] = nl->tune.net_blocks;  // 0: one block per tile up to the resident capacity
+  v[6] = radial_lanes(nl);
+  // the tensor-core network modes always take 128-atom tiles
+  v[7] = (m->shape.lmax > 4 || m->precision == GNEP_PREC_FP32) ? net_tile_atoms(nl, m->shape.ns) : 128;
 }
 
 // Median over `reps` of one loss + gradient evaluation (no update), in ms.
@@ -793,6 +798,10 @@ int gnep_tuning_set(gnep_model* m, gnep_nlist* nl, const int32_t* values, void* 
   for (int k = 0; k < kTuneKnobs; ++k)
     if (values[k] < 0 || values[k] > (k == 4 ? kCgBlocksMax : k == 5 ? kNetBlocks : 1 << 20))
       return set_error(GNEP_ERR_INVALID_ARG, "tuning value out of range");
+  if (values[6] != 0 && values[6] != 4 && values[6] != 8 && values[6] != 16)
+    return set_error(GNEP_ERR_INVALID_ARG, "radial lanes per atom must be 4, 8 or 16 (or 0)");
+  if (values[7] != 0 && values[7] != 32 && values[7] != 128)
+    return set_error(GNEP_ERR_INVALID_ARG, "atoms per network tile must be 32 or 128 (or 0)");
   for (int k = 0; k < kTuneKnobs; ++k) *knob(nl, k) = values[k];
   ++nl->gen;
   if (nl->n_atoms == 0) return GNEP_OK;
@@ -813,7 +822,8 @@ int gnep_autotune(gnep_model* m, gnep_nlist* nl, const gnep_labels* y, int reps,
   const std::vector<std::vector<int>> cand = {
       {na0, na0 / 2, na0 / 4},  {64, 128, 256, 384, 512},
       {na1, na1 / 2, na1 / 4},  {32, 48, 64, 96, 128, 192},
-      {152, 304, 456, 608},     {0, 152, 304}};
+      {152, 304, 456, 608},     {0, 152, 304},
+      {4, 8, 16},               {32, 128}};
   for (int k = 0; k < kTuneKnobs; ++k) *knob(nl, k) = cur[k];
   ++nl->gen;
   if ((rc = build_angular_tiles(m, nl, st))) return rc;

@@ -92,9 +92,10 @@ struct gnep_nlist {
   int64_t atile_cap[2] = {0, 0};  // allocated tile-bound slots
   // Launch shapes chosen by gnep_autotune (0 = built-in default): atoms and
   // pairs per tile of each tile set, persistent blocks of the c-gradient sweep
-  // and of the network kernels.
+  // and of the network kernels, lanes per atom of the radial sweeps (4, 8, 16)
+  // and atoms per FP32 network tile (32, 128).
   struct Tuning {
-    int na[2] = {0, 0}, ch[2] = {0, 0}, cg_blocks = 0, net_blocks = 0;
+    int na[2] = {0, 0}, ch[2] = {0, 0}, cg_blocks = 0, net_blocks = 0, radial_lanes = 0, net_tile = 0;
   } tune;
   uint64_t gen = 0;  // bumped whenever lists or tiles change (captured graphs check it)
   std::vector<int> host_types;  // species of the last build (host copy)
@@ -175,6 +176,9 @@ int md_kick_drift(const gnep_nlist* nl, double* pos, double* vel, const double* 
                   cudaStream_t st);
 int md_kick(const gnep_nlist* nl, double* vel, const double* inv_mass, const float* F, double dt, cudaStream_t st);
 int cgrad_blocks(const gnep_nlist* nl);
+int sm_count();                                   // SMs of this GPU
+int radial_lanes(const gnep_nlist* nl);           // lanes per atom of the radial sweeps
+int net_tile_atoms(const gnep_nlist* nl, int ns); // atoms per FP32 network tile
 // Persistent blocks of a network kernel: `fit` (resident capacity, capped at the
 // tile count) or the tuned count, whichever is smaller.
 inline int net_blocks(const gnep_nlist* nl, int fit) {

@@ -1,21 +1,22 @@
 // Per-element one-hidden-layer network (D1.1-D1.10) in FP32 on the CUDA
 // cores, and its tangent/reverse pass (D1.18-D1.21 through the tangent/adjoint
-// route), over species-homogeneous tiles of 128 atoms of the species-grouped
-// atom order.  Persistent blocks keep one species' weights in shared memory
+// route), over species-homogeneous tiles of the species-grouped atom order:
+// 128 atoms per tile, or 32 for batches too small to give every SM a tile.  Persistent blocks keep one species' weights in shared memory
 // and walk the tiles.  Every sum runs in a fixed order (no atomics), so results
 // are bit-reproducible.
 //
-// Thread map: 256 threads, two per atom.  Lanes l and l ^ 16 of warp w take
-// atom 16 w + (l mod 16) and the two halves of the hidden units, so that each
-// thread's descriptor row (and, backward, its tangent row and the adjoint it
-// accumulates) lives in registers while the weight row of hidden unit mu is
-// read by 16-byte loads that the lanes of a half-warp share (one shared-memory
-// wavefront per load for the whole half).  For each mu a thread forms
-// z = W0_mu . (s.G) (interleaved partial sums), the element-wise terms and then
-// the rank-one update of E' (forward) or Gbar (backward) with the same row.
-// The hidden activations are recomputed in the backward pass instead of being
-// stored.  The halves are combined by one exchange between lanes l and l ^ 16
-// (commutative, so both lanes hold the same sum).
+// Thread map: 256 threads, G per atom (G = 2 for 128-atom tiles, 8 for 32).
+// With AW = 32 / G atoms per warp, lane l of warp w takes atom AW w + (l mod AW)
+// and part l / AW of the hidden units (the units padded to a multiple of G), so
+// that each thread's descriptor row (and, backward, its tangent row and the
+// adjoint it accumulates) lives in registers while the weight row of hidden
+// unit mu is read by 16-byte loads that the AW lanes of a part share.  For each
+// mu a thread forms z = W0_mu . (s.G) (interleaved partial sums), the
+// element-wise terms and then the rank-one update of E' (forward) or Gbar
+// (backward) with the same row.  The hidden activations are recomputed in the
+// backward pass instead of being stored.  The parts are combined by exchanges
+// between lanes l and l ^ AW, l ^ 2 AW, ... (a butterfly, so every part's lane
+// holds the same sum).
 //
 // The weight gradient dW0 += alpha^T (s.G) - beta^T (s.Gdot) contracts over the
 // tile's atoms: after the per-atom phase alpha and -beta are in shared memory
@@ -24,7 +25,7 @@
 // s.Gdot).  db0 and dw1 are column sums of alpha and of e x - (1 - x^2) zdot
 // over the tile's atoms, taken from shared memory in the same phase (hidden
 // widths up to 64; above that the rows would not fit and the sums are formed
-// by shuffles within each half-warp in the per-atom phase).
+// by shuffles over the lanes of each part in the per-atom phase).
 #include <cstdio>
 
 #include "gnep_internal.h"
@@ -34,10 +35,17 @@ namespace gnep {
 
 namespace {
 
-constexpr int TA = 128;  // atoms per tile
-constexpr int NT = 256;  // threads per block (two per atom)
+constexpr int NT = 256;  // threads per block
 constexpr int NW = NT / 32;
 
+// Tile of TA atoms: G = NT / TA threads per atom, AW = 32 / G atoms per warp.
+template <int TA>
+struct TileMap {
+  static_assert(TA == 32 || TA == 128, "network tiles hold 32 or 128 atoms");
+  static constexpr int G = NT / TA, AW = 32 / G;
+};
+
+template <int TA>
 __device__ __forceinline__ void tile_of(const Tiles& T, int t, int& e, int& a0, int& na) {
   e = 0;
   while (e + 1 < T.ns && t >= T.tbase[e + 1]) ++e;
@@ -45,23 +53,25 @@ __device__ __forceinline__ void tile_of(const Tiles& T, int t, int& e, int& a0, 
   na = min(TA, T.soff[e + 1] - a0);
 }
 
-// Row widths: descriptor rows padded to 16 bytes; hidden units padded to an
-// even count (the two halves take the same number of units; the padding unit
-// has zero weights) and the alpha / beta rows to a multiple of 4.
+// Row widths: descriptor rows padded to 16 bytes; hidden units padded to a
+// multiple of G (the parts take the same number of units; padding units have
+// zero weights) and the alpha / beta rows to a multiple of 4.
 template <int D>
 struct RowW {
   static constexpr int DW = (D + 3) / 4 * 4;
 };
-__host__ __device__ inline int h_even(int H) { return (H + 1) / 2 * 2; }
-__host__ __device__ inline int h_row(int H) { return (h_even(H) + 3) / 4 * 4; }
+template <int G>
+__host__ __device__ inline int h_even(int H) { return (H + G - 1) / G * G; }
+template <int G>
+__host__ __device__ inline int h_row(int H) { return (h_even<G>(H) + 3) / 4 * 4; }
 
 // Weights of species e: W [H2][DW] (row mu = W0_mu, zero beyond D and H),
 // b0, w1 [H2] (zero beyond H).
-template <int D>
+template <int D, int G>
 __device__ void load_weights(const DevModel& dm, int e, float* W, float* b0, float* w1) {
   constexpr int DW = RowW<D>::DW;
   const float* P = dm.params + (size_t)e * dm.net_size;
-  const int H = dm.H, H2 = h_even(H);
+  const int H = dm.H, H2 = h_even<G>(H);
   for (int q = threadIdx.x; q < H2 * DW; q += NT) {
     const int mu = q / DW, v = q % DW;
     W[q] = (v < D && mu < H) ? P[mu * D + v] : 0.f;
@@ -76,7 +86,7 @@ __device__ void load_weights(const DevModel& dm, int e, float* W, float* b0, flo
 // NA arrays at once: every thread issues all of its gathered loads before the
 // first store, so that a tile waits for one global-memory latency, not one per
 // element.
-template <int D, int NA>
+template <int D, int NA, int TA>
 __device__ __forceinline__ void stage_rows(const float* __restrict__ s0, const float* __restrict__ s1,
                                            const int* rows, const float* sc, float* R0, float* R1) {
   constexpr int DW = RowW<D>::DW, N = TA * DW, IT = (N + NT - 1) / NT;
@@ -160,23 +170,23 @@ __device__ __forceinline__ void axpy_row(float (&acc)[DW], float c, const float4
 
 }  // namespace
 
-template <int D, int NS, int NQR, int KR>
+template <int D, int NS, int NQR, int KR, int TA>
 size_t mlp_fwd_smem(int H) {
   constexpr int DW = RowW<D>::DW;
-  const int H2 = h_even(H);
+  const int H2 = h_even<TileMap<TA>::G>(H);
   return sizeof(float) * ((size_t)H2 * DW + (size_t)TA * DW + 2 * H2 + DW + NS * NQR * KR);
 }
 
 // Forward, persistent over tiles: z = W0 (s.G) + b0, x = tanh z, E = w1.x + b1,
 // E' = s . (W0^T (w1 (1 - x^2)))  (D1.1-D1.5), and the per-atom radial
 // contraction chat_i[J][k] = sum_n E'_n c^R_nk^{IJ} used by the force sweep.
-template <int D, int NS, int NQR, int KR>
+template <int D, int NS, int NQR, int KR, int TA>
 __global__ void __launch_bounds__(NT, 1) k_mlp_fwd_row(Tiles T, int ntiles, DevModel dm, const float* __restrict__ G,
                                                        float* __restrict__ Ep, float* __restrict__ Eatom,
                                                        float* __restrict__ chat) {
-  constexpr int DW = RowW<D>::DW, NJK = NS * KR;
+  constexpr int DW = RowW<D>::DW, NJK = NS * KR, GP = TileMap<TA>::G, AW = TileMap<TA>::AW;
   extern __shared__ float4 sm4[];
-  const int H = dm.H, H2 = h_even(H), Hh = H2 / 2;
+  const int H = dm.H, H2 = h_even<GP>(H), Hh = H2 / GP;
   float* W = reinterpret_cast<float*>(sm4);  // [H2][DW]
   float* R = W + H2 * DW;                    // [TA][DW] s.G, then the scaled E'
   float* b0 = R + TA * DW;                   // [H2]
@@ -185,40 +195,43 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_fwd_row(Tiles T, int ntiles, DevM
   float* cR = sc + DW;                       // [NS][NQR][KR] of the tile's species
   __shared__ int rows[TA];
   const int tid = threadIdx.x, lane = tid & 31;
-  const int a = 16 * (tid >> 5) + (lane & 15), half = lane >> 4;
+  const int a = AW * (tid >> 5) + (lane % AW), hpart = lane / AW;
   for (int v = tid; v < DW; v += NT) sc[v] = v < D ? dm.scale[v] : 0.f;
   int cur_e = -1;
   float b1 = 0.f;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     int e, a0, na;
-    tile_of(T, t, e, a0, na);
+    tile_of<TA>(T, t, e, a0, na);
     __syncthreads();  // the previous tile's readers of R, rows and the weights are done
     if (e != cur_e) {
-      load_weights<D>(dm, e, W, b0, w1);
+      load_weights<D, GP>(dm, e, W, b0, w1);
       for (int q = tid; q < NS * NQR * KR; q += NT) cR[q] = dm.params[dm.off_cR + e * NS * NQR * KR + q];
       b1 = dm.params[(size_t)e * dm.net_size + D * H + 2 * H];
       cur_e = e;
     }
     if (tid < TA) rows[tid] = tid < na ? T.perm[a0 + tid] : -1;
     __syncthreads();
-    stage_rows<D, 1>(G, nullptr, rows, sc, R, nullptr);
+    stage_rows<D, 1, TA>(G, nullptr, rows, sc, R, nullptr);
     __syncthreads();
     float g[DW], ep[DW];
     load_row<DW>(R + a * DW, g);
 #pragma unroll
     for (int v = 0; v < DW; ++v) ep[v] = 0.f;
     float E = 0.f;
-    for (int mu = half * Hh; mu < (half + 1) * Hh; ++mu) {
+    for (int mu = hpart * Hh; mu < (hpart + 1) * Hh; ++mu) {
       const float4* wr = reinterpret_cast<const float4*>(W + mu * DW);
       const float x = tanhf(dot_row<DW>(g, wr, b0[mu]));
       E = fmaf(w1[mu], x, E);
       axpy_row<DW>(ep, w1[mu] * (1.f - x * x), wr);
     }
 #pragma unroll
-    for (int v = 0; v < DW; ++v) ep[v] += __shfl_xor_sync(0xffffffffu, ep[v], 16);
-    E += __shfl_xor_sync(0xffffffffu, E, 16);
+    for (int o = AW; o < 32; o <<= 1) {
+#pragma unroll
+      for (int v = 0; v < DW; ++v) ep[v] += __shfl_xor_sync(0xffffffffu, ep[v], o);
+      E += __shfl_xor_sync(0xffffffffu, E, o);
+    }
     __syncthreads();  // every row of R has been read
-    if (half == 0 && a < na) {
+    if (hpart == 0 && a < na) {
       Eatom[rows[a]] = E + b1;
       float4* o = reinterpret_cast<float4*>(R + a * DW);
 #pragma unroll
@@ -242,10 +255,10 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_fwd_row(Tiles T, int ntiles, DevM
   }
 }
 
-template <int D, int HP>
+template <int D, int HP, int TA>
 size_t mlp_bwd_smem(int H) {
-  constexpr int DW = RowW<D>::DW;
-  const int H2 = h_even(H), HR = h_row(H);
+  constexpr int DW = RowW<D>::DW, GP = TileMap<TA>::G;
+  const int H2 = h_even<GP>(H), HR = h_row<GP>(H);
   const size_t rows = HP <= 64 ? 3 * (size_t)TA * HR : 2 * (size_t)TA * HR + 2 * (size_t)NW * HP;
   return sizeof(float) * ((size_t)H2 * DW + 2 * (size_t)TA * DW + rows + 2 * H2 + DW + TA);
 }
@@ -258,17 +271,17 @@ size_t mlp_bwd_smem(int H) {
 //   dw1 += e_i x - (1 - x^2) zdot, db1 += e_i.
 // Each block writes one partial per species it visited into
 // part[block][species] (zeroed beforehand).  HP: hidden width padded to 32, 64
-// or 128 (sets the dW0 blocks a thread owns).
-template <int D, int HP>
+// or 128 (sets the dW0 blocks a thread owns); TA: atoms per tile.
+template <int D, int HP, int TA>
 __global__ void __launch_bounds__(NT, 1) k_mlp_bwd_row(Tiles T, int ntiles, DevModel dm,
                                                        const int* __restrict__ atom_struct,
                                                        const float* __restrict__ es, const float* __restrict__ G,
                                                        const float* __restrict__ Gd, float* __restrict__ Gb,
                                                        float* __restrict__ part, int part_stride) {
-  constexpr int DW = RowW<D>::DW, NVB = DW / 4;
+  constexpr int DW = RowW<D>::DW, NVB = DW / 4, GP = TileMap<TA>::G, AW = TileMap<TA>::AW;
   constexpr int NBK = ((HP / 4) * NVB + NT - 1) / NT;  // dW0 4 x 4 blocks per thread
   extern __shared__ float4 sm4[];
-  const int H = dm.H, H2 = h_even(H), Hh = H2 / 2, HR = h_row(H);
+  const int H = dm.H, H2 = h_even<GP>(H), Hh = H2 / GP, HR = h_row<GP>(H);
   float* W = reinterpret_cast<float*>(sm4);  // [H2][DW]
   float* SG = W + H2 * DW;                   // [TA][DW] s.G, then the Gbar output rows
   float* SD = SG + TA * DW;                  // [TA][DW] s.Gdot
@@ -284,7 +297,7 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_bwd_row(Tiles T, int ntiles, DevM
   float* ev = sc + DW;                       // [TA] e_i of the tile's atoms
   __shared__ int rows[TA];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int a = 16 * warp + (lane & 15), half = lane >> 4;
+  const int a = AW * warp + (lane % AW), hpart = lane / AW;
   for (int v = tid; v < DW; v += NT) sc[v] = v < D ? dm.scale[v] : 0.f;
   for (int q = tid; q < 2 * TA * HR + (kRows ? TA * HR : 0); q += NT) Al[q] = 0.f;  // Be, Q1 follow Al
   float acc[NBK][4][4];
@@ -340,13 +353,13 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_bwd_row(Tiles T, int ntiles, DevM
 
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     int e, a0, na;
-    tile_of(T, t, e, a0, na);
+    tile_of<TA>(T, t, e, a0, na);
     __syncthreads();  // the previous tile is done with every shared array
     if (e != cur_e) {
       if (cur_e >= 0) flush(cur_e);
       __syncthreads();
       reset();
-      load_weights<D>(dm, e, W, b0, w1);
+      load_weights<D, GP>(dm, e, W, b0, w1);
       cur_e = e;
     }
     if (tid < TA) {
@@ -355,7 +368,7 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_bwd_row(Tiles T, int ntiles, DevM
       ev[tid] = r >= 0 ? es[atom_struct[r]] : 0.f;
     }
     __syncthreads();
-    stage_rows<D, 2>(G, Gd, rows, sc, SG, SD);
+    stage_rows<D, 2, TA>(G, Gd, rows, sc, SG, SD);
     if (tid == 0)
       for (int r = 0; r < na; ++r) cb1 += ev[r];
     __syncthreads();
@@ -368,7 +381,7 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_bwd_row(Tiles T, int ntiles, DevM
 #pragma unroll
       for (int v = 0; v < DW; ++v) gb[v] = 0.f;
       const float ea = ev[a];
-      for (int mu = half * Hh; mu < (half + 1) * Hh; ++mu) {
+      for (int mu = hpart * Hh; mu < (hpart + 1) * Hh; ++mu) {
         const float4* wr = reinterpret_cast<const float4*>(W + mu * DW);
         float z, zd;
         dot_row2<DW>(g, gd, wr, b0[mu], z, zd);
@@ -383,13 +396,13 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_bwd_row(Tiles T, int ntiles, DevM
         if constexpr (kRows) {
           Q1[a * HR + mu] = q1;
         } else {
-          float as = alpha;
+          float as = alpha;  // summed over the AW atoms of this part in the warp
 #pragma unroll
-          for (int o = 1; o < 16; o <<= 1) {
+          for (int o = 1; o < AW; o <<= 1) {
             as += __shfl_xor_sync(0xffffffffu, as, o);
             q1 += __shfl_xor_sync(0xffffffffu, q1, o);
           }
-          if ((lane & 15) == 0) {
+          if (lane % AW == 0) {
             wdb0[warp * HP + mu] += as;
             wdw1[warp * HP + mu] += q1;
           }
@@ -397,7 +410,9 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_bwd_row(Tiles T, int ntiles, DevM
       }
     }
 #pragma unroll
-    for (int v = 0; v < DW; ++v) gb[v] += __shfl_xor_sync(0xffffffffu, gb[v], 16);
+    for (int o = AW; o < 32; o <<= 1)
+#pragma unroll
+      for (int v = 0; v < DW; ++v) gb[v] += __shfl_xor_sync(0xffffffffu, gb[v], o);
     __syncthreads();  // alpha and -beta of the tile are complete
     // dW0 += alpha^T (s.G) - beta^T (s.Gdot) over the tile's atoms
 #pragma unroll
@@ -428,7 +443,7 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_bwd_row(Tiles T, int ntiles, DevM
       cdw1 += s1;
     }
     __syncthreads();  // s.G rows are no longer read: they take the Gbar rows
-    if (half == 0) {
+    if (hpart == 0) {
       float4* o = reinterpret_cast<float4*>(SG + a * DW);
 #pragma unroll
       for (int v4 = 0; v4 < DW / 4; ++v4)
@@ -474,25 +489,40 @@ int resident_blocks(K kern, size_t smem, int& out) {
 }
 }  // namespace
 
-template <int D, int HP, int NS, int NQR, int KR>
-int mlp_setup() {
+// Atoms per network tile: the tuned value, else 128 while the batch has at
+// least one such tile per two SMs, and 32 below (four times the tiles, each
+// with four times the threads per atom, so that small batches spread over more
+// SMs and each atom's hidden-unit loop is a quarter as long).
+int net_tile_atoms(const gnep_nlist* nl, int ns) {
+  if (nl->tune.net_tile > 0) return nl->tune.net_tile;
+  return 2 * make_tiles(nl, ns, 128).tbase[ns] >= sm_count() ? 128 : 32;
+}
+
+template <int D, int HP, int NS, int NQR, int KR, int TA>
+int mlp_setup_ta() {
   // shared memory for the largest hidden width of this padding
-  GNEP_CUDA(cudaFuncSetAttribute(k_mlp_fwd_row<D, NS, NQR, KR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)mlp_fwd_smem<D, NS, NQR, KR>(kMaxHidden)));
-  GNEP_CUDA(cudaFuncSetAttribute(k_mlp_bwd_row<D, HP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)mlp_bwd_smem<D, HP>(HP)));
-  GNEP_CUDA(cudaFuncSetAttribute(k_mlp_bwd_row<D, HP>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+  GNEP_CUDA(cudaFuncSetAttribute(k_mlp_fwd_row<D, NS, NQR, KR, TA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)mlp_fwd_smem<D, NS, NQR, KR, TA>(kMaxHidden)));
+  GNEP_CUDA(cudaFuncSetAttribute(k_mlp_bwd_row<D, HP, TA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)mlp_bwd_smem<D, HP, TA>(HP)));
+  GNEP_CUDA(cudaFuncSetAttribute(k_mlp_bwd_row<D, HP, TA>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   return GNEP_OK;
 }
 
 template <int D, int HP, int NS, int NQR, int KR>
-int mlp_forward(const gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
+int mlp_setup() {
+  if (int rc = mlp_setup_ta<D, HP, NS, NQR, KR, 128>()) return rc;
+  return mlp_setup_ta<D, HP, NS, NQR, KR, 32>();
+}
+
+template <int D, int NS, int NQR, int KR, int TA>
+int mlp_forward_ta(const gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
   const Tiles T = make_tiles(nl, NS, TA);
   const int ntiles = T.tbase[NS];
   if (ntiles == 0) return GNEP_OK;
   Workspace& w = nl->ws;
-  auto kern = k_mlp_fwd_row<D, NS, NQR, KR>;
-  const size_t smem = mlp_fwd_smem<D, NS, NQR, KR>(m->shape.H);
+  auto kern = k_mlp_fwd_row<D, NS, NQR, KR, TA>;
+  const size_t smem = mlp_fwd_smem<D, NS, NQR, KR, TA>(m->shape.H);
   int cap = 0;
   if (int rc = resident_blocks(kern, smem, cap)) return rc;
   const int grid = net_blocks(nl, ntiles < cap ? ntiles : cap);
@@ -501,14 +531,20 @@ int mlp_forward(const gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
   return GNEP_OK;
 }
 
-template <int D, int HP>
-int mlp_backward(const gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
+template <int D, int HP, int NS, int NQR, int KR>
+int mlp_forward(const gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
+  return net_tile_atoms(nl, NS) == 32 ? mlp_forward_ta<D, NS, NQR, KR, 32>(m, nl, st)
+                                      : mlp_forward_ta<D, NS, NQR, KR, 128>(m, nl, st);
+}
+
+template <int D, int HP, int TA>
+int mlp_backward_ta(const gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
   const int ns = m->shape.ns;
   const Tiles T = make_tiles(nl, ns, TA);
   const int ntiles = T.tbase[ns];
   Workspace& w = nl->ws;
-  auto kern = k_mlp_bwd_row<D, HP>;
-  const size_t smem = mlp_bwd_smem<D, HP>(m->shape.H);
+  auto kern = k_mlp_bwd_row<D, HP, TA>;
+  const size_t smem = mlp_bwd_smem<D, HP, TA>(m->shape.H);
   int cap = 0;
   if (int rc = resident_blocks(kern, smem, cap)) return rc;
   if (cap > kNetBlocks) cap = kNetBlocks;  // net_part holds kNetBlocks partials
@@ -520,6 +556,12 @@ int mlp_backward(const gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
                                m->net_size);
   GNEP_CHECK_LAUNCH("k_mlp_bwd_row");
   return GNEP_OK;
+}
+
+template <int D, int HP>
+int mlp_backward(const gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
+  return net_tile_atoms(nl, m->shape.ns) == 32 ? mlp_backward_ta<D, HP, 32>(m, nl, st)
+                                               : mlp_backward_ta<D, HP, 128>(m, nl, st);
 }
 
 // Instantiations: descriptor length D (with the radial block NQR x KR) and the

@@ -17,7 +17,10 @@
 // derivative tensors.
 //
 // Thread mappings.  Radial sweeps: RL consecutive lanes per atom, each taking
-// every RL-th pair, combined by warp shuffles.  Angular sweeps 1, 3, 4:
+// every RL-th pair, combined by warp shuffles; RL is 4 for batches that give
+// every SM several blocks, 8 or 16 for smaller ones, where the per-lane pair
+// loop (one dependent global load per pair) sets the kernel's length.
+// Angular sweeps 1, 3, 4:
 // persistent blocks over tiles of atoms; the per-pair geometry (basis,
 // harmonics, directional derivatives) of a chunk of the tile's pairs is computed
 // once per pair into shared memory, then one warp per atom contracts it with
@@ -37,7 +40,6 @@
 
 namespace gnep {
 
-constexpr int RL = 4;           // lanes per atom in radial sweeps
 constexpr int CH = 128;         // pairs per geometry chunk
 constexpr int kCgBlocksPerSm = 2;  // default persistent blocks of the c-gradient sweep per SM
 
@@ -78,7 +80,7 @@ __device__ __forceinline__ float3 sym_apply(const float* b, float3 r) {  // b = 
                      b[5] * r.x + b[4] * r.y + b[2] * r.z);
 }
 
-template <int NS, int K>
+template <int RL, int NS, int K>
 __device__ __forceinline__ void lane_reduce(float (&acc)[NS][K]) {
 #pragma unroll
   for (int o = 1; o < RL; o <<= 1)
@@ -94,7 +96,7 @@ __device__ __forceinline__ void lane_reduce(float (&acc)[NS][K]) {
 
 // Radial descriptors: per-atom basis sums FR[J][k] = sum_{j in J} f_k(r_ij) and
 // q_n = sum_J sum_k c^R_nk^{IJ} FR[J][k]  (Eqs. 5-6).
-template <class C>
+template <class C, int RL>
 __global__ void __launch_bounds__(128) k_desc_radial(int N, DevModel dm, const int* __restrict__ type,
                                                      const int* __restrict__ off, const float4* __restrict__ rij,
                                                      float* __restrict__ FR, float* __restrict__ G) {
@@ -122,7 +124,7 @@ __global__ void __launch_bounds__(128) k_desc_radial(int N, DevModel dm, const i
       acc_row<C::NS, C::KR>(acc, (int)r.w, f, 1.f);
     }
   }
-  lane_reduce(acc);
+  lane_reduce<RL>(acc);
   if (!ok) return;
   const int I = type[i];
   float* fr = FR + (size_t)i * C::NS * C::KR;
@@ -231,7 +233,7 @@ __global__ void __launch_bounds__(128) k_force_angular(int N, DevModel dm, const
 //                 (C1.1, C3.6 with the per-atom contraction chat = sum_n E'_n c^R_n)
 //   angular pairs: d_ij - d_rev(ij) from the pair forces of k_force_angular (Eq. 3)
 //   virial: -sum_j r_ij (x) d_ij, symmetrised (Eq. 4 summed over atoms).
-template <class C>
+template <class C, int RL>
 __global__ void __launch_bounds__(128) k_force_atoms(int N, DevModel dm, const int* __restrict__ type,
                                                      const int* __restrict__ offR, const int* __restrict__ jR,
                                                      const float4* __restrict__ rijR, const float* __restrict__ chat,
@@ -342,7 +344,7 @@ __global__ void __launch_bounds__(128) k_struct_sum(const int* __restrict__ soff
 
 // Radial tangent: FRd[J][k] = sum_{j in J} f_k'(r_ij) (u_hat . u_ij),
 // qdot_n = sum_J sum_k c^R_nk^{IJ} FRd[J][k].
-template <class C>
+template <class C, int RL>
 __global__ void __launch_bounds__(128) k_tangent_radial(int N, DevModel dm, const int* __restrict__ type,
                                                         const int* __restrict__ atom_struct, const int* __restrict__ off,
                                                         const int* __restrict__ jj, const float4* __restrict__ rij,
@@ -384,7 +386,7 @@ __global__ void __launch_bounds__(128) k_tangent_radial(int N, DevModel dm, cons
       acc_row<C::NS, C::KR>(acc, (int)r.w, fp, ru);
     }
   }
-  lane_reduce(acc);
+  lane_reduce<RL>(acc);
   if (!ok) return;
   float* fr = FRd + (size_t)i * C::NS * C::KR;
 #pragma unroll
@@ -1155,6 +1157,23 @@ int setup_ang() {
 
 // ------------------------------------------------------------- launchers
 
+// Launch CALL (which names RL) with RL = the radial sweeps' lanes per atom.
+#define GNEP_RADIAL_LANES(RLV, CALL)  \
+  switch (RLV) {                      \
+    case 16: {                        \
+      constexpr int RL = 16;          \
+      CALL;                           \
+    } break;                          \
+    case 8: {                         \
+      constexpr int RL = 8;           \
+      CALL;                           \
+    } break;                          \
+    default: {                        \
+      constexpr int RL = 4;           \
+      CALL;                           \
+    }                                 \
+  }
+
 namespace {
 
 template <class C>
@@ -1222,8 +1241,8 @@ struct Runner {
     // caller's stream: beside the angular sweeps' persistent blocks a radial
     // kernel found room for one block per SM, and the pair on two streams took
     // longer than the two in turn (0.431 against 0.420 ms for the step).
-    k_desc_radial<C><<<blocks_for((int64_t)N * RL, 128), 128, 0, A.st>>>(N, dm, nl->type, nl->L[0].off,
-                                                                          nl->L[0].rij, w.FR, w.G);
+    GNEP_RADIAL_LANES(radial_lanes(nl), (k_desc_radial<C, RL><<<blocks_for((int64_t)N * RL, 128), 128, 0, A.st>>>(
+                                             N, dm, nl->type, nl->L[0].off, nl->L[0].rij, w.FR, w.G)));
     stage("desc_radial");
     if constexpr (C::LMAX > 4) {
       if (int rc = hi_desc_angular<C>(m, nl, A.st, w.S, w.G)) return rc;
@@ -1255,9 +1274,9 @@ struct Runner {
       }
       stage("force_angular");
     }
-    k_force_atoms<C><<<blocks_for((int64_t)N * RL, 128), 128, 0, A.st>>>(
-        N, dm, nl->type, nl->L[0].off, nl->L[0].j, nl->L[0].rij, w.chat, nl->L[1].off, nl->L[1].rev, nl->L[1].rij,
-        w.dA, w.F, w.Wat);
+    GNEP_RADIAL_LANES(radial_lanes(nl), (k_force_atoms<C, RL><<<blocks_for((int64_t)N * RL, 128), 128, 0, A.st>>>(
+                                             N, dm, nl->type, nl->L[0].off, nl->L[0].j, nl->L[0].rij, w.chat,
+                                             nl->L[1].off, nl->L[1].rev, nl->L[1].rij, w.dA, w.F, w.Wat)));
     stage("force_atoms");
     if (!A.loss_follows) {  // otherwise the loss kernel forms these sums
       k_struct_sum<<<nl->n_struct, 128, 0, A.st>>>(nl->struct_off, w.Eatom, w.Wat, w.Es, w.Ws);
@@ -1274,8 +1293,10 @@ struct Runner {
     const DevModel dm = m->dev();
     const int N = nl->n_atoms;
     if (N == 0) return GNEP_OK;
-    k_tangent_radial<C><<<blocks_for((int64_t)N * RL, 128), 128, 0, A.st>>>(
-        N, dm, nl->type, nl->atom_struct, nl->L[0].off, nl->L[0].j, nl->L[0].rij, w.a, w.Bs, w.FRd, w.Gd);
+    GNEP_RADIAL_LANES(radial_lanes(nl),
+                      (k_tangent_radial<C, RL><<<blocks_for((int64_t)N * RL, 128), 128, 0, A.st>>>(
+                          N, dm, nl->type, nl->atom_struct, nl->L[0].off, nl->L[0].j, nl->L[0].rij, w.a, w.Bs, w.FRd,
+                          w.Gd)));
     stage("tangent_radial");
     if constexpr (C::LMAX > 4) {
       if (int rc = hi_tangent_angular<C>(m, nl, A.st, w.a, w.Bs, w.S, w.Sd, w.Gd, w.wij)) return rc;
@@ -1391,18 +1412,33 @@ int run_backward(const StepArgs& A) {
   return set_error(GNEP_ERR_UNSUPPORTED, "no kernel for this shape");
 }
 
+// SMs of this GPU (looked up once).
+int sm_count() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        n < 1)
+      n = 1;
+    sms = n;
+  }
+  return sms;
+}
+
+// Lanes per atom of the radial sweeps: the tuned value, else 4 while that
+// gives every SM at least four blocks of 128 threads, and 8 or 16 below.
+int radial_lanes(const gnep_nlist* nl) {
+  if (nl->tune.radial_lanes > 0) return nl->tune.radial_lanes;
+  const int64_t full = 4LL * 128 * sm_count();  // threads of four blocks per SM
+  const int64_t N = nl->n_atoms;
+  return 4 * N >= full ? 4 : 8 * N >= full ? 8 : 16;
+}
+
 // Persistent blocks of the c-gradient sweep: one per tile up to the default
 // (or tuned) count, at most kCgBlocksMax (the size of the partial buffer).
 int cgrad_blocks(const gnep_nlist* nl) {
   const int ntiles = nl->natile[1];
-  static int sms = 0;  // SMs of this GPU (looked up once)
-  if (!sms) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        sms < 1)
-      sms = 1;
-  }
-  int cap = nl->tune.cg_blocks > 0 ? nl->tune.cg_blocks : kCgBlocksPerSm * sms;
+  int cap = nl->tune.cg_blocks > 0 ? nl->tune.cg_blocks : kCgBlocksPerSm * sm_count();
   if (cap > kCgBlocksMax) cap = kCgBlocksMax;
   return ntiles < cap ? (ntiles > 0 ? ntiles : 1) : cap;
 }
@@ -1479,8 +1515,8 @@ int descriptors_static(const StepArgs& A, float* G) {
   const DevModel dm = m->dev();
   // Both kernels overwrite every scratch element they later read, so the
   // array needs no clearing between calls.
-  k_desc_radial<C><<<blocks_for(N * RL, 128), 128, 0, A.st>>>((int)N, dm, nl->type, nl->L[0].off, nl->L[0].rij,
-                                                              scratch, G);
+  GNEP_RADIAL_LANES(radial_lanes(nl), (k_desc_radial<C, RL><<<blocks_for(N * RL, 128), 128, 0, A.st>>>(
+                                           (int)N, dm, nl->type, nl->L[0].off, nl->L[0].rij, scratch, G)));
   if constexpr (C::LMAX > 4) {
     if ((rc = hi_desc_angular<C>(m, nl, A.st, scratch + fr_padded, G))) return rc;
   } else {

@@ -123,7 +123,10 @@ __global__ void __launch_bounds__(256) k_loss_final(LossArgs a, int nred, const 
 // warps combine their lanes as FP32 pairs (F2) and the four warp sums are
 // added in FP64 in order.  The last block to finish (counted in *done, which
 // it resets) forms the loss terms from all blocks' residuals in structure
-// order.
+// order.  In the MSE form the residual weights cf, ce, cv are constants
+// (Eqs. 14-16 without the RMSE chain factor), so each block also writes the
+// residual weights a_i, e_s and B_s of its structure (what k_residuals forms
+// otherwise, with the same arithmetic).
 __global__ void __launch_bounds__(128) k_struct_loss(const int* __restrict__ soff, const float* __restrict__ Eatom,
                                                      const float* __restrict__ Wat, const float* __restrict__ F,
                                                      const double* __restrict__ le, const float* __restrict__ lf,
@@ -131,19 +134,25 @@ __global__ void __launch_bounds__(128) k_struct_loss(const int* __restrict__ sof
                                                      double* __restrict__ Ws, double* __restrict__ red,
                                                      double* __restrict__ rn, LossArgs la,
                                                      const float* __restrict__ params, double* __restrict__ coef,
-                                                     int* __restrict__ err, int* __restrict__ done) {
+                                                     int* __restrict__ err, int* __restrict__ done,
+                                                     float4* __restrict__ aw, float* __restrict__ es,
+                                                     float* __restrict__ Bs) {
   const int s = blockIdx.x;
   const int a0 = soff[s], a1 = soff[s + 1];
+  const bool fused = la.form != GNEP_LOSS_RMSE;
+  const float cf = (float)(2.0 * la.lf * la.inv_3N);  // coef[4] of the MSE form
   float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
     acc[0] += Eatom[i];
 #pragma unroll
     for (int q = 0; q < 6; ++q) acc[1 + q] += Wat[6 * (size_t)i + q];
+    float d[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const float d = F[3 * (size_t)i + c] - lf[3 * (size_t)i + c];
-      acc[7] = fmaf(d, d, acc[7]);
+      d[c] = F[3 * (size_t)i + c] - lf[3 * (size_t)i + c];
+      acc[7] = fmaf(d[c], d[c], acc[7]);
     }
+    if (fused) aw[i] = make_float4(cf * d[0], cf * d[1], cf * d[2], 0.f);
   }
   __shared__ float2 wsum[4][8];
   __shared__ double tot[8];
@@ -179,6 +188,13 @@ __global__ void __launch_bounds__(128) k_struct_loss(const int* __restrict__ sof
     red[3 * s] = de * de;
     red[3 * s + 1] = tot[7];
     red[3 * s + 2] = sv;
+    if (fused) {  // coef[5], coef[6] of the MSE form times the residuals over N_s
+      es[s] = (float)(2.0 * la.le * la.inv_S * rn[7 * s]);
+      for (int c = 0; c < 6; ++c) {
+        const double g = 2.0 * la.lv * la.inv_6S * rn[7 * s + 1 + c];
+        Bs[6 * s + c] = (float)(c < 3 ? g : 0.5 * g);
+      }
+    }
     __threadfence();
     last = atomicAdd(done, 1) == (int)gridDim.x - 1;
   }
@@ -431,15 +447,17 @@ int run_loss_impl(const gnep_model* m, gnep_nlist* nl, const double* le, const f
   a.inv_np = 1.0 / (double)m->n_params;
   if (S > 0) {  // per-structure residuals; the last block forms the loss terms
     k_struct_loss<<<S, 128, 0, st>>>(nl->struct_off, w.Eatom, w.Wat, w.F, le, lf, lv, w.Es, w.Ws, w.red,
-                                     w.red + 3 * (size_t)S, a, m->params, w.coef, m->err, m->err + 2);
+                                     w.red + 3 * (size_t)S, a, m->params, w.coef, m->err, m->err + 2, w.a, w.es,
+                                     w.Bs);
   } else {
     k_loss_final<<<1, 256, 0, st>>>(a, 0, w.red, m->params, w.coef, m->err);
   }
   stage("struct_loss");
-  if (N + S > 0)
+  if (N + S > 0 && (S == 0 || a.form == GNEP_LOSS_RMSE)) {  // the loss kernel wrote them in the MSE form
     k_residuals<<<blocks_for(N + S, 256), 256, 0, st>>>(N, S, w.F, lf, w.red + 3 * (size_t)S, w.coef, w.a, w.es,
                                                          w.Bs);
-  stage("residuals");
+    stage("residuals");
+  }
   GNEP_CHECK_LAUNCH("loss");
   return GNEP_OK;
 }

@@ -130,7 +130,7 @@ class NeighborList:
         return off, j[:n], sh[:n]
 
     TUNING_KEYS = ("desc_tile_atoms", "desc_tile_pairs", "force_tile_atoms", "force_tile_pairs", "cgrad_blocks",
-                   "net_blocks")
+                   "net_blocks", "radial_lanes", "net_tile_atoms")
 
     def autotune(self, y: "Labels", reps: int = 3, stream=None) -> dict:
         """Pick the fastest launch shapes of the angular sweeps for this batch

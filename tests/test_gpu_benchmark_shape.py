@@ -4,10 +4,12 @@ several network tiles of each species.
 
 The batch is the smallest structures of the 256-structure workload, at least
 420 atoms: more than 128 atoms of each species, so that each species spans at
-least two 128-atom tensor-core tiles and several 32-atom FP32 tiles.  Running
-the network kernels with the default, one and three persistent blocks puts
-several tiles, and a species switch, inside one block, and gives the gradient
-assembly one or many block partials to combine.  Checked against the oracle:
+least two 128-atom tiles and several 32-atom tiles.  Running the network
+kernels with the default, one and three persistent blocks puts several tiles,
+and a species switch, inside one block, and gives the gradient assembly one or
+many block partials to combine.  The FP32 network runs with both tile sizes
+(32 atoms, eight threads per atom; 128 atoms, two) and the radial sweeps with
+4, 8 and 16 lanes per atom.  Checked against the oracle:
 the loss terms and gradient (Eqs. 9-16, D1.18-D1.21) in the FP32 form at the
 FP32 tolerances and in the TF32 and BF16 network modes within four rounding
 units of their operand format; the descriptor scale computed on the GPU; and
@@ -48,10 +50,12 @@ def case():
     return c
 
 
-def _grad(c, mode, net_blocks):
+def _grad(c, mode, net_blocks, net_tile_atoms=0, radial_lanes=0):
     c.m.set_precision(mode)
     c.m.set_params(torch.from_numpy(c.P))
-    c.nl.set_tuning(dict(net_blocks=net_blocks))
+    c.nl.set_tuning(dict(net_blocks=net_blocks, net_tile_atoms=net_tile_atoms, radial_lanes=radial_lanes))
+    t = c.nl.tuning()
+    assert net_tile_atoms in (0, t["net_tile_atoms"]) and radial_lanes in (0, t["radial_lanes"]), t
     terms, g = c.m.loss_grad(c.nl, c.gpu_labels())
     c.m.sync_status()
     return terms.cpu().numpy(), g.double().cpu().numpy()
@@ -62,9 +66,10 @@ def test_batch_spans_several_tiles_per_species(case):
     assert case.batch.n_atoms >= 420 and counts.min() > 128, counts
 
 
-@pytest.mark.parametrize("net_blocks", [0, 1, 3])
-def test_fp32_gradient_matches_oracle(case, net_blocks):
-    terms, g = _grad(case, "fp32", net_blocks)
+@pytest.mark.parametrize("net_blocks,net_tile_atoms,radial_lanes",
+                         [(0, 0, 0), (1, 32, 4), (3, 32, 8), (0, 128, 16), (1, 128, 4), (3, 128, 0)])
+def test_fp32_gradient_matches_oracle(case, net_blocks, net_tile_atoms, radial_lanes):
+    terms, g = _grad(case, "fp32", net_blocks, net_tile_atoms, radial_lanes)
     np.testing.assert_allclose(terms, case.ref_terms, rtol=2e-5, atol=1e-12)
     ref = case.ref_g
     assert rel_l2(g, ref) < G_TOL, rel_l2(g, ref)
