@@ -30,6 +30,7 @@
 
 #include "gnep_internal.h"
 #include "network.cuh"
+#include "warp_mma.cuh"
 
 namespace gnep {
 
@@ -71,10 +72,17 @@ template <int D, int G>
 __device__ void load_weights(const DevModel& dm, int e, float* W, float* b0, float* w1) {
   constexpr int DW = RowW<D>::DW;
   const float* P = dm.params + (size_t)e * dm.net_size;
-  const int H = dm.H, H2 = h_even<G>(H);
-  for (int q = threadIdx.x; q < H2 * DW; q += NT) {
-    const int mu = q / DW, v = q % DW;
-    W[q] = (v < D && mu < H) ? P[mu * D + v] : 0.f;
+  const int H = dm.H, H2 = h_even<G>(H), N = H2 * DW;
+  for (int q0 = threadIdx.x; q0 < N; q0 += 4 * NT) {  // four loads in flight per thread
+    float x[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int q = q0 + k * NT, mu = q / DW, v = q % DW;
+      x[k] = (q < N && v < D && mu < H) ? __ldg(P + mu * D + v) : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (q0 + k * NT < N) W[q0 + k * NT] = x[k];
   }
   for (int mu = threadIdx.x; mu < H2; mu += NT) {
     b0[mu] = mu < H ? P[D * H + mu] : 0.f;
@@ -82,18 +90,18 @@ __device__ void load_weights(const DevModel& dm, int e, float* W, float* b0, flo
   }
 }
 
-// Scaled rows s.src of the tile's atoms into R [TA][DW] (zero padding), for
+// Scaled rows s.src of the tile's atoms into R [TA][RS] (zero padding), for
 // NA arrays at once: every thread issues all of its gathered loads before the
 // first store, so that a tile waits for one global-memory latency, not one per
 // element.
-template <int D, int NA, int TA>
+template <int D, int NA, int TA, int RS = RowW<D>::DW, int NTH = NT>
 __device__ __forceinline__ void stage_rows(const float* __restrict__ s0, const float* __restrict__ s1,
                                            const int* rows, const float* sc, float* R0, float* R1) {
-  constexpr int DW = RowW<D>::DW, N = TA * DW, IT = (N + NT - 1) / NT;
+  constexpr int DW = RS, N = TA * DW, IT = (N + NTH - 1) / NTH;
   float x[NA][IT];
 #pragma unroll
   for (int k = 0; k < IT; ++k) {
-    const int q = threadIdx.x + k * NT, a = q / DW, v = q % DW;
+    const int q = threadIdx.x + k * NTH, a = q / DW, v = q % DW;
     const int r = q < N ? rows[a] : -1;
     const bool in = r >= 0 && v < D;
     x[0][k] = in ? __ldg(s0 + (size_t)r * D + v) : 0.f;
@@ -101,7 +109,7 @@ __device__ __forceinline__ void stage_rows(const float* __restrict__ s0, const f
   }
 #pragma unroll
   for (int k = 0; k < IT; ++k) {
-    const int q = threadIdx.x + k * NT;
+    const int q = threadIdx.x + k * NTH;
     if (q < N) {
       const float c = sc[q % DW];
       R0[q] = c * x[0][k];
@@ -460,6 +468,408 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_bwd_row(Tiles T, int ntiles, DevM
   if (cur_e >= 0) flush(cur_e);
 }
 
+// ------------------------------------------------------------- tensor-core tiles (FP32 accuracy)
+//
+// The same forward and backward passes on the warp-level tensor cores, with
+// every product carried in split TF32 (hi*hi plus the two cross terms in two
+// accumulators, warp_mma.cuh), which keeps FP32 accuracy.  128-atom tiles,
+// eight warps; warp w owns the tile's atoms 16 w .. 16 w + 15 as the M = 16
+// rows of its products:
+//   Z  = (s.G) W0^T      M 16 atoms, N 8 hidden units, K 8 descriptors
+//   Zd = (s.Gdot) W0^T   (backward; same B fragments)
+//   E' = beta W0         (forward)   M 16 atoms, N 8 descriptors, K 8 units
+//   Gb = alpha W0        (backward)
+// The hidden units go in chunks of 16 (two N tiles).  The B columns of the
+// first products are permuted (column c holds unit c/2 + 4 (c mod 2)) so that
+// a lane's C fragment of Z is, register for register, its A fragment of the
+// second product: the element-wise terms never leave the registers.  W0 sits
+// in shared memory already split (hi and lo TF32 words).  The weight gradient
+// dW0 and its column sums take the contraction over atoms as before.
+template <int D>
+struct MmaW {
+  static constexpr int DP = (D + 7) / 8 * 8;  // descriptors padded to k-steps of 8
+  static constexpr int KD = DP / 8;
+  static constexpr int SW = DP + 4;  // row stride (4 mod 8 words: the A and Z-product B fragments hit 32 banks)
+};
+
+// Weights of species e split into TF32 hi / lo words: Wh, Wl [HP][SW] (zero
+// beyond D and H), b0, w1 [HP] (zero beyond H).
+template <int D, int HP, int NTH>
+__device__ void load_weights_split(const DevModel& dm, int e, uint32_t* Wh, uint32_t* Wl, float* b0, float* w1) {
+  constexpr int SW = MmaW<D>::SW;
+  const float* P = dm.params + (size_t)e * dm.net_size;
+  const int H = dm.H;
+  for (int q = threadIdx.x; q < HP * SW; q += NTH) {
+    const int mu = q / SW, v = q % SW;
+    split_tf32<true>((v < D && mu < H) ? P[mu * D + v] : 0.f, Wh[q], Wl[q]);
+  }
+  for (int mu = threadIdx.x; mu < HP; mu += NTH) {
+    b0[mu] = mu < H ? P[D * H + mu] : 0.f;
+    w1[mu] = mu < H ? P[D * H + H + mu] : 0.f;
+  }
+}
+
+// B fragment of a first product: column g of hidden chunk n0 (unit n0 + pg),
+// rows c and c + 4 of the descriptor k-step.
+template <int SW>
+__device__ __forceinline__ void frag_w_cols(FragB& b, const uint32_t* Wh, const uint32_t* Wl, int mu, int c) {
+  b.h[0] = Wh[mu * SW + c];
+  b.l[0] = Wl[mu * SW + c];
+  b.h[1] = Wh[mu * SW + c + 4];
+  b.l[1] = Wl[mu * SW + c + 4];
+}
+// B fragment of a second product: rows k0 and k0 + 4 (hidden units), column d.
+template <int SW>
+__device__ __forceinline__ void frag_w_rows(FragB& b, const uint32_t* Wh, const uint32_t* Wl, int k0, int d) {
+  b.h[0] = Wh[k0 * SW + d];
+  b.l[0] = Wl[k0 * SW + d];
+  b.h[1] = Wh[(k0 + 4) * SW + d];
+  b.l[1] = Wl[(k0 + 4) * SW + d];
+}
+
+template <int D, int HP, int NS, int NQR, int KR, int TA>
+size_t mlp_fwd_mma_smem() {
+  constexpr int SW = MmaW<D>::SW;
+  return sizeof(float) * (2 * (size_t)HP * SW + TA * (size_t)SW + 2 * HP + SW + NS * NQR * KR);
+}
+
+// Forward on tensor cores: z = W0 (s.G) + b0, x = tanh z, E = w1.x + b1,
+// E' = s . (W0^T (w1 (1 - x^2)))  (D1.1-D1.5), and chat as in k_mlp_fwd_row.
+template <int D, int HP, int NS, int NQR, int KR, int TA>
+__global__ void __launch_bounds__(2 * TA, 1) k_mlp_fwd_mma(Tiles T, int ntiles, DevModel dm, const float* __restrict__ G,
+                                                       float* __restrict__ Ep, float* __restrict__ Eatom,
+                                                       float* __restrict__ chat) {
+  constexpr int NTB = 2 * TA, SW = MmaW<D>::SW, KD = MmaW<D>::KD, NJK = NS * KR;
+  static_assert(HP % 16 == 0 && TA == 128, "16-unit chunks, 16 atoms per warp");
+  extern __shared__ float4 sm4[];
+  uint32_t* Wh = reinterpret_cast<uint32_t*>(sm4);  // [HP][SW]
+  uint32_t* Wl = Wh + HP * SW;                       // [HP][SW]
+  float* R = reinterpret_cast<float*>(Wl + HP * SW);  // [TA][SW] s.G, then the scaled E'
+  float* b0 = R + TA * SW;                           // [HP]
+  float* w1 = b0 + HP;                               // [HP]
+  float* sc = w1 + HP;                               // [SW]
+  float* cR = sc + SW;                               // [NS][NQR][KR] of the tile's species
+  __shared__ int rows[TA];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, t = lane & 3, pg = (g >> 1) | ((g & 1) << 2);
+  const int H = dm.H;
+  for (int v = tid; v < SW; v += NTB) sc[v] = v < D ? dm.scale[v] : 0.f;
+  int cur_e = -1;
+  float b1 = 0.f;
+  for (int tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
+    int e, a0, na;
+    tile_of<TA>(T, tt, e, a0, na);
+    __syncthreads();  // the previous tile's readers of R, rows and the weights are done
+    if (e != cur_e) {
+      load_weights_split<D, HP, NTB>(dm, e, Wh, Wl, b0, w1);
+      for (int q = tid; q < NS * NQR * KR; q += NTB) cR[q] = dm.params[dm.off_cR + e * NS * NQR * KR + q];
+      b1 = dm.params[(size_t)e * dm.net_size + D * H + 2 * H];
+      cur_e = e;
+    }
+    if (tid < TA) rows[tid] = tid < na ? T.perm[a0 + tid] : -1;
+    __syncthreads();
+    stage_rows<D, 1, TA, SW, NTB>(G, nullptr, rows, sc, R, nullptr);
+    __syncthreads();
+    float* Rw = R + 16 * warp * SW;  // this warp's 16 rows
+    Acc<true> ep[KD];
+#pragma unroll
+    for (int nd = 0; nd < KD; ++nd) ep[nd].zero();
+    float Eg = 0.f, Eg8 = 0.f;  // energies of atoms g and g + 8 (this lane's units)
+    if (16 * warp < na) {
+      for (int hc = 0; hc < HP / 16 && 16 * hc < H; ++hc) {
+        Acc<true> z[2];
+        z[0].zero();
+        z[1].zero();
+#pragma unroll
+        for (int ks = 0; ks < KD; ++ks) {
+          const int c = 8 * ks + t;
+          FragA a;
+          frag_a<true>(a, Rw[g * SW + c], Rw[(g + 8) * SW + c], Rw[g * SW + c + 4], Rw[(g + 8) * SW + c + 4]);
+#pragma unroll
+          for (int nt = 0; nt < 2; ++nt) {
+            FragB b;
+            frag_w_cols<SW>(b, Wh, Wl, 16 * hc + 8 * nt + pg, c);
+            mma_acc<true>(z[nt], a, b);
+          }
+        }
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+          const int m0 = 16 * hc + 8 * nt + t, m1 = m0 + 4;  // units of C columns 2t and 2t + 1
+          const float x0 = tanhf(z[nt].get(0) + b0[m0]), x1 = tanhf(z[nt].get(1) + b0[m1]);
+          const float x2 = tanhf(z[nt].get(2) + b0[m0]), x3 = tanhf(z[nt].get(3) + b0[m1]);
+          Eg = fmaf(w1[m1], x1, fmaf(w1[m0], x0, Eg));
+          Eg8 = fmaf(w1[m1], x3, fmaf(w1[m0], x2, Eg8));
+          FragA ab;  // beta = w1 (1 - x^2) as the A fragment (rows g, g + 8; k = t, t + 4)
+          frag_a<true>(ab, w1[m0] * (1.f - x0 * x0), w1[m0] * (1.f - x2 * x2), w1[m1] * (1.f - x1 * x1),
+                       w1[m1] * (1.f - x3 * x3));
+#pragma unroll
+          for (int nd = 0; nd < KD; ++nd) {
+            FragB b;
+            frag_w_rows<SW>(b, Wh, Wl, m0, 8 * nd + g);
+            mma_acc<true>(ep[nd], ab, b);
+          }
+        }
+      }
+    }
+    Eg += __shfl_xor_sync(0xffffffffu, Eg, 1);
+    Eg += __shfl_xor_sync(0xffffffffu, Eg, 2);
+    Eg8 += __shfl_xor_sync(0xffffffffu, Eg8, 1);
+    Eg8 += __shfl_xor_sync(0xffffffffu, Eg8, 2);
+    __syncwarp();  // the warp's rows of R have been read: they take the scaled E'
+#pragma unroll
+    for (int nd = 0; nd < KD; ++nd) {
+      const int d = 8 * nd + 2 * t;
+      Rw[g * SW + d] = ep[nd].get(0) * sc[d];
+      Rw[g * SW + d + 1] = ep[nd].get(1) * sc[d + 1];
+      Rw[(g + 8) * SW + d] = ep[nd].get(2) * sc[d];
+      Rw[(g + 8) * SW + d + 1] = ep[nd].get(3) * sc[d + 1];
+    }
+    if (t == 0) {
+      if (16 * warp + g < na) Eatom[rows[16 * warp + g]] = Eg + b1;
+      if (16 * warp + g + 8 < na) Eatom[rows[16 * warp + g + 8]] = Eg8 + b1;
+    }
+    __syncthreads();
+    // coalesced row writes: E' and chat
+    for (int q = tid; q < na * D; q += NTB) {
+      const int r = q / D, v = q % D;
+      Ep[(size_t)rows[r] * D + v] = R[r * SW + v];
+    }
+    for (int q = tid; q < na * NJK; q += NTB) {
+      const int r = q / NJK, jk = q % NJK, J = jk / KR, k = jk % KR;
+      float s = 0.f;
+#pragma unroll
+      for (int n = 0; n < NQR; ++n) s = fmaf(R[r * SW + n], cR[(J * NQR + n) * KR + k], s);
+      chat[(size_t)rows[r] * NJK + jk] = s;
+    }
+  }
+}
+
+template <int D, int HP>
+size_t mlp_bwd_mma_smem() {
+  constexpr int SW = MmaW<D>::SW, HR = HP + 8, TA = 128, NWB = TA / 16;
+  return sizeof(float) * (2 * (size_t)HP * SW + 2 * (size_t)TA * SW + 2 * (size_t)TA * HR + 2 * (size_t)NWB * HP +
+                          2 * HP + SW + TA);
+}
+
+// Tangent and reverse pass on tensor cores (the terms of k_mlp_bwd_row):
+// per chunk of 16 hidden units, Z and Zdot by split-TF32 products, the
+// element-wise alpha, -beta, q1 in the accumulator registers, Gbar += alpha W0;
+// alpha and -beta go to shared rows, the column sums of alpha and q1 over the
+// warp's atoms to per-warp shared sums.  Then the weight gradient
+//   dW0 += alpha^T (s.G) - beta^T (s.Gdot)      M 16 units, N 8 descriptors, K 8 atoms
+// by split-TF32 products too: warp w takes the 16-unit block w mod (HP/16) and
+// one of 8 / (HP/16) groups of the tile's atoms, keeping its partial dW0 in
+// registers over all tiles of a species; the partials are added in warp order
+// when the block flushes.  Writes part[block][species] like k_mlp_bwd_row.
+// 128-atom tiles, HP (hidden width padded) 32 or 64.
+template <int D, int HP>
+__global__ void __launch_bounds__(256, 1) k_mlp_bwd_mma(Tiles T, int ntiles, DevModel dm,
+                                                       const int* __restrict__ atom_struct,
+                                                       const float* __restrict__ es, const float* __restrict__ G,
+                                                       const float* __restrict__ Gd, float* __restrict__ Gb,
+                                                       float* __restrict__ part, int part_stride) {
+  constexpr int TA = 128, NTB = 256, NWB = 8, SW = MmaW<D>::SW, KD = MmaW<D>::KD, HR = HP + 8;
+  constexpr int MT = HP / 16, KG = NWB / MT, KA = TA / KG;  // dW0: unit blocks, atom groups, atoms per group
+  static_assert(HP % 16 == 0 && HP <= 64 && NWB % MT == 0, "16-unit chunks, 16 atoms per warp");
+  extern __shared__ float4 sm4[];
+  uint32_t* Wh = reinterpret_cast<uint32_t*>(sm4);  // [HP][SW]
+  uint32_t* Wl = Wh + HP * SW;                       // [HP][SW]
+  float* SG = reinterpret_cast<float*>(Wl + HP * SW);  // [TA][SW] s.G, then the Gbar output rows
+  float* SD = SG + TA * SW;                          // [TA][SW] s.Gdot
+  float* Al = SD + TA * SW;                          // [TA][HR] alpha
+  float* Be = Al + TA * HR;                          // [TA][HR] -beta
+  float* wdb0 = Be + TA * HR;                        // [NWB][HP] per-warp column sums of alpha
+  float* wdw1 = wdb0 + NWB * HP;                     // [NWB][HP] per-warp column sums of q1
+  float* b0 = wdw1 + NWB * HP;                       // [HP]
+  float* w1 = b0 + HP;                               // [HP]
+  float* sc = w1 + HP;                               // [SW]
+  float* ev = sc + SW;                               // [TA] e_i of the tile's atoms
+  __shared__ int rows[TA];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, t = lane & 3, pg = (g >> 1) | ((g & 1) << 2);
+  const int mw = warp % MT, kw = warp / MT;  // this warp's dW0 unit block and atom group
+  const int H = dm.H;
+  for (int v = tid; v < SW; v += NTB) sc[v] = v < D ? dm.scale[v] : 0.f;
+  for (int q = tid; q < 2 * TA * HR; q += NTB) Al[q] = 0.f;  // Be follows Al
+  Acc<true> dw[KD];  // dW0[16 mw + (g, g + 8)][8 nd + 2t, + 1], partial over atom group kw
+  float cb1 = 0.f;
+  int cur_e = -1;
+
+  auto reset = [&]() {
+#pragma unroll
+    for (int nd = 0; nd < KD; ++nd) dw[nd].zero();
+    for (int q = tid; q < 2 * NWB * HP; q += NTB) wdb0[q] = 0.f;  // wdw1 follows wdb0
+    cb1 = 0.f;
+  };
+  // after a barrier that follows the last tile of species e; uses SG as scratch
+  auto flush = [&](int e) {
+    float* red = SG;  // [NWB][16][8 KD] the warps' partial dW0 blocks
+#pragma unroll
+    for (int nd = 0; nd < KD; ++nd) {
+      const int d = 8 * nd + 2 * t;
+      red[(warp * 16 + g) * 8 * KD + d] = dw[nd].get(0);
+      red[(warp * 16 + g) * 8 * KD + d + 1] = dw[nd].get(1);
+      red[(warp * 16 + g + 8) * 8 * KD + d] = dw[nd].get(2);
+      red[(warp * 16 + g + 8) * 8 * KD + d + 1] = dw[nd].get(3);
+    }
+    __syncthreads();
+    float* out = part + ((size_t)blockIdx.x * T.ns + e) * part_stride;
+    for (int q = tid; q < H * D; q += NTB) {
+      const int mu = q / D, v = q % D, m = mu / 16, r = mu % 16;
+      float s = 0.f;
+      for (int k = 0; k < KG; ++k) s += red[((k * MT + m) * 16 + r) * 8 * KD + v];  // atom groups in order
+      out[q] = s;
+    }
+    for (int mu = tid; mu < H; mu += NTB) {
+      float s0 = 0.f, s1 = 0.f;
+      for (int w = 0; w < NWB; ++w) {  // warps in order
+        s0 += wdb0[w * HP + mu];
+        s1 += wdw1[w * HP + mu];
+      }
+      out[D * H + mu] = s0;
+      out[D * H + H + mu] = s1;
+    }
+    if (tid == 0) out[D * H + 2 * H] = cb1;
+  };
+  reset();
+
+  for (int tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
+    int e, a0, na;
+    tile_of<TA>(T, tt, e, a0, na);
+    __syncthreads();  // the previous tile is done with every shared array
+    if (e != cur_e) {
+      if (cur_e >= 0) flush(cur_e);
+      __syncthreads();
+      reset();
+      load_weights_split<D, HP, NTB>(dm, e, Wh, Wl, b0, w1);
+      cur_e = e;
+    }
+    if (tid < TA) {
+      const int r = tid < na ? T.perm[a0 + tid] : -1;
+      rows[tid] = r;
+      ev[tid] = r >= 0 ? es[atom_struct[r]] : 0.f;
+    }
+    __syncthreads();
+    stage_rows<D, 2, TA, SW, NTB>(G, Gd, rows, sc, SG, SD);
+    if (tid == 0)
+      for (int r = 0; r < na; ++r) cb1 += ev[r];
+    __syncthreads();
+    // per warp: Z, Zdot, the element-wise terms and Gbar of its 16 atoms
+    const float* Gw = SG + 16 * warp * SW;
+    const float* Dw = SD + 16 * warp * SW;
+    Acc<true> gb[KD];
+#pragma unroll
+    for (int nd = 0; nd < KD; ++nd) gb[nd].zero();
+    if (16 * warp < na) {
+      const float ea = ev[16 * warp + g], ea8 = ev[16 * warp + g + 8];
+      float* Alw = Al + 16 * warp * HR;
+      float* Bew = Be + 16 * warp * HR;
+      for (int hc = 0; hc < HP / 16 && 16 * hc < H; ++hc) {
+        Acc<true> z[2], zd[2];
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+          z[nt].zero();
+          zd[nt].zero();
+        }
+#pragma unroll
+        for (int ks = 0; ks < KD; ++ks) {
+          const int c = 8 * ks + t;
+          FragA a, ad;
+          frag_a<true>(a, Gw[g * SW + c], Gw[(g + 8) * SW + c], Gw[g * SW + c + 4], Gw[(g + 8) * SW + c + 4]);
+          frag_a<true>(ad, Dw[g * SW + c], Dw[(g + 8) * SW + c], Dw[g * SW + c + 4], Dw[(g + 8) * SW + c + 4]);
+#pragma unroll
+          for (int nt = 0; nt < 2; ++nt) {
+            FragB b;
+            frag_w_cols<SW>(b, Wh, Wl, 16 * hc + 8 * nt + pg, c);
+            mma_acc<true>(z[nt], a, b);
+            mma_acc<true>(zd[nt], ad, b);
+          }
+        }
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+          const int m[2] = {16 * hc + 8 * nt + t, 16 * hc + 8 * nt + t + 4};  // units of C columns 2t, 2t + 1
+          float al[4], q1[4];  // C positions: (g, m0) (g, m1) (g + 8, m0) (g + 8, m1)
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const int mu = m[r & 1];
+            const float ee = r < 2 ? ea : ea8;
+            const float x = tanhf(z[nt].get(r) + b0[mu]);
+            const float t1 = 1.f - x * x;
+            const float beta = w1[mu] * t1;
+            const float zdr = zd[nt].get(r);
+            al[r] = ee * beta + 2.f * x * beta * zdr;
+            q1[r] = ee * x - t1 * zdr;  // zero for padding atoms (e = 0, zdot = 0) and padding units
+            const int row = (r < 2 ? g : g + 8) * HR + mu;
+            Alw[row] = al[r];
+            Bew[row] = -beta;
+          }
+          // column sums over the warp's 16 atoms (rows g and g + 8 of the eight lanes t)
+          float s[4] = {al[0] + al[2], al[1] + al[3], q1[0] + q1[2], q1[1] + q1[3]};
+#pragma unroll
+          for (int o = 4; o < 32; o <<= 1)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
+          if (g == 0) {
+            wdb0[warp * HP + m[0]] += s[0];
+            wdb0[warp * HP + m[1]] += s[1];
+            wdw1[warp * HP + m[0]] += s[2];
+            wdw1[warp * HP + m[1]] += s[3];
+          }
+          FragA aa;  // alpha as the A fragment (rows g, g + 8; k = t, t + 4)
+          frag_a<true>(aa, al[0], al[2], al[1], al[3]);
+#pragma unroll
+          for (int nd = 0; nd < KD; ++nd) {
+            FragB b;
+            frag_w_rows<SW>(b, Wh, Wl, m[0], 8 * nd + g);
+            mma_acc<true>(gb[nd], aa, b);
+          }
+        }
+      }
+    }
+    __syncthreads();  // alpha and -beta of the tile are complete
+    // dW0 += alpha^T (s.G) - beta^T (s.Gdot) over this warp's atom group
+    if (16 * mw < H) {
+      const int k1 = min(na, KA * (kw + 1));
+      for (int k0 = KA * kw; k0 < k1; k0 += 8) {
+        const int u = 16 * mw + g;  // A rows g, g + 8: units; columns t, t + 4: atoms
+        FragA fa, fb;
+        frag_a<true>(fa, Al[(k0 + t) * HR + u], Al[(k0 + t) * HR + u + 8], Al[(k0 + t + 4) * HR + u],
+                     Al[(k0 + t + 4) * HR + u + 8]);
+        frag_a<true>(fb, Be[(k0 + t) * HR + u], Be[(k0 + t) * HR + u + 8], Be[(k0 + t + 4) * HR + u],
+                     Be[(k0 + t + 4) * HR + u + 8]);
+#pragma unroll
+        for (int nd = 0; nd < KD; ++nd) {
+          const int d = 8 * nd + g;  // B rows t, t + 4: atoms; column g: descriptor
+          FragB bg, bd;
+          frag_b<true>(bg, SG[(k0 + t) * SW + d], SG[(k0 + t + 4) * SW + d]);
+          frag_b<true>(bd, SD[(k0 + t) * SW + d], SD[(k0 + t + 4) * SW + d]);
+          mma_acc<true>(dw[nd], fa, bg);
+          mma_acc<true>(dw[nd], fb, bd);
+        }
+      }
+    }
+    __syncthreads();  // s.G rows are no longer read: they take the Gbar rows
+    {
+      float* Ow = SG + 16 * warp * SW;
+#pragma unroll
+      for (int nd = 0; nd < KD; ++nd) {
+        const int d = 8 * nd + 2 * t;
+        Ow[g * SW + d] = gb[nd].get(0) * sc[d];
+        Ow[g * SW + d + 1] = gb[nd].get(1) * sc[d + 1];
+        Ow[(g + 8) * SW + d] = gb[nd].get(2) * sc[d];
+        Ow[(g + 8) * SW + d + 1] = gb[nd].get(3) * sc[d + 1];
+      }
+    }
+    __syncthreads();
+    for (int q = tid; q < na * D; q += NTB) {
+      const int r = q / D, v = q % D;
+      Gb[(size_t)rows[r] * D + v] = SG[r * SW + v];
+    }
+  }
+  __syncthreads();
+  if (cur_e >= 0) flush(cur_e);
+}
+
 // ------------------------------------------------------------- launchers
 
 Tiles make_tiles(const gnep_nlist* nl, int ns, int tile_atoms) {
@@ -478,9 +888,9 @@ Tiles make_tiles(const gnep_nlist* nl, int ns, int tile_atoms) {
 namespace {
 // Resident blocks of a kernel on this GPU.
 template <class K>
-int resident_blocks(K kern, size_t smem, int& out) {
+int resident_blocks(K kern, int threads, size_t smem, int& out) {
   int per_sm = 0, dev = 0, sms = 0;
-  GNEP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
+  GNEP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
   GNEP_CUDA(cudaGetDevice(&dev));
   GNEP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   if (per_sm < 1) return set_error(GNEP_ERR_CUDA, "FP32 network kernel does not fit on an SM");
@@ -498,70 +908,90 @@ int net_tile_atoms(const gnep_nlist* nl, int ns) {
   return 2 * make_tiles(nl, ns, 128).tbase[ns] >= sm_count() ? 128 : 32;
 }
 
-template <int D, int HP, int NS, int NQR, int KR, int TA>
-int mlp_setup_ta() {
-  // shared memory for the largest hidden width of this padding
-  GNEP_CUDA(cudaFuncSetAttribute(k_mlp_fwd_row<D, NS, NQR, KR, TA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)mlp_fwd_smem<D, NS, NQR, KR, TA>(kMaxHidden)));
-  GNEP_CUDA(cudaFuncSetAttribute(k_mlp_bwd_row<D, HP, TA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)mlp_bwd_smem<D, HP, TA>(HP)));
-  GNEP_CUDA(cudaFuncSetAttribute(k_mlp_bwd_row<D, HP, TA>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+template <class K>
+int set_smem(K kern, size_t bytes) {
+  GNEP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  GNEP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   return GNEP_OK;
 }
 
+// Kernels per tile size: 32-atom tiles on the CUDA cores (eight threads per
+// atom); 128-atom tiles on the tensor cores, except the backward pass above 64
+// hidden units (its alpha and beta rows would not fit next to the split
+// weights), which takes the CUDA-core kernel with two threads per atom.
 template <int D, int HP, int NS, int NQR, int KR>
 int mlp_setup() {
-  if (int rc = mlp_setup_ta<D, HP, NS, NQR, KR, 128>()) return rc;
-  return mlp_setup_ta<D, HP, NS, NQR, KR, 32>();
+  // shared memory for the largest hidden width of this padding
+  if (int rc = set_smem(k_mlp_fwd_row<D, NS, NQR, KR, 32>, mlp_fwd_smem<D, NS, NQR, KR, 32>(kMaxHidden))) return rc;
+  if (int rc = set_smem(k_mlp_bwd_row<D, HP, 32>, mlp_bwd_smem<D, HP, 32>(HP))) return rc;
+  if (int rc = set_smem(k_mlp_fwd_mma<D, HP, NS, NQR, KR, 128>, mlp_fwd_mma_smem<D, HP, NS, NQR, KR, 128>()))
+    return rc;
+  if constexpr (HP <= 64) {
+    return set_smem(k_mlp_bwd_mma<D, HP>, mlp_bwd_mma_smem<D, HP>());
+  } else {
+    return set_smem(k_mlp_bwd_row<D, HP, 128>, mlp_bwd_smem<D, HP, 128>(HP));
+  }
 }
 
-template <int D, int NS, int NQR, int KR, int TA>
-int mlp_forward_ta(const gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
-  const Tiles T = make_tiles(nl, NS, TA);
-  const int ntiles = T.tbase[NS];
+template <class K>
+int launch_forward(K kern, int threads, size_t smem, int tile_atoms, const gnep_model* m, gnep_nlist* nl,
+                   cudaStream_t st, const char* what) {
+  const Tiles T = make_tiles(nl, m->shape.ns, tile_atoms);
+  const int ntiles = T.tbase[m->shape.ns];
   if (ntiles == 0) return GNEP_OK;
   Workspace& w = nl->ws;
-  auto kern = k_mlp_fwd_row<D, NS, NQR, KR, TA>;
-  const size_t smem = mlp_fwd_smem<D, NS, NQR, KR, TA>(m->shape.H);
   int cap = 0;
-  if (int rc = resident_blocks(kern, smem, cap)) return rc;
+  if (int rc = resident_blocks(kern, threads, smem, cap)) return rc;
   const int grid = net_blocks(nl, ntiles < cap ? ntiles : cap);
-  kern<<<grid, NT, smem, st>>>(T, ntiles, m->dev(), w.G, w.Ep, w.Eatom, w.chat);
-  GNEP_CHECK_LAUNCH("k_mlp_fwd_row");
+  kern<<<grid, threads, smem, st>>>(T, ntiles, m->dev(), w.G, w.Ep, w.Eatom, w.chat);
+  GNEP_CHECK_LAUNCH(what);
   return GNEP_OK;
 }
 
 template <int D, int HP, int NS, int NQR, int KR>
 int mlp_forward(const gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
-  return net_tile_atoms(nl, NS) == 32 ? mlp_forward_ta<D, NS, NQR, KR, 32>(m, nl, st)
-                                      : mlp_forward_ta<D, NS, NQR, KR, 128>(m, nl, st);
+  switch (net_tile_atoms(nl, NS)) {
+    case 32:
+      return launch_forward(k_mlp_fwd_row<D, NS, NQR, KR, 32>, NT, mlp_fwd_smem<D, NS, NQR, KR, 32>(m->shape.H), 32,
+                            m, nl, st, "k_mlp_fwd_row");
+    default:
+      return launch_forward(k_mlp_fwd_mma<D, HP, NS, NQR, KR, 128>, 256, mlp_fwd_mma_smem<D, HP, NS, NQR, KR, 128>(),
+                            128, m, nl, st, "k_mlp_fwd_mma");
+  }
 }
 
-template <int D, int HP, int TA>
-int mlp_backward_ta(const gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
+template <class K>
+int launch_backward(K kern, int threads, size_t smem, int tile_atoms, const gnep_model* m, gnep_nlist* nl,
+                    cudaStream_t st, const char* what) {
   const int ns = m->shape.ns;
-  const Tiles T = make_tiles(nl, ns, TA);
+  const Tiles T = make_tiles(nl, ns, tile_atoms);
   const int ntiles = T.tbase[ns];
   Workspace& w = nl->ws;
-  auto kern = k_mlp_bwd_row<D, HP, TA>;
-  const size_t smem = mlp_bwd_smem<D, HP, TA>(m->shape.H);
   int cap = 0;
-  if (int rc = resident_blocks(kern, smem, cap)) return rc;
+  if (int rc = resident_blocks(kern, threads, smem, cap)) return rc;
   if (cap > kNetBlocks) cap = kNetBlocks;  // net_part holds kNetBlocks partials
   const int grid = net_blocks(nl, ntiles < cap ? (ntiles > 0 ? ntiles : 1) : cap);
   w.net_blocks = grid;
   GNEP_CUDA(cudaMemsetAsync(w.net_part, 0, sizeof(float) * (size_t)grid * ns * m->net_size, st));
   if (ntiles == 0) return GNEP_OK;
-  kern<<<grid, NT, smem, st>>>(T, ntiles, m->dev(), nl->atom_struct, w.es, w.G, w.Gd, w.Gb, w.net_part,
-                               m->net_size);
-  GNEP_CHECK_LAUNCH("k_mlp_bwd_row");
+  kern<<<grid, threads, smem, st>>>(T, ntiles, m->dev(), nl->atom_struct, w.es, w.G, w.Gd, w.Gb, w.net_part,
+                                    m->net_size);
+  GNEP_CHECK_LAUNCH(what);
   return GNEP_OK;
 }
 
 template <int D, int HP>
 int mlp_backward(const gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
-  return net_tile_atoms(nl, m->shape.ns) == 32 ? mlp_backward_ta<D, HP, 32>(m, nl, st)
-                                               : mlp_backward_ta<D, HP, 128>(m, nl, st);
+  const int ta = net_tile_atoms(nl, m->shape.ns);
+  if (ta == 32)
+    return launch_backward(k_mlp_bwd_row<D, HP, 32>, NT, mlp_bwd_smem<D, HP, 32>(m->shape.H), 32, m, nl, st,
+                           "k_mlp_bwd_row");
+  if constexpr (HP <= 64) {
+    return launch_backward(k_mlp_bwd_mma<D, HP>, 256, mlp_bwd_mma_smem<D, HP>(), 128, m, nl, st, "k_mlp_bwd_mma");
+  } else {
+    return launch_backward(k_mlp_bwd_row<D, HP, 128>, NT, mlp_bwd_smem<D, HP, 128>(m->shape.H), 128, m, nl, st,
+                           "k_mlp_bwd_row");
+  }
 }
 
 // Instantiations: descriptor length D (with the radial block NQR x KR) and the

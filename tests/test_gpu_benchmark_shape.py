@@ -7,9 +7,9 @@ The batch is the smallest structures of the 256-structure workload, at least
 least two 128-atom tiles and several 32-atom tiles.  Running the network
 kernels with the default, one and three persistent blocks puts several tiles,
 and a species switch, inside one block, and gives the gradient assembly one or
-many block partials to combine.  The FP32 network runs with both tile sizes
-(32 atoms, eight threads per atom; 128 atoms, two) and the radial sweeps with
-4, 8 and 16 lanes per atom.  Checked against the oracle:
+many block partials to combine.  The FP32 network runs with each tile size
+(32 atoms on the CUDA cores, 128 atoms on the tensor cores) and the
+radial sweeps with 4, 8 and 16 lanes per atom.  Checked against the oracle:
 the loss terms and gradient (Eqs. 9-16, D1.18-D1.21) in the FP32 form at the
 FP32 tolerances and in the TF32 and BF16 network modes within four rounding
 units of their operand format; the descriptor scale computed on the GPU; and
