@@ -159,10 +159,17 @@ __global__ void __launch_bounds__(128) k_force_angular(int N, DevModel dm, const
                                                        const float* __restrict__ Sang, const float* __restrict__ Ep,
                                                        float4* __restrict__ dA) {
   constexpr int NAF = AMap<C::NQ, 1>::NA;
-  __shared__ float cA[C::NCA];
-  __shared__ float sh[NAF][C::NQA][NLM];
+  constexpr int KP = (C::KA + 3) / 4 * 4;  // basis functions padded to 16-byte rows
+  static_assert(NLM % 4 == 0, "16-byte Shat rows");
+  // c^A_nk^{IJ} as [IJ][n][KP] and Shat [atom][n][lm]: both read as float4 (one
+  // shared-memory load per four products)
+  __shared__ __align__(16) float cA[C::NS * C::NS * C::NQA * KP];
+  __shared__ __align__(16) float sh[NAF][C::NQA][NLM];
   const int i0 = tiles[blockIdx.x], i1 = tiles[blockIdx.x + 1];
-  for (int q = threadIdx.x; q < C::NCA; q += blockDim.x) cA[q] = dm.params[dm.off_cA + q];
+  for (int q = threadIdx.x; q < C::NS * C::NS * C::NQA * KP; q += blockDim.x) {
+    const int k = q % KP, r = q / KP;  // r = (I NS + J) NQA + n
+    cA[q] = k < C::KA ? dm.params[dm.off_cA + r * C::KA + k] : 0.f;
+  }
   for (int t = threadIdx.x; t < NAF * C::NQA; t += blockDim.x) {
     const int a = t / C::NQA, n = t % C::NQA, i = i0 + a;
     if (i >= i1) continue;
@@ -192,17 +199,23 @@ __global__ void __launch_bounds__(128) k_force_angular(int N, DevModel dm, const
     const float rr = sqrtf(r.x * r.x + r.y * r.y + r.z * r.z);
     const float ri = 1.f / rr;
     const float ux = r.x * ri, uy = r.y * ri, uz = r.z * ri;
-    float f[C::KA], fp[C::KA];
-    radial_basis_d<C::KA>(rr, dm.rca_inv, f, fp);
-    const float* cIJ = cA + (I * C::NS + J) * C::NQA * C::KA;
+    float fk[C::KA], fpk[C::KA], f[KP], fp[KP];
+    radial_basis_d<C::KA>(rr, dm.rca_inv, fk, fpk);
+#pragma unroll
+    for (int k = 0; k < KP; ++k) {
+      f[k] = k < C::KA ? fk[k] : 0.f;
+      fp[k] = k < C::KA ? fpk[k] : 0.f;
+    }
+    const float4* cIJ = reinterpret_cast<const float4*>(cA + (I * C::NS + J) * C::NQA * KP);
     float g[C::NQA], gp[C::NQA];
 #pragma unroll
     for (int n = 0; n < C::NQA; ++n) {
       float a1 = 0.f, a2 = 0.f;
 #pragma unroll
-      for (int k = 0; k < C::KA; ++k) {
-        a1 = fmaf(cIJ[n * C::KA + k], f[k], a1);
-        a2 = fmaf(cIJ[n * C::KA + k], fp[k], a2);
+      for (int k4 = 0; k4 < KP / 4; ++k4) {
+        const float4 c = cIJ[n * (KP / 4) + k4];
+        a1 = fmaf(c.x, f[4 * k4], fmaf(c.y, f[4 * k4 + 1], fmaf(c.z, f[4 * k4 + 2], fmaf(c.w, f[4 * k4 + 3], a1))));
+        a2 = fmaf(c.x, fp[4 * k4], fmaf(c.y, fp[4 * k4 + 1], fmaf(c.z, fp[4 * k4 + 2], fmaf(c.w, fp[4 * k4 + 3], a2))));
       }
       g[n] = a1;
       gp[n] = a2;
@@ -210,19 +223,28 @@ __global__ void __launch_bounds__(128) k_force_angular(int N, DevModel dm, const
     float B[NLM], gx[NLM], gy[NLM], gz[NLM];
     harmonics_grad(ux, uy, uz, 1.f, B, gx, gy, gz);
     float P = 0.f, vx = 0.f, vy = 0.f, vz = 0.f;
+    const float4* sa = reinterpret_cast<const float4*>(&sh[a][0][0]);
 #pragma unroll
-    for (int q = 0; q < NLM; ++q) {
-      float gh = 0.f, ghp = 0.f;
+    for (int q4 = 0; q4 < NLM / 4; ++q4) {
+      float gh[4] = {0.f, 0.f, 0.f, 0.f}, ghp[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int n = 0; n < C::NQA; ++n) {
-        const float s = sh[a][n][q];
-        gh = fmaf(g[n], s, gh);
-        ghp = fmaf(gp[n], s, ghp);
+        const float4 s4 = sa[n * (NLM / 4) + q4];
+        const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          gh[e] = fmaf(g[n], sv[e], gh[e]);
+          ghp[e] = fmaf(gp[n], sv[e], ghp[e]);
+        }
       }
-      P = fmaf(ghp, B[q], P);
-      vx = fmaf(gh, gx[q], vx);
-      vy = fmaf(gh, gy[q], vy);
-      vz = fmaf(gh, gz[q], vz);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int q = 4 * q4 + e;
+        P = fmaf(ghp[e], B[q], P);
+        vx = fmaf(gh[e], gx[q], vx);
+        vy = fmaf(gh[e], gy[q], vy);
+        vz = fmaf(gh[e], gz[q], vz);
+      }
     }
     dA[p] = make_float4(P * ux + vx * ri, P * uy + vy * ri, P * uz + vz * ri, 0.f);
   }
