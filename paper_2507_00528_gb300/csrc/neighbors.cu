@@ -20,6 +20,11 @@ namespace gnep {
 
 namespace {
 
+// Structures with more atoms than this take the binned search, the others
+// the all-pairs one (the two give identical lists).
+constexpr int kCellMinAtoms = 1024;
+
+
 __global__ void k_atom_struct(const int* __restrict__ off, int S, int N, int* __restrict__ out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
@@ -33,9 +38,14 @@ __global__ void k_atom_struct(const int* __restrict__ off, int S, int N, int* __
 
 // Images needed per cell direction: floor(rc / w) + 1, w = V / |b x c| etc.
 // tw[s][x] = rc / w_x bounds |df_x + n_x| for any pair within rc.  Also the
-// inverse cell (FP64) and the cell split into FP32 high and low parts.
-__global__ void k_image_range(const double* __restrict__ cell, int S, double rc, int* __restrict__ kr,
-                              float* __restrict__ tw, double* __restrict__ hinv, float* __restrict__ hsplit) {
+// inverse cell (FP64), the cell split into FP32 high and low parts, and the
+// bins of the binned search: nbin[s][x] = floor(w_x / (rc / 2)) bins along
+// direction x (at least 1), reduced until the structure has no more bins than
+// atoms (so that the bins of structure s can be numbered from its first atom
+// index on).
+__global__ void k_image_range(const double* __restrict__ cell, int S, double rc, const int* __restrict__ soff,
+                              int* __restrict__ kr, float* __restrict__ tw, double* __restrict__ hinv,
+                              float* __restrict__ hsplit, int* __restrict__ nbin) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= S) return;
   const double* H = cell + 9 * s;
@@ -61,10 +71,52 @@ __global__ void k_image_range(const double* __restrict__ cell, int S, double rc,
   const double ab[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
   const double vol = fabs(a[0] * bc[0] + a[1] * bc[1] + a[2] * bc[2]);
   const double n[3] = {norm3d(bc[0], bc[1], bc[2]), norm3d(ca[0], ca[1], ca[2]), norm3d(ab[0], ab[1], ab[2])};
+  int nb[3];
   for (int x = 0; x < 3; ++x) {
     kr[3 * s + x] = (int)floor(rc / (vol / n[x])) + 1;
     tw[3 * s + x] = (float)(rc / (vol / n[x]));
+    const double q = floor((vol / n[x]) / (0.5 * rc));
+    nb[x] = q < 1.0 ? 1 : q > 64.0 ? 64 : (int)q;
   }
+  const int cap = max(1, soff[s + 1] - soff[s]);
+  while (nb[0] * nb[1] * nb[2] > cap) {  // at most 189 steps
+    const int x = (nb[0] >= nb[1] && nb[0] >= nb[2]) ? 0 : (nb[1] >= nb[2] ? 1 : 2);
+    --nb[x];
+  }
+  for (int x = 0; x < 3; ++x) nbin[3 * s + x] = nb[x];
+}
+
+// Bin of atom i of structure s in the binned search (from its FP32 fractional
+// coordinates; any consistent assignment is valid, since the search visits
+// every bin that can hold a neighbour and the lists are sorted afterwards).
+__device__ __forceinline__ int atom_bin(float4 f, const int* nb) {
+  const int bx = min(nb[0] - 1, max(0, (int)floorf(f.x * (float)nb[0])));
+  const int by = min(nb[1] - 1, max(0, (int)floorf(f.y * (float)nb[1])));
+  const int bz = min(nb[2] - 1, max(0, (int)floorf(f.z * (float)nb[2])));
+  return bx + nb[0] * (by + nb[1] * bz);
+}
+
+// Atoms per bin (bins of structure s are numbered from its first atom index).
+__global__ void k_bin_count(int N, const int* __restrict__ atom_struct, const int* __restrict__ soff,
+                            const int* __restrict__ nbin, const float4* __restrict__ frac, int* __restrict__ bcount) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int s = atom_struct[i];
+  if (soff[s + 1] - soff[s] <= kCellMinAtoms) return;  // searched without bins
+  atomicAdd(&bcount[soff[s] + atom_bin(frac[i], nbin + 3 * s)], 1);
+}
+
+// Atom indices by bin, at the scanned bin starts (the order inside a bin is
+// free: it only sets the order in which candidates are tested).
+__global__ void k_bin_fill(int N, const int* __restrict__ atom_struct, const int* __restrict__ soff,
+                           const int* __restrict__ nbin, const float4* __restrict__ frac,
+                           const long long* __restrict__ bstart, int* __restrict__ bcursor, int* __restrict__ batom) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int s = atom_struct[i];
+  if (soff[s + 1] - soff[s] <= kCellMinAtoms) return;  // searched without bins
+  const int b = soff[s] + atom_bin(frac[i], nbin + 3 * s);
+  batom[bstart[b] + atomicAdd(&bcursor[b], 1)] = i;
 }
 
 // Per atom: fractional coordinates f = r H^-1 (FP32; only used to bound image
@@ -141,13 +193,44 @@ struct ListParams {
   float reject2;     // max(hi2): candidates above it are outside both
 };
 
+// The list decisions for neighbour j of atom i at image n (na, nb, nc) of
+// structure s: FP32 away from the cut-offs, the exact FP64 expression within
+// the band.  dj = phi_j - phi_i (high parts), Hh the FP32 high parts of the
+// cell.  Both searches (all pairs, binned) take their decisions here.
+__device__ __forceinline__ void decide_pair(int i, int j, int na, int nb, int nc, const float (&dj)[3],
+                                            const float (&Hh)[9], const ListParams& lp,
+                                            const double* __restrict__ cell, const double* __restrict__ pos, int s,
+                                            bool& in0, bool& in1) {
+  in0 = in1 = false;
+  if (j == i && na == 0 && nb == 0 && nc == 0) return;
+  const float fx = dj[0] + ((float)na * Hh[0] + (float)nb * Hh[3] + (float)nc * Hh[6]);
+  const float fy = dj[1] + ((float)na * Hh[1] + (float)nb * Hh[4] + (float)nc * Hh[7]);
+  const float fz = dj[2] + ((float)na * Hh[2] + (float)nb * Hh[5] + (float)nc * Hh[8]);
+  const float d2f = fx * fx + fy * fy + fz * fz;
+  if (d2f > lp.reject2) return;
+  in0 = d2f < lp.lo2[0];
+  in1 = d2f < lp.lo2[1];
+  const bool band0 = !in0 && d2f <= lp.hi2[0], band1 = !in1 && d2f <= lp.hi2[1];
+  if (band0 || band1) {  // near a cut-off: the FP64 decision
+    const double* Hd = cell + 9 * s;
+    const double H[9] = {Hd[0], Hd[1], Hd[2], Hd[3], Hd[4], Hd[5], Hd[6], Hd[7], Hd[8]};
+    const double pi[3] = {pos[3 * (size_t)i], pos[3 * (size_t)i + 1], pos[3 * (size_t)i + 2]};
+    const double pj[3] = {pos[3 * (size_t)j], pos[3 * (size_t)j + 1], pos[3 * (size_t)j + 2]};
+    double d[3];
+    const double d2 = pair_d2_exact(H, pi, pj, na, nb, nc, d);
+    if (band0) in0 = d2 < lp.rc2[0];
+    if (band1) in1 = d2 < lp.rc2[1];
+  }
+}
+
 // One warp per central atom i.  Lane l tests the neighbours j = a0 + l,
 // a0 + l + 32, ...: in each round of 32 consecutive j every lane walks the
 // images of its j in lexicographic order, and the warp places the accepted
 // entries by an exclusive scan of the per-lane counts, so each list comes out
 // in canonical order (j ascending, then image).  kMode 1 writes the CSR lists
-// at the scanned offsets; kMode 2 counts and writes each atom's first cap
-// entries into its slots (the slots are then compacted).  Both modes take the
+// at the scanned offsets (every structure); kMode 2 counts and writes each
+// atom's first cap entries into its slots (the slots are then compacted), for
+// the structures of at most kCellMinAtoms atoms.  Both modes take the
 // same decisions (FP32 away from the cut-offs, FP64 within the band).  A lane
 // keeps up to kBuf accepted images of its j in a packed register; a round in
 // which some lane accepts more walks the images again to place them.
@@ -174,6 +257,7 @@ __global__ void __launch_bounds__(128) k_pairs(
   if (i >= N) return;  // the whole warp
   const int s = atom_struct[i];
   const int a0 = struct_off[s], a1 = struct_off[s + 1];
+  if (!kFill && a1 - a0 > kCellMinAtoms) return;  // the binned search takes this structure's slot pass
   float Hh[9], Hl[9];
 #pragma unroll
   for (int q = 0; q < 9; ++q) {
@@ -200,26 +284,7 @@ __global__ void __launch_bounds__(128) k_pairs(
     const int clo = max(-kc, (int)ceilf(-t2 - dfc)), chi = min(kc, (int)floorf(t2 - dfc));
     // the list decisions for image n of this lane's j
     auto decide = [&](int na, int nb, int nc, bool& in0, bool& in1) {
-      in0 = in1 = false;
-      if (j == i && na == 0 && nb == 0 && nc == 0) return;
-      const float fx = dj[0] + ((float)na * Hh[0] + (float)nb * Hh[3] + (float)nc * Hh[6]);
-      const float fy = dj[1] + ((float)na * Hh[1] + (float)nb * Hh[4] + (float)nc * Hh[7]);
-      const float fz = dj[2] + ((float)na * Hh[2] + (float)nb * Hh[5] + (float)nc * Hh[8]);
-      const float d2f = fx * fx + fy * fy + fz * fz;
-      if (d2f > lp.reject2) return;
-      in0 = d2f < lp.lo2[0];
-      in1 = d2f < lp.lo2[1];
-      const bool band0 = !in0 && d2f <= lp.hi2[0], band1 = !in1 && d2f <= lp.hi2[1];
-      if (band0 || band1) {  // near a cut-off: the FP64 decision
-        const double* Hd = cell + 9 * s;
-        const double H[9] = {Hd[0], Hd[1], Hd[2], Hd[3], Hd[4], Hd[5], Hd[6], Hd[7], Hd[8]};
-        const double pi[3] = {pos[3 * (size_t)i], pos[3 * (size_t)i + 1], pos[3 * (size_t)i + 2]};
-        const double pj[3] = {pos[3 * (size_t)j], pos[3 * (size_t)j + 1], pos[3 * (size_t)j + 2]};
-        double d[3];
-        const double d2 = pair_d2_exact(H, pi, pj, na, nb, nc, d);
-        if (band0) in0 = d2 < lp.rc2[0];
-        if (band1) in1 = d2 < lp.rc2[1];
-      }
+      decide_pair(i, j, na, nb, nc, dj, Hh, lp, cell, pos, s, in0, in1);
     };
     // places one accepted entry at the next positions of its lists
     auto put = [&](int na, int nb, int nc, bool in0, bool in1, int& w0, int& w1) {
@@ -293,6 +358,122 @@ __global__ void __launch_bounds__(128) k_pairs(
   if (!kFill && lane == 0) {
     cnt0[i] = base0;
     cnt1[i] = base1;
+  }
+}
+
+// Binned search, one warp per central atom i (the slot pass) of the
+// structures above kCellMinAtoms atoms; the smaller ones take the all-pairs
+// search (k_pairs), which is as fast there: at cell widths below 3 r_c the
+// visited bins cover about the whole cell.  The bins of structure s split its
+// cell into nbin[s] parts along each cell direction; every (j, n) within r_c of
+// i has f_j + n inside (f_i - t, f_i + t) along each direction (t = r_c / w_x,
+// with a margin), i.e. in one of the extended bins floor((f_i - t) nbin) ..
+// floor((f_i + t) nbin), so the warp visits those bins (lane per bin; extended
+// bin B holds the atoms of bin B mod nbin at the image floor(B / nbin)) and
+// tests their atoms with the same decision as the all-pairs search.  Accepted
+// entries collect in shared memory as keys (j, image, lists); each entry's
+// position in each list is its rank among the list's entries in canonical
+// order (j ascending, then image lexicographic), so the slots hold exactly the
+// lists of the all-pairs search.  Counts are exact even when an atom overflows
+// its slots (the writing pass then takes the batch).
+constexpr int kCellWarps = 4;
+constexpr int kCellBuf = 160;  // accepted entries a warp ranks per atom (both lists)
+
+__device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+__global__ void __launch_bounds__(32 * kCellWarps) k_pairs_cell(
+    int N, const int* __restrict__ struct_off, const int* __restrict__ atom_struct,
+    const double* __restrict__ pos, const double* __restrict__ cell, const float* __restrict__ tw,
+    const float* __restrict__ hsplit, const int* __restrict__ nbin, const long long* __restrict__ bstart,
+    const int* __restrict__ batom, const float4* __restrict__ frac, const float4* __restrict__ phi, ListParams lp,
+    int* __restrict__ cnt0, int* __restrict__ cnt1, Slots sl) {
+  __shared__ unsigned long long key[kCellWarps][kCellBuf];
+  __shared__ int nacc[kCellWarps], nin[kCellWarps][2];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ib = blockIdx.x * kCellWarps;
+  {
+    const int i = ib + w;
+    if (i >= N) return;  // the whole warp; no block-wide barrier follows
+    const int s = atom_struct[i], a0 = struct_off[s];
+    if (struct_off[s + 1] - a0 <= kCellMinAtoms) return;  // taken by the all-pairs search
+    if (lane == 0) {
+      nacc[w] = 0;
+      nin[w][0] = nin[w][1] = 0;
+    }
+    __syncwarp();
+    const long long Q0 = bstart[a0];
+    float Hh[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) Hh[q] = hsplit[18 * s + q];
+    const float4 pih = phi[i], fi = frac[i];
+    const float f[3] = {fi.x, fi.y, fi.z};
+    int nb[3], lo[3], cnt[3];
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      nb[x] = nbin[3 * s + x];
+      const float t = tw[3 * s + x] + 2e-3f;
+      lo[x] = (int)floorf((f[x] - t) * (float)nb[x]);
+      cnt[x] = (int)floorf((f[x] + t) * (float)nb[x]) - lo[x] + 1;
+    }
+    const int NB = cnt[0] * cnt[1] * cnt[2];
+    for (int e = lane; e < NB; e += 32) {
+      const int B[3] = {lo[0] + e % cnt[0], lo[1] + (e / cnt[0]) % cnt[1], lo[2] + e / (cnt[0] * cnt[1])};
+      int n[3], bx[3];
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        n[x] = floor_div(B[x], nb[x]);
+        bx[x] = B[x] - n[x] * nb[x];
+      }
+      const int bin = bx[0] + nb[0] * (bx[1] + nb[1] * bx[2]);
+      const int q0 = (int)(bstart[a0 + bin] - Q0), q1 = (int)(bstart[a0 + bin + 1] - Q0);
+      for (int q = q0; q < q1; ++q) {
+        const int j = batom[Q0 + q];
+        const float4 pjh = phi[j];
+        const float dj[3] = {pjh.x - pih.x, pjh.y - pih.y, pjh.z - pih.z};
+        bool in0, in1;
+        decide_pair(i, j, n[0], n[1], n[2], dj, Hh, lp, cell, pos, s, in0, in1);
+        if (!in0 && !in1) continue;
+        if (in0) atomicAdd(&nin[w][0], 1);
+        if (in1) atomicAdd(&nin[w][1], 1);
+        const int slot = atomicAdd(&nacc[w], 1);
+        if (slot < kCellBuf)
+          key[w][slot] = ((unsigned long long)j << 26) | ((unsigned long long)(n[0] + 128) << 18) |
+                         ((unsigned long long)(n[1] + 128) << 10) | ((unsigned long long)(n[2] + 128) << 2) |
+                         ((unsigned long long)in1 << 1) | (unsigned long long)in0;
+      }
+    }
+    __syncwarp();
+    const int M = nacc[w], c0 = nin[w][0], c1 = nin[w][1];
+    if (lane == 0) {
+      cnt0[i] = c0;
+      cnt1[i] = c1;
+    }
+    if (M <= kCellBuf && c0 <= sl.cap[0] && c1 <= sl.cap[1]) {  // else the writing pass takes the batch
+      for (int e = lane; e < M; e += 32) {
+        const unsigned long long ke = key[w][e];
+        int r0 = 0, r1 = 0;
+        for (int e2 = 0; e2 < M; ++e2) {  // keys are distinct: ranks are positions
+          const unsigned long long k2 = key[w][e2];
+          const bool lt = k2 < ke;
+          r0 += (lt && (k2 & 1ull)) ? 1 : 0;
+          r1 += (lt && (k2 & 2ull)) ? 1 : 0;
+        }
+        const int j = (int)(ke >> 26);
+        const char4 sv = make_char4((signed char)((int)((ke >> 18) & 255ull) - 128),
+                                    (signed char)((int)((ke >> 10) & 255ull) - 128),
+                                    (signed char)((int)((ke >> 2) & 255ull) - 128), 0);
+        if (ke & 1ull) {
+          const size_t q = (size_t)i * sl.cap[0] + r0;
+          sl.j[0][q] = j;
+          sl.sh[0][q] = sv;
+        }
+        if (ke & 2ull) {
+          const size_t q = (size_t)i * sl.cap[1] + r1;
+          sl.j[1][q] = j;
+          sl.sh[1][q] = sv;
+        }
+      }
+    }
   }
 }
 
@@ -423,7 +604,7 @@ int build_lists(gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
   auto cleanup = [&]() {
     for (auto p : tmp) cudaFreeAsync(p, st);
   };
-  int *cnt = nullptr, *kr = nullptr;
+  int *cnt = nullptr, *kr = nullptr, *bins = nullptr;
   float *tw = nullptr, *hsplit = nullptr;
   double* hinv = nullptr;
   float4 *frac = nullptr, *phi = nullptr, *plo = nullptr;
@@ -437,16 +618,35 @@ int build_lists(gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
   GNEP_CUDA(cudaMallocAsync(&frac, sizeof(float4) * 3 * (size_t)N, st));
   phi = frac + N;
   plo = frac + 2 * (size_t)N;
-  for (void* p : {(void*)cnt, (void*)kr, (void*)tw, (void*)hsplit, (void*)hinv, (void*)frac, (void*)offs})
+  // bins: nbin [3 S], counts and cursors [N + 1] each, atoms by bin [N]
+  GNEP_CUDA(cudaMallocAsync(&bins, sizeof(int) * (3 * (size_t)S + 3 * (size_t)N + 2), st));
+  int* nbin = bins;
+  int* bcount = bins + 3 * (size_t)S;
+  int* bcursor = bcount + (N + 1);
+  int* batom = bcursor + (N + 1);
+  for (void* p : {(void*)cnt, (void*)kr, (void*)tw, (void*)hsplit, (void*)hinv, (void*)frac, (void*)offs, (void*)bins})
     tmp.push_back(p);
   GNEP_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * 2 * (size_t)(N + 1), st));
+  GNEP_CUDA(cudaMemsetAsync(bcount, 0, sizeof(int) * 2 * (size_t)(N + 1), st));  // and bcursor
 
   k_atom_struct<<<blocks_for(N, 256), 256, 0, st>>>(nl->struct_off, S, N, nl->atom_struct);
   const double rcmax = nl->rcr > nl->rca ? nl->rcr : nl->rca;
-  k_image_range<<<blocks_for(S, 128), 128, 0, st>>>(nl->cell, S, rcmax, kr, tw, hinv, hsplit);
+  k_image_range<<<blocks_for(S, 128), 128, 0, st>>>(nl->cell, S, rcmax, nl->struct_off, kr, tw, hinv, hsplit, nbin);
   k_atom_prep<<<blocks_for(N, 256), 256, 0, st>>>(N, nl->atom_struct, nl->pos, nl->type, hinv, frac, phi, plo,
                                                    m->err);
   GNEP_CHECK_LAUNCH("k_image_range");
+  // atoms by bin
+  long long* bstart = nullptr;
+  GNEP_CUDA(cudaMallocAsync(&bstart, sizeof(long long) * (size_t)(N + 1), st));
+  tmp.push_back(bstart);
+  k_bin_count<<<blocks_for(N, 256), 256, 0, st>>>(N, nl->atom_struct, nl->struct_off, nbin, frac, bcount);
+  if (int rc = scan_rec(nullptr, bcount, N + 1, bstart, tmp, st)) {
+    cleanup();
+    return rc;
+  }
+  k_bin_fill<<<blocks_for(N, 256), 256, 0, st>>>(N, nl->atom_struct, nl->struct_off, nbin, frac, bstart, bcursor,
+                                                  batom);
+  GNEP_CHECK_LAUNCH("k_bin_fill");
 
   ListParams lp;
   lp.rc2[0] = nl->rcr * nl->rcr;
@@ -477,7 +677,10 @@ int build_lists(gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
   k_pairs<2><<<blocks_for((int64_t)N * 32, 128), 128, 0, st>>>(
       N, nl->struct_off, nl->atom_struct, nl->pos, nl->cell, kr, tw, hsplit, frac, phi, plo, lp, cnt0, cnt1,
       nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, sl);
-  GNEP_CHECK_LAUNCH("k_pairs<stage>");
+  k_pairs_cell<<<(unsigned)((N + kCellWarps - 1) / kCellWarps), 32 * kCellWarps, 0, st>>>(
+      N, nl->struct_off, nl->atom_struct, nl->pos, nl->cell, tw, hsplit, nbin, bstart, batom, frac, phi, lp, cnt0,
+      cnt1, sl);
+  GNEP_CHECK_LAUNCH("pair search");
   int* maxc = nullptr;
   GNEP_CUDA(cudaMallocAsync(&maxc, sizeof(int) * 2, st));
   tmp.push_back(maxc);

@@ -299,6 +299,26 @@ def test_skewed_cells_many_images_and_largest_structure():
     assert rel_l2(F[26:], fo) < F_TOL and rel_l2(W[2], wo[0]) < F_TOL
 
 
+def test_binned_search_large_structures_bit_exact():
+    """Structures above 1024 atoms take the binned pair search, the others the
+    all-pairs one, in the same build: a 1500-atom rocksalt cell, a 1300-atom
+    strained (triclinic) cell and a 40-atom cell.  Both lists equal the
+    oracle's (Eq. 2) entry for entry, and so do the forces of the large cells."""
+    b = synth.make_batch([1500, 40, 1300], [0, 2, 2], np.random.default_rng(41))
+    c = Case("nmax4_basis8_h30", b.subset([1]), labels=False)
+    nl = c.m.neighbors(gnep.DeviceBatch.from_host(b))
+    for which, rc in ((0, 7.0), (1, 4.0)):
+        off, j, sh = nl.export(which)
+        ooff, oj, osh = O.neighbors(b, rc)
+        np.testing.assert_array_equal(off, ooff)
+        np.testing.assert_array_equal(j, oj)
+        np.testing.assert_array_equal(sh, osh)
+    _, Es, F, W = (t.double().cpu().numpy() for t in c.m.forward(nl))
+    _, eso, fo, wo = O.forward(c.cfg, c.P64, c.s64, b)
+    assert rel_l2(Es, eso) < E_TOL
+    assert rel_l2(F, fo) < F_TOL and rel_l2(W, wo) < F_TOL
+
+
 def test_dense_image_lattice_overflows_the_slots():
     """A one-atom cubic cell of 2.3 A holds about 118 images within the radial
     cut-off, more than the 96 per-atom slots of the one-pass search: the lists
