@@ -499,9 +499,17 @@ __device__ void load_weights_split(const DevModel& dm, int e, uint32_t* Wh, uint
   constexpr int SW = MmaW<D>::SW;
   const float* P = dm.params + (size_t)e * dm.net_size;
   const int H = dm.H;
-  for (int q = threadIdx.x; q < HP * SW; q += NTH) {
-    const int mu = q / SW, v = q % SW;
-    split_tf32<true>((v < D && mu < H) ? P[mu * D + v] : 0.f, Wh[q], Wl[q]);
+  constexpr int N = HP * SW;
+  for (int q0 = threadIdx.x; q0 < N; q0 += 4 * NTH) {  // four loads in flight per thread
+    float x[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int q = q0 + k * NTH, mu = q / SW, v = q % SW;
+      x[k] = (q < N && v < D && mu < H) ? __ldg(P + mu * D + v) : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (q0 + k * NTH < N) split_tf32<true>(x[k], Wh[q0 + k * NTH], Wl[q0 + k * NTH]);
   }
   for (int mu = threadIdx.x; mu < HP; mu += NTH) {
     b0[mu] = mu < H ? P[D * H + mu] : 0.f;
