@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/gnep.h"
@@ -149,6 +150,30 @@ int cuda_error(cudaError_t e, const char* what);
     cudaError_t e_ = (call);                                   \
     if (e_ != cudaSuccess) return gnep::cuda_error(e_, #call); \
   } while (0)
+// Programmatic dependent launch.  The kernels of a step are launched with
+// launch_pdl, so a kernel's blocks may be scheduled (and reach their first
+// instruction) while the previous kernel's last blocks still run; every such
+// kernel executes GNEP_PDL_WAIT before its first access to device memory,
+// which returns once the previous kernel has completed and its writes are
+// visible.  Outside a dependent launch the wait returns at once.
+#define GNEP_PDL_WAIT() asm volatile("griddepcontrol.wait;" ::: "memory")
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 #define GNEP_CHECK_LAUNCH(what)                                \
   do {                                                         \
     cudaError_t e_ = cudaGetLastError();                       \

@@ -192,6 +192,7 @@ template <int D, int NS, int NQR, int KR, int TA>
 __global__ void __launch_bounds__(NT, 1) k_mlp_fwd_row(Tiles T, int ntiles, DevModel dm, const float* __restrict__ G,
                                                        float* __restrict__ Ep, float* __restrict__ Eatom,
                                                        float* __restrict__ chat) {
+  GNEP_PDL_WAIT();
   constexpr int DW = RowW<D>::DW, NJK = NS * KR, GP = TileMap<TA>::G, AW = TileMap<TA>::AW;
   extern __shared__ float4 sm4[];
   const int H = dm.H, H2 = h_even<GP>(H), Hh = H2 / GP;
@@ -286,6 +287,7 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_bwd_row(Tiles T, int ntiles, DevM
                                                        const float* __restrict__ es, const float* __restrict__ G,
                                                        const float* __restrict__ Gd, float* __restrict__ Gb,
                                                        float* __restrict__ part, int part_stride) {
+  GNEP_PDL_WAIT();
   constexpr int DW = RowW<D>::DW, NVB = DW / 4, GP = TileMap<TA>::G, AW = TileMap<TA>::AW;
   constexpr int NBK = ((HP / 4) * NVB + NT - 1) / NT;  // dW0 4 x 4 blocks per thread
   extern __shared__ float4 sm4[];
@@ -547,6 +549,7 @@ template <int D, int HP, int NS, int NQR, int KR, int TA>
 __global__ void __launch_bounds__(2 * TA, 1) k_mlp_fwd_mma(Tiles T, int ntiles, DevModel dm, const float* __restrict__ G,
                                                        float* __restrict__ Ep, float* __restrict__ Eatom,
                                                        float* __restrict__ chat) {
+  GNEP_PDL_WAIT();
   constexpr int NTB = 2 * TA, SW = MmaW<D>::SW, KD = MmaW<D>::KD, NJK = NS * KR;
   static_assert(HP % 16 == 0 && TA == 128, "16-unit chunks, 16 atoms per warp");
   extern __shared__ float4 sm4[];
@@ -676,6 +679,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd_mma(Tiles T, int ntiles, Dev
                                                        const float* __restrict__ es, const float* __restrict__ G,
                                                        const float* __restrict__ Gd, float* __restrict__ Gb,
                                                        float* __restrict__ part, int part_stride) {
+  GNEP_PDL_WAIT();
   constexpr int TA = 128, NTB = 256, NWB = 8, SW = MmaW<D>::SW, KD = MmaW<D>::KD, HR = HP + 8;
   constexpr int MT = HP / 16, KG = NWB / MT, KA = TA / KG;  // dW0: unit blocks, atom groups, atoms per group
   static_assert(HP % 16 == 0 && HP <= 64 && NWB % MT == 0, "16-unit chunks, 16 atoms per warp");
@@ -951,7 +955,7 @@ int launch_forward(K kern, int threads, size_t smem, int tile_atoms, const gnep_
   int cap = 0;
   if (int rc = resident_blocks(kern, threads, smem, cap)) return rc;
   const int grid = net_blocks(nl, ntiles < cap ? ntiles : cap);
-  kern<<<grid, threads, smem, st>>>(T, ntiles, m->dev(), w.G, w.Ep, w.Eatom, w.chat);
+  (void)launch_pdl(kern, grid, threads, smem, st, T, ntiles, m->dev(), w.G, w.Ep, w.Eatom, w.chat);
   GNEP_CHECK_LAUNCH(what);
   return GNEP_OK;
 }
@@ -982,7 +986,7 @@ int launch_backward(K kern, int threads, size_t smem, int tile_atoms, const gnep
   w.net_blocks = grid;
   GNEP_CUDA(cudaMemsetAsync(w.net_part, 0, sizeof(float) * (size_t)grid * ns * m->net_size, st));
   if (ntiles == 0) return GNEP_OK;
-  kern<<<grid, threads, smem, st>>>(T, ntiles, m->dev(), nl->atom_struct, w.es, w.G, w.Gd, w.Gb, w.net_part,
+  (void)launch_pdl(kern, grid, threads, smem, st, T, ntiles, m->dev(), nl->atom_struct, w.es, w.G, w.Gd, w.Gb, w.net_part,
                                     m->net_size);
   GNEP_CHECK_LAUNCH(what);
   return GNEP_OK;

@@ -304,6 +304,7 @@ template <bool TF32, int D, int HPn, int NS, int NQR, int KR>
 __global__ void __launch_bounds__(NTC, (Dims<TF32, D, HPn>::fwd_minb))
     k_mlp_fwd_tc(Tiles T, int ntiles, DevModel dm, const float* __restrict__ G, float* __restrict__ Ep,
                  float* __restrict__ Eatom, float* __restrict__ chat, int* __restrict__ err) {
+  GNEP_PDL_WAIT();
   using Dm = Dims<TF32, D, HPn>;
   constexpr int DPn = Dm::DPn, OW = Dm::OW, NCZ = HPn / 16, NCE = DPn / 16, NJK = NS * KR;
   constexpr int EW = 4 / tc::Elem<TF32>::ES;  // operand elements per 4-byte word
@@ -427,6 +428,7 @@ __global__ void __launch_bounds__(NTC, (Dims<TF32, D, HPn>::bwd_minb))
     k_mlp_bwd_tc(Tiles T, int ntiles, DevModel dm, const int* __restrict__ atom_struct, const float* __restrict__ es,
                  const float* __restrict__ G, const float* __restrict__ Gd, float* __restrict__ Gb,
                  float* __restrict__ part, int part_stride, int* __restrict__ err) {
+  GNEP_PDL_WAIT();
   using Dm = Dims<TF32, D, HPn>;
   constexpr int DPn = Dm::DPn, OW = Dm::OW, NCZ = HPn / 16, NCD = DPn / 16;
   constexpr int EW = 4 / tc::Elem<TF32>::ES;  // operand elements per 4-byte word
@@ -683,7 +685,7 @@ int mlp_forward_tc(const gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
   int smem = 0, grid = 0;
   if (int rc = tc_launch_shape(kern, Dm::fwd_smem, Dm::fwd_cols, ntiles, smem, grid)) return rc;
   grid = net_blocks(nl, grid);
-  kern<<<grid, NTC, smem, st>>>(T, ntiles, m->dev(), w.G, w.Ep, w.Eatom, w.chat, m->err);
+  (void)launch_pdl(kern, grid, NTC, smem, st, T, ntiles, m->dev(), w.G, w.Ep, w.Eatom, w.chat, m->err);
   GNEP_CHECK_LAUNCH("k_mlp_fwd_tc");
   return GNEP_OK;
 }
@@ -704,7 +706,7 @@ int mlp_backward_tc(const gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
   w.net_blocks = grid;
   GNEP_CUDA(cudaMemsetAsync(w.net_part, 0, sizeof(float) * (size_t)grid * ns * m->net_size, st));
   if (ntiles == 0) return GNEP_OK;
-  kern<<<grid, NTC, smem, st>>>(T, ntiles, m->dev(), nl->atom_struct, w.es, w.G, w.Gd, w.Gb, w.net_part,
+  (void)launch_pdl(kern, grid, NTC, smem, st, T, ntiles, m->dev(), nl->atom_struct, w.es, w.G, w.Gd, w.Gb, w.net_part,
                                 m->net_size, m->err);
   GNEP_CHECK_LAUNCH("k_mlp_bwd_tc");
   return GNEP_OK;

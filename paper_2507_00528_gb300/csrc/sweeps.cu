@@ -100,6 +100,7 @@ template <class C, int RL>
 __global__ void __launch_bounds__(128) k_desc_radial(int N, DevModel dm, const int* __restrict__ type,
                                                      const int* __restrict__ off, const float4* __restrict__ rij,
                                                      float* __restrict__ FR, float* __restrict__ G) {
+  GNEP_PDL_WAIT();
   __shared__ float cR[C::NCR];
   for (int q = threadIdx.x; q < C::NCR; q += blockDim.x) cR[q] = dm.params[dm.off_cR + q];
   __syncthreads();
@@ -158,6 +159,7 @@ __global__ void __launch_bounds__(128) k_force_angular(int N, DevModel dm, const
                                                        const int* __restrict__ own, const float4* __restrict__ rij,
                                                        const float* __restrict__ Sang, const float* __restrict__ Ep,
                                                        float4* __restrict__ dA) {
+  GNEP_PDL_WAIT();
   constexpr int NAF = AMap<C::NQ, 1>::NA;
   constexpr int KP = (C::KA + 3) / 4 * 4;  // basis functions padded to 16-byte rows
   static_assert(NLM % 4 == 0, "16-byte Shat rows");
@@ -262,6 +264,7 @@ __global__ void __launch_bounds__(128) k_force_atoms(int N, DevModel dm, const i
                                                      const int* __restrict__ offA, const int* __restrict__ revA,
                                                      const float4* __restrict__ rijA, const float4* __restrict__ dA,
                                                      float* __restrict__ F, float* __restrict__ Wat) {
+  GNEP_PDL_WAIT();
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = gt / RL, lane = gt % RL;
   const bool ok = i < N;
@@ -336,6 +339,7 @@ __global__ void __launch_bounds__(128) k_force_atoms(int N, DevModel dm, const i
 __global__ void __launch_bounds__(128) k_struct_sum(const int* __restrict__ soff, const float* __restrict__ Eatom,
                                                     const float* __restrict__ Wat, double* __restrict__ Es,
                                                     double* __restrict__ Ws) {
+  GNEP_PDL_WAIT();
   const int s = blockIdx.x;
   const int a0 = soff[s], a1 = soff[s + 1];
   float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -372,6 +376,7 @@ __global__ void __launch_bounds__(128) k_tangent_radial(int N, DevModel dm, cons
                                                         const int* __restrict__ jj, const float4* __restrict__ rij,
                                                         const float4* __restrict__ a, const float* __restrict__ Bs,
                                                         float* __restrict__ FRd, float* __restrict__ Gd) {
+  GNEP_PDL_WAIT();
   __shared__ float cR[C::NCR];
   for (int q = threadIdx.x; q < C::NCR; q += blockDim.x) cR[q] = dm.params[dm.off_cR + q];
   __syncthreads();
@@ -547,6 +552,7 @@ __global__ void __launch_bounds__(32 * kCgWarps, 2)
                 const int* __restrict__ off, const float4* __restrict__ rij, const float4* __restrict__ wij,
                 const float* __restrict__ Sang, const float* __restrict__ Sdd, const float* __restrict__ Gb,
                 const float* __restrict__ Ep, float* __restrict__ cpart) {
+  GNEP_PDL_WAIT();
   using SM = CgSmem<C>;
   constexpr int NA = SM::NA, KT = SM::KT, NQA = C::NQA, KA = C::KA, NS = C::NS, KS = NLM / 8;
   static_assert(NLM % 8 == 0 && NLM % 4 == 0 && NQA <= 16 && NA * NQA <= 128 && CH == 128, "fragment shapes");
@@ -766,6 +772,7 @@ __global__ void __launch_bounds__(32 * kCgRadialWarps) k_cgrad_radial(int N, con
                                                                     const float* __restrict__ FR,
                                                                     const float* __restrict__ FRd,
                                                                     float* __restrict__ cpart) {
+  GNEP_PDL_WAIT();
   constexpr int NCOL = C::NS * C::KR, NW = kCgRadialWarps;
   static_assert(NCOL <= 32, "one lane per radial column");
   __shared__ float red[NW][C::NS][C::NQR][32];
@@ -900,6 +907,7 @@ __global__ void __launch_bounds__(32 * kAngWarps, (TAN || SPLIT) ? 2 : 3)
               const int* __restrict__ jj, const float4* __restrict__ rij, const float4* __restrict__ a,
               const float* __restrict__ Bs, const float* __restrict__ Sin, float* __restrict__ Sout,
               float* __restrict__ Gout, float4* __restrict__ wij) {
+  GNEP_PDL_WAIT();
   using SM = AngSmem<C, TAN>;
   using GEO = AGeo<C, TAN>;
   constexpr int CHT = GEO::CHT, NQA = C::NQA, KA = C::KA, NS = C::NS;
@@ -1163,7 +1171,7 @@ int launch_ang(const gnep_model* m, const gnep_nlist* nl, cudaStream_t st, const
   const int cap = ang_grid_cap<C, TAN, true>();
   const int nb = ntile < cap ? ntile : cap;
   auto kern = k_ang_mma<C, TAN, true>;
-  kern<<<nb, 32 * kAngWarps, sizeof(AngSmem<C, TAN>), st>>>(ntile, nl->atile[0], m->dev(), nl->type, nl->atom_struct,
+  (void)launch_pdl(kern, nb, 32 * kAngWarps, sizeof(AngSmem<C, TAN>), st, ntile, nl->atile[0], m->dev(), nl->type, nl->atom_struct,
                                                             nl->L[1].off, nl->L[1].owner, nl->L[1].j, nl->L[1].rij,
                                                             a, Bs, Sin, Sout, Gout, wij);
   return GNEP_OK;
@@ -1263,7 +1271,7 @@ struct Runner {
     // caller's stream: beside the angular sweeps' persistent blocks a radial
     // kernel found room for one block per SM, and the pair on two streams took
     // longer than the two in turn (0.431 against 0.420 ms for the step).
-    GNEP_RADIAL_LANES(radial_lanes(nl), (k_desc_radial<C, RL><<<blocks_for((int64_t)N * RL, 128), 128, 0, A.st>>>(
+    GNEP_RADIAL_LANES(radial_lanes(nl), ((void)launch_pdl(k_desc_radial<C, RL>, blocks_for((int64_t)N * RL, 128), 128, 0, A.st, 
                                              N, dm, nl->type, nl->L[0].off, nl->L[0].rij, w.FR, w.G)));
     stage("desc_radial");
     if constexpr (C::LMAX > 4) {
@@ -1291,17 +1299,17 @@ struct Runner {
       if constexpr (C::LMAX > 4) {
         if (int rc = hi_force_angular<C>(m, nl, A.st, w.S, w.Ep, w.dA)) return rc;
       } else {
-        k_force_angular<C><<<nl->natile[1], 128, 0, A.st>>>(N, dm, nl->atile[1], nl->type, nl->L[1].off,
+        (void)launch_pdl(k_force_angular<C>, nl->natile[1], 128, 0, A.st, N, dm, nl->atile[1], nl->type, nl->L[1].off,
                                                              nl->L[1].owner, nl->L[1].rij, w.S, w.Ep, w.dA);
       }
       stage("force_angular");
     }
-    GNEP_RADIAL_LANES(radial_lanes(nl), (k_force_atoms<C, RL><<<blocks_for((int64_t)N * RL, 128), 128, 0, A.st>>>(
+    GNEP_RADIAL_LANES(radial_lanes(nl), ((void)launch_pdl(k_force_atoms<C, RL>, blocks_for((int64_t)N * RL, 128), 128, 0, A.st, 
                                              N, dm, nl->type, nl->L[0].off, nl->L[0].j, nl->L[0].rij, w.chat,
                                              nl->L[1].off, nl->L[1].rev, nl->L[1].rij, w.dA, w.F, w.Wat)));
     stage("force_atoms");
     if (!A.loss_follows) {  // otherwise the loss kernel forms these sums
-      k_struct_sum<<<nl->n_struct, 128, 0, A.st>>>(nl->struct_off, w.Eatom, w.Wat, w.Es, w.Ws);
+      (void)launch_pdl(k_struct_sum, nl->n_struct, 128, 0, A.st, nl->struct_off, w.Eatom, w.Wat, w.Es, w.Ws);
       stage("struct_sum");
     }
     GNEP_CHECK_LAUNCH("force sweep");
@@ -1316,7 +1324,7 @@ struct Runner {
     const int N = nl->n_atoms;
     if (N == 0) return GNEP_OK;
     GNEP_RADIAL_LANES(radial_lanes(nl),
-                      (k_tangent_radial<C, RL><<<blocks_for((int64_t)N * RL, 128), 128, 0, A.st>>>(
+                      ((void)launch_pdl(k_tangent_radial<C, RL>, blocks_for((int64_t)N * RL, 128), 128, 0, A.st, 
                           N, dm, nl->type, nl->atom_struct, nl->L[0].off, nl->L[0].j, nl->L[0].rij, w.a, w.Bs, w.FRd,
                           w.Gd)));
     stage("tangent_radial");
@@ -1329,13 +1337,13 @@ struct Runner {
     if (int rc = network_backward(m, nl, A.st)) return rc;
     stage("mlp_bwd");
     const int nb = cgrad_blocks(nl);
-    k_cgrad_radial<C><<<nb, 32 * kCgRadialWarps, 0, A.st>>>(N, nl->type, w.Gb, w.Ep, w.FR, w.FRd, w.cpart);
+    (void)launch_pdl(k_cgrad_radial<C>, nb, 32 * kCgRadialWarps, 0, A.st, N, nl->type, w.Gb, w.Ep, w.FR, w.FRd, w.cpart);
     stage("cgrad_radial");
     if constexpr (C::LMAX > 4) {
       if (int rc = hi_cgrad_angular<C>(m, nl, A.st, nb, w.wij, w.S, w.Sd, w.Gb, w.Ep, w.cpart)) return rc;
     } else {
       auto ang = k_cgrad_ang<C, true>;  // split TF32 in every precision mode
-      ang<<<nb, 32 * kCgWarps, sizeof(CgSmem<C>), A.st>>>(nl->natile[1], nl->atile[1], dm, nl->type, nl->L[1].off,
+      (void)launch_pdl(ang, nb, 32 * kCgWarps, sizeof(CgSmem<C>), A.st, nl->natile[1], nl->atile[1], dm, nl->type, nl->L[1].off,
                                                            nl->L[1].rij, w.wij, w.S, w.Sd, w.Gb, w.Ep, w.cpart);
     }
     stage("cgrad");
@@ -1537,7 +1545,7 @@ int descriptors_static(const StepArgs& A, float* G) {
   const DevModel dm = m->dev();
   // Both kernels overwrite every scratch element they later read, so the
   // array needs no clearing between calls.
-  GNEP_RADIAL_LANES(radial_lanes(nl), (k_desc_radial<C, RL><<<blocks_for(N * RL, 128), 128, 0, A.st>>>(
+  GNEP_RADIAL_LANES(radial_lanes(nl), ((void)launch_pdl(k_desc_radial<C, RL>, blocks_for(N * RL, 128), 128, 0, A.st, 
                                            (int)N, dm, nl->type, nl->L[0].off, nl->L[0].rij, scratch, G)));
   if constexpr (C::LMAX > 4) {
     if ((rc = hi_desc_angular<C>(m, nl, A.st, scratch + fr_padded, G))) return rc;

@@ -162,6 +162,7 @@ template <class C>
 __global__ void __launch_bounds__(32 * kHiWarps) k_desc_hi(int N, DevModel dm, const int* __restrict__ type,
                                                            const int* __restrict__ off, const float4* __restrict__ rij,
                                                            float* __restrict__ Sout, float* __restrict__ G) {
+  GNEP_PDL_WAIT();
   constexpr int NQA = C::NQA, KA = C::KA, NLX = C::NLX, NE = NQA * NLX, NT = (NE + 31) / 32;
   extern __shared__ float4 smraw[];
   __shared__ float cA[C::NCA];
@@ -247,6 +248,7 @@ __global__ void __launch_bounds__(32 * kHiWarps) k_force_hi(int N, DevModel dm, 
                                                             const float4* __restrict__ rij,
                                                             const float* __restrict__ S, const float* __restrict__ Ep,
                                                             float4* __restrict__ dA) {
+  GNEP_PDL_WAIT();
   constexpr int NQA = C::NQA, KA = C::KA, NLX = C::NLX, NE = NQA * NLX;
   extern __shared__ float4 smraw[];
   __shared__ float cA[C::NCA];
@@ -349,6 +351,7 @@ __global__ void __launch_bounds__(32 * kHiWarps) k_tangent_hi(int N, DevModel dm
                                                               const float* __restrict__ Bs,
                                                               const float* __restrict__ Sin, float* __restrict__ Sout,
                                                               float* __restrict__ Gd, float4* __restrict__ wij) {
+  GNEP_PDL_WAIT();
   constexpr int NQA = C::NQA, KA = C::KA, NLX = C::NLX, NE = NQA * NLX, NT = (NE + 31) / 32;
   extern __shared__ float4 smraw[];
   __shared__ float cA[C::NCA];
@@ -465,6 +468,7 @@ __global__ void __launch_bounds__(32 * kHiWarps) k_cgrad_hi(int N, DevModel dm, 
                                                             const float* __restrict__ S, const float* __restrict__ Sd,
                                                             const float* __restrict__ Gb,
                                                             const float* __restrict__ Ep, float* __restrict__ cpart) {
+  GNEP_PDL_WAIT();
   constexpr int NQA = C::NQA, KA = C::KA, NS = C::NS, NLX = C::NLX, NE = NQA * NLX;
   constexpr int NEA = NS * NQA * KA, NTA = (NEA + 31) / 32;  // (J, n, k) entries of one species I
   extern __shared__ float4 smraw[];
@@ -603,7 +607,7 @@ template <class C>
 int hi_desc_angular(const gnep_model* m, const gnep_nlist* nl, cudaStream_t st, float* S, float* G) {
   const int N = nl->n_atoms;
   if (N == 0) return GNEP_OK;
-  k_desc_hi<C><<<hi_grid(N), 32 * kHiWarps, hi_smem<C>(), st>>>(N, m->dev(), nl->type, nl->L[1].off, nl->L[1].rij,
+  (void)launch_pdl(k_desc_hi<C>, hi_grid(N), 32 * kHiWarps, hi_smem<C>(), st, N, m->dev(), nl->type, nl->L[1].off, nl->L[1].rij,
                                                                 S, G);
   GNEP_CHECK_LAUNCH("k_desc_hi");
   return GNEP_OK;
@@ -614,7 +618,7 @@ int hi_force_angular(const gnep_model* m, const gnep_nlist* nl, cudaStream_t st,
                      float4* dA) {
   const int N = nl->n_atoms;
   if (N == 0 || nl->L[1].n == 0) return GNEP_OK;
-  k_force_hi<C><<<hi_grid(N), 32 * kHiWarps, hi_smem<C>(), st>>>(N, m->dev(), nl->type, nl->L[1].off,
+  (void)launch_pdl(k_force_hi<C>, hi_grid(N), 32 * kHiWarps, hi_smem<C>(), st, N, m->dev(), nl->type, nl->L[1].off,
                                                                  nl->L[1].rij, S, Ep, dA);
   GNEP_CHECK_LAUNCH("k_force_hi");
   return GNEP_OK;
@@ -625,7 +629,7 @@ int hi_tangent_angular(const gnep_model* m, const gnep_nlist* nl, cudaStream_t s
                        const float* S, float* Sd, float* Gd, float4* wij) {
   const int N = nl->n_atoms;
   if (N == 0) return GNEP_OK;
-  k_tangent_hi<C><<<hi_grid(N), 32 * kHiWarps, hi_smem<C>(), st>>>(N, m->dev(), nl->type, nl->atom_struct,
+  (void)launch_pdl(k_tangent_hi<C>, hi_grid(N), 32 * kHiWarps, hi_smem<C>(), st, N, m->dev(), nl->type, nl->atom_struct,
                                                                    nl->L[1].off, nl->L[1].j, nl->L[1].rij, a, Bs, S,
                                                                    Sd, Gd, wij);
   GNEP_CHECK_LAUNCH("k_tangent_hi");
@@ -635,7 +639,7 @@ int hi_tangent_angular(const gnep_model* m, const gnep_nlist* nl, cudaStream_t s
 template <class C>
 int hi_cgrad_angular(const gnep_model* m, const gnep_nlist* nl, cudaStream_t st, int nb, const float4* wij,
                      const float* S, const float* Sd, const float* Gb, const float* Ep, float* cpart) {
-  k_cgrad_hi<C><<<nb, 32 * kHiWarps, hi_smem<C>(), st>>>(nl->n_atoms, m->dev(), nl->type, nl->L[1].off,
+  (void)launch_pdl(k_cgrad_hi<C>, nb, 32 * kHiWarps, hi_smem<C>(), st, nl->n_atoms, m->dev(), nl->type, nl->L[1].off,
                                                           nl->L[1].rij, wij, S, Sd, Gb, Ep, cpart);
   GNEP_CHECK_LAUNCH("k_cgrad_hi");
   return GNEP_OK;

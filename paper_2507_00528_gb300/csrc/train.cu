@@ -112,6 +112,7 @@ __device__ void loss_final_block(const LossArgs& a, int nred, const double* __re
 __global__ void __launch_bounds__(256) k_loss_final(LossArgs a, int nred, const double* __restrict__ red,
                                                     const float* __restrict__ params, double* __restrict__ coef,
                                                     int* __restrict__ err) {
+  GNEP_PDL_WAIT();
   loss_final_block(a, nred, red, params, coef, err);
 }
 
@@ -137,6 +138,7 @@ __global__ void __launch_bounds__(128) k_struct_loss(const int* __restrict__ sof
                                                      int* __restrict__ err, int* __restrict__ done,
                                                      float4* __restrict__ aw, float* __restrict__ es,
                                                      float* __restrict__ Bs) {
+  GNEP_PDL_WAIT();
   const int s = blockIdx.x;
   const int a0 = soff[s], a1 = soff[s + 1];
   const bool fused = la.form != GNEP_LOSS_RMSE;
@@ -211,6 +213,7 @@ __global__ void __launch_bounds__(128) k_struct_loss(const int* __restrict__ sof
 __global__ void k_residuals(int N, int S, const float* __restrict__ F, const float* __restrict__ lf,
                             const double* __restrict__ rn, const double* __restrict__ coef, float4* __restrict__ a,
                             float* __restrict__ es, float* __restrict__ Bs) {
+  GNEP_PDL_WAIT();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < N) {
     const float cf = (float)coef[4];
@@ -242,6 +245,7 @@ __global__ void __launch_bounds__(kGfCols* kGfRows) k_grad_final(DevModel dm, in
                                                                  const float* __restrict__ net_part,
                                                                  const float* __restrict__ cpart, double l2coef,
                                                                  double* __restrict__ grad) {
+  GNEP_PDL_WAIT();
   __shared__ double sh[kGfRows][kGfCols];
   const int tx = threadIdx.x % kGfCols, ty = threadIdx.x / kGfCols;
   const int64_t q = (int64_t)blockIdx.x * kGfCols + tx;
@@ -300,6 +304,7 @@ __device__ float lr_eq17(const AdamArgs& a, long long s) {
 __global__ void k_adam(int64_t n, float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
                        const double* __restrict__ g, long long* __restrict__ step, int* __restrict__ err,
                        AdamArgs a) {
+  GNEP_PDL_WAIT();
   if (*err & kErrNonFinite) return;  // the step is skipped (uniform over the grid)
   const long long s = *step;
   const float tf = (float)(s + 1);
@@ -446,15 +451,15 @@ int run_loss_impl(const gnep_model* m, gnep_nlist* nl, const double* le, const f
   a.inv_6S = S > 0 ? 1.0 / (6.0 * S) : 0.0;
   a.inv_np = 1.0 / (double)m->n_params;
   if (S > 0) {  // per-structure residuals; the last block forms the loss terms
-    k_struct_loss<<<S, 128, 0, st>>>(nl->struct_off, w.Eatom, w.Wat, w.F, le, lf, lv, w.Es, w.Ws, w.red,
+    (void)launch_pdl(k_struct_loss, S, 128, 0, st, nl->struct_off, w.Eatom, w.Wat, w.F, le, lf, lv, w.Es, w.Ws, w.red,
                                      w.red + 3 * (size_t)S, a, m->params, w.coef, m->err, m->err + 2, w.a, w.es,
                                      w.Bs);
   } else {
-    k_loss_final<<<1, 256, 0, st>>>(a, 0, w.red, m->params, w.coef, m->err);
+    (void)launch_pdl(k_loss_final, 1, 256, 0, st, a, 0, w.red, m->params, w.coef, m->err);
   }
   stage("struct_loss");
   if (N + S > 0 && (S == 0 || a.form == GNEP_LOSS_RMSE)) {  // the loss kernel wrote them in the MSE form
-    k_residuals<<<blocks_for(N + S, 256), 256, 0, st>>>(N, S, w.F, lf, w.red + 3 * (size_t)S, w.coef, w.a, w.es,
+    (void)launch_pdl(k_residuals, blocks_for(N + S, 256), 256, 0, st, N, S, w.F, lf, w.red + 3 * (size_t)S, w.coef, w.a, w.es,
                                                          w.Bs);
     stage("residuals");
   }
@@ -468,7 +473,7 @@ int run_grad_reduce_impl(const gnep_model* m, gnep_nlist* nl, double lambda_l2, 
   const int nb_net = nl->ws.net_blocks;
   const int nb_cg = nl->n_atoms > 0 ? cgrad_blocks(nl) : 0;
   const double l2coef = 2.0 * lambda_l2 / (double)m->n_params;
-  k_grad_final<<<blocks_for(m->n_params, kGfCols), kGfCols * kGfRows, 0, st>>>(dm, ns, nb_net, nb_cg, nl->ws.net_part,
+  (void)launch_pdl(k_grad_final, blocks_for(m->n_params, kGfCols), kGfCols * kGfRows, 0, st, dm, ns, nb_net, nb_cg, nl->ws.net_part,
                                                                               nl->ws.cpart, l2coef, m->grad);
   stage("grad_final");
   GNEP_CHECK_LAUNCH("gradient reduction");
@@ -485,7 +490,7 @@ int run_adam(gnep_model* m, const double*, double lr, double b1, double b2, doub
   a.scheduled = scheduled ? 1 : 0;
   a.lr_start = (float)lr_start; a.lr_stop = (float)lr_stop; a.nw = nw; a.nt = nt;
   const int nb = blocks_for(m->n_params, 256);
-  k_adam<<<nb < 1 ? 1 : nb, 256, 0, st>>>(m->n_params, m->params, m->adam_m, m->adam_v, m->grad, m->step, m->err, a);
+  (void)launch_pdl(k_adam, nb < 1 ? 1 : nb, 256, 0, st, m->n_params, m->params, m->adam_m, m->adam_v, m->grad, m->step, m->err, a);
   stage("adam");
   GNEP_CHECK_LAUNCH("adam");
   return GNEP_OK;
