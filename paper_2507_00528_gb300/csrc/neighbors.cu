@@ -11,6 +11,7 @@
 // above the FP32 error of d2 for coordinates below 10^4 A) take the FP64 test.
 // The stored r_ij is formed in float-float arithmetic (about 44 bits) and
 // rounded to FP32.
+#include <algorithm>
 #include <cstdio>
 #include <vector>
 
@@ -45,7 +46,7 @@ __global__ void k_atom_struct(const int* __restrict__ off, int S, int N, int* __
 // index on).
 __global__ void k_image_range(const double* __restrict__ cell, int S, double rc, const int* __restrict__ soff,
                               int* __restrict__ kr, float* __restrict__ tw, double* __restrict__ hinv,
-                              float* __restrict__ hsplit, int* __restrict__ nbin) {
+                              float* __restrict__ hsplit, int* __restrict__ nbin, int* __restrict__ big) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= S) return;
   const double* H = cell + 9 * s;
@@ -79,6 +80,7 @@ __global__ void k_image_range(const double* __restrict__ cell, int S, double rc,
     nb[x] = q < 1.0 ? 1 : q > 64.0 ? 64 : (int)q;
   }
   const int cap = max(1, soff[s + 1] - soff[s]);
+  if (cap > kCellMinAtoms) atomicOr(big, 1);  // some structure takes the binned search
   while (nb[0] * nb[1] * nb[2] > cap) {  // at most 189 steps
     const int x = (nb[0] >= nb[1] && nb[0] >= nb[2]) ? 0 : (nb[1] >= nb[2] ? 1 : 2);
     --nb[x];
@@ -98,9 +100,10 @@ __device__ __forceinline__ int atom_bin(float4 f, const int* nb) {
 
 // Atoms per bin (bins of structure s are numbered from its first atom index).
 __global__ void k_bin_count(int N, const int* __restrict__ atom_struct, const int* __restrict__ soff,
-                            const int* __restrict__ nbin, const float4* __restrict__ frac, int* __restrict__ bcount) {
+                            const int* __restrict__ nbin, const float4* __restrict__ frac, const int* __restrict__ big,
+                            int* __restrict__ bcount) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
+  if (i >= N || *big == 0) return;
   const int s = atom_struct[i];
   if (soff[s + 1] - soff[s] <= kCellMinAtoms) return;  // searched without bins
   atomicAdd(&bcount[soff[s] + atom_bin(frac[i], nbin + 3 * s)], 1);
@@ -110,9 +113,10 @@ __global__ void k_bin_count(int N, const int* __restrict__ atom_struct, const in
 // free: it only sets the order in which candidates are tested).
 __global__ void k_bin_fill(int N, const int* __restrict__ atom_struct, const int* __restrict__ soff,
                            const int* __restrict__ nbin, const float4* __restrict__ frac,
-                           const long long* __restrict__ bstart, int* __restrict__ bcursor, int* __restrict__ batom) {
+                           const long long* __restrict__ bstart, const int* __restrict__ big, int* __restrict__ bcursor,
+                           int* __restrict__ batom) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
+  if (i >= N || *big == 0) return;
   const int s = atom_struct[i];
   if (soff[s + 1] - soff[s] <= kCellMinAtoms) return;  // searched without bins
   const int b = soff[s] + atom_bin(frac[i], nbin + 3 * s);
@@ -361,6 +365,116 @@ __global__ void __launch_bounds__(128) k_pairs(
   }
 }
 
+// The slot pass for structures of at most kCellMinAtoms atoms, one warp per
+// central atom i, with the candidates flattened: in each round of 32
+// consecutive j the lanes count the images their j may have within the cut-offs
+// (the fractional bounds of k_pairs), a warp scan lays those (j, image)
+// candidates out in canonical order (j ascending, then image lexicographic),
+// and the lanes then take them 32 at a time, so that every lane tests a
+// candidate in every step instead of walking its own j's images while the
+// others wait.  Each lane finds its candidate's j by a binary search over the
+// scan; accepted entries are placed by ballots in the same canonical order
+// (counts exact; the first cap entries of each list go to the atom's slots).
+__global__ void __launch_bounds__(128) k_pairs_flat(
+    int N, const int* __restrict__ struct_off, const int* __restrict__ atom_struct,
+    const double* __restrict__ pos, const double* __restrict__ cell, const int* __restrict__ krange,
+    const float* __restrict__ tw, const float* __restrict__ hsplit, const float4* __restrict__ frac,
+    const float4* __restrict__ phi, ListParams lp, int* __restrict__ cnt0, int* __restrict__ cnt1, Slots sl) {
+  const int i = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= N) return;  // the whole warp
+  const int s = atom_struct[i];
+  const int a0 = struct_off[s], a1 = struct_off[s + 1];
+  if (a1 - a0 > kCellMinAtoms) return;  // the binned search takes this structure
+  float Hh[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) Hh[q] = hsplit[18 * s + q];
+  const float4 pih = phi[i];
+  const int ka = krange[3 * s], kb = krange[3 * s + 1], kc = krange[3 * s + 2];
+  const float4 fi = frac[i];
+  const float t0 = tw[3 * s] + 1e-3f, t1 = tw[3 * s + 1] + 1e-3f, t2 = tw[3 * s + 2] + 1e-3f;
+  const unsigned lt = (1u << lane) - 1u;
+  int w0 = 0, w1 = 0;  // entries of each list so far (warp-uniform)
+  for (int jb = a0; jb < a1; jb += 32) {
+    const int j = jb + lane;
+    const bool vj = j < a1;
+    const float4 pjh = vj ? phi[j] : pih;
+    const float4 fj = vj ? frac[j] : fi;
+    const float dj[3] = {pjh.x - pih.x, pjh.y - pih.y, pjh.z - pih.z};
+    const float dfa = fj.x - fi.x, dfb = fj.y - fi.y, dfc = fj.z - fi.z;
+    const int alo = max(-ka, (int)ceilf(-t0 - dfa)), ahi = vj ? min(ka, (int)floorf(t0 - dfa)) : alo - 1;
+    const int blo = max(-kb, (int)ceilf(-t1 - dfb)), bhi = min(kb, (int)floorf(t1 - dfb));
+    const int clo = max(-kc, (int)ceilf(-t2 - dfc)), chi = min(kc, (int)floorf(t2 - dfc));
+    const int nbc = max(0, bhi - blo + 1), ncc = max(0, chi - clo + 1);
+    const int ncand = max(0, ahi - alo + 1) * nbc * ncc;  // this lane's candidate images
+    int incl = ncand;  // inclusive scan over the lanes
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += u;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    const int excl = incl - ncand;
+    for (int cb = 0; cb < total; cb += 32) {
+      const int c = cb + lane;
+      const bool valid = c < total;
+      int L = 0;  // the lane whose j owns candidate c: incl[L - 1] <= c < incl[L]
+#pragma unroll
+      for (int st = 16; st >= 1; st >>= 1)
+        if (__shfl_sync(0xffffffffu, incl, L + st - 1) <= c) L += st;
+      const int m = c - __shfl_sync(0xffffffffu, excl, L);
+      const int oj = __shfl_sync(0xffffffffu, j, L);
+      const int oa = __shfl_sync(0xffffffffu, alo, L), ob = __shfl_sync(0xffffffffu, blo, L);
+      const int oc = __shfl_sync(0xffffffffu, clo, L);
+      const int onb = __shfl_sync(0xffffffffu, nbc, L), onc = __shfl_sync(0xffffffffu, ncc, L);
+      const float odj[3] = {__shfl_sync(0xffffffffu, dj[0], L), __shfl_sync(0xffffffffu, dj[1], L),
+                            __shfl_sync(0xffffffffu, dj[2], L)};
+      bool in0 = false, in1 = false;
+      int na = 0, nb = 0, nc = 0;
+      if (valid) {  // image m of the owner's (na, nb, nc) ranges, nc fastest (a few steps: no division)
+        int r = m;
+        const int bc = onb * onc;
+        na = oa;
+        while (r >= bc) {
+          r -= bc;
+          ++na;
+        }
+        nb = ob;
+        while (r >= onc) {
+          r -= onc;
+          ++nb;
+        }
+        nc = oc + r;
+        decide_pair(i, oj, na, nb, nc, odj, Hh, lp, cell, pos, s, in0, in1);
+      }
+      const unsigned b0 = __ballot_sync(0xffffffffu, in0), b1 = __ballot_sync(0xffffffffu, in1);
+      const char4 sv = make_char4((signed char)na, (signed char)nb, (signed char)nc, 0);
+      if (in0) {
+        const int w = w0 + __popc(b0 & lt);
+        if (w < sl.cap[0]) {
+          const size_t q = (size_t)i * sl.cap[0] + w;
+          sl.j[0][q] = oj;
+          sl.sh[0][q] = sv;
+        }
+      }
+      if (in1) {
+        const int w = w1 + __popc(b1 & lt);
+        if (w < sl.cap[1]) {
+          const size_t q = (size_t)i * sl.cap[1] + w;
+          sl.j[1][q] = oj;
+          sl.sh[1][q] = sv;
+        }
+      }
+      w0 += __popc(b0);
+      w1 += __popc(b1);
+    }
+  }
+  if (lane == 0) {
+    cnt0[i] = w0;
+    cnt1[i] = w1;
+  }
+}
+
 // Binned search, one warp per central atom i (the slot pass) of the
 // structures above kCellMinAtoms atoms; the smaller ones take the all-pairs
 // search (k_pairs), which is as fast there: at cell widths below 3 r_c the
@@ -386,16 +500,16 @@ __global__ void __launch_bounds__(32 * kCellWarps) k_pairs_cell(
     const double* __restrict__ pos, const double* __restrict__ cell, const float* __restrict__ tw,
     const float* __restrict__ hsplit, const int* __restrict__ nbin, const long long* __restrict__ bstart,
     const int* __restrict__ batom, const float4* __restrict__ frac, const float4* __restrict__ phi, ListParams lp,
-    int* __restrict__ cnt0, int* __restrict__ cnt1, Slots sl) {
+    const int* __restrict__ big, int* __restrict__ cnt0, int* __restrict__ cnt1, Slots sl) {
+  if (*big == 0) return;  // no structure of this batch takes the binned search
   __shared__ unsigned long long key[kCellWarps][kCellBuf];
   __shared__ int nacc[kCellWarps], nin[kCellWarps][2];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ib = blockIdx.x * kCellWarps;
-  {
-    const int i = ib + w;
-    if (i >= N) return;  // the whole warp; no block-wide barrier follows
+  // warps stride over the atoms (a small grid: most batches have no structure
+  // for this search, and then it ends after one pass of cheap tests)
+  for (int i = blockIdx.x * kCellWarps + w; i < N; i += gridDim.x * kCellWarps) {
     const int s = atom_struct[i], a0 = struct_off[s];
-    if (struct_off[s + 1] - a0 <= kCellMinAtoms) return;  // taken by the all-pairs search
+    if (struct_off[s + 1] - a0 <= kCellMinAtoms) continue;  // taken by the all-pairs search
     if (lane == 0) {
       nacc[w] = 0;
       nin[w][0] = nin[w][1] = 0;
@@ -474,6 +588,7 @@ __global__ void __launch_bounds__(32 * kCellWarps) k_pairs_cell(
         }
       }
     }
+    __syncwarp();  // the keys are read before the next atom's entries replace them
   }
 }
 
@@ -619,19 +734,21 @@ int build_lists(gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
   phi = frac + N;
   plo = frac + 2 * (size_t)N;
   // bins: nbin [3 S], counts and cursors [N + 1] each, atoms by bin [N]
-  GNEP_CUDA(cudaMallocAsync(&bins, sizeof(int) * (3 * (size_t)S + 3 * (size_t)N + 2), st));
+  GNEP_CUDA(cudaMallocAsync(&bins, sizeof(int) * (3 * (size_t)S + 3 * (size_t)N + 3), st));
   int* nbin = bins;
   int* bcount = bins + 3 * (size_t)S;
   int* bcursor = bcount + (N + 1);
-  int* batom = bcursor + (N + 1);
+  int* big = bcursor + (N + 1);  // set when some structure takes the binned search
+  int* batom = big + 1;
   for (void* p : {(void*)cnt, (void*)kr, (void*)tw, (void*)hsplit, (void*)hinv, (void*)frac, (void*)offs, (void*)bins})
     tmp.push_back(p);
   GNEP_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * 2 * (size_t)(N + 1), st));
-  GNEP_CUDA(cudaMemsetAsync(bcount, 0, sizeof(int) * 2 * (size_t)(N + 1), st));  // and bcursor
+  GNEP_CUDA(cudaMemsetAsync(bcount, 0, sizeof(int) * (2 * (size_t)(N + 1) + 1), st));  // and bcursor, big
 
   k_atom_struct<<<blocks_for(N, 256), 256, 0, st>>>(nl->struct_off, S, N, nl->atom_struct);
   const double rcmax = nl->rcr > nl->rca ? nl->rcr : nl->rca;
-  k_image_range<<<blocks_for(S, 128), 128, 0, st>>>(nl->cell, S, rcmax, nl->struct_off, kr, tw, hinv, hsplit, nbin);
+  k_image_range<<<blocks_for(S, 128), 128, 0, st>>>(nl->cell, S, rcmax, nl->struct_off, kr, tw, hinv, hsplit, nbin,
+                                                     big);
   k_atom_prep<<<blocks_for(N, 256), 256, 0, st>>>(N, nl->atom_struct, nl->pos, nl->type, hinv, frac, phi, plo,
                                                    m->err);
   GNEP_CHECK_LAUNCH("k_image_range");
@@ -639,13 +756,13 @@ int build_lists(gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
   long long* bstart = nullptr;
   GNEP_CUDA(cudaMallocAsync(&bstart, sizeof(long long) * (size_t)(N + 1), st));
   tmp.push_back(bstart);
-  k_bin_count<<<blocks_for(N, 256), 256, 0, st>>>(N, nl->atom_struct, nl->struct_off, nbin, frac, bcount);
+  k_bin_count<<<blocks_for(N, 256), 256, 0, st>>>(N, nl->atom_struct, nl->struct_off, nbin, frac, big, bcount);
   if (int rc = scan_rec(nullptr, bcount, N + 1, bstart, tmp, st)) {
     cleanup();
     return rc;
   }
-  k_bin_fill<<<blocks_for(N, 256), 256, 0, st>>>(N, nl->atom_struct, nl->struct_off, nbin, frac, bstart, bcursor,
-                                                  batom);
+  k_bin_fill<<<blocks_for(N, 256), 256, 0, st>>>(N, nl->atom_struct, nl->struct_off, nbin, frac, bstart, big,
+                                                  bcursor, batom);
   GNEP_CHECK_LAUNCH("k_bin_fill");
 
   ListParams lp;
@@ -674,12 +791,12 @@ int build_lists(gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
     sl.sh[0] = reinterpret_cast<char4*>(sl.j[1] + n1);
     sl.sh[1] = sl.sh[0] + n0;
   }
-  k_pairs<2><<<blocks_for((int64_t)N * 32, 128), 128, 0, st>>>(
-      N, nl->struct_off, nl->atom_struct, nl->pos, nl->cell, kr, tw, hsplit, frac, phi, plo, lp, cnt0, cnt1,
-      nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, sl);
-  k_pairs_cell<<<(unsigned)((N + kCellWarps - 1) / kCellWarps), 32 * kCellWarps, 0, st>>>(
-      N, nl->struct_off, nl->atom_struct, nl->pos, nl->cell, tw, hsplit, nbin, bstart, batom, frac, phi, lp, cnt0,
-      cnt1, sl);
+  k_pairs_flat<<<blocks_for((int64_t)N * 32, 128), 128, 0, st>>>(N, nl->struct_off, nl->atom_struct, nl->pos,
+                                                                 nl->cell, kr, tw, hsplit, frac, phi, lp, cnt0, cnt1,
+                                                                 sl);
+  k_pairs_cell<<<(unsigned)std::min<int64_t>((N + kCellWarps - 1) / kCellWarps, 1216), 32 * kCellWarps, 0, st>>>(
+      N, nl->struct_off, nl->atom_struct, nl->pos, nl->cell, tw, hsplit, nbin, bstart, batom, frac, phi, lp, big,
+      cnt0, cnt1, sl);
   GNEP_CHECK_LAUNCH("pair search");
   int* maxc = nullptr;
   GNEP_CUDA(cudaMallocAsync(&maxc, sizeof(int) * 2, st));
