@@ -227,46 +227,45 @@ __device__ __forceinline__ void decide_pair(int i, int j, int na, int nb, int nc
   }
 }
 
-// One warp per central atom i.  Lane l tests the neighbours j = a0 + l,
-// a0 + l + 32, ...: in each round of 32 consecutive j every lane walks the
-// images of its j in lexicographic order, and the warp places the accepted
-// entries by an exclusive scan of the per-lane counts, so each list comes out
-// in canonical order (j ascending, then image).  kMode 1 writes the CSR lists
-// at the scanned offsets (every structure); kMode 2 counts and writes each
-// atom's first cap entries into its slots (the slots are then compacted), for
-// the structures of at most kCellMinAtoms atoms.  Both modes take the
-// same decisions (FP32 away from the cut-offs, FP64 within the band).  A lane
-// keeps up to kBuf accepted images of its j in a packed register; a round in
-// which some lane accepts more walks the images again to place them.
+// Per-atom slots of the slot passes: the first cap[L] entries of atom i's
+// list L go to j[L][i cap[L] + k], sh[L][...]; k_compact moves them into the
+// CSR lists once the counts are scanned.
 struct Slots {
   int cap[2];
   int* j[2];
   char4* sh[2];
 };
 
+// One warp per central atom i.  Lane l tests the neighbours j = a0 + l,
+// a0 + l + 32, ...: in each round of 32 consecutive j every lane walks the
+// images of its j in lexicographic order, and the warp places the accepted
+// entries by an exclusive scan of the per-lane counts, so each list comes out
+// in canonical order (j ascending, then image), written into the CSR lists at
+// the offsets that the slot pass counted: the writing pass of a batch in which
+// some atom has more entries than its slots hold.  It takes the slot passes'
+// decisions (FP32 away from the cut-offs, FP64 within the band).  A lane
+// keeps up to kBuf accepted images of its j in a packed register; a round in
+// which some lane accepts more walks the images again to place them.
 constexpr int kBuf = 4;
 
-template <int kMode>
 __global__ void __launch_bounds__(128) k_pairs(
     int N, const int* __restrict__ struct_off, const int* __restrict__ atom_struct,
     const double* __restrict__ pos, const double* __restrict__ cell, const int* __restrict__ krange,
     const float* __restrict__ tw, const float* __restrict__ hsplit, const float4* __restrict__ frac,
-    const float4* __restrict__ phi, const float4* __restrict__ plo, ListParams lp, int* __restrict__ cnt0,
-    int* __restrict__ cnt1, const long long* __restrict__ off0, const long long* __restrict__ off1,
-    int* __restrict__ j0, int* __restrict__ own0, float4* __restrict__ r0, char4* __restrict__ sh0,
-    int* __restrict__ j1, int* __restrict__ own1, float4* __restrict__ r1, char4* __restrict__ sh1, Slots sl) {
-  constexpr bool kFill = kMode == 1;
+    const float4* __restrict__ phi, const float4* __restrict__ plo, ListParams lp,
+    const long long* __restrict__ off0, const long long* __restrict__ off1, int* __restrict__ j0,
+    int* __restrict__ own0, float4* __restrict__ r0, char4* __restrict__ sh0, int* __restrict__ j1,
+    int* __restrict__ own1, float4* __restrict__ r1, char4* __restrict__ sh1) {
   const int i = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (i >= N) return;  // the whole warp
   const int s = atom_struct[i];
   const int a0 = struct_off[s], a1 = struct_off[s + 1];
-  if (!kFill && a1 - a0 > kCellMinAtoms) return;  // the binned search takes this structure's slot pass
   float Hh[9], Hl[9];
 #pragma unroll
   for (int q = 0; q < 9; ++q) {
     Hh[q] = hsplit[18 * s + q];
-    Hl[q] = kFill ? hsplit[18 * s + 9 + q] : 0.f;
+    Hl[q] = hsplit[18 * s + 9 + q];
   }
   const float4 pih = phi[i], pil = plo[i];
   const int ka = krange[3 * s], kb = krange[3 * s + 1], kc = krange[3 * s + 2];
@@ -293,26 +292,13 @@ __global__ void __launch_bounds__(128) k_pairs(
     // places one accepted entry at the next positions of its lists
     auto put = [&](int na, int nb, int nc, bool in0, bool in1, int& w0, int& w1) {
       const char4 sv = make_char4((signed char)na, (signed char)nb, (signed char)nc, 0);
-      if (kFill) {
-        const float4 pjl = plo[j];
-        const float rx = pair_component(pjh.x, pjl.x, pih.x, pil.x, na, nb, nc, Hh[0], Hl[0], Hh[3], Hl[3], Hh[6], Hl[6]);
-        const float ry = pair_component(pjh.y, pjl.y, pih.y, pil.y, na, nb, nc, Hh[1], Hl[1], Hh[4], Hl[4], Hh[7], Hl[7]);
-        const float rz = pair_component(pjh.z, pjl.z, pih.z, pil.z, na, nb, nc, Hh[2], Hl[2], Hh[5], Hl[5], Hh[8], Hl[8]);
-        const float4 rv = make_float4(rx, ry, rz, pjh.w);
-        if (in0) { const long long d = off0[i] + w0; j0[d] = j; own0[d] = i; r0[d] = rv; sh0[d] = sv; }
-        if (in1) { const long long d = off1[i] + w1; j1[d] = j; own1[d] = i; r1[d] = rv; sh1[d] = sv; }
-      } else {  // r_ij is formed by the compaction
-        if (in0 && w0 < sl.cap[0]) {
-          const size_t q = (size_t)i * sl.cap[0] + w0;
-          sl.j[0][q] = j;
-          sl.sh[0][q] = sv;
-        }
-        if (in1 && w1 < sl.cap[1]) {
-          const size_t q = (size_t)i * sl.cap[1] + w1;
-          sl.j[1][q] = j;
-          sl.sh[1][q] = sv;
-        }
-      }
+      const float4 pjl = plo[j];
+      const float rx = pair_component(pjh.x, pjl.x, pih.x, pil.x, na, nb, nc, Hh[0], Hl[0], Hh[3], Hl[3], Hh[6], Hl[6]);
+      const float ry = pair_component(pjh.y, pjl.y, pih.y, pil.y, na, nb, nc, Hh[1], Hl[1], Hh[4], Hl[4], Hh[7], Hl[7]);
+      const float rz = pair_component(pjh.z, pjl.z, pih.z, pil.z, na, nb, nc, Hh[2], Hl[2], Hh[5], Hl[5], Hh[8], Hl[8]);
+      const float4 rv = make_float4(rx, ry, rz, pjh.w);
+      if (in0) { const long long d = off0[i] + w0; j0[d] = j; own0[d] = i; r0[d] = rv; sh0[d] = sv; }
+      if (in1) { const long long d = off1[i] + w1; j1[d] = j; own1[d] = i; r1[d] = rv; sh1[d] = sv; }
       w0 += in0;
       w1 += in1;
     };
@@ -358,10 +344,6 @@ __global__ void __launch_bounds__(128) k_pairs(
     }
     base0 += tot0;
     base1 += tot1;
-  }
-  if (!kFill && lane == 0) {
-    cnt0[i] = base0;
-    cnt1[i] = base1;
   }
 }
 
@@ -868,10 +850,10 @@ int build_lists(gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
     }
     GNEP_CHECK_LAUNCH("k_compact");
   } else {
-    k_pairs<1><<<blocks_for((int64_t)N * 32, 128), 128, 0, st>>>(
-        N, nl->struct_off, nl->atom_struct, nl->pos, nl->cell, kr, tw, hsplit, frac, phi, plo, lp, nullptr, nullptr,
-        off0, off1, nl->L[0].j, nl->L[0].owner, nl->L[0].rij, nl->L[0].shift, nl->L[1].j, nl->L[1].owner,
-        nl->L[1].rij, nl->L[1].shift, sl);
+    k_pairs<<<blocks_for((int64_t)N * 32, 128), 128, 0, st>>>(
+        N, nl->struct_off, nl->atom_struct, nl->pos, nl->cell, kr, tw, hsplit, frac, phi, plo, lp, off0, off1,
+        nl->L[0].j, nl->L[0].owner, nl->L[0].rij, nl->L[0].shift, nl->L[1].j, nl->L[1].owner, nl->L[1].rij,
+        nl->L[1].shift);
     GNEP_CHECK_LAUNCH("k_pairs<fill>");
   }
   {  // reverse entries of the angular list (the radial force terms need none)
