@@ -314,6 +314,7 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_bwd_row(Tiles T, int ntiles, DevM
   float cdb0 = 0.f, cdw1 = 0.f;  // column sums of hidden unit tid (tid < H2)
   float cb1 = 0.f;
   int cur_e = -1;
+  unsigned visited = 0;  // species whose partial this block writes
 
   auto reset = [&]() {
 #pragma unroll
@@ -371,6 +372,7 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_bwd_row(Tiles T, int ntiles, DevM
       reset();
       load_weights<D, GP>(dm, e, W, b0, w1);
       cur_e = e;
+      visited |= 1u << e;
     }
     if (tid < TA) {
       const int r = tid < na ? T.perm[a0 + tid] : -1;
@@ -468,6 +470,12 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_bwd_row(Tiles T, int ntiles, DevM
   }
   __syncthreads();
   if (cur_e >= 0) flush(cur_e);
+  // the partials of the species this block did not visit are zero (the
+  // gradient assembly reads every block's row of every species)
+  for (int e = 0; e < T.ns; ++e)
+    if (!(visited & (1u << e)))
+      for (int q = threadIdx.x; q < part_stride; q += blockDim.x)
+        part[((size_t)blockIdx.x * T.ns + e) * part_stride + q] = 0.f;
 }
 
 // ------------------------------------------------------------- tensor-core tiles (FP32 accuracy)
@@ -706,6 +714,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd_mma(Tiles T, int ntiles, Dev
   Acc<true> dw[KD];  // dW0[16 mw + (g, g + 8)][8 nd + 2t, + 1], partial over atom group kw
   float cb1 = 0.f;
   int cur_e = -1;
+  unsigned visited = 0;  // species whose partial this block writes
 
   auto reset = [&]() {
 #pragma unroll
@@ -755,6 +764,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd_mma(Tiles T, int ntiles, Dev
       reset();
       load_weights_split<D, HP, NTB>(dm, e, Wh, Wl, b0, w1);
       cur_e = e;
+      visited |= 1u << e;
     }
     if (tid < TA) {
       const int r = tid < na ? T.perm[a0 + tid] : -1;
@@ -880,6 +890,12 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd_mma(Tiles T, int ntiles, Dev
   }
   __syncthreads();
   if (cur_e >= 0) flush(cur_e);
+  // the partials of the species this block did not visit are zero (the
+  // gradient assembly reads every block's row of every species)
+  for (int e = 0; e < T.ns; ++e)
+    if (!(visited & (1u << e)))
+      for (int q = threadIdx.x; q < part_stride; q += blockDim.x)
+        part[((size_t)blockIdx.x * T.ns + e) * part_stride + q] = 0.f;
 }
 
 // ------------------------------------------------------------- launchers
@@ -984,8 +1000,10 @@ int launch_backward(K kern, int threads, size_t smem, int tile_atoms, const gnep
   if (cap > kNetBlocks) cap = kNetBlocks;  // net_part holds kNetBlocks partials
   const int grid = net_blocks(nl, ntiles < cap ? (ntiles > 0 ? ntiles : 1) : cap);
   w.net_blocks = grid;
-  GNEP_CUDA(cudaMemsetAsync(w.net_part, 0, sizeof(float) * (size_t)grid * ns * m->net_size, st));
-  if (ntiles == 0) return GNEP_OK;
+  if (ntiles == 0) {  // no block runs: the single partial is zero
+    GNEP_CUDA(cudaMemsetAsync(w.net_part, 0, sizeof(float) * (size_t)grid * ns * m->net_size, st));
+    return GNEP_OK;
+  }
   (void)launch_pdl(kern, grid, threads, smem, st, T, ntiles, m->dev(), nl->atom_struct, w.es, w.G, w.Gd, w.Gb, w.net_part,
                                     m->net_size);
   GNEP_CHECK_LAUNCH(what);
