@@ -276,9 +276,9 @@ def run_reference(args):
     batch = synth.make_config(2)
     # The oracle needs ~2 s for even the smallest structure of this workload, so
     # the arm keeps to a wall-clock budget: one structure-sample per step, at
-    # most one warm-up step, and as many of the requested steps as fit.
+    # most three warm-up steps, and as many of the requested steps as fit.
     budget_s, per_step = 150.0, 2.5
-    warm = min(args.warmup, 1)
+    warm = min(args.warmup, 3)
     timed = max(1, min(args.steps, int(budget_s / per_step) - warm))
     n_atoms, n_s, times = oracle_sample_step(batch, per_step, warm + timed)
     times = times[warm:]
