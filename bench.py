@@ -569,7 +569,7 @@ def run_e2e(student, nl, batch, y, args, gnep, torch):
     s_train, s_load = torch.cuda.Stream(), torch.cuda.Stream()
     st, sl = C.c_void_p(s_train.cuda_stream), C.c_void_p(s_load.cuda_stream)
     done = [torch.cuda.Event(), torch.cuda.Event()]  # step that last read list 0 / 1 has finished
-    steps = max(3, min(args.steps, 20))
+    steps = max(3, min(args.steps, 100))
 
     def load(k):  # structures of step k to the device, lists rebuilt into nls[k % 2]
         s_load.wait_event(done[k % 2])
