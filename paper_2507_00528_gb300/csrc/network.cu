@@ -548,7 +548,12 @@ __device__ __forceinline__ void frag_w_rows(FragB& b, const uint32_t* Wh, const 
 template <int D, int HP, int NS, int NQR, int KR, int TA>
 size_t mlp_fwd_mma_smem() {
   constexpr int SW = MmaW<D>::SW;
-  return sizeof(float) * (2 * (size_t)HP * SW + TA * (size_t)SW + 2 * HP + SW + NS * NQR * KR);
+  return sizeof(float) * (2 * (size_t)HP * SW + 2 * TA * (size_t)SW + 2 * HP + SW + NS * NQR * KR);
+}
+
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
 }
 
 // Forward on tensor cores: z = W0 (s.G) + b0, x = tanh z, E = w1.x + b1,
@@ -563,31 +568,60 @@ __global__ void __launch_bounds__(2 * TA, 1) k_mlp_fwd_mma(Tiles T, int ntiles, 
   extern __shared__ float4 sm4[];
   uint32_t* Wh = reinterpret_cast<uint32_t*>(sm4);  // [HP][SW]
   uint32_t* Wl = Wh + HP * SW;                       // [HP][SW]
-  float* R = reinterpret_cast<float*>(Wl + HP * SW);  // [TA][SW] s.G, then the scaled E'
-  float* b0 = R + TA * SW;                           // [HP]
+  float* Rbuf = reinterpret_cast<float*>(Wl + HP * SW);  // [2][TA][SW] s.G, then the scaled E'
+  float* b0 = Rbuf + 2 * TA * SW;                    // [HP]
   float* w1 = b0 + HP;                               // [HP]
   float* sc = w1 + HP;                               // [SW]
   float* cR = sc + SW;                               // [NS][NQR][KR] of the tile's species
-  __shared__ int rows[TA];
+  __shared__ int rowsb[2][TA];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, t = lane & 3, pg = (g >> 1) | ((g & 1) << 2);
   const int H = dm.H;
+  // Staging: the rows of a tile are copied into one of two buffers with
+  // cp.async (thread 2a + h copies the elements h, h + 2, ... of atom a's row)
+  // while the previous tile writes its outputs, then scaled in place by the
+  // thread that copied them.  Columns beyond D stay zero (the buffers start
+  // zeroed and the E' rows written there carry s = 0 beyond D); rows beyond a
+  // tile's atoms keep earlier finite values and only feed discarded rows.
+  const int sa = tid >> 1, sh = tid & 1;
+  for (int q = tid; q < 2 * TA * SW; q += NTB) Rbuf[q] = 0.f;
   for (int v = tid; v < SW; v += NTB) sc[v] = v < D ? dm.scale[v] : 0.f;
-  int cur_e = -1;
-  float b1 = 0.f;
-  for (int tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
+  __syncthreads();
+  auto issue = [&](int r, int buf) {  // row r of G into this thread's atom slot of buffer buf
+    rowsb[buf][sa] = r;  // both threads of the atom write the same value
+    if (r >= 0) {
+      float* dst = Rbuf + (size_t)buf * TA * SW + sa * SW;
+      const float* src = G + (size_t)r * D;
+      for (int v = sh; v < D; v += 2) cp_async4(dst + v, src + v);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  auto tile_row = [&](int tt) {  // row index of this thread's atom in tile tt (-1 beyond it)
+    if (tt >= ntiles) return -1;
     int e, a0, na;
     tile_of<TA>(T, tt, e, a0, na);
-    __syncthreads();  // the previous tile's readers of R, rows and the weights are done
+    return sa < na ? T.perm[a0 + sa] : -1;
+  };
+  int cur_e = -1;
+  float b1 = 0.f;
+  int buf = 0;
+  if (blockIdx.x < ntiles) issue(tile_row(blockIdx.x), 0);
+  for (int tt = blockIdx.x; tt < ntiles; tt += gridDim.x, buf ^= 1) {
+    int e, a0, na;
+    tile_of<TA>(T, tt, e, a0, na);
+    const int rnext = tile_row(tt + gridDim.x);  // loaded now, used after the products
+    __syncthreads();  // the previous tile's readers of the weights are done
     if (e != cur_e) {
       load_weights_split<D, HP, NTB>(dm, e, Wh, Wl, b0, w1);
       for (int q = tid; q < NS * NQR * KR; q += NTB) cR[q] = dm.params[dm.off_cR + e * NS * NQR * KR + q];
       b1 = dm.params[(size_t)e * dm.net_size + D * H + 2 * H];
       cur_e = e;
     }
-    if (tid < TA) rows[tid] = tid < na ? T.perm[a0 + tid] : -1;
-    __syncthreads();
-    stage_rows<D, 1, TA, SW, NTB>(G, nullptr, rows, sc, R, nullptr);
+    float* R = Rbuf + (size_t)buf * TA * SW;
+    const int* rows = rowsb[buf];
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    if (sa < na)
+      for (int v = sh; v < D; v += 2) R[sa * SW + v] *= sc[v];
     __syncthreads();
     float* Rw = R + 16 * warp * SW;  // this warp's 16 rows
     Acc<true> ep[KD];
@@ -648,6 +682,7 @@ __global__ void __launch_bounds__(2 * TA, 1) k_mlp_fwd_mma(Tiles T, int ntiles, 
       if (16 * warp + g + 8 < na) Eatom[rows[16 * warp + g + 8]] = Eg8 + b1;
     }
     __syncthreads();
+    issue(rnext, buf ^ 1);  // the next tile's rows arrive while this one writes its outputs
     // coalesced row writes: E' and chat
     for (int q = tid; q < na * D; q += NTB) {
       const int r = q / D, v = q % D;
@@ -661,6 +696,7 @@ __global__ void __launch_bounds__(2 * TA, 1) k_mlp_fwd_mma(Tiles T, int ntiles, 
       chat[(size_t)rows[r] * NJK + jk] = s;
     }
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");  // no copy outlives the block
 }
 
 template <int D, int HP>
