@@ -265,6 +265,36 @@ def test_autograd_function_and_gpu_finite_differences():
         assert abs(fd - gh[k]) <= 2e-2 * (abs(gh[k]) + 1e-2 * np.abs(gh).max()), (k, fd, gh[k])
 
 
+@pytest.mark.parametrize("loss_form", [0, 1])
+def test_directional_derivatives_match_finite_differences(loss_form):
+    """The GPU gradient against central differences of the GPU loss along
+    random directions of all parameters at once (the network weights and both
+    coefficient sets move together), at the benchmark model shape, in the MSE
+    and RMSE forms (Eqs. 9-12).  A step of at most 3e-3 per parameter moves the
+    loss far more than its FP32 rounding, and the cubic term of the central
+    difference stays far below the 2e-3 relative tolerance."""
+    b = synth.make_config(1, n_struct=3)
+    c = Case("nmax8_basis12_h50_4b", b, lambdas=(1.0, 1.0, 0.1, 0.0), loss_form=loss_form)
+    y = c.gpu_labels()
+    _, g = c.m.loss_grad(c.nl, y)
+    gh = g.double().cpu().numpy()
+    rng = np.random.default_rng(7)
+    for _ in range(3):
+        v = rng.standard_normal(len(gh))
+        d = 3e-3 * v / np.abs(v).max()
+        pp = torch.from_numpy((c.P.astype(np.float64) + d).astype(np.float32))
+        pm = torch.from_numpy((c.P.astype(np.float64) - d).astype(np.float32))
+        dp = pp.double().numpy() - pm.double().numpy()  # the step actually taken, after FP32 rounding
+        c.m.set_params(pp)
+        lp = c.m.loss(c.nl, y)[0].item()
+        c.m.set_params(pm)
+        lm = c.m.loss(c.nl, y)[0].item()
+        fd = lp - lm
+        an = float(gh @ dp)
+        assert abs(fd - an) <= 2e-3 * abs(an), (fd, an)
+    c.m.set_params(torch.from_numpy(c.P))
+
+
 def test_skewed_cells_many_images_and_largest_structure():
     """A strongly sheared triclinic cell, a two-atom cell far below both
     cut-offs (dozens of images of each atom in both lists), and one structure
