@@ -110,9 +110,15 @@ def algo_bytes(nqr=9, kr=13, nqa=9, ka=13, ns=2, H=50, fb=True, N=1, PR=1, PA=1,
 # ----------------------------------------------------------------- helpers
 
 def csrc_sha() -> str:
+    """Hash of the kernel sources without their comments and with white space
+    collapsed, so that a profile stays matched to the code it measured across
+    edits of comments only."""
     h = hashlib.sha256()
     for p in sorted(glob.glob(os.path.join(ROOT, "paper_2507_00528_gb300", "csrc", "*"))):
-        h.update(open(p, "rb").read())
+        txt = open(p, encoding="utf-8", errors="replace").read()
+        txt = re.sub(r"/\*.*?\*/", " ", txt, flags=re.S)
+        txt = re.sub(r"//[^\n]*", " ", txt)
+        h.update(" ".join(txt.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -1,11 +1,15 @@
-// Per-element one-hidden-layer network (D1.1-D1.10) in FP32 on the CUDA
-// cores, and its tangent/reverse pass (D1.18-D1.21 through the tangent/adjoint
-// route), over species-homogeneous tiles of the species-grouped atom order:
-// 128 atoms per tile, or 32 for batches too small to give every SM a tile.  Persistent blocks keep one species' weights in shared memory
-// and walk the tiles.  Every sum runs in a fixed order (no atomics), so results
-// are bit-reproducible.
+// Per-element one-hidden-layer network (D1.1-D1.10) with FP32 accuracy, and
+// its tangent/reverse pass (D1.18-D1.21 through the tangent/adjoint route),
+// over species-homogeneous tiles of the species-grouped atom order, in two
+// forms: 128-atom tiles on warp-level tensor cores in split TF32 (the second
+// half of this file), and CUDA-core kernels (below) on 32-atom tiles for
+// batches too small to give every other SM a tile, and for the backward pass
+// above 64 hidden units on 128-atom tiles.  Persistent blocks keep one
+// species' weights in shared memory and walk the tiles.  Every sum runs in a
+// fixed order (no atomics), so results are bit-reproducible.
 //
-// Thread map: 256 threads, G per atom (G = 2 for 128-atom tiles, 8 for 32).
+// CUDA-core thread map: 256 threads, G per atom (G = 2 for 128-atom tiles, 8
+// for 32).
 // With AW = 32 / G atoms per warp, lane l of warp w takes atom AW w + (l mod AW)
 // and part l / AW of the hidden units (the units padded to a multiple of G), so
 // that each thread's descriptor row (and, backward, its tangent row and the
