@@ -349,6 +349,38 @@ def test_binned_search_large_structures_bit_exact():
     assert rel_l2(F, fo) < F_TOL and rel_l2(W, wo) < F_TOL
 
 
+@pytest.mark.parametrize("dense", [False, True])
+def test_binned_search_sheared_and_elongated_cells_bit_exact(dense):
+    """The binned pair search on cells that stress its bounds: a 1200-atom
+    cell under a strong shear (the extended bins follow the fractional bounds
+    along each cell direction, not Cartesian boxes) and a 1100-atom cell
+    elongated along c (many bins along c, two along a and b, the bin count
+    reduced to the atom count).  At the workload density the lists come from
+    the slots; at 3.5 times that density (about 170 radial neighbours) the
+    slots overflow and the binned search's counts place the entries of the
+    writing pass.  Both lists equal the oracle's (Eq. 2) entry for entry."""
+    rng = np.random.default_rng(43)
+    n1, n2 = 1200, 1100
+    shear = np.array([[22.0, 0.0, 0.0], [9.5, 21.0, 0.0], [-7.0, 6.5, 22.5]])
+    rho = 0.115 if dense else 0.033
+    H1 = shear * (n1 / rho / abs(np.linalg.det(shear))) ** (1.0 / 3.0)
+    H2 = np.diag([10.4, 10.1, n2 / rho / (10.4 * 10.1)])
+    f1, f2 = rng.random((n1, 3)), rng.random((n2, 3))
+    pos = np.concatenate([f1 @ H1, f2 @ H2])
+    types = rng.integers(0, 2, n1 + n2).astype(np.int32)
+    b = synth.Batch(np.array([0, n1, n1 + n2], dtype=np.int32), pos, types, np.stack([H1, H2]))
+    c = Case("nmax4_basis8_h30", b.subset([0]), labels=False)
+    nl = c.m.neighbors(gnep.DeviceBatch.from_host(b))
+    for which, rc in ((0, 7.0), (1, 4.0)):
+        off, j, sh = nl.export(which)
+        ooff, oj, osh = O.neighbors(b, rc)
+        if which == 0:
+            assert (np.diff(ooff).max() > 96) == dense
+        np.testing.assert_array_equal(off, ooff)
+        np.testing.assert_array_equal(j, oj)
+        np.testing.assert_array_equal(sh, osh)
+
+
 def test_dense_image_lattice_overflows_the_slots():
     """A one-atom cubic cell of 2.3 A holds about 118 images within the radial
     cut-off, more than the 96 per-atom slots of the one-pass search: the lists
