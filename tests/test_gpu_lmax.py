@@ -57,9 +57,14 @@ def test_forward_energy_force_virial(shape):
     ("nmax4_basis8_lmax8_4b_h30", (1.0, 1.0, 0.1, 0.0), 0),
     ("nmax4_basis8_lmax8_4b_h30", (0.5, 2.0, 0.3, 0.05), 1),
 ])
-def test_loss_and_gradient(shape, lambdas, form):
+@pytest.mark.parametrize("net_tile_atoms,radial_lanes", [(0, 0), (128, 4)])
+def test_loss_and_gradient(shape, lambdas, form, net_tile_atoms, radial_lanes):
+    """With the small-batch defaults (32-atom CUDA-core network tiles, 16
+    radial lanes) and with the large-batch kernels forced (128-atom
+    tensor-core network tiles, 4 radial lanes)."""
     b = synth.make_batch([20, 13, 17], [2, 1, 0], np.random.default_rng(7))
     c = Case(shape, b, lambdas=lambdas, loss_form=form)
+    c.nl.set_tuning(dict(net_tile_atoms=net_tile_atoms, radial_lanes=radial_lanes))
     terms, g = c.m.loss_grad(c.nl, c.gpu_labels())
     c.m.sync_status()
     ref_terms, ref_g = O.loss_grad(c.cfg, c.P64, c.s64, b, c.y)
