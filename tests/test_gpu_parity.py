@@ -95,6 +95,26 @@ def test_loss_and_gradient(shape, which_batch, lambdas, form):
     check_grad(g.cpu().numpy(), ref_g)
 
 
+@pytest.mark.parametrize("shape,which_batch,form", [
+    ("nmax4_basis8_h30", "cfg1_2", 1),
+    ("nmax8_basis12_h50_4b", "tiny_mixed", 0),
+    ("nmax8_basis12_h100", "tiny_mixed", 1),
+])
+def test_loss_and_gradient_large_batch_kernels(shape, which_batch, form):
+    """The kernels that large batches take, forced on small ones: 128-atom
+    network tiles (tensor-core forward; tensor-core backward up to 64 hidden
+    units, the two-thread CUDA-core backward at 100) and four radial lanes."""
+    b = {"cfg1_2": lambda: synth.make_config(1, n_struct=2),
+         "tiny_mixed": lambda: synth.make_batch([20, 13], [2, 1], np.random.default_rng(7))}[which_batch]()
+    c = Case(shape, b, lambdas=(1.0, 1.0, 0.1, 0.0), loss_form=form)
+    c.nl.set_tuning(dict(net_tile_atoms=128, radial_lanes=4))
+    terms, g = c.m.loss_grad(c.nl, c.gpu_labels())
+    c.m.sync_status()
+    ref_terms, ref_g = O.loss_grad(c.cfg, c.P64, c.s64, b, c.y)
+    np.testing.assert_allclose(terms.cpu().numpy(), ref_terms, rtol=2e-5, atol=1e-12)
+    check_grad(g.cpu().numpy(), ref_g)
+
+
 def test_adam_step_matches_oracle():
     b = synth.make_config(1, n_struct=2)
     c = Case("nmax4_basis8_h30", b)
