@@ -445,7 +445,10 @@ def run_gnep(args):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "other_modes": other_modes,
-        "gpu_launches": args.steps * sum(1 for k in stage_ms if not k.startswith("memset")),
+        # kernels of the captured step (its gradient reduction and Adam are one
+        # kernel), or of the eager data-parallel step
+        "gpu_launches": args.steps * (graph.kernel_count() if world == 1 else
+                                      sum(1 for k in stage_ms if not k.startswith("memset"))),
         "clocks": clocks,
         "loss": {"after_warmup": loss0.tolist(), "end": loss_end.tolist()},
         "source_sha": csrc_sha(),
@@ -883,7 +886,7 @@ def report_small_batch(args):
 
         default = nl.tuning()
         variants = {}
-        for key, vals in (("radial_lanes", (4, 8, 16)), ("net_tile_atoms", (32, 128))):
+        for key, vals in (("radial_lanes", (4, 8, 16)), ("net_tile_atoms", (32, 128)), ("radial_beside", (1, 2))):
             for v in vals:
                 nl.set_tuning({key: v})
                 variants[f"{key}={v}"] = round(graph_ms(), 4)
@@ -895,7 +898,7 @@ def report_small_batch(args):
                 prof[k] = prof.get(k, 0.0) + v / 5
         student.sync_status()
         out[str(B)] = {"atoms": int(sub.n_atoms), "ms_per_step": round(step_ms, 4),
-                       "default_shapes": {k: default[k] for k in ("radial_lanes", "net_tile_atoms")},
+                       "default_shapes": {k: default[k] for k in ("radial_lanes", "net_tile_atoms", "radial_beside")},
                        "forced_shapes_ms_per_step": variants,
                        "stage_ms": {k: round(v, 4) for k, v in prof.items()},
                        "stage_sum_ms": round(sum(prof.values()), 4)}

@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define GNEP_ABI_VERSION 4
+#define GNEP_ABI_VERSION 5
 
 typedef enum {
   GNEP_OK = 0,
@@ -232,12 +232,13 @@ int gnep_loss_grad(gnep_model *m, const gnep_nlist *nl, const gnep_labels *y,
  * descriptor and tangent sweeps' tiles and of the angular force and
  * c-gradient sweeps' tiles, the number of persistent blocks of the c-gradient
  * sweep and of the network kernels, the lanes per atom of the radial sweeps,
- * and the atoms per tile of the FP32 network.  gnep_autotune times the
+ * the atoms per tile of the FP32 network, and whether the radial sweeps run
+ * beside the angular ones.  gnep_autotune times the
  * loss + gradient evaluation of this batch (median of `reps` runs, no
  * parameter update) over candidate values of each in turn and keeps the
  * fastest in the neighbour list.  It synchronizes `stream` and must not run
  * during stream capture; graphs captured earlier on this list are invalidated
- * (gnep_graph_launch then returns INVALID_ARG).  values [8] =
+ * (gnep_graph_launch then returns INVALID_ARG).  values [9] =
  *   [0] atoms per descriptor tile   [1] pairs per descriptor tile
  *   [2] atoms per force tile        [3] pairs per force tile
  *   [4] c-gradient blocks (at most 608)
@@ -246,6 +247,11 @@ int gnep_loss_grad(gnep_model *m, const gnep_nlist *nl, const gnep_labels *y,
  *       blocks per SM are filled, more for smaller batches)
  *   [7] atoms per FP32 network tile: 32 or 128 (default: 128 while the batch
  *       has a tile per two SMs, else 32; the tensor-core modes always take 128).
+ *   [8] radial sweeps: 1 = in turn with the angular sweeps on `stream`,
+ *       2 = beside them on a second stream owned by the list, forked from and
+ *       joined back to `stream` by events within each call (default: 2 while
+ *       the angular descriptor sweep has fewer than eight tiles per SM, else
+ *       1).  The results are the same bit for bit.
  * gnep_tuning_get gives the effective values; gnep_tuning_set takes the same
  * layout (0 = default) and rebuilds the tiles.  Results agree with the
  * untuned ones to FP32 summation order.
@@ -296,8 +302,11 @@ double gnep_lr_schedule(double lr_start, double lr_stop, int64_t s,
                         int64_t n_warmup, int64_t n_total);
 
 /* One training step captured once as a CUDA graph and replayed: loss_grad then
- * adam_step_scheduled.  loss_out is a device pointer [4] written each replay.
- * The nlist, labels (device pointers) and loss_out must outlive the graph. */
+ * adam_step_scheduled, with the same results bit for bit (the gradient stays
+ * in the model for gnep_get_grad; the gradient reduction, the copy of the loss
+ * terms and the update run as one kernel).  loss_out is a device pointer [4]
+ * (may be NULL) written each replay.  The nlist, labels (device pointers) and
+ * loss_out must outlive the graph. */
 typedef struct gnep_graph gnep_graph;
 int gnep_graph_create(gnep_model *m, const gnep_nlist *nl, const gnep_labels *y,
                       double *loss_out, double lr_start, double lr_stop,
@@ -306,6 +315,9 @@ int gnep_graph_create(gnep_model *m, const gnep_nlist *nl, const gnep_labels *y,
                       void *stream, gnep_graph **out);
 int gnep_graph_launch(gnep_graph *g, void *stream);
 int gnep_graph_destroy(gnep_graph *g);
+/* Kernels one replay launches (the graph's kernel nodes), to *n.
+ * Errors: INVALID_ARG (NULL), CUDA. */
+int gnep_graph_kernel_count(const gnep_graph *g, int32_t *n);
 
 /* ------------------------------------------------------------ profiling */
 

@@ -28,7 +28,8 @@ EXPORTS = [
     "gnep_compute_descriptor_scale", "gnep_build_neighbors", "gnep_rebuild_neighbors",
     "gnep_nlist_destroy", "gnep_nlist_info", "gnep_nlist_export", "gnep_descriptors", "gnep_forward",
     "gnep_loss_grad", "gnep_adam_step", "gnep_adam_step_scheduled", "gnep_get_step",
-    "gnep_lr_schedule", "gnep_graph_create", "gnep_graph_launch", "gnep_graph_destroy", "gnep_save",
+    "gnep_lr_schedule", "gnep_graph_create", "gnep_graph_launch", "gnep_graph_destroy",
+    "gnep_graph_kernel_count", "gnep_save",
     "gnep_load", "gnep_sync_status", "gnep_last_error", "gnep_abi_version", "gnep_profile_step",
     "gnep_profile_stage_name", "gnep_descriptors_noalloc", "gnep_loss", "gnep_get_grad", "gnep_set_grad",
     "gnep_autotune", "gnep_tuning_get", "gnep_tuning_set", "gnep_md_verlet", "gnep_shard_loss_weights",
@@ -92,6 +93,7 @@ _SIGS = {
                           C.POINTER(_vp)],
     "gnep_graph_launch": [_vp, _vp],
     "gnep_graph_destroy": [_vp],
+    "gnep_graph_kernel_count": [_vp, _vp],
     "gnep_save": [_vp, C.c_char_p],
     "gnep_load": [_vp, C.c_char_p],
     "gnep_sync_status": [_vp, _vp],

@@ -391,6 +391,11 @@ static int finish_build(gnep_model* m, gnep_nlist* nl, cudaStream_t st, bool wai
   }
   if ((rc = alloc_workspace(m, nl))) return rc;
   if (!nl->ready_ev) GNEP_CUDA(cudaEventCreateWithFlags(&nl->ready_ev, cudaEventDisableTiming));
+  if (!nl->side) {  // created here, outside any stream capture
+    GNEP_CUDA(cudaStreamCreateWithFlags(&nl->side, cudaStreamNonBlocking));
+    GNEP_CUDA(cudaEventCreateWithFlags(&nl->fork_ev, cudaEventDisableTiming));
+    GNEP_CUDA(cudaEventCreateWithFlags(&nl->join_ev, cudaEventDisableTiming));
+  }
   GNEP_CUDA(cudaEventRecord(nl->ready_ev, st));
   if (!wait) return GNEP_OK;
   int herr = 0;
@@ -415,6 +420,12 @@ int gnep_nlist_destroy(gnep_nlist* nl) {
   if (nl->tile_ev) {
     cudaEventSynchronize(nl->tile_ev);
     cudaEventDestroy(nl->tile_ev);
+  }
+  if (nl->side) {
+    cudaStreamSynchronize(nl->side);
+    cudaStreamDestroy(nl->side);
+    cudaEventDestroy(nl->fork_ev);
+    cudaEventDestroy(nl->join_ev);
   }
   if (nl->tile_host) cudaFreeHost(nl->tile_host);
   if (nl->host_aoff) cudaFreeHost(nl->host_aoff);
@@ -687,12 +698,14 @@ int gnep_graph_create(gnep_model* m, const gnep_nlist* nl_, const gnep_labels* y
   cudaStream_t st = (cudaStream_t)stream;
   if (nl->ready_ev) GNEP_CUDA(cudaEventSynchronize(nl->ready_ev));  // a capture cannot wait on it
   GNEP_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-  rc = loss_grad_core(m, nl, y, st);
-  if (!rc && loss_out) {
-    if (cudaMemcpyAsync(loss_out, nl->ws.coef, 4 * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
-      rc = set_error(GNEP_ERR_CUDA, "capture memcpy");
-  }
-  if (!rc) rc = run_adam(m, nullptr, 0.0, beta1, beta2, eps, weight_decay, true, lr_start, lr_stop, n_warmup, n_total, st);
+  // the step of gnep_loss_grad + gnep_adam_step_scheduled, with the gradient
+  // reduction, the copy of the loss terms and the update in one kernel
+  rc = forward_loss(m, nl, y, st);
+  StepArgs A{m, nl, st};
+  if (!rc) rc = run_backward(A);
+  if (!rc)
+    rc = run_grad_adam(m, nl, y->lambda_l2, loss_out, beta1, beta2, eps, weight_decay, lr_start, lr_stop, n_warmup,
+                       n_total, st);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(st, &g);
   if (rc) {
@@ -723,11 +736,27 @@ int gnep_graph_launch(gnep_graph* g, void* stream) {
   return GNEP_OK;
 }
 
+int gnep_graph_kernel_count(const gnep_graph* g, int32_t* n) {
+  if (!g || !n) return set_error(GNEP_ERR_INVALID_ARG, "NULL argument");
+  size_t nn = 0;
+  GNEP_CUDA(cudaGraphGetNodes(g->g, nullptr, &nn));
+  std::vector<cudaGraphNode_t> nodes(nn);
+  if (nn) GNEP_CUDA(cudaGraphGetNodes(g->g, nodes.data(), &nn));
+  int32_t k = 0;
+  for (size_t i = 0; i < nn; ++i) {
+    cudaGraphNodeType t;
+    GNEP_CUDA(cudaGraphNodeGetType(nodes[i], &t));
+    if (t == cudaGraphNodeTypeKernel) ++k;
+  }
+  *n = k;
+  return GNEP_OK;
+}
+
 // ---------------------------------------------------------------- autotuner
 
 namespace {
 
-constexpr int kTuneKnobs = 8;  // na[0], ch[0], na[1], ch[1], cg_blocks, net_blocks, radial_lanes, net_tile
+constexpr int kTuneKnobs = 9;  // na[0], ch[0], na[1], ch[1], cg_blocks, net_blocks, radial_lanes, net_tile, beside
 
 int* knob(gnep_nlist* nl, int k) {
   switch (k) {
@@ -738,7 +767,8 @@ int* knob(gnep_nlist* nl, int k) {
     case 4: return &nl->tune.cg_blocks;
     case 5: return &nl->tune.net_blocks;
     case 6: return &nl->tune.radial_lanes;
-    default: return &nl->tune.net_tile;
+    case 7: return &nl->tune.net_tile;
+    default: return &nl->tune.beside;
   }
 }
 
@@ -755,6 +785,7 @@ void effective_tuning(const gnep_model* m, const gnep_nlist* nl, int32_t* v) {
   v[6] = radial_lanes(nl);
   // the tensor-core network modes always take 128-atom tiles
   v[7] = (m->shape.lmax > 4 || m->precision == GNEP_PREC_FP32) ? net_tile_atoms(nl, m->shape.ns) : 128;
+  v[8] = radial_beside(nl) ? 2 : 1;
 }
 
 // Median over `reps` of one loss + gradient evaluation (no update), in ms.
@@ -802,6 +833,8 @@ int gnep_tuning_set(gnep_model* m, gnep_nlist* nl, const int32_t* values, void* 
     return set_error(GNEP_ERR_INVALID_ARG, "radial lanes per atom must be 4, 8 or 16 (or 0)");
   if (values[7] != 0 && values[7] != 32 && values[7] != 128)
     return set_error(GNEP_ERR_INVALID_ARG, "atoms per network tile must be 32 or 128 (or 0)");
+  if (values[8] > 2)
+    return set_error(GNEP_ERR_INVALID_ARG, "radial sweep placement must be 1 (in turn) or 2 (beside) (or 0)");
   for (int k = 0; k < kTuneKnobs; ++k) *knob(nl, k) = values[k];
   ++nl->gen;
   if (nl->n_atoms == 0) return GNEP_OK;
@@ -823,7 +856,8 @@ int gnep_autotune(gnep_model* m, gnep_nlist* nl, const gnep_labels* y, int reps,
       {na0, na0 / 2, na0 / 4},  {64, 128, 256, 384, 512},
       {na1, na1 / 2, na1 / 4},  {32, 48, 64, 96, 128, 192},
       {152, 304, 456, 608},     {0, 152, 304},
-      {4, 8, 16},               {32, 128}};
+      {4, 8, 16},               {32, 128},
+      {1, 2}};
   for (int k = 0; k < kTuneKnobs; ++k) *knob(nl, k) = cur[k];
   ++nl->gen;
   if ((rc = build_angular_tiles(m, nl, st))) return rc;

@@ -93,10 +93,11 @@ struct gnep_nlist {
   int64_t atile_cap[2] = {0, 0};  // allocated tile-bound slots
   // Launch shapes chosen by gnep_autotune (0 = built-in default): atoms and
   // pairs per tile of each tile set, persistent blocks of the c-gradient sweep
-  // and of the network kernels, lanes per atom of the radial sweeps (4, 8, 16)
-  // and atoms per FP32 network tile (32, 128).
+  // and of the network kernels, lanes per atom of the radial sweeps (4, 8, 16),
+  // atoms per FP32 network tile (32, 128) and where the radial sweeps run
+  // (1: in turn with the angular ones, 2: beside them on the second stream).
   struct Tuning {
-    int na[2] = {0, 0}, ch[2] = {0, 0}, cg_blocks = 0, net_blocks = 0, radial_lanes = 0, net_tile = 0;
+    int na[2] = {0, 0}, ch[2] = {0, 0}, cg_blocks = 0, net_blocks = 0, radial_lanes = 0, net_tile = 0, beside = 0;
   } tune;
   uint64_t gen = 0;  // bumped whenever lists or tiles change (captured graphs check it)
   std::vector<int> host_types;  // species of the last build (host copy)
@@ -107,6 +108,10 @@ struct gnep_nlist {
   int64_t tile_host_cap = 0;
   cudaEvent_t tile_ev = nullptr;     // the last upload from tile_host
   cudaEvent_t ready_ev = nullptr;    // the end of the last build's device work (consumers wait on it)
+  // A second stream for the radial sweeps of small batches, with the events
+  // that fork it from the caller's stream and join it back.
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   gnep::Workspace ws;
   void* ws_mem = nullptr;      // one allocation carved into the workspace
   int64_t ws_pairs[2] = {-1, -1};  // pair counts the workspace was sized for
@@ -158,9 +163,11 @@ int cuda_error(cudaError_t e, const char* what);
 // visible.  Outside a dependent launch the wait returns at once.
 #define GNEP_PDL_WAIT() asm volatile("griddepcontrol.wait;" ::: "memory")
 
+// launch_on launches as a dependent of the stream's previous kernel when `pdl`
+// is set, else as an ordinary launch.
 template <typename... KArgs, typename... Args>
-inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
-                              Args&&... args) {
+inline cudaError_t launch_on(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                             Args&&... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = block;
@@ -170,8 +177,13 @@ inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = pdl ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args&&... args) {
+  return launch_on(true, kern, grid, block, smem, st, std::forward<Args>(args)...);
 }
 
 #define GNEP_CHECK_LAUNCH(what)                                \
@@ -203,6 +215,7 @@ int md_kick(const gnep_nlist* nl, double* vel, const double* inv_mass, const flo
 int cgrad_blocks(const gnep_nlist* nl);
 int sm_count();                                   // SMs of this GPU
 int radial_lanes(const gnep_nlist* nl);           // lanes per atom of the radial sweeps
+bool radial_beside(const gnep_nlist* nl);         // radial sweeps on the list's second stream
 int net_tile_atoms(const gnep_nlist* nl, int ns); // atoms per FP32 network tile
 // Persistent blocks of a network kernel: `fit` (resident capacity, capped at the
 // tile count) or the tuned count, whichever is smaller.
@@ -222,6 +235,10 @@ int grad_to_float(const gnep_model* m, float* dst, cudaStream_t st);
 int run_adam(gnep_model* m, const double* lr_dev, double lr, double b1, double b2, double eps,
              double wd, bool scheduled, double lr_start, double lr_stop, int64_t nw, int64_t nt,
              cudaStream_t st);
+// The gradient, the loss terms to loss_out (device, may be NULL) and the
+// scheduled Adam update of a training step in one launch.
+int run_grad_adam(gnep_model* m, gnep_nlist* nl, double lambda_l2, double* loss_out, double b1, double b2,
+                  double eps, double wd, double lr_start, double lr_stop, int64_t nw, int64_t nt, cudaStream_t st);
 int run_scale(gnep_model* m, gnep_nlist* nl, cudaStream_t st);
 int run_species_perm(gnep_nlist* nl, cudaStream_t st);
 

@@ -1188,6 +1188,26 @@ int setup_ang() {
 // ------------------------------------------------------------- launchers
 
 // Launch CALL (which names RL) with RL = the radial sweeps' lanes per atom.
+// The radial sweep of a phase beside its angular sweep: the radial kernel goes
+// to the list's second stream, which first waits for the caller's stream (fork)
+// and which the caller's stream waits for before the phase's consumer (join).
+// The two kernels write disjoint columns of G, Gdot and the c-gradient
+// partials.  Per-stage timing keeps them in turn.  *rs is the radial stream.
+static int radial_fork(gnep_nlist* nl, cudaStream_t st, cudaStream_t* rs) {
+  *rs = st;
+  if (g_prof.on || !nl->side || !radial_beside(nl)) return GNEP_OK;
+  GNEP_CUDA(cudaEventRecord(nl->fork_ev, st));
+  GNEP_CUDA(cudaStreamWaitEvent(nl->side, nl->fork_ev, 0));
+  *rs = nl->side;
+  return GNEP_OK;
+}
+static int radial_join(gnep_nlist* nl, cudaStream_t st, cudaStream_t rs) {
+  if (rs == st) return GNEP_OK;
+  GNEP_CUDA(cudaEventRecord(nl->join_ev, rs));
+  GNEP_CUDA(cudaStreamWaitEvent(st, nl->join_ev, 0));
+  return GNEP_OK;
+}
+
 #define GNEP_RADIAL_LANES(RLV, CALL)  \
   switch (RLV) {                      \
     case 16: {                        \
@@ -1267,11 +1287,10 @@ struct Runner {
     const DevModel dm = m->dev();
     const int N = nl->n_atoms;
     if (N == 0) return GNEP_OK;
-    // The radial and angular sweeps of a phase run one after the other on the
-    // caller's stream: beside the angular sweeps' persistent blocks a radial
-    // kernel found room for one block per SM, and the pair on two streams took
-    // longer than the two in turn (0.431 against 0.420 ms for the step).
-    GNEP_RADIAL_LANES(radial_lanes(nl), ((void)launch_pdl(k_desc_radial<C, RL>, blocks_for((int64_t)N * RL, 128), 128, 0, A.st, 
+    cudaStream_t rs;
+    if (int rc = radial_fork(nl, A.st, &rs)) return rc;
+    GNEP_RADIAL_LANES(radial_lanes(nl), ((void)launch_on(rs == A.st, k_desc_radial<C, RL>,
+                                             blocks_for((int64_t)N * RL, 128), 128, 0, rs,
                                              N, dm, nl->type, nl->L[0].off, nl->L[0].rij, w.FR, w.G)));
     stage("desc_radial");
     if constexpr (C::LMAX > 4) {
@@ -1280,6 +1299,7 @@ struct Runner {
       if (int rc = launch_ang<C, false>(m, nl, A.st, nullptr, nullptr, nullptr, w.S, w.G, nullptr)) return rc;
     }
     stage("desc_angular");
+    if (int rc = radial_join(nl, A.st, rs)) return rc;
     GNEP_CHECK_LAUNCH("descriptor sweep");
     if (with_mlp) {
       if (int rc = network_forward(m, nl, A.st)) return rc;
@@ -1323,10 +1343,12 @@ struct Runner {
     const DevModel dm = m->dev();
     const int N = nl->n_atoms;
     if (N == 0) return GNEP_OK;
+    cudaStream_t rs;
+    if (int rc = radial_fork(nl, A.st, &rs)) return rc;
     GNEP_RADIAL_LANES(radial_lanes(nl),
-                      ((void)launch_pdl(k_tangent_radial<C, RL>, blocks_for((int64_t)N * RL, 128), 128, 0, A.st, 
-                          N, dm, nl->type, nl->atom_struct, nl->L[0].off, nl->L[0].j, nl->L[0].rij, w.a, w.Bs, w.FRd,
-                          w.Gd)));
+                      ((void)launch_on(rs == A.st, k_tangent_radial<C, RL>, blocks_for((int64_t)N * RL, 128), 128, 0,
+                          rs, N, dm, nl->type, nl->atom_struct, nl->L[0].off, nl->L[0].j, nl->L[0].rij, w.a, w.Bs,
+                          w.FRd, w.Gd)));
     stage("tangent_radial");
     if constexpr (C::LMAX > 4) {
       if (int rc = hi_tangent_angular<C>(m, nl, A.st, w.a, w.Bs, w.S, w.Sd, w.Gd, w.wij)) return rc;
@@ -1334,10 +1356,13 @@ struct Runner {
       if (int rc = launch_ang<C, true>(m, nl, A.st, w.a, w.Bs, w.S, w.Sd, w.Gd, w.wij)) return rc;
     }
     stage("tangent_angular");
+    if (int rc = radial_join(nl, A.st, rs)) return rc;
     if (int rc = network_backward(m, nl, A.st)) return rc;
     stage("mlp_bwd");
     const int nb = cgrad_blocks(nl);
-    (void)launch_pdl(k_cgrad_radial<C>, nb, 32 * kCgRadialWarps, 0, A.st, N, nl->type, w.Gb, w.Ep, w.FR, w.FRd, w.cpart);
+    if (int rc = radial_fork(nl, A.st, &rs)) return rc;
+    (void)launch_on(rs == A.st, k_cgrad_radial<C>, nb, 32 * kCgRadialWarps, 0, rs, N, nl->type, w.Gb, w.Ep, w.FR,
+                    w.FRd, w.cpart);
     stage("cgrad_radial");
     if constexpr (C::LMAX > 4) {
       if (int rc = hi_cgrad_angular<C>(m, nl, A.st, nb, w.wij, w.S, w.Sd, w.Gb, w.Ep, w.cpart)) return rc;
@@ -1347,6 +1372,7 @@ struct Runner {
                                                            nl->L[1].rij, w.wij, w.S, w.Sd, w.Gb, w.Ep, w.cpart);
     }
     stage("cgrad");
+    if (int rc = radial_join(nl, A.st, rs)) return rc;
     GNEP_CHECK_LAUNCH("backward sweeps");
     return GNEP_OK;
   }
@@ -1462,6 +1488,18 @@ int radial_lanes(const gnep_nlist* nl) {
   const int64_t full = 4LL * 128 * sm_count();  // threads of four blocks per SM
   const int64_t N = nl->n_atoms;
   return 4 * N >= full ? 4 : 8 * N >= full ? 8 : 16;
+}
+
+// The radial sweeps run beside the angular ones when tuned so, and by default
+// while the angular descriptor sweep has fewer than eight tiles per SM.  The
+// sweeps of both kinds are chains of dependent loads and products with idle
+// issue slots: on a small batch neither fills the GPU and the two at once hide
+// the shorter one; up to a few tiles per SM the radial warps still fill issue
+// slots the angular warps leave (on the 256-structure workload, about 1,900
+// tiles, the two placements time the same).
+bool radial_beside(const gnep_nlist* nl) {
+  if (nl->tune.beside > 0) return nl->tune.beside == 2;
+  return nl->natile[0] < 8 * sm_count();
 }
 
 // Persistent blocks of the c-gradient sweep: one per tile up to the default

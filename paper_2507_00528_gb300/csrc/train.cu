@@ -241,11 +241,12 @@ __global__ void k_residuals(int N, int S, const float* __restrict__ F, const flo
 // fixed order.
 constexpr int kGfCols = 32, kGfRows = 32;
 
-__global__ void __launch_bounds__(kGfCols* kGfRows) k_grad_final(DevModel dm, int ns, int nb_net, int nb_cg,
-                                                                 const float* __restrict__ net_part,
-                                                                 const float* __restrict__ cpart, double l2coef,
-                                                                 double* __restrict__ grad) {
-  GNEP_PDL_WAIT();
+// The block's part of the gradient: returns grad[q] (also written) on the
+// threads of row 0 for their column q < n_params, and 0 elsewhere.  `params`
+// is read for the L2 term only.
+__device__ __forceinline__ double grad_block(const DevModel& dm, int ns, int nb_net, int nb_cg,
+                                             const float* __restrict__ net_part, const float* __restrict__ cpart,
+                                             double l2coef, const float* params, double* __restrict__ grad) {
   __shared__ double sh[kGfRows][kGfCols];
   const int tx = threadIdx.x % kGfCols, ty = threadIdx.x / kGfCols;
   const int64_t q = (int64_t)blockIdx.x * kGfCols + tx;
@@ -269,12 +270,22 @@ __global__ void __launch_bounds__(kGfCols* kGfRows) k_grad_final(DevModel dm, in
   }
   sh[ty][tx] = (double)leaf;
   __syncthreads();
+  double t = 0.0;
   if (ty == 0 && q < dm.n_params) {
-    double t = 0.0;
 #pragma unroll
     for (int k = 0; k < kGfRows; ++k) t += sh[k][tx];
-    grad[q] = t + l2coef * (double)dm.params[q];
+    t += l2coef * (double)params[q];
+    grad[q] = t;
   }
+  return t;
+}
+
+__global__ void __launch_bounds__(kGfCols* kGfRows) k_grad_final(DevModel dm, int ns, int nb_net, int nb_cg,
+                                                                 const float* __restrict__ net_part,
+                                                                 const float* __restrict__ cpart, double l2coef,
+                                                                 double* __restrict__ grad) {
+  GNEP_PDL_WAIT();
+  (void)grad_block(dm, ns, nb_net, nb_cg, net_part, cpart, l2coef, dm.params, grad);
 }
 
 // ---------------------------------------------------------- Adam, Eq. 17
@@ -300,26 +311,31 @@ __device__ float lr_eq17(const AdamArgs& a, long long s) {
 // Adam (Kingma-Ba bias correction, optional decoupled weight decay) with the
 // step size of Eq. 17 when scheduled, in FP32 (moments are FP32).  The bias
 // corrections 1 - beta^t are formed as -expm1(t log beta), accurate also when
-// beta^t is close to 1.
-__global__ void k_adam(int64_t n, float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
-                       const double* __restrict__ g, long long* __restrict__ step, int* __restrict__ err,
-                       AdamArgs a) {
-  GNEP_PDL_WAIT();
-  if (*err & kErrNonFinite) return;  // the step is skipped (uniform over the grid)
-  const long long s = *step;
+// beta^t is close to 1.  adam_rates gives the step size and the two inverse
+// corrections of update s + 1; adam_entry updates one parameter.
+struct AdamRates {
+  float lr, ic1, ic2;
+};
+__device__ __forceinline__ AdamRates adam_rates(const AdamArgs& a, long long s) {
   const float tf = (float)(s + 1);
-  const float lr = a.scheduled ? lr_eq17(a, s) : a.lr;
-  const float ic1 = -1.f / expm1f(tf * a.lb1), ic2 = -1.f / expm1f(tf * a.lb2);
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
-    const float gq = (float)g[q];
-    const float mq = fmaf(a.b1, m[q], (1.f - a.b1) * gq);
-    const float vq = fmaf(a.b2, v[q], (1.f - a.b2) * gq * gq);
-    m[q] = mq;
-    v[q] = vq;
-    const float upd = (mq * ic1) / (sqrtf(vq * ic2) + a.eps) + a.wd * p[q];
-    p[q] = p[q] - lr * upd;
-  }
-  // the last block to finish advances the update count (every block has read it)
+  AdamRates r;
+  r.lr = a.scheduled ? lr_eq17(a, s) : a.lr;
+  r.ic1 = -1.f / expm1f(tf * a.lb1);
+  r.ic2 = -1.f / expm1f(tf * a.lb2);
+  return r;
+}
+__device__ __forceinline__ void adam_entry(int64_t q, float gq, float* p, float* __restrict__ m,
+                                           float* __restrict__ v, const AdamArgs& a, const AdamRates& r) {
+  const float mq = fmaf(a.b1, m[q], (1.f - a.b1) * gq);
+  const float vq = fmaf(a.b2, v[q], (1.f - a.b2) * gq * gq);
+  m[q] = mq;
+  v[q] = vq;
+  const float upd = (mq * r.ic1) / (sqrtf(vq * r.ic2) + a.eps) + a.wd * p[q];
+  p[q] = p[q] - r.lr * upd;
+}
+// The last block to finish advances the update count (every block read it
+// before its own arrival).
+__device__ __forceinline__ void adam_count(long long* step, int* err) {
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
@@ -328,6 +344,39 @@ __global__ void k_adam(int64_t n, float* __restrict__ p, float* __restrict__ m, 
       err[1] = 0;
     }
   }
+}
+
+__global__ void k_adam(int64_t n, float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
+                       const double* __restrict__ g, long long* __restrict__ step, int* __restrict__ err,
+                       AdamArgs a) {
+  GNEP_PDL_WAIT();
+  if (*err & kErrNonFinite) return;  // the step is skipped (uniform over the grid)
+  const AdamRates r = adam_rates(a, *step);
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+    adam_entry(q, (float)g[q], p, m, v, a, r);
+  adam_count(step, err);
+}
+
+// The end of a captured training step in one kernel: the gradient of
+// k_grad_final, the loss terms copied to loss_out (may be NULL), and then,
+// unless the loss was not finite, the Adam update of k_adam on the same
+// entries with the same arithmetic.
+__global__ void __launch_bounds__(kGfCols* kGfRows) k_grad_adam(DevModel dm, int ns, int nb_net, int nb_cg,
+                                                                const float* __restrict__ net_part,
+                                                                const float* __restrict__ cpart, double l2coef,
+                                                                double* __restrict__ grad, float* p, float* __restrict__ m,
+                                                                float* __restrict__ v, long long* __restrict__ step,
+                                                                int* __restrict__ err, AdamArgs a,
+                                                                const double* __restrict__ coef,
+                                                                double* __restrict__ loss_out) {
+  GNEP_PDL_WAIT();
+  const double gq = grad_block(dm, ns, nb_net, nb_cg, net_part, cpart, l2coef, p, grad);
+  if (loss_out && blockIdx.x == 0 && threadIdx.x < 4) loss_out[threadIdx.x] = coef[threadIdx.x];
+  if (*err & kErrNonFinite) return;  // the update is skipped (uniform over the grid)
+  const AdamRates r = adam_rates(a, *step);
+  const int64_t q = (int64_t)blockIdx.x * kGfCols + threadIdx.x;
+  if (threadIdx.x < kGfCols && q < dm.n_params) adam_entry(q, (float)gq, p, m, v, a, r);
+  adam_count(step, err);
 }
 
 // ---------------------------------------------------------- scale, perm
@@ -480,19 +529,40 @@ int run_grad_reduce_impl(const gnep_model* m, gnep_nlist* nl, double lambda_l2, 
   return GNEP_OK;
 }
 
-int run_adam(gnep_model* m, const double*, double lr, double b1, double b2, double eps, double wd, bool scheduled,
-             double lr_start, double lr_stop, int64_t nw, int64_t nt, cudaStream_t st) {
+static int adam_args(double lr, double b1, double b2, double eps, double wd, bool scheduled, double lr_start,
+                     double lr_stop, int64_t nw, int64_t nt, AdamArgs* a) {
   if (!(b1 > 0.0 && b1 < 1.0 && b2 > 0.0 && b2 < 1.0 && eps > 0.0))
     return set_error(GNEP_ERR_INVALID_ARG, "Adam needs 0 < beta1, beta2 < 1 and eps > 0");
+  a->lr = (float)lr; a->b1 = (float)b1; a->b2 = (float)b2; a->eps = (float)eps; a->wd = (float)wd;
+  a->lb1 = (float)std::log(b1); a->lb2 = (float)std::log(b2);
+  a->scheduled = scheduled ? 1 : 0;
+  a->lr_start = (float)lr_start; a->lr_stop = (float)lr_stop; a->nw = nw; a->nt = nt;
+  return GNEP_OK;
+}
+
+int run_adam(gnep_model* m, const double*, double lr, double b1, double b2, double eps, double wd, bool scheduled,
+             double lr_start, double lr_stop, int64_t nw, int64_t nt, cudaStream_t st) {
   AdamArgs a;
-  a.lr = (float)lr; a.b1 = (float)b1; a.b2 = (float)b2; a.eps = (float)eps; a.wd = (float)wd;
-  a.lb1 = (float)std::log(b1); a.lb2 = (float)std::log(b2);
-  a.scheduled = scheduled ? 1 : 0;
-  a.lr_start = (float)lr_start; a.lr_stop = (float)lr_stop; a.nw = nw; a.nt = nt;
+  if (int rc = adam_args(lr, b1, b2, eps, wd, scheduled, lr_start, lr_stop, nw, nt, &a)) return rc;
   const int nb = blocks_for(m->n_params, 256);
   (void)launch_pdl(k_adam, nb < 1 ? 1 : nb, 256, 0, st, m->n_params, m->params, m->adam_m, m->adam_v, m->grad, m->step, m->err, a);
   stage("adam");
   GNEP_CHECK_LAUNCH("adam");
+  return GNEP_OK;
+}
+
+int run_grad_adam(gnep_model* m, gnep_nlist* nl, double lambda_l2, double* loss_out, double b1, double b2,
+                  double eps, double wd, double lr_start, double lr_stop, int64_t nw, int64_t nt, cudaStream_t st) {
+  AdamArgs a;
+  if (int rc = adam_args(0.0, b1, b2, eps, wd, true, lr_start, lr_stop, nw, nt, &a)) return rc;
+  const DevModel dm = m->dev();
+  const int nb_cg = nl->n_atoms > 0 ? cgrad_blocks(nl) : 0;
+  const double l2coef = 2.0 * lambda_l2 / (double)m->n_params;
+  (void)launch_pdl(k_grad_adam, blocks_for(m->n_params, kGfCols), kGfCols * kGfRows, 0, st, dm, m->shape.ns,
+                   nl->ws.net_blocks, nb_cg, nl->ws.net_part, nl->ws.cpart, l2coef, m->grad, m->params, m->adam_m, m->adam_v,
+                   m->step, m->err, a, nl->ws.coef, loss_out);
+  stage("grad_adam");
+  GNEP_CHECK_LAUNCH("gradient and adam");
   return GNEP_OK;
 }
 

@@ -130,7 +130,7 @@ class NeighborList:
         return off, j[:n], sh[:n]
 
     TUNING_KEYS = ("desc_tile_atoms", "desc_tile_pairs", "force_tile_atoms", "force_tile_pairs", "cgrad_blocks",
-                   "net_blocks", "radial_lanes", "net_tile_atoms")
+                   "net_blocks", "radial_lanes", "net_tile_atoms", "radial_beside")
 
     def autotune(self, y: "Labels", reps: int = 3, stream=None) -> dict:
         """Pick the fastest launch shapes of the angular sweeps for this batch
@@ -318,6 +318,12 @@ class TrainGraph:
         replay is ordered with the caller's subsequent torch operations)."""
         s = stream if stream is not None else torch.cuda.current_stream()
         check(_lib.load().gnep_graph_launch(self.h, C.c_void_p(s.cuda_stream)))
+
+    def kernel_count(self) -> int:
+        """Kernels one replay launches."""
+        n = C.c_int32()
+        check(_lib.load().gnep_graph_kernel_count(self.h, C.byref(n)))
+        return n.value
 
     def close(self):
         if getattr(self, "h", None):

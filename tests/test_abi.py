@@ -31,7 +31,7 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_abi_version(lib):
-    assert lib.gnep_abi_version() == 4
+    assert lib.gnep_abi_version() == 5
 
 
 def test_lr_schedule_matches_oracle(lib, oracle):

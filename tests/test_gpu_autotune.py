@@ -48,6 +48,7 @@ def test_autotune_in_range_and_invalidates_graphs():
     assert after["desc_tile_pairs"] >= 1 and after["force_tile_pairs"] >= 1
     assert 1 <= after["cgrad_blocks"] <= 608
     assert after["radial_lanes"] in (4, 8, 16) and after["net_tile_atoms"] in (32, 128)
+    assert after["radial_beside"] in (1, 2)
     _, g1 = c.m.loss_grad(nl, y)
     c.m.sync_status()
     assert rel_l2(g1.cpu().numpy(), g0.cpu().numpy()) < 1e-5
@@ -63,10 +64,12 @@ def test_launch_shape_values_are_checked():
     b = synth.make_batch([20, 13], [2, 1], np.random.default_rng(5))
     c = Case("nmax4_basis8_h30", b, labels=False)
     t = c.nl.tuning()
-    assert t["radial_lanes"] == 16 and t["net_tile_atoms"] == 32, t  # a 33-atom batch takes the small-batch shapes
-    for bad in (dict(radial_lanes=5), dict(radial_lanes=32), dict(net_tile_atoms=64), dict(cgrad_blocks=10 ** 6)):
+    # a 33-atom batch takes the small-batch shapes
+    assert t["radial_lanes"] == 16 and t["net_tile_atoms"] == 32 and t["radial_beside"] == 2, t
+    for bad in (dict(radial_lanes=5), dict(radial_lanes=32), dict(net_tile_atoms=64), dict(cgrad_blocks=10 ** 6),
+                dict(radial_beside=3)):
         with pytest.raises(gnep._lib.GnepError):
             c.nl.set_tuning(bad)
-    c.nl.set_tuning(dict(radial_lanes=8, net_tile_atoms=128))
+    c.nl.set_tuning(dict(radial_lanes=8, net_tile_atoms=128, radial_beside=1))
     t = c.nl.tuning()
-    assert t["radial_lanes"] == 8 and t["net_tile_atoms"] == 128
+    assert t["radial_lanes"] == 8 and t["net_tile_atoms"] == 128 and t["radial_beside"] == 1

@@ -9,7 +9,8 @@ kernels with the default, one and three persistent blocks puts several tiles,
 and a species switch, inside one block, and gives the gradient assembly one or
 many block partials to combine.  The FP32 network runs with each tile size
 (32 atoms on the CUDA cores, 128 atoms on the tensor cores) and the
-radial sweeps with 4, 8 and 16 lanes per atom.  Checked against the oracle:
+radial sweeps with 4, 8 and 16 lanes per atom, in turn with the angular
+sweeps or beside them on a second stream.  Checked against the oracle:
 the loss terms and gradient (Eqs. 9-16, D1.18-D1.21) in the FP32 form at the
 FP32 tolerances and in the TF32 and BF16 network modes within four rounding
 units of their operand format; the descriptor scale computed on the GPU; and
@@ -50,12 +51,14 @@ def case():
     return c
 
 
-def _grad(c, mode, net_blocks, net_tile_atoms=0, radial_lanes=0):
+def _grad(c, mode, net_blocks, net_tile_atoms=0, radial_lanes=0, radial_beside=0):
     c.m.set_precision(mode)
     c.m.set_params(torch.from_numpy(c.P))
-    c.nl.set_tuning(dict(net_blocks=net_blocks, net_tile_atoms=net_tile_atoms, radial_lanes=radial_lanes))
+    c.nl.set_tuning(dict(net_blocks=net_blocks, net_tile_atoms=net_tile_atoms, radial_lanes=radial_lanes,
+                         radial_beside=radial_beside))
     t = c.nl.tuning()
     assert net_tile_atoms in (0, t["net_tile_atoms"]) and radial_lanes in (0, t["radial_lanes"]), t
+    assert radial_beside in (0, t["radial_beside"]), t
     terms, g = c.m.loss_grad(c.nl, c.gpu_labels())
     c.m.sync_status()
     return terms.cpu().numpy(), g.double().cpu().numpy()
@@ -66,15 +69,40 @@ def test_batch_spans_several_tiles_per_species(case):
     assert case.batch.n_atoms >= 420 and counts.min() > 128, counts
 
 
-@pytest.mark.parametrize("net_blocks,net_tile_atoms,radial_lanes",
-                         [(0, 0, 0), (1, 32, 4), (3, 32, 8), (0, 128, 16), (1, 128, 4), (3, 128, 0)])
-def test_fp32_gradient_matches_oracle(case, net_blocks, net_tile_atoms, radial_lanes):
-    terms, g = _grad(case, "fp32", net_blocks, net_tile_atoms, radial_lanes)
+@pytest.mark.parametrize("net_blocks,net_tile_atoms,radial_lanes,radial_beside",
+                         [(0, 0, 0, 0), (1, 32, 4, 1), (3, 32, 8, 2), (0, 128, 16, 1), (1, 128, 4, 2),
+                          (3, 128, 0, 0)])
+def test_fp32_gradient_matches_oracle(case, net_blocks, net_tile_atoms, radial_lanes, radial_beside):
+    terms, g = _grad(case, "fp32", net_blocks, net_tile_atoms, radial_lanes, radial_beside)
     np.testing.assert_allclose(terms, case.ref_terms, rtol=2e-5, atol=1e-12)
     ref = case.ref_g
     assert rel_l2(g, ref) < G_TOL, rel_l2(g, ref)
     bad = np.nonzero(np.abs(g - ref) > G_TOL * (np.abs(ref) + np.abs(ref).max()))[0]
     assert bad.size == 0, (bad[:10], g[bad[:10]], ref[bad[:10]])
+
+
+def test_radial_sweeps_beside_the_angular_ones_change_no_bit(case, tmp_path):
+    """The radial sweeps on the second stream run the same kernels on the same
+    data as in turn: the loss terms, the gradient and two graph-replayed
+    training steps (from the same saved model and Adam state) agree bit for
+    bit."""
+    ck = str(tmp_path / "start.ckpt")
+    case.m.save(ck)
+    out = {}
+    for beside in (1, 2):
+        case.m.load(ck)
+        terms, g = _grad(case, "fp32", 0, radial_beside=beside)
+        gr = gnep.TrainGraph(case.m, case.nl, case.gpu_labels(), 1e-3, 1e-5, 2, 10)
+        gr.launch()
+        gr.launch()
+        torch.cuda.synchronize()
+        gr.close()
+        case.m.sync_status()
+        out[beside] = (terms, g, case.m.get_params().cpu().numpy())
+    case.m.load(ck)
+    case.nl.set_tuning(None)
+    for a, b in zip(out[1], out[2]):
+        assert np.array_equal(a, b)
 
 
 @pytest.mark.parametrize("mode", ["tf32", "bf16"])

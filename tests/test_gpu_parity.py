@@ -207,6 +207,18 @@ def test_nonfinite_loss_skips_update():
     assert torch.equal(c.m.get_params(), p0)
     assert c.m.step_count() == 0
     c.m.sync_status()  # flag cleared
+    # the captured step (gradient, loss copy and update in one kernel) skips
+    # its update too, and still reports the loss
+    g = gnep.TrainGraph(c.m, c.nl, y, 1e-3, 1e-5, 2, 10)
+    g.launch()
+    torch.cuda.synchronize()
+    with pytest.raises(gnep._lib.GnepError, match="NONFINITE"):
+        c.m.sync_status()
+    assert torch.equal(c.m.get_params(), p0)
+    assert c.m.step_count() == 0
+    assert torch.isnan(g.loss[0]).item() and torch.equal(g.loss[2:].cpu(), terms[2:].cpu())
+    g.close()
+    c.m.sync_status()
 
 
 def test_step_is_deterministic_and_graph_replay_matches():
@@ -219,14 +231,18 @@ def test_step_is_deterministic_and_graph_replay_matches():
     assert torch.equal(g_a, g_b) and torch.equal(t_a, t_b)
     # eager steps on c1, graph replays on c2, same schedule
     for _ in range(3):
-        c1.m.loss_grad(c1.nl, y1, grad=False)
+        t_last, _ = c1.m.loss_grad(c1.nl, y1, grad=False)
         c1.m.adam_step_scheduled(1e-3, 1e-5, 2, 10)
     g = gnep.TrainGraph(c2.m, c2.nl, y2, 1e-3, 1e-5, 2, 10)
     for _ in range(3):
         g.launch()
     torch.cuda.synchronize()
     assert torch.equal(c1.m.get_params(), c2.m.get_params())
+    assert torch.equal(c1.m.get_grad(), c2.m.get_grad())  # the graph's gradient is kept for the API too
+    assert torch.equal(g.loss, t_last)  # the loss terms of the third step, before its update
     assert c2.m.step_count() == 3
+    # eleven sweep, network and loss kernels, and the gradient with the update
+    assert g.kernel_count() == 12
 
 
 def test_checkpoint_roundtrip_and_corruption(tmp_path):
