@@ -792,7 +792,9 @@ def report_batch_size(args):
     synthetic data): the same student trained for a fixed number of epochs over
     the 256-structure workload split into batches of B structures, with the
     Eq. 17 schedule over the whole run; final training loss, held-out force and
-    energy RMSE, and wall time per B."""
+    energy RMSE, and wall time per B, with the steps of an epoch captured as
+    one graph and, for comparison, as one graph per step (the same training
+    bit for bit, checked)."""
     from paper_2507_00528_gb300 import synth
     import torch
     from paper_2507_00528_gb300 import build as gbuild
@@ -811,35 +813,53 @@ def report_batch_size(args):
     order = np.random.default_rng(5).permutation(train.n_struct)  # fixed batch composition
     epochs = args.epochs
     out = {}
-    for B in (1, 4, 16, 64, 256):
+    for B in [int(b) for b in args.study_batches.split(",")]:
         groups = [order[k:k + B] for k in range(0, train.n_struct, B)]
         subs = [train.subset(sorted(g)) for g in groups]
         nls = [teacher.neighbors(gnep.DeviceBatch.from_host(b)) for b in subs]
+        if args.radial_beside:
+            for nl in nls:
+                nl.set_tuning({"radial_beside": args.radial_beside})
         ys = [teacher.teacher_labels(nl, b.sizes(), **LAMBDAS) for nl, b in zip(nls, subs)]
-        student = gnep.GNEP(**MODEL_KW, seed=11, precision=args.precision)
-        student.set_scale(scale)
         n_steps = epochs * len(nls)
-        graphs = [gnep.TrainGraph(student, nl, y, 2e-3, 2e-5, len(nls), n_steps) for nl, y in zip(nls, ys)]
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(epochs):
+
+        def run_training(epoch_graph):
+            # one graph per epoch (all its steps), or one graph per step
+            student = gnep.GNEP(**MODEL_KW, seed=11, precision=args.precision)
+            student.set_scale(scale)
+            if epoch_graph:
+                graphs = [gnep.TrainGraph(student, nls, ys, 2e-3, 2e-5, len(nls), n_steps)]
+            else:
+                graphs = [gnep.TrainGraph(student, nl, y, 2e-3, 2e-5, len(nls), n_steps) for nl, y in zip(nls, ys)]
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(epochs):
+                for gr in graphs:
+                    gr.launch()
+            e1.record()
+            torch.cuda.synchronize()
+            student.sync_status()
             for gr in graphs:
-                gr.launch()
-        e1.record()
-        torch.cuda.synchronize()
-        student.sync_status()
-        ms = e0.elapsed_time(e1)
+                gr.close()
+            return student, e0.elapsed_time(e1)
+
+        per_step, ms_step = run_training(False)
+        student, ms = run_training(True)
+        assert torch.equal(per_step.get_params(), student.get_params())  # the same training, bit for bit
         full = student.loss(nl_all, teacher.teacher_labels(nl_all, train.sizes(), **LAMBDAS)).cpu().numpy()
         _, Es, F, _ = student.forward(nl_te)
         out[str(B)] = {"steps": n_steps, "train_ms": round(ms, 2), "ms_per_step": round(ms / n_steps, 4),
+                       "ms_per_step_graph_per_step": round(ms_step / n_steps, 4),
                        "train_loss_full_batch": float(full[0]),
                        "test_force_rmse": float(np.sqrt(np.mean((F.double().cpu().numpy() - F_te) ** 2))),
                        "test_energy_rmse": float(np.sqrt(np.mean((Es.cpu().numpy() / test.sizes() - E_te) ** 2)))}
-        del graphs, nls, ys
+        del nls, ys
     line = {"report": "batch-size", "workload": WORKLOAD["workload"], "epochs": epochs,
+            "graphs": "one per epoch (ms_per_step); one per step (ms_per_step_graph_per_step)",
             "precision": args.precision, "lr": "Eq. 17, 2e-3 -> 2e-5, warm-up one epoch",
             "held_out": f"{test.n_struct} structures ({test.n_atoms} atoms) from another seed",
+            "radial_beside": args.radial_beside or "default",
             "by_batch_structures": out, "source_sha": csrc_sha()}
     print(json.dumps(line), flush=True)
 
@@ -946,6 +966,10 @@ def main():
     ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--batches", default="1,4,16,64",
                     help="small-batch report: batch sizes in structures, comma separated")
+    ap.add_argument("--study-batches", default="1,4,16,64,256",
+                    help="batch-size report: batch sizes in structures, comma separated")
+    ap.add_argument("--radial-beside", type=int, default=0, choices=[0, 1, 2],
+                    help="batch-size report: radial sweeps in turn (1) or beside the angular ones (2); 0 = default")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

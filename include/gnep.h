@@ -313,6 +313,22 @@ int gnep_graph_create(gnep_model *m, const gnep_nlist *nl, const gnep_labels *y,
                       int64_t n_warmup, int64_t n_total, double beta1,
                       double beta2, double eps, double weight_decay,
                       void *stream, gnep_graph **out);
+/* n_steps training steps captured as one CUDA graph: step b trains on the
+ * batch (nls[b], ys[b]) as gnep_graph_create's step does, in order, so that
+ * one launch replays, for instance, a whole epoch of one-structure batches
+ * with the same results bit for bit as the n_steps single-step graphs (or the
+ * eager call pairs) launched in turn.  A list may appear more than once.
+ * loss_out: device [4 n_steps] (may be NULL), step b's loss terms at 4 b.
+ * Lists, labels and loss_out must outlive the graph; launching after any of
+ * the lists was rebuilt or retuned returns INVALID_ARG.
+ * Errors: INVALID_ARG (NULL, n_steps < 1, host labels or loss buffer, the
+ * default stream, a list of another model), UNSUPPORTED, OOM, CUDA. */
+int gnep_graph_create_steps(gnep_model *m, const gnep_nlist *const *nls,
+                            const gnep_labels *ys, int32_t n_steps,
+                            double *loss_out, double lr_start, double lr_stop,
+                            int64_t n_warmup, int64_t n_total, double beta1,
+                            double beta2, double eps, double weight_decay,
+                            void *stream, gnep_graph **out);
 int gnep_graph_launch(gnep_graph *g, void *stream);
 int gnep_graph_destroy(gnep_graph *g);
 /* Kernels one replay launches (the graph's kernel nodes), to *n.

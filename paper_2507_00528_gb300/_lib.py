@@ -29,7 +29,7 @@ EXPORTS = [
     "gnep_nlist_destroy", "gnep_nlist_info", "gnep_nlist_export", "gnep_descriptors", "gnep_forward",
     "gnep_loss_grad", "gnep_adam_step", "gnep_adam_step_scheduled", "gnep_get_step",
     "gnep_lr_schedule", "gnep_graph_create", "gnep_graph_launch", "gnep_graph_destroy",
-    "gnep_graph_kernel_count", "gnep_save",
+    "gnep_graph_kernel_count", "gnep_graph_create_steps", "gnep_save",
     "gnep_load", "gnep_sync_status", "gnep_last_error", "gnep_abi_version", "gnep_profile_step",
     "gnep_profile_stage_name", "gnep_descriptors_noalloc", "gnep_loss", "gnep_get_grad", "gnep_set_grad",
     "gnep_autotune", "gnep_tuning_get", "gnep_tuning_set", "gnep_md_verlet", "gnep_shard_loss_weights",
@@ -91,6 +91,8 @@ _SIGS = {
     "gnep_graph_create": [_vp, _vp, C.POINTER(Labels), _vp, C.c_double, C.c_double, C.c_int64,
                           C.c_int64, C.c_double, C.c_double, C.c_double, C.c_double, _vp,
                           C.POINTER(_vp)],
+    "gnep_graph_create_steps": [_vp, _vp, C.POINTER(Labels), C.c_int32, _vp, C.c_double, C.c_double, C.c_int64,
+                                C.c_int64, C.c_double, C.c_double, C.c_double, C.c_double, _vp, C.POINTER(_vp)],
     "gnep_graph_launch": [_vp, _vp],
     "gnep_graph_destroy": [_vp],
     "gnep_graph_kernel_count": [_vp, _vp],

@@ -681,31 +681,39 @@ double gnep_lr_schedule(double lr_start, double lr_stop, int64_t s, int64_t n_wa
 struct gnep_graph {
   cudaGraph_t g = nullptr;
   cudaGraphExec_t ge = nullptr;
-  const gnep_nlist* nl = nullptr;
-  uint64_t gen = 0;  // generation of the neighbour list at capture
+  std::vector<const gnep_nlist*> nl;  // the batch of each captured step
+  std::vector<uint64_t> gen;          // generation of each list at capture
 };
 
-int gnep_graph_create(gnep_model* m, const gnep_nlist* nl_, const gnep_labels* y, double* loss_out,
-                      double lr_start, double lr_stop, int64_t n_warmup, int64_t n_total, double beta1,
-                      double beta2, double eps, double weight_decay, void* stream, gnep_graph** out) {
-  int rc = check_nlist(m, nl_);
-  if (rc) return rc;
-  if (!out || !y || !stream) return set_error(GNEP_ERR_INVALID_ARG, "graph capture needs labels and a non-default stream");
-  if (!is_device_ptr(y->energy) || !is_device_ptr(y->force) || !is_device_ptr(y->virial) ||
-      (loss_out && !is_device_ptr(loss_out)))
-    return set_error(GNEP_ERR_INVALID_ARG, "graph capture needs device labels and a device loss buffer");
-  gnep_nlist* nl = const_cast<gnep_nlist*>(nl_);
+// Captures the training steps b = 0 .. n-1 (forward, loss, backward, then the
+// gradient with the scheduled Adam update in one kernel) on batches
+// (nls[b], ys[b]) into one graph.
+static int graph_create(gnep_model* m, const gnep_nlist* const* nls, const gnep_labels* ys, int n, double* loss_out,
+                        double lr_start, double lr_stop, int64_t n_warmup, int64_t n_total, double beta1,
+                        double beta2, double eps, double weight_decay, void* stream, gnep_graph** out) {
+  if (!out || !nls || !ys || n < 1 || !stream)
+    return set_error(GNEP_ERR_INVALID_ARG, "graph capture needs lists, labels, n >= 1 and a non-default stream");
+  if (loss_out && !is_device_ptr(loss_out))
+    return set_error(GNEP_ERR_INVALID_ARG, "graph capture needs a device loss buffer");
+  for (int b = 0; b < n; ++b) {
+    if (int rc = check_nlist(m, nls[b])) return rc;
+    const gnep_labels& y = ys[b];
+    if (!is_device_ptr(y.energy) || !is_device_ptr(y.force) || !is_device_ptr(y.virial))
+      return set_error(GNEP_ERR_INVALID_ARG, "graph capture needs device labels");
+    if (nls[b]->ready_ev) GNEP_CUDA(cudaEventSynchronize(nls[b]->ready_ev));  // a capture cannot wait on it
+  }
   cudaStream_t st = (cudaStream_t)stream;
-  if (nl->ready_ev) GNEP_CUDA(cudaEventSynchronize(nl->ready_ev));  // a capture cannot wait on it
   GNEP_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-  // the step of gnep_loss_grad + gnep_adam_step_scheduled, with the gradient
-  // reduction, the copy of the loss terms and the update in one kernel
-  rc = forward_loss(m, nl, y, st);
-  StepArgs A{m, nl, st};
-  if (!rc) rc = run_backward(A);
-  if (!rc)
-    rc = run_grad_adam(m, nl, y->lambda_l2, loss_out, beta1, beta2, eps, weight_decay, lr_start, lr_stop, n_warmup,
-                       n_total, st);
+  int rc = GNEP_OK;
+  for (int b = 0; b < n && !rc; ++b) {
+    gnep_nlist* nl = const_cast<gnep_nlist*>(nls[b]);
+    rc = forward_loss(m, nl, &ys[b], st);
+    StepArgs A{m, nl, st};
+    if (!rc) rc = run_backward(A);
+    if (!rc)
+      rc = run_grad_adam(m, nl, ys[b].lambda_l2, loss_out ? loss_out + 4 * (size_t)b : nullptr, beta1, beta2, eps,
+                         weight_decay, lr_start, lr_stop, n_warmup, n_total, st);
+  }
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(st, &g);
   if (rc) {
@@ -715,8 +723,10 @@ int gnep_graph_create(gnep_model* m, const gnep_nlist* nl_, const gnep_labels* y
   if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture");
   gnep_graph* gr = new gnep_graph();
   gr->g = g;
-  gr->nl = nl;
-  gr->gen = nl->gen;
+  for (int b = 0; b < n; ++b) {
+    gr->nl.push_back(nls[b]);
+    gr->gen.push_back(nls[b]->gen);
+  }
   e = cudaGraphInstantiate(&gr->ge, g, 0);
   if (e != cudaSuccess) {
     cudaGraphDestroy(g);
@@ -727,11 +737,33 @@ int gnep_graph_create(gnep_model* m, const gnep_nlist* nl_, const gnep_labels* y
   return GNEP_OK;
 }
 
+int gnep_graph_create(gnep_model* m, const gnep_nlist* nl, const gnep_labels* y, double* loss_out,
+                      double lr_start, double lr_stop, int64_t n_warmup, int64_t n_total, double beta1,
+                      double beta2, double eps, double weight_decay, void* stream, gnep_graph** out) {
+  if (!y) return set_error(GNEP_ERR_INVALID_ARG, "graph capture needs labels");
+  return graph_create(m, &nl, y, 1, loss_out, lr_start, lr_stop, n_warmup, n_total, beta1, beta2, eps,
+                      weight_decay, stream, out);
+}
+
+int gnep_graph_create_steps(gnep_model* m, const gnep_nlist* const* nls, const gnep_labels* ys, int32_t n_steps,
+                            double* loss_out, double lr_start, double lr_stop, int64_t n_warmup, int64_t n_total,
+                            double beta1, double beta2, double eps, double weight_decay, void* stream,
+                            gnep_graph** out) {
+  return graph_create(m, nls, ys, n_steps, loss_out, lr_start, lr_stop, n_warmup, n_total, beta1, beta2, eps,
+                      weight_decay, stream, out);
+}
+
 int gnep_graph_launch(gnep_graph* g, void* stream) {
   if (!g) return set_error(GNEP_ERR_INVALID_ARG, "NULL graph");
-  if (g->nl && g->nl->gen != g->gen)
-    return set_error(GNEP_ERR_INVALID_ARG, "the neighbour list was rebuilt or retuned after this graph was captured");
-  if (int rc = after_build(g->nl, (cudaStream_t)stream)) return rc;
+  for (size_t b = 0; b < g->nl.size(); ++b)
+    if (g->nl[b]->gen != g->gen[b])
+      return set_error(GNEP_ERR_INVALID_ARG, "a neighbour list was rebuilt or retuned after this graph was captured");
+  const gnep_nlist* last = nullptr;
+  for (const gnep_nlist* nl : g->nl)
+    if (nl != last) {  // consecutive repeats need one wait
+      if (int rc = after_build(nl, (cudaStream_t)stream)) return rc;
+      last = nl;
+    }
   GNEP_CUDA(cudaGraphLaunch(g->ge, (cudaStream_t)stream));
   return GNEP_OK;
 }

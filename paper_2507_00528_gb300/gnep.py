@@ -298,19 +298,33 @@ def lr_schedule(lr_start, lr_stop, s, n_warmup, n_total) -> float:
 
 
 class TrainGraph:
-    """One captured training step (loss + gradient + scheduled Adam) replayed as a CUDA graph."""
+    """One captured training step (loss + gradient + scheduled Adam) replayed as
+    a CUDA graph; with lists of neighbour lists and labels, that many steps in
+    order (for instance an epoch of one-structure batches) in one graph, whose
+    `loss` holds the loss terms of each step (shape [n_steps, 4])."""
 
-    def __init__(self, model: GNEP, nl: NeighborList, y: Labels, lr_start, lr_stop, n_warmup, n_total,
+    def __init__(self, model: GNEP, nl, y, lr_start, lr_stop, n_warmup, n_total,
                  beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0, stream=None):
         self.stream = stream or torch.cuda.Stream()
-        self.loss = torch.zeros(4, dtype=torch.float64, device="cuda")
-        self._keep = (model, nl, y)
-        self._yc = y.c()
+        steps = isinstance(nl, (list, tuple))
+        nls, ys = (list(nl), list(y)) if steps else ([nl], [y])
+        assert len(nls) == len(ys) and len(nls) >= 1
+        self.loss = torch.zeros((len(nls), 4) if steps else (4,), dtype=torch.float64, device="cuda")
+        self._keep = (model, nls, ys)
         h = C.c_void_p()
         torch.cuda.synchronize()
-        check(_lib.load().gnep_graph_create(model.h, nl.h, C.byref(self._yc), _ptr(self.loss), lr_start, lr_stop,
-                                            n_warmup, n_total, beta1, beta2, eps, weight_decay,
-                                            C.c_void_p(self.stream.cuda_stream), C.byref(h)))
+        if steps:
+            self._yc = (_lib.Labels * len(ys))(*[yy.c() for yy in ys])
+            self._nlh = (C.c_void_p * len(nls))(*[n.h.value for n in nls])
+            check(_lib.load().gnep_graph_create_steps(model.h, self._nlh, self._yc, len(nls), _ptr(self.loss),
+                                                      lr_start, lr_stop, n_warmup, n_total, beta1, beta2, eps,
+                                                      weight_decay, C.c_void_p(self.stream.cuda_stream),
+                                                      C.byref(h)))
+        else:
+            self._yc = y.c()
+            check(_lib.load().gnep_graph_create(model.h, nl.h, C.byref(self._yc), _ptr(self.loss), lr_start,
+                                                lr_stop, n_warmup, n_total, beta1, beta2, eps, weight_decay,
+                                                C.c_void_p(self.stream.cuda_stream), C.byref(h)))
         self.h = h
 
     def launch(self, stream=None):

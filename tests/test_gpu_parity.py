@@ -467,3 +467,45 @@ def test_atoms_without_angular_neighbours():
     _, g = c.m.loss_grad(c.nl, y)
     _, ref = O.loss_grad(c.cfg, c.P64, c.s64, b, c.y)
     check_grad(g.cpu().numpy(), ref)
+
+
+def test_step_sequence_graph_matches_single_steps():
+    """Four training steps over three one-structure batches (the first batch
+    twice) captured as one graph give, bit for bit, the parameters, the
+    update count and each step's loss terms of the eager step pairs; a second
+    launch continues the same way, and a retuned list refuses the launch."""
+    kw = dict(n_max=(8, 8), basis=(12, 12), hidden=50, four_body=True)
+    b = synth.make_config(2, n_struct=6)
+    teacher = gnep.GNEP(**kw, seed=12)
+    teacher.compute_scale(teacher.neighbors(gnep.DeviceBatch.from_host(b)))
+    subs = [b.subset([k]) for k in (0, 3, 5)]
+    ys = [teacher.teacher_labels(teacher.neighbors(gnep.DeviceBatch.from_host(s)), s.sizes(), lambda_e=1.0,
+                                 lambda_f=1.0, lambda_v=0.1) for s in subs]
+    seq = [0, 1, 2, 0]
+
+    def student():
+        m = gnep.GNEP(**kw, seed=11)
+        m.set_scale(teacher.get_scale())
+        return m, [m.neighbors(gnep.DeviceBatch.from_host(s)) for s in subs]
+
+    ma, nla = student()
+    mb, nlb = student()
+    g = gnep.TrainGraph(mb, [nlb[k] for k in seq], [ys[k] for k in seq], 1e-3, 1e-5, 2, 10)
+    assert g.kernel_count() == 12 * len(seq)
+    for rep in range(2):
+        terms = []
+        for k in seq:
+            t, _ = ma.loss_grad(nla[k], ys[k], grad=False)
+            ma.adam_step_scheduled(1e-3, 1e-5, 2, 10)
+            terms.append(t.clone())
+        g.launch()
+        torch.cuda.synchronize()
+        ma.sync_status()
+        mb.sync_status()
+        assert torch.equal(ma.get_params(), mb.get_params()), rep
+        assert torch.equal(g.loss, torch.stack(terms)), rep
+        assert mb.step_count() == len(seq) * (rep + 1)
+    nlb[1].set_tuning(None)
+    with pytest.raises(gnep._lib.GnepError, match="INVALID_ARG"):
+        g.launch()
+    g.close()
