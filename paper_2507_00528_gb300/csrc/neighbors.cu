@@ -459,7 +459,7 @@ __global__ void __launch_bounds__(128) k_pairs_flat(
 
 // Binned search, one warp per central atom i (the slot pass) of the
 // structures above kCellMinAtoms atoms; the smaller ones take the all-pairs
-// search (k_pairs), which is as fast there: at cell widths below 3 r_c the
+// search (k_pairs_flat), which is as fast there: at cell widths below 3 r_c the
 // visited bins cover about the whole cell.  The bins of structure s split its
 // cell into nbin[s] parts along each cell direction; every (j, n) within r_c of
 // i has f_j + n inside (f_i - t, f_i + t) along each direction (t = r_c / w_x,
