@@ -348,22 +348,33 @@ __global__ void __launch_bounds__(128) k_pairs(
 }
 
 // The slot pass for structures of at most kCellMinAtoms atoms, one warp per
-// central atom i, with the candidates flattened: in each round of 32
-// consecutive j the lanes count the images their j may have within the cut-offs
-// (the fractional bounds of k_pairs), a warp scan lays those (j, image)
-// candidates out in canonical order (j ascending, then image lexicographic),
-// and the lanes then take them 32 at a time, so that every lane tests a
-// candidate in every step instead of walking its own j's images while the
-// others wait.  Each lane finds its candidate's j by a binary search over the
-// scan; accepted entries are placed by ballots in the same canonical order
-// (counts exact; the first cap entries of each list go to the atom's slots).
-__global__ void __launch_bounds__(128) k_pairs_flat(
+// central atom i, with the candidates flattened: in each round of kFlatJ = 64
+// consecutive j (two per lane) the lanes count the images their j may have
+// within the cut-offs (the fractional bounds of k_pairs), a warp scan lays
+// those (j, image) candidates out in canonical order (j ascending, then image
+// lexicographic) and the lanes then take them 32 at a time, so that every lane
+// tests a candidate in every step instead of walking its own j's images while
+// the others wait.  The round's per-j bounds and scan sit in the warp's shared
+// memory; each lane finds its candidate's j by a binary search over the scan.
+// Accepted entries are placed by ballots in the same canonical order (counts
+// exact; the first cap entries of each list go to the atom's slots).  Two j per
+// lane fill about half of the candidate steps' lanes on cells of the
+// 32-400-atom workload, where one j per lane filled under a third.
+constexpr int kFlatWarps = 4, kFlatJ = 64;
+
+__global__ void __launch_bounds__(32 * kFlatWarps) k_pairs_flat(
     int N, const int* __restrict__ struct_off, const int* __restrict__ atom_struct,
     const double* __restrict__ pos, const double* __restrict__ cell, const int* __restrict__ krange,
     const float* __restrict__ tw, const float* __restrict__ hsplit, const float4* __restrict__ frac,
     const float4* __restrict__ phi, ListParams lp, int* __restrict__ cnt0, int* __restrict__ cnt1, Slots sl) {
+  // per warp and round: dj = phi_j - phi_i, (alo, blo, clo, j), (nb count, nc
+  // count, candidates before this j) and the inclusive candidate counts
+  __shared__ float4 sdj[kFlatWarps][kFlatJ];
+  __shared__ int4 slo[kFlatWarps][kFlatJ];
+  __shared__ int4 scnt[kFlatWarps][kFlatJ];
+  __shared__ int sincl[kFlatWarps][kFlatJ];
   const int i = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
   if (i >= N) return;  // the whole warp
   const int s = atom_struct[i];
   const int a0 = struct_off[s], a1 = struct_off[s + 1];
@@ -377,56 +388,63 @@ __global__ void __launch_bounds__(128) k_pairs_flat(
   const float t0 = tw[3 * s] + 1e-3f, t1 = tw[3 * s + 1] + 1e-3f, t2 = tw[3 * s + 2] + 1e-3f;
   const unsigned lt = (1u << lane) - 1u;
   int w0 = 0, w1 = 0;  // entries of each list so far (warp-uniform)
-  for (int jb = a0; jb < a1; jb += 32) {
-    const int j = jb + lane;
-    const bool vj = j < a1;
-    const float4 pjh = vj ? phi[j] : pih;
-    const float4 fj = vj ? frac[j] : fi;
-    const float dj[3] = {pjh.x - pih.x, pjh.y - pih.y, pjh.z - pih.z};
-    const float dfa = fj.x - fi.x, dfb = fj.y - fi.y, dfc = fj.z - fi.z;
-    const int alo = max(-ka, (int)ceilf(-t0 - dfa)), ahi = vj ? min(ka, (int)floorf(t0 - dfa)) : alo - 1;
-    const int blo = max(-kb, (int)ceilf(-t1 - dfb)), bhi = min(kb, (int)floorf(t1 - dfb));
-    const int clo = max(-kc, (int)ceilf(-t2 - dfc)), chi = min(kc, (int)floorf(t2 - dfc));
-    const int nbc = max(0, bhi - blo + 1), ncc = max(0, chi - clo + 1);
-    const int ncand = max(0, ahi - alo + 1) * nbc * ncc;  // this lane's candidate images
-    int incl = ncand;  // inclusive scan over the lanes
+  for (int jb = a0; jb < a1; jb += kFlatJ) {
+    int base = 0;  // candidates of the round's first half (after its scan)
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int u = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += u;
+    for (int h = 0; h < 2; ++h) {  // j = jb + 32 h + lane at position 32 h + lane
+      const int j = jb + 32 * h + lane;
+      const bool vj = j < a1;
+      const float4 pjh = vj ? phi[j] : pih;
+      const float4 fj = vj ? frac[j] : fi;
+      const float dfa = fj.x - fi.x, dfb = fj.y - fi.y, dfc = fj.z - fi.z;
+      const int alo = max(-ka, (int)ceilf(-t0 - dfa)), ahi = vj ? min(ka, (int)floorf(t0 - dfa)) : alo - 1;
+      const int blo = max(-kb, (int)ceilf(-t1 - dfb)), bhi = min(kb, (int)floorf(t1 - dfb));
+      const int clo = max(-kc, (int)ceilf(-t2 - dfc)), chi = min(kc, (int)floorf(t2 - dfc));
+      const int nbc = max(0, bhi - blo + 1), ncc = max(0, chi - clo + 1);
+      const int ncand = max(0, ahi - alo + 1) * nbc * ncc;  // this j's candidate images
+      int incl = ncand;  // inclusive scan over the lanes
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+      }
+      incl += base;
+      const int x = 32 * h + lane;
+      sdj[wb][x] = make_float4(pjh.x - pih.x, pjh.y - pih.y, pjh.z - pih.z, 0.f);
+      slo[wb][x] = make_int4(alo, blo, clo, j);
+      scnt[wb][x] = make_int4(nbc, ncc, incl - ncand, 0);
+      sincl[wb][x] = incl;
+      base = __shfl_sync(0xffffffffu, incl, 31);
     }
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
-    const int excl = incl - ncand;
+    __syncwarp();
+    const int total = base;
     for (int cb = 0; cb < total; cb += 32) {
       const int c = cb + lane;
       const bool valid = c < total;
-      int L = 0;  // the lane whose j owns candidate c: incl[L - 1] <= c < incl[L]
+      int L = 0;  // the position whose j owns candidate c: incl[L - 1] <= c < incl[L] (at most 63)
 #pragma unroll
-      for (int st = 16; st >= 1; st >>= 1)
-        if (__shfl_sync(0xffffffffu, incl, L + st - 1) <= c) L += st;
-      const int m = c - __shfl_sync(0xffffffffu, excl, L);
-      const int oj = __shfl_sync(0xffffffffu, j, L);
-      const int oa = __shfl_sync(0xffffffffu, alo, L), ob = __shfl_sync(0xffffffffu, blo, L);
-      const int oc = __shfl_sync(0xffffffffu, clo, L);
-      const int onb = __shfl_sync(0xffffffffu, nbc, L), onc = __shfl_sync(0xffffffffu, ncc, L);
-      const float odj[3] = {__shfl_sync(0xffffffffu, dj[0], L), __shfl_sync(0xffffffffu, dj[1], L),
-                            __shfl_sync(0xffffffffu, dj[2], L)};
+      for (int st = kFlatJ / 2; st >= 1; st >>= 1)
+        if (sincl[wb][L + st - 1] <= c) L += st;
       bool in0 = false, in1 = false;
-      int na = 0, nb = 0, nc = 0;
+      int na = 0, nb = 0, nc = 0, oj = 0;
       if (valid) {  // image m of the owner's (na, nb, nc) ranges, nc fastest (a few steps: no division)
-        int r = m;
-        const int bc = onb * onc;
-        na = oa;
+        const float4 d4 = sdj[wb][L];
+        const int4 lo = slo[wb][L], cn = scnt[wb][L];
+        const float odj[3] = {d4.x, d4.y, d4.z};
+        oj = lo.w;
+        int r = c - cn.z;
+        const int bc = cn.x * cn.y;
+        na = lo.x;
         while (r >= bc) {
           r -= bc;
           ++na;
         }
-        nb = ob;
-        while (r >= onc) {
-          r -= onc;
+        nb = lo.y;
+        while (r >= cn.y) {
+          r -= cn.y;
           ++nb;
         }
-        nc = oc + r;
+        nc = lo.z + r;
         decide_pair(i, oj, na, nb, nc, odj, Hh, lp, cell, pos, s, in0, in1);
       }
       const unsigned b0 = __ballot_sync(0xffffffffu, in0), b1 = __ballot_sync(0xffffffffu, in1);
@@ -450,6 +468,7 @@ __global__ void __launch_bounds__(128) k_pairs_flat(
       w0 += __popc(b0);
       w1 += __popc(b1);
     }
+    __syncwarp();  // the round's shared entries are read before the next round writes them
   }
   if (lane == 0) {
     cnt0[i] = w0;
@@ -773,7 +792,7 @@ int build_lists(gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
     sl.sh[0] = reinterpret_cast<char4*>(sl.j[1] + n1);
     sl.sh[1] = sl.sh[0] + n0;
   }
-  k_pairs_flat<<<blocks_for((int64_t)N * 32, 128), 128, 0, st>>>(N, nl->struct_off, nl->atom_struct, nl->pos,
+  k_pairs_flat<<<blocks_for((int64_t)N * 32, 32 * kFlatWarps), 32 * kFlatWarps, 0, st>>>(N, nl->struct_off, nl->atom_struct, nl->pos,
                                                                  nl->cell, kr, tw, hsplit, frac, phi, lp, cnt0, cnt1,
                                                                  sl);
   k_pairs_cell<<<(unsigned)std::min<int64_t>((N + kCellWarps - 1) / kCellWarps, 1216), 32 * kCellWarps, 0, st>>>(
