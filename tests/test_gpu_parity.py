@@ -469,18 +469,21 @@ def test_atoms_without_angular_neighbours():
     check_grad(g.cpu().numpy(), ref)
 
 
-def test_step_sequence_graph_matches_single_steps():
+@pytest.mark.parametrize("loss_form,lambda_l2", [(0, 0.0), (1, 1e-3)])
+def test_step_sequence_graph_matches_single_steps(loss_form, lambda_l2):
     """Four training steps over three one-structure batches (the first batch
     twice) captured as one graph give, bit for bit, the parameters, the
-    update count and each step's loss terms of the eager step pairs; a second
-    launch continues the same way, and a retuned list refuses the launch."""
+    update count and each step's loss terms of the eager step pairs, in the
+    MSE form and in the RMSE form with the L2 term; a second launch continues
+    the same way, and a retuned list refuses the launch."""
     kw = dict(n_max=(8, 8), basis=(12, 12), hidden=50, four_body=True)
     b = synth.make_config(2, n_struct=6)
     teacher = gnep.GNEP(**kw, seed=12)
     teacher.compute_scale(teacher.neighbors(gnep.DeviceBatch.from_host(b)))
     subs = [b.subset([k]) for k in (0, 3, 5)]
     ys = [teacher.teacher_labels(teacher.neighbors(gnep.DeviceBatch.from_host(s)), s.sizes(), lambda_e=1.0,
-                                 lambda_f=1.0, lambda_v=0.1) for s in subs]
+                                 lambda_f=1.0, lambda_v=0.1, lambda_l2=lambda_l2, loss_form=loss_form)
+          for s in subs]
     seq = [0, 1, 2, 0]
 
     def student():
@@ -491,7 +494,7 @@ def test_step_sequence_graph_matches_single_steps():
     ma, nla = student()
     mb, nlb = student()
     g = gnep.TrainGraph(mb, [nlb[k] for k in seq], [ys[k] for k in seq], 1e-3, 1e-5, 2, 10)
-    assert g.kernel_count() == 12 * len(seq)
+    assert g.kernel_count() == (12 + loss_form) * len(seq)  # the RMSE form adds the residual-weight kernel
     for rep in range(2):
         terms = []
         for k in seq:
