@@ -51,7 +51,7 @@ L2_BYTES = 129 * 1024 * 1024
 
 # ----------------------------------------------------------------- FLOP model
 
-def survey_flops(nqr=9, kr=13, nqa=9, ka=13, ns=2, H=50, fb=True, N=1, PR=1, PA=1, L=24):
+def work_model_flops(nqr=9, kr=13, nqa=9, ka=13, ns=2, H=50, fb=True, N=1, PR=1, PA=1, L=24):
     """Algorithmic FP32 FLOPs per launch of each kernel, on the fixed work
     model of the method (FMA = 2 FLOP), counted per unit as the formulation
     needs it, whatever the kernels do:
@@ -473,7 +473,7 @@ def roofline_line(stage_ms, n_atoms, PR, PA, props, clocks, step_ms):
     measured), at the maximum clock and at the median clock of the run.  The
     kernel's compulsory bytes against the measured copy bandwidth, and the
     whole step's FLOPs and compulsory bytes per atom, stand beside it."""
-    fl = survey_flops(N=n_atoms, PR=PR, PA=PA)
+    fl = work_model_flops(N=n_atoms, PR=PR, PA=PA)
     by = algo_bytes(N=n_atoms, PR=PR, PA=PA)
     kernels = {k: v for k, v in stage_ms.items() if k in fl}
     dom = max(kernels, key=kernels.get)

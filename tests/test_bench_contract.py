@@ -56,11 +56,11 @@ def test_work_model_of_the_benchmark_workload():
     the tangent sweep's angular part costs 4 N_q^A K + 270 + 4 N_q^A L =
     468 + 270 + 864 = 1,602 FLOP per angular pair plus 2 N_q^A L = 432 per
     atom, 0.785 GFLOP per launch; the network 12 N_des H per atom in all."""
-    f = bench.survey_flops(N=57101, PR=2679524, PA=474686)
+    f = bench.work_model_flops(N=57101, PR=2679524, PA=474686)
     assert f["tangent_angular"] == 1602 * 474686 + 432 * 57101
     assert f["tangent_angular"] == pytest.approx(0.785e9, rel=1e-3)
     assert f["mlp_fwd"] + f["mlp_bwd"] == 12 * 54 * 50 * 57101
     assert f["desc_radial"] == (15 + 4 * 13 + 2 * 9 * 13) * 2679524
-    double = bench.survey_flops(N=2 * 57101, PR=2 * 2679524, PA=2 * 474686)
+    double = bench.work_model_flops(N=2 * 57101, PR=2 * 2679524, PA=2 * 474686)
     for k, v in f.items():
         assert v > 0 and double[k] == 2 * v, k
