@@ -93,7 +93,7 @@ typedef struct {
 /* ---------------------------------------------------------------- model */
 
 /* Create a model (Sec. II.B-C; Eq. 6 basis, Eq. 8 harmonics, D1.1 network).
- * n_species        species count (only 2 has compiled kernels in this build)
+ * n_species        species count (the library compiles kernels for 2)
  * species_z        [n_species] atomic numbers, informative (may be NULL)
  * rc_radial/angular cut-offs r_c^R, r_c^A (A), 0 < rc_angular <= rc_radial
  * n_max_*          descriptors per family are n_max + 1 (n = 0..n_max)

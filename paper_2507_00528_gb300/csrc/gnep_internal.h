@@ -11,7 +11,7 @@
 
 namespace gnep {
 
-// Compile-time maxima of this build.
+// Compile-time maxima of the library.
 constexpr int kMaxHidden = 128;
 constexpr int kMaxDes = 64;
 constexpr int kLmax = 4;
