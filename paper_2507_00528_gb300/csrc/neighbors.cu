@@ -593,30 +593,51 @@ __global__ void __launch_bounds__(32 * kCellWarps) k_pairs_cell(
   }
 }
 
-// Copies the per-atom slots into the CSR lists and forms r_ij (thread per atom
-// and slot, so the float-float arithmetic runs on dense lanes).
-__global__ void k_compact(int N, int cap, const int* __restrict__ cnt, const long long* __restrict__ off,
-                          const int* __restrict__ sj, const char4* __restrict__ ssh,
-                          const int* __restrict__ atom_struct, const float* __restrict__ hsplit,
-                          const float4* __restrict__ phi, const float4* __restrict__ plo, int* __restrict__ j,
-                          int* __restrict__ own, float4* __restrict__ r, char4* __restrict__ sh) {
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= (int64_t)N * cap) return;
-  const int i = (int)(g / cap), c = (int)(g % cap);
-  if (c >= cnt[i]) return;
-  const long long d = off[i] + c;
-  const int jj = sj[g];
-  const char4 sv = ssh[g];
+// Copies the per-atom slots of both lists into the CSR lists and forms r_ij,
+// one warp per atom: the atom's cell, position and offsets are read once per
+// warp and the lanes take its entries (the float-float arithmetic runs on
+// dense lanes).
+__global__ void __launch_bounds__(256) k_compact(int N, Slots sl, const int* __restrict__ cnt0,
+                                                 const int* __restrict__ cnt1, const long long* __restrict__ off0,
+                                                 const long long* __restrict__ off1,
+                                                 const int* __restrict__ atom_struct, const float* __restrict__ hsplit,
+                                                 const float4* __restrict__ phi, const float4* __restrict__ plo,
+                                                 int* __restrict__ j0, int* __restrict__ own0, float4* __restrict__ r0,
+                                                 char4* __restrict__ sh0, int* __restrict__ j1, int* __restrict__ own1,
+                                                 float4* __restrict__ r1, char4* __restrict__ sh1) {
+  const int i = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= N) return;  // the whole warp
   const float* Hs = hsplit + 18 * atom_struct[i];
-  const float4 pih = phi[i], pil = plo[i], pjh = phi[jj], pjl = plo[jj];
-  const int na = sv.x, nb = sv.y, nc = sv.z;
-  const float rx = pair_component(pjh.x, pjl.x, pih.x, pil.x, na, nb, nc, Hs[0], Hs[9], Hs[3], Hs[12], Hs[6], Hs[15]);
-  const float ry = pair_component(pjh.y, pjl.y, pih.y, pil.y, na, nb, nc, Hs[1], Hs[10], Hs[4], Hs[13], Hs[7], Hs[16]);
-  const float rz = pair_component(pjh.z, pjl.z, pih.z, pil.z, na, nb, nc, Hs[2], Hs[11], Hs[5], Hs[14], Hs[8], Hs[17]);
-  j[d] = jj;
-  own[d] = i;
-  r[d] = make_float4(rx, ry, rz, pjh.w);
-  sh[d] = sv;
+  float H[18];
+#pragma unroll
+  for (int q = 0; q < 18; ++q) H[q] = Hs[q];
+  const float4 pih = phi[i], pil = plo[i];
+  // the lanes run over the radial entries and then the angular ones as one range
+  const int n0 = cnt0[i], n1 = cnt1[i];  // at most the slots (the writing pass takes the batch otherwise)
+  const long long d00 = off0[i], d01 = off1[i];
+  for (int e = lane; e < n0 + n1; e += 32) {
+    const int L = e >= n0 ? 1 : 0, c = L ? e - n0 : e;
+    int* jo = L ? j1 : j0;
+    int* ow = L ? own1 : own0;
+    float4* ro = L ? r1 : r0;
+    char4* so = L ? sh1 : sh0;
+    {
+      const size_t g = (size_t)i * (L ? sl.cap[1] : sl.cap[0]) + c;
+      const long long d = (L ? d01 : d00) + c;
+      const int jj = (L ? sl.j[1] : sl.j[0])[g];
+      const char4 sv = (L ? sl.sh[1] : sl.sh[0])[g];
+      const float4 pjh = phi[jj], pjl = plo[jj];
+      const int na = sv.x, nb = sv.y, nc = sv.z;
+      const float rx = pair_component(pjh.x, pjl.x, pih.x, pil.x, na, nb, nc, H[0], H[9], H[3], H[12], H[6], H[15]);
+      const float ry = pair_component(pjh.y, pjl.y, pih.y, pil.y, na, nb, nc, H[1], H[10], H[4], H[13], H[7], H[16]);
+      const float rz = pair_component(pjh.z, pjl.z, pih.z, pil.z, na, nb, nc, H[2], H[11], H[5], H[14], H[8], H[17]);
+      jo[d] = jj;
+      ow[d] = i;
+      ro[d] = make_float4(rx, ry, rz, pjh.w);
+      so[d] = sv;
+    }
+  }
 }
 
 // Exclusive scan of int counts into int64 offsets: one block per 1024 items,
@@ -858,15 +879,10 @@ int build_lists(gnep_model* m, gnep_nlist* nl, cudaStream_t st) {
     k_to_int<<<blocks_for(N + 1, 256), 256, 0, st>>>(L == 0 ? off0 : off1, N + 1, P.off);
   }
   if (hmax[0] <= sl.cap[0] && hmax[1] <= sl.cap[1]) {
-    for (int L = 0; L < 2; ++L) {
-      PairList& P = nl->L[L];
-      const int64_t nt = (int64_t)N * sl.cap[L];
-      if (nt > 0)
-        k_compact<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(N, sl.cap[L], L == 0 ? cnt0 : cnt1,
-                                                                L == 0 ? off0 : off1, sl.j[L], sl.sh[L],
-                                                                nl->atom_struct, hsplit, phi, plo, P.j, P.owner,
-                                                                P.rij, P.shift);
-    }
+    if (N > 0)
+      k_compact<<<blocks_for((int64_t)N * 32, 256), 256, 0, st>>>(
+          N, sl, cnt0, cnt1, off0, off1, nl->atom_struct, hsplit, phi, plo, nl->L[0].j, nl->L[0].owner,
+          nl->L[0].rij, nl->L[0].shift, nl->L[1].j, nl->L[1].owner, nl->L[1].rij, nl->L[1].shift);
     GNEP_CHECK_LAUNCH("k_compact");
   } else {
     k_pairs<<<blocks_for((int64_t)N * 32, 128), 128, 0, st>>>(
