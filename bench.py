@@ -51,7 +51,7 @@ L2_BYTES = 129 * 1024 * 1024
 
 # ----------------------------------------------------------------- FLOP model
 
-def work_model_flops(nqr=9, kr=13, nqa=9, ka=13, ns=2, H=50, fb=True, N=1, PR=1, PA=1, L=24):
+def work_model_flops(nqr=9, kr=13, nqa=9, ka=13, ns=2, H=50, fb=True, N=1, PR=1, PA=1, L=24, lmax=4):
     """Algorithmic FP32 FLOPs per launch of each kernel, on the fixed work
     model of the method (FMA = 2 FLOP), counted per unit as the formulation
     needs it, whatever the kernels do:
@@ -65,11 +65,13 @@ def work_model_flops(nqr=9, kr=13, nqa=9, ka=13, ns=2, H=50, fb=True, N=1, PR=1,
       sweep 4 (c-gradient)   radial pair 8K + 4 N_q^R K;
                              angular pair 8K + 120 + 6 N_q^A L + 6 N_q^A K
       network                atom 4 N_des H (forward), 8 N_des H (backward)
-    with K the basis functions, N_q the channels and L = 24 (l, m) components.
+    with K the basis functions, N_q the channels and L = 24 (l, m) components
+    (l_max 4; lmax sets the angular descriptor columns, L is passed with it,
+    and the per-pair constants stay those of l_max 4).
     Each sweep's radial part is charged to the kernel that does it (the radial
     force is fused into the force gather, the radial c-gradient works on
     per-atom basis sums but is charged per pair here)."""
-    D = nqr + 4 * nqa + (nqa if fb else 0)
+    D = nqr + lmax * nqa + (nqa if fb else 0)
     q4 = 60 * nqa if fb else 0
     f = {}
     f["desc_radial"] = PR * (15 + 4 * kr + 2 * nqr * kr)
@@ -932,6 +934,65 @@ def report_small_batch(args):
                       "steps": args.steps, "by_batch_structures": out, "source_sha": csrc_sha()}), flush=True)
 
 
+def report_lmax(args):
+    """Angular degrees above 4 (App. B, B5-B8): the training step on the
+    256-structure workload with n_max 4/4, basis 8/8 and 30 hidden neurons at
+    l_max 4 (3-body), 6 (3-body) and 8 (4-body), the compiled shapes of the
+    higher degrees, in the FP32 form: the graph-replayed step time (`--steps`
+    replays after `--warmup`; the step's data exceed L2), atoms/s, each
+    kernel's time from the library's per-stage events, and the work model's
+    FLOPs of the step against the FP32 peak."""
+    import torch
+    from paper_2507_00528_gb300 import build as gbuild
+    gbuild.build()
+    from paper_2507_00528_gb300 import gnep, synth
+    batch = synth.make_config(2)
+    props = torch.cuda.get_device_properties(0)
+    sm_max = float(measured_peaks().get("sm_max_mhz", 2070.0))
+    peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
+    out = {}
+    for lmax, fb in ((4, False), (6, False), (8, True)):
+        kw = dict(n_max=(4, 4), basis=(8, 8), l_max=lmax, four_body=fb, hidden=30)
+        teacher = gnep.GNEP(**kw, seed=12)
+        nl = teacher.neighbors(gnep.DeviceBatch.from_host(batch))
+        PR, PA = nl.info()
+        teacher.compute_scale(nl)
+        y = teacher.teacher_labels(nl, batch.sizes(), **LAMBDAS)
+        student = gnep.GNEP(**kw, seed=11)
+        student.set_scale(teacher.get_scale())
+        gr = gnep.TrainGraph(student, nl, y, 1e-3, 1e-5, 10, args.steps + args.warmup + 10)
+        for _ in range(args.warmup):
+            gr.launch()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            gr.launch()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        kernels = gr.kernel_count()
+        gr.close()
+        prof = {}
+        for _ in range(5):
+            for k, v in student_profile(student, nl, y, gnep):
+                prof[k] = prof.get(k, 0.0) + v / 5
+        student.sync_status()
+        fl = work_model_flops(nqr=5, kr=9, nqa=5, ka=9, H=30, fb=fb, N=batch.n_atoms, PR=PR, PA=PA,
+                              L=lmax * (lmax + 2), lmax=lmax)
+        step_fl = sum(fl.values())
+        out[str(lmax)] = {"four_body": fb, "n_desc": student.n_des, "n_params": student.n_params,
+                          "ms_per_step": round(ms, 4), "atoms_per_s": batch.n_atoms / (ms / 1e3),
+                          "kernels_per_step": kernels, "stage_ms": {k: round(v, 4) for k, v in prof.items()},
+                          "work_model_gflop": round(step_fl / 1e9, 3),
+                          "work_model_tflops": round(step_fl / (ms / 1e3) / 1e12, 2),
+                          "fp32_frac": round(step_fl / (ms / 1e3) / 1e12 / peak, 3)}
+        del gr, nl, teacher, student
+    print(json.dumps({"report": "lmax", "workload": "sbte_256_structures_32-400_atoms_nmax4_basis8_h30",
+                      "precision": "fp32", "steps": args.steps, "n_atoms": batch.n_atoms,
+                      "fp32_peak_tflops": round(peak, 2), "by_lmax": out, "source_sha": csrc_sha()}), flush=True)
+
+
 def report_step(args):
     """A driver for profiler captures: the benchmark model and batch, then
     `--steps` loss + gradient evaluations in `--precision` (no timing, no
@@ -967,7 +1028,8 @@ def main():
                     help="times the K timed steps are repeated (the median repeat is reported)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--report", choices=["precision", "epoch", "batch-size", "small-batch", "step"], default=None,
+    ap.add_argument("--report", choices=["precision", "epoch", "batch-size", "small-batch", "step", "lmax"],
+                    default=None,
                     help="a workload report instead of the headline line")
     ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--batches", default="1,4,16,64",
@@ -989,6 +1051,8 @@ def main():
         report_small_batch(args)
     elif args.report == "step":
         report_step(args)
+    elif args.report == "lmax":
+        report_lmax(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
