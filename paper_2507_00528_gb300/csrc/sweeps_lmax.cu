@@ -38,6 +38,7 @@ namespace {
 
 constexpr int kHiWarps = 4;   // warps (atoms in flight) per block
 constexpr int kHiChunk = 32;  // pairs per chunk (one per lane)
+constexpr int kForcePairs = 10;  // pairs per round of the force sweep (three lanes each)
 
 constexpr double csqrt(double x) {  // square root by Newton's method, for compile-time constants
   double r = x > 1.0 ? x : 1.0;
@@ -155,6 +156,15 @@ template <class C>
 constexpr size_t hi_smem() {
   return kHiWarps * sizeof(HiSm<C>);
 }
+// The force sweep keeps only the atom's rows per warp.
+template <class C>
+struct HiForceSm {
+  float A[C::NQA][C::NLX];
+};
+template <class C>
+constexpr size_t hi_force_smem() {
+  return kHiWarps * sizeof(HiForceSm<C>);
+}
 
 // ------------------------------------------------------------- sweep 1
 
@@ -253,7 +263,8 @@ __global__ void __launch_bounds__(32 * kHiWarps) k_force_hi(int N, DevModel dm, 
   extern __shared__ float4 smraw[];
   __shared__ float cA[C::NCA];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  HiSm<C>& sm = reinterpret_cast<HiSm<C>*>(smraw)[warp];
+  HiForceSm<C>& sm = reinterpret_cast<HiForceSm<C>*>(smraw)[warp];
+  const int fslot = lane / 3, fdir = lane - 3 * fslot;  // pair slot and direction of this lane
   for (int q = threadIdx.x; q < C::NCA; q += blockDim.x) cA[q] = dm.params[dm.off_cA + q];
   __syncthreads();
   for (int i = blockIdx.x * kHiWarps + warp; i < N; i += gridDim.x * kHiWarps) {
@@ -273,35 +284,40 @@ __global__ void __launch_bounds__(32 * kHiWarps) k_force_hi(int N, DevModel dm, 
       for (int m = 0; m < 5; ++m) sm.A[lane][3 + m] = fmaf(e4, g4[m], sm.A[lane][3 + m]);
     }
     __syncwarp();
-    for (int p = p0 + lane; p < p1; p += 32) {
-      const float4 r = rij[p];
-      const int J = (int)r.w;
-      const float rr = sqrtf(r.x * r.x + r.y * r.y + r.z * r.z), ri = 1.f / rr;
-      const float ux = r.x * ri, uy = r.y * ri, uz = r.z * ri;
-      float f[KA], fp[KA];
-      radial_basis_d<KA>(rr, dm.rca_inv, f, fp);
-      const float* c = cA + (I * C::NS + J) * NQA * KA;
-      float g[NQA], gp[NQA];
+    // Lane 3 s + e takes Cartesian direction e of the round's pair s (ten
+    // pairs a round; an atom has about eight angular pairs, so a pair per
+    // lane with the three directions in turn left most lanes idle).
+    for (int pb = p0; pb < p1; pb += kForcePairs) {
+      const int p = pb + fslot;
+      const bool act = fslot < kForcePairs && p < p1;
+      float P = 0.f, vd = 0.f, ux = 0.f, uy = 0.f, uz = 0.f;
+      if (act) {
+        const float4 r = rij[p];
+        const int J = (int)r.w;
+        const float rr = sqrtf(r.x * r.x + r.y * r.y + r.z * r.z), ri = 1.f / rr;
+        ux = r.x * ri;
+        uy = r.y * ri;
+        uz = r.z * ri;
+        float f[KA], fp[KA];
+        radial_basis_d<KA>(rr, dm.rca_inv, f, fp);
+        const float* c = cA + (I * C::NS + J) * NQA * KA;
+        float g[NQA], gp[NQA];
 #pragma unroll
-      for (int n = 0; n < NQA; ++n) {
-        float a1 = 0.f, a2 = 0.f;
+        for (int n = 0; n < NQA; ++n) {
+          float a1 = 0.f, a2 = 0.f;
 #pragma unroll
-        for (int k = 0; k < KA; ++k) {
-          a1 = fmaf(c[n * KA + k], f[k], a1);
-          a2 = fmaf(c[n * KA + k], fp[k], a2);
+          for (int k = 0; k < KA; ++k) {
+            a1 = fmaf(c[n * KA + k], f[k], a1);
+            a2 = fmaf(c[n * KA + k], fp[k], a2);
+          }
+          g[n] = a1;
+          gp[n] = a2;
         }
-        g[n] = a1;
-        gp[n] = a2;
-      }
-      // One Cartesian direction e per pass: D_q = grad B_q . e (the printed
-      // forms for l <= 4, the recurrence with one dual component for l >= 5),
-      // V_e = sum_q ghat_q D_q; the first pass also forms P = sum_q ghat'_q B_q.
-      float P = 0.f, V[3];
-#pragma unroll 1
-      for (int dir = 0; dir < 3; ++dir) {
-        const float ex = dir == 0 ? 1.f : 0.f, ey = dir == 1 ? 1.f : 0.f, ez = dir == 2 ? 1.f : 0.f;
-        const float ue = dir == 0 ? ux : (dir == 1 ? uy : uz);
-        float vd = 0.f;
+        // direction e: D_q = grad B_q . e (the printed forms for l <= 4, the
+        // recurrence with one dual component for l >= 5), V_e = sum_q ghat_q
+        // D_q; direction 0 also forms P = sum_q ghat'_q B_q.
+        const float ex = fdir == 0 ? 1.f : 0.f, ey = fdir == 1 ? 1.f : 0.f, ez = fdir == 2 ? 1.f : 0.f;
+        const float ue = fdir == 0 ? ux : (fdir == 1 ? uy : uz);
         {
           float Bl[NLM], Dl[NLM];
           harmonics_dir(ux, uy, uz, ri, ex, ey, ez, Bl, Dl);
@@ -314,7 +330,7 @@ __global__ void __launch_bounds__(32 * kHiWarps) k_force_hi(int N, DevModel dm, 
               ghp = fmaf(gp[n], sm.A[n][q], ghp);
             }
             vd = fmaf(gh, Dl[q], vd);
-            if (dir == 0) P = fmaf(ghp, Bl[q], P);
+            if (fdir == 0) P = fmaf(ghp, Bl[q], P);
           }
         }
         Dn<1> X = dn<1>(ux), Y = dn<1>(uy), Z = dn<1>(uz);
@@ -327,11 +343,12 @@ __global__ void __launch_bounds__(32 * kHiWarps) k_force_hi(int N, DevModel dm, 
             ghp = fmaf(gp[n], sm.A[n][q], ghp);
           }
           vd = fmaf(gh, (h.d[0] - (float)l * h.v * ue) * ri, vd);
-          if (dir == 0) P = fmaf(ghp, h.v, P);
+          if (fdir == 0) P = fmaf(ghp, h.v, P);
         });
-        V[dir] = vd;
       }
-      dA[p] = make_float4(P * ux + V[0], P * uy + V[1], P * uz + V[2], 0.f);
+      // directions 1 and 2 of the pair to its direction-0 lane
+      const float v1 = __shfl_down_sync(0xffffffffu, vd, 1), v2 = __shfl_down_sync(0xffffffffu, vd, 2);
+      if (act && fdir == 0) dA[p] = make_float4(P * ux + vd, P * uy + v1, P * uz + v2, 0.f);
     }
     __syncwarp();
   }
@@ -597,7 +614,7 @@ template <class C>
 int hi_setup() {
   const int sm = (int)hi_smem<C>();
   GNEP_CUDA(cudaFuncSetAttribute(k_desc_hi<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-  GNEP_CUDA(cudaFuncSetAttribute(k_force_hi<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  GNEP_CUDA(cudaFuncSetAttribute(k_force_hi<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hi_force_smem<C>()));
   GNEP_CUDA(cudaFuncSetAttribute(k_tangent_hi<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
   GNEP_CUDA(cudaFuncSetAttribute(k_cgrad_hi<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
   return GNEP_OK;
@@ -618,7 +635,7 @@ int hi_force_angular(const gnep_model* m, const gnep_nlist* nl, cudaStream_t st,
                      float4* dA) {
   const int N = nl->n_atoms;
   if (N == 0 || nl->L[1].n == 0) return GNEP_OK;
-  (void)launch_pdl(k_force_hi<C>, hi_grid(N), 32 * kHiWarps, hi_smem<C>(), st, N, m->dev(), nl->type, nl->L[1].off,
+  (void)launch_pdl(k_force_hi<C>, hi_grid(N), 32 * kHiWarps, hi_force_smem<C>(), st, N, m->dev(), nl->type, nl->L[1].off,
                                                                  nl->L[1].rij, S, Ep, dA);
   GNEP_CHECK_LAUNCH("k_force_hi");
   return GNEP_OK;
